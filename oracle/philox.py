@@ -1,0 +1,124 @@
+"""Philox4x32-10 and the sampler's random-draw contract (oracle side).
+
+Philox4x32-10 is the counter-based generator of Salmon, Moraes, Dror and
+Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11): ten rounds of
+two 32x32->64-bit multiplications on a 4-word counter with a 2-word key
+bumped by the Weyl constants after every round.  Implemented here from that
+published definition in numpy uint32/uint64 arithmetic.
+
+Parity: pinned by the GPU test that compares this function with the
+independent device implementation shipped in CUDA's curand header
+(`curand_Philox4x32_10(counter, key)`), and by chi-square uniformity and
+bijectivity checks on the CPU.
+
+Draw contract (shared by definition with the CUDA path, implemented
+independently on each side).  key = (seed mod 2^32, seed div 2^32);
+counter = (index, sweep, chain, phase << 24 | sub).
+
+* dual bit of edge slot e, table entry k, chain c, sweep t:
+    prefix byte  = byte (k mod 16) of Philox(e, t, c, DUAL    << 24 | k div 16)
+    low 16 bits  = half (k mod 8)  of Philox(e, t, c, DUAL_LO << 24 | k div 8)
+    U24 = prefix << 16 | low16,  u = (U24 + 1/2) / 2^24,  theta = [u < p]
+  (bytes and halves are little-endian within the four 32-bit words, words in
+  order 0..3).
+* label draw of site v, chain c, sweep t (plain sweep):
+    U = word 0 of Philox(v, t, c, PRIMAL << 24),  u = ((U >> 8) + 1/2) / 2^24
+* label draw inside a tree block (blocked sweep): phase FFBS, same layout.
+* initial label of site v, chain c:  a = ((U >> 8) * L) >> 24 with U = word 0 of
+  Philox(v, 0, c, INIT << 24).
+* block offset of the blocked sweep t: o_d = word d of Philox(0, t, 0, SPLASH << 24) >> 30.
+* learned proposal (block b, chain c, sweep t): proposal bytes/words from
+  phase PROPOSAL, accept uniform from phase ACCEPT (word 0, 24-bit form).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+PHILOX_M0 = np.uint64(0xD2511F53)
+PHILOX_M1 = np.uint64(0xCD9E8D57)
+PHILOX_W0 = np.uint32(0x9E3779B9)
+PHILOX_W1 = np.uint32(0xBB67AE85)
+
+PH_DUAL = 1
+PH_DUAL_LO = 2
+PH_PRIMAL = 3
+PH_INIT = 4
+PH_FFBS = 5
+PH_SPLASH = 6
+PH_PROPOSAL = 7
+PH_ACCEPT = 8
+
+_MASK32 = np.uint64(0xFFFFFFFF)
+
+
+def philox4x32_10(c0, c1, c2, c3, k0, k1):
+    """Philox4x32-10 on broadcastable uint32 arrays.  Returns four uint32 arrays."""
+    c0 = np.asarray(c0, np.uint32); c1 = np.asarray(c1, np.uint32)
+    c2 = np.asarray(c2, np.uint32); c3 = np.asarray(c3, np.uint32)
+    k0 = np.asarray(k0, np.uint64) & _MASK32; k1 = np.asarray(k1, np.uint64) & _MASK32
+    c0, c1, c2, c3 = np.broadcast_arrays(c0, c1, c2, c3)
+    c0 = c0.copy(); c1 = c1.copy(); c2 = c2.copy(); c3 = c3.copy()
+    for r in range(10):
+        p0 = PHILOX_M0 * c0.astype(np.uint64)
+        p1 = PHILOX_M1 * c2.astype(np.uint64)
+        hi0 = (p0 >> np.uint64(32)).astype(np.uint32); lo0 = (p0 & _MASK32).astype(np.uint32)
+        hi1 = (p1 >> np.uint64(32)).astype(np.uint32); lo1 = (p1 & _MASK32).astype(np.uint32)
+        n0 = hi1 ^ c1 ^ k0.astype(np.uint32)
+        n2 = hi0 ^ c3 ^ k1.astype(np.uint32)
+        c0, c1, c2, c3 = n0, lo1, n2, lo0
+        if r < 9:                                   # Weyl key schedule, mod 2^32
+            k0 = (k0 + np.uint64(PHILOX_W0)) & _MASK32
+            k1 = (k1 + np.uint64(PHILOX_W1)) & _MASK32
+    return c0, c1, c2, c3
+
+
+def seed_key(seed: int):
+    seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    return np.uint32(seed & 0xFFFFFFFF), np.uint32(seed >> 32)
+
+
+def _words(index, sweep, chain, c3, seed):
+    k0, k1 = seed_key(seed)
+    return np.stack(philox4x32_10(index, sweep, chain, c3, k0, k1), axis=-1)   # [..., 4]
+
+
+def dual_u24(edge, k, chain, sweep, seed):
+    """24-bit integer uniforms U24 of dual draws; all arguments broadcast."""
+    edge = np.asarray(edge, np.int64); k = np.asarray(k, np.int64); chain = np.asarray(chain, np.int64)
+    hi = _words(edge, sweep, chain, (PH_DUAL << 24) | (k >> 4), seed)
+    kk = np.broadcast_to(k, hi.shape[:-1])
+    wsel = np.take_along_axis(hi, ((kk & 15) >> 2)[..., None], axis=-1)[..., 0]
+    prefix = (wsel >> (8 * (kk & 3)).astype(np.uint32)) & np.uint32(0xFF)
+    lo = _words(edge, sweep, chain, (PH_DUAL_LO << 24) | (k >> 3), seed)
+    wsel = np.take_along_axis(lo, ((kk & 7) >> 1)[..., None], axis=-1)[..., 0]
+    low = (wsel >> (16 * (kk & 1)).astype(np.uint32)) & np.uint32(0xFFFF)
+    return (prefix.astype(np.int64) << 16) | low.astype(np.int64)
+
+
+def u24_to_unit(u24):
+    """u = (U24 + 1/2) / 2^24, exactly representable in float32 and float64."""
+    return (np.asarray(u24, np.float64) + 0.5) / 16777216.0
+
+
+def dual_uniform(edge, k, chain, sweep, seed):
+    return u24_to_unit(dual_u24(edge, k, chain, sweep, seed))
+
+
+def site_uniform(site, chain, sweep, seed, phase=PH_PRIMAL):
+    """Uniform of a label draw (plain sweep: phase PRIMAL; tree blocks: FFBS)."""
+    w = _words(np.asarray(site, np.int64), sweep, np.asarray(chain, np.int64), phase << 24, seed)[..., 0]
+    return u24_to_unit(w >> np.uint32(8))
+
+
+def init_labels(n_vars: int, n_labels: int, n_chains: int, seed: int):
+    """Initial labels [C][N]: a = ((U >> 8) * L) >> 24 with U from phase INIT."""
+    v = np.arange(n_vars, dtype=np.int64)[None, :]
+    c = np.arange(n_chains, dtype=np.int64)[:, None]
+    w = _words(v, 0, c, PH_INIT << 24, seed)[..., 0]
+    return (((w >> np.uint32(8)).astype(np.int64) * n_labels) >> 24).astype(np.int64)
+
+
+def splash_offset(sweep: int, seed: int):
+    """Block-grid offset (ox, oy, oz) in [0,4)^3 for blocked sweep `sweep`."""
+    w = _words(0, sweep, 0, PH_SPLASH << 24, seed)
+    return tuple(int(x) >> 30 for x in w[:3])
