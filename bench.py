@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Throughput of the primal-dual Gibbs sweep on GB300.
+
+One step = one full sweep of the sampler over the whole model for every chain:
+the dual half-step (theta | x over all edges), the primal half-step (x | theta
+over all sites) and the marginal-count accumulation.  Default workload: the
+3-D 6-neighbour Potts grid 128^3 (2,097,152 sites, 6,242,304 edges), L = 8,
+random positive tables exp(U[-0.3, 0.3]), unaries N(0, 1), 64 chains.
+
+Metric: site-updates/s (= chains x sites x sweeps / device time).  Multi-GPU
+runs (torchrun) give every rank its own independent chains (weak scaling, no
+data-path collective); value = all ranks' site-updates / max time.
+
+`--impl reference` times the CPU oracle (the float64 numpy statement of the
+method) on a bounded sample of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "site-updates/s"
+
+WORKLOADS = {
+    # name: (generator, chains, description)
+    "potts3d": (lambda: __import__("paper_1611_06684_gb300.workloads", fromlist=["x"]).potts_grid3d(128, L=8, seed=0),
+                64, "3-D 6-neighbour Potts grid 128^3, L=8, tables exp(U[-0.3,0.3]), unaries N(0,1), 64 chains"),
+    "ising32": (lambda: __import__("paper_1611_06684_gb300.workloads", fromlist=["x"]).ising_grid(32, 32, seed=0),
+                1, "2-D Ising grid 32x32, L=2, h~N(0,0.5^2), J~U[0,0.3], 1 chain"),
+    "dense4096": (lambda: __import__("paper_1611_06684_gb300.workloads", fromlist=["x"]).dense_potts(4096, L=4, seed=0),
+                  16, "fully connected N=4096 (8,386,560 edges), L=4, w~N(0,(0.2/64)^2), unaries N(0,1), 16 chains"),
+}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def clocks_start(path):
+    try:
+        f = open(path, "w")
+        p = subprocess.Popen(["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                              "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
+                             stdout=f, stderr=subprocess.DEVNULL)
+        return p, f
+    except Exception:
+        return None, None
+
+
+def clocks_stop(handle, path, gpu_index):
+    p, f = handle
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    f.close()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9 or parts[0] != str(gpu_index):
+            continue
+        try:
+            sm.append(float(parts[1])); mx.append(float(parts[2]))
+        except ValueError:
+            continue
+        for n, v in zip(names, parts[5:9]):
+            if v.lower() == "active":
+                reasons.add(n)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def alu_peak_philox_calls(sm_mhz):
+    """Philox4x32-10 calls/s bound of the integer-multiply pipe: 152 SMs x 64
+    32-bit multiply results per SM per clock; one call needs 10 rounds x 2
+    products x 2 halves = 40 multiply results."""
+    return 152 * 64 / 40.0 * sm_mhz * 1e6
+
+
+def kernel_work(name, model_info, C):
+    """Algorithmic work of one launch: (philox calls, bytes) for the kernel."""
+    E, N, L, m = model_info["E"], model_info["N"], model_info["L"], model_info["m"]
+    W = (m + 31) // 32
+    calls_dual = E * C * math.ceil(m / 16)
+    if name == "k_dual":
+        return calls_dual, E * m * 4 + E * C * W * 4 + N * C
+    if name == "k_primal":
+        return N * C, 2 * E * C * W * 4 + 2 * E * m * 4 + N * L * 8 + 2 * E * 8 + 2 * N * C + N * 16
+    if name == "k_primal<fused>":
+        return 2 * calls_dual + N * C, 2 * E * m * 4 + N * L * 8 + 2 * E * 8 + 2 * N * C
+    if name == "k_accumulate":
+        return 0, N * C + 2 * N * L * 4
+    return 0, 0
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_1611_06684_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    from paper_1611_06684_gb300 import mrf as M
+    gen, C, desc = WORKLOADS[args.workload]
+    model = gen()
+    mode = {"plain": M.MODE_PLAIN, "fused": M.MODE_FUSED}[args.mode]
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        h = M.MRF(model.n_vars, model.n_labels, C, seed=args.seed + 1000003 * rank, stream=stream.cuda_stream,
+                  kernel_timing=True)
+        h.set_factors(model.unary, model.src, model.dst, model.pair)
+    inf = h.info()
+    minfo = dict(E=inf.n_edge_slots, N=inf.n_vars, L=inf.n_labels, m=inf.n_entries)
+    # warm-up
+    h.sweep(args.warmup, mode)
+    h.kernel_times()
+    torch.cuda.synchronize()
+    clk_path = os.path.join(tempfile.gettempdir(), f"bench_clocks_{rank}.csv")
+    clk = clocks_start(clk_path)
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    h.sweep(args.steps, mode)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    clocks = clocks_stop(clk, clk_path, local)
+    ktimes = h.kernel_times()
+    if ws > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    units = ws * C * model.n_vars * args.steps
+    value = units / (ms_total / 1e3)
+    launches = sum(n for _, n in ktimes.values()) + args.steps   # + k_advance per sweep
+
+    # roofline of the dominant kernel (device time inside the timed region)
+    peaks, peak_src = load_peaks()
+    dom = max(ktimes, key=lambda k: ktimes[k][0])
+    dom_ms = ktimes[dom][0] / ktimes[dom][1]
+    calls, nbytes = kernel_work(dom, minfo, C)
+    sm_mhz = clocks["sm_mhz"] if clocks else peaks.get("sm_max_mhz", 2070.0)
+    hbm = {"bound": "hbm", "achieved": nbytes / (dom_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    hbm["frac"] = hbm["achieved"] / hbm["peak"]
+    if calls and dom in ("k_dual", "k_primal<fused>"):
+        alu_peak = alu_peak_philox_calls(peaks.get("sm_max_mhz", 2070.0))
+        roof = {"bound": "alu", "achieved": calls / (dom_ms / 1e3) / 1e9, "peak": alu_peak / 1e9,
+                "unit": "G Philox4x32-10 calls/s", "frac": calls / (dom_ms / 1e3) / alu_peak, "traffic": None,
+                "kernel": dom, "peak_source": "derived: 152 SMs x 64 int32 multiplies/clk x 2070 MHz / 40 per call",
+                "hbm_view": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac")}}
+    else:
+        roof = dict(hbm, traffic=None, kernel=dom, peak_source=f"MEASURED_PEAKS.json hbm_gbs ({peak_src})")
+
+    # end to end through the C ABI with pinned host buffers: labels in, sweep, labels out
+    e2e = None
+    if not args.no_e2e:
+        x_host = torch.empty((C, model.n_vars), dtype=torch.uint8).pin_memory()
+        h.get_labels_into(x_host)
+        h2 = M.MRF(model.n_vars, model.n_labels, C, seed=args.seed + 1000003 * rank, stream=stream.cuda_stream)
+        with torch.cuda.stream(stream):
+            h2.set_factors(model.unary, model.src, model.dst, model.pair)
+        k_e2e = max(3, min(args.steps, 20))
+        h2.set_labels(x_host); h2.sweep(1, mode); h2.get_labels_into(x_host)     # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            h2.set_labels(x_host)
+            h2.sweep(1, mode)
+            h2.get_labels_into(x_host)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([dt], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": ws * C * model.n_vars * k_e2e / dt, "unit": METRIC,
+               "h2d_bytes_per_step": C * model.n_vars, "d2h_bytes_per_step": C * model.n_vars,
+               "steps": k_e2e, "api": "mrf_set_labels(host) + mrf_sweep(1) + mrf_get_labels(host), pinned buffers"}
+        h2.close()
+
+    out = None
+    if rank == 0:
+        cpu = None if (ws > 1 or args.no_cpu) else cpu_baseline(args)
+        out = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (f64 unary/field accumulation, u32 integer draws)",
+            "data": "synthetic (seeded generators)",
+            "config": {"workload": args.workload, "description": desc, "n_vars": model.n_vars,
+                       "n_edges": model.n_edges, "n_labels": model.n_labels, "chains": C, "mode": args.mode,
+                       "dual_bits_per_edge": inf.n_entries, "layout": ["pivot", "diag"][inf.layout],
+                       "l2": "inputs larger than L2 (tables and theta are GBs); no flush needed",
+                       "parallelism": f"replicas x{ws} (independent chains per GPU)"},
+            "roofline": roof,
+            "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in ktimes.items()},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+    h.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+class OracleSample:
+    """The oracle, as it stands, on a bounded sample of the workload."""
+
+    def __init__(self, args):
+        from paper_1611_06684_gb300 import workloads as wl
+        from oracle import decompose as dc, philox as ph
+        if args.workload == "potts3d":
+            self.C = 2
+            model = wl.potts_grid3d(24, L=8, seed=0)
+            self.sample = "{C} chains x {S} sweeps of a 24^3 sub-lattice with the same L=8 table and unary distributions"
+        elif args.workload == "dense4096":
+            self.C = 1
+            model = wl.dense_potts(256, L=4, w_std=0.2 / 64, seed=0)
+            self.sample = "{C} chain x {S} sweeps of a N=256 fully connected model with the same L=4 distributions"
+        else:
+            self.C = 1
+            model = WORKLOADS[args.workload][0]()
+            self.sample = "{C} chain x {S} sweeps of the full workload"
+        self.model = model
+        self.dec = dc.decompose(model)
+        self.seed = args.seed
+        self.x = ph.init_labels(model.n_vars, model.n_labels, self.C, args.seed)
+        self.t = 0
+
+    def sweep(self):
+        """One oracle sweep; returns its wall time in seconds."""
+        from oracle import sampler
+        t0 = time.perf_counter()
+        self.x = sampler.sweep(self.dec, self.x, self.t, self.seed)["x"]
+        self.t += 1
+        return time.perf_counter() - t0
+
+    @property
+    def units_per_sweep(self):
+        return self.C * self.model.n_vars
+
+
+def cpu_baseline(args, budget_s=10.0):
+    o = OracleSample(args)
+    el, S = 0.0, 0
+    while el < budget_s:
+        el += o.sweep(); S += 1
+    return {"value": o.units_per_sweep * S / el, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": o.sample.format(C=o.C, S=S), "seconds": el,
+            "host_cores_available": len(os.sched_getaffinity(0))}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    o = OracleSample(args)
+    for _ in range(args.warmup):
+        o.sweep()
+    secs = [o.sweep() for _ in range(args.steps)]
+    mean_s = statistics.mean(secs)
+    value = o.units_per_sweep / mean_s
+    sample = o.sample.format(C=o.C, S=1) + " per step"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generators)",
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload][2],
+                       "reference": "CPU float64 oracle (oracle/), one bounded-sample sweep per step"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value, "unit": METRIC},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="potts3d", choices=list(WORKLOADS))
+    ap.add_argument("--mode", default="plain", choices=["plain", "fused"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+    else:
+        out = run_ours(args, ws, rank, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

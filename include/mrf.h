@@ -1,0 +1,171 @@
+/*
+ * mrf.h -- C ABI of the GB300 primal-dual Gibbs sampler (libmrf.so).
+ *
+ * Method: "Probabilistic Duality for Parallel Gibbs Sampling without Graph
+ * Coloring" (Mescheder, Nowozin, Geiger).  A discrete pairwise MRF with
+ * strictly positive factors (abstract; Section 4, Hammersley-Clifford form)
+ *
+ *     p(x) ~ exp( sum_v u_v(x_v) + sum_e w_e(x_s(e), x_t(e)) ),  x_v in {0..L-1}
+ *
+ * is sampled by the two-block Gibbs sampler of Section 5.1 on the dual
+ * representation of Sections 4.1-4.2: every dualised entry of every pairwise
+ * table gets one binary dual variable theta; one sweep draws all theta | x
+ * (fully parallel over edges) and then all x | theta (fully parallel over
+ * sites), without any graph coloring.  Section 5.4's blocked variant keeps a
+ * spanning forest of every lattice block exact and samples it by
+ * forward-filtering/backward-sampling.
+ *
+ * Conventions for every entry point
+ *  - Return value: MRF_OK or an error status; nothing aborts the process.
+ *    mrf_last_error() returns a text for the last failing call on a handle.
+ *  - ptr_kind: MRF_PTR_HOST for host memory, MRF_PTR_DEVICE for device
+ *    memory of the handle's device.  Inputs are copied; the caller keeps
+ *    ownership of every buffer it passes.
+ *  - All device work is ordered on the stream given to mrf_create; calls
+ *    that return data to a host pointer synchronise that stream.  A handle is
+ *    not thread-safe.
+ *  - Layouts are row-major, innermost index last.
+ *  - Random draws follow a fixed counter-based Philox4x32-10 contract keyed
+ *    by (seed, chain, sweep, site or edge slot), so results do not depend on
+ *    launch shapes and a run resumed at sweep t repeats the original run.
+ */
+#ifndef MRF_H
+#define MRF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mrf mrf_t;
+
+typedef enum {
+    MRF_OK = 0,
+    MRF_EINVAL = 1,      /* bad argument (null pointer, size, mode, state)      */
+    MRF_ENONFINITE = 2,  /* a log-potential is NaN or infinite (factor not > 0) */
+    MRF_ENOMEM = 3,      /* device allocation failed                             */
+    MRF_ECUDA = 4,       /* a CUDA call failed                                   */
+    MRF_ERANGE = 5,      /* index out of range, self-loop, L out of [2,16]       */
+    MRF_ETIMEOUT = 6,    /* a bounded device wait gave up                        */
+    MRF_ESTATE = 7       /* call not valid in the handle's current state         */
+} mrf_status;
+
+enum { MRF_PTR_HOST = 0, MRF_PTR_DEVICE = 1 };
+
+/* Sweep modes (mrf_sweep). */
+enum {
+    MRF_MODE_PLAIN = 0,  /* Section 5.1: dual kernel writes bit-packed theta,
+                            primal kernel gathers it over the CSR incidence  */
+    MRF_MODE_FUSED = 1,  /* same chain, theta regenerated at both endpoints
+                            from the counter-based RNG (never stored)        */
+    MRF_MODE_SPLASH = 2  /* Section 5.4 blocked sweep on a lattice (needs
+                            mrf_options.grid); 4x4x4 blocks, comb trees      */
+};
+
+/* Dualised table layout chosen by mrf_set_factors (mrf_info.layout). */
+enum { MRF_LAYOUT_PIVOT = 0, MRF_LAYOUT_DIAG = 1 };
+
+typedef struct {
+    int32_t grid_nx, grid_ny, grid_nz; /* lattice shape (site v = x + nx*(y + ny*z))
+                                          for MRF_MODE_SPLASH; 0 = not a lattice  */
+    int32_t record_logp;               /* 1: keep the last sweep's log p(x_v|.)
+                                          [C][N][L] for mrf_debug_logp            */
+    int32_t use_graphs;                /* 1 (default): replay sweeps as a CUDA graph */
+    int32_t schedule;                  /* primal schedule: 0 auto, 1 thread/site,
+                                          2 CTA/site (high degree)               */
+    int32_t kernel_timing;             /* 1: bracket every sweep kernel with CUDA
+                                          events (graphs off); see mrf_kernel_times */
+    int32_t reserved[7];
+} mrf_options;
+
+typedef struct {
+    int32_t n_vars, n_labels, n_chains, layout, n_entries;  /* m = dual bits per edge */
+    int64_t n_edges;        /* live edges                                         */
+    int64_t n_edge_slots;   /* slots (live + free), the RNG index space of edges  */
+    int64_t sweep_index;    /* index t of the next sweep                          */
+    int64_t n_samples;      /* label samples accumulated per site (sweeps x chains) */
+    double log_const;       /* log p~(x) = log sum_theta p~(x,theta) + log_const  */
+} mrf_info;
+
+/* Fill *opt with defaults (no lattice, no logp record, graphs on, auto schedule). */
+void mrf_default_options(mrf_options* opt);
+
+/* Create a sampler for n_vars sites with n_labels in [2,16] labels and
+ * n_chains independent chains, keyed by seed.  cuda_stream is a
+ * cudaStream_t (0 = legacy default stream) on the current device.
+ * Initial labels are drawn from the contract (uniform over labels). */
+mrf_status mrf_create(mrf_t** out, int32_t n_vars, int32_t n_labels, int32_t n_chains,
+                      uint64_t seed, const mrf_options* opt, void* cuda_stream);
+
+/* Set the model (Section 4): unary_log [n_vars][L]; n_edges pairwise factors
+ * (src[e], dst[e]) with pair_log [n_edges][L][L], row = label of src.  Every
+ * value must be finite (strict positivity, abstract).  Duplicate (s,t) pairs
+ * are allowed and multiply (Theorem 1).  Runs the Section 4.1-4.2
+ * decomposition on the device: per dualised entry the dual weight tau and its
+ * sampling thresholds, and the folded unaries.  Edge e gets slot e.
+ * Errors: MRF_ENONFINITE, MRF_ERANGE (ids, self-loops), MRF_ENOMEM. */
+mrf_status mrf_set_factors(mrf_t* h, const float* unary_log, int64_t n_edges,
+                           const int32_t* src, const int32_t* dst, const float* pair_log,
+                           int32_t ptr_kind);
+
+/* Dynamic model (abstract, Section 6: factors added and removed between
+ * sweeps): remove the edges in slots edge_ids[0..n_remove) and add n_add new
+ * factors.  New edges take the freed slots in increasing slot order, then
+ * fresh slots; their slot ids are written to out_new_ids (host memory).
+ * Only the touched edges are re-decomposed; no coloring is maintained.
+ * Errors: MRF_ERANGE for a slot that is not live, MRF_ENONFINITE. */
+mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
+                            int64_t n_add, const int32_t* src, const int32_t* dst,
+                            const float* pair_log, int64_t* out_new_ids, int32_t ptr_kind);
+
+/* Run n_sweeps sweeps (Section 5.1 or 5.4) and accumulate label counts for
+ * sweeps with index >= burn-in.  Asynchronous on the handle's stream. */
+mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode);
+
+/* Estimated marginals out[n_vars][L] = counts / n_samples (float32) and the
+ * number of samples per site.  Synchronises. */
+mrf_status mrf_marginals(mrf_t* h, float* out, int64_t* n_samples, int32_t ptr_kind);
+
+/* Raw label counts [n_vars][L] (uint32) summed over chains.  Synchronises. */
+mrf_status mrf_get_counts(mrf_t* h, uint32_t* out, int32_t ptr_kind);
+
+/* Zero the counts; sweeps with index < sweep_index + burn_in_sweeps are not counted. */
+mrf_status mrf_reset_marginals(mrf_t* h, int32_t burn_in_sweeps);
+
+/* Labels of all chains, [n_chains][n_vars] uint8.  get synchronises. */
+mrf_status mrf_get_labels(mrf_t* h, uint8_t* out, int32_t ptr_kind);
+mrf_status mrf_set_labels(mrf_t* h, const uint8_t* in, int32_t ptr_kind);
+
+/* Index t of the next sweep (the RNG's sweep counter); set it to resume or
+ * to replay one sweep from a given state. */
+mrf_status mrf_set_sweep_index(mrf_t* h, int64_t t);
+
+mrf_status mrf_get_info(const mrf_t* h, mrf_info* out);
+
+/* Debug/parity views (host pointers; synchronise):
+ * tau [slots][m] signed dual weight (+tau for l>0, -tau for l<0, 0 inactive),
+ * thr [slots][m] packed thresholds, utilde [n_vars][L] folded unaries (float64). */
+mrf_status mrf_debug_tables(mrf_t* h, float* tau, uint32_t* thr, double* utilde);
+/* log p(x_v = a | .) of the last sweep [C][N][L] (needs record_logp) and the
+ * number of draws the device saw within 1e-6 of a decision boundary. */
+mrf_status mrf_debug_logp(mrf_t* h, float* out, uint64_t* boundary_draws);
+/* Bit-packed theta of the last PLAIN/SPLASH sweep [slots][C][ceil(m/32)] uint32. */
+mrf_status mrf_debug_theta(mrf_t* h, uint32_t* out);
+
+/* Kernel ids of mrf_kernel_times. */
+enum { MRF_K_DUAL = 0, MRF_K_PRIMAL = 1, MRF_K_FUSED = 2, MRF_K_POTENTIAL = 3, MRF_K_FFBS = 4,
+       MRF_K_ACCUMULATE = 5, MRF_K_COUNT = 6 };
+/* With options.kernel_timing: total device milliseconds ms[MRF_K_COUNT] and
+ * launch counts launches[MRF_K_COUNT] of every sweep kernel since the last
+ * call (CUDA events on the handle's stream); resets the totals.  Synchronises. */
+mrf_status mrf_kernel_times(mrf_t* h, double* ms, int64_t* launches);
+
+const char* mrf_last_error(const mrf_t* h);
+const char* mrf_status_string(mrf_status s);
+void mrf_destroy(mrf_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRF_H */

@@ -1,0 +1,89 @@
+// Internal declarations shared by the CUDA translation units of libmrf.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mrf.h"
+#include "philox.cuh"
+
+namespace mrfk {
+
+constexpr int kMaxLabels = 16;
+
+// Control block in device memory, read by every sweep kernel so that a
+// captured CUDA graph of one sweep can be replayed: the sweep index decides
+// the RNG counter and which half of the label double buffer is current.
+struct Ctl {
+    unsigned long long sweep;          // index t of the sweep being run / next
+    unsigned long long count_from;     // sweeps with t >= count_from are counted
+    unsigned long long boundary;       // draws within 1e-6 of a decision boundary
+    unsigned long long splash_offset;  // packed (ox | oy << 8 | oz << 16) of the last blocked sweep
+};
+
+// Dualised-entry layout: entry k <-> table position (i_k, j_k).
+template <int L, int LAYOUT>
+struct Ent {
+    static constexpr int M = (LAYOUT == MRF_LAYOUT_PIVOT) ? (L - 1) * (L - 1) : L;
+    static constexpr int W = (M + 31) / 32;
+    __host__ __device__ static constexpr int i(int k) { return LAYOUT == MRF_LAYOUT_PIVOT ? 1 + k / (L - 1) : k; }
+    __host__ __device__ static constexpr int j(int k) { return LAYOUT == MRF_LAYOUT_PIVOT ? 1 + k % (L - 1) : k; }
+};
+
+__host__ __device__ inline int n_entries(int L, int layout) {
+    return layout == MRF_LAYOUT_PIVOT ? (L - 1) * (L - 1) : L;
+}
+
+// Everything a sweep kernel needs, passed by value.
+struct SweepArgs {
+    int32_t N, C, L, M, W;
+    int64_t E;                 // edge slots
+    const int32_t* src;        // [E] (-1 = free slot)
+    const int32_t* dst;        // [E]
+    const float* tau;          // [E][M] signed dual weight
+    const uint32_t* thr;       // [E][M] packed thresholds
+    const float* resid;        // [E][L][L] exact tree-edge potentials (blocked sweep)
+    const int64_t* inc_ptr;    // [N+1]
+    const int2* inc;           // [2E] {edge*2 + side, neighbour}
+    const double* ut;          // [N][L] folded unaries
+    uint8_t* x;                // [2][N][C] label double buffer
+    uint32_t* theta;           // [E][C][W]
+    uint32_t* counts;          // [N][L]
+    float* logp;               // [C][N][L] or null
+    Ctl* ctl;
+    uint2 key;
+    int32_t grid_nx, grid_ny, grid_nz;
+};
+
+// Kernel launchers (sweep.cu, splash.cu, decompose.cu).  All return cudaGetLastError().
+cudaError_t launch_init_labels(const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_dual(const SweepArgs& a, int layout, cudaStream_t s);
+cudaError_t launch_primal(const SweepArgs& a, int layout, int schedule, cudaStream_t s);
+cudaError_t launch_fused(const SweepArgs& a, int layout, int schedule, cudaStream_t s);
+cudaError_t launch_accumulate(const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_advance(const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_splash(const SweepArgs& a, int layout, cudaStream_t s);
+cudaError_t launch_labels_to_abi(const uint8_t* x, uint8_t* y, int N, int C, cudaStream_t s);
+cudaError_t launch_labels_from_abi(const uint8_t* y, uint8_t* x, int N, int C, cudaStream_t s);
+cudaError_t launch_count_ge(const uint8_t* y, int64_t n, int L, unsigned long long* bad, cudaStream_t s);
+
+struct DecompArgs {
+    int32_t L, M, layout;
+    int64_t n;                 // edges to decompose
+    const int64_t* slots;      // [n] slot of each edge (null: slot = first_slot + i)
+    int64_t first_slot;
+    const float* pair;         // [n][L][L] raw log tables
+    float* tau;                // [E][M]
+    uint32_t* thr;             // [E][M]
+    double* fold;              // [E][2][L]
+    double* cst;               // [E] per-edge log constant
+    float* resid;              // [E][L][L] or null
+};
+cudaError_t launch_check_finite(const float* p, int64_t n, unsigned long long* bad, cudaStream_t s);
+cudaError_t launch_count_offdiag(const float* pair, int64_t n_edges, int L, unsigned long long* nz, cudaStream_t s);
+cudaError_t launch_decompose(const DecompArgs& a, cudaStream_t s);
+cudaError_t launch_fold_unary(const float* unary, const double* fold, const int64_t* inc_ptr, const int2* inc,
+                              int N, int L, double* ut, cudaStream_t s);
+
+}  // namespace mrfk

@@ -1,0 +1,146 @@
+// Factor decomposition of Sections 4.1-4.2 on the device (setup and edits).
+//
+// For every edge e with log-table w (L x L, row = label of the source):
+//  * PIVOT layout: l(i,j) = w(i,j) - w(i,0) - w(0,j) + w(0,0) for i, j >= 1;
+//    offsets w(a,0) - w(0,0) fold into the source unary, w(0,b) - w(0,0) into
+//    the destination unary, w(0,0) into the log constant.
+//  * DIAG layout (Potts-type tables, Section 4.2): l(a,a) = w(a,a), no offsets.
+// Every entry with l != 0 gets one dual bit (Section 4.2: none for 1-entries).
+// Its one-hot 2x2 factor [[1,1],[1,e^l]] factors as in Lemmas 2-4 and Theorem 2;
+// in closed form, with tau = 2 arccosh(e^{|l|/2}) evaluated stably as
+// tau = |l| + 2 log1p(sqrt(-expm1(-|l|))):
+//    l > 0:  q = -tau, beta1 = beta2 = tau, alpha1 = alpha2 = (l - tau)/2
+//    l < 0:  q = 0, beta1 = -tau, beta2 = tau, alpha1 = (l + tau)/2, alpha2 = (l - tau)/2
+// so the dual logit q + beta1 y + beta2 z takes one of {-tau, 0, +tau}.
+//
+// Stored per entry: tau_signed (= beta1; beta2 = |tau_signed|) as float, and a
+// packed threshold word: T+ = ceil(sigmoid(tau) 2^24 - 1/2) in bits 0..24,
+// d = T+ + T- - (2^24 - 1) in bits 25..26 (T- from sigmoid(-tau)), the sign of
+// l in bit 31; 0 marks an entry without a dual bit.  A draw with 24-bit
+// integer uniform U sets theta iff U < T for the case's threshold, which is
+// exactly u = (U + 1/2) / 2^24 < p.  All of this runs in float64.
+#include "common.cuh"
+
+#include <cmath>
+
+namespace mrfk {
+
+__global__ void k_check_finite(const float* p, int64_t n, unsigned long long* bad) {
+    unsigned long long cnt = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        cnt += !isfinite(p[i]);
+    if (cnt) atomicAdd(bad, cnt);
+}
+
+__global__ void k_count_offdiag(const float* pair, int64_t n_edges, int L, unsigned long long* nz) {
+    const int64_t n = n_edges * L * L;
+    unsigned long long cnt = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)((i / L) % L), c = (int)(i % L);
+        cnt += (r != c) && (pair[i] != 0.0f);
+    }
+    if (cnt) atomicAdd(nz, cnt);
+}
+
+__device__ inline uint32_t threshold24(double p) {
+    return (uint32_t)ceil(p * 16777216.0 - 0.5);
+}
+
+__global__ void k_decompose(DecompArgs a) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int L = a.L, M = a.M;
+    const int64_t e = a.slots ? a.slots[i] : a.first_slot + i;
+    const float* w = a.pair + i * L * L;
+    double fs[kMaxLabels], ft[kMaxLabels];
+    double cst = 0.0;
+    if (a.layout == MRF_LAYOUT_PIVOT) {
+        const double w00 = w[0];
+        for (int x = 0; x < L; ++x) {
+            fs[x] = (double)w[x * L] - w00;
+            ft[x] = (double)w[x] - w00;
+        }
+        cst = w00;
+    } else {
+        for (int x = 0; x < L; ++x) fs[x] = ft[x] = 0.0;
+    }
+    for (int k = 0; k < M; ++k) {
+        int ii, jj;
+        double l;
+        if (a.layout == MRF_LAYOUT_PIVOT) {
+            ii = 1 + k / (L - 1); jj = 1 + k % (L - 1);
+            l = (double)w[ii * L + jj] - (double)w[ii * L] - (double)w[jj] + (double)w[0];
+        } else {
+            ii = jj = k;
+            l = (double)w[k * L + k];
+        }
+        float tau_s = 0.0f;
+        uint32_t word = 0;
+        if (l != 0.0) {
+            const double al = fabs(l);
+            const double tau = al + 2.0 * log1p(sqrt(-expm1(-al)));
+            const double pp = 1.0 / (1.0 + exp(-tau));   // sigmoid(+tau)
+            const double pm = 1.0 / (1.0 + exp(tau));    // sigmoid(-tau)
+            const uint32_t tp = threshold24(pp), tm = threshold24(pm);
+            const uint32_t d = tp + tm - ((1u << 24) - 1u);   // in {0,1,2}
+            word = tp | (d << 25) | (l < 0 ? 0x80000000u : 0u);
+            tau_s = (float)(l > 0 ? tau : -tau);
+            const double q = l > 0 ? -tau : 0.0;
+            fs[ii] += l > 0 ? 0.5 * (l - tau) : 0.5 * (l + tau);
+            ft[jj] += 0.5 * (l - tau);
+            cst -= (q > 0 ? q + log1p(exp(-q)) : log1p(exp(q)));   // -log(1 + e^q)
+        }
+        a.tau[e * M + k] = tau_s;
+        a.thr[e * M + k] = word;
+    }
+    for (int x = 0; x < L; ++x) {
+        a.fold[(e * 2 + 0) * L + x] = fs[x];
+        a.fold[(e * 2 + 1) * L + x] = ft[x];
+    }
+    a.cst[e] = cst;
+    if (a.resid) {
+        // exact pairwise potential in the folded representation (tree edges of
+        // the blocked sweep): w(a,b) - fold_s(a) - fold_t(b)
+        for (int x = 0; x < L; ++x)
+            for (int y = 0; y < L; ++y)
+                a.resid[(e * L + x) * L + y] = (float)((double)w[x * L + y] - fs[x] - ft[y]);
+    }
+}
+
+__global__ void k_fold_unary(const float* unary, const double* fold, const int64_t* inc_ptr, const int2* inc,
+                             int N, int L, double* ut) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= N) return;
+    double acc[kMaxLabels];
+    for (int x = 0; x < L; ++x) acc[x] = unary[(int64_t)v * L + x];
+    for (int64_t p = inc_ptr[v]; p < inc_ptr[v + 1]; ++p) {
+        const int code = inc[p].x;
+        const int64_t e = code >> 1;
+        const double* f = fold + (e * 2 + (code & 1)) * L;
+        for (int x = 0; x < L; ++x) acc[x] += f[x];
+    }
+    for (int x = 0; x < L; ++x) ut[(int64_t)v * L + x] = acc[x];
+}
+
+cudaError_t launch_check_finite(const float* p, int64_t n, unsigned long long* bad, cudaStream_t s) {
+    if (n > 0) k_check_finite<<<1216, 256, 0, s>>>(p, n, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_offdiag(const float* pair, int64_t n_edges, int L, unsigned long long* nz, cudaStream_t s) {
+    if (n_edges > 0) k_count_offdiag<<<1216, 256, 0, s>>>(pair, n_edges, L, nz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decompose(const DecompArgs& a, cudaStream_t s) {
+    if (a.n > 0) k_decompose<<<(unsigned)((a.n + 127) / 128), 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold_unary(const float* unary, const double* fold, const int64_t* inc_ptr, const int2* inc,
+                              int N, int L, double* ut, cudaStream_t s) {
+    if (N > 0) k_fold_unary<<<(N + 127) / 128, 128, 0, s>>>(unary, fold, inc_ptr, inc, N, L, ut);
+    return cudaGetLastError();
+}
+
+}  // namespace mrfk

@@ -1,0 +1,66 @@
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) for the device, and the
+// sampler's draw contract.  Written from the published definition: ten rounds,
+// each multiplying counter words 0 and 2 by the two round multipliers,
+// exchanging the halves with xor of the key, then bumping the key by the two
+// Weyl constants.
+//
+// Draw contract: key = (seed lo, seed hi); counter = (index, sweep, chain,
+// phase << 24 | sub).  See mrf.h for the draws that use each phase.
+#pragma once
+#include <cstdint>
+
+namespace mrfk {
+
+enum Phase : uint32_t {
+    PH_DUAL = 1,      // prefix bytes of dual-bit uniforms (16 per call)
+    PH_DUAL_LO = 2,   // low 16 bits of dual-bit uniforms (8 per call)
+    PH_PRIMAL = 3,    // label draw of the plain sweep (word 0)
+    PH_INIT = 4,      // initial labels (word 0)
+    PH_FFBS = 5,      // label draw inside a tree block (word 0)
+    PH_SPLASH = 6,    // block-grid offset of a blocked sweep (words 0..2)
+    PH_PROPOSAL = 7,
+    PH_ACCEPT = 8,
+};
+
+__host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+    constexpr uint32_t kMul0 = 0xD2511F53u, kMul1 = 0xCD9E8D57u;
+    constexpr uint32_t kWeyl0 = 0x9E3779B9u, kWeyl1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+#ifdef __CUDA_ARCH__
+        const uint32_t hi0 = __umulhi(kMul0, c.x), lo0 = kMul0 * c.x;
+        const uint32_t hi1 = __umulhi(kMul1, c.z), lo1 = kMul1 * c.z;
+#else
+        const uint64_t p0 = (uint64_t)kMul0 * c.x, p1 = (uint64_t)kMul1 * c.z;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+#endif
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += kWeyl0;
+        k.y += kWeyl1;
+    }
+    return c;
+}
+
+__host__ __device__ __forceinline__ uint2 seed_key(uint64_t seed) {
+    return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+__host__ __device__ __forceinline__ uint4 draw(uint32_t index, uint32_t sweep, uint32_t chain,
+                                               uint32_t phase, uint32_t sub, uint2 key) {
+    return philox4x32_10(make_uint4(index, sweep, chain, (phase << 24) | sub), key);
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4& r, int w) {
+    return w == 0 ? r.x : (w == 1 ? r.y : (w == 2 ? r.z : r.w));
+}
+
+// Low 16 bits of the uniform of dual entry k (drawn only when the prefix byte
+// ties with the threshold's prefix).
+__device__ __forceinline__ uint32_t dual_low16(uint32_t e, uint32_t sweep, uint32_t c, int k, uint2 key) {
+    const uint4 r = draw(e, sweep, c, PH_DUAL_LO, (uint32_t)k >> 3, key);
+    const uint32_t w = word_of(r, (k & 7) >> 1);
+    return (w >> (16 * (k & 1))) & 0xFFFFu;
+}
+
+}  // namespace mrfk

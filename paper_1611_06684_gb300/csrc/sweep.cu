@@ -1,0 +1,159 @@
+// Sweep driver kernels (initial labels, count accumulation, sweep counter) and
+// the dispatch from the runtime (L, layout) to the templated half-step kernels
+// of sweep_impl.cuh, instantiated in sweep_la.cu, sweep_lb.cu and sweep_lc.cu.
+#include "common.cuh"
+
+namespace mrfk {
+
+template <int L, int LAYOUT> cudaError_t run_dual(const SweepArgs& a, cudaStream_t s);
+template <int L, int LAYOUT, bool FUSED> cudaError_t run_primal(const SweepArgs& a, cudaStream_t s);
+
+__global__ void k_init_labels(SweepArgs a) {
+    const int64_t n = (int64_t)a.N * a.C;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = (uint32_t)(g / a.C), c = (uint32_t)(g % a.C);
+        const uint32_t U = draw(v, 0, c, PH_INIT, 0, a.key).x >> 8;
+        a.x[g] = (uint8_t)(((uint64_t)U * (uint32_t)a.L) >> 24);
+    }
+}
+
+// counts[v][a] += #{c : x_new[v][c] = a} for counted sweeps.
+__global__ void k_accumulate(SweepArgs a) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= a.N) return;
+    const unsigned long long t = a.ctl->sweep;
+    if (t < a.ctl->count_from) return;
+    const uint8_t* xo = a.x + (size_t)((t + 1) & 1) * a.N * a.C + (int64_t)v * a.C;
+    uint32_t cnt[kMaxLabels];
+    for (int x = 0; x < kMaxLabels; ++x) cnt[x] = 0;
+    for (int c = 0; c < a.C; ++c) cnt[xo[c] & 15]++;
+    for (int x = 0; x < a.L; ++x)
+        if (cnt[x]) a.counts[(int64_t)v * a.L + x] += cnt[x];
+}
+
+__global__ void k_advance(Ctl* ctl) { ctl->sweep += 1; }
+
+// Label layout conversion between the internal x[v][c] (chain-innermost) and
+// the ABI view y[c][v], through 32x32 shared-memory tiles.
+__global__ void k_labels_to_abi(const uint8_t* __restrict__ x, uint8_t* __restrict__ y, int N, int C) {
+    __shared__ uint8_t tile[32][33];
+    const int v0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int v = v0 + r, c = c0 + threadIdx.x;
+        if (v < N && c < C) tile[r][threadIdx.x] = x[(int64_t)v * C + c];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int c = c0 + r, v = v0 + threadIdx.x;
+        if (v < N && c < C) y[(int64_t)c * N + v] = tile[threadIdx.x][r];
+    }
+}
+
+__global__ void k_labels_from_abi(const uint8_t* __restrict__ y, uint8_t* __restrict__ x, int N, int C) {
+    __shared__ uint8_t tile[32][33];
+    const int v0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int c = c0 + r, v = v0 + threadIdx.x;
+        if (v < N && c < C) tile[r][threadIdx.x] = y[(int64_t)c * N + v];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int v = v0 + r, c = c0 + threadIdx.x;
+        if (v < N && c < C) x[(int64_t)v * C + c] = tile[threadIdx.x][r];
+    }
+}
+
+__global__ void k_count_ge(const uint8_t* __restrict__ y, int64_t n, int L, unsigned long long* bad) {
+    unsigned long long cnt = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        cnt += y[i] >= L;
+    if (cnt) atomicAdd(bad, cnt);
+}
+
+cudaError_t launch_labels_to_abi(const uint8_t* x, uint8_t* y, int N, int C, cudaStream_t s) {
+    k_labels_to_abi<<<dim3((N + 31) / 32, (C + 31) / 32), dim3(32, 8), 0, s>>>(x, y, N, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_labels_from_abi(const uint8_t* y, uint8_t* x, int N, int C, cudaStream_t s) {
+    k_labels_from_abi<<<dim3((N + 31) / 32, (C + 31) / 32), dim3(32, 8), 0, s>>>(y, x, N, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_ge(const uint8_t* y, int64_t n, int L, unsigned long long* bad, cudaStream_t s) {
+    k_count_ge<<<1216, 256, 0, s>>>(y, n, L, bad);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- dispatch
+
+#define MRF_DISPATCH_L(L_, ...)                                                   \
+    switch (L_) {                                                                 \
+        case 2: { constexpr int LL = 2; __VA_ARGS__; } break;                     \
+        case 3: { constexpr int LL = 3; __VA_ARGS__; } break;                     \
+        case 4: { constexpr int LL = 4; __VA_ARGS__; } break;                     \
+        case 5: { constexpr int LL = 5; __VA_ARGS__; } break;                     \
+        case 6: { constexpr int LL = 6; __VA_ARGS__; } break;                     \
+        case 7: { constexpr int LL = 7; __VA_ARGS__; } break;                     \
+        case 8: { constexpr int LL = 8; __VA_ARGS__; } break;                     \
+        case 9: { constexpr int LL = 9; __VA_ARGS__; } break;                     \
+        case 10: { constexpr int LL = 10; __VA_ARGS__; } break;                   \
+        case 11: { constexpr int LL = 11; __VA_ARGS__; } break;                   \
+        case 12: { constexpr int LL = 12; __VA_ARGS__; } break;                   \
+        case 13: { constexpr int LL = 13; __VA_ARGS__; } break;                   \
+        case 14: { constexpr int LL = 14; __VA_ARGS__; } break;                   \
+        case 15: { constexpr int LL = 15; __VA_ARGS__; } break;                   \
+        case 16: { constexpr int LL = 16; __VA_ARGS__; } break;                   \
+        default: return cudaErrorInvalidValue;                                    \
+    }
+
+
+cudaError_t launch_init_labels(const SweepArgs& a, cudaStream_t s) {
+    k_init_labels<<<1216, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dual(const SweepArgs& a, int layout, cudaStream_t s) {
+    const int64_t n = a.E * a.C;
+    if (n == 0) return cudaSuccess;
+    if (layout == MRF_LAYOUT_PIVOT) {
+        MRF_DISPATCH_L(a.L, return (run_dual<LL, MRF_LAYOUT_PIVOT>(a, s)));
+    } else {
+        MRF_DISPATCH_L(a.L, return (run_dual<LL, MRF_LAYOUT_DIAG>(a, s)));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_primal(const SweepArgs& a, int layout, int schedule, cudaStream_t s) {
+    (void)schedule;
+    const int64_t n = (int64_t)a.N * a.C;
+    if (layout == MRF_LAYOUT_PIVOT) {
+        MRF_DISPATCH_L(a.L, return (run_primal<LL, MRF_LAYOUT_PIVOT, false>(a, s)));
+    } else {
+        MRF_DISPATCH_L(a.L, return (run_primal<LL, MRF_LAYOUT_DIAG, false>(a, s)));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused(const SweepArgs& a, int layout, int schedule, cudaStream_t s) {
+    (void)schedule;
+    const int64_t n = (int64_t)a.N * a.C;
+    if (layout == MRF_LAYOUT_PIVOT) {
+        MRF_DISPATCH_L(a.L, return (run_primal<LL, MRF_LAYOUT_PIVOT, true>(a, s)));
+    } else {
+        MRF_DISPATCH_L(a.L, return (run_primal<LL, MRF_LAYOUT_DIAG, true>(a, s)));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(const SweepArgs& a, cudaStream_t s) {
+    k_accumulate<<<(a.N + 255) / 256, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance(const SweepArgs& a, cudaStream_t s) {
+    k_advance<<<1, 1, 0, s>>>(a.ctl);
+    return cudaGetLastError();
+}
+
+}  // namespace mrfk

@@ -1,0 +1,255 @@
+"""Python binding of libmrf (include/mrf.h): argument marshalling only.
+
+Every function of the C ABI is exposed under its own name (mrf_create,
+mrf_set_factors, mrf_sweep, ...) through ctypes; the class `MRF` wraps a
+handle.  Arrays may be numpy arrays (host memory) or torch tensors (host or
+CUDA memory); PyTorch supplies device memory and the CUDA stream.  All
+sampling runs in the library's CUDA kernels.  There is no fallback: if
+libmrf.so has not been built, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmrf.so")
+
+MRF_OK, MRF_EINVAL, MRF_ENONFINITE, MRF_ENOMEM, MRF_ECUDA, MRF_ERANGE, MRF_ETIMEOUT, MRF_ESTATE = range(8)
+MRF_PTR_HOST, MRF_PTR_DEVICE = 0, 1
+MODE_PLAIN, MODE_FUSED, MODE_SPLASH = 0, 1, 2
+LAYOUT_PIVOT, LAYOUT_DIAG = 0, 1
+K_DUAL, K_PRIMAL, K_FUSED, K_POTENTIAL, K_FFBS, K_ACCUMULATE, K_COUNT = range(7)
+KERNEL_NAMES = ["k_dual", "k_primal", "k_primal<fused>", "k_splash_potential", "k_ffbs", "k_accumulate"]
+
+
+class mrf_options(ct.Structure):
+    _fields_ = [("grid_nx", ct.c_int32), ("grid_ny", ct.c_int32), ("grid_nz", ct.c_int32),
+                ("record_logp", ct.c_int32), ("use_graphs", ct.c_int32), ("schedule", ct.c_int32),
+                ("kernel_timing", ct.c_int32), ("reserved", ct.c_int32 * 7)]
+
+
+class mrf_info(ct.Structure):
+    _fields_ = [("n_vars", ct.c_int32), ("n_labels", ct.c_int32), ("n_chains", ct.c_int32),
+                ("layout", ct.c_int32), ("n_entries", ct.c_int32), ("n_edges", ct.c_int64),
+                ("n_edge_slots", ct.c_int64), ("sweep_index", ct.c_int64), ("n_samples", ct.c_int64),
+                ("log_const", ct.c_double)]
+
+
+_P = ct.c_void_p
+_SIGS = {
+    "mrf_default_options": (None, [ct.POINTER(mrf_options)]),
+    "mrf_create": (ct.c_int, [ct.POINTER(_P), ct.c_int32, ct.c_int32, ct.c_int32, ct.c_uint64,
+                              ct.POINTER(mrf_options), _P]),
+    "mrf_set_factors": (ct.c_int, [_P, _P, ct.c_int64, _P, _P, _P, ct.c_int32]),
+    "mrf_edit_factors": (ct.c_int, [_P, ct.c_int64, _P, ct.c_int64, _P, _P, _P, _P, ct.c_int32]),
+    "mrf_sweep": (ct.c_int, [_P, ct.c_int32, ct.c_int32]),
+    "mrf_marginals": (ct.c_int, [_P, _P, ct.POINTER(ct.c_int64), ct.c_int32]),
+    "mrf_get_counts": (ct.c_int, [_P, _P, ct.c_int32]),
+    "mrf_reset_marginals": (ct.c_int, [_P, ct.c_int32]),
+    "mrf_get_labels": (ct.c_int, [_P, _P, ct.c_int32]),
+    "mrf_set_labels": (ct.c_int, [_P, _P, ct.c_int32]),
+    "mrf_set_sweep_index": (ct.c_int, [_P, ct.c_int64]),
+    "mrf_get_info": (ct.c_int, [_P, ct.POINTER(mrf_info)]),
+    "mrf_debug_tables": (ct.c_int, [_P, _P, _P, _P]),
+    "mrf_debug_logp": (ct.c_int, [_P, _P, ct.POINTER(ct.c_uint64)]),
+    "mrf_debug_theta": (ct.c_int, [_P, _P]),
+    "mrf_kernel_times": (ct.c_int, [_P, _P, _P]),
+    "mrf_last_error": (ct.c_char_p, [_P]),
+    "mrf_status_string": (ct.c_char_p, [ct.c_int]),
+    "mrf_destroy": (None, [_P]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libmrf.so and declare every exported signature."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_1611_06684_gb300.build.build()")
+    lib = ct.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+class MrfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+def _ptr(a):
+    """(pointer, ptr_kind, keepalive) of a numpy array or torch tensor."""
+    if a is None:
+        return None, MRF_PTR_HOST, None
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a)
+        return a.ctypes.data, MRF_PTR_HOST, a
+    import torch  # noqa: F401  (only for tensors)
+    t = a.contiguous()
+    return t.data_ptr(), (MRF_PTR_DEVICE if t.is_cuda else MRF_PTR_HOST), t
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return 0
+
+
+class MRF:
+    """Owner of one mrf_t handle (see include/mrf.h for semantics)."""
+
+    def __init__(self, n_vars: int, n_labels: int, n_chains: int, seed: int = 0, grid=None,
+                 record_logp: bool = False, use_graphs: bool = True, schedule: int = 0, stream=None,
+                 kernel_timing: bool = False):
+        lib = load()
+        opt = mrf_options()
+        lib.mrf_default_options(ct.byref(opt))
+        if grid is not None:
+            opt.grid_nx, opt.grid_ny, opt.grid_nz = (int(g) for g in grid)
+        opt.record_logp = int(record_logp)
+        opt.use_graphs = int(use_graphs)
+        opt.schedule = int(schedule)
+        opt.kernel_timing = int(kernel_timing)
+        self.stream = _current_stream() if stream is None else int(stream)
+        h = _P()
+        st = lib.mrf_create(ct.byref(h), n_vars, n_labels, n_chains, ct.c_uint64(seed & (2**64 - 1)), ct.byref(opt),
+                            _P(self.stream))
+        if st != MRF_OK:
+            raise MrfError(st, lib.mrf_status_string(st).decode())
+        self.h = h
+        self.lib = lib
+        self.N, self.L, self.C = n_vars, n_labels, n_chains
+
+    def _check(self, st):
+        if st != MRF_OK:
+            raise MrfError(st, self.lib.mrf_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mrf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- model
+    def set_factors(self, unary, src, dst, pair):
+        pu, ku, a = _ptr(unary); ps, ks, b = _ptr(src); pd, kd, c = _ptr(dst); pp, kp, d = _ptr(pair)
+        kinds = {ku, ks, kd, kp} if int(np.prod(np.shape(src))) else {ku}
+        if len(kinds) != 1:
+            raise ValueError("all arrays must be on the same side (host or device)")
+        n = int(np.prod(src.shape)) if src is not None else 0
+        self._check(self.lib.mrf_set_factors(self.h, pu, n, ps, pd, pp, ku))
+
+    def edit_factors(self, remove_ids, src, dst, pair):
+        rem = np.ascontiguousarray(remove_ids, np.int64)
+        s = np.ascontiguousarray(src, np.int32); t = np.ascontiguousarray(dst, np.int32)
+        p = np.ascontiguousarray(pair, np.float32)
+        out = np.zeros(s.shape[0], np.int64)
+        self._check(self.lib.mrf_edit_factors(self.h, rem.shape[0], rem.ctypes.data, s.shape[0], s.ctypes.data,
+                                              t.ctypes.data, p.ctypes.data, out.ctypes.data, MRF_PTR_HOST))
+        return out
+
+    # -- sampling
+    def sweep(self, n: int = 1, mode: int = MODE_PLAIN):
+        self._check(self.lib.mrf_sweep(self.h, int(n), int(mode)))
+
+    def reset_marginals(self, burn_in: int = 0):
+        self._check(self.lib.mrf_reset_marginals(self.h, int(burn_in)))
+
+    def marginals(self):
+        out = np.zeros((self.N, self.L), np.float32)
+        ns = ct.c_int64()
+        self._check(self.lib.mrf_marginals(self.h, out.ctypes.data, ct.byref(ns), MRF_PTR_HOST))
+        return out, ns.value
+
+    def counts(self):
+        out = np.zeros((self.N, self.L), np.uint32)
+        self._check(self.lib.mrf_get_counts(self.h, out.ctypes.data, MRF_PTR_HOST))
+        return out
+
+    def get_labels(self):
+        out = np.zeros((self.C, self.N), np.uint8)
+        self._check(self.lib.mrf_get_labels(self.h, out.ctypes.data, MRF_PTR_HOST))
+        return out
+
+    def set_labels(self, x):
+        p, k, keep = _ptr(np.ascontiguousarray(x, np.uint8) if isinstance(x, np.ndarray) else x)
+        self._check(self.lib.mrf_set_labels(self.h, p, k))
+
+    def get_labels_into(self, out):
+        """Labels [C][N] into a caller buffer (numpy, pinned or CUDA torch tensor)."""
+        p, k, keep = _ptr(out)
+        self._check(self.lib.mrf_get_labels(self.h, p, k))
+        return out
+
+    def set_sweep_index(self, t: int):
+        self._check(self.lib.mrf_set_sweep_index(self.h, int(t)))
+
+    def info(self) -> mrf_info:
+        inf = mrf_info()
+        self._check(self.lib.mrf_get_info(self.h, ct.byref(inf)))
+        return inf
+
+    # -- debug / parity views
+    def debug_tables(self):
+        inf = self.info()
+        tau = np.zeros((inf.n_edge_slots, inf.n_entries), np.float32)
+        thr = np.zeros((inf.n_edge_slots, inf.n_entries), np.uint32)
+        ut = np.zeros((self.N, self.L), np.float64)
+        self._check(self.lib.mrf_debug_tables(self.h, tau.ctypes.data, thr.ctypes.data, ut.ctypes.data))
+        return tau, thr, ut
+
+    def debug_logp(self):
+        out = np.zeros((self.C, self.N, self.L), np.float32)
+        b = ct.c_uint64()
+        self._check(self.lib.mrf_debug_logp(self.h, out.ctypes.data, ct.byref(b)))
+        return out, b.value
+
+    def boundary_draws(self) -> int:
+        b = ct.c_uint64()
+        self._check(self.lib.mrf_debug_logp(self.h, None, ct.byref(b)))
+        return b.value
+
+    def kernel_times(self):
+        """{kernel name: (total ms, launches)} since the previous call."""
+        ms = np.zeros(K_COUNT, np.float64); n = np.zeros(K_COUNT, np.int64)
+        self._check(self.lib.mrf_kernel_times(self.h, ms.ctypes.data, n.ctypes.data))
+        return {KERNEL_NAMES[i]: (float(ms[i]), int(n[i])) for i in range(K_COUNT) if n[i]}
+
+    def debug_theta(self):
+        inf = self.info()
+        W = (inf.n_entries + 31) // 32
+        out = np.zeros((inf.n_edge_slots, self.C, W), np.uint32)
+        self._check(self.lib.mrf_debug_theta(self.h, out.ctypes.data))
+        return out
+
+
+def unpack_theta(words: np.ndarray, m: int) -> np.ndarray:
+    """[E][C][W] uint32 -> [C][E][m] bool (bit k of word k // 32)."""
+    E, C, W = words.shape
+    k = np.arange(m)
+    bits = (words[:, :, k // 32] >> (k % 32).astype(np.uint32)) & 1
+    return np.transpose(bits.astype(bool), (1, 0, 2))
