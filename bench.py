@@ -138,7 +138,12 @@ def run_ours(args, ws, rank, local):
         torch.distributed.barrier()
     from paper_1611_06684_gb300 import mrf as M
     gen, C, desc = WORKLOADS[args.workload]
-    model = gen()
+    if args.scale and args.workload == "potts3d":
+        from paper_1611_06684_gb300 import workloads as wl
+        model = wl.potts_grid3d(args.scale, L=8, seed=0)
+        desc = desc.replace("128^3", f"{args.scale}^3")
+    else:
+        model = gen()
     mode = {"plain": M.MODE_PLAIN, "fused": M.MODE_FUSED}[args.mode]
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
@@ -322,6 +327,7 @@ def main():
     ap.add_argument("--workload", default="potts3d", choices=list(WORKLOADS))
     ap.add_argument("--mode", default="plain", choices=["plain", "fused"])
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--scale", type=int, default=0, help="lattice edge for potts3d (default 128)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

@@ -15,14 +15,19 @@ Draw contract (shared by definition with the CUDA path, implemented
 independently on each side).  key = (seed mod 2^32, seed div 2^32);
 counter = (index, sweep, chain, phase << 24 | sub).
 
-* dual bit of edge slot e, table entry k, chain c, sweep t:
-    prefix byte  = byte (k mod 16) of Philox(e, t, c, DUAL    << 24 | k div 16)
-    low 16 bits  = half (k mod 8)  of Philox(e, t, c, DUAL_LO << 24 | k div 8)
+* dual bit of edge slot e, table entry k, chain c, sweep t: entries come in
+  groups g = k div 32 with position b = k mod 32.  The 8-bit prefix of the
+  uniform is spread over eight "planes": bit (7 - p) of the prefix (p = 0 is
+  the most significant) is bit b of word (p mod 4) of
+        Philox(e, t, c, DUAL << 24 | 2g + p div 4),
+  and the low 16 bits are half (k mod 8) of Philox(e, t, c, DUAL_LO << 24 | k div 8)
+  (halves little-endian within the words, words in order 0..3).
     U24 = prefix << 16 | low16,  u = (U24 + 1/2) / 2^24,  theta = [u < p]
-  (bytes and halves are little-endian within the four 32-bit words, words in
-  order 0..3).
+  The plane layout lets the device compare 32 entries at once bit-serially;
+  the low bits only matter when the prefix equals the threshold's prefix.
 * label draw of site v, chain c, sweep t (plain sweep):
-    U = word 0 of Philox(v, t, c, PRIMAL << 24),  u = ((U >> 8) + 1/2) / 2^24
+    U = word 0 of Philox(v, t, c, PRIMAL << 24),  u = ((U >> 9) + 1/2) / 2^23
+  (23 bits, so that u is exactly representable in single precision).
 * label draw inside a tree block (blocked sweep): phase FFBS, same layout.
 * initial label of site v, chain c:  a = ((U >> 8) * L) >> 24 with U = word 0 of
   Philox(v, 0, c, INIT << 24).
@@ -82,22 +87,39 @@ def _words(index, sweep, chain, c3, seed):
     return np.stack(philox4x32_10(index, sweep, chain, c3, k0, k1), axis=-1)   # [..., 4]
 
 
+def dual_prefix(edge, k, chain, sweep, seed):
+    """8-bit prefixes of dual uniforms from the bit planes; arguments broadcast."""
+    edge = np.asarray(edge, np.int64); k = np.asarray(k, np.int64); chain = np.asarray(chain, np.int64)
+    g, b = k >> 5, (k & 31).astype(np.uint32)
+    prefix = 0
+    for half in range(2):
+        w = _words(edge, sweep, chain, (PH_DUAL << 24) | (2 * g + half), seed)      # [..., 4]
+        for q in range(4):
+            p = 4 * half + q                                                       # plane index
+            bit = (w[..., q] >> b) & np.uint32(1)
+            prefix = prefix | (bit.astype(np.int64) << (7 - p))
+    return prefix
+
+
 def dual_u24(edge, k, chain, sweep, seed):
     """24-bit integer uniforms U24 of dual draws; all arguments broadcast."""
     edge = np.asarray(edge, np.int64); k = np.asarray(k, np.int64); chain = np.asarray(chain, np.int64)
-    hi = _words(edge, sweep, chain, (PH_DUAL << 24) | (k >> 4), seed)
-    kk = np.broadcast_to(k, hi.shape[:-1])
-    wsel = np.take_along_axis(hi, ((kk & 15) >> 2)[..., None], axis=-1)[..., 0]
-    prefix = (wsel >> (8 * (kk & 3)).astype(np.uint32)) & np.uint32(0xFF)
+    prefix = dual_prefix(edge, k, chain, sweep, seed)
     lo = _words(edge, sweep, chain, (PH_DUAL_LO << 24) | (k >> 3), seed)
+    kk = np.broadcast_to(k, lo.shape[:-1])
     wsel = np.take_along_axis(lo, ((kk & 7) >> 1)[..., None], axis=-1)[..., 0]
     low = (wsel >> (16 * (kk & 1)).astype(np.uint32)) & np.uint32(0xFFFF)
     return (prefix.astype(np.int64) << 16) | low.astype(np.int64)
 
 
 def u24_to_unit(u24):
-    """u = (U24 + 1/2) / 2^24, exactly representable in float32 and float64."""
+    """u = (U24 + 1/2) / 2^24 (exact in float64)."""
     return (np.asarray(u24, np.float64) + 0.5) / 16777216.0
+
+
+def u23_to_unit(u23):
+    """u = (U23 + 1/2) / 2^23 (exact in float32 and float64)."""
+    return (np.asarray(u23, np.float64) + 0.5) / 8388608.0
 
 
 def dual_uniform(edge, k, chain, sweep, seed):
@@ -107,7 +129,7 @@ def dual_uniform(edge, k, chain, sweep, seed):
 def site_uniform(site, chain, sweep, seed, phase=PH_PRIMAL):
     """Uniform of a label draw (plain sweep: phase PRIMAL; tree blocks: FFBS)."""
     w = _words(np.asarray(site, np.int64), sweep, np.asarray(chain, np.int64), phase << 24, seed)[..., 0]
-    return u24_to_unit(w >> np.uint32(8))
+    return u23_to_unit(w >> np.uint32(9))
 
 
 def init_labels(n_vars: int, n_labels: int, n_chains: int, seed: int):

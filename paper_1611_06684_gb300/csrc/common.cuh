@@ -35,14 +35,31 @@ __host__ __device__ inline int n_entries(int L, int layout) {
     return layout == MRF_LAYOUT_PIVOT ? (L - 1) * (L - 1) : L;
 }
 
+// Exact 24-bit threshold of a dual draw from the packed entry word `w`
+// (T+ in bits 0..24, d = T+ + T- - (2^24 - 1) in bits 25..26, sign of l in
+// bit 31, 0 = no dual bit) for the case y = [x_s = i_k], z = [x_t = j_k]:
+// the dual logit q + beta1 y + beta2 z is -tau, 0 or +tau.
+__host__ __device__ __forceinline__ uint32_t case_threshold(uint32_t w, int y, int z) {
+    const uint32_t tp = w & 0x1FFFFFFu;
+    const uint32_t tm = (1u << 24) - tp + ((w >> 25) & 3u) - 1u;
+    const int lvl = (w >> 31) ? (z - y + 1) : (y + z);      // 0: -tau, 1: 0, 2: +tau
+    const uint32_t t = lvl == 0 ? tm : (lvl == 1 ? (1u << 23) : tp);
+    return w ? t : 0u;
+}
+
+// 8-bit prefix of a threshold (255 stands for T = 2^24, decided by the low bits).
+__host__ __device__ __forceinline__ uint32_t threshold_prefix(uint32_t t) { return t >= (1u << 24) ? 255u : (t >> 16); }
+
 // Everything a sweep kernel needs, passed by value.
 struct SweepArgs {
-    int32_t N, C, L, M, W;
+    int32_t N, C, L, M, W;     // W = G = ceil(M/32) groups of 32 entries
     int64_t E;                 // edge slots
     const int32_t* src;        // [E] (-1 = free slot)
     const int32_t* dst;        // [E]
     const float* tau;          // [E][M] signed dual weight
     const uint32_t* thr;       // [E][M] packed thresholds
+    const uint32_t* tpl;       // [E][G][32] threshold prefix planes (P00, D10, D01, D11 x 8 planes)
+    const float* utf;          // [N][L] folded unaries, float32
     const float* resid;        // [E][L][L] exact tree-edge potentials (blocked sweep)
     const int64_t* inc_ptr;    // [N+1]
     const int2* inc;           // [2E] {edge*2 + side, neighbour}
@@ -83,7 +100,9 @@ struct DecompArgs {
 cudaError_t launch_check_finite(const float* p, int64_t n, unsigned long long* bad, cudaStream_t s);
 cudaError_t launch_count_offdiag(const float* pair, int64_t n_edges, int L, unsigned long long* nz, cudaStream_t s);
 cudaError_t launch_decompose(const DecompArgs& a, cudaStream_t s);
+cudaError_t launch_build_planes(const uint32_t* thr, int64_t n, const int64_t* slots, int64_t first_slot, int M,
+                                uint32_t* tpl, cudaStream_t s);
 cudaError_t launch_fold_unary(const float* unary, const double* fold, const int64_t* inc_ptr, const int2* inc,
-                              int N, int L, double* ut, cudaStream_t s);
+                              int N, int L, double* ut, float* utf, cudaStream_t s);
 
 }  // namespace mrfk

@@ -107,8 +107,44 @@ __global__ void k_decompose(DecompArgs a) {
     }
 }
 
+// Threshold prefix planes of the bit-sliced dual draw, per edge and group of
+// 32 entries: for each case (y, z) of an entry the 8-bit prefix of its
+// threshold, stored as 8 bit planes (plane p holds bit 7-p of the prefix of
+// entry 32g + b at bit b).  Kept in difference form so that a chain with
+// row mask R (entries with y = 1) and column mask C (z = 1) gets its planes as
+//   P00 ^ (D10 & R) ^ (D01 & C) ^ (D11 & R & C),
+// with D10 = P00^P10, D01 = P00^P01, D11 = P00^P10^P01^P11.
+__global__ void k_build_planes(const uint32_t* thr, int64_t n, const int64_t* slots, int64_t first_slot, int M,
+                               uint32_t* tpl) {
+    const int G = (M + 31) / 32;
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gid >= n * G) return;
+    const int64_t i = gid / G;
+    const int g = (int)(gid % G);
+    const int64_t e = slots ? slots[i] : first_slot + i;
+    uint32_t P[4][8];
+    for (int cs = 0; cs < 4; ++cs)
+        for (int p = 0; p < 8; ++p) P[cs][p] = 0;
+    for (int b = 0; b < 32; ++b) {
+        const int k = 32 * g + b;
+        if (k >= M) break;
+        const uint32_t w = thr[e * M + k];
+        for (int cs = 0; cs < 4; ++cs) {
+            const uint32_t pre = threshold_prefix(case_threshold(w, cs & 1, cs >> 1));
+            for (int p = 0; p < 8; ++p) P[cs][p] |= ((pre >> (7 - p)) & 1u) << b;
+        }
+    }
+    uint32_t* out = tpl + (e * G + g) * 32;
+    for (int p = 0; p < 8; ++p) {
+        out[p] = P[0][p];
+        out[8 + p] = P[0][p] ^ P[1][p];
+        out[16 + p] = P[0][p] ^ P[2][p];
+        out[24 + p] = P[0][p] ^ P[1][p] ^ P[2][p] ^ P[3][p];
+    }
+}
+
 __global__ void k_fold_unary(const float* unary, const double* fold, const int64_t* inc_ptr, const int2* inc,
-                             int N, int L, double* ut) {
+                             int N, int L, double* ut, float* utf) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= N) return;
     double acc[kMaxLabels];
@@ -119,7 +155,10 @@ __global__ void k_fold_unary(const float* unary, const double* fold, const int64
         const double* f = fold + (e * 2 + (code & 1)) * L;
         for (int x = 0; x < L; ++x) acc[x] += f[x];
     }
-    for (int x = 0; x < L; ++x) ut[(int64_t)v * L + x] = acc[x];
+    for (int x = 0; x < L; ++x) {
+        ut[(int64_t)v * L + x] = acc[x];
+        utf[(int64_t)v * L + x] = (float)acc[x];
+    }
 }
 
 cudaError_t launch_check_finite(const float* p, int64_t n, unsigned long long* bad, cudaStream_t s) {
@@ -138,8 +177,15 @@ cudaError_t launch_decompose(const DecompArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_fold_unary(const float* unary, const double* fold, const int64_t* inc_ptr, const int2* inc,
-                              int N, int L, double* ut, cudaStream_t s) {
-    if (N > 0) k_fold_unary<<<(N + 127) / 128, 128, 0, s>>>(unary, fold, inc_ptr, inc, N, L, ut);
+                              int N, int L, double* ut, float* utf, cudaStream_t s) {
+    if (N > 0) k_fold_unary<<<(N + 127) / 128, 128, 0, s>>>(unary, fold, inc_ptr, inc, N, L, ut, utf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_planes(const uint32_t* thr, int64_t n, const int64_t* slots, int64_t first_slot, int M,
+                                uint32_t* tpl, cudaStream_t s) {
+    const int64_t work = n * ((M + 31) / 32);
+    if (work > 0) k_build_planes<<<(unsigned)((work + 127) / 128), 128, 0, s>>>(thr, n, slots, first_slot, M, tpl);
     return cudaGetLastError();
 }
 

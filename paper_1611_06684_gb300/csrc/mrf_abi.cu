@@ -26,6 +26,8 @@ struct mrf {
     int32_t* d_dst = nullptr;
     float* d_tau = nullptr;
     uint32_t* d_thr = nullptr;
+    uint32_t* d_tpl = nullptr;         // [E][W][32] threshold prefix planes
+    float* d_utf = nullptr;            // [N][L] folded unaries, float32
     double* d_fold = nullptr;
     double* d_cst = nullptr;
     float* d_resid = nullptr;
@@ -110,6 +112,7 @@ SweepArgs make_args(const mrf_t* h) {
     a.N = h->N; a.C = h->C; a.L = h->L; a.M = h->M; a.W = h->W;
     a.E = h->E_slots;
     a.src = h->d_src; a.dst = h->d_dst; a.tau = h->d_tau; a.thr = h->d_thr; a.resid = h->d_resid;
+    a.tpl = h->d_tpl; a.utf = h->d_utf;
     a.inc_ptr = h->d_inc_ptr; a.inc = h->d_inc; a.ut = h->d_ut;
     a.x = h->d_x; a.theta = h->d_theta; a.counts = h->d_counts; a.logp = h->d_logp;
     a.ctl = h->d_ctl; a.key = h->key;
@@ -252,7 +255,7 @@ mrf_status mrf_create(mrf_t** out, int32_t n_vars, int32_t n_labels, int32_t n_c
     if (opt) h->opt = *opt; else mrf_default_options(&h->opt);
     auto bail = [&](mrf_status st) { mrf_destroy(h); return st; };
     const size_t NL = (size_t)n_vars * n_labels, NC = (size_t)n_vars * n_chains;
-    if (dalloc(h->d_unary, NL) || dalloc(h->d_ut, NL) || dalloc(h->d_x, 2 * NC) || dalloc(h->d_counts, NL) ||
+    if (dalloc(h->d_unary, NL) || dalloc(h->d_ut, NL) || dalloc(h->d_utf, NL) || dalloc(h->d_x, 2 * NC) || dalloc(h->d_counts, NL) ||
         dalloc(h->d_ctl, 1) || dalloc(h->d_flag, 1)) {
         cudaGetLastError();
         return bail(MRF_ENOMEM);
@@ -279,7 +282,7 @@ void mrf_destroy(mrf_t* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
     drop_graphs(h);
-    dfree(h->d_unary); dfree(h->d_ut); dfree(h->d_src); dfree(h->d_dst); dfree(h->d_tau); dfree(h->d_thr);
+    dfree(h->d_unary); dfree(h->d_ut); dfree(h->d_utf); dfree(h->d_tpl); dfree(h->d_src); dfree(h->d_dst); dfree(h->d_tau); dfree(h->d_thr);
     dfree(h->d_fold); dfree(h->d_cst); dfree(h->d_resid); dfree(h->d_inc_ptr); dfree(h->d_inc); dfree(h->d_x);
     dfree(h->d_theta); dfree(h->d_counts); dfree(h->d_logp); dfree(h->d_ctl); dfree(h->d_flag); dfree(h->d_stage);
     for (auto& r : h->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -333,6 +336,7 @@ mrf_status mrf_set_factors(mrf_t* h, const float* unary_log, int64_t n_edges, co
     const size_t E = (size_t)n_edges;
     MRF_CUDA(h, dalloc(h->d_src, E)); MRF_CUDA(h, dalloc(h->d_dst, E));
     MRF_CUDA(h, dalloc(h->d_tau, E * h->M)); MRF_CUDA(h, dalloc(h->d_thr, E * h->M));
+    MRF_CUDA(h, dalloc(h->d_tpl, E * h->W * 32));
     MRF_CUDA(h, dalloc(h->d_fold, E * 2 * L)); MRF_CUDA(h, dalloc(h->d_cst, E));
     if (want_resid) MRF_CUDA(h, dalloc(h->d_resid, E * L * L)); else dfree(h->d_resid);
     MRF_CUDA(h, dalloc(h->d_theta, E * h->C * h->W));
@@ -343,7 +347,8 @@ mrf_status mrf_set_factors(mrf_t* h, const float* unary_log, int64_t n_edges, co
     d.L = L; d.M = h->M; d.layout = h->layout; d.n = n_edges; d.slots = nullptr; d.first_slot = 0;
     d.pair = d_pair; d.tau = h->d_tau; d.thr = h->d_thr; d.fold = h->d_fold; d.cst = h->d_cst; d.resid = h->d_resid;
     MRF_CUDA(h, launch_decompose(d, h->stream));
-    MRF_CUDA(h, launch_fold_unary(h->d_unary, h->d_fold, h->d_inc_ptr, h->d_inc, N, L, h->d_ut, h->stream));
+    MRF_CUDA(h, launch_build_planes(h->d_thr, n_edges, nullptr, 0, h->M, h->d_tpl, h->stream));
+    MRF_CUDA(h, launch_fold_unary(h->d_unary, h->d_fold, h->d_inc_ptr, h->d_inc, N, L, h->d_ut, h->d_utf, h->stream));
     // log constant (for log-partition estimates): sum of per-edge constants
     std::vector<double> cst((size_t)n_edges);
     if (n_edges) MRF_CUDA(h, cudaMemcpyAsync(cst.data(), h->d_cst, E * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -423,7 +428,7 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
             return cudaSuccess;
         };
         MRF_CUDA(h, grow(h->d_src, 1)); MRF_CUDA(h, grow(h->d_dst, 1));
-        MRF_CUDA(h, grow(h->d_tau, h->M)); MRF_CUDA(h, grow(h->d_thr, h->M));
+        MRF_CUDA(h, grow(h->d_tau, h->M)); MRF_CUDA(h, grow(h->d_thr, h->M)); MRF_CUDA(h, grow(h->d_tpl, h->W * 32));
         MRF_CUDA(h, grow(h->d_fold, 2 * L)); MRF_CUDA(h, grow(h->d_cst, 1));
         MRF_CUDA(h, dalloc(h->d_theta, (size_t)cap * h->C * h->W));
         h->E_cap = cap;
@@ -442,8 +447,9 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
     d.L = L; d.M = h->M; d.layout = h->layout; d.n = n_add; d.slots = d_slots;
     d.pair = d_pair; d.tau = h->d_tau; d.thr = h->d_thr; d.fold = h->d_fold; d.cst = h->d_cst; d.resid = nullptr;
     MRF_CUDA(h, launch_decompose(d, h->stream));
+    MRF_CUDA(h, launch_build_planes(h->d_thr, n_add, d_slots, 0, h->M, h->d_tpl, h->stream));
     MRF_CUDA(h, build_csr(h));
-    MRF_CUDA(h, launch_fold_unary(h->d_unary, h->d_fold, h->d_inc_ptr, h->d_inc, N, L, h->d_ut, h->stream));
+    MRF_CUDA(h, launch_fold_unary(h->d_unary, h->d_fold, h->d_inc_ptr, h->d_inc, N, L, h->d_ut, h->d_utf, h->stream));
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));
     std::copy(slots.begin(), slots.end(), out_new_ids);
     return MRF_OK;

@@ -8,85 +8,144 @@
 //                (destination side) is a                                 (k_primal)
 //   fused form   both in one vertex-centric kernel: each endpoint regenerates
 //                the dual bits of its incident edges from the counter-based
-//                RNG (identical at both ends), so theta is never stored (k_fused)
+//                RNG (identical at both ends), so theta is never stored
 //
 // Labels are stored chain-innermost, x[buf][v][c], so that lanes of a warp
 // working on consecutive chains of one site or edge read consecutive bytes and
-// share the edge's table row (one broadcast load per entry for the warp).
+// share the edge's table row (one broadcast load per word for the warp).
 // The dual bits of one (edge, chain) are packed into W = ceil(m/32) words,
-// theta[e][c][w].  Both kernels read the sweep index from device memory (Ctl),
+// theta[e][c][w].  The kernels read the sweep index from device memory (Ctl),
 // so one sweep can be captured once as a CUDA graph and replayed.
 #pragma once
 #include "common.cuh"
 
 namespace mrfk {
 
-// ---------------------------------------------------------------------------- dual bits
+// ---------------------------------------------------------------------------- entry masks
 
-// Threshold of entry word `w` for the dual-logit case (y, z): logit is -tau, 0
-// or +tau; 0 marks an entry without a dual bit.
-__device__ __forceinline__ uint32_t case_threshold(uint32_t w, int y, int z) {
-    const uint32_t tp = w & 0x1FFFFFFu;
-    const uint32_t tm = (1u << 24) - tp + ((w >> 25) & 3u) - 1u;
-    const int lvl = (w >> 31) ? (z - y + 1) : (y + z);      // 0: -tau, 1: 0, 2: +tau
-    const uint32_t t = lvl == 0 ? tm : (lvl == 1 ? (1u << 23) : tp);
-    return w ? t : 0u;
+// Bits [lo, hi) of a 32-bit word (lo, hi relative to the word, clipped).
+__device__ __forceinline__ uint32_t range_mask(int lo, int hi) {
+    lo = max(lo, 0);
+    hi = min(hi, 32);
+    if (hi <= lo) return 0u;
+    const uint32_t upto = hi == 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u);
+    return upto & ~((1u << lo) - 1u);
 }
 
-// Dual bits of edge e, chain c, given the endpoint labels (xs, xt).  The 8-bit
-// prefix of each uniform decides unless it equals the threshold's prefix; only
-// then are the low 16 bits drawn (the comparison result is the same as with
-// the full 24-bit uniform).
+// Word g of the PIVOT column-1 pattern: entries k = r (L-1), r = 0..L-2.
+__host__ __device__ constexpr uint32_t col_pattern_word(int L, int g) {
+    uint32_t w = 0;
+    for (int r = 0; r < L - 1; ++r) {
+        const int k = r * (L - 1) - 32 * g;
+        if (k >= 0 && k < 32) w |= 1u << k;
+    }
+    return w;
+}
+
+__host__ __device__ constexpr uint32_t valid_word(int M, int g) {
+    return M - 32 * g >= 32 ? 0xFFFFFFFFu : (M - 32 * g <= 0 ? 0u : ((1u << (M - 32 * g)) - 1u));
+}
+
+// Entries of group g whose row is label a (y = 1) and whose column is b (z = 1).
 template <int L, int LAYOUT>
-__device__ __forceinline__ void dual_bits(uint32_t e, uint32_t c, int xs, int xt, const uint32_t* __restrict__ thr_e,
-                                          uint32_t sweep, uint2 key, uint32_t (&bits)[Ent<L, LAYOUT>::W]) {
+__device__ __forceinline__ uint32_t row_mask(int a, int g) {
+    if (LAYOUT == MRF_LAYOUT_DIAG) return (a >> 5) == g ? (1u << (a & 31)) : 0u;
+    if (a == 0) return 0u;
+    const int lo = (a - 1) * (L - 1) - 32 * g;
+    return range_mask(lo, lo + L - 1);
+}
+
+template <int L, int LAYOUT>
+__device__ __forceinline__ uint32_t col_mask(int b, int g) {
+    if (LAYOUT == MRF_LAYOUT_DIAG) return (b >> 5) == g ? (1u << (b & 31)) : 0u;
+    if (b == 0) return 0u;
+    const uint32_t hi = col_pattern_word(L, g);
+    const uint32_t lo = g > 0 ? col_pattern_word(L, g - 1) : 0u;
+    return __funnelshift_l(lo, hi, (unsigned)(b - 1));
+}
+
+// ---------------------------------------------------------------------------- dual bits
+
+// Dual bits of edge e, chain c, given the endpoint labels (xs, xt).
+// Bit-sliced: the 8-bit prefixes of 32 uniforms arrive as 8 planes (two
+// Philox calls per group of 32 entries); each plane is compared with the
+// matching threshold plane for the chain's cases, most significant first:
+//   lt |= eq & ~r & t;  eq &= ~(r ^ t)
+// so lt = [prefix < threshold prefix] and eq = ties for all 32 entries at once.
+// Ties (probability 1/256 per entry) draw the low 16 bits and decide with the
+// exact 24-bit threshold.
+template <int L, int LAYOUT>
+__device__ __forceinline__ void dual_bits(uint32_t e, uint32_t c, int xs, int xt, const uint32_t* __restrict__ tpl_e,
+                                          const uint32_t* __restrict__ thr_e, uint32_t sweep, uint2 key,
+                                          uint32_t (&bits)[Ent<L, LAYOUT>::W]) {
     using E = Ent<L, LAYOUT>;
+    uint32_t ties[E::W];
 #pragma unroll
-    for (int w = 0; w < E::W; ++w) bits[w] = 0;
+    for (int g = 0; g < E::W; ++g) {
+        const uint4 r0 = draw(e, sweep, c, PH_DUAL, 2u * g, key);
+        const uint4 r1 = draw(e, sweep, c, PH_DUAL, 2u * g + 1u, key);
+        const uint32_t R[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+        const uint32_t rm = row_mask<L, LAYOUT>(xs, g), cm = col_mask<L, LAYOUT>(xt, g), km = rm & cm;
+        const uint4* tp = reinterpret_cast<const uint4*>(tpl_e + g * 32);
+        const uint4 q[8] = {__ldg(tp + 0), __ldg(tp + 1), __ldg(tp + 2), __ldg(tp + 3),
+                            __ldg(tp + 4), __ldg(tp + 5), __ldg(tp + 6), __ldg(tp + 7)};
+        const uint32_t P00[8] = {q[0].x, q[0].y, q[0].z, q[0].w, q[1].x, q[1].y, q[1].z, q[1].w};
+        const uint32_t D10[8] = {q[2].x, q[2].y, q[2].z, q[2].w, q[3].x, q[3].y, q[3].z, q[3].w};
+        const uint32_t D01[8] = {q[4].x, q[4].y, q[4].z, q[4].w, q[5].x, q[5].y, q[5].z, q[5].w};
+        const uint32_t D11[8] = {q[6].x, q[6].y, q[6].z, q[6].w, q[7].x, q[7].y, q[7].z, q[7].w};
+        uint32_t lt = 0u, eq = valid_word(E::M, g);
 #pragma unroll
-    for (int kb = 0; kb < (E::M + 15) / 16; ++kb) {
-        const uint4 r = draw(e, sweep, c, PH_DUAL, (uint32_t)kb, key);
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            const int k = kb * 16 + kk;
-            if (k < E::M) {
-                const uint32_t t = case_threshold(__ldg(thr_e + k), xs == E::i(k), xt == E::j(k));
-                const uint32_t pre = (word_of(r, kk >> 2) >> (8 * (kk & 3))) & 0xFFu;
-                const uint32_t th = t >> 16;
-                uint32_t bit = pre < th;
-                if (pre == th && (t & 0xFFFFu)) bit = dual_low16(e, sweep, c, k, key) < (t & 0xFFFFu);
-                bits[k >> 5] |= bit << (k & 31);
-            }
+        for (int p = 0; p < 8; ++p) {
+            const uint32_t t = P00[p] ^ (D10[p] & rm) ^ (D01[p] & cm) ^ (D11[p] & km);
+            const uint32_t r = R[p];
+            lt |= eq & ~r & t;
+            eq &= ~(r ^ t);
+        }
+        bits[g] = lt;
+        ties[g] = eq;
+    }
+#pragma unroll 1
+    for (int g = 0; g < E::W; ++g) {
+        uint32_t tg = ties[g];
+        while (tg) {
+            const int b = __ffs(tg) - 1;
+            tg &= tg - 1u;
+            const int k = 32 * g + b;
+            const int ik = LAYOUT == MRF_LAYOUT_PIVOT ? 1 + k / (L - 1) : k;
+            const int jk = LAYOUT == MRF_LAYOUT_PIVOT ? 1 + k % (L - 1) : k;
+            const uint32_t t = case_threshold(__ldg(thr_e + k), xs == ik, xt == jk);
+            const uint32_t rem = t - (threshold_prefix(t) << 16);      // in [0, 65536]
+            if (rem && dual_low16(e, sweep, c, k, key) < rem) bits[g] |= 1u << b;
         }
     }
 }
 
 // ---------------------------------------------------------------------------- label draw
 
-// Draw x_v from exp(F)/Z by the inverse CDF with u from Philox (phase `phase`);
-// optionally record log p.  Counts draws within 1e-6 of a CDF boundary.
+// Draw x_v from exp(F)/Z by the inverse CDF with the 23-bit uniform u of
+// Philox phase `phase` (u is exact in float32); optionally record log p.
+// Counts draws within 1e-6 of a CDF boundary.
 template <int L>
-__device__ __forceinline__ int draw_label(const double (&F)[L], uint32_t v, uint32_t c, uint32_t sweep, uint2 key,
+__device__ __forceinline__ int draw_label(const float (&F)[L], uint32_t v, uint32_t c, uint32_t sweep, uint2 key,
                                           uint32_t phase, float* __restrict__ logp_out, Ctl* ctl) {
-    double mx = F[0];
+    float mx = F[0];
 #pragma unroll
-    for (int a = 1; a < L; ++a) mx = fmax(mx, F[a]);
-    float d[L], ex[L];
+    for (int a = 1; a < L; ++a) mx = fmaxf(mx, F[a]);
+    float ex[L];
     float s = 0.0f;
 #pragma unroll
     for (int a = 0; a < L; ++a) {
-        d[a] = (float)(F[a] - mx);
-        ex[a] = expf(d[a]);
+        ex[a] = expf(F[a] - mx);
         s += ex[a];
     }
     const float inv = 1.0f / s;
     if (logp_out) {
         const float ls = logf(s);
 #pragma unroll
-        for (int a = 0; a < L; ++a) logp_out[a] = d[a] - ls;
+        for (int a = 0; a < L; ++a) logp_out[a] = (F[a] - mx) - ls;
     }
-    const uint32_t U = draw(v, sweep, c, phase, 0, key).x >> 8;
-    const double u = ((double)U + 0.5) * (1.0 / 16777216.0);
+    const uint32_t U = draw(v, sweep, c, phase, 0, key).x >> 9;
+    const float u = ((float)U + 0.5f) * (1.0f / 8388608.0f);
     float cdf = 0.0f;
     int lab = -1, last_pos = 0;
     bool near = false;
@@ -95,8 +154,8 @@ __device__ __forceinline__ int draw_label(const double (&F)[L], uint32_t v, uint
         const float p = ex[a] * inv;
         cdf += p;
         if (p > 0.0f) last_pos = a;
-        if (lab < 0 && u < (double)cdf) lab = a;
-        near |= fabs(u - (double)cdf) < 1e-6;
+        if (lab < 0 && u < cdf) lab = a;
+        near |= fabsf(u - cdf) < 1e-6f;
     }
     if (near) atomicAdd(&ctl->boundary, 1ull);
     return lab < 0 ? last_pos : lab;
@@ -118,7 +177,7 @@ __global__ void __launch_bounds__(256) k_dual(SweepArgs a) {
     if (s >= 0) {
         const int t = a.dst[e];
         dual_bits<L, LAYOUT>((uint32_t)e, c, xin[(int64_t)s * a.C + c], xin[(int64_t)t * a.C + c],
-                             a.thr + e * E::M, sweep, a.key, bits);
+                             a.tpl + e * E::W * 32, a.thr + e * E::M, sweep, a.key, bits);
     } else {
 #pragma unroll
         for (int w = 0; w < E::W; ++w) bits[w] = 0;
@@ -144,6 +203,15 @@ __device__ __forceinline__ void add_side(const uint32_t (&bits)[Ent<L, LAYOUT>::
     }
 }
 
+// Compensated (two-sum) flush of a float32 partial sum into a hi/lo pair, used
+// every 32 incident edges so that high-degree sites keep ~double precision.
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (x - bp);
+    hi = s;
+}
+
 // FUSED = false: read theta written by k_dual.  FUSED = true: regenerate it.
 template <int L, int LAYOUT, bool FUSED>
 __global__ void __launch_bounds__(256) k_primal(SweepArgs a) {
@@ -154,14 +222,14 @@ __global__ void __launch_bounds__(256) k_primal(SweepArgs a) {
     const uint32_t sweep = (uint32_t)a.ctl->sweep;
     const uint8_t* xin = a.x + (size_t)(sweep & 1) * a.N * a.C;
     uint8_t* xout = a.x + (size_t)((sweep + 1) & 1) * a.N * a.C;
-    double F[L];
-    float acc[L];
+    float acc[L], hi[L], lo[L];
 #pragma unroll
-    for (int x = 0; x < L; ++x) { F[x] = a.ut[(int64_t)v * L + x]; acc[x] = 0.0f; }
+    for (int x = 0; x < L; ++x) { acc[x] = 0.0f; hi[x] = 0.0f; lo[x] = 0.0f; }
     int xv = 0;
     if (FUSED) xv = xin[g];
     const int64_t p0 = a.inc_ptr[v], p1 = a.inc_ptr[v + 1];
     int chunk = 0;
+    bool flushed = false;
     for (int64_t p = p0; p < p1; ++p) {
         const int2 ic = a.inc[p];
         const int64_t e = ic.x >> 1;
@@ -169,22 +237,30 @@ __global__ void __launch_bounds__(256) k_primal(SweepArgs a) {
         uint32_t bits[E::W];
         if (FUSED) {
             const int xn = xin[(int64_t)ic.y * a.C + c];
-            dual_bits<L, LAYOUT>((uint32_t)e, c, side == 0 ? xv : xn, side == 0 ? xn : xv, a.thr + e * E::M, sweep,
-                                 a.key, bits);
+            dual_bits<L, LAYOUT>((uint32_t)e, c, side == 0 ? xv : xn, side == 0 ? xn : xv, a.tpl + e * E::W * 32,
+                                 a.thr + e * E::M, sweep, a.key, bits);
         } else {
             const uint32_t* th = a.theta + (e * a.C + c) * E::W;
 #pragma unroll
             for (int w = 0; w < E::W; ++w) bits[w] = th[w];
         }
         add_side<L, LAYOUT>(bits, a.tau + e * E::M, side, acc);
-        if (++chunk == 16) {            // fp32 partial sums per 16 edges, fp64 across chunks
+        if (++chunk == 32) {
 #pragma unroll
-            for (int x = 0; x < L; ++x) { F[x] += acc[x]; acc[x] = 0.0f; }
+            for (int x = 0; x < L; ++x) { two_sum_add(hi[x], lo[x], acc[x]); acc[x] = 0.0f; }
             chunk = 0;
+            flushed = true;
         }
     }
+    float F[L];
+    const float* uf = a.utf + (int64_t)v * L;
+    if (flushed) {
 #pragma unroll
-    for (int x = 0; x < L; ++x) F[x] += acc[x];
+        for (int x = 0; x < L; ++x) { two_sum_add(hi[x], lo[x], acc[x]); F[x] = __ldg(uf + x) + (hi[x] + lo[x]); }
+    } else {
+#pragma unroll
+        for (int x = 0; x < L; ++x) F[x] = __ldg(uf + x) + acc[x];
+    }
     float* lp = a.logp ? a.logp + ((int64_t)c * a.N + v) * L : nullptr;
     xout[g] = (uint8_t)draw_label<L>(F, v, c, sweep, a.key, PH_PRIMAL, lp, a.ctl);
 }

@@ -28,11 +28,26 @@ def test_philox_counter_and_key_sensitivity():
         assert abs(flips - 0.5) < 0.01       # avalanche: half the output bits change
 
 
-def test_u24_mapping_is_exact():
+def test_uniform_mappings_are_exact():
     U = np.array([0, 1, 12345, (1 << 23) - 1, 1 << 23, (1 << 24) - 1])
     u = ph.u24_to_unit(U)
     assert np.all(u * 16777216.0 - 0.5 == U)        # exact in float64
     assert u[0] > 0 and u[-1] < 1
+    V = np.array([0, 1, 777, (1 << 22), (1 << 23) - 1])
+    v = ph.u23_to_unit(V)
+    assert np.all(v.astype(np.float32).astype(np.float64) == v)   # exact in float32
+    assert np.all(v * 8388608.0 - 0.5 == V)
+
+
+def test_dual_prefix_planes_uniform_and_independent_of_position():
+    pre = ph.dual_prefix(np.arange(4000)[:, None], np.arange(64)[None, :], 2, 9, 5)
+    assert pre.min() >= 0 and pre.max() <= 255
+    h = np.bincount(pre.ravel(), minlength=256)
+    chi2 = ((h - pre.size / 256) ** 2 / (pre.size / 256)).sum()
+    assert 160 < chi2 < 360
+    # entries of the same group share Philox calls but use different bits
+    c = np.corrcoef(pre[:, 0], pre[:, 1])[0, 1]
+    assert abs(c) < 0.05
 
 
 def test_dual_uniform_prefix_and_low_bits_independent_streams():
