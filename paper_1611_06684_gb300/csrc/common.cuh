@@ -22,10 +22,30 @@ struct Ctl {
     unsigned long long splash_offset;  // packed (ox | oy << 8 | oz << 16) of the last blocked sweep
 };
 
-// Dualised-entry layout: entry k <-> table position (i_k, j_k).
+// Division by a fixed 32-bit divisor d via a multiply (Granlund & Montgomery,
+// "Division by invariant integers using multiplication", 1994):
+// q = (umulhi(m, n) + n) >> l with l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1.
+struct FastDiv {
+    uint32_t d, m, l;
+    static FastDiv make(uint32_t d) {
+        uint32_t l = 0;
+        while ((1ull << l) < d) ++l;
+        const uint64_t m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+        return FastDiv{d, (uint32_t)m, l};
+    }
+    __device__ __forceinline__ uint32_t div(uint32_t n) const {
+        return (uint32_t)(((uint64_t)__umulhi(m, n) + n) >> l);
+    }
+};
+
+// Dualised-entry layout: entry k <-> table position (i_k, j_k).  Rows of the
+// tau table are padded to MP = M rounded up to 4 floats (16-byte loads).
+__host__ __device__ constexpr int pad4(int m) { return (m + 3) & ~3; }
+
 template <int L, int LAYOUT>
 struct Ent {
     static constexpr int M = (LAYOUT == MRF_LAYOUT_PIVOT) ? (L - 1) * (L - 1) : L;
+    static constexpr int MP = pad4(M);
     static constexpr int W = (M + 31) / 32;
     __host__ __device__ static constexpr int i(int k) { return LAYOUT == MRF_LAYOUT_PIVOT ? 1 + k / (L - 1) : k; }
     __host__ __device__ static constexpr int j(int k) { return LAYOUT == MRF_LAYOUT_PIVOT ? 1 + k % (L - 1) : k; }
@@ -56,9 +76,9 @@ struct SweepArgs {
     int64_t E;                 // edge slots
     const int32_t* src;        // [E] (-1 = free slot)
     const int32_t* dst;        // [E]
-    const float* tau;          // [E][M] signed dual weight
+    const float* tau;          // [E][MP] signed dual weight (rows padded to 4)
     const uint32_t* thr;       // [E][M] packed thresholds
-    const uint32_t* tpl;       // [E][G][32] threshold prefix planes (P00, D10, D01, D11 x 8 planes)
+    const uint32_t* tpl;       // [E][G][8][4] threshold prefix planes {P00, D10, D01, D11} per plane
     const float* utf;          // [N][L] folded unaries, float32
     const float* resid;        // [E][L][L] exact tree-edge potentials (blocked sweep)
     const int64_t* inc_ptr;    // [N+1]
@@ -70,6 +90,7 @@ struct SweepArgs {
     float* logp;               // [C][N][L] or null
     Ctl* ctl;
     uint2 key;
+    FastDiv fdC;               // division by the chain count
     int32_t grid_nx, grid_ny, grid_nz;
 };
 
@@ -91,7 +112,7 @@ struct DecompArgs {
     const int64_t* slots;      // [n] slot of each edge (null: slot = first_slot + i)
     int64_t first_slot;
     const float* pair;         // [n][L][L] raw log tables
-    float* tau;                // [E][M]
+    float* tau;                // [E][MP]
     uint32_t* thr;             // [E][M]
     double* fold;              // [E][2][L]
     double* cst;               // [E] per-edge log constant

@@ -90,9 +90,10 @@ __global__ void k_decompose(DecompArgs a) {
             ft[jj] += 0.5 * (l - tau);
             cst -= (q > 0 ? q + log1p(exp(-q)) : log1p(exp(q)));   // -log(1 + e^q)
         }
-        a.tau[e * M + k] = tau_s;
+        a.tau[e * pad4(M) + k] = tau_s;
         a.thr[e * M + k] = word;
     }
+    for (int k = M; k < pad4(M); ++k) a.tau[e * pad4(M) + k] = 0.0f;
     for (int x = 0; x < L; ++x) {
         a.fold[(e * 2 + 0) * L + x] = fs[x];
         a.fold[(e * 2 + 1) * L + x] = ft[x];
@@ -134,13 +135,9 @@ __global__ void k_build_planes(const uint32_t* thr, int64_t n, const int64_t* sl
             for (int p = 0; p < 8; ++p) P[cs][p] |= ((pre >> (7 - p)) & 1u) << b;
         }
     }
-    uint32_t* out = tpl + (e * G + g) * 32;
-    for (int p = 0; p < 8; ++p) {
-        out[p] = P[0][p];
-        out[8 + p] = P[0][p] ^ P[1][p];
-        out[16 + p] = P[0][p] ^ P[2][p];
-        out[24 + p] = P[0][p] ^ P[1][p] ^ P[2][p] ^ P[3][p];
-    }
+    uint4* out = reinterpret_cast<uint4*>(tpl + (e * G + g) * 32);
+    for (int p = 0; p < 8; ++p)
+        out[p] = make_uint4(P[0][p], P[0][p] ^ P[1][p], P[0][p] ^ P[2][p], P[0][p] ^ P[1][p] ^ P[2][p] ^ P[3][p]);
 }
 
 __global__ void k_fold_unary(const float* unary, const double* fold, const int64_t* inc_ptr, const int2* inc,

@@ -116,6 +116,7 @@ SweepArgs make_args(const mrf_t* h) {
     a.inc_ptr = h->d_inc_ptr; a.inc = h->d_inc; a.ut = h->d_ut;
     a.x = h->d_x; a.theta = h->d_theta; a.counts = h->d_counts; a.logp = h->d_logp;
     a.ctl = h->d_ctl; a.key = h->key;
+    a.fdC = FastDiv::make((uint32_t)h->C);
     a.grid_nx = h->opt.grid_nx; a.grid_ny = h->opt.grid_ny; a.grid_nz = h->opt.grid_nz;
     return a;
 }
@@ -248,7 +249,7 @@ mrf_status mrf_create(mrf_t** out, int32_t n_vars, int32_t n_labels, int32_t n_c
     *out = nullptr;
     if (n_vars <= 0 || n_chains <= 0) return MRF_EINVAL;
     if (n_labels < 2 || n_labels > kMaxLabels) return MRF_ERANGE;
-    if ((int64_t)n_vars * n_chains > (int64_t)1 << 40) return MRF_EINVAL;
+    if ((int64_t)n_vars * n_chains >= (int64_t)1 << 32) return MRF_ERANGE;
     mrf_t* h = new mrf_t();
     h->N = n_vars; h->L = n_labels; h->C = n_chains; h->seed = seed; h->key = seed_key(seed);
     h->stream = (cudaStream_t)cuda_stream;
@@ -335,7 +336,8 @@ mrf_status mrf_set_factors(mrf_t* h, const float* unary_log, int64_t n_edges, co
     }
     const size_t E = (size_t)n_edges;
     MRF_CUDA(h, dalloc(h->d_src, E)); MRF_CUDA(h, dalloc(h->d_dst, E));
-    MRF_CUDA(h, dalloc(h->d_tau, E * h->M)); MRF_CUDA(h, dalloc(h->d_thr, E * h->M));
+    if ((uint64_t)E * h->C >= (1ull << 32)) return fail(h, MRF_ERANGE, "edges x chains must be below 2^32");
+    MRF_CUDA(h, dalloc(h->d_tau, E * pad4(h->M))); MRF_CUDA(h, dalloc(h->d_thr, E * h->M));
     MRF_CUDA(h, dalloc(h->d_tpl, E * h->W * 32));
     MRF_CUDA(h, dalloc(h->d_fold, E * 2 * L)); MRF_CUDA(h, dalloc(h->d_cst, E));
     if (want_resid) MRF_CUDA(h, dalloc(h->d_resid, E * L * L)); else dfree(h->d_resid);
@@ -428,7 +430,8 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
             return cudaSuccess;
         };
         MRF_CUDA(h, grow(h->d_src, 1)); MRF_CUDA(h, grow(h->d_dst, 1));
-        MRF_CUDA(h, grow(h->d_tau, h->M)); MRF_CUDA(h, grow(h->d_thr, h->M)); MRF_CUDA(h, grow(h->d_tpl, h->W * 32));
+        if ((uint64_t)cap * h->C >= (1ull << 32)) return fail(h, MRF_ERANGE, "edges x chains must be below 2^32");
+        MRF_CUDA(h, grow(h->d_tau, pad4(h->M))); MRF_CUDA(h, grow(h->d_thr, h->M)); MRF_CUDA(h, grow(h->d_tpl, h->W * 32));
         MRF_CUDA(h, grow(h->d_fold, 2 * L)); MRF_CUDA(h, grow(h->d_cst, 1));
         MRF_CUDA(h, dalloc(h->d_theta, (size_t)cap * h->C * h->W));
         h->E_cap = cap;
@@ -597,7 +600,8 @@ mrf_status mrf_debug_tables(mrf_t* h, float* tau, uint32_t* thr, double* utilde)
     if (!h) return MRF_EINVAL;
     if (!h->has_factors) return fail(h, MRF_ESTATE, "no factors");
     const size_t EM = (size_t)h->E_slots * h->M;
-    if (tau) MRF_CUDA(h, cudaMemcpyAsync(tau, h->d_tau, EM * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (tau) MRF_CUDA(h, cudaMemcpy2DAsync(tau, h->M * sizeof(float), h->d_tau, pad4(h->M) * sizeof(float),
+                                           h->M * sizeof(float), (size_t)h->E_slots, cudaMemcpyDeviceToHost, h->stream));
     if (thr) MRF_CUDA(h, cudaMemcpyAsync(thr, h->d_thr, EM * sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
     if (utilde) MRF_CUDA(h, cudaMemcpyAsync(utilde, h->d_ut, (size_t)h->N * h->L * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));

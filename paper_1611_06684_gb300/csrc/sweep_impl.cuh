@@ -87,16 +87,11 @@ __device__ __forceinline__ void dual_bits(uint32_t e, uint32_t c, int xs, int xt
         const uint32_t R[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
         const uint32_t rm = row_mask<L, LAYOUT>(xs, g), cm = col_mask<L, LAYOUT>(xt, g), km = rm & cm;
         const uint4* tp = reinterpret_cast<const uint4*>(tpl_e + g * 32);
-        const uint4 q[8] = {__ldg(tp + 0), __ldg(tp + 1), __ldg(tp + 2), __ldg(tp + 3),
-                            __ldg(tp + 4), __ldg(tp + 5), __ldg(tp + 6), __ldg(tp + 7)};
-        const uint32_t P00[8] = {q[0].x, q[0].y, q[0].z, q[0].w, q[1].x, q[1].y, q[1].z, q[1].w};
-        const uint32_t D10[8] = {q[2].x, q[2].y, q[2].z, q[2].w, q[3].x, q[3].y, q[3].z, q[3].w};
-        const uint32_t D01[8] = {q[4].x, q[4].y, q[4].z, q[4].w, q[5].x, q[5].y, q[5].z, q[5].w};
-        const uint32_t D11[8] = {q[6].x, q[6].y, q[6].z, q[6].w, q[7].x, q[7].y, q[7].z, q[7].w};
         uint32_t lt = 0u, eq = valid_word(E::M, g);
 #pragma unroll
         for (int p = 0; p < 8; ++p) {
-            const uint32_t t = P00[p] ^ (D10[p] & rm) ^ (D01[p] & cm) ^ (D11[p] & km);
+            const uint4 q = __ldg(tp + p);                 // {P00, D10, D01, D11} of plane p
+            const uint32_t t = q.x ^ (q.y & rm) ^ (q.z & cm) ^ (q.w & km);
             const uint32_t r = R[p];
             lt |= eq & ~r & t;
             eq &= ~(r ^ t);
@@ -164,42 +159,63 @@ __device__ __forceinline__ int draw_label(const float (&F)[L], uint32_t v, uint3
 // ---------------------------------------------------------------------------- kernels
 
 template <int L, int LAYOUT>
-__global__ void __launch_bounds__(256) k_dual(SweepArgs a) {
+__global__ void __launch_bounds__(256, 4) k_dual(SweepArgs a) {
     using E = Ent<L, LAYOUT>;
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= a.E * a.C) return;
-    const int64_t e = g / a.C;
-    const uint32_t c = (uint32_t)(g % a.C);
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;     // E * C < 2^32 (checked by the host)
+    if (g >= (uint64_t)a.E * a.C) return;
+    const uint32_t e = a.fdC.div(g);
+    const uint32_t c = g - e * (uint32_t)a.C;
     const uint32_t sweep = (uint32_t)a.ctl->sweep;
     const uint8_t* xin = a.x + (size_t)(sweep & 1) * a.N * a.C;
     uint32_t bits[E::W];
     const int s = a.src[e];
     if (s >= 0) {
         const int t = a.dst[e];
-        dual_bits<L, LAYOUT>((uint32_t)e, c, xin[(int64_t)s * a.C + c], xin[(int64_t)t * a.C + c],
-                             a.tpl + e * E::W * 32, a.thr + e * E::M, sweep, a.key, bits);
+        dual_bits<L, LAYOUT>(e, c, xin[(int64_t)s * a.C + c], xin[(int64_t)t * a.C + c],
+                             a.tpl + (int64_t)e * E::W * 32, a.thr + (int64_t)e * E::M, sweep, a.key, bits);
     } else {
 #pragma unroll
         for (int w = 0; w < E::W; ++w) bits[w] = 0;
     }
-    uint32_t* out = a.theta + g * E::W;
+    uint32_t* out = a.theta + (int64_t)g * E::W;
+    if (E::W % 2 == 0) {
 #pragma unroll
-    for (int w = 0; w < E::W; ++w) out[w] = bits[w];
+        for (int w = 0; w < E::W; w += 2) *reinterpret_cast<uint2*>(out + w) = make_uint2(bits[w], bits[w + 1 < E::W ? w + 1 : w]);
+    } else {
+#pragma unroll
+        for (int w = 0; w < E::W; ++w) out[w] = bits[w];
+    }
 }
 
-// Accumulate the beta terms of edge e's set dual bits for one endpoint side.
+// Accumulate the beta terms of edge e's set dual bits for one endpoint side
+// (tau row loaded as 16-byte vectors; beta1 = tau_signed, beta2 = |tau_signed|).
 template <int L, int LAYOUT>
 __device__ __forceinline__ void add_side(const uint32_t (&bits)[Ent<L, LAYOUT>::W], const float* __restrict__ tau_e,
                                          int side, float (&acc)[L]) {
     using E = Ent<L, LAYOUT>;
+    const float4* t4 = reinterpret_cast<const float4*>(tau_e);
     if (side == 0) {
 #pragma unroll
-        for (int k = 0; k < E::M; ++k)
-            if ((bits[k >> 5] >> (k & 31)) & 1u) acc[E::i(k)] += __ldg(tau_e + k);
+        for (int k4 = 0; k4 < E::MP / 4; ++k4) {
+            const float4 q = __ldg(t4 + k4);
+            const float tv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = 4 * k4 + u;
+                if (k < E::M && ((bits[k >> 5] >> (k & 31)) & 1u)) acc[E::i(k)] += tv[u];
+            }
+        }
     } else {
 #pragma unroll
-        for (int k = 0; k < E::M; ++k)
-            if ((bits[k >> 5] >> (k & 31)) & 1u) acc[E::j(k)] += fabsf(__ldg(tau_e + k));
+        for (int k4 = 0; k4 < E::MP / 4; ++k4) {
+            const float4 q = __ldg(t4 + k4);
+            const float tv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = 4 * k4 + u;
+                if (k < E::M && ((bits[k >> 5] >> (k & 31)) & 1u)) acc[E::j(k)] += fabsf(tv[u]);
+            }
+        }
     }
 }
 
@@ -214,11 +230,11 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
 
 // FUSED = false: read theta written by k_dual.  FUSED = true: regenerate it.
 template <int L, int LAYOUT, bool FUSED>
-__global__ void __launch_bounds__(256) k_primal(SweepArgs a) {
+__global__ void __launch_bounds__(256, FUSED ? 2 : 4) k_primal(SweepArgs a) {
     using E = Ent<L, LAYOUT>;
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= (int64_t)a.N * a.C) return;
-    const uint32_t v = (uint32_t)(g / a.C), c = (uint32_t)(g % a.C);
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;     // N * C < 2^32 (checked by the host)
+    if (g >= (uint64_t)a.N * a.C) return;
+    const uint32_t v = a.fdC.div(g), c = g - v * (uint32_t)a.C;
     const uint32_t sweep = (uint32_t)a.ctl->sweep;
     const uint8_t* xin = a.x + (size_t)(sweep & 1) * a.N * a.C;
     uint8_t* xout = a.x + (size_t)((sweep + 1) & 1) * a.N * a.C;
@@ -244,7 +260,7 @@ __global__ void __launch_bounds__(256) k_primal(SweepArgs a) {
 #pragma unroll
             for (int w = 0; w < E::W; ++w) bits[w] = th[w];
         }
-        add_side<L, LAYOUT>(bits, a.tau + e * E::M, side, acc);
+        add_side<L, LAYOUT>(bits, a.tau + e * E::MP, side, acc);
         if (++chunk == 32) {
 #pragma unroll
             for (int x = 0; x < L; ++x) { two_sum_add(hi[x], lo[x], acc[x]); acc[x] = 0.0f; }
