@@ -28,6 +28,7 @@ struct Ctl {
 struct FastDiv {
     uint32_t d, m, l;
     static FastDiv make(uint32_t d) {
+        if (d == 0) d = 1;
         uint32_t l = 0;
         while ((1ull << l) < d) ++l;
         const uint64_t m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
@@ -92,6 +93,11 @@ struct SweepArgs {
     uint2 key;
     FastDiv fdC;               // division by the chain count
     int32_t grid_nx, grid_ny, grid_nz;
+    // blocked sweep (lattice): tree edges of the sweep's comb forest get theta = 0
+    int32_t splash;            // 1 while running a blocked sweep
+    int64_t nxe, nye;          // numbers of x- and y-edges (canonical lattice order)
+    FastDiv fdX1, fdX, fdY1, fdY;   // division by nx-1, nx, ny-1, ny
+    float* pot;                // [N][L][C] node potentials / beliefs of the blocked sweep
 };
 
 // Kernel launchers (sweep.cu, splash.cu, decompose.cu).  All return cudaGetLastError().
@@ -102,6 +108,9 @@ cudaError_t launch_fused(const SweepArgs& a, int layout, int schedule, cudaStrea
 cudaError_t launch_accumulate(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_advance(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_splash(const SweepArgs& a, int layout, cudaStream_t s);
+cudaError_t launch_splash_offset(const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_potential(const SweepArgs& a, int layout, cudaStream_t s);
+cudaError_t launch_ffbs(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_labels_to_abi(const uint8_t* x, uint8_t* y, int N, int C, cudaStream_t s);
 cudaError_t launch_labels_from_abi(const uint8_t* y, uint8_t* x, int N, int C, cudaStream_t s);
 cudaError_t launch_count_ge(const uint8_t* y, int64_t n, int L, unsigned long long* bad, cudaStream_t s);

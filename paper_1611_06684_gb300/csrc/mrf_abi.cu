@@ -47,6 +47,7 @@ struct mrf {
     std::string err;
     cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
     uint8_t* d_stage = nullptr;        // [C][N] staging for the ABI label view
+    float* d_pot = nullptr;            // [N][L][C] node potentials of the blocked sweep
     // kernel timing (options.kernel_timing)
     struct Rec { int id; cudaEvent_t a, b; };
     std::vector<Rec> pending;
@@ -117,6 +118,14 @@ SweepArgs make_args(const mrf_t* h) {
     a.x = h->d_x; a.theta = h->d_theta; a.counts = h->d_counts; a.logp = h->d_logp;
     a.ctl = h->d_ctl; a.key = h->key;
     a.fdC = FastDiv::make((uint32_t)h->C);
+    const int nx = h->opt.grid_nx, ny = h->opt.grid_ny, nz = h->opt.grid_nz;
+    if (nx > 0) {
+        a.nxe = (int64_t)(nx - 1) * ny * nz;
+        a.nye = (int64_t)nx * (ny - 1) * nz;
+        a.fdX1 = FastDiv::make((uint32_t)(nx - 1)); a.fdX = FastDiv::make((uint32_t)nx);
+        a.fdY1 = FastDiv::make((uint32_t)(ny - 1)); a.fdY = FastDiv::make((uint32_t)ny);
+    }
+    a.pot = h->d_pot;
     a.grid_nx = h->opt.grid_nx; a.grid_ny = h->opt.grid_ny; a.grid_nz = h->opt.grid_nz;
     return a;
 }
@@ -285,7 +294,7 @@ void mrf_destroy(mrf_t* h) {
     drop_graphs(h);
     dfree(h->d_unary); dfree(h->d_ut); dfree(h->d_utf); dfree(h->d_tpl); dfree(h->d_src); dfree(h->d_dst); dfree(h->d_tau); dfree(h->d_thr);
     dfree(h->d_fold); dfree(h->d_cst); dfree(h->d_resid); dfree(h->d_inc_ptr); dfree(h->d_inc); dfree(h->d_x);
-    dfree(h->d_theta); dfree(h->d_counts); dfree(h->d_logp); dfree(h->d_ctl); dfree(h->d_flag); dfree(h->d_stage);
+    dfree(h->d_theta); dfree(h->d_counts); dfree(h->d_logp); dfree(h->d_ctl); dfree(h->d_flag); dfree(h->d_stage); dfree(h->d_pot);
     for (auto& r : h->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : h->pool) cudaEventDestroy(e);
     delete h;
@@ -468,7 +477,11 @@ static mrf_status enqueue_sweep(mrf_t* h, int mode) {
     } else if (mode == MRF_MODE_FUSED) {
         e = timed(h, MRF_K_FUSED, [&] { return launch_fused(a, h->layout, h->opt.schedule, s); });
     } else {
-        e = launch_splash(a, h->layout, s);
+        a.splash = 1;
+        e = launch_splash_offset(a, s);
+        if (e == cudaSuccess) e = timed(h, MRF_K_DUAL, [&] { return launch_dual(a, h->layout, s); });
+        if (e == cudaSuccess) e = timed(h, MRF_K_POTENTIAL, [&] { return launch_potential(a, h->layout, s); });
+        if (e == cudaSuccess) e = timed(h, MRF_K_FFBS, [&] { return launch_ffbs(a, s); });
     }
     if (e == cudaSuccess) e = timed(h, MRF_K_ACCUMULATE, [&] { return launch_accumulate(a, s); });
     if (e == cudaSuccess) e = launch_advance(a, s);
@@ -481,6 +494,10 @@ mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode) {
     if (!h->has_factors) return fail(h, MRF_ESTATE, "mrf_set_factors first");
     if (n_sweeps < 0 || mode < MRF_MODE_PLAIN || mode > MRF_MODE_SPLASH) return fail(h, MRF_EINVAL, "bad sweep count or mode");
     if (mode == MRF_MODE_SPLASH && h->opt.grid_nx <= 0) return fail(h, MRF_ESTATE, "splash mode needs options.grid");
+    if (mode == MRF_MODE_SPLASH && !h->d_pot) {
+        drop_graphs(h);
+        MRF_CUDA(h, dalloc(h->d_pot, (size_t)h->N * h->L * h->C));
+    }
     const bool graphs = h->opt.use_graphs && h->stream != nullptr && !h->opt.kernel_timing;
     if (graphs && !h->graph[mode] && n_sweeps > 0) {
         cudaGraph_t g = nullptr;

@@ -17,18 +17,48 @@ __global__ void k_init_labels(SweepArgs a) {
     }
 }
 
-// counts[v][a] += #{c : x_new[v][c] = a} for counted sweeps.
+// counts[v][a] += #{c : x_new[v][c] = a} for counted sweeps.  Per-label
+// counts of up to 255 chains per pass are kept as sixteen 8-bit lanes of two
+// 64-bit registers (label x adds 1 << 8x to the low or high word).
 __global__ void k_accumulate(SweepArgs a) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= a.N) return;
     const unsigned long long t = a.ctl->sweep;
     if (t < a.ctl->count_from) return;
     const uint8_t* xo = a.x + (size_t)((t + 1) & 1) * a.N * a.C + (int64_t)v * a.C;
-    uint32_t cnt[kMaxLabels];
-    for (int x = 0; x < kMaxLabels; ++x) cnt[x] = 0;
-    for (int c = 0; c < a.C; ++c) cnt[xo[c] & 15]++;
-    for (int x = 0; x < a.L; ++x)
-        if (cnt[x]) a.counts[(int64_t)v * a.L + x] += cnt[x];
+    uint32_t tot[kMaxLabels];
+#pragma unroll
+    for (int x = 0; x < kMaxLabels; ++x) tot[x] = 0;
+    for (int c0 = 0; c0 < a.C; c0 += 255) {
+        const int c1 = min(a.C, c0 + 255);
+        unsigned long long lo = 0, hi = 0;
+        int c = c0;
+        if (((a.C | c0) & 3) == 0) {
+            for (; c + 4 <= c1; c += 4) {
+                const uint32_t w = *reinterpret_cast<const uint32_t*>(xo + c);
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const uint32_t x = (w >> (8 * b)) & 15u;
+                    lo += x < 8 ? 1ull << (8 * x) : 0ull;
+                    hi += x >= 8 ? 1ull << (8 * (x - 8)) : 0ull;
+                }
+            }
+        }
+        for (; c < c1; ++c) {
+            const uint32_t x = xo[c] & 15u;
+            lo += x < 8 ? 1ull << (8 * x) : 0ull;
+            hi += x >= 8 ? 1ull << (8 * (x - 8)) : 0ull;
+        }
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            tot[x] += (uint32_t)((lo >> (8 * x)) & 0xFF);
+            tot[x + 8] += (uint32_t)((hi >> (8 * x)) & 0xFF);
+        }
+    }
+    uint32_t* cnt = a.counts + (int64_t)v * a.L;
+#pragma unroll
+    for (int x = 0; x < kMaxLabels; ++x)
+        if (x < a.L && tot[x]) cnt[x] += tot[x];
 }
 
 __global__ void k_advance(Ctl* ctl) { ctl->sweep += 1; }

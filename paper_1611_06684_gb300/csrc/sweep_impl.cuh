@@ -64,6 +64,44 @@ __device__ __forceinline__ uint32_t col_mask(int b, int g) {
     return __funnelshift_l(lo, hi, (unsigned)(b - 1));
 }
 
+// ---------------------------------------------------------------------------- blocked sweep
+
+// Offset (ox, oy, oz) of the block grid of the current blocked sweep.
+__device__ __forceinline__ void splash_offset(const Ctl* ctl, int& ox, int& oy, int& oz) {
+    const uint32_t o = (uint32_t)ctl->splash_offset;
+    ox = o & 0xFF; oy = (o >> 8) & 0xFF; oz = (o >> 16) & 0xFF;
+}
+
+// Lowest coordinate of the (clipped) 4-block containing coordinate x.
+__device__ __forceinline__ int block_lo(int x, int o) { return max(0, ((x + o) >> 2) * 4 - o); }
+
+// Is lattice edge slot e an edge of the comb forest of the current blocked
+// sweep?  x-edges inside a block always are; y-edges when both ends have
+// local x = 0; z-edges when both ends have local x = y = 0.
+__device__ __forceinline__ bool is_tree_edge(const SweepArgs& a, uint32_t e) {
+    int ox, oy, oz;
+    splash_offset(a.ctl, ox, oy, oz);
+    if (e < (uint64_t)a.nxe) {
+        const uint32_t r = a.fdX1.div(e);
+        const int x = (int)(e - r * (uint32_t)(a.grid_nx - 1));
+        return ((x + ox) >> 2) == ((x + 1 + ox) >> 2);
+    }
+    if (e < (uint64_t)(a.nxe + a.nye)) {
+        const uint32_t f = e - (uint32_t)a.nxe;
+        const uint32_t r = a.fdX.div(f);
+        const int x = (int)(f - r * (uint32_t)a.grid_nx);
+        const uint32_t r2 = a.fdY1.div(r);
+        const int y = (int)(r - r2 * (uint32_t)(a.grid_ny - 1));
+        return x == block_lo(x, ox) && ((y + oy) >> 2) == ((y + 1 + oy) >> 2);
+    }
+    const uint32_t f = e - (uint32_t)(a.nxe + a.nye);
+    const uint32_t r = a.fdX.div(f);
+    const int x = (int)(f - r * (uint32_t)a.grid_nx);
+    const uint32_t z = a.fdY.div(r);
+    const int y = (int)(r - z * (uint32_t)a.grid_ny);
+    return x == block_lo(x, ox) && y == block_lo(y, oy) && ((int(z) + oz) >> 2) == ((int(z) + 1 + oz) >> 2);
+}
+
 // ---------------------------------------------------------------------------- dual bits
 
 // Dual bits of edge e, chain c, given the endpoint labels (xs, xt).
@@ -169,7 +207,7 @@ __global__ void __launch_bounds__(256, 4) k_dual(SweepArgs a) {
     const uint8_t* xin = a.x + (size_t)(sweep & 1) * a.N * a.C;
     uint32_t bits[E::W];
     const int s = a.src[e];
-    if (s >= 0) {
+    if (s >= 0 && !(a.splash && is_tree_edge(a, e))) {
         const int t = a.dst[e];
         dual_bits<L, LAYOUT>(e, c, xin[(int64_t)s * a.C + c], xin[(int64_t)t * a.C + c],
                              a.tpl + (int64_t)e * E::W * 32, a.thr + (int64_t)e * E::M, sweep, a.key, bits);
@@ -229,7 +267,9 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
 }
 
 // FUSED = false: read theta written by k_dual.  FUSED = true: regenerate it.
-template <int L, int LAYOUT, bool FUSED>
+// POT = true (blocked sweep): write the node potentials F to a.pot instead of
+// drawing labels.
+template <int L, int LAYOUT, bool FUSED, bool POT = false>
 __global__ void __launch_bounds__(256, FUSED ? 2 : 4) k_primal(SweepArgs a) {
     using E = Ent<L, LAYOUT>;
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;     // N * C < 2^32 (checked by the host)
@@ -246,26 +286,51 @@ __global__ void __launch_bounds__(256, FUSED ? 2 : 4) k_primal(SweepArgs a) {
     const int64_t p0 = a.inc_ptr[v], p1 = a.inc_ptr[v + 1];
     int chunk = 0;
     bool flushed = false;
-    for (int64_t p = p0; p < p1; ++p) {
-        const int2 ic = a.inc[p];
-        const int64_t e = ic.x >> 1;
-        const int side = ic.x & 1;
-        uint32_t bits[E::W];
-        if (FUSED) {
-            const int xn = xin[(int64_t)ic.y * a.C + c];
-            dual_bits<L, LAYOUT>((uint32_t)e, c, side == 0 ? xv : xn, side == 0 ? xn : xv, a.tpl + e * E::W * 32,
-                                 a.thr + e * E::M, sweep, a.key, bits);
-        } else {
-            const uint32_t* th = a.theta + (e * a.C + c) * E::W;
+    // Incidences in batches of B: all incidence records and (plain form) all
+    // theta words of a batch are loaded before any is used, so the dependent
+    // loads of B edges are in flight together.
+    constexpr int B = FUSED ? 1 : 4;
+    for (int64_t base = p0; base < p1; base += B) {
+        int2 ic[B];
+        uint32_t bits[B][E::W];
 #pragma unroll
-            for (int w = 0; w < E::W; ++w) bits[w] = th[w];
+        for (int u = 0; u < B; ++u) ic[u] = base + u < p1 ? __ldg(&a.inc[base + u]) : make_int2(-1, 0);
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const int64_t e = ic[u].x >> 1;
+            if (ic[u].x < 0) {
+#pragma unroll
+                for (int w = 0; w < E::W; ++w) bits[u][w] = 0;
+            } else if (FUSED) {
+                const int side = ic[u].x & 1;
+                const int xn = xin[(int64_t)ic[u].y * a.C + c];
+                dual_bits<L, LAYOUT>((uint32_t)e, c, side == 0 ? xv : xn, side == 0 ? xn : xv, a.tpl + e * E::W * 32,
+                                     a.thr + e * E::M, sweep, a.key, bits[u]);
+            } else {
+                const uint32_t* th = a.theta + (e * a.C + c) * E::W;
+                if (E::W % 2 == 0) {
+#pragma unroll
+                    for (int w = 0; w < E::W; w += 2) {
+                        const uint2 q = __ldcs(reinterpret_cast<const uint2*>(th + w));
+                        bits[u][w] = q.x;
+                        bits[u][w + 1 < E::W ? w + 1 : w] = q.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int w = 0; w < E::W; ++w) bits[u][w] = __ldcs(th + w);
+                }
+            }
         }
-        add_side<L, LAYOUT>(bits, a.tau + e * E::MP, side, acc);
-        if (++chunk == 32) {
 #pragma unroll
-            for (int x = 0; x < L; ++x) { two_sum_add(hi[x], lo[x], acc[x]); acc[x] = 0.0f; }
-            chunk = 0;
-            flushed = true;
+        for (int u = 0; u < B; ++u) {
+            if (ic[u].x < 0) continue;
+            add_side<L, LAYOUT>(bits[u], a.tau + (ic[u].x >> 1) * (int64_t)E::MP, ic[u].x & 1, acc);
+            if (++chunk == 32) {
+#pragma unroll
+                for (int x = 0; x < L; ++x) { two_sum_add(hi[x], lo[x], acc[x]); acc[x] = 0.0f; }
+                chunk = 0;
+                flushed = true;
+            }
         }
     }
     float F[L];
@@ -276,6 +341,12 @@ __global__ void __launch_bounds__(256, FUSED ? 2 : 4) k_primal(SweepArgs a) {
     } else {
 #pragma unroll
         for (int x = 0; x < L; ++x) F[x] = __ldg(uf + x) + acc[x];
+    }
+    if (POT) {
+        float* pv = a.pot + (int64_t)v * L * a.C + c;
+#pragma unroll
+        for (int x = 0; x < L; ++x) pv[(int64_t)x * a.C] = F[x];
+        return;
     }
     float* lp = a.logp ? a.logp + ((int64_t)c * a.N + v) * L : nullptr;
     xout[g] = (uint8_t)draw_label<L>(F, v, c, sweep, a.key, PH_PRIMAL, lp, a.ctl);
@@ -297,7 +368,16 @@ cudaError_t run_primal(const SweepArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int L, int LAYOUT>
+cudaError_t run_potential(const SweepArgs& a, cudaStream_t s) {
+    const int64_t n = (int64_t)a.N * a.C;
+    if (n > 0) k_primal<L, LAYOUT, false, true><<<blocks_for(n, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 #define MRF_INSTANTIATE_SWEEP(L)                                                                 \
+    template cudaError_t run_potential<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, cudaStream_t);      \
+    template cudaError_t run_potential<L, MRF_LAYOUT_DIAG>(const SweepArgs&, cudaStream_t);       \
     template cudaError_t run_dual<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, cudaStream_t);           \
     template cudaError_t run_dual<L, MRF_LAYOUT_DIAG>(const SweepArgs&, cudaStream_t);            \
     template cudaError_t run_primal<L, MRF_LAYOUT_PIVOT, false>(const SweepArgs&, cudaStream_t);  \
