@@ -148,7 +148,7 @@ def run_ours(args, ws, rank, local):
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         h = M.MRF(model.n_vars, model.n_labels, C, seed=args.seed + 1000003 * rank, stream=stream.cuda_stream,
-                  kernel_timing=True)
+                  kernel_timing=True, grid=model.grid if model.grid else None)
         h.set_factors(model.unary, model.src, model.dst, model.pair)
     inf = h.info()
     minfo = dict(E=inf.n_edge_slots, N=inf.n_vars, L=inf.n_labels, m=inf.n_entries)
@@ -198,6 +198,25 @@ def run_ours(args, ws, rank, local):
     else:
         roof = dict(hbm, traffic=None, kernel=dom, peak_source=f"MEASURED_PEAKS.json hbm_gbs ({peak_src})")
 
+    # other sweep forms on the same handle, timed separately (not part of the headline)
+    variants = {}
+    if not args.no_variants:
+        forms = [("fused", M.MODE_FUSED)] + ([("splash", M.MODE_SPLASH)] if model.grid else [])
+        for name, md in forms:
+            h.sweep(1, md)
+            h.kernel_times()
+            torch.cuda.synchronize()
+            kv = 5
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.sweep(kv, md)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            msv = e0.elapsed_time(e1) / kv
+            kt = h.kernel_times()
+            variants[name] = {"ms_per_step": msv, "value": C * model.n_vars / (msv / 1e3), "unit": METRIC,
+                              "kernels": {k: v[0] / v[1] for k, v in kt.items()}}
+
     # end to end through the C ABI with pinned host buffers: labels in, sweep, labels out
     e2e = None
     if not args.no_e2e:
@@ -241,6 +260,7 @@ def run_ours(args, ws, rank, local):
             "roofline": roof,
             "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in ktimes.items()},
             "gpu_launches": launches,
+            "variants": variants,
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
@@ -330,6 +350,7 @@ def main():
     ap.add_argument("--scale", type=int, default=0, help="lattice edge for potts3d (default 128)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()
