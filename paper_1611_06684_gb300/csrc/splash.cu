@@ -21,9 +21,13 @@ __global__ void k_splash_offset(SweepArgs a) {
     a.ctl->splash_offset = (r.x >> 30) | ((r.y >> 30) << 8) | ((r.z >> 30) << 16);
 }
 
-// out[b] = log sum_a exp(bel[a] + psi[b][a])  (message to the parent, label b)
+// out[b] = log sum_a exp(bel[a] + psi[b][a]) - max_b(...)  (message to the
+// parent with label b).  Subtracting the maximum over b keeps beliefs of the
+// size of one node's potentials however large the subtree; a constant shift
+// of a message changes no conditional.
 template <int L>
 __device__ __forceinline__ void tree_message(const float (&bel)[L], const float* __restrict__ psi, float (&out)[L]) {
+    float top = -INFINITY;
 #pragma unroll
     for (int b = 0; b < L; ++b) {
         float t[L];
@@ -37,7 +41,10 @@ __device__ __forceinline__ void tree_message(const float (&bel)[L], const float*
 #pragma unroll
         for (int x = 0; x < L; ++x) s += expf(t[x] - mx);
         out[b] = mx + logf(s);
+        top = fmaxf(top, out[b]);
     }
+#pragma unroll
+    for (int b = 0; b < L; ++b) out[b] -= top;
 }
 
 template <int L>
