@@ -161,6 +161,37 @@ enum { MRF_K_DUAL = 0, MRF_K_PRIMAL = 1, MRF_K_FUSED = 2, MRF_K_POTENTIAL = 3, M
  * call (CUDA events on the handle's stream); resets the totals.  Synchronises. */
 mrf_status mrf_kernel_times(mrf_t* h, double* ms, int64_t* launches);
 
+/* Capacity, in 32-bit words, of the fixed device array that holds the dual
+ * bits of mrf_sweep_noalloc (16 MiB). */
+#define MRF_NOALLOC_THETA_WORDS (1u << 22)
+
+/* One plain sweep that allocates no device memory.  The paper has no
+ * counterpart: this is for callers that cannot allocate device memory at the
+ * moment they sweep, such as code recording a stream into a CUDA graph under
+ * a framework that forbids allocation during capture, or code that keeps all
+ * device memory inside its own fixed pool and wants to push several label sets
+ * of its own through one loaded model.
+ *   h           a handle after mrf_set_factors (its tables are the inputs)
+ *   labels_in   device pointer, [n_vars][n_chains] uint8 labels (chain
+ *               innermost), the state before the sweep; not modified
+ *   labels_out  device pointer, [n_vars][n_chains] uint8, receives the new
+ *               labels; must not overlap labels_in
+ *   sweep_index index t of the sweep in the random-draw contract
+ * The result equals that of mrf_sweep(h, 1, MRF_MODE_PLAIN) from the same
+ * labels at sweep index t.  The handle's own labels, sweep index and counts
+ * are neither read nor changed.  The dual bits go to a file-scope device array
+ * of MRF_NOALLOC_THETA_WORDS words instead of a buffer of the handle; every GPU
+ * that loads the library holds that array until the process exits.  The first
+ * call on a device looks up the array's device address (once per device, with
+ * that device current); make that first call before any stream capture.  All
+ * calls share the one array and each overwrites it, so calls whose work
+ * overlaps on the GPU (other streams, other threads) race.  Work is enqueued
+ * on the handle's stream; the call returns without synchronising.
+ * Errors: MRF_ERANGE when edge slots x chains x ceil(m/32) exceeds
+ * MRF_NOALLOC_THETA_WORDS; MRF_EINVAL for null or overlapping buffers;
+ * MRF_ESTATE before mrf_set_factors. */
+mrf_status mrf_sweep_noalloc(mrf_t* h, const uint8_t* labels_in, uint8_t* labels_out, int64_t sweep_index);
+
 const char* mrf_last_error(const mrf_t* h);
 const char* mrf_status_string(mrf_status s);
 void mrf_destroy(mrf_t* h);

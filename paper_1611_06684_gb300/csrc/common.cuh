@@ -111,6 +111,9 @@ cudaError_t launch_splash(const SweepArgs& a, int layout, cudaStream_t s);
 cudaError_t launch_splash_offset(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_potential(const SweepArgs& a, int layout, cudaStream_t s);
 cudaError_t launch_ffbs(const SweepArgs& a, cudaStream_t s);
+cudaError_t noalloc_scratch(uint32_t** out);
+cudaError_t launch_sweep_noalloc(const SweepArgs& a, int layout, const uint8_t* xin, uint8_t* xout, uint32_t sweep,
+                                 cudaStream_t s);
 cudaError_t launch_labels_to_abi(const uint8_t* x, uint8_t* y, int N, int C, cudaStream_t s);
 cudaError_t launch_labels_from_abi(const uint8_t* y, uint8_t* x, int N, int C, cudaStream_t s);
 cudaError_t launch_count_ge(const uint8_t* y, int64_t n, int L, unsigned long long* bad, cudaStream_t s);

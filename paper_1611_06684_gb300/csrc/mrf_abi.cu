@@ -647,4 +647,26 @@ mrf_status mrf_debug_theta(mrf_t* h, uint32_t* out) {
     return MRF_OK;
 }
 
+mrf_status mrf_sweep_noalloc(mrf_t* h, const uint8_t* labels_in, uint8_t* labels_out, int64_t sweep_index) {
+    if (!h) return MRF_EINVAL;
+    if (!h->has_factors) return fail(h, MRF_ESTATE, "mrf_set_factors first");
+    if (!labels_in || !labels_out) return fail(h, MRF_EINVAL, "null label buffer");
+    const uint64_t NC = (uint64_t)h->N * h->C;
+    if (labels_in < labels_out + NC && labels_out < labels_in + NC) return fail(h, MRF_EINVAL, "label buffers overlap");
+    if (sweep_index < 0 || sweep_index >= ((int64_t)1 << 32)) return fail(h, MRF_EINVAL, "sweep index out of range");
+    const uint64_t words = (uint64_t)h->E_slots * h->C * h->W;
+    if (words > MRF_NOALLOC_THETA_WORDS)
+        return fail(h, MRF_ERANGE, "edge slots x chains x ceil(m/32) = " + std::to_string(words) +
+                                       " words exceeds the static scratch of " +
+                                       std::to_string(MRF_NOALLOC_THETA_WORDS) + " words");
+    uint32_t* scratch = nullptr;
+    MRF_CUDA(h, noalloc_scratch(&scratch));
+    SweepArgs a = make_args(h);
+    a.ctl = reinterpret_cast<Ctl*>(scratch);
+    a.theta = scratch + 64;
+    a.logp = nullptr;
+    MRF_CUDA(h, launch_sweep_noalloc(a, h->layout, labels_in, labels_out, (uint32_t)sweep_index, h->stream));
+    return MRF_OK;
+}
+
 }  // extern "C"

@@ -58,6 +58,7 @@ _SIGS = {
     "mrf_debug_logp": (ct.c_int, [_P, _P, ct.POINTER(ct.c_uint64)]),
     "mrf_debug_theta": (ct.c_int, [_P, _P]),
     "mrf_kernel_times": (ct.c_int, [_P, _P, _P]),
+    "mrf_sweep_noalloc": (ct.c_int, [_P, _P, _P, ct.c_int64]),
     "mrf_last_error": (ct.c_char_p, [_P]),
     "mrf_status_string": (ct.c_char_p, [ct.c_int]),
     "mrf_destroy": (None, [_P]),
@@ -232,6 +233,11 @@ class MRF:
         b = ct.c_uint64()
         self._check(self.lib.mrf_debug_logp(self.h, None, ct.byref(b)))
         return b.value
+
+    def sweep_noalloc(self, labels_in, labels_out, sweep_index: int):
+        """One plain sweep without device allocation (mrf_sweep_noalloc): labels
+        are CUDA tensors [n_vars][n_chains] uint8 owned by the caller."""
+        self._check(self.lib.mrf_sweep_noalloc(self.h, labels_in.data_ptr(), labels_out.data_ptr(), int(sweep_index)))
 
     def kernel_times(self):
         """{kernel name: (total ms, launches)} since the previous call."""
