@@ -86,6 +86,9 @@ typedef struct {
     int64_t sweep_index;    /* index t of the next sweep                          */
     int64_t n_samples;      /* label samples accumulated per site (sweeps x chains) */
     double log_const;       /* log p~(x) = log sum_theta p~(x,theta) + log_const  */
+    int32_t schedule;       /* primal schedule picked by the autotuner: 1 thread per
+                               (site, chain), 2 CTA per site; 0 before the first sweep */
+    float tune_ms_thread, tune_ms_cta;   /* the autotuner's timings per launch      */
 } mrf_info;
 
 /* Fill *opt with defaults (no lattice, no logp record, graphs on, auto schedule). */
@@ -160,6 +163,58 @@ enum { MRF_K_DUAL = 0, MRF_K_PRIMAL = 1, MRF_K_FUSED = 2, MRF_K_POTENTIAL = 3, M
  * launch counts launches[MRF_K_COUNT] of every sweep kernel since the last
  * call (CUDA events on the handle's stream); resets the totals.  Synchronises. */
 mrf_status mrf_kernel_times(mrf_t* h, double* ms, int64_t* launches);
+
+/* ---- Batches of uneven graphs (dynamic-network workloads) --------------------
+ * Many independent graphs, each with its own size and label count, sampled
+ * together.  Graphs with the same L form one class; a class is the disjoint
+ * union of its graphs and is swept by the same kernels as a single model, so
+ * a batch sweep is a handful of launches (one dual and one primal kernel per
+ * class) replayed as one CUDA graph, independent of the number of graphs.
+ * Random draws of class L use the key of seed + L * 0x9E3779B97F4A7C15 and the
+ * class-union site and edge-slot indices. */
+typedef struct mrf_batch mrf_batch_t;
+
+typedef struct {
+    int32_t n_vars, n_labels;
+    int32_t class_index;       /* class (sorted by L) that holds the graph            */
+    int32_t site_offset;       /* first site of the graph in its class union          */
+    int64_t first_edge_slot;   /* slot of the graph's edge 0 after mrf_batch_set_factors */
+} mrf_batch_graph_info;
+
+/* n_graphs graphs with n_vars[g] sites and n_labels[g] in [2,16] labels; every
+ * graph gets n_chains chains. */
+mrf_status mrf_batch_create(mrf_batch_t** out, int32_t n_graphs, const int32_t* n_vars, const int32_t* n_labels,
+                            int32_t n_chains, uint64_t seed, const mrf_options* opt, void* cuda_stream);
+
+/* All graphs at once, host memory, concatenated in graph order: unary_log
+ * (graph g: [n_vars[g]][L_g]), n_edges[g], src/dst (graph-local site ids), and
+ * pair_log (graph g's edges: [L_g][L_g] each).  Same checks as mrf_set_factors. */
+mrf_status mrf_batch_set_factors(mrf_batch_t* b, const float* unary_log, const int64_t* n_edges,
+                                 const int32_t* src, const int32_t* dst, const float* pair_log);
+
+/* One edit of many graphs (host memory): remove the edges (remove_graph[i],
+ * remove_slot[i]) -- slots are class-union slots as reported by
+ * mrf_batch_graph_info and earlier edits -- and add edges (add_graph[i],
+ * src[i], dst[i]) with graph-local ids and tables pair_log (L_g x L_g each,
+ * concatenated).  Slots of the added edges go to out_slots.  Per class the
+ * freed slots are reused in increasing order (mrf_edit_factors). */
+mrf_status mrf_batch_edit_factors(mrf_batch_t* b, int64_t n_remove, const int32_t* remove_graph,
+                                  const int64_t* remove_slot, int64_t n_add, const int32_t* add_graph,
+                                  const int32_t* src, const int32_t* dst, const float* pair_log, int64_t* out_slots);
+
+/* n_sweeps sweeps of every graph (MRF_MODE_PLAIN or MRF_MODE_FUSED). */
+mrf_status mrf_batch_sweep(mrf_batch_t* b, int32_t n_sweeps, int32_t mode);
+mrf_status mrf_batch_reset_marginals(mrf_batch_t* b, int32_t burn_in_sweeps);
+/* Counts [n_vars[g]][L_g] and labels [n_chains][n_vars[g]] of graph g (host). */
+mrf_status mrf_batch_get_counts(mrf_batch_t* b, int32_t graph, uint32_t* out);
+mrf_status mrf_batch_get_labels(mrf_batch_t* b, int32_t graph, uint8_t* out);
+mrf_status mrf_batch_graph(const mrf_batch_t* b, int32_t graph, mrf_batch_graph_info* out);
+/* Number of classes and the mrf_t of class k (for info, timing and debug views;
+ * owned by the batch). */
+int32_t mrf_batch_n_classes(const mrf_batch_t* b);
+mrf_t* mrf_batch_class(mrf_batch_t* b, int32_t k);
+const char* mrf_batch_last_error(const mrf_batch_t* b);
+void mrf_batch_destroy(mrf_batch_t* b);
 
 /* Capacity, in 32-bit words, of the fixed device array that holds the dual
  * bits of mrf_sweep_noalloc (16 MiB). */

@@ -111,6 +111,10 @@ cudaError_t launch_splash(const SweepArgs& a, int layout, cudaStream_t s);
 cudaError_t launch_splash_offset(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_potential(const SweepArgs& a, int layout, cudaStream_t s);
 cudaError_t launch_ffbs(const SweepArgs& a, cudaStream_t s);
+cudaError_t build_csr_device(const int32_t* src, const int32_t* dst, int64_t E, int N, int64_t* ptr, int2* inc,
+                             int32_t* work, int64_t* sums, unsigned long long* too_long, int max_deg, cudaStream_t s);
+cudaError_t launch_scatter_edges(const int64_t* slots, const int32_t* s, const int32_t* t, int64_t n, int32_t* src,
+                                 int32_t* dst, cudaStream_t st);
 cudaError_t noalloc_scratch(uint32_t** out);
 cudaError_t launch_sweep_noalloc(const SweepArgs& a, int layout, const uint8_t* xin, uint8_t* xout, uint32_t sweep,
                                  cudaStream_t s);

@@ -48,6 +48,12 @@ struct mrf {
     cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
     uint8_t* d_stage = nullptr;        // [C][N] staging for the ABI label view
     float* d_pot = nullptr;            // [N][L][C] node potentials of the blocked sweep
+    int schedule = 0;                  // primal schedule in use (1 thread, 2 CTA); 0 = not tuned yet
+    int32_t* d_csr_work = nullptr;     // [2N] degrees and cursors of the device CSR build
+    int64_t* d_csr_sums = nullptr;     // block sums of the device scan
+    int64_t inc_cap = 0;               // capacity of d_inc (incidences)
+    int64_t n_device_csr = 0, n_host_csr = 0;   // CSR builds after edits, by path
+    float tune_ms[2] = {0.0f, 0.0f};   // autotuner timings (thread, CTA) per primal launch
     // kernel timing (options.kernel_timing)
     struct Rec { int id; cudaEvent_t a, b; };
     std::vector<Rec> pending;
@@ -173,6 +179,7 @@ cudaError_t build_csr(mrf_t* h) {
     cudaError_t err;
     if ((err = dalloc(h->d_inc_ptr, ptr.size())) != cudaSuccess) return err;
     if ((err = dalloc(h->d_inc, std::max<size_t>(inc.size(), 1))) != cudaSuccess) return err;
+    h->inc_cap = (int64_t)inc.size();
     if ((err = cudaMemcpyAsync(h->d_inc_ptr, ptr.data(), ptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
                                h->stream)) != cudaSuccess)
         return err;
@@ -295,6 +302,7 @@ void mrf_destroy(mrf_t* h) {
     dfree(h->d_unary); dfree(h->d_ut); dfree(h->d_utf); dfree(h->d_tpl); dfree(h->d_src); dfree(h->d_dst); dfree(h->d_tau); dfree(h->d_thr);
     dfree(h->d_fold); dfree(h->d_cst); dfree(h->d_resid); dfree(h->d_inc_ptr); dfree(h->d_inc); dfree(h->d_x);
     dfree(h->d_theta); dfree(h->d_counts); dfree(h->d_logp); dfree(h->d_ctl); dfree(h->d_flag); dfree(h->d_stage); dfree(h->d_pot);
+    dfree(h->d_csr_work); dfree(h->d_csr_sums);
     for (auto& r : h->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : h->pool) cudaEventDestroy(e);
     delete h;
@@ -366,6 +374,7 @@ mrf_status mrf_set_factors(mrf_t* h, const float* unary_log, int64_t n_edges, co
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));
     h->log_const = std::accumulate(cst.begin(), cst.end(), 0.0);
     h->has_factors = true;
+    h->schedule = 0;
     return MRF_OK;
 }
 
@@ -447,23 +456,83 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
     }
     h->h_src.resize(new_slots, -1); h->h_dst.resize(new_slots, -1);
     for (int64_t i = 0; i < n_add; ++i) { h->h_src[slots[i]] = as[i]; h->h_dst[slots[i]] = at[i]; }
+    // device: removed slots get src = dst = -1, new slots their endpoints
+    std::vector<int64_t> upd_slot(rem.begin(), rem.end());
+    upd_slot.insert(upd_slot.end(), slots.begin(), slots.end());
+    std::vector<int32_t> upd_s((size_t)n_remove, -1), upd_t((size_t)n_remove, -1);
+    upd_s.insert(upd_s.end(), as.begin(), as.end());
+    upd_t.insert(upd_t.end(), at.begin(), at.end());
+    const int64_t n_upd = (int64_t)upd_slot.size();
+    int64_t* d_slots = nullptr;
+    int32_t* d_us = nullptr;
+    int32_t* d_ut2 = nullptr;
+    MRF_CUDA(h, dalloc(d_slots, (size_t)n_upd)); MRF_CUDA(h, dalloc(d_us, (size_t)n_upd)); MRF_CUDA(h, dalloc(d_ut2, (size_t)n_upd));
+    struct Guard2 { int64_t*& p; int32_t*& q; int32_t*& r; ~Guard2() { dfree(p); dfree(q); dfree(r); } } guard2{d_slots, d_us, d_ut2};
+    MRF_CUDA(h, to_device(d_slots, upd_slot.data(), n_upd, MRF_PTR_HOST, h->stream));
+    MRF_CUDA(h, to_device(d_us, upd_s.data(), n_upd, MRF_PTR_HOST, h->stream));
+    MRF_CUDA(h, to_device(d_ut2, upd_t.data(), n_upd, MRF_PTR_HOST, h->stream));
+    if (new_slots > h->E_slots) {     // fresh slots start free on the device too
+        std::vector<int32_t> neg((size_t)(new_slots - h->E_slots), -1);
+        MRF_CUDA(h, to_device(h->d_src + h->E_slots, neg.data(), new_slots - h->E_slots, MRF_PTR_HOST, h->stream));
+        MRF_CUDA(h, to_device(h->d_dst + h->E_slots, neg.data(), new_slots - h->E_slots, MRF_PTR_HOST, h->stream));
+    }
+    MRF_CUDA(h, launch_scatter_edges(d_slots, d_us, d_ut2, n_upd, h->d_src, h->d_dst, h->stream));
     h->E_slots = new_slots;
     h->E_live += n_add - n_remove;
-    MRF_CUDA(h, to_device(h->d_src, h->h_src.data(), new_slots, MRF_PTR_HOST, h->stream));
-    MRF_CUDA(h, to_device(h->d_dst, h->h_dst.data(), new_slots, MRF_PTR_HOST, h->stream));
-    int64_t* d_slots = nullptr;
-    MRF_CUDA(h, dalloc(d_slots, (size_t)n_add));
-    struct Guard2 { int64_t*& p; ~Guard2() { dfree(p); } } guard2{d_slots};
-    MRF_CUDA(h, to_device(d_slots, slots.data(), n_add, MRF_PTR_HOST, h->stream));
     DecompArgs d{};
-    d.L = L; d.M = h->M; d.layout = h->layout; d.n = n_add; d.slots = d_slots;
+    d.L = L; d.M = h->M; d.layout = h->layout; d.n = n_add; d.slots = d_slots + n_remove;
     d.pair = d_pair; d.tau = h->d_tau; d.thr = h->d_thr; d.fold = h->d_fold; d.cst = h->d_cst; d.resid = nullptr;
     MRF_CUDA(h, launch_decompose(d, h->stream));
-    MRF_CUDA(h, launch_build_planes(h->d_thr, n_add, d_slots, 0, h->M, h->d_tpl, h->stream));
-    MRF_CUDA(h, build_csr(h));
+    MRF_CUDA(h, launch_build_planes(h->d_thr, n_add, d_slots + n_remove, 0, h->M, h->d_tpl, h->stream));
+    // incidence lists rebuilt on the device (host build if a site is very long)
+    if (2 * h->E_live > h->inc_cap) {
+        MRF_CUDA(h, dalloc(h->d_inc, (size_t)(2 * h->E_live + h->E_live / 4 + 64)));
+        h->inc_cap = 2 * h->E_live + h->E_live / 4 + 64;
+    }
+    if (!h->d_csr_work) {
+        MRF_CUDA(h, dalloc(h->d_csr_work, 2 * (size_t)N + 2));
+        MRF_CUDA(h, dalloc(h->d_csr_sums, (size_t)((N + 1 + 1023) / 1024 + 2)));
+    }
+    MRF_CUDA(h, cudaMemsetAsync(h->d_flag, 0, sizeof(unsigned long long), h->stream));
+    MRF_CUDA(h, build_csr_device(h->d_src, h->d_dst, h->E_slots, N, h->d_inc_ptr, h->d_inc, h->d_csr_work,
+                                 h->d_csr_sums, h->d_flag, 512, h->stream));
+    unsigned long long too_long = 0;
+    MRF_CUDA(h, cudaMemcpyAsync(&too_long, h->d_flag, sizeof(too_long), cudaMemcpyDeviceToHost, h->stream));
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (too_long) { MRF_CUDA(h, build_csr(h)); h->n_host_csr++; } else h->n_device_csr++;
     MRF_CUDA(h, launch_fold_unary(h->d_unary, h->d_fold, h->d_inc_ptr, h->d_inc, N, L, h->d_ut, h->d_utf, h->stream));
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->schedule = 0;
     std::copy(slots.begin(), slots.end(), out_new_ids);
+    return MRF_OK;
+}
+
+// Autotuner for the plain primal schedule: with theta of the coming sweep in
+// place, time the thread-per-(site, chain) and CTA-per-site kernels (each only
+// rewrites the next label buffer from the same theta, so the chain state is
+// unchanged) and keep the faster.  The boundary counter is restored after.
+static mrf_status tune_schedule(mrf_t* h) {
+    if (h->opt.schedule == 1 || h->opt.schedule == 2) { h->schedule = h->opt.schedule; return MRF_OK; }
+    SweepArgs a = make_args(h);
+    a.logp = nullptr;
+    unsigned long long bnd = 0;
+    MRF_CUDA(h, cudaMemcpyAsync(&bnd, &h->d_ctl->boundary, sizeof(bnd), cudaMemcpyDeviceToHost, h->stream));
+    MRF_CUDA(h, launch_dual(a, h->layout, h->stream));
+    cudaEvent_t e0 = take_event(h), e1 = take_event(h);
+    for (int sched = 1; sched <= 2; ++sched) {
+        MRF_CUDA(h, launch_primal(a, h->layout, sched, h->stream));     // warm
+        MRF_CUDA(h, cudaEventRecord(e0, h->stream));
+        for (int r = 0; r < 3; ++r) MRF_CUDA(h, launch_primal(a, h->layout, sched, h->stream));
+        MRF_CUDA(h, cudaEventRecord(e1, h->stream));
+        MRF_CUDA(h, cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        MRF_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
+        h->tune_ms[sched - 1] = ms / 3.0f;
+    }
+    h->pool.push_back(e0); h->pool.push_back(e1);
+    MRF_CUDA(h, cudaMemcpyAsync(&h->d_ctl->boundary, &bnd, sizeof(bnd), cudaMemcpyHostToDevice, h->stream));
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->schedule = h->tune_ms[1] < 0.9f * h->tune_ms[0] ? 2 : 1;
     return MRF_OK;
 }
 
@@ -473,7 +542,7 @@ static mrf_status enqueue_sweep(mrf_t* h, int mode) {
     cudaError_t e = cudaSuccess;
     if (mode == MRF_MODE_PLAIN) {
         e = timed(h, MRF_K_DUAL, [&] { return launch_dual(a, h->layout, s); });
-        if (e == cudaSuccess) e = timed(h, MRF_K_PRIMAL, [&] { return launch_primal(a, h->layout, h->opt.schedule, s); });
+        if (e == cudaSuccess) e = timed(h, MRF_K_PRIMAL, [&] { return launch_primal(a, h->layout, h->schedule, s); });
     } else if (mode == MRF_MODE_FUSED) {
         e = timed(h, MRF_K_FUSED, [&] { return launch_fused(a, h->layout, h->opt.schedule, s); });
     } else {
@@ -497,6 +566,10 @@ mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode) {
     if (mode == MRF_MODE_SPLASH && !h->d_pot) {
         drop_graphs(h);
         MRF_CUDA(h, dalloc(h->d_pot, (size_t)h->N * h->L * h->C));
+    }
+    if (mode == MRF_MODE_PLAIN && h->schedule == 0 && n_sweeps > 0) {
+        mrf_status st = tune_schedule(h);
+        if (st != MRF_OK) return st;
     }
     const bool graphs = h->opt.use_graphs && h->stream != nullptr && !h->opt.kernel_timing;
     if (graphs && !h->graph[mode] && n_sweeps > 0) {
@@ -610,6 +683,9 @@ mrf_status mrf_get_info(const mrf_t* h, mrf_info* out) {
     out->n_edges = h->E_live; out->n_edge_slots = h->E_slots; out->sweep_index = h->sweep_host;
     out->n_samples = std::max<int64_t>(0, h->sweep_host - h->count_from_host) * h->C;
     out->log_const = h->log_const;
+    out->schedule = h->schedule;
+    out->tune_ms_thread = h->tune_ms[0];
+    out->tune_ms_cta = h->tune_ms[1];
     return MRF_OK;
 }
 
@@ -666,6 +742,269 @@ mrf_status mrf_sweep_noalloc(mrf_t* h, const uint8_t* labels_in, uint8_t* labels
     a.theta = scratch + 64;
     a.logp = nullptr;
     MRF_CUDA(h, launch_sweep_noalloc(a, h->layout, labels_in, labels_out, (uint32_t)sweep_index, h->stream));
+    return MRF_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================ batches
+
+struct mrf_batch {
+    int32_t G = 0, C = 0;
+    uint64_t seed = 0;
+    cudaStream_t stream = nullptr;
+    mrf_options opt{};
+    std::vector<int32_t> n_vars, n_labels, cls, site_off;
+    std::vector<int64_t> edge_off;
+    std::vector<int32_t> class_L, class_N;
+    std::vector<std::vector<int32_t>> class_graphs;
+    std::vector<mrf_t*> h;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    std::string err;
+};
+
+namespace {
+
+mrf_status bfail(mrf_batch_t* b, mrf_status st, const std::string& msg) {
+    if (b) b->err = msg;
+    return st;
+}
+
+void drop_batch_graphs(mrf_batch_t* b) {
+    for (auto& g : b->graph)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
+mrf_status class_status(mrf_batch_t* b, int k, mrf_status st) {
+    if (st != MRF_OK) b->err = "class L=" + std::to_string(b->class_L[k]) + ": " + b->h[k]->err;
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+mrf_status mrf_batch_create(mrf_batch_t** out, int32_t n_graphs, const int32_t* n_vars, const int32_t* n_labels,
+                            int32_t n_chains, uint64_t seed, const mrf_options* opt, void* cuda_stream) {
+    if (!out || n_graphs <= 0 || !n_vars || !n_labels || n_chains <= 0) return MRF_EINVAL;
+    *out = nullptr;
+    mrf_batch_t* b = new mrf_batch_t();
+    b->G = n_graphs; b->C = n_chains; b->seed = seed; b->stream = (cudaStream_t)cuda_stream;
+    if (opt) b->opt = *opt; else mrf_default_options(&b->opt);
+    b->n_vars.assign(n_vars, n_vars + n_graphs);
+    b->n_labels.assign(n_labels, n_labels + n_graphs);
+    for (int g = 0; g < n_graphs; ++g) {
+        if (n_vars[g] <= 0) { delete b; return MRF_EINVAL; }
+        if (n_labels[g] < 2 || n_labels[g] > kMaxLabels) { delete b; return MRF_ERANGE; }
+    }
+    std::vector<int32_t> Ls(b->n_labels);
+    std::sort(Ls.begin(), Ls.end());
+    Ls.erase(std::unique(Ls.begin(), Ls.end()), Ls.end());
+    b->class_L = Ls;
+    b->class_N.assign(Ls.size(), 0);
+    b->class_graphs.assign(Ls.size(), {});
+    b->cls.assign(n_graphs, 0);
+    b->site_off.assign(n_graphs, 0);
+    b->edge_off.assign(n_graphs, 0);
+    for (int g = 0; g < n_graphs; ++g) {
+        const int k = (int)(std::lower_bound(Ls.begin(), Ls.end(), n_labels[g]) - Ls.begin());
+        b->cls[g] = k;
+        if ((int64_t)b->class_N[k] + n_vars[g] >= (1ll << 31)) { delete b; return MRF_ERANGE; }
+        b->site_off[g] = b->class_N[k];
+        b->class_N[k] += n_vars[g];
+        b->class_graphs[k].push_back(g);
+    }
+    mrf_options copt = b->opt;
+    copt.use_graphs = 0;          // the batch captures all classes together
+    copt.grid_nx = copt.grid_ny = copt.grid_nz = 0;
+    for (size_t k = 0; k < Ls.size(); ++k) {
+        mrf_t* hk = nullptr;
+        const uint64_t ks = seed + (uint64_t)Ls[k] * 0x9E3779B97F4A7C15ull;
+        mrf_status st = mrf_create(&hk, b->class_N[k], Ls[k], n_chains, ks, &copt, cuda_stream);
+        if (st != MRF_OK) { mrf_batch_destroy(b); return st; }
+        b->h.push_back(hk);
+    }
+    *out = b;
+    return MRF_OK;
+}
+
+void mrf_batch_destroy(mrf_batch_t* b) {
+    if (!b) return;
+    drop_batch_graphs(b);
+    for (auto* hk : b->h) mrf_destroy(hk);
+    delete b;
+}
+
+const char* mrf_batch_last_error(const mrf_batch_t* b) { return b ? b->err.c_str() : "null batch"; }
+int32_t mrf_batch_n_classes(const mrf_batch_t* b) { return b ? (int32_t)b->h.size() : 0; }
+mrf_t* mrf_batch_class(mrf_batch_t* b, int32_t k) { return (b && k >= 0 && k < (int)b->h.size()) ? b->h[k] : nullptr; }
+
+mrf_status mrf_batch_graph(const mrf_batch_t* b, int32_t g, mrf_batch_graph_info* out) {
+    if (!b || !out || g < 0 || g >= b->G) return MRF_EINVAL;
+    out->n_vars = b->n_vars[g]; out->n_labels = b->n_labels[g]; out->class_index = b->cls[g];
+    out->site_offset = b->site_off[g]; out->first_edge_slot = b->edge_off[g];
+    return MRF_OK;
+}
+
+mrf_status mrf_batch_set_factors(mrf_batch_t* b, const float* unary_log, const int64_t* n_edges, const int32_t* src,
+                                 const int32_t* dst, const float* pair_log) {
+    if (!b || !unary_log || !n_edges) return MRF_EINVAL;
+    drop_batch_graphs(b);
+    const int G = b->G, K = (int)b->h.size();
+    std::vector<int64_t> u_off(G + 1, 0), e_off(G + 1, 0), p_off(G + 1, 0);
+    for (int g = 0; g < G; ++g) {
+        if (n_edges[g] < 0) return bfail(b, MRF_EINVAL, "negative edge count");
+        const int64_t L = b->n_labels[g];
+        u_off[g + 1] = u_off[g] + (int64_t)b->n_vars[g] * L;
+        e_off[g + 1] = e_off[g] + n_edges[g];
+        p_off[g + 1] = p_off[g] + n_edges[g] * L * L;
+    }
+    if (e_off[G] > 0 && (!src || !dst || !pair_log)) return bfail(b, MRF_EINVAL, "null edge arrays");
+    for (int k = 0; k < K; ++k) {
+        const int L = b->class_L[k];
+        std::vector<float> u, p;
+        std::vector<int32_t> s, t;
+        int64_t ne = 0;
+        for (int g : b->class_graphs[k]) ne += n_edges[g];
+        u.reserve((size_t)b->class_N[k] * L); s.reserve(ne); t.reserve(ne); p.reserve((size_t)ne * L * L);
+        int64_t slot = 0;
+        for (int g : b->class_graphs[k]) {
+            u.insert(u.end(), unary_log + u_off[g], unary_log + u_off[g + 1]);
+            b->edge_off[g] = slot;
+            for (int64_t e = e_off[g]; e < e_off[g + 1]; ++e) {
+                const int32_t a = src[e], c = dst[e];
+                if (a < 0 || a >= b->n_vars[g] || c < 0 || c >= b->n_vars[g])
+                    return bfail(b, MRF_ERANGE, "graph " + std::to_string(g) + ": vertex id out of range");
+                s.push_back(a + b->site_off[g]);
+                t.push_back(c + b->site_off[g]);
+            }
+            p.insert(p.end(), pair_log + p_off[g], pair_log + p_off[g + 1]);
+            slot += n_edges[g];
+        }
+        mrf_status st = mrf_set_factors(b->h[k], u.data(), ne, s.data(), t.data(), p.data(), MRF_PTR_HOST);
+        if (st != MRF_OK) return class_status(b, k, st);
+    }
+    return MRF_OK;
+}
+
+mrf_status mrf_batch_edit_factors(mrf_batch_t* b, int64_t n_remove, const int32_t* remove_graph,
+                                  const int64_t* remove_slot, int64_t n_add, const int32_t* add_graph,
+                                  const int32_t* src, const int32_t* dst, const float* pair_log, int64_t* out_slots) {
+    if (!b || n_remove < 0 || n_add < 0) return MRF_EINVAL;
+    if ((n_remove && (!remove_graph || !remove_slot)) || (n_add && (!add_graph || !src || !dst || !pair_log || !out_slots)))
+        return bfail(b, MRF_EINVAL, "null edit arrays");
+    drop_batch_graphs(b);
+    const int K = (int)b->h.size();
+    std::vector<std::vector<int64_t>> rm(K);
+    for (int64_t i = 0; i < n_remove; ++i) {
+        const int g = remove_graph[i];
+        if (g < 0 || g >= b->G) return bfail(b, MRF_ERANGE, "edit: graph id out of range");
+        rm[b->cls[g]].push_back(remove_slot[i]);
+    }
+    std::vector<std::vector<int64_t>> idx(K);
+    std::vector<std::vector<int32_t>> s(K), t(K);
+    std::vector<std::vector<float>> p(K);
+    int64_t poff = 0;
+    for (int64_t i = 0; i < n_add; ++i) {
+        const int g = add_graph[i];
+        if (g < 0 || g >= b->G) return bfail(b, MRF_ERANGE, "edit: graph id out of range");
+        const int k = b->cls[g], L = b->n_labels[g];
+        if (src[i] < 0 || src[i] >= b->n_vars[g] || dst[i] < 0 || dst[i] >= b->n_vars[g])
+            return bfail(b, MRF_ERANGE, "edit: vertex id out of range");
+        idx[k].push_back(i);
+        s[k].push_back(src[i] + b->site_off[g]);
+        t[k].push_back(dst[i] + b->site_off[g]);
+        p[k].insert(p[k].end(), pair_log + poff, pair_log + poff + (int64_t)L * L);
+        poff += (int64_t)L * L;
+    }
+    for (int k = 0; k < K; ++k) {
+        if (rm[k].empty() && idx[k].empty()) continue;
+        std::vector<int64_t> ids(idx[k].size());
+        mrf_status st = mrf_edit_factors(b->h[k], (int64_t)rm[k].size(), rm[k].data(), (int64_t)idx[k].size(),
+                                         s[k].data(), t[k].data(), p[k].data(), ids.data(), MRF_PTR_HOST);
+        if (st != MRF_OK) return class_status(b, k, st);
+        for (size_t j = 0; j < ids.size(); ++j) out_slots[idx[k][j]] = ids[j];
+    }
+    return MRF_OK;
+}
+
+mrf_status mrf_batch_sweep(mrf_batch_t* b, int32_t n_sweeps, int32_t mode) {
+    if (!b) return MRF_EINVAL;
+    if (n_sweeps < 0 || (mode != MRF_MODE_PLAIN && mode != MRF_MODE_FUSED)) return bfail(b, MRF_EINVAL, "bad sweep count or mode");
+    const int K = (int)b->h.size();
+    for (int k = 0; k < K; ++k) {
+        if (!b->h[k]->has_factors) return bfail(b, MRF_ESTATE, "mrf_batch_set_factors first");
+        if (mode == MRF_MODE_PLAIN && b->h[k]->schedule == 0 && n_sweeps > 0) {
+            mrf_status st = tune_schedule(b->h[k]);
+            if (st != MRF_OK) return class_status(b, k, st);
+        }
+    }
+    const bool graphs = b->opt.use_graphs && b->stream != nullptr && !b->opt.kernel_timing;
+    if (graphs && !b->graph[mode] && n_sweeps > 0) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return bfail(b, MRF_ECUDA, "stream capture failed");
+        mrf_status st = MRF_OK;
+        for (int k = 0; k < K && st == MRF_OK; ++k) st = enqueue_sweep(b->h[k], mode);
+        cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+        if (st != MRF_OK || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return bfail(b, st != MRF_OK ? st : MRF_ECUDA, "batch graph capture failed");
+        }
+        ce = cudaGraphInstantiate(&b->graph[mode], g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) { cudaGetLastError(); return bfail(b, MRF_ECUDA, "batch graph instantiate failed"); }
+    }
+    for (int i = 0; i < n_sweeps; ++i) {
+        if (graphs) {
+            if (cudaGraphLaunch(b->graph[mode], b->stream) != cudaSuccess) { cudaGetLastError(); return bfail(b, MRF_ECUDA, "graph launch"); }
+        } else {
+            for (int k = 0; k < K; ++k) {
+                mrf_status st = enqueue_sweep(b->h[k], mode);
+                if (st != MRF_OK) return class_status(b, k, st);
+            }
+        }
+    }
+    for (int k = 0; k < K; ++k) b->h[k]->sweep_host += n_sweeps;
+    return MRF_OK;
+}
+
+mrf_status mrf_batch_reset_marginals(mrf_batch_t* b, int32_t burn_in_sweeps) {
+    if (!b) return MRF_EINVAL;
+    for (int k = 0; k < (int)b->h.size(); ++k) {
+        mrf_status st = mrf_reset_marginals(b->h[k], burn_in_sweeps);
+        if (st != MRF_OK) return class_status(b, k, st);
+    }
+    return MRF_OK;
+}
+
+mrf_status mrf_batch_get_counts(mrf_batch_t* b, int32_t g, uint32_t* out) {
+    if (!b || !out || g < 0 || g >= b->G) return MRF_EINVAL;
+    mrf_t* h = b->h[b->cls[g]];
+    const size_t L = (size_t)b->n_labels[g];
+    if (cudaMemcpyAsync(out, h->d_counts + (size_t)b->site_off[g] * L, (size_t)b->n_vars[g] * L * sizeof(uint32_t),
+                        cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, MRF_ECUDA, "copy counts");
+    }
+    return MRF_OK;
+}
+
+mrf_status mrf_batch_get_labels(mrf_batch_t* b, int32_t g, uint8_t* out) {
+    if (!b || !out || g < 0 || g >= b->G) return MRF_EINVAL;
+    mrf_t* h = b->h[b->cls[g]];
+    const size_t n = (size_t)b->n_vars[g], C = (size_t)h->C;
+    std::vector<uint8_t> buf(n * C);
+    const uint8_t* src = h->d_x + (h->sweep_host & 1) * (size_t)h->N * C + (size_t)b->site_off[g] * C;
+    if (cudaMemcpyAsync(buf.data(), src, n * C, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, MRF_ECUDA, "copy labels");
+    }
+    for (size_t v = 0; v < n; ++v)
+        for (size_t c = 0; c < C; ++c) out[c * n + v] = buf[v * C + c];
     return MRF_OK;
 }
 

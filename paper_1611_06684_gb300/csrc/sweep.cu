@@ -7,6 +7,7 @@ namespace mrfk {
 
 template <int L, int LAYOUT> cudaError_t run_dual(const SweepArgs& a, cudaStream_t s);
 template <int L, int LAYOUT, bool FUSED> cudaError_t run_primal(const SweepArgs& a, cudaStream_t s);
+template <int L, int LAYOUT> cudaError_t run_primal_cta(const SweepArgs& a, cudaStream_t s);
 
 __global__ void k_init_labels(SweepArgs a) {
     const int64_t n = (int64_t)a.N * a.C;
@@ -155,8 +156,13 @@ cudaError_t launch_dual(const SweepArgs& a, int layout, cudaStream_t s) {
 }
 
 cudaError_t launch_primal(const SweepArgs& a, int layout, int schedule, cudaStream_t s) {
-    (void)schedule;
-    const int64_t n = (int64_t)a.N * a.C;
+    if (schedule == 2) {
+        if (layout == MRF_LAYOUT_PIVOT) {
+            MRF_DISPATCH_L(a.L, return (run_primal_cta<LL, MRF_LAYOUT_PIVOT>(a, s)));
+        } else {
+            MRF_DISPATCH_L(a.L, return (run_primal_cta<LL, MRF_LAYOUT_DIAG>(a, s)));
+        }
+    }
     if (layout == MRF_LAYOUT_PIVOT) {
         MRF_DISPATCH_L(a.L, return (run_primal<LL, MRF_LAYOUT_PIVOT, false>(a, s)));
     } else {

@@ -352,7 +352,78 @@ __global__ void __launch_bounds__(256, FUSED ? 2 : 4) k_primal(SweepArgs a) {
     xout[g] = (uint8_t)draw_label<L>(F, v, c, sweep, a.key, PH_PRIMAL, lp, a.ctl);
 }
 
+// CTA-per-site schedule of the plain primal step for high-degree sites: a CTA
+// of 256 threads covers one site and CG = min(C, 32) chains; its CG x S threads
+// (S = 256 / CG incidence slices) each sum a strided share of the incidence
+// list for one chain, the S partial sums are combined in shared memory with
+// the two-sum pair, and the first slice draws the labels.
+template <int L, int LAYOUT>
+__global__ void __launch_bounds__(256) k_primal_cta(SweepArgs a, int CG) {
+    using E = Ent<L, LAYOUT>;
+    __shared__ float red_hi[256][L];
+    __shared__ float red_lo[256][L];
+    const int S = 256 / CG;
+    const int lane = threadIdx.x % CG, slice = threadIdx.x / CG;
+    const int groups = (a.C + CG - 1) / CG;
+    const uint32_t v = blockIdx.x / groups;
+    const int c = (blockIdx.x % groups) * CG + lane;
+    const bool active = slice < S && c < a.C;
+    const uint32_t sweep = (uint32_t)a.ctl->sweep;
+    float acc[L], hi[L], lo[L];
+#pragma unroll
+    for (int x = 0; x < L; ++x) { acc[x] = 0.0f; hi[x] = 0.0f; lo[x] = 0.0f; }
+    if (active) {
+        const int64_t p0 = a.inc_ptr[v], p1 = a.inc_ptr[v + 1];
+        int chunk = 0;
+        for (int64_t p = p0 + slice; p < p1; p += S) {
+            const int2 ic = __ldg(&a.inc[p]);
+            const int64_t e = ic.x >> 1;
+            uint32_t bits[E::W];
+            const uint32_t* th = a.theta + (e * a.C + c) * E::W;
+#pragma unroll
+            for (int w = 0; w < E::W; ++w) bits[w] = __ldcs(th + w);
+            add_side<L, LAYOUT>(bits, a.tau + e * E::MP, ic.x & 1, acc);
+            if (++chunk == 32) {
+#pragma unroll
+                for (int x = 0; x < L; ++x) { two_sum_add(hi[x], lo[x], acc[x]); acc[x] = 0.0f; }
+                chunk = 0;
+            }
+        }
+#pragma unroll
+        for (int x = 0; x < L; ++x) two_sum_add(hi[x], lo[x], acc[x]);
+    }
+#pragma unroll
+    for (int x = 0; x < L; ++x) { red_hi[threadIdx.x][x] = hi[x]; red_lo[threadIdx.x][x] = lo[x]; }
+    __syncthreads();
+    if (slice == 0 && c < a.C) {
+#pragma unroll
+        for (int x = 0; x < L; ++x) {
+            float h = 0.0f, l = 0.0f;
+            for (int q = 0; q < S; ++q) {
+                two_sum_add(h, l, red_hi[q * CG + lane][x]);
+                l += red_lo[q * CG + lane][x];
+            }
+            hi[x] = h; lo[x] = l;
+        }
+        float F[L];
+        const float* uf = a.utf + (int64_t)v * L;
+#pragma unroll
+        for (int x = 0; x < L; ++x) F[x] = __ldg(uf + x) + (hi[x] + lo[x]);
+        uint8_t* xout = a.x + (size_t)((sweep + 1) & 1) * a.N * a.C;
+        float* lp = a.logp ? a.logp + ((int64_t)c * a.N + v) * L : nullptr;
+        xout[(int64_t)v * a.C + c] = (uint8_t)draw_label<L>(F, v, (uint32_t)c, sweep, a.key, PH_PRIMAL, lp, a.ctl);
+    }
+}
+
 static inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+template <int L, int LAYOUT>
+cudaError_t run_primal_cta(const SweepArgs& a, cudaStream_t s) {
+    const int CG = a.C >= 32 ? 32 : a.C;
+    const int64_t blocks = (int64_t)a.N * ((a.C + CG - 1) / CG);
+    if (blocks > 0) k_primal_cta<L, LAYOUT><<<(unsigned)blocks, 256, 0, s>>>(a, CG);
+    return cudaGetLastError();
+}
 
 template <int L, int LAYOUT>
 cudaError_t run_dual(const SweepArgs& a, cudaStream_t s) {
@@ -376,6 +447,8 @@ cudaError_t run_potential(const SweepArgs& a, cudaStream_t s) {
 }
 
 #define MRF_INSTANTIATE_SWEEP(L)                                                                 \
+    template cudaError_t run_primal_cta<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, cudaStream_t);     \
+    template cudaError_t run_primal_cta<L, MRF_LAYOUT_DIAG>(const SweepArgs&, cudaStream_t);      \
     template cudaError_t run_potential<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, cudaStream_t);      \
     template cudaError_t run_potential<L, MRF_LAYOUT_DIAG>(const SweepArgs&, cudaStream_t);       \
     template cudaError_t run_dual<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, cudaStream_t);           \

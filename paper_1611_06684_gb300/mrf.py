@@ -36,7 +36,8 @@ class mrf_info(ct.Structure):
     _fields_ = [("n_vars", ct.c_int32), ("n_labels", ct.c_int32), ("n_chains", ct.c_int32),
                 ("layout", ct.c_int32), ("n_entries", ct.c_int32), ("n_edges", ct.c_int64),
                 ("n_edge_slots", ct.c_int64), ("sweep_index", ct.c_int64), ("n_samples", ct.c_int64),
-                ("log_const", ct.c_double)]
+                ("log_const", ct.c_double), ("schedule", ct.c_int32), ("tune_ms_thread", ct.c_float),
+                ("tune_ms_cta", ct.c_float)]
 
 
 _P = ct.c_void_p
@@ -59,6 +60,19 @@ _SIGS = {
     "mrf_debug_theta": (ct.c_int, [_P, _P]),
     "mrf_kernel_times": (ct.c_int, [_P, _P, _P]),
     "mrf_sweep_noalloc": (ct.c_int, [_P, _P, _P, ct.c_int64]),
+    "mrf_batch_create": (ct.c_int, [ct.POINTER(_P), ct.c_int32, _P, _P, ct.c_int32, ct.c_uint64,
+                                    ct.POINTER(mrf_options), _P]),
+    "mrf_batch_set_factors": (ct.c_int, [_P, _P, _P, _P, _P, _P]),
+    "mrf_batch_edit_factors": (ct.c_int, [_P, ct.c_int64, _P, _P, ct.c_int64, _P, _P, _P, _P, _P]),
+    "mrf_batch_sweep": (ct.c_int, [_P, ct.c_int32, ct.c_int32]),
+    "mrf_batch_reset_marginals": (ct.c_int, [_P, ct.c_int32]),
+    "mrf_batch_get_counts": (ct.c_int, [_P, ct.c_int32, _P]),
+    "mrf_batch_get_labels": (ct.c_int, [_P, ct.c_int32, _P]),
+    "mrf_batch_graph": (ct.c_int, [_P, ct.c_int32, _P]),
+    "mrf_batch_n_classes": (ct.c_int32, [_P]),
+    "mrf_batch_class": (_P, [_P, ct.c_int32]),
+    "mrf_batch_last_error": (ct.c_char_p, [_P]),
+    "mrf_batch_destroy": (None, [_P]),
     "mrf_last_error": (ct.c_char_p, [_P]),
     "mrf_status_string": (ct.c_char_p, [ct.c_int]),
     "mrf_destroy": (None, [_P]),
@@ -145,9 +159,9 @@ class MRF:
             raise MrfError(st, self.lib.mrf_last_error(self.h).decode())
 
     def close(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and not getattr(self, "_borrowed", False):
             self.lib.mrf_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
@@ -251,6 +265,108 @@ class MRF:
         out = np.zeros((inf.n_edge_slots, self.C, W), np.uint32)
         self._check(self.lib.mrf_debug_theta(self.h, out.ctypes.data))
         return out
+
+
+class mrf_batch_graph_info(ct.Structure):
+    _fields_ = [("n_vars", ct.c_int32), ("n_labels", ct.c_int32), ("class_index", ct.c_int32),
+                ("site_offset", ct.c_int32), ("first_edge_slot", ct.c_int64)]
+
+
+BATCH_KEY_STEP = 0x9E3779B97F4A7C15
+
+
+class MRFBatch:
+    """Owner of one mrf_batch_t: many uneven graphs swept together (see mrf.h)."""
+
+    def __init__(self, n_vars, n_labels, n_chains: int, seed: int = 0, use_graphs: bool = True, stream=None,
+                 kernel_timing: bool = False, schedule: int = 0):
+        lib = load()
+        opt = mrf_options()
+        lib.mrf_default_options(ct.byref(opt))
+        opt.use_graphs = int(use_graphs)
+        opt.kernel_timing = int(kernel_timing)
+        opt.schedule = int(schedule)
+        self.stream = _current_stream() if stream is None else int(stream)
+        nv = np.ascontiguousarray(n_vars, np.int32); nl = np.ascontiguousarray(n_labels, np.int32)
+        b = _P()
+        st = lib.mrf_batch_create(ct.byref(b), nv.shape[0], nv.ctypes.data, nl.ctypes.data, n_chains,
+                                  ct.c_uint64(seed & (2**64 - 1)), ct.byref(opt), _P(self.stream))
+        if st != MRF_OK:
+            raise MrfError(st, lib.mrf_status_string(st).decode())
+        self.b, self.lib = b, lib
+        self.n_vars, self.n_labels, self.C, self.G = nv, nl, n_chains, nv.shape[0]
+
+    def _check(self, st):
+        if st != MRF_OK:
+            raise MrfError(st, self.lib.mrf_batch_last_error(self.b).decode())
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.mrf_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_factors(self, models):
+        """models: list of workloads.Model in graph order."""
+        u = np.ascontiguousarray(np.concatenate([m.unary.ravel() for m in models]), np.float32)
+        ne = np.array([m.n_edges for m in models], np.int64)
+        s = np.ascontiguousarray(np.concatenate([m.src for m in models]), np.int32)
+        t = np.ascontiguousarray(np.concatenate([m.dst for m in models]), np.int32)
+        p = np.ascontiguousarray(np.concatenate([m.pair.ravel() for m in models]), np.float32)
+        self._check(self.lib.mrf_batch_set_factors(self.b, u.ctypes.data, ne.ctypes.data, s.ctypes.data,
+                                                   t.ctypes.data, p.ctypes.data))
+
+    def edit_factors(self, rm_graph, rm_slot, add_graph, src, dst, pair_flat):
+        rg = np.ascontiguousarray(rm_graph, np.int32); rs = np.ascontiguousarray(rm_slot, np.int64)
+        ag = np.ascontiguousarray(add_graph, np.int32)
+        s = np.ascontiguousarray(src, np.int32); t = np.ascontiguousarray(dst, np.int32)
+        p = np.ascontiguousarray(pair_flat, np.float32)
+        out = np.zeros(ag.shape[0], np.int64)
+        self._check(self.lib.mrf_batch_edit_factors(self.b, rg.shape[0], rg.ctypes.data, rs.ctypes.data, ag.shape[0],
+                                                    ag.ctypes.data, s.ctypes.data, t.ctypes.data, p.ctypes.data,
+                                                    out.ctypes.data))
+        return out
+
+    def sweep(self, n: int = 1, mode: int = MODE_PLAIN):
+        self._check(self.lib.mrf_batch_sweep(self.b, int(n), int(mode)))
+
+    def reset_marginals(self, burn_in: int = 0):
+        self._check(self.lib.mrf_batch_reset_marginals(self.b, int(burn_in)))
+
+    def counts(self, g: int):
+        out = np.zeros((int(self.n_vars[g]), int(self.n_labels[g])), np.uint32)
+        self._check(self.lib.mrf_batch_get_counts(self.b, g, out.ctypes.data))
+        return out
+
+    def get_labels(self, g: int):
+        out = np.zeros((self.C, int(self.n_vars[g])), np.uint8)
+        self._check(self.lib.mrf_batch_get_labels(self.b, g, out.ctypes.data))
+        return out
+
+    def graph(self, g: int):
+        inf = mrf_batch_graph_info()
+        self._check(self.lib.mrf_batch_graph(self.b, g, ct.byref(inf)))
+        return inf
+
+    def n_classes(self) -> int:
+        return int(self.lib.mrf_batch_n_classes(self.b))
+
+    def class_handle(self, k: int) -> "MRF":
+        """A non-owning MRF view of class k (info, kernel times, debug views)."""
+        view = MRF.__new__(MRF)
+        view.lib = self.lib
+        view.h = _P(self.lib.mrf_batch_class(self.b, k))
+        view._borrowed = True
+        view._batch = self                    # keeps the batch alive while the view is used
+        inf = mrf_info()
+        self.lib.mrf_get_info(view.h, ct.byref(inf))
+        view.N, view.L, view.C = inf.n_vars, inf.n_labels, inf.n_chains
+        return view
 
 
 def unpack_theta(words: np.ndarray, m: int) -> np.ndarray:

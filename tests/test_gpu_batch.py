@@ -1,0 +1,119 @@
+"""GPU parity of batched uneven graphs with edits (the paper's dynamic-network
+case, abstract and Section 6): a batch of graphs with mixed label counts is
+swept per class of equal L as the disjoint union of its graphs; every graph's
+labels and counts must equal the oracle run on that union with the class key,
+before and after factor insertions and deletions."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from oracle import decompose as dc, sampler, philox as ph
+from paper_1611_06684_gb300 import workloads as wl
+from paper_1611_06684_gb300 import mrf as M
+from tests.gpu_helpers import compare_sweep
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1611_06684_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _union(models, ids):
+    """Disjoint union of models[ids] (sites and edges appended in order)."""
+    off = 0
+    us, ss, ts, ps = [], [], [], []
+    for g in ids:
+        m = models[g]
+        us.append(m.unary); ss.append(m.src + off); ts.append(m.dst + off); ps.append(m.pair)
+        off += m.n_vars
+    return wl.Model(off, models[ids[0]].n_labels, np.concatenate(us), np.concatenate(ss).astype(np.int32),
+                    np.concatenate(ts).astype(np.int32), np.concatenate(ps))
+
+
+def _batch_models(n=9, seed=3):
+    specs = wl.er_batch_specs(n, n_min=40, n_max=300, labels=(2, 3, 4, 8), seed=seed)
+    return [wl.er_graph(s) for s in specs]
+
+
+def test_batch_sweeps_match_oracle_union_with_edits():
+    torch = pytest.importorskip("torch")
+    models = _batch_models()
+    C, seed = 3, 77
+    stream = torch.cuda.Stream()
+    b = M.MRFBatch([m.n_vars for m in models], [m.n_labels for m in models], C, seed=seed,
+                   stream=stream.cuda_stream, use_graphs=True)
+    b.set_factors(models)
+    classes = sorted(set(m.n_labels for m in models))
+    assert b.n_classes() == len(classes)
+    members = {L: [g for g, m in enumerate(models) if m.n_labels == L] for L in classes}
+    rng = np.random.default_rng(4)
+    # oracle state per class
+    unions = {L: _union(models, members[L]) for L in classes}
+    slots_u = {L: np.arange(unions[L].n_edges) for L in classes}
+    xs = {L: ph.init_labels(unions[L].n_vars, L, C, seed + L * M.BATCH_KEY_STEP) for L in classes}
+    t = 0
+    for rnd in range(3):
+        b.sweep(4, M.MODE_PLAIN)
+        torch.cuda.synchronize()
+        for L in classes:
+            dec = dc.decompose(unions[L])
+            key = (seed + L * M.BATCH_KEY_STEP) & (2**64 - 1)
+            x = xs[L]
+            for s_ in range(4):
+                ref = sampler.sweep(dec, x, t + s_, key, edge_ids=slots_u[L])
+                x = ref["x"]
+            xs[L] = x
+            off = 0
+            for g in members[L]:
+                got = b.get_labels(g)
+                want = x[:, off:off + models[g].n_vars]
+                assert (got != want).mean() < 0.01, (L, g)     # boundary draws only, in practice none
+                off += models[g].n_vars
+        t += 4
+        # edit: remove 5% of each graph's edges, add as many
+        rm_g, rm_s, add_g, add_s, add_t, add_p = [], [], [], [], [], []
+        for g, m in enumerate(models):
+            info = b.graph(g)
+            if not hasattr(m, "slots"):
+                m.slots = np.arange(m.n_edges) + info.first_edge_slot
+            rem, s_new, t_new, p_new = wl.er_edit(m, 0.05, rng)
+            rm_g += [g] * len(rem); rm_s += list(m.slots[rem])
+            add_g += [g] * len(s_new); add_s += list(s_new); add_t += list(t_new); add_p.append(p_new.ravel())
+            m._pending = (rem, s_new, t_new, p_new)
+        new_slots = b.edit_factors(rm_g, rm_s, add_g, add_s, add_t, np.concatenate(add_p))
+        # apply the same edit to the oracle unions: removed slots replaced in slot order
+        pos = 0
+        for g, m in enumerate(models):
+            rem, s_new, t_new, p_new = m._pending
+            k = len(s_new)
+            ids = new_slots[pos:pos + k]; pos += k
+            keep = np.ones(m.n_edges, bool); keep[rem] = False
+            m.src = np.concatenate([m.src[keep], s_new]).astype(np.int32)
+            m.dst = np.concatenate([m.dst[keep], t_new]).astype(np.int32)
+            m.pair = np.concatenate([m.pair[keep], p_new])
+            m.slots = np.concatenate([m.slots[keep], ids])
+        for L in classes:
+            # the union's edges in slot order, with their slots as RNG indices
+            us = _union(models, members[L])
+            slots = np.concatenate([models[g].slots for g in members[L]])
+            order = np.argsort(slots)
+            unions[L] = wl.Model(us.n_vars, L, us.unary, us.src[order], us.dst[order], us.pair[order])
+            slots_u[L] = slots[order]
+
+
+def test_batch_counts_per_graph():
+    models = _batch_models(5, seed=8)
+    b = M.MRFBatch([m.n_vars for m in models], [m.n_labels for m in models], 2, seed=1, use_graphs=False)
+    b.set_factors(models)
+    b.reset_marginals(1)
+    b.sweep(5, M.MODE_FUSED)
+    for g, m in enumerate(models):
+        c = b.counts(g)
+        assert c.shape == (m.n_vars, m.n_labels)
+        assert np.all(c.sum(1) == 4 * 2)
