@@ -456,19 +456,24 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
     }
     h->h_src.resize(new_slots, -1); h->h_dst.resize(new_slots, -1);
     for (int64_t i = 0; i < n_add; ++i) { h->h_src[slots[i]] = as[i]; h->h_dst[slots[i]] = at[i]; }
-    // device: removed slots get src = dst = -1, new slots their endpoints
+    // device: every touched slot gets its final endpoints from the host mirror
+    // (a removed slot is usually reused by an added edge of the same edit)
     std::vector<int64_t> upd_slot(rem.begin(), rem.end());
     upd_slot.insert(upd_slot.end(), slots.begin(), slots.end());
-    std::vector<int32_t> upd_s((size_t)n_remove, -1), upd_t((size_t)n_remove, -1);
-    upd_s.insert(upd_s.end(), as.begin(), as.end());
-    upd_t.insert(upd_t.end(), at.begin(), at.end());
+    std::sort(upd_slot.begin(), upd_slot.end());
+    upd_slot.erase(std::unique(upd_slot.begin(), upd_slot.end()), upd_slot.end());
+    std::vector<int32_t> upd_s(upd_slot.size()), upd_t(upd_slot.size());
+    for (size_t i = 0; i < upd_slot.size(); ++i) { upd_s[i] = h->h_src[upd_slot[i]]; upd_t[i] = h->h_dst[upd_slot[i]]; }
     const int64_t n_upd = (int64_t)upd_slot.size();
     int64_t* d_slots = nullptr;
+    int64_t* d_new = nullptr;
     int32_t* d_us = nullptr;
     int32_t* d_ut2 = nullptr;
     MRF_CUDA(h, dalloc(d_slots, (size_t)n_upd)); MRF_CUDA(h, dalloc(d_us, (size_t)n_upd)); MRF_CUDA(h, dalloc(d_ut2, (size_t)n_upd));
-    struct Guard2 { int64_t*& p; int32_t*& q; int32_t*& r; ~Guard2() { dfree(p); dfree(q); dfree(r); } } guard2{d_slots, d_us, d_ut2};
+    MRF_CUDA(h, dalloc(d_new, (size_t)n_add));
+    struct Guard2 { int64_t*& p; int32_t*& q; int32_t*& r; int64_t*& n; ~Guard2() { dfree(p); dfree(q); dfree(r); dfree(n); } } guard2{d_slots, d_us, d_ut2, d_new};
     MRF_CUDA(h, to_device(d_slots, upd_slot.data(), n_upd, MRF_PTR_HOST, h->stream));
+    MRF_CUDA(h, to_device(d_new, slots.data(), n_add, MRF_PTR_HOST, h->stream));
     MRF_CUDA(h, to_device(d_us, upd_s.data(), n_upd, MRF_PTR_HOST, h->stream));
     MRF_CUDA(h, to_device(d_ut2, upd_t.data(), n_upd, MRF_PTR_HOST, h->stream));
     if (new_slots > h->E_slots) {     // fresh slots start free on the device too
@@ -480,10 +485,10 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
     h->E_slots = new_slots;
     h->E_live += n_add - n_remove;
     DecompArgs d{};
-    d.L = L; d.M = h->M; d.layout = h->layout; d.n = n_add; d.slots = d_slots + n_remove;
+    d.L = L; d.M = h->M; d.layout = h->layout; d.n = n_add; d.slots = d_new;
     d.pair = d_pair; d.tau = h->d_tau; d.thr = h->d_thr; d.fold = h->d_fold; d.cst = h->d_cst; d.resid = nullptr;
     MRF_CUDA(h, launch_decompose(d, h->stream));
-    MRF_CUDA(h, launch_build_planes(h->d_thr, n_add, d_slots + n_remove, 0, h->M, h->d_tpl, h->stream));
+    MRF_CUDA(h, launch_build_planes(h->d_thr, n_add, d_new, 0, h->M, h->d_tpl, h->stream));
     // incidence lists rebuilt on the device (host build if a site is very long)
     if (2 * h->E_live > h->inc_cap) {
         MRF_CUDA(h, dalloc(h->d_inc, (size_t)(2 * h->E_live + h->E_live / 4 + 64)));

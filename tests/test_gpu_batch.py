@@ -58,24 +58,24 @@ def test_batch_sweeps_match_oracle_union_with_edits():
     slots_u = {L: np.arange(unions[L].n_edges) for L in classes}
     xs = {L: ph.init_labels(unions[L].n_vars, L, C, seed + L * M.BATCH_KEY_STEP) for L in classes}
     t = 0
+    def gpu_union_labels(L):
+        return np.concatenate([b.get_labels(g) for g in members[L]], axis=1).astype(np.int64)
     for rnd in range(3):
-        b.sweep(4, M.MODE_PLAIN)
-        torch.cuda.synchronize()
-        for L in classes:
-            dec = dc.decompose(unions[L])
-            key = (seed + L * M.BATCH_KEY_STEP) & (2**64 - 1)
-            x = xs[L]
-            for s_ in range(4):
-                ref = sampler.sweep(dec, x, t + s_, key, edge_ids=slots_u[L])
-                x = ref["x"]
-            xs[L] = x
-            off = 0
-            for g in members[L]:
-                got = b.get_labels(g)
-                want = x[:, off:off + models[g].n_vars]
-                assert (got != want).mean() < 0.01, (L, g)     # boundary draws only, in practice none
-                off += models[g].n_vars
-        t += 4
+        for s_ in range(3):                      # one sweep at a time from the common state
+            before = {L: gpu_union_labels(L) for L in classes}
+            b.sweep(1, M.MODE_PLAIN)
+            torch.cuda.synchronize()
+            for L in classes:
+                dec = dc.decompose(unions[L])
+                key = (seed + L * M.BATCH_KEY_STEP) & (2**64 - 1)
+                if t == 0:
+                    assert np.array_equal(before[L], ph.init_labels(unions[L].n_vars, L, C, key))
+                ref = sampler.sweep(dec, before[L], t, key, edge_ids=slots_u[L])
+                try:
+                    compare_sweep(dec, ref, gpu_union_labels(L))
+                except AssertionError as exc:
+                    raise AssertionError(f"class L={L} sweep t={t} round {rnd}: {exc}")
+            t += 1
         # edit: remove 5% of each graph's edges, add as many
         rm_g, rm_s, add_g, add_s, add_t, add_p = [], [], [], [], [], []
         for g, m in enumerate(models):
