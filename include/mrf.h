@@ -59,8 +59,11 @@ enum {
                             primal kernel gathers it over the CSR incidence  */
     MRF_MODE_FUSED = 1,  /* same chain, theta regenerated at both endpoints
                             from the counter-based RNG (never stored)        */
-    MRF_MODE_SPLASH = 2  /* Section 5.4 blocked sweep on a lattice (needs
+    MRF_MODE_SPLASH = 2, /* Section 5.4 blocked sweep on a lattice (needs
                             mrf_options.grid); 4x4x4 blocks, comb trees      */
+    MRF_MODE_LEARNED = 3 /* cut-edge duals, then one Metropolis-Hastings step
+                            per block with the learned proposal (needs
+                            mrf_learned_setup)                               */
 };
 
 /* Dualised table layout chosen by mrf_set_factors (mrf_info.layout). */
@@ -76,7 +79,9 @@ typedef struct {
                                           2 CTA/site (high degree)               */
     int32_t kernel_timing;             /* 1: bracket every sweep kernel with CUDA
                                           events (graphs off); see mrf_kernel_times */
-    int32_t reserved[7];
+    int32_t exact_edges;               /* 1: keep every edge's exact folded table
+                                          (needed by mrf_learned_setup)          */
+    int32_t reserved[6];
 } mrf_options;
 
 typedef struct {
@@ -158,7 +163,7 @@ mrf_status mrf_debug_theta(mrf_t* h, uint32_t* out);
 
 /* Kernel ids of mrf_kernel_times. */
 enum { MRF_K_DUAL = 0, MRF_K_PRIMAL = 1, MRF_K_FUSED = 2, MRF_K_POTENTIAL = 3, MRF_K_FFBS = 4,
-       MRF_K_ACCUMULATE = 5, MRF_K_COUNT = 6 };
+       MRF_K_ACCUMULATE = 5, MRF_K_FEATURES = 6, MRF_K_MLP = 7, MRF_K_MH = 8, MRF_K_COUNT = 9 };
 /* With options.kernel_timing: total device milliseconds ms[MRF_K_COUNT] and
  * launch counts launches[MRF_K_COUNT] of every sweep kernel since the last
  * call (CUDA events on the handle's stream); resets the totals.  Synchronises. */
@@ -215,6 +220,51 @@ int32_t mrf_batch_n_classes(const mrf_batch_t* b);
 mrf_t* mrf_batch_class(mrf_batch_t* b, int32_t k);
 const char* mrf_batch_last_error(const mrf_batch_t* b);
 void mrf_batch_destroy(mrf_batch_t* b);
+
+/* ---- Learned block proposal (no counterpart in the paper) ---------------------
+ * Blocks of at most 16 sites (Section 5.4 allows blocking with respect to
+ * arbitrary subgraphs).  A learned sweep draws the duals of the cut edges
+ * (between blocks), then gives every (block, chain) one independence
+ * Metropolis-Hastings step: an MLP (features -> hidden -> hidden -> 16 x L
+ * logits, bf16 weights, fp32 accumulation) proposes all the block's labels at
+ * once; the step accepts with min(1, pi(x') q(x) / (pi(x) q(x'))) under the
+ * exact block conditional pi (intra-block factors kept exact), so the chain
+ * keeps the target whatever the weights.  Features per (block, chain):
+ * centred node potentials of the members (sorted site ids) and the block's
+ * pair couplings kappa_e = mean_a w(a,a) - mean_{a!=b} w(a,b); width
+ * 16 L + 120 padded to a multiple of 32.  Parameters (float32, flat):
+ * W1 [H][Dp], b1 [H], W2 [H][H], b2 [H], W3 [16L][H], b3 [16L]. */
+
+/* Partition into blocks (block_of_site[v] in [0, n_blocks), host memory, at
+ * most 16 sites each), hidden width H (multiple of 64), He-uniform weights from
+ * init_seed.  Needs mrf_options.exact_edges.  Errors: MRF_ERANGE for a block
+ * over 16 sites, MRF_ESTATE without factors or exact edges. */
+mrf_status mrf_learned_setup(mrf_t* h, const int32_t* block_of_site, int32_t hidden, uint64_t init_seed);
+int64_t mrf_learned_param_count(const mrf_t* h);
+/* Parameters to / from host float32 (weights are used rounded to bf16). */
+mrf_status mrf_learned_set_params(mrf_t* h, const float* params, int64_t n);
+mrf_status mrf_learned_get_params(mrf_t* h, float* params, int64_t n);
+/* Run n_sweeps plain sweeps; after each, compute the cut duals and features
+ * of the new state and keep every stride-th (block, chain) row (features and
+ * the block's labels) in the on-device training set (at most max_rows rows).
+ * Returns the number of rows held in *rows. */
+mrf_status mrf_learned_harvest(mrf_t* h, int32_t n_sweeps, int32_t stride, int64_t max_rows, int64_t* rows);
+/* steps Adam steps (lr, betas 0.9/0.999, eps 1e-8) on minibatches of `batch`
+ * rows drawn with replacement by a generator seeded with shuffle_seed; the
+ * cross-entropy of every step goes to loss_trace[steps] (host, may be null). */
+mrf_status mrf_learned_train(mrf_t* h, int32_t steps, int32_t batch, float lr, uint64_t shuffle_seed,
+                             float* loss_trace);
+/* Gradient of the mean cross-entropy on given rows (host): X [rows][Dp]
+ * float32 (used as bf16), y [rows][16], nmem [rows]; grads [param_count]. */
+mrf_status mrf_learned_grad(mrf_t* h, const float* X, const uint8_t* y, const uint8_t* nmem, int32_t rows,
+                            float* grads, double* loss);
+/* Logits z [rows][16 L] of the tensor-core forward pass on given features. */
+mrf_status mrf_learned_forward(mrf_t* h, const float* X, int32_t rows, float* z);
+/* Proposals made and accepted by learned sweeps so far. */
+mrf_status mrf_learned_stats(mrf_t* h, uint64_t* proposed, uint64_t* accepted);
+/* Features [n_blocks * C][Dp] and logits [n_blocks * C][16 L] of the last learned
+ * sweep (host float32; rows b * C + c). */
+mrf_status mrf_learned_debug(mrf_t* h, float* X, float* z);
 
 /* Capacity, in 32-bit words, of the fixed device array that holds the dual
  * bits of mrf_sweep_noalloc (16 MiB). */

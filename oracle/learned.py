@@ -112,6 +112,17 @@ def mlp_forward(params, X):
     return z, (X, a1, h1, a2, h2)
 
 
+def mlp_forward_bf16(params, X):
+    """Forward pass with the inputs and hidden activations rounded to bfloat16
+    between layers (the precision in which the device stores them); the
+    arithmetic itself stays float64."""
+    W1, b1, W2, b2, W3, b3 = params
+    Xb = to_bf16(X)
+    h1 = to_bf16(np.maximum(Xb @ W1.T + b1, 0.0))
+    h2 = to_bf16(np.maximum(h1 @ W2.T + b2, 0.0))
+    return h2 @ W3.T + b3
+
+
 def ce_loss(z, y, nmem, L, B=BLOCK):
     """Mean over rows of -sum_{i < n_b} log softmax(z_i)(y_i)."""
     R = z.shape[0]
@@ -180,8 +191,11 @@ def intra_edge_lists(model, block_of_site, n_blocks):
     return lists
 
 
-def learned_sweep(model, dec: Decomposition, x, sweep_index, seed, block_of_site, params, edge_ids=None):
-    """One learned sweep from labels x [C][N]; returns a dict with the new labels."""
+def learned_sweep(model, dec: Decomposition, x, sweep_index, seed, block_of_site, params, edge_ids=None,
+                  bf16_activations=False):
+    """One learned sweep from labels x [C][N]; returns a dict with the new labels.
+    bf16_activations: evaluate the proposal with inputs and hidden activations
+    rounded to bfloat16 (the device's storage precision)."""
     C, N = x.shape
     L = model.n_labels
     members = block_members(block_of_site)
@@ -195,7 +209,7 @@ def learned_sweep(model, dec: Decomposition, x, sweep_index, seed, block_of_site
     phi = node_potentials(model, dec, intra, theta)               # target field
     cf = coupling_features(model, block_of_site, members)
     X = features(phi_f, members, cf, L)
-    z, _ = mlp_forward(params, X)
+    z = mlp_forward_bf16(params, X) if bf16_activations else mlp_forward(params, X)[0]
     lz = log_softmax(z.reshape(nb * C, BLOCK, L))                 # rows b*C + c
     w = np.asarray(model.pair, np.float64)
     lists = intra_edge_lists(model, block_of_site, nb)

@@ -5,6 +5,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "../../include/mrf.h"
 #include "philox.cuh"
 
@@ -98,6 +100,32 @@ struct SweepArgs {
     int64_t nxe, nye;          // numbers of x- and y-edges (canonical lattice order)
     FastDiv fdX1, fdX, fdY1, fdY;   // division by nx-1, nx, ny-1, ny
     float* pot;                // [N][L][C] node potentials / beliefs of the blocked sweep
+    const uint8_t* skip;       // [E] 1 = edge kept exact (no dual bit) in a learned sweep; null otherwise
+};
+
+// Learned block proposal (learned.cu).
+constexpr int kLearnBlock = 16;                                   // sites per block (max)
+constexpr int kLearnPairs = kLearnBlock * (kLearnBlock - 1) / 2;  // pair-coupling features
+
+struct LearnedArgs {
+    int32_t nb, L, Dp, H, O;            // blocks, labels, padded feature width, hidden, 16*L
+    const int32_t* members;             // [nb][16] site ids (sorted, -1 padding)
+    const int32_t* nmem;                // [nb]
+    const int64_t* intra_ptr;           // [nb+1]
+    const int4* intra;                  // {edge slot, member index of src, of dst, 0}
+    const float* cf;                    // [nb][120] pair couplings
+    __nv_bfloat16* X;                   // [R][Dp] features, R = nb * C
+    __nv_bfloat16* H1;                  // [R][H]
+    __nv_bfloat16* H2;                  // [R][H]
+    float* Zm;                          // [R][O] logits
+    const float* Z;                     // = Zm
+    float* w32;                         // flat float32 parameters W1,b1,W2,b2,W3,b3
+    const float* b1; const float* b2; const float* b3;
+    __nv_bfloat16* W1b; __nv_bfloat16* W2b; __nv_bfloat16* W3b;
+    float* grad; float* adam_m; float* adam_v;
+    float* t_h1; float* t_h2; float* t_z; float* t_dz; float* t_d2; float* t_d1;   // training scratch
+    __nv_bfloat16* ds_X; uint8_t* ds_y; uint8_t* ds_n;                               // dataset
+    unsigned long long* n_accepted;
 };
 
 // Kernel launchers (sweep.cu, splash.cu, decompose.cu).  All return cudaGetLastError().
@@ -115,6 +143,19 @@ cudaError_t build_csr_device(const int32_t* src, const int32_t* dst, int64_t E, 
                              int32_t* work, int64_t* sums, unsigned long long* too_long, int max_deg, cudaStream_t s);
 cudaError_t launch_scatter_edges(const int64_t* slots, const int32_t* s, const int32_t* t, int64_t n, int32_t* src,
                                  int32_t* dst, cudaStream_t st);
+cudaError_t launch_learned_features(const LearnedArgs& a, const SweepArgs& s, cudaStream_t st);
+cudaError_t launch_learned_couplings(const LearnedArgs& a, const float* resid, float* cf, cudaStream_t st);
+cudaError_t launch_learned_mlp(const LearnedArgs& a, int64_t rows, const __nv_bfloat16* X, cudaStream_t st);
+cudaError_t launch_learned_mh(const LearnedArgs& a, const SweepArgs& s, cudaStream_t st);
+cudaError_t launch_learned_harvest(const LearnedArgs& a, const SweepArgs& s, int stride, int phase, int64_t base,
+                                   int64_t cap, cudaStream_t st);
+cudaError_t learned_forward_backward(const LearnedArgs& a, int R, const __nv_bfloat16* X, const uint8_t* y,
+                                     const uint8_t* nm, double* loss, cudaStream_t s);
+cudaError_t learned_adam(const LearnedArgs& a, int64_t n_params, float lr, int step, cudaStream_t s);
+cudaError_t learned_sync_bf16(const LearnedArgs& a, cudaStream_t s);
+cudaError_t learned_gather(const LearnedArgs& a, const int32_t* idx, int R, __nv_bfloat16* X, uint8_t* y, uint8_t* nm,
+                           cudaStream_t s);
+cudaError_t launch_to_bf16(const float* src, __nv_bfloat16* dst, int64_t n, cudaStream_t s);
 cudaError_t noalloc_scratch(uint32_t** out);
 cudaError_t launch_sweep_noalloc(const SweepArgs& a, int layout, const uint8_t* xin, uint8_t* xout, uint32_t sweep,
                                  cudaStream_t s);

@@ -45,7 +45,7 @@ struct mrf {
     int64_t sweep_host = 0, count_from_host = 0;
     double log_const = NAN;
     std::string err;
-    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
     uint8_t* d_stage = nullptr;        // [C][N] staging for the ABI label view
     float* d_pot = nullptr;            // [N][L][C] node potentials of the blocked sweep
     int schedule = 0;                  // primal schedule in use (1 thread, 2 CTA); 0 = not tuned yet
@@ -53,6 +53,22 @@ struct mrf {
     int64_t* d_csr_sums = nullptr;     // block sums of the device scan
     int64_t inc_cap = 0;               // capacity of d_inc (incidences)
     int64_t n_device_csr = 0, n_host_csr = 0;   // CSR builds after edits, by path
+    // learned block proposal
+    bool learned = false;
+    LearnedArgs la{};
+    int64_t n_params = 0;
+    int32_t* d_members = nullptr; int32_t* d_nmem = nullptr; int64_t* d_intra_ptr = nullptr; int4* d_intra = nullptr;
+    float* d_cf = nullptr; uint8_t* d_skip = nullptr;
+    __nv_bfloat16* d_X = nullptr; __nv_bfloat16* d_H1 = nullptr; __nv_bfloat16* d_H2 = nullptr; float* d_Z = nullptr;
+    float* d_w32 = nullptr; __nv_bfloat16* d_Wb = nullptr; float* d_grad = nullptr; float* d_m = nullptr; float* d_v = nullptr;
+    float* d_train = nullptr; int64_t train_rows = 0;
+    int32_t* d_bidx = nullptr; __nv_bfloat16* d_bX = nullptr; uint8_t* d_by = nullptr; uint8_t* d_bn = nullptr;
+    __nv_bfloat16* d_dsX = nullptr; uint8_t* d_dsy = nullptr; uint8_t* d_dsn = nullptr;
+    int64_t ds_cap = 0, ds_rows = 0;
+    double* d_loss = nullptr; int64_t loss_cap = 0;
+    unsigned long long* d_acc = nullptr;
+    uint64_t proposed = 0;
+    int adam_step = 0;
     float tune_ms[2] = {0.0f, 0.0f};   // autotuner timings (thread, CTA) per primal launch
     // kernel timing (options.kernel_timing)
     struct Rec { int id; cudaEvent_t a, b; };
@@ -303,6 +319,10 @@ void mrf_destroy(mrf_t* h) {
     dfree(h->d_fold); dfree(h->d_cst); dfree(h->d_resid); dfree(h->d_inc_ptr); dfree(h->d_inc); dfree(h->d_x);
     dfree(h->d_theta); dfree(h->d_counts); dfree(h->d_logp); dfree(h->d_ctl); dfree(h->d_flag); dfree(h->d_stage); dfree(h->d_pot);
     dfree(h->d_csr_work); dfree(h->d_csr_sums);
+    dfree(h->d_members); dfree(h->d_nmem); dfree(h->d_intra_ptr); dfree(h->d_intra); dfree(h->d_cf); dfree(h->d_skip);
+    dfree(h->d_X); dfree(h->d_H1); dfree(h->d_H2); dfree(h->d_Z); dfree(h->d_w32); dfree(h->d_Wb); dfree(h->d_grad);
+    dfree(h->d_m); dfree(h->d_v); dfree(h->d_train); dfree(h->d_bidx); dfree(h->d_bX); dfree(h->d_by); dfree(h->d_bn);
+    dfree(h->d_dsX); dfree(h->d_dsy); dfree(h->d_dsn); dfree(h->d_loss); dfree(h->d_acc);
     for (auto& r : h->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : h->pool) cudaEventDestroy(e);
     delete h;
@@ -346,8 +366,8 @@ mrf_status mrf_set_factors(mrf_t* h, const float* unary_log, int64_t n_edges, co
     h->W = (h->M + 31) / 32;
     h->E_live = h->E_slots = h->E_cap = n_edges;
     h->free_slots.clear();
-    const bool want_resid = h->opt.grid_nx > 0;
-    if (want_resid && !lattice_ok(h)) {
+    const bool want_resid = h->opt.grid_nx > 0 || h->opt.exact_edges;
+    if (h->opt.grid_nx > 0 && !lattice_ok(h)) {
         h->has_factors = false;
         return fail(h, MRF_EINVAL, "options.grid set but the edges are not the lattice's in canonical order");
     }
@@ -386,6 +406,8 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
     if (n_remove < 0 || n_add < 0 || (n_remove && !edge_ids) || (n_add && (!src || !dst || !pair_log || !out_new_ids)))
         return fail(h, MRF_EINVAL, "bad edit arguments");
     if (h->opt.grid_nx > 0) return fail(h, MRF_ESTATE, "edits are not available on a lattice handle");
+    if (h->learned) return fail(h, MRF_ESTATE, "edits are not available once the learned proposal is set up");
+    if (h->d_resid) return fail(h, MRF_ESTATE, "edits are not available with exact edge tables");
     const int L = h->L, N = h->N;
     std::vector<int64_t> rem;
     std::vector<int32_t> as, at;
@@ -550,6 +572,13 @@ static mrf_status enqueue_sweep(mrf_t* h, int mode) {
         if (e == cudaSuccess) e = timed(h, MRF_K_PRIMAL, [&] { return launch_primal(a, h->layout, h->schedule, s); });
     } else if (mode == MRF_MODE_FUSED) {
         e = timed(h, MRF_K_FUSED, [&] { return launch_fused(a, h->layout, h->opt.schedule, s); });
+    } else if (mode == MRF_MODE_LEARNED) {
+        a.skip = h->d_skip;
+        e = timed(h, MRF_K_DUAL, [&] { return launch_dual(a, h->layout, s); });
+        if (e == cudaSuccess) e = timed(h, MRF_K_POTENTIAL, [&] { return launch_potential(a, h->layout, s); });
+        if (e == cudaSuccess) e = timed(h, MRF_K_FEATURES, [&] { return launch_learned_features(h->la, a, s); });
+        if (e == cudaSuccess) e = timed(h, MRF_K_MLP, [&] { return launch_learned_mlp(h->la, (int64_t)h->la.nb * h->C, h->la.X, s); });
+        if (e == cudaSuccess) e = timed(h, MRF_K_MH, [&] { return launch_learned_mh(h->la, a, s); });
     } else {
         a.splash = 1;
         e = launch_splash_offset(a, s);
@@ -566,7 +595,8 @@ static mrf_status enqueue_sweep(mrf_t* h, int mode) {
 mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode) {
     if (!h) return MRF_EINVAL;
     if (!h->has_factors) return fail(h, MRF_ESTATE, "mrf_set_factors first");
-    if (n_sweeps < 0 || mode < MRF_MODE_PLAIN || mode > MRF_MODE_SPLASH) return fail(h, MRF_EINVAL, "bad sweep count or mode");
+    if (n_sweeps < 0 || mode < MRF_MODE_PLAIN || mode > MRF_MODE_LEARNED) return fail(h, MRF_EINVAL, "bad sweep count or mode");
+    if (mode == MRF_MODE_LEARNED && !h->learned) return fail(h, MRF_ESTATE, "learned mode needs mrf_learned_setup");
     if (mode == MRF_MODE_SPLASH && h->opt.grid_nx <= 0) return fail(h, MRF_ESTATE, "splash mode needs options.grid");
     if (mode == MRF_MODE_SPLASH && !h->d_pot) {
         drop_graphs(h);
@@ -597,6 +627,7 @@ mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode) {
         }
     }
     h->sweep_host += n_sweeps;
+    if (mode == MRF_MODE_LEARNED) h->proposed += (uint64_t)n_sweeps * h->la.nb * h->C;
     return MRF_OK;
 }
 
@@ -1010,6 +1041,277 @@ mrf_status mrf_batch_get_labels(mrf_batch_t* b, int32_t g, uint8_t* out) {
     }
     for (size_t v = 0; v < n; ++v)
         for (size_t c = 0; c < C; ++c) out[c * n + v] = buf[v * C + c];
+    return MRF_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================ learned proposal
+
+namespace {
+
+// splitmix64 (Steele, Lea, Flood 2014): seeding and shuffling on the host.
+uint64_t splitmix64(uint64_t& x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+mrf_status learned_train_buffers(mrf_t* h, int64_t rows) {
+    if (rows <= h->train_rows) return MRF_OK;
+    const int64_t H = h->la.H, O = h->la.O, Dp = h->la.Dp;
+    MRF_CUDA(h, dalloc(h->d_train, (size_t)rows * (4 * H + 2 * O)));
+    MRF_CUDA(h, dalloc(h->d_bidx, (size_t)rows));
+    MRF_CUDA(h, dalloc(h->d_bX, (size_t)rows * Dp));
+    MRF_CUDA(h, dalloc(h->d_by, (size_t)rows * kLearnBlock));
+    MRF_CUDA(h, dalloc(h->d_bn, (size_t)rows));
+    float* t = h->d_train;
+    h->la.t_h1 = t; t += rows * H;
+    h->la.t_h2 = t; t += rows * H;
+    h->la.t_d2 = t; t += rows * H;
+    h->la.t_d1 = t; t += rows * H;
+    h->la.t_z = t; t += rows * O;
+    h->la.t_dz = t;
+    h->train_rows = rows;
+    return MRF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t mrf_learned_param_count(const mrf_t* h) { return h && h->learned ? h->n_params : 0; }
+
+mrf_status mrf_learned_setup(mrf_t* h, const int32_t* block_of_site, int32_t hidden, uint64_t init_seed) {
+    if (!h || !block_of_site) return MRF_EINVAL;
+    if (!h->has_factors) return fail(h, MRF_ESTATE, "mrf_set_factors first");
+    if (!h->d_resid) return fail(h, MRF_ESTATE, "create the handle with options.exact_edges = 1");
+    if (hidden < 64 || hidden % 64) return fail(h, MRF_EINVAL, "hidden width must be a positive multiple of 64");
+    const int N = h->N, L = h->L, C = h->C;
+    int nb = 0;
+    for (int v = 0; v < N; ++v) {
+        if (block_of_site[v] < 0) return fail(h, MRF_ERANGE, "every site needs a block");
+        nb = std::max(nb, block_of_site[v] + 1);
+    }
+    std::vector<std::vector<int32_t>> mem(nb);
+    for (int v = 0; v < N; ++v) mem[block_of_site[v]].push_back(v);
+    std::vector<int32_t> members((size_t)nb * kLearnBlock, -1), nmem(nb), pos(N);
+    for (int b = 0; b < nb; ++b) {
+        if (mem[b].empty() || mem[b].size() > (size_t)kLearnBlock)
+            return fail(h, MRF_ERANGE, "block " + std::to_string(b) + " has " + std::to_string(mem[b].size()) + " sites");
+        nmem[b] = (int32_t)mem[b].size();
+        for (size_t i = 0; i < mem[b].size(); ++i) { members[(size_t)b * kLearnBlock + i] = mem[b][i]; pos[mem[b][i]] = (int32_t)i; }
+    }
+    std::vector<int64_t> iptr(nb + 1, 0);
+    std::vector<uint8_t> skip((size_t)h->E_slots, 0);
+    for (int64_t e = 0; e < h->E_slots; ++e) {
+        const int s = h->h_src[e];
+        if (s >= 0 && block_of_site[s] == block_of_site[h->h_dst[e]]) { iptr[block_of_site[s] + 1]++; skip[e] = 1; }
+    }
+    for (int b = 0; b < nb; ++b) iptr[b + 1] += iptr[b];
+    std::vector<int4> intra((size_t)iptr[nb]);
+    std::vector<int64_t> fill(iptr.begin(), iptr.end() - 1);
+    for (int64_t e = 0; e < h->E_slots; ++e) {
+        if (!skip[e]) continue;
+        const int s = h->h_src[e], t = h->h_dst[e];
+        intra[fill[block_of_site[s]]++] = make_int4((int)e, pos[s], pos[t], 0);
+    }
+    LearnedArgs& a = h->la;
+    a = LearnedArgs{};
+    a.nb = nb; a.L = L; a.H = hidden; a.O = kLearnBlock * L;
+    a.Dp = (kLearnBlock * L + kLearnPairs + 31) / 32 * 32;
+    const int64_t H = hidden, Dp = a.Dp, O = a.O;
+    h->n_params = H * Dp + H + H * H + H + O * H + O;
+    const int64_t R = (int64_t)nb * C;
+    MRF_CUDA(h, dalloc(h->d_members, members.size())); MRF_CUDA(h, dalloc(h->d_nmem, (size_t)nb));
+    MRF_CUDA(h, dalloc(h->d_intra_ptr, (size_t)nb + 1)); MRF_CUDA(h, dalloc(h->d_intra, std::max<size_t>(intra.size(), 1)));
+    MRF_CUDA(h, dalloc(h->d_cf, (size_t)nb * kLearnPairs)); MRF_CUDA(h, dalloc(h->d_skip, (size_t)h->E_slots));
+    MRF_CUDA(h, dalloc(h->d_X, (size_t)R * Dp)); MRF_CUDA(h, dalloc(h->d_H1, (size_t)R * H));
+    MRF_CUDA(h, dalloc(h->d_H2, (size_t)R * H)); MRF_CUDA(h, dalloc(h->d_Z, (size_t)R * O));
+    MRF_CUDA(h, dalloc(h->d_w32, (size_t)h->n_params)); MRF_CUDA(h, dalloc(h->d_grad, (size_t)h->n_params));
+    MRF_CUDA(h, dalloc(h->d_m, (size_t)h->n_params)); MRF_CUDA(h, dalloc(h->d_v, (size_t)h->n_params));
+    MRF_CUDA(h, dalloc(h->d_Wb, (size_t)(H * Dp + H * H + O * H)));
+    MRF_CUDA(h, dalloc(h->d_acc, 1));
+    if (!h->d_pot) MRF_CUDA(h, dalloc(h->d_pot, (size_t)N * L * C));
+    MRF_CUDA(h, to_device(h->d_members, members.data(), (int64_t)members.size(), MRF_PTR_HOST, h->stream));
+    MRF_CUDA(h, to_device(h->d_nmem, nmem.data(), nb, MRF_PTR_HOST, h->stream));
+    MRF_CUDA(h, to_device(h->d_intra_ptr, iptr.data(), nb + 1, MRF_PTR_HOST, h->stream));
+    if (!intra.empty()) MRF_CUDA(h, to_device(h->d_intra, intra.data(), (int64_t)intra.size(), MRF_PTR_HOST, h->stream));
+    MRF_CUDA(h, to_device(h->d_skip, skip.data(), h->E_slots, MRF_PTR_HOST, h->stream));
+    // He-uniform weights, zero biases (host generator, then float32 master copy)
+    std::vector<float> w((size_t)h->n_params, 0.0f);
+    uint64_t st = init_seed;
+    auto uni = [&]() { return (double)(splitmix64(st) >> 11) * (1.0 / 9007199254740992.0); };
+    auto fill_w = [&](int64_t off, int64_t rows, int64_t cols) {
+        const double lim = std::sqrt(6.0 / (double)cols);
+        for (int64_t i = 0; i < rows * cols; ++i) w[off + i] = (float)((2.0 * uni() - 1.0) * lim);
+    };
+    fill_w(0, H, Dp);
+    fill_w(H * Dp + H, H, H);
+    fill_w(H * Dp + H + H * H + H, O, H);
+    MRF_CUDA(h, to_device(h->d_w32, w.data(), h->n_params, MRF_PTR_HOST, h->stream));
+    MRF_CUDA(h, cudaMemsetAsync(h->d_m, 0, sizeof(float) * h->n_params, h->stream));
+    MRF_CUDA(h, cudaMemsetAsync(h->d_v, 0, sizeof(float) * h->n_params, h->stream));
+    MRF_CUDA(h, cudaMemsetAsync(h->d_acc, 0, sizeof(unsigned long long), h->stream));
+    a.members = h->d_members; a.nmem = h->d_nmem; a.intra_ptr = h->d_intra_ptr; a.intra = h->d_intra; a.cf = h->d_cf;
+    a.X = h->d_X; a.H1 = h->d_H1; a.H2 = h->d_H2; a.Zm = h->d_Z; a.Z = h->d_Z;
+    a.w32 = h->d_w32;
+    a.b1 = h->d_w32 + H * Dp; a.b2 = h->d_w32 + H * Dp + H + H * H; a.b3 = h->d_w32 + H * Dp + H + H * H + H + O * H;
+    a.W1b = h->d_Wb; a.W2b = h->d_Wb + H * Dp; a.W3b = h->d_Wb + H * Dp + H * H;
+    a.grad = h->d_grad; a.adam_m = h->d_m; a.adam_v = h->d_v; a.n_accepted = h->d_acc;
+    a.ds_X = h->d_dsX; a.ds_y = h->d_dsy; a.ds_n = h->d_dsn;
+    MRF_CUDA(h, learned_sync_bf16(a, h->stream));
+    MRF_CUDA(h, launch_learned_couplings(a, h->d_resid, h->d_cf, h->stream));
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
+    h->learned = true;
+    h->adam_step = 0;
+    h->proposed = 0;
+    return MRF_OK;
+}
+
+mrf_status mrf_learned_set_params(mrf_t* h, const float* params, int64_t n) {
+    if (!h || !params) return MRF_EINVAL;
+    if (!h->learned) return fail(h, MRF_ESTATE, "mrf_learned_setup first");
+    if (n != h->n_params) return fail(h, MRF_EINVAL, "parameter count " + std::to_string(n) + " != " + std::to_string(h->n_params));
+    MRF_CUDA(h, to_device(h->d_w32, params, n, MRF_PTR_HOST, h->stream));
+    MRF_CUDA(h, learned_sync_bf16(h->la, h->stream));
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    return MRF_OK;
+}
+
+mrf_status mrf_learned_get_params(mrf_t* h, float* params, int64_t n) {
+    if (!h || !params) return MRF_EINVAL;
+    if (!h->learned) return fail(h, MRF_ESTATE, "mrf_learned_setup first");
+    if (n != h->n_params) return fail(h, MRF_EINVAL, "parameter count mismatch");
+    MRF_CUDA(h, cudaMemcpyAsync(params, h->d_w32, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream));
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    return MRF_OK;
+}
+
+mrf_status mrf_learned_harvest(mrf_t* h, int32_t n_sweeps, int32_t stride, int64_t max_rows, int64_t* rows) {
+    if (!h || n_sweeps < 0 || stride <= 0 || max_rows <= 0) return MRF_EINVAL;
+    if (!h->learned) return fail(h, MRF_ESTATE, "mrf_learned_setup first");
+    if (max_rows > h->ds_cap) {
+        if (h->ds_rows) return fail(h, MRF_ESTATE, "the training set cannot grow once filled");
+        MRF_CUDA(h, dalloc(h->d_dsX, (size_t)max_rows * h->la.Dp));
+        MRF_CUDA(h, dalloc(h->d_dsy, (size_t)max_rows * kLearnBlock));
+        MRF_CUDA(h, dalloc(h->d_dsn, (size_t)max_rows));
+        h->ds_cap = max_rows;
+        h->la.ds_X = h->d_dsX; h->la.ds_y = h->d_dsy; h->la.ds_n = h->d_dsn;
+    }
+    const int64_t R = (int64_t)h->la.nb * h->C;
+    for (int i = 0; i < n_sweeps && h->ds_rows < h->ds_cap; ++i) {
+        if (h->schedule == 0) { mrf_status st = tune_schedule(h); if (st != MRF_OK) return st; }
+        mrf_status st = enqueue_sweep(h, MRF_MODE_PLAIN);
+        if (st != MRF_OK) return st;
+        h->sweep_host += 1;
+        SweepArgs a = make_args(h);
+        a.skip = h->d_skip;
+        const int phase = (int)(h->sweep_host % stride);
+        MRF_CUDA(h, launch_dual(a, h->layout, h->stream));
+        MRF_CUDA(h, launch_potential(a, h->layout, h->stream));
+        MRF_CUDA(h, launch_learned_features(h->la, a, h->stream));
+        MRF_CUDA(h, launch_learned_harvest(h->la, a, stride, phase, h->ds_rows, h->ds_cap, h->stream));
+        const int64_t k = phase < R ? (R - phase + stride - 1) / stride : 0;
+        h->ds_rows = std::min(h->ds_cap, h->ds_rows + k);
+    }
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (rows) *rows = h->ds_rows;
+    return MRF_OK;
+}
+
+mrf_status mrf_learned_train(mrf_t* h, int32_t steps, int32_t batch, float lr, uint64_t shuffle_seed, float* loss_trace) {
+    if (!h || steps < 0 || batch <= 0) return MRF_EINVAL;
+    if (!h->learned) return fail(h, MRF_ESTATE, "mrf_learned_setup first");
+    if (h->ds_rows <= 0) return fail(h, MRF_ESTATE, "harvest a training set first");
+    mrf_status st = learned_train_buffers(h, batch);
+    if (st != MRF_OK) return st;
+    if (steps > h->loss_cap) { MRF_CUDA(h, dalloc(h->d_loss, (size_t)steps)); h->loss_cap = steps; }
+    std::vector<int32_t> idx((size_t)batch);
+    uint64_t rs = shuffle_seed;
+    for (int s = 0; s < steps; ++s) {
+        for (int j = 0; j < batch; ++j) idx[j] = (int32_t)(splitmix64(rs) % (uint64_t)h->ds_rows);
+        MRF_CUDA(h, to_device(h->d_bidx, idx.data(), batch, MRF_PTR_HOST, h->stream));
+        MRF_CUDA(h, learned_gather(h->la, h->d_bidx, batch, h->d_bX, h->d_by, h->d_bn, h->stream));
+        MRF_CUDA(h, learned_forward_backward(h->la, batch, h->d_bX, h->d_by, h->d_bn, h->d_loss + s, h->stream));
+        h->adam_step += 1;
+        MRF_CUDA(h, learned_adam(h->la, h->n_params, lr, h->adam_step, h->stream));
+    }
+    std::vector<double> losses((size_t)steps);
+    if (steps) MRF_CUDA(h, cudaMemcpyAsync(losses.data(), h->d_loss, sizeof(double) * steps, cudaMemcpyDeviceToHost, h->stream));
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    drop_graphs(h);   // weights changed; captured learned sweeps read them through pointers, so this is only hygiene
+    if (loss_trace) for (int s = 0; s < steps; ++s) loss_trace[s] = (float)losses[s];
+    return MRF_OK;
+}
+
+mrf_status mrf_learned_grad(mrf_t* h, const float* X, const uint8_t* y, const uint8_t* nmem, int32_t rows, float* grads,
+                            double* loss) {
+    if (!h || !X || !y || !nmem || rows <= 0 || !grads) return MRF_EINVAL;
+    if (!h->learned) return fail(h, MRF_ESTATE, "mrf_learned_setup first");
+    mrf_status st = learned_train_buffers(h, rows);
+    if (st != MRF_OK) return st;
+    const int64_t Dp = h->la.Dp;
+    float* d_xf = nullptr;
+    MRF_CUDA(h, dalloc(d_xf, (size_t)rows * Dp));
+    struct G { float*& p; ~G() { dfree(p); } } guard{d_xf};
+    MRF_CUDA(h, to_device(d_xf, X, rows * Dp, MRF_PTR_HOST, h->stream));
+    MRF_CUDA(h, launch_to_bf16(d_xf, h->d_bX, rows * Dp, h->stream));
+    MRF_CUDA(h, to_device(h->d_by, y, (int64_t)rows * kLearnBlock, MRF_PTR_HOST, h->stream));
+    MRF_CUDA(h, to_device(h->d_bn, nmem, rows, MRF_PTR_HOST, h->stream));
+    if (h->loss_cap < 1) { MRF_CUDA(h, dalloc(h->d_loss, 1)); h->loss_cap = 1; }
+    MRF_CUDA(h, learned_forward_backward(h->la, rows, h->d_bX, h->d_by, h->d_bn, h->d_loss, h->stream));
+    MRF_CUDA(h, cudaMemcpyAsync(grads, h->d_grad, sizeof(float) * h->n_params, cudaMemcpyDeviceToHost, h->stream));
+    double l = 0.0;
+    MRF_CUDA(h, cudaMemcpyAsync(&l, h->d_loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (loss) *loss = l;
+    return MRF_OK;
+}
+
+mrf_status mrf_learned_forward(mrf_t* h, const float* X, int32_t rows, float* z) {
+    if (!h || !X || !z || rows <= 0) return MRF_EINVAL;
+    if (!h->learned) return fail(h, MRF_ESTATE, "mrf_learned_setup first");
+    if ((int64_t)rows > (int64_t)h->la.nb * h->C) return fail(h, MRF_ERANGE, "at most n_blocks x chains rows");
+    const int64_t Dp = h->la.Dp;
+    float* d_xf = nullptr;
+    MRF_CUDA(h, dalloc(d_xf, (size_t)rows * Dp));
+    struct G { float*& p; ~G() { dfree(p); } } guard{d_xf};
+    MRF_CUDA(h, to_device(d_xf, X, rows * Dp, MRF_PTR_HOST, h->stream));
+    MRF_CUDA(h, launch_to_bf16(d_xf, h->d_X, rows * Dp, h->stream));
+    MRF_CUDA(h, launch_learned_mlp(h->la, rows, h->d_X, h->stream));
+    MRF_CUDA(h, cudaMemcpyAsync(z, h->d_Z, sizeof(float) * rows * h->la.O, cudaMemcpyDeviceToHost, h->stream));
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    return MRF_OK;
+}
+
+mrf_status mrf_learned_stats(mrf_t* h, uint64_t* proposed, uint64_t* accepted) {
+    if (!h) return MRF_EINVAL;
+    if (!h->learned) return fail(h, MRF_ESTATE, "mrf_learned_setup first");
+    unsigned long long acc = 0;
+    MRF_CUDA(h, cudaMemcpyAsync(&acc, h->d_acc, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (proposed) *proposed = h->proposed;
+    if (accepted) *accepted = acc;
+    return MRF_OK;
+}
+
+mrf_status mrf_learned_debug(mrf_t* h, float* X, float* z) {
+    if (!h) return MRF_EINVAL;
+    if (!h->learned) return fail(h, MRF_ESTATE, "mrf_learned_setup first");
+    const int64_t R = (int64_t)h->la.nb * h->C;
+    if (X) {
+        std::vector<__nv_bfloat16> xb((size_t)(R * h->la.Dp));
+        MRF_CUDA(h, cudaMemcpyAsync(xb.data(), h->d_X, sizeof(__nv_bfloat16) * xb.size(), cudaMemcpyDeviceToHost, h->stream));
+        MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+        for (size_t i = 0; i < xb.size(); ++i) X[i] = __bfloat162float(xb[i]);
+    }
+    if (z) {
+        MRF_CUDA(h, cudaMemcpyAsync(z, h->d_Z, sizeof(float) * R * h->la.O, cudaMemcpyDeviceToHost, h->stream));
+        MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
     return MRF_OK;
 }
 

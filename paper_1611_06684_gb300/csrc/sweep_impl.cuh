@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(256, 4) k_dual(SweepArgs a) {
     const uint8_t* xin = a.x + (size_t)(sweep & 1) * a.N * a.C;
     uint32_t bits[E::W];
     const int s = a.src[e];
-    if (s >= 0 && !(a.splash && is_tree_edge(a, e))) {
+    if (s >= 0 && !(a.splash && is_tree_edge(a, e)) && !(a.skip && a.skip[e])) {
         const int t = a.dst[e];
         dual_bits<L, LAYOUT>(e, c, xin[(int64_t)s * a.C + c], xin[(int64_t)t * a.C + c],
                              a.tpl + (int64_t)e * E::W * 32, a.thr + (int64_t)e * E::M, sweep, a.key, bits);

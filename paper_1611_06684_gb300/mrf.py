@@ -20,16 +20,17 @@ LIB_PATH = os.path.join(HERE, "libmrf.so")
 
 MRF_OK, MRF_EINVAL, MRF_ENONFINITE, MRF_ENOMEM, MRF_ECUDA, MRF_ERANGE, MRF_ETIMEOUT, MRF_ESTATE = range(8)
 MRF_PTR_HOST, MRF_PTR_DEVICE = 0, 1
-MODE_PLAIN, MODE_FUSED, MODE_SPLASH = 0, 1, 2
+MODE_PLAIN, MODE_FUSED, MODE_SPLASH, MODE_LEARNED = 0, 1, 2, 3
 LAYOUT_PIVOT, LAYOUT_DIAG = 0, 1
-K_DUAL, K_PRIMAL, K_FUSED, K_POTENTIAL, K_FFBS, K_ACCUMULATE, K_COUNT = range(7)
-KERNEL_NAMES = ["k_dual", "k_primal", "k_primal<fused>", "k_splash_potential", "k_ffbs", "k_accumulate"]
+K_DUAL, K_PRIMAL, K_FUSED, K_POTENTIAL, K_FFBS, K_ACCUMULATE, K_FEATURES, K_MLP, K_MH, K_COUNT = range(10)
+KERNEL_NAMES = ["k_dual", "k_primal", "k_primal<fused>", "k_potential", "k_ffbs", "k_accumulate",
+                "k_learned_features", "k_gemm_nt (mlp)", "k_learned_mh"]
 
 
 class mrf_options(ct.Structure):
     _fields_ = [("grid_nx", ct.c_int32), ("grid_ny", ct.c_int32), ("grid_nz", ct.c_int32),
                 ("record_logp", ct.c_int32), ("use_graphs", ct.c_int32), ("schedule", ct.c_int32),
-                ("kernel_timing", ct.c_int32), ("reserved", ct.c_int32 * 7)]
+                ("kernel_timing", ct.c_int32), ("exact_edges", ct.c_int32), ("reserved", ct.c_int32 * 6)]
 
 
 class mrf_info(ct.Structure):
@@ -60,6 +61,16 @@ _SIGS = {
     "mrf_debug_theta": (ct.c_int, [_P, _P]),
     "mrf_kernel_times": (ct.c_int, [_P, _P, _P]),
     "mrf_sweep_noalloc": (ct.c_int, [_P, _P, _P, ct.c_int64]),
+    "mrf_learned_setup": (ct.c_int, [_P, _P, ct.c_int32, ct.c_uint64]),
+    "mrf_learned_param_count": (ct.c_int64, [_P]),
+    "mrf_learned_set_params": (ct.c_int, [_P, _P, ct.c_int64]),
+    "mrf_learned_get_params": (ct.c_int, [_P, _P, ct.c_int64]),
+    "mrf_learned_harvest": (ct.c_int, [_P, ct.c_int32, ct.c_int32, ct.c_int64, ct.POINTER(ct.c_int64)]),
+    "mrf_learned_train": (ct.c_int, [_P, ct.c_int32, ct.c_int32, ct.c_float, ct.c_uint64, _P]),
+    "mrf_learned_grad": (ct.c_int, [_P, _P, _P, _P, ct.c_int32, _P, ct.POINTER(ct.c_double)]),
+    "mrf_learned_forward": (ct.c_int, [_P, _P, ct.c_int32, _P]),
+    "mrf_learned_stats": (ct.c_int, [_P, ct.POINTER(ct.c_uint64), ct.POINTER(ct.c_uint64)]),
+    "mrf_learned_debug": (ct.c_int, [_P, _P, _P]),
     "mrf_batch_create": (ct.c_int, [ct.POINTER(_P), ct.c_int32, _P, _P, ct.c_int32, ct.c_uint64,
                                     ct.POINTER(mrf_options), _P]),
     "mrf_batch_set_factors": (ct.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -134,7 +145,7 @@ class MRF:
 
     def __init__(self, n_vars: int, n_labels: int, n_chains: int, seed: int = 0, grid=None,
                  record_logp: bool = False, use_graphs: bool = True, schedule: int = 0, stream=None,
-                 kernel_timing: bool = False):
+                 kernel_timing: bool = False, exact_edges: bool = False):
         lib = load()
         opt = mrf_options()
         lib.mrf_default_options(ct.byref(opt))
@@ -144,6 +155,7 @@ class MRF:
         opt.use_graphs = int(use_graphs)
         opt.schedule = int(schedule)
         opt.kernel_timing = int(kernel_timing)
+        opt.exact_edges = int(exact_edges)
         self.stream = _current_stream() if stream is None else int(stream)
         h = _P()
         st = lib.mrf_create(ct.byref(h), n_vars, n_labels, n_chains, ct.c_uint64(seed & (2**64 - 1)), ct.byref(opt),
@@ -252,6 +264,57 @@ class MRF:
         """One plain sweep without device allocation (mrf_sweep_noalloc): labels
         are CUDA tensors [n_vars][n_chains] uint8 owned by the caller."""
         self._check(self.lib.mrf_sweep_noalloc(self.h, labels_in.data_ptr(), labels_out.data_ptr(), int(sweep_index)))
+
+    # -- learned block proposal
+    def learned_setup(self, block_of_site, hidden: int = 256, seed: int = 0):
+        bos = np.ascontiguousarray(block_of_site, np.int32)
+        self._check(self.lib.mrf_learned_setup(self.h, bos.ctypes.data, int(hidden), ct.c_uint64(seed)))
+        self.n_params = int(self.lib.mrf_learned_param_count(self.h))
+
+    def learned_set_params(self, flat):
+        f = np.ascontiguousarray(flat, np.float32)
+        self._check(self.lib.mrf_learned_set_params(self.h, f.ctypes.data, f.shape[0]))
+
+    def learned_get_params(self):
+        out = np.zeros(self.n_params, np.float32)
+        self._check(self.lib.mrf_learned_get_params(self.h, out.ctypes.data, out.shape[0]))
+        return out
+
+    def learned_harvest(self, n_sweeps: int, stride: int, max_rows: int) -> int:
+        rows = ct.c_int64()
+        self._check(self.lib.mrf_learned_harvest(self.h, int(n_sweeps), int(stride), int(max_rows), ct.byref(rows)))
+        return rows.value
+
+    def learned_train(self, steps: int, batch: int, lr: float, seed: int = 0):
+        trace = np.zeros(max(steps, 1), np.float32)
+        self._check(self.lib.mrf_learned_train(self.h, int(steps), int(batch), ct.c_float(lr), ct.c_uint64(seed),
+                                               trace.ctypes.data))
+        return trace[:steps]
+
+    def learned_grad(self, X, y, nmem):
+        X = np.ascontiguousarray(X, np.float32); y = np.ascontiguousarray(y, np.uint8)
+        n = np.ascontiguousarray(nmem, np.uint8)
+        g = np.zeros(self.n_params, np.float32)
+        loss = ct.c_double()
+        self._check(self.lib.mrf_learned_grad(self.h, X.ctypes.data, y.ctypes.data, n.ctypes.data, X.shape[0],
+                                              g.ctypes.data, ct.byref(loss)))
+        return loss.value, g
+
+    def learned_forward(self, X, n_out: int):
+        X = np.ascontiguousarray(X, np.float32)
+        z = np.zeros((X.shape[0], n_out), np.float32)
+        self._check(self.lib.mrf_learned_forward(self.h, X.ctypes.data, X.shape[0], z.ctypes.data))
+        return z
+
+    def learned_stats(self):
+        p, a = ct.c_uint64(), ct.c_uint64()
+        self._check(self.lib.mrf_learned_stats(self.h, ct.byref(p), ct.byref(a)))
+        return p.value, a.value
+
+    def learned_debug(self, rows: int, width: int, n_out: int):
+        X = np.zeros((rows, width), np.float32); z = np.zeros((rows, n_out), np.float32)
+        self._check(self.lib.mrf_learned_debug(self.h, X.ctypes.data, z.ctypes.data))
+        return X, z
 
     def kernel_times(self):
         """{kernel name: (total ms, launches)} since the previous call."""

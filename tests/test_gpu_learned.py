@@ -1,0 +1,160 @@
+"""GPU parity of the learned block proposal: the tensor-core MLP forward and the
+training gradients against the float64 oracle, one learned MH sweep against
+oracle.learned, exactness of the MH-corrected chain (marginals within 3 sigma
+for untrained weights), and the gain training gives (loss and acceptance)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from oracle import brute, decompose as dc, learned as ln, sampler
+from paper_1611_06684_gb300 import workloads as wl
+from paper_1611_06684_gb300 import mrf as M
+from tests.gpu_helpers import compare_sweep
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1611_06684_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _flat(params):
+    return np.concatenate([np.asarray(p, np.float64).ravel() for p in params]).astype(np.float32)
+
+
+def _params(L, hidden, seed, bias_scale=0.1):
+    p = ln.init_params(L, hidden=hidden, seed=seed)
+    rng = np.random.default_rng(seed + 100)
+    for k in (1, 3, 5):
+        p[k] = rng.normal(0, bias_scale, p[k].shape).astype(np.float32).astype(np.float64)
+    return p
+
+
+def _setup(model, C, seed, hidden, bos, wseed=5):
+    h = M.MRF(model.n_vars, model.n_labels, C, seed=seed, exact_edges=True, use_graphs=False, record_logp=False)
+    h.set_factors(model.unary, model.src, model.dst, model.pair)
+    h.learned_setup(bos, hidden=hidden, seed=1)
+    params = _params(model.n_labels, hidden, wseed)
+    h.learned_set_params(_flat(params))
+    return h, params
+
+
+def test_forward_matches_oracle():
+    model = wl.ba_potts(2000, m=5, L=4, seed=1)
+    bos = wl.bfs_blocks(model, 16, seed=2)
+    h, params = _setup(model, 4, 3, 128, bos)
+    d, dp = ln.feature_width(4)
+    rng = np.random.default_rng(0)
+    X = ln.to_bf16(rng.normal(0, 1.0, size=(300, dp)))
+    X[:, d:] = 0
+    zg = h.learned_forward(X, 64)
+    zr = ln.mlp_forward_bf16(params, X)
+    err = np.abs(zg - zr) / np.maximum(1.0, np.abs(zr))
+    assert err.max() < 1e-2, err.max()
+    assert np.median(err) < 1e-4
+
+
+def test_training_gradients_match_oracle():
+    model = wl.ba_potts(1500, m=5, L=4, seed=2)
+    bos = wl.bfs_blocks(model, 16, seed=3)
+    h, params = _setup(model, 2, 4, 64, bos)
+    d, dp = ln.feature_width(4)
+    rng = np.random.default_rng(1)
+    R = 257
+    X = ln.to_bf16(rng.normal(0, 1.0, size=(R, dp))); X[:, d:] = 0
+    y = rng.integers(0, 4, size=(R, 16)).astype(np.uint8)
+    nmem = rng.integers(1, 17, size=R).astype(np.uint8)
+    loss_g, g = h.learned_grad(X, y, nmem)
+    loss_r, grads = ln.loss_and_grads(params, X, y.astype(np.int64), nmem.astype(np.int64), 4)
+    assert abs(loss_g - loss_r) <= 1e-3 * abs(loss_r)
+    off = 0
+    for gr in grads:
+        n = gr.size
+        gg = g[off:off + n].reshape(gr.shape)
+        off += n
+        assert np.abs(gg - gr).max() <= 1e-2 * max(np.abs(gr).max(), 1e-6)
+
+
+def test_learned_sweep_matches_oracle():
+    model = wl.ba_potts(900, m=5, L=4, seed=3)
+    dec = dc.decompose(model)
+    bos = wl.bfs_blocks(model, 16, seed=4)
+    C, seed, t = 4, 21, 6
+    h, params = _setup(model, C, seed, 64, bos)
+    rng = np.random.default_rng(2)
+    x0 = rng.integers(0, 4, size=(C, model.n_vars))
+    h.set_labels(x0.astype(np.uint8))
+    h.set_sweep_index(t)
+    h.sweep(1, M.MODE_LEARNED)
+    ref = ln.learned_sweep(model, dec, x0, t, seed, bos, params, bf16_activations=True)
+    # cut duals identical except boundary draws
+    th = M.unpack_theta(h.debug_theta(), dec.n_entries)
+    dual_b = np.abs(ref["u_dual"] - ref["p_dual"]) < 1e-6
+    assert not ((th != ref["theta"]) & ~dual_b).any()
+    nb = len(ref["members"])
+    d, dp = ln.feature_width(4)
+    Xg, zg = h.learned_debug(nb * C, dp, 64)
+    Xr = ln.to_bf16(ref["X"])
+    assert np.abs(Xg - Xr).max() <= 2.0 ** -7 * max(1.0, np.abs(Xr).max())
+    errz = np.abs(zg - ref["z"]) / np.maximum(1.0, np.abs(ref["z"]))
+    assert errz.max() < 1e-2
+    x_gpu = h.get_labels()
+    compared = 0
+    for b, m in enumerate(ref["members"]):
+        u_prop, cdf = ref["prop"][b]
+        for c in range(C):
+            near = np.any(np.abs(u_prop[c][:, None] - cdf[c]) < 1e-3)
+            near |= abs(ref["u_acc"][b, c] - np.exp(min(0.0, ref["log_alpha"][b, c]))) < 1e-3
+            if near:
+                continue
+            compared += 1
+            assert np.array_equal(x_gpu[c, m], ref["x"][c, m]), (b, c)
+    assert compared > 0.8 * nb * C
+    p, a = h.learned_stats()
+    assert p == nb * C and 0 <= a <= p
+
+
+def test_learned_chain_marginals_within_3_sigma():
+    model = wl.tiny_potts(10, 3, 16, seed=7, beta_max=1.0)
+    exact, _ = brute.exact_marginals(model)
+    bos = wl.bfs_blocks(model, 4, seed=1)
+    C, T, burn = 4096, 150, 30
+    h, _ = _setup(model, C, 8, 64, bos, wseed=11)         # untrained proposal
+    acc = np.zeros((C, model.n_vars, 3))
+    for t in range(T):
+        h.sweep(1, M.MODE_LEARNED)
+        if t >= burn:
+            x = h.get_labels()
+            acc[np.arange(C)[:, None], np.arange(model.n_vars)[None, :], x] += 1
+    cm = acc / (T - burn)
+    est, sig = cm.mean(0), cm.std(0, ddof=1) / np.sqrt(C)
+    z = np.abs(est - exact) / np.maximum(sig, 1e-12)
+    assert z.max() < 4.0 and np.mean(z < 3.0) > 0.95, z.max()
+    p, a = h.learned_stats()
+    assert a > 0
+
+
+def test_training_reduces_loss_and_raises_acceptance():
+    model = wl.ba_potts(4000, m=5, L=4, seed=5)
+    bos = wl.bfs_blocks(model, 16, seed=6)
+    C = 8
+    h, _ = _setup(model, C, 9, 128, bos)
+    h.sweep(30, M.MODE_PLAIN)                         # towards stationarity
+    def acceptance(n):
+        p0, a0 = h.learned_stats()
+        h.sweep(n, M.MODE_LEARNED)
+        p1, a1 = h.learned_stats()
+        return (a1 - a0) / (p1 - p0)
+    before = acceptance(4)
+    rows = h.learned_harvest(40, 4, 200000)
+    assert rows > 10000
+    trace = h.learned_train(400, 512, 2e-3, seed=3)
+    assert trace[-40:].mean() < 0.8 * trace[:40].mean()
+    after = acceptance(4)
+    print("acceptance before", before, "after", after, "loss", trace[:5], trace[-5:])
+    assert after > before + 0.05
