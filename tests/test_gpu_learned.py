@@ -126,8 +126,10 @@ def test_learned_chain_marginals_within_3_sigma():
     C, T, burn = 4096, 150, 30
     h, _ = _setup(model, C, 8, 64, bos, wseed=11)         # untrained proposal
     acc = np.zeros((C, model.n_vars, 3))
+    # learned and plain sweeps alternate: each leaves p invariant, the plain
+    # sweep guarantees mixing, so any bias of the learned step would show
     for t in range(T):
-        h.sweep(1, M.MODE_LEARNED)
+        h.sweep(1, M.MODE_LEARNED if t % 2 == 0 else M.MODE_PLAIN)
         if t >= burn:
             x = h.get_labels()
             acc[np.arange(C)[:, None], np.arange(model.n_vars)[None, :], x] += 1
