@@ -338,13 +338,169 @@ def run_reference(args, ws, rank):
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def _timed(stream, fn):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_batch_workload(args):
+    """Batched dynamic workload: many Erdos-Renyi graphs (sizes logU[100, 50000],
+    mean degree U[3, 20], L in {2,4,8,16}, tables exp(U[-0.5, 0.5])), one chain
+    each; a round = one edit (remove ceil(1%) of every graph's edges, add as many
+    with fresh tables) + 10 sweeps.  Compared with one handle per graph."""
+    import torch
+    from paper_1611_06684_gb300 import build as B, mrf as M, workloads as wl
+    B.build()
+    n_graphs = args.scale or 500
+    specs = wl.er_batch_specs(n_graphs, seed=0)
+    t0 = time.time()
+    models = [wl.er_graph(sp) for sp in specs]
+    gen_s = time.time() - t0
+    stream = torch.cuda.Stream()
+    b = M.MRFBatch([m.n_vars for m in models], [m.n_labels for m in models], 1, seed=args.seed,
+                   stream=stream.cuda_stream, use_graphs=True)
+    b.set_factors(models)
+    for g, m in enumerate(models):
+        m.slots = np.arange(m.n_edges) + b.graph(g).first_edge_slot
+    rng = np.random.default_rng(1)
+    N = sum(m.n_vars for m in models)
+    sweeps_per_round = 10
+    times = []
+    for r in range(args.warmup + args.steps):
+        # the edit's inputs are drawn (untimed), then the library edits and sweeps (timed)
+        rm_g, rm_s, ad_g, ad_s, ad_t, ad_p, pend = [], [], [], [], [], [], []
+        for g, m in enumerate(models):
+            rem, s_, t_, p_ = wl.er_edit(m, 0.01, rng)
+            rm_g.append(np.full(len(rem), g)); rm_s.append(m.slots[rem])
+            ad_g.append(np.full(len(s_), g)); ad_s.append(s_); ad_t.append(t_); ad_p.append(p_.ravel())
+            pend.append((rem, s_, t_, p_))
+        args_e = (np.concatenate(rm_g), np.concatenate(rm_s), np.concatenate(ad_g), np.concatenate(ad_s),
+                  np.concatenate(ad_t), np.concatenate(ad_p))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ids = b.edit_factors(*args_e)
+        b.sweep(sweeps_per_round, M.MODE_PLAIN)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t1)
+        pos = 0
+        for g, m in enumerate(models):
+            rem, s_, t_, p_ = pend[g]
+            keep = np.ones(m.n_edges, bool); keep[rem] = False
+            m.src = np.concatenate([m.src[keep], s_]).astype(np.int32)
+            m.dst = np.concatenate([m.dst[keep], t_]).astype(np.int32)
+            m.pair = np.concatenate([m.pair[keep], p_])
+            m.slots = np.concatenate([m.slots[keep], ids[pos:pos + len(s_)]]); pos += len(s_)
+    E = sum(m.n_edges for m in models)
+    dt = sum(times[args.warmup:])
+    value = N * sweeps_per_round * args.steps / dt
+    # sweep-only throughput of the batch (CUDA events)
+    ms_sweep = _timed(stream, lambda: b.sweep(sweeps_per_round, M.MODE_PLAIN)) / sweeps_per_round
+    # the same graphs with one handle each (a subset, to bound the time)
+    sub = models[: min(len(models), 100)]
+    hs = []
+    for m in sub:
+        h = M.MRF(m.n_vars, m.n_labels, 1, seed=1, stream=stream.cuda_stream, use_graphs=False)
+        h.set_factors(m.unary, m.src, m.dst, m.pair)
+        h.sweep(1, M.MODE_PLAIN)
+        hs.append(h)
+    ms_sep = _timed(stream, lambda: [h.sweep(1, M.MODE_PLAIN) for h in hs])
+    n_sub = sum(m.n_vars for m in sub)
+    return {"metric": METRIC, "workload": f"er_batch_{n_graphs}", "value": value, "unit": METRIC,
+            "n_vars": N, "n_edges": E, "graphs": n_graphs, "rounds": args.steps,
+            "round": "edit(1% remove + 1% add, every graph) + 10 sweeps", "generation_s": gen_s,
+            "sweep_only": {"ms_per_sweep": ms_sweep, "value": N / (ms_sweep / 1e3)},
+            "one_handle_per_graph": {"graphs": len(sub), "ms_per_sweep": ms_sep, "value": n_sub / (ms_sep / 1e3)},
+            "classes": [b.class_handle(k).info().n_labels for k in range(b.n_classes())]}
+
+
+def run_learned_workload(args):
+    """Barabasi-Albert Potts graph (m = 5, L = 4, beta_e ~ U[0, 0.8]), 32 chains,
+    BFS blocks of 16 sites: plain sweeps, harvest of ~1e5 (block, chain) samples,
+    training, learned sweeps; ESS/s and marginal TV of plain-only and of
+    learned+plain alternation against a long plain reference run."""
+    import torch
+    from paper_1611_06684_gb300 import build as B, mrf as M, workloads as wl
+    from oracle import diagnostics as dg
+    B.build()
+    N = args.scale or 1_000_000
+    C = 32
+    t0 = time.time()
+    model = wl.ba_potts(N, m=5, L=4, seed=0)
+    bos = wl.bfs_blocks(model, 16, seed=0)
+    gen_s = time.time() - t0
+    stream = torch.cuda.Stream()
+    h = M.MRF(N, 4, C, seed=args.seed, stream=stream.cuda_stream, exact_edges=True, use_graphs=True)
+    h.set_factors(model.unary, model.src, model.dst, model.pair)
+    h.learned_setup(bos, hidden=256, seed=1)
+    nb = int(bos.max()) + 1
+    h.sweep(200, M.MODE_PLAIN)                                   # burn-in
+    ms_plain = _timed(stream, lambda: h.sweep(20, M.MODE_PLAIN)) / 20
+    t1 = time.time()
+    stride = max(1, (nb * C * 5) // 100000)
+    rows = h.learned_harvest(5, stride, 100000)
+    harvest_s = time.time() - t1
+    p0, a0 = h.learned_stats()
+    h.sweep(2, M.MODE_LEARNED)
+    p1, a1 = h.learned_stats()
+    acc_untrained = (a1 - a0) / max(1, p1 - p0)
+    t1 = time.time()
+    trace = h.learned_train(2000, 1024, 1e-3, seed=0)
+    torch.cuda.synchronize()
+    train_s = time.time() - t1
+    ms_learned = _timed(stream, lambda: h.sweep(10, M.MODE_LEARNED)) / 10
+    p0, a0 = h.learned_stats()
+    h.sweep(4, M.MODE_LEARNED)
+    p1, a1 = h.learned_stats()
+    acc_trained = (a1 - a0) / max(1, p1 - p0)
+    # reference marginals: long plain run
+    x_start = h.get_labels()
+    t_start = h.info().sweep_index
+    h.reset_marginals(0)
+    h.sweep(args.ref_sweeps, M.MODE_PLAIN)
+    ref, _ = h.marginals()
+    rng = np.random.default_rng(0)
+    subset = np.sort(rng.choice(N, size=4096, replace=False))
+    T = args.ess_sweeps
+    out = {}
+    for name, pattern in (("plain", [M.MODE_PLAIN]), ("learned+plain", [M.MODE_LEARNED, M.MODE_PLAIN])):
+        h.set_labels(x_start)
+        h.set_sweep_index(t_start + 1000003)
+        h.reset_marginals(0)
+        trace_stat = np.zeros((T, C))
+        for t in range(T):
+            h.sweep(1, pattern[t % len(pattern)])
+            x = h.get_labels()
+            trace_stat[t] = (x[:, subset] == 0).mean(axis=1)
+        est, _ = h.marginals()
+        ess = sum(dg.ess_geyer(trace_stat[:, c]) for c in range(C))
+        ms = (ms_plain if len(pattern) == 1 else (ms_plain + ms_learned) / 2)
+        out[name] = {"ess": ess, "ms_per_sweep": ms, "ess_per_s": ess / (T * ms / 1e3),
+                     "tv_vs_reference": dg.tv_mean(est, ref), "sweeps": T}
+    return {"metric": "ESS/s", "workload": f"ba_potts_N{N}_L4_C32_blocks16", "blocks": nb,
+            "generation_s": gen_s, "plain": {"ms_per_sweep": ms_plain, "site_updates_per_s": N * C / (ms_plain / 1e3)},
+            "learned": {"ms_per_sweep": ms_learned, "site_updates_per_s": N * C / (ms_learned / 1e3),
+                        "acceptance_untrained": acc_untrained, "acceptance_trained": acc_trained,
+                        "train_rows": rows, "harvest_s": harvest_s, "train_s": train_s, "train_steps": 2000,
+                        "loss_first": float(trace[:20].mean()), "loss_last": float(trace[-20:].mean())},
+            "reference_sweeps": args.ref_sweeps, "statistic": "fraction of label 0 over 4096 fixed sites, per chain",
+            "comparison": out}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="potts3d", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="potts3d", choices=list(WORKLOADS) + ["er_batch", "ba_learned"])
+    ap.add_argument("--ref-sweeps", type=int, default=2000)
+    ap.add_argument("--ess-sweeps", type=int, default=200)
     ap.add_argument("--mode", default="plain", choices=["plain", "fused"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--scale", type=int, default=0, help="lattice edge for potts3d (default 128)")
@@ -354,6 +510,10 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()
+    if args.workload in ("er_batch", "ba_learned") and args.impl == "ours":
+        out = run_batch_workload(args) if args.workload == "er_batch" else run_learned_workload(args)
+        print(json.dumps(out))
+        return
     if args.impl == "reference":
         out = run_reference(args, ws, rank)
     else:
