@@ -371,7 +371,7 @@ def run_batch_workload(args):
     rng = np.random.default_rng(1)
     N = sum(m.n_vars for m in models)
     sweeps_per_round = 10
-    times = []
+    times, edit_times = [], []
     for r in range(args.warmup + args.steps):
         # the edit's inputs are drawn (untimed), then the library edits and sweeps (timed)
         rm_g, rm_s, ad_g, ad_s, ad_t, ad_p, pend = [], [], [], [], [], [], []
@@ -385,9 +385,12 @@ def run_batch_workload(args):
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         ids = b.edit_factors(*args_e)
+        torch.cuda.synchronize()
+        t_edit = time.perf_counter()
         b.sweep(sweeps_per_round, M.MODE_PLAIN)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t1)
+        edit_times.append(t_edit - t1)
         pos = 0
         for g, m in enumerate(models):
             rem, s_, t_, p_ = pend[g]
@@ -414,6 +417,8 @@ def run_batch_workload(args):
     return {"metric": METRIC, "workload": f"er_batch_{n_graphs}", "value": value, "unit": METRIC,
             "n_vars": N, "n_edges": E, "graphs": n_graphs, "rounds": args.steps,
             "round": "edit(1% remove + 1% add, every graph) + 10 sweeps", "generation_s": gen_s,
+            "edit_s_per_round": float(np.mean(edit_times[args.warmup:])),
+            "edges_edited_per_round": int(sum(math.ceil(0.01 * m.n_edges) for m in models)),
             "sweep_only": {"ms_per_sweep": ms_sweep, "value": N / (ms_sweep / 1e3)},
             "one_handle_per_graph": {"graphs": len(sub), "ms_per_sweep": ms_sep, "value": n_sub / (ms_sep / 1e3)},
             "classes": [b.class_handle(k).info().n_labels for k in range(b.n_classes())]}
@@ -454,6 +459,16 @@ def run_learned_workload(args):
     torch.cuda.synchronize()
     train_s = time.time() - t1
     ms_learned = _timed(stream, lambda: h.sweep(10, M.MODE_LEARNED)) / 10
+    h.set_kernel_timing(True)
+    h.kernel_times()
+    h.sweep(5, M.MODE_LEARNED)
+    kt_learned = {k: v[0] / v[1] for k, v in h.kernel_times().items()}
+    h.sweep(5, M.MODE_PLAIN)
+    kt_plain = {k: v[0] / v[1] for k, v in h.kernel_times().items()}
+    h.set_kernel_timing(False)
+    R = nb * C
+    mlp_flop = 2.0 * R * (256 * 192 + 256 * 256 + 256 * 64)
+    ms_mlp = kt_learned.get("k_gemm_nt (mlp)", float("nan"))
     p0, a0 = h.learned_stats()
     h.sweep(4, M.MODE_LEARNED)
     p1, a1 = h.learned_stats()
@@ -466,21 +481,27 @@ def run_learned_workload(args):
     ref, _ = h.marginals()
     rng = np.random.default_rng(0)
     subset = np.sort(rng.choice(N, size=4096, replace=False))
+    esub = np.sort(rng.choice(model.n_edges, size=50000, replace=False))
+    es, et, ew = model.src[esub], model.dst[esub], model.pair[esub].astype(np.float64)
     T = args.ess_sweeps
     out = {}
-    for name, pattern in (("plain", [M.MODE_PLAIN]), ("learned+plain", [M.MODE_LEARNED, M.MODE_PLAIN])):
+    for name, pattern in (("plain", [M.MODE_PLAIN]), ("learned", [M.MODE_LEARNED]),
+                          ("learned+plain", [M.MODE_LEARNED, M.MODE_PLAIN])):
         h.set_labels(x_start)
         h.set_sweep_index(t_start + 1000003)
         h.reset_marginals(0)
-        trace_stat = np.zeros((T, C))
+        stat_a = np.zeros((T, C)); stat_b = np.zeros((T, C))
         for t in range(T):
             h.sweep(1, pattern[t % len(pattern)])
             x = h.get_labels()
-            trace_stat[t] = (x[:, subset] == 0).mean(axis=1)
+            stat_a[t] = (x[:, subset] == 0).mean(axis=1)
+            stat_b[t] = ew[np.arange(len(esub))[None, :], x[:, es], x[:, et]].sum(axis=1)
         est, _ = h.marginals()
-        ess = sum(dg.ess_geyer(trace_stat[:, c]) for c in range(C))
-        ms = (ms_plain if len(pattern) == 1 else (ms_plain + ms_learned) / 2)
-        out[name] = {"ess": ess, "ms_per_sweep": ms, "ess_per_s": ess / (T * ms / 1e3),
+        ess_a = sum(dg.ess_geyer(stat_a[:, c]) for c in range(C))
+        ess_b = sum(dg.ess_geyer(stat_b[:, c]) for c in range(C))
+        ms = sum(ms_plain if md == M.MODE_PLAIN else ms_learned for md in pattern) / len(pattern)
+        out[name] = {"ms_per_sweep": ms, "ess_label0_fraction": ess_a, "ess_pair_energy": ess_b,
+                     "ess_per_s_label0": ess_a / (T * ms / 1e3), "ess_per_s_pair_energy": ess_b / (T * ms / 1e3),
                      "tv_vs_reference": dg.tv_mean(est, ref), "sweeps": T}
     return {"metric": "ESS/s", "workload": f"ba_potts_N{N}_L4_C32_blocks16", "blocks": nb,
             "generation_s": gen_s, "plain": {"ms_per_sweep": ms_plain, "site_updates_per_s": N * C / (ms_plain / 1e3)},
@@ -488,7 +509,10 @@ def run_learned_workload(args):
                         "acceptance_untrained": acc_untrained, "acceptance_trained": acc_trained,
                         "train_rows": rows, "harvest_s": harvest_s, "train_s": train_s, "train_steps": 2000,
                         "loss_first": float(trace[:20].mean()), "loss_last": float(trace[-20:].mean())},
-            "reference_sweeps": args.ref_sweeps, "statistic": "fraction of label 0 over 4096 fixed sites, per chain",
+            "kernels_learned_ms": kt_learned, "kernels_plain_ms": kt_plain,
+            "mlp_tflops": mlp_flop / (ms_mlp / 1e3) / 1e12 if ms_mlp == ms_mlp else None, "mlp_rows": R,
+            "reference_sweeps": args.ref_sweeps,
+            "statistics": "per chain: fraction of label 0 over 4096 fixed sites; pairwise energy of 50,000 fixed edges",
             "comparison": out}
 
 

@@ -168,6 +168,8 @@ enum { MRF_K_DUAL = 0, MRF_K_PRIMAL = 1, MRF_K_FUSED = 2, MRF_K_POTENTIAL = 3, M
  * launch counts launches[MRF_K_COUNT] of every sweep kernel since the last
  * call (CUDA events on the handle's stream); resets the totals.  Synchronises. */
 mrf_status mrf_kernel_times(mrf_t* h, double* ms, int64_t* launches);
+/* Switch options.kernel_timing on (1) or off (0) for later sweeps. */
+mrf_status mrf_set_kernel_timing(mrf_t* h, int32_t on);
 
 /* ---- Batches of uneven graphs (dynamic-network workloads) --------------------
  * Many independent graphs, each with its own size and label count, sampled

@@ -53,6 +53,10 @@ struct mrf {
     int64_t* d_csr_sums = nullptr;     // block sums of the device scan
     int64_t inc_cap = 0;               // capacity of d_inc (incidences)
     int64_t n_device_csr = 0, n_host_csr = 0;   // CSR builds after edits, by path
+    // edit staging (grow-only, so that an edit allocates nothing in steady state)
+    float* d_ed_pair = nullptr; int64_t ed_pair_cap = 0;
+    int64_t* d_ed_slots = nullptr; int64_t* d_ed_new = nullptr; int32_t* d_ed_s = nullptr; int32_t* d_ed_t = nullptr;
+    int64_t ed_cap = 0;
     // learned block proposal
     bool learned = false;
     LearnedArgs la{};
@@ -261,6 +265,12 @@ const char* mrf_status_string(mrf_status s) {
 
 const char* mrf_last_error(const mrf_t* h) { return h ? h->err.c_str() : "null handle"; }
 
+mrf_status mrf_set_kernel_timing(mrf_t* h, int32_t on) {
+    if (!h) return MRF_EINVAL;
+    h->opt.kernel_timing = on ? 1 : 0;
+    return MRF_OK;
+}
+
 mrf_status mrf_kernel_times(mrf_t* h, double* ms, int64_t* launches) {
     if (!h || !ms || !launches) return MRF_EINVAL;
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -319,6 +329,7 @@ void mrf_destroy(mrf_t* h) {
     dfree(h->d_fold); dfree(h->d_cst); dfree(h->d_resid); dfree(h->d_inc_ptr); dfree(h->d_inc); dfree(h->d_x);
     dfree(h->d_theta); dfree(h->d_counts); dfree(h->d_logp); dfree(h->d_ctl); dfree(h->d_flag); dfree(h->d_stage); dfree(h->d_pot);
     dfree(h->d_csr_work); dfree(h->d_csr_sums);
+    dfree(h->d_ed_pair); dfree(h->d_ed_slots); dfree(h->d_ed_new); dfree(h->d_ed_s); dfree(h->d_ed_t);
     dfree(h->d_members); dfree(h->d_nmem); dfree(h->d_intra_ptr); dfree(h->d_intra); dfree(h->d_cf); dfree(h->d_skip);
     dfree(h->d_X); dfree(h->d_H1); dfree(h->d_H2); dfree(h->d_Z); dfree(h->d_w32); dfree(h->d_Wb); dfree(h->d_grad);
     dfree(h->d_m); dfree(h->d_v); dfree(h->d_train); dfree(h->d_bidx); dfree(h->d_bX); dfree(h->d_by); dfree(h->d_bn);
@@ -427,9 +438,12 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
         if (as[i] < 0 || as[i] >= N || at[i] < 0 || at[i] >= N) return fail(h, MRF_ERANGE, "edit: vertex id out of range");
         if (as[i] == at[i]) return fail(h, MRF_ERANGE, "edit: self-loop");
     }
-    float* d_pair = nullptr;
-    MRF_CUDA(h, dalloc(d_pair, (size_t)n_add * L * L));
-    struct Guard { float*& p; ~Guard() { dfree(p); } } guard{d_pair};
+    if (n_add * L * L > h->ed_pair_cap) {
+        const int64_t cap = std::max<int64_t>(n_add * L * L, h->ed_pair_cap * 2);
+        MRF_CUDA(h, dalloc(h->d_ed_pair, (size_t)cap));
+        h->ed_pair_cap = cap;
+    }
+    float* d_pair = h->d_ed_pair;
     MRF_CUDA(h, to_device(d_pair, pair_log, n_add * L * L, ptr_kind, h->stream));
     mrf_status st = check_finite_device(h, d_pair, n_add * L * L, "pair_log");
     if (st != MRF_OK) return st;
@@ -487,13 +501,16 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
     std::vector<int32_t> upd_s(upd_slot.size()), upd_t(upd_slot.size());
     for (size_t i = 0; i < upd_slot.size(); ++i) { upd_s[i] = h->h_src[upd_slot[i]]; upd_t[i] = h->h_dst[upd_slot[i]]; }
     const int64_t n_upd = (int64_t)upd_slot.size();
-    int64_t* d_slots = nullptr;
-    int64_t* d_new = nullptr;
-    int32_t* d_us = nullptr;
-    int32_t* d_ut2 = nullptr;
-    MRF_CUDA(h, dalloc(d_slots, (size_t)n_upd)); MRF_CUDA(h, dalloc(d_us, (size_t)n_upd)); MRF_CUDA(h, dalloc(d_ut2, (size_t)n_upd));
-    MRF_CUDA(h, dalloc(d_new, (size_t)n_add));
-    struct Guard2 { int64_t*& p; int32_t*& q; int32_t*& r; int64_t*& n; ~Guard2() { dfree(p); dfree(q); dfree(r); dfree(n); } } guard2{d_slots, d_us, d_ut2, d_new};
+    if (n_upd > h->ed_cap || n_add > h->ed_cap) {
+        const int64_t cap = std::max<int64_t>(std::max(n_upd, n_add), h->ed_cap * 2);
+        MRF_CUDA(h, dalloc(h->d_ed_slots, (size_t)cap)); MRF_CUDA(h, dalloc(h->d_ed_new, (size_t)cap));
+        MRF_CUDA(h, dalloc(h->d_ed_s, (size_t)cap)); MRF_CUDA(h, dalloc(h->d_ed_t, (size_t)cap));
+        h->ed_cap = cap;
+    }
+    int64_t* d_slots = h->d_ed_slots;
+    int64_t* d_new = h->d_ed_new;
+    int32_t* d_us = h->d_ed_s;
+    int32_t* d_ut2 = h->d_ed_t;
     MRF_CUDA(h, to_device(d_slots, upd_slot.data(), n_upd, MRF_PTR_HOST, h->stream));
     MRF_CUDA(h, to_device(d_new, slots.data(), n_add, MRF_PTR_HOST, h->stream));
     MRF_CUDA(h, to_device(d_us, upd_s.data(), n_upd, MRF_PTR_HOST, h->stream));
@@ -529,7 +546,6 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
     if (too_long) { MRF_CUDA(h, build_csr(h)); h->n_host_csr++; } else h->n_device_csr++;
     MRF_CUDA(h, launch_fold_unary(h->d_unary, h->d_fold, h->d_inc_ptr, h->d_inc, N, L, h->d_ut, h->d_utf, h->stream));
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));
-    h->schedule = 0;
     std::copy(slots.begin(), slots.end(), out_new_ids);
     return MRF_OK;
 }

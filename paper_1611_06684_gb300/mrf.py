@@ -60,6 +60,7 @@ _SIGS = {
     "mrf_debug_logp": (ct.c_int, [_P, _P, ct.POINTER(ct.c_uint64)]),
     "mrf_debug_theta": (ct.c_int, [_P, _P]),
     "mrf_kernel_times": (ct.c_int, [_P, _P, _P]),
+    "mrf_set_kernel_timing": (ct.c_int, [_P, ct.c_int32]),
     "mrf_sweep_noalloc": (ct.c_int, [_P, _P, _P, ct.c_int64]),
     "mrf_learned_setup": (ct.c_int, [_P, _P, ct.c_int32, ct.c_uint64]),
     "mrf_learned_param_count": (ct.c_int64, [_P]),
@@ -315,6 +316,9 @@ class MRF:
         X = np.zeros((rows, width), np.float32); z = np.zeros((rows, n_out), np.float32)
         self._check(self.lib.mrf_learned_debug(self.h, X.ctypes.data, z.ctypes.data))
         return X, z
+
+    def set_kernel_timing(self, on: bool):
+        self._check(self.lib.mrf_set_kernel_timing(self.h, int(bool(on))))
 
     def kernel_times(self):
         """{kernel name: (total ms, launches)} since the previous call."""
