@@ -93,6 +93,7 @@ struct SweepArgs {
     float* logp;               // [C][N][L] or null
     Ctl* ctl;
     uint2 key;
+    RoundKeys rk;              // Philox round keys of `key`
     FastDiv fdC;               // division by the chain count
     int32_t grid_nx, grid_ny, grid_nz;
     // blocked sweep (lattice): tree edges of the sweep's comb forest get theta = 0

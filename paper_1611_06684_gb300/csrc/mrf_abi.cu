@@ -143,6 +143,7 @@ SweepArgs make_args(const mrf_t* h) {
     a.inc_ptr = h->d_inc_ptr; a.inc = h->d_inc; a.ut = h->d_ut;
     a.x = h->d_x; a.theta = h->d_theta; a.counts = h->d_counts; a.logp = h->d_logp;
     a.ctl = h->d_ctl; a.key = h->key;
+    a.rk = round_keys(h->key);
     a.fdC = FastDiv::make((uint32_t)h->C);
     const int nx = h->opt.grid_nx, ny = h->opt.grid_ny, nz = h->opt.grid_nz;
     if (nx > 0) {

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256, 4) k_dual_noalloc(SweepArgs a, const uint
     if (s >= 0) {
         const int t = a.dst[e];
         dual_bits<L, LAYOUT>(e, c, xin[(int64_t)s * a.C + c], xin[(int64_t)t * a.C + c],
-                             a.tpl + (int64_t)e * E::W * 32, a.thr + (int64_t)e * E::M, sweep, a.key, bits);
+                             a.tpl + (int64_t)e * E::W * 32, a.thr + (int64_t)e * E::M, sweep, a.rk, bits);
     } else {
 #pragma unroll
         for (int w = 0; w < E::W; ++w) bits[w] = 0;
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256, 4) k_primal_noalloc(SweepArgs a, uint8_t*
         if (flushed) two_sum_add(hi[x], lo[x], acc[x]);
         F[x] = flushed ? __ldg(uf + x) + (hi[x] + lo[x]) : __ldg(uf + x) + acc[x];
     }
-    xout[g] = (uint8_t)draw_label<L>(F, v, c, sweep, a.key, PH_PRIMAL, nullptr, a.ctl);
+    xout[g] = (uint8_t)draw_label<L>(F, v, c, sweep, a.rk, PH_PRIMAL, nullptr, a.ctl);
 }
 
 #define MRF_DISPATCH_L3(L_, ...)                                                  \

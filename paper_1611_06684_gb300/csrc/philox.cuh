@@ -42,6 +42,40 @@ __host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     return c;
 }
 
+// The ten round keys of a key (k + r * Weyl, r = 0..9), precomputed once on
+// the host and passed as kernel parameters, so a call executes no key updates.
+struct RoundKeys {
+    uint32_t k0[10], k1[10];
+};
+
+__host__ __device__ inline RoundKeys round_keys(uint2 k) {
+    RoundKeys rk{};
+    for (int r = 0; r < 10; ++r) {
+        rk.k0[r] = k.x + (uint32_t)r * 0x9E3779B9u;
+        rk.k1[r] = k.y + (uint32_t)r * 0xBB67AE85u;
+    }
+    return rk;
+}
+
+// Same function as philox4x32_10 with precomputed round keys; each product is
+// one 32x32 -> 64-bit multiply.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const RoundKeys& rk) {
+    constexpr uint32_t kMul0 = 0xD2511F53u, kMul1 = 0xCD9E8D57u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)kMul0 * c.x;
+        const uint64_t p1 = (uint64_t)kMul1 * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk.k0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ rk.k1[r],
+                       (uint32_t)p0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw_rk(uint32_t index, uint32_t sweep, uint32_t chain, uint32_t phase, uint32_t sub,
+                                         const RoundKeys& rk) {
+    return philox4x32_10_rk(make_uint4(index, sweep, chain, (phase << 24) | sub), rk);
+}
+
 __host__ __device__ __forceinline__ uint2 seed_key(uint64_t seed) {
     return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
 }
@@ -57,8 +91,8 @@ __device__ __forceinline__ uint32_t word_of(const uint4& r, int w) {
 
 // Low 16 bits of the uniform of dual entry k (drawn only when the prefix byte
 // ties with the threshold's prefix).
-__device__ __forceinline__ uint32_t dual_low16(uint32_t e, uint32_t sweep, uint32_t c, int k, uint2 key) {
-    const uint4 r = draw(e, sweep, c, PH_DUAL_LO, (uint32_t)k >> 3, key);
+__device__ __forceinline__ uint32_t dual_low16(uint32_t e, uint32_t sweep, uint32_t c, int k, const RoundKeys& rk) {
+    const uint4 r = draw_rk(e, sweep, c, PH_DUAL_LO, (uint32_t)k >> 3, rk);
     const uint32_t w = word_of(r, (k & 7) >> 1);
     return (w >> (16 * (k & 1))) & 0xFFFFu;
 }

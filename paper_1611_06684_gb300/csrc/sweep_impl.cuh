@@ -114,14 +114,14 @@ __device__ __forceinline__ bool is_tree_edge(const SweepArgs& a, uint32_t e) {
 // exact 24-bit threshold.
 template <int L, int LAYOUT>
 __device__ __forceinline__ void dual_bits(uint32_t e, uint32_t c, int xs, int xt, const uint32_t* __restrict__ tpl_e,
-                                          const uint32_t* __restrict__ thr_e, uint32_t sweep, uint2 key,
+                                          const uint32_t* __restrict__ thr_e, uint32_t sweep, const RoundKeys& key,
                                           uint32_t (&bits)[Ent<L, LAYOUT>::W]) {
     using E = Ent<L, LAYOUT>;
     uint32_t ties[E::W];
 #pragma unroll
     for (int g = 0; g < E::W; ++g) {
-        const uint4 r0 = draw(e, sweep, c, PH_DUAL, 2u * g, key);
-        const uint4 r1 = draw(e, sweep, c, PH_DUAL, 2u * g + 1u, key);
+        const uint4 r0 = draw_rk(e, sweep, c, PH_DUAL, 2u * g, key);
+        const uint4 r1 = draw_rk(e, sweep, c, PH_DUAL, 2u * g + 1u, key);
         const uint32_t R[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
         const uint32_t rm = row_mask<L, LAYOUT>(xs, g), cm = col_mask<L, LAYOUT>(xt, g), km = rm & cm;
         const uint4* tp = reinterpret_cast<const uint4*>(tpl_e + g * 32);
@@ -159,8 +159,8 @@ __device__ __forceinline__ void dual_bits(uint32_t e, uint32_t c, int xs, int xt
 // Philox phase `phase` (u is exact in float32); optionally record log p.
 // Counts draws within 1e-6 of a CDF boundary.
 template <int L>
-__device__ __forceinline__ int draw_label(const float (&F)[L], uint32_t v, uint32_t c, uint32_t sweep, uint2 key,
-                                          uint32_t phase, float* __restrict__ logp_out, Ctl* ctl) {
+__device__ __forceinline__ int draw_label(const float (&F)[L], uint32_t v, uint32_t c, uint32_t sweep,
+                                          const RoundKeys& key, uint32_t phase, float* __restrict__ logp_out, Ctl* ctl) {
     float mx = F[0];
 #pragma unroll
     for (int a = 1; a < L; ++a) mx = fmaxf(mx, F[a]);
@@ -177,7 +177,7 @@ __device__ __forceinline__ int draw_label(const float (&F)[L], uint32_t v, uint3
 #pragma unroll
         for (int a = 0; a < L; ++a) logp_out[a] = (F[a] - mx) - ls;
     }
-    const uint32_t U = draw(v, sweep, c, phase, 0, key).x >> 9;
+    const uint32_t U = draw_rk(v, sweep, c, phase, 0, key).x >> 9;
     const float u = ((float)U + 0.5f) * (1.0f / 8388608.0f);
     float cdf = 0.0f;
     int lab = -1, last_pos = 0;
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(256, 4) k_dual(SweepArgs a) {
     if (s >= 0 && !(a.splash && is_tree_edge(a, e)) && !(a.skip && a.skip[e])) {
         const int t = a.dst[e];
         dual_bits<L, LAYOUT>(e, c, xin[(int64_t)s * a.C + c], xin[(int64_t)t * a.C + c],
-                             a.tpl + (int64_t)e * E::W * 32, a.thr + (int64_t)e * E::M, sweep, a.key, bits);
+                             a.tpl + (int64_t)e * E::W * 32, a.thr + (int64_t)e * E::M, sweep, a.rk, bits);
     } else {
 #pragma unroll
         for (int w = 0; w < E::W; ++w) bits[w] = 0;
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(256, FUSED ? 2 : 4) k_primal(SweepArgs a) {
                 const int side = ic[u].x & 1;
                 const int xn = xin[(int64_t)ic[u].y * a.C + c];
                 dual_bits<L, LAYOUT>((uint32_t)e, c, side == 0 ? xv : xn, side == 0 ? xn : xv, a.tpl + e * E::W * 32,
-                                     a.thr + e * E::M, sweep, a.key, bits[u]);
+                                     a.thr + e * E::M, sweep, a.rk, bits[u]);
             } else {
                 const uint32_t* th = a.theta + (e * a.C + c) * E::W;
                 if (E::W % 2 == 0) {
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(256, FUSED ? 2 : 4) k_primal(SweepArgs a) {
         return;
     }
     float* lp = a.logp ? a.logp + ((int64_t)c * a.N + v) * L : nullptr;
-    xout[g] = (uint8_t)draw_label<L>(F, v, c, sweep, a.key, PH_PRIMAL, lp, a.ctl);
+    xout[g] = (uint8_t)draw_label<L>(F, v, c, sweep, a.rk, PH_PRIMAL, lp, a.ctl);
 }
 
 // CTA-per-site schedule of the plain primal step for high-degree sites: a CTA
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(256) k_primal_cta(SweepArgs a, int CG) {
         for (int x = 0; x < L; ++x) F[x] = __ldg(uf + x) + (hi[x] + lo[x]);
         uint8_t* xout = a.x + (size_t)((sweep + 1) & 1) * a.N * a.C;
         float* lp = a.logp ? a.logp + ((int64_t)c * a.N + v) * L : nullptr;
-        xout[(int64_t)v * a.C + c] = (uint8_t)draw_label<L>(F, v, (uint32_t)c, sweep, a.key, PH_PRIMAL, lp, a.ctl);
+        xout[(int64_t)v * a.C + c] = (uint8_t)draw_label<L>(F, v, (uint32_t)c, sweep, a.rk, PH_PRIMAL, lp, a.ctl);
     }
 }
 
