@@ -124,6 +124,25 @@ def kernel_work(name, model_info, C):
     return 0, 0
 
 
+def rank_seed(seed: int, rank: int) -> int:
+    """Independent chains per rank: the draw key of rank r is seed + 1000003 r."""
+    return seed + 1000003 * rank
+
+
+def aggregate(ms_local: float, units_local: int, ws: int, device=None):
+    """Whole-job throughput over ranks: the slowest rank's time and the sum of
+    all ranks' units (replicas; the only collective is this timing reduction)."""
+    if ws == 1:
+        return ms_local, units_local / (ms_local / 1e3)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_local, float(units_local)], dtype=torch.float64, device=device)
+    mx = t[:1].clone(); tot = t[1:].clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    return float(mx.item()), float(tot.item()) / (float(mx.item()) / 1e3)
+
+
 def run_ours(args, ws, rank, local):
     import torch
     torch.cuda.set_device(local)
@@ -147,7 +166,7 @@ def run_ours(args, ws, rank, local):
     mode = {"plain": M.MODE_PLAIN, "fused": M.MODE_FUSED}[args.mode]
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
-        h = M.MRF(model.n_vars, model.n_labels, C, seed=args.seed + 1000003 * rank, stream=stream.cuda_stream,
+        h = M.MRF(model.n_vars, model.n_labels, C, seed=rank_seed(args.seed, rank), stream=stream.cuda_stream,
                   kernel_timing=True, grid=model.grid if model.grid else None)
         h.set_factors(model.unary, model.src, model.dst, model.pair)
     inf = h.info()
@@ -172,13 +191,8 @@ def run_ours(args, ws, rank, local):
     ms_total = ev0.elapsed_time(ev1)
     clocks = clocks_stop(clk, clk_path, local)
     ktimes = h.kernel_times()
-    if ws > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total, value = aggregate(ms_total, C * model.n_vars * args.steps, ws, dev)
     ms_step = ms_total / args.steps
-    units = ws * C * model.n_vars * args.steps
-    value = units / (ms_total / 1e3)
     launches = sum(n for _, n in ktimes.values()) + args.steps   # + k_advance per sweep
 
     # roofline of the dominant kernel (device time inside the timed region)
