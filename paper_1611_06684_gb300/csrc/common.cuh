@@ -110,6 +110,7 @@ constexpr int kLearnPairs = kLearnBlock * (kLearnBlock - 1) / 2;  // pair-coupli
 
 struct LearnedArgs {
     int32_t nb, L, Dp, H, O;            // blocks, labels, padded feature width, hidden, 16*L
+    int32_t Kx, C;                      // width of the per-chain feature part (16 L padded to 32), chains
     const int32_t* members;             // [nb][16] site ids (sorted, -1 padding)
     const int32_t* nmem;                // [nb]
     const int64_t* intra_ptr;           // [nb+1]
@@ -123,6 +124,9 @@ struct LearnedArgs {
     float* w32;                         // flat float32 parameters W1,b1,W2,b2,W3,b3
     const float* b1; const float* b2; const float* b3;
     __nv_bfloat16* W1b; __nv_bfloat16* W2b; __nv_bfloat16* W3b;
+    __nv_bfloat16* W1xb;                // [H][Kx] first 16 L columns of W1 (zero padded)
+    __nv_bfloat16* cfb;                 // [nb][120] pair couplings rounded to bf16
+    float* rowbias;                     // [nb][H] b1 + cf_b W1[:, 16L:16L+120]^T (per block)
     float* grad; float* adam_m; float* adam_v;
     float* t_h1; float* t_h2; float* t_z; float* t_dz; float* t_d2; float* t_d1;   // training scratch
     __nv_bfloat16* ds_X; uint8_t* ds_y; uint8_t* ds_n;                               // dataset
@@ -154,6 +158,8 @@ cudaError_t learned_forward_backward(const LearnedArgs& a, int R, const __nv_bfl
                                      const uint8_t* nm, double* loss, cudaStream_t s);
 cudaError_t learned_adam(const LearnedArgs& a, int64_t n_params, float lr, int step, cudaStream_t s);
 cudaError_t learned_sync_bf16(const LearnedArgs& a, cudaStream_t s);
+cudaError_t learned_rowbias(const LearnedArgs& a, cudaStream_t s);
+cudaError_t launch_learned_mlp_blocks(const LearnedArgs& a, cudaStream_t st);
 cudaError_t learned_gather(const LearnedArgs& a, const int32_t* idx, int R, __nv_bfloat16* X, uint8_t* y, uint8_t* nm,
                            cudaStream_t s);
 cudaError_t launch_to_bf16(const float* src, __nv_bfloat16* dst, int64_t n, cudaStream_t s);

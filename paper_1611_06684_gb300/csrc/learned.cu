@@ -22,36 +22,46 @@ using bf16 = __nv_bfloat16;
 
 // ============================================================================ features
 
+// Per-chain features: centred potentials of the members, Kx columns (the
+// block's pair couplings enter the first layer as a per-block bias instead).
 __global__ void k_learned_features(const LearnedArgs a, FastDiv fdC, const float* __restrict__ pot, int C) {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= (uint64_t)a.nb * C) return;
     const uint32_t b = fdC.div(r), c = r - b * (uint32_t)C;
     const int L = a.L, n = a.nmem[b];
-    bf16* x = a.X + (int64_t)r * a.Dp;
-    int col = 0;
+    uint4* x = reinterpret_cast<uint4*>(a.X + (int64_t)r * a.Kx);
+    uint32_t pk[4];
+    int fill = 0, q16 = 0;
+    auto push = [&](float v0, float v1) {
+        __nv_bfloat162 t = __floats2bfloat162_rn(v0, v1);
+        pk[fill++] = *reinterpret_cast<uint32_t*>(&t);
+        if (fill == 4) { x[q16++] = make_uint4(pk[0], pk[1], pk[2], pk[3]); fill = 0; }
+    };
+    float pend = 0.0f;
+    bool have = false;
     for (int i = 0; i < kLearnBlock; ++i) {
+        float phi[kMaxLabels];
+        float mean = 0.0f;
         if (i < n) {
             const int v = a.members[b * kLearnBlock + i];
-            float phi[kMaxLabels];
-            float mean = 0.0f;
-            for (int q = 0; q < L; ++q) {
-                phi[q] = pot[((int64_t)v * L + q) * C + c];
-                mean += phi[q];
-            }
+            for (int q = 0; q < L; ++q) { phi[q] = pot[((int64_t)v * L + q) * C + c]; mean += phi[q]; }
             mean /= (float)L;
-            for (int q = 0; q < L; ++q) x[col++] = __float2bfloat16_rn(phi[q] - mean);
         } else {
-            for (int q = 0; q < L; ++q) x[col++] = __float2bfloat16_rn(0.0f);
+            for (int q = 0; q < L; ++q) phi[q] = 0.0f;
+        }
+        for (int q = 0; q < L; ++q) {
+            const float val = phi[q] - mean;
+            if (have) { push(pend, val); have = false; } else { pend = val; have = true; }
         }
     }
-    const float* cf = a.cf + (int64_t)b * kLearnPairs;
-    for (int p = 0; p < kLearnPairs; ++p) x[col++] = __float2bfloat16_rn(cf[p]);
-    for (; col < a.Dp; ++col) x[col] = __float2bfloat16_rn(0.0f);
+    for (int col = kLearnBlock * L; col < a.Kx; ++col) {
+        if (have) { push(pend, 0.0f); have = false; } else { pend = 0.0f; have = true; }
+    }
 }
 
 // Pair couplings kappa_e = mean_a psi(a,a) - mean_{a != b} psi(a,b) of every
 // intra-block edge (psi = w - folds has the same kappa as w), summed per pair.
-__global__ void k_learned_couplings(const LearnedArgs a, const float* __restrict__ resid, float* cf) {
+__global__ void k_learned_couplings(LearnedArgs a, const float* __restrict__ resid, float* cf) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= a.nb) return;
     const int L = a.L;
@@ -69,6 +79,7 @@ __global__ void k_learned_couplings(const LearnedArgs a, const float* __restrict
         const int i = min(ie.y, ie.z), j = max(ie.y, ie.z);
         cf[(int64_t)b * kLearnPairs + i * (2 * kLearnBlock - i - 1) / 2 + (j - i - 1)] += kappa;
     }
+    for (int p = 0; p < kLearnPairs; ++p) a.cfb[(int64_t)b * kLearnPairs + p] = __float2bfloat16_rn(cf[(int64_t)b * kLearnPairs + p]);
 }
 
 // ============================================================================ tensor-core GEMM
@@ -104,7 +115,7 @@ constexpr int kBM = 128, kBN = 64, kBK = 32, kPad = 8;
 template <bool RELU, bool OUT_BF16>
 __global__ void __launch_bounds__(256) k_gemm_nt(const bf16* __restrict__ A, const bf16* __restrict__ W,
                                                  const float* __restrict__ bias, void* __restrict__ Cout, int M, int N,
-                                                 int K) {
+                                                 int K, const float* __restrict__ rowbias, FastDiv rows_per_bias) {
     __shared__ __align__(16) bf16 As[2][kBM][kBK + kPad];
     __shared__ __align__(16) bf16 Bs[2][kBN][kBK + kPad];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -179,11 +190,15 @@ __global__ void __launch_bounds__(256) k_gemm_nt(const bf16* __restrict__ A, con
         for (int j = 0; j < 4; ++j) {
             const int col = n0 + wn * 32 + j * 8 + 2 * t;
             if (col >= N) continue;
-            const float b0 = bias ? bias[col] : 0.0f, b1 = bias ? bias[col + 1] : 0.0f;
+            float b0 = bias ? bias[col] : 0.0f, b1 = bias ? bias[col + 1] : 0.0f;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int64_t row = m0 + wm * 32 + i * 16 + g + h * 8;
                 if (row >= M) continue;
+                if (rowbias) {
+                    const float* rb = rowbias + (int64_t)rows_per_bias.div((uint32_t)row) * N;
+                    b0 = rb[col]; b1 = rb[col + 1];
+                }
                 float v0 = acc[i][j][2 * h] + b0, v1 = acc[i][j][2 * h + 1] + b1;
                 if (RELU) { v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); }
                 if (OUT_BF16) {
@@ -197,14 +212,15 @@ __global__ void __launch_bounds__(256) k_gemm_nt(const bf16* __restrict__ A, con
 }
 
 cudaError_t launch_gemm_nt(const bf16* A, const bf16* W, const float* bias, void* C, int M, int N, int K, bool relu,
-                           bool out_bf16, cudaStream_t s) {
+                           bool out_bf16, cudaStream_t s, const float* rowbias = nullptr, int rows_per_bias = 1) {
     if (M <= 0) return cudaSuccess;
     if (K % kBK || N % 2) return cudaErrorInvalidValue;
     dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((N + kBN - 1) / kBN));
-    if (relu && out_bf16) k_gemm_nt<true, true><<<grid, 256, 0, s>>>(A, W, bias, C, M, N, K);
-    else if (relu) k_gemm_nt<true, false><<<grid, 256, 0, s>>>(A, W, bias, C, M, N, K);
-    else if (out_bf16) k_gemm_nt<false, true><<<grid, 256, 0, s>>>(A, W, bias, C, M, N, K);
-    else k_gemm_nt<false, false><<<grid, 256, 0, s>>>(A, W, bias, C, M, N, K);
+    const FastDiv rpb = FastDiv::make((uint32_t)rows_per_bias);
+    if (relu && out_bf16) k_gemm_nt<true, true><<<grid, 256, 0, s>>>(A, W, bias, C, M, N, K, rowbias, rpb);
+    else if (relu) k_gemm_nt<true, false><<<grid, 256, 0, s>>>(A, W, bias, C, M, N, K, rowbias, rpb);
+    else if (out_bf16) k_gemm_nt<false, true><<<grid, 256, 0, s>>>(A, W, bias, C, M, N, K, rowbias, rpb);
+    else k_gemm_nt<false, false><<<grid, 256, 0, s>>>(A, W, bias, C, M, N, K, rowbias, rpb);
     return cudaGetLastError();
 }
 
@@ -396,7 +412,14 @@ __global__ void k_learned_harvest(const LearnedArgs a, SweepArgs s, int stride, 
     if (slot >= cap) return;
     const uint32_t b = s.fdC.div(r), c = r - b * (uint32_t)C;
     const uint8_t* xcur = s.x + (size_t)(((uint32_t)s.ctl->sweep) & 1) * s.N * C;
-    for (int q = 0; q < a.Dp; ++q) a.ds_X[slot * a.Dp + q] = a.X[(int64_t)r * a.Dp + q];
+    // full feature row: per-chain part from X, the block's couplings, zero padding
+    const int fx = kLearnBlock * a.L;
+    for (int q = 0; q < a.Dp; ++q) {
+        bf16 v = __float2bfloat16_rn(0.0f);
+        if (q < fx) v = a.X[(int64_t)r * a.Kx + q];
+        else if (q < fx + kLearnPairs) v = a.cfb[(int64_t)b * kLearnPairs + (q - fx)];
+        a.ds_X[slot * a.Dp + q] = v;
+    }
     const int n = a.nmem[b];
     for (int i = 0; i < kLearnBlock; ++i)
         a.ds_y[slot * kLearnBlock + i] = i < n ? xcur[(int64_t)a.members[b * kLearnBlock + i] * C + c] : 0;
@@ -430,6 +453,32 @@ cudaError_t launch_learned_mlp(const LearnedArgs& a, int64_t rows, const bf16* X
     cudaError_t e = launch_gemm_nt(X, a.W1b, a.b1, a.H1, (int)rows, a.H, a.Dp, true, true, st);
     if (e == cudaSuccess) e = launch_gemm_nt(a.H1, a.W2b, a.b2, a.H2, (int)rows, a.H, a.H, true, true, st);
     if (e == cudaSuccess) e = launch_gemm_nt(a.H2, a.W3b, a.b3, a.Zm, (int)rows, a.O, a.H, false, false, st);
+    return e;
+}
+
+// Sweep path: layer 1 on the per-chain features only (K = Kx) with the
+// per-block bias b1 + cf_b W1_cf^T, then layers 2 and 3.
+cudaError_t launch_learned_mlp_blocks(const LearnedArgs& a, cudaStream_t st) {
+    const int rows = a.nb * a.C;
+    cudaError_t e = launch_gemm_nt(a.X, a.W1xb, nullptr, a.H1, rows, a.H, a.Kx, true, true, st, a.rowbias, a.C);
+    if (e == cudaSuccess) e = launch_gemm_nt(a.H1, a.W2b, a.b2, a.H2, rows, a.H, a.H, true, true, st);
+    if (e == cudaSuccess) e = launch_gemm_nt(a.H2, a.W3b, a.b3, a.Zm, rows, a.O, a.H, false, false, st);
+    return e;
+}
+
+__global__ void k_copy_cols_bf16(const bf16* __restrict__ src, int64_t src_ld, int cols, bf16* __restrict__ dst,
+                                 int dst_ld, int rows) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)rows * dst_ld) return;
+    const int64_t r = i / dst_ld;
+    const int c = (int)(i % dst_ld);
+    dst[i] = c < cols ? src[r * src_ld + c] : __float2bfloat16_rn(0.0f);
+}
+
+// rowbias[b][h] = b1[h] + sum_p bf16(cf[b][p]) W1b[h][16L + p]   (float32)
+cudaError_t learned_rowbias(const LearnedArgs& a, cudaStream_t s) {
+    cudaError_t e = gemm_f32(a.nb, a.H, kLearnPairs, (const bf16*)a.cfb, kLearnPairs, 1,
+                             (const bf16*)(a.W1b + kLearnBlock * a.L), 1, a.Dp, a.rowbias, a.H, a.b1, false, s);
     return e;
 }
 
@@ -495,6 +544,10 @@ cudaError_t learned_sync_bf16(const LearnedArgs& a, cudaStream_t s) {
     k_to_bf16<<<(unsigned)((n1 + 255) / 256), 256, 0, s>>>(w1, a.W1b, n1);
     k_to_bf16<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(w2, a.W2b, n2);
     k_to_bf16<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(w3, a.W3b, n3);
+    if (a.W1xb) {
+        const int64_t nx = (int64_t)a.H * a.Kx;
+        k_copy_cols_bf16<<<(unsigned)((nx + 255) / 256), 256, 0, s>>>(a.W1b, a.Dp, kLearnBlock * a.L, a.W1xb, a.Kx, a.H);
+    }
     return cudaGetLastError();
 }
 

@@ -70,6 +70,8 @@ struct mrf {
     __nv_bfloat16* d_dsX = nullptr; uint8_t* d_dsy = nullptr; uint8_t* d_dsn = nullptr;
     int64_t ds_cap = 0, ds_rows = 0;
     double* d_loss = nullptr; int64_t loss_cap = 0;
+    __nv_bfloat16* d_W1x = nullptr; __nv_bfloat16* d_cfb = nullptr; float* d_rowbias = nullptr;
+    bool rowbias_dirty = true;
     unsigned long long* d_acc = nullptr;
     uint64_t proposed = 0;
     int adam_step = 0;
@@ -335,6 +337,7 @@ void mrf_destroy(mrf_t* h) {
     dfree(h->d_X); dfree(h->d_H1); dfree(h->d_H2); dfree(h->d_Z); dfree(h->d_w32); dfree(h->d_Wb); dfree(h->d_grad);
     dfree(h->d_m); dfree(h->d_v); dfree(h->d_train); dfree(h->d_bidx); dfree(h->d_bX); dfree(h->d_by); dfree(h->d_bn);
     dfree(h->d_dsX); dfree(h->d_dsy); dfree(h->d_dsn); dfree(h->d_loss); dfree(h->d_acc);
+    dfree(h->d_W1x); dfree(h->d_cfb); dfree(h->d_rowbias);
     for (auto& r : h->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : h->pool) cudaEventDestroy(e);
     delete h;
@@ -594,7 +597,7 @@ static mrf_status enqueue_sweep(mrf_t* h, int mode) {
         e = timed(h, MRF_K_DUAL, [&] { return launch_dual(a, h->layout, s); });
         if (e == cudaSuccess) e = timed(h, MRF_K_POTENTIAL, [&] { return launch_potential(a, h->layout, s); });
         if (e == cudaSuccess) e = timed(h, MRF_K_FEATURES, [&] { return launch_learned_features(h->la, a, s); });
-        if (e == cudaSuccess) e = timed(h, MRF_K_MLP, [&] { return launch_learned_mlp(h->la, (int64_t)h->la.nb * h->C, h->la.X, s); });
+        if (e == cudaSuccess) e = timed(h, MRF_K_MLP, [&] { return launch_learned_mlp_blocks(h->la, s); });
         if (e == cudaSuccess) e = timed(h, MRF_K_MH, [&] { return launch_learned_mh(h->la, a, s); });
     } else {
         a.splash = 1;
@@ -614,6 +617,10 @@ mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode) {
     if (!h->has_factors) return fail(h, MRF_ESTATE, "mrf_set_factors first");
     if (n_sweeps < 0 || mode < MRF_MODE_PLAIN || mode > MRF_MODE_LEARNED) return fail(h, MRF_EINVAL, "bad sweep count or mode");
     if (mode == MRF_MODE_LEARNED && !h->learned) return fail(h, MRF_ESTATE, "learned mode needs mrf_learned_setup");
+    if (mode == MRF_MODE_LEARNED && h->rowbias_dirty) {      // per-block first-layer bias of the current weights
+        MRF_CUDA(h, learned_rowbias(h->la, h->stream));
+        h->rowbias_dirty = false;
+    }
     if (mode == MRF_MODE_SPLASH && h->opt.grid_nx <= 0) return fail(h, MRF_ESTATE, "splash mode needs options.grid");
     if (mode == MRF_MODE_SPLASH && !h->d_pot) {
         drop_graphs(h);
@@ -1138,13 +1145,17 @@ mrf_status mrf_learned_setup(mrf_t* h, const int32_t* block_of_site, int32_t hid
     a = LearnedArgs{};
     a.nb = nb; a.L = L; a.H = hidden; a.O = kLearnBlock * L;
     a.Dp = (kLearnBlock * L + kLearnPairs + 31) / 32 * 32;
+    a.Kx = (kLearnBlock * L + 31) / 32 * 32;
+    a.C = C;
     const int64_t H = hidden, Dp = a.Dp, O = a.O;
     h->n_params = H * Dp + H + H * H + H + O * H + O;
     const int64_t R = (int64_t)nb * C;
     MRF_CUDA(h, dalloc(h->d_members, members.size())); MRF_CUDA(h, dalloc(h->d_nmem, (size_t)nb));
     MRF_CUDA(h, dalloc(h->d_intra_ptr, (size_t)nb + 1)); MRF_CUDA(h, dalloc(h->d_intra, std::max<size_t>(intra.size(), 1)));
     MRF_CUDA(h, dalloc(h->d_cf, (size_t)nb * kLearnPairs)); MRF_CUDA(h, dalloc(h->d_skip, (size_t)h->E_slots));
-    MRF_CUDA(h, dalloc(h->d_X, (size_t)R * Dp)); MRF_CUDA(h, dalloc(h->d_H1, (size_t)R * H));
+    MRF_CUDA(h, dalloc(h->d_X, (size_t)R * a.Kx)); MRF_CUDA(h, dalloc(h->d_H1, (size_t)R * H));
+    MRF_CUDA(h, dalloc(h->d_W1x, (size_t)H * a.Kx)); MRF_CUDA(h, dalloc(h->d_cfb, (size_t)nb * kLearnPairs));
+    MRF_CUDA(h, dalloc(h->d_rowbias, (size_t)nb * H));
     MRF_CUDA(h, dalloc(h->d_H2, (size_t)R * H)); MRF_CUDA(h, dalloc(h->d_Z, (size_t)R * O));
     MRF_CUDA(h, dalloc(h->d_w32, (size_t)h->n_params)); MRF_CUDA(h, dalloc(h->d_grad, (size_t)h->n_params));
     MRF_CUDA(h, dalloc(h->d_m, (size_t)h->n_params)); MRF_CUDA(h, dalloc(h->d_v, (size_t)h->n_params));
@@ -1178,8 +1189,10 @@ mrf_status mrf_learned_setup(mrf_t* h, const int32_t* block_of_site, int32_t hid
     a.W1b = h->d_Wb; a.W2b = h->d_Wb + H * Dp; a.W3b = h->d_Wb + H * Dp + H * H;
     a.grad = h->d_grad; a.adam_m = h->d_m; a.adam_v = h->d_v; a.n_accepted = h->d_acc;
     a.ds_X = h->d_dsX; a.ds_y = h->d_dsy; a.ds_n = h->d_dsn;
+    a.W1xb = h->d_W1x; a.cfb = h->d_cfb; a.rowbias = h->d_rowbias;
     MRF_CUDA(h, learned_sync_bf16(a, h->stream));
     MRF_CUDA(h, launch_learned_couplings(a, h->d_resid, h->d_cf, h->stream));
+    h->rowbias_dirty = true;
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));
     drop_graphs(h);
     h->learned = true;
@@ -1194,6 +1207,7 @@ mrf_status mrf_learned_set_params(mrf_t* h, const float* params, int64_t n) {
     if (n != h->n_params) return fail(h, MRF_EINVAL, "parameter count " + std::to_string(n) + " != " + std::to_string(h->n_params));
     MRF_CUDA(h, to_device(h->d_w32, params, n, MRF_PTR_HOST, h->stream));
     MRF_CUDA(h, learned_sync_bf16(h->la, h->stream));
+    h->rowbias_dirty = true;
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));
     return MRF_OK;
 }
@@ -1259,7 +1273,7 @@ mrf_status mrf_learned_train(mrf_t* h, int32_t steps, int32_t batch, float lr, u
     std::vector<double> losses((size_t)steps);
     if (steps) MRF_CUDA(h, cudaMemcpyAsync(losses.data(), h->d_loss, sizeof(double) * steps, cudaMemcpyDeviceToHost, h->stream));
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));
-    drop_graphs(h);   // weights changed; captured learned sweeps read them through pointers, so this is only hygiene
+    h->rowbias_dirty = true;
     if (loss_trace) for (int s = 0; s < steps; ++s) loss_trace[s] = (float)losses[s];
     return MRF_OK;
 }
@@ -1294,11 +1308,13 @@ mrf_status mrf_learned_forward(mrf_t* h, const float* X, int32_t rows, float* z)
     if ((int64_t)rows > (int64_t)h->la.nb * h->C) return fail(h, MRF_ERANGE, "at most n_blocks x chains rows");
     const int64_t Dp = h->la.Dp;
     float* d_xf = nullptr;
+    __nv_bfloat16* d_xb = nullptr;
     MRF_CUDA(h, dalloc(d_xf, (size_t)rows * Dp));
-    struct G { float*& p; ~G() { dfree(p); } } guard{d_xf};
+    MRF_CUDA(h, dalloc(d_xb, (size_t)rows * Dp));
+    struct G { float*& p; __nv_bfloat16*& q; ~G() { dfree(p); dfree(q); } } guard{d_xf, d_xb};
     MRF_CUDA(h, to_device(d_xf, X, rows * Dp, MRF_PTR_HOST, h->stream));
-    MRF_CUDA(h, launch_to_bf16(d_xf, h->d_X, rows * Dp, h->stream));
-    MRF_CUDA(h, launch_learned_mlp(h->la, rows, h->d_X, h->stream));
+    MRF_CUDA(h, launch_to_bf16(d_xf, d_xb, rows * Dp, h->stream));
+    MRF_CUDA(h, launch_learned_mlp(h->la, rows, d_xb, h->stream));
     MRF_CUDA(h, cudaMemcpyAsync(z, h->d_Z, sizeof(float) * rows * h->la.O, cudaMemcpyDeviceToHost, h->stream));
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));
     return MRF_OK;
@@ -1320,10 +1336,20 @@ mrf_status mrf_learned_debug(mrf_t* h, float* X, float* z) {
     if (!h->learned) return fail(h, MRF_ESTATE, "mrf_learned_setup first");
     const int64_t R = (int64_t)h->la.nb * h->C;
     if (X) {
-        std::vector<__nv_bfloat16> xb((size_t)(R * h->la.Dp));
+        const int Kx = h->la.Kx, Dp = h->la.Dp, fx = kLearnBlock * h->L;
+        std::vector<__nv_bfloat16> xb((size_t)(R * Kx)), cb((size_t)h->la.nb * kLearnPairs);
         MRF_CUDA(h, cudaMemcpyAsync(xb.data(), h->d_X, sizeof(__nv_bfloat16) * xb.size(), cudaMemcpyDeviceToHost, h->stream));
+        MRF_CUDA(h, cudaMemcpyAsync(cb.data(), h->d_cfb, sizeof(__nv_bfloat16) * cb.size(), cudaMemcpyDeviceToHost, h->stream));
         MRF_CUDA(h, cudaStreamSynchronize(h->stream));
-        for (size_t i = 0; i < xb.size(); ++i) X[i] = __bfloat162float(xb[i]);
+        for (int64_t r = 0; r < R; ++r) {
+            const int64_t b = r / h->C;
+            for (int q = 0; q < Dp; ++q) {
+                float v = 0.0f;
+                if (q < fx) v = __bfloat162float(xb[r * Kx + q]);
+                else if (q < fx + kLearnPairs) v = __bfloat162float(cb[b * kLearnPairs + (q - fx)]);
+                X[r * Dp + q] = v;
+            }
+        }
     }
     if (z) {
         MRF_CUDA(h, cudaMemcpyAsync(z, h->d_Z, sizeof(float) * R * h->la.O, cudaMemcpyDeviceToHost, h->stream));
