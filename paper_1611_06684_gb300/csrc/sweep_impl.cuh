@@ -118,11 +118,28 @@ __device__ __forceinline__ void dual_bits(uint32_t e, uint32_t c, int xs, int xt
                                           uint32_t (&bits)[Ent<L, LAYOUT>::W]) {
     using E = Ent<L, LAYOUT>;
     uint32_t ties[E::W];
+    // up to four Philox calls (two groups) in flight together for ILP
+    constexpr int GA = E::W < 2 ? E::W : 2;
+    uint32_t R[GA][8];
 #pragma unroll
-    for (int g = 0; g < E::W; ++g) {
+    for (int g = 0; g < GA; ++g) {
         const uint4 r0 = draw_rk(e, sweep, c, PH_DUAL, 2u * g, key);
         const uint4 r1 = draw_rk(e, sweep, c, PH_DUAL, 2u * g + 1u, key);
-        const uint32_t R[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+        R[g][0] = r0.x; R[g][1] = r0.y; R[g][2] = r0.z; R[g][3] = r0.w;
+        R[g][4] = r1.x; R[g][5] = r1.y; R[g][6] = r1.z; R[g][7] = r1.w;
+    }
+#pragma unroll
+    for (int g = 0; g < E::W; ++g) {
+        uint32_t Rg[8];
+        if (g < GA) {
+#pragma unroll
+            for (int p = 0; p < 8; ++p) Rg[p] = R[g < GA ? g : 0][p];
+        } else {
+            const uint4 r0 = draw_rk(e, sweep, c, PH_DUAL, 2u * g, key);
+            const uint4 r1 = draw_rk(e, sweep, c, PH_DUAL, 2u * g + 1u, key);
+            Rg[0] = r0.x; Rg[1] = r0.y; Rg[2] = r0.z; Rg[3] = r0.w;
+            Rg[4] = r1.x; Rg[5] = r1.y; Rg[6] = r1.z; Rg[7] = r1.w;
+        }
         const uint32_t rm = row_mask<L, LAYOUT>(xs, g), cm = col_mask<L, LAYOUT>(xt, g), km = rm & cm;
         const uint4* tp = reinterpret_cast<const uint4*>(tpl_e + g * 32);
         uint32_t lt = 0u, eq = valid_word(E::M, g);
@@ -130,7 +147,7 @@ __device__ __forceinline__ void dual_bits(uint32_t e, uint32_t c, int xs, int xt
         for (int p = 0; p < 8; ++p) {
             const uint4 q = __ldg(tp + p);                 // {P00, D10, D01, D11} of plane p
             const uint32_t t = q.x ^ (q.y & rm) ^ (q.z & cm) ^ (q.w & km);
-            const uint32_t r = R[p];
+            const uint32_t r = Rg[p];
             lt |= eq & ~r & t;
             eq &= ~(r ^ t);
         }
