@@ -203,12 +203,18 @@ def run_ours(args, ws, rank, local):
     sm_mhz = clocks["sm_mhz"] if clocks else peaks.get("sm_max_mhz", 2070.0)
     hbm = {"bound": "hbm", "achieved": nbytes / (dom_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     hbm["frac"] = hbm["achieved"] / hbm["peak"]
+    try:
+        philox_measured = M.philox_rate(stream=stream.cuda_stream)
+    except Exception:
+        philox_measured = None
     if calls and dom in ("k_dual", "k_primal<fused>"):
         alu_peak = alu_peak_philox_calls(peaks.get("sm_max_mhz", 2070.0))
         roof = {"bound": "alu", "achieved": calls / (dom_ms / 1e3) / 1e9, "peak": alu_peak / 1e9,
                 "unit": "G Philox4x32-10 calls/s", "frac": calls / (dom_ms / 1e3) / alu_peak, "traffic": None,
                 "kernel": dom, "peak_source": "derived: 152 SMs x 64 int32 multiplies/clk x 2070 MHz / 40 per call",
-                "hbm_view": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac")}}
+                "hbm_view": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac")},
+                "philox_only_kernel": {"calls_per_s": philox_measured,
+                                       "frac": (calls / (dom_ms / 1e3) / philox_measured) if philox_measured else None}}
     else:
         roof = dict(hbm, traffic=None, kernel=dom, peak_source=f"MEASURED_PEAKS.json hbm_gbs ({peak_src})")
 

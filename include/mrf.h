@@ -168,6 +168,12 @@ enum { MRF_K_DUAL = 0, MRF_K_PRIMAL = 1, MRF_K_FUSED = 2, MRF_K_POTENTIAL = 3, M
  * launch counts launches[MRF_K_COUNT] of every sweep kernel since the last
  * call (CUDA events on the handle's stream); resets the totals.  Synchronises. */
 mrf_status mrf_kernel_times(mrf_t* h, double* ms, int64_t* launches);
+/* Throughput of the device's Philox4x32-10 (calls per second) measured by a
+ * kernel that does nothing else: `threads` threads x `calls` calls, timed with
+ * CUDA events on `cuda_stream` (0 = default stream).  A diagnostic for the
+ * integer-ALU roof of the dual step. */
+mrf_status mrf_philox_rate(uint64_t threads, int32_t calls, void* cuda_stream, double* calls_per_s);
+
 /* Switch options.kernel_timing on (1) or off (0) for later sweeps. */
 mrf_status mrf_set_kernel_timing(mrf_t* h, int32_t on);
 

@@ -139,6 +139,7 @@ cudaError_t launch_dual(const SweepArgs& a, int layout, cudaStream_t s);
 cudaError_t launch_primal(const SweepArgs& a, int layout, int schedule, cudaStream_t s);
 cudaError_t launch_fused(const SweepArgs& a, int layout, int schedule, cudaStream_t s);
 cudaError_t launch_accumulate(const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_philox_rate(uint64_t threads, int calls, uint32_t* sink, cudaStream_t s);
 cudaError_t launch_advance(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_splash(const SweepArgs& a, int layout, cudaStream_t s);
 cudaError_t launch_splash_offset(const SweepArgs& a, cudaStream_t s);

@@ -268,6 +268,26 @@ const char* mrf_status_string(mrf_status s) {
 
 const char* mrf_last_error(const mrf_t* h) { return h ? h->err.c_str() : "null handle"; }
 
+mrf_status mrf_philox_rate(uint64_t threads, int32_t calls, void* cuda_stream, double* calls_per_s) {
+    if (!threads || calls <= 0 || calls % 4 || !calls_per_s) return MRF_EINVAL;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    uint32_t* sink = nullptr;
+    if (cudaMalloc(&sink, 1024 * sizeof(uint32_t)) != cudaSuccess) { cudaGetLastError(); return MRF_ENOMEM; }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0); cudaEventCreate(&e1);
+    launch_philox_rate(threads, calls, sink, s);                 // warm
+    cudaEventRecord(e0, s);
+    launch_philox_rate(threads, calls, sink, s);
+    cudaEventRecord(e1, s);
+    cudaError_t err = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0); cudaEventDestroy(e1); cudaFree(sink);
+    if (err != cudaSuccess) { cudaGetLastError(); return MRF_ECUDA; }
+    *calls_per_s = (double)threads * calls / (ms / 1e3);
+    return MRF_OK;
+}
+
 mrf_status mrf_set_kernel_timing(mrf_t* h, int32_t on) {
     if (!h) return MRF_EINVAL;
     h->opt.kernel_timing = on ? 1 : 0;

@@ -116,6 +116,27 @@ cudaError_t launch_count_ge(const uint8_t* y, int64_t n, int L, unsigned long lo
     return cudaGetLastError();
 }
 
+// Philox4x32-10 throughput probe: every thread runs `calls` independent calls
+// (counters distinct across threads and calls, four in flight) and folds the
+// outputs into one word so that nothing is optimised away.
+__global__ void __launch_bounds__(256) k_philox_rate(RoundKeys rk, int calls, uint32_t* sink) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t acc = 0;
+    for (int i = 0; i < calls; i += 4) {
+        const uint4 a = draw_rk(g, (uint32_t)i, 0, PH_DUAL, 0, rk);
+        const uint4 b = draw_rk(g, (uint32_t)i + 1, 0, PH_DUAL, 0, rk);
+        const uint4 c = draw_rk(g, (uint32_t)i + 2, 0, PH_DUAL, 0, rk);
+        const uint4 d = draw_rk(g, (uint32_t)i + 3, 0, PH_DUAL, 0, rk);
+        acc ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w ^ c.x ^ c.y ^ c.z ^ c.w ^ d.x ^ d.y ^ d.z ^ d.w;
+    }
+    if (acc == 0x12345678u) sink[g & 1023] = acc;    // practically never; keeps the work live
+}
+
+cudaError_t launch_philox_rate(uint64_t threads, int calls, uint32_t* sink, cudaStream_t s) {
+    k_philox_rate<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(round_keys(make_uint2(1u, 2u)), calls, sink);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------- dispatch
 
 #define MRF_DISPATCH_L(L_, ...)                                                   \

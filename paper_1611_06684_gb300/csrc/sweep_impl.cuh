@@ -110,14 +110,15 @@ __device__ __forceinline__ bool is_tree_edge(const SweepArgs& a, uint32_t e) {
 // matching threshold plane for the chain's cases, most significant first:
 //   lt |= eq & ~r & t;  eq &= ~(r ^ t)
 // so lt = [prefix < threshold prefix] and eq = ties for all 32 entries at once.
-// Ties (probability 1/256 per entry) draw the low 16 bits and decide with the
-// exact 24-bit threshold.
+// Returns lt in bits and the ties in ties; a tie (probability 1/256 per entry)
+// is decided by the low 16 bits of its uniform against the exact 24-bit
+// threshold (resolve_tie).
 template <int L, int LAYOUT>
-__device__ __forceinline__ void dual_bits(uint32_t e, uint32_t c, int xs, int xt, const uint32_t* __restrict__ tpl_e,
-                                          const uint32_t* __restrict__ thr_e, uint32_t sweep, const RoundKeys& key,
-                                          uint32_t (&bits)[Ent<L, LAYOUT>::W]) {
+__device__ __forceinline__ void dual_prefix_bits(uint32_t e, uint32_t c, int xs, int xt,
+                                                 const uint32_t* __restrict__ tpl_e, uint32_t sweep,
+                                                 const RoundKeys& key, uint32_t (&bits)[Ent<L, LAYOUT>::W],
+                                                 uint32_t (&ties)[Ent<L, LAYOUT>::W]) {
     using E = Ent<L, LAYOUT>;
-    uint32_t ties[E::W];
     // up to four Philox calls (two groups) in flight together for ILP
     constexpr int GA = E::W < 2 ? E::W : 2;
     uint32_t R[GA][8];
@@ -154,6 +155,29 @@ __device__ __forceinline__ void dual_bits(uint32_t e, uint32_t c, int xs, int xt
         bits[g] = lt;
         ties[g] = eq;
     }
+}
+
+// Decision of a tie at entry k: low 16 bits of the uniform < the part of the
+// case threshold below its 8-bit prefix.
+template <int L, int LAYOUT>
+__device__ __forceinline__ bool resolve_tie(uint32_t e, uint32_t c, int xs, int xt, int k, uint32_t thr_word,
+                                            uint32_t sweep, const RoundKeys& key) {
+    const int ik = LAYOUT == MRF_LAYOUT_PIVOT ? 1 + k / (L - 1) : k;
+    const int jk = LAYOUT == MRF_LAYOUT_PIVOT ? 1 + k % (L - 1) : k;
+    const uint32_t t = case_threshold(thr_word, xs == ik, xt == jk);
+    const uint32_t rem = t - (threshold_prefix(t) << 16);      // in [0, 65536]
+    return rem && dual_low16(e, sweep, c, k, key) < rem;
+}
+
+// Dual bits with the ties decided by the thread itself, one after another
+// (for callers whose lanes are not converged).
+template <int L, int LAYOUT>
+__device__ __forceinline__ void dual_bits(uint32_t e, uint32_t c, int xs, int xt, const uint32_t* __restrict__ tpl_e,
+                                          const uint32_t* __restrict__ thr_e, uint32_t sweep, const RoundKeys& key,
+                                          uint32_t (&bits)[Ent<L, LAYOUT>::W]) {
+    using E = Ent<L, LAYOUT>;
+    uint32_t ties[E::W];
+    dual_prefix_bits<L, LAYOUT>(e, c, xs, xt, tpl_e, sweep, key, bits, ties);
 #pragma unroll 1
     for (int g = 0; g < E::W; ++g) {
         uint32_t tg = ties[g];
@@ -161,13 +185,77 @@ __device__ __forceinline__ void dual_bits(uint32_t e, uint32_t c, int xs, int xt
             const int b = __ffs(tg) - 1;
             tg &= tg - 1u;
             const int k = 32 * g + b;
-            const int ik = LAYOUT == MRF_LAYOUT_PIVOT ? 1 + k / (L - 1) : k;
-            const int jk = LAYOUT == MRF_LAYOUT_PIVOT ? 1 + k % (L - 1) : k;
-            const uint32_t t = case_threshold(__ldg(thr_e + k), xs == ik, xt == jk);
-            const uint32_t rem = t - (threshold_prefix(t) << 16);      // in [0, 65536]
-            if (rem && dual_low16(e, sweep, c, k, key) < rem) bits[g] |= 1u << b;
+            if (resolve_tie<L, LAYOUT>(e, c, xs, xt, k, __ldg(thr_e + k), sweep, key)) bits[g] |= 1u << b;
         }
     }
+}
+
+// Ties of a whole warp decided together: the warp's ties are numbered by an
+// exclusive scan of the per-lane counts and dealt out one per lane, so a warp
+// with up to 32 ties pays for one threshold load and one Philox call per lane
+// instead of its busiest lane's ties in sequence.  The decisions are those of
+// dual_bits (the uniforms are counter-based).  All 32 lanes must call this;
+// lanes without work pass ties = 0.  s_bits: this warp's 32 * W shared words.
+template <int L, int LAYOUT>
+__device__ __forceinline__ void resolve_ties_warp(uint32_t e, uint32_t c, int xs, int xt,
+                                                  const uint32_t* __restrict__ thr, uint32_t sweep,
+                                                  const RoundKeys& key, uint32_t (&bits)[Ent<L, LAYOUT>::W],
+                                                  const uint32_t (&ties)[Ent<L, LAYOUT>::W], uint32_t* s_bits) {
+    using E = Ent<L, LAYOUT>;
+    constexpr uint32_t FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    int n = 0;
+#pragma unroll
+    for (int w = 0; w < E::W; ++w) n += __popc(ties[w]);
+    int incl = n;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += y;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    if (total == 0) return;                                   // warp-uniform
+    const int off = incl - n;                                 // exclusive offset, non-decreasing over lanes
+#pragma unroll
+    for (int w = 0; w < E::W; ++w) s_bits[lane * E::W + w] = bits[w];
+    __syncwarp();
+    for (int base = 0; base < total; base += 32) {            // warp-uniform
+        const int j = base + lane;
+        // owner = the last lane whose offset is <= j (it holds at least one tie when j < total)
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step; step >>= 1) {
+            const int oc = __shfl_sync(FULL, off, owner + step);
+            if (oc <= j) owner += step;
+        }
+        int r = j - __shfl_sync(FULL, off, owner);
+        uint32_t tw[E::W];
+#pragma unroll
+        for (int w = 0; w < E::W; ++w) tw[w] = __shfl_sync(FULL, ties[w], owner);
+        const uint32_t eo = __shfl_sync(FULL, e, owner), co = __shfl_sync(FULL, c, owner);
+        const int xso = __shfl_sync(FULL, xs, owner), xto = __shfl_sync(FULL, xt, owner);
+        if (j < total) {
+            int k = -1;
+#pragma unroll
+            for (int w = 0; w < E::W; ++w) {
+                const int pc = __popc(tw[w]);
+                if (k < 0) {
+                    if (r < pc) {
+                        uint32_t m = tw[w];
+                        for (int i = 0; i < r; ++i) m &= m - 1u;   // drop the r lowest ties of the word
+                        k = 32 * w + __ffs(m) - 1;
+                    } else {
+                        r -= pc;
+                    }
+                }
+            }
+            if (resolve_tie<L, LAYOUT>(eo, co, xso, xto, k, __ldg(thr + (size_t)eo * E::M + k), sweep, key))
+                atomicOr(&s_bits[owner * E::W + (k >> 5)], 1u << (k & 31));
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int w = 0; w < E::W; ++w) bits[w] = s_bits[lane * E::W + w];
 }
 
 // ---------------------------------------------------------------------------- label draw
@@ -216,22 +304,27 @@ __device__ __forceinline__ int draw_label(const float (&F)[L], uint32_t v, uint3
 template <int L, int LAYOUT>
 __global__ void __launch_bounds__(256, 4) k_dual(SweepArgs a) {
     using E = Ent<L, LAYOUT>;
+    __shared__ uint32_t s_bits[256 * E::W];
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;     // E * C < 2^32 (checked by the host)
-    if (g >= (uint64_t)a.E * a.C) return;
-    const uint32_t e = a.fdC.div(g);
-    const uint32_t c = g - e * (uint32_t)a.C;
+    const bool in_range = g < (uint64_t)a.E * a.C;                // every lane stays for the warp's tie pass
+    const uint32_t e = in_range ? a.fdC.div(g) : 0u;
+    const uint32_t c = in_range ? g - e * (uint32_t)a.C : 0u;
     const uint32_t sweep = (uint32_t)a.ctl->sweep;
     const uint8_t* xin = a.x + (size_t)(sweep & 1) * a.N * a.C;
-    uint32_t bits[E::W];
-    const int s = a.src[e];
+    uint32_t bits[E::W], ties[E::W];
+    int xs = 0, xt = 0;
+    const int s = in_range ? a.src[e] : -1;
     if (s >= 0 && !(a.splash && is_tree_edge(a, e)) && !(a.skip && a.skip[e])) {
         const int t = a.dst[e];
-        dual_bits<L, LAYOUT>(e, c, xin[(int64_t)s * a.C + c], xin[(int64_t)t * a.C + c],
-                             a.tpl + (int64_t)e * E::W * 32, a.thr + (int64_t)e * E::M, sweep, a.rk, bits);
+        xs = xin[(int64_t)s * a.C + c];
+        xt = xin[(int64_t)t * a.C + c];
+        dual_prefix_bits<L, LAYOUT>(e, c, xs, xt, a.tpl + (int64_t)e * E::W * 32, sweep, a.rk, bits, ties);
     } else {
 #pragma unroll
-        for (int w = 0; w < E::W; ++w) bits[w] = 0;
+        for (int w = 0; w < E::W; ++w) { bits[w] = 0; ties[w] = 0; }
     }
+    resolve_ties_warp<L, LAYOUT>(e, c, xs, xt, a.thr, sweep, a.rk, bits, ties, s_bits + (threadIdx.x & ~31u) * E::W);
+    if (!in_range) return;
     uint32_t* out = a.theta + (int64_t)g * E::W;
     if (E::W % 2 == 0) {
 #pragma unroll

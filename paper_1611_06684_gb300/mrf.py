@@ -61,6 +61,7 @@ _SIGS = {
     "mrf_debug_theta": (ct.c_int, [_P, _P]),
     "mrf_kernel_times": (ct.c_int, [_P, _P, _P]),
     "mrf_set_kernel_timing": (ct.c_int, [_P, ct.c_int32]),
+    "mrf_philox_rate": (ct.c_int, [ct.c_uint64, ct.c_int32, _P, ct.POINTER(ct.c_double)]),
     "mrf_sweep_noalloc": (ct.c_int, [_P, _P, _P, ct.c_int64]),
     "mrf_learned_setup": (ct.c_int, [_P, _P, ct.c_int32, ct.c_uint64]),
     "mrf_learned_param_count": (ct.c_int64, [_P]),
@@ -434,6 +435,16 @@ class MRFBatch:
         self.lib.mrf_get_info(view.h, ct.byref(inf))
         view.N, view.L, view.C = inf.n_vars, inf.n_labels, inf.n_chains
         return view
+
+
+def philox_rate(threads: int = 152 * 2048 * 8, calls: int = 64, stream: int = 0) -> float:
+    """Measured Philox4x32-10 calls per second of a Philox-only kernel."""
+    lib = load()
+    out = ct.c_double()
+    st = lib.mrf_philox_rate(ct.c_uint64(threads), calls, _P(stream), ct.byref(out))
+    if st != MRF_OK:
+        raise MrfError(st, lib.mrf_status_string(st).decode())
+    return out.value
 
 
 def unpack_theta(words: np.ndarray, m: int) -> np.ndarray:
