@@ -124,6 +124,10 @@ def kernel_work(name, model_info, C):
     return 0, 0
 
 
+# kernels behind one kernel-timing record of the library
+KERNELS_PER_RECORD = {"k_dual": 2}
+
+
 def rank_seed(seed: int, rank: int) -> int:
     """Independent chains per rank: the draw key of rank r is seed + 1000003 r."""
     return seed + 1000003 * rank
@@ -193,7 +197,8 @@ def run_ours(args, ws, rank, local):
     ktimes = h.kernel_times()
     ms_total, value = aggregate(ms_total, C * model.n_vars * args.steps, ws, dev)
     ms_step = ms_total / args.steps
-    launches = sum(n for _, n in ktimes.values()) + args.steps   # + k_advance per sweep
+    # a timed dual step is two kernels (k_dual, k_dual_ties); + k_advance per sweep
+    launches = sum(n * KERNELS_PER_RECORD.get(k, 1) for k, (_, n) in ktimes.items()) + args.steps
 
     # roofline of the dominant kernel (device time inside the timed region)
     peaks, peak_src = load_peaks()

@@ -102,7 +102,20 @@ struct SweepArgs {
     FastDiv fdX1, fdX, fdY1, fdY;   // division by nx-1, nx, ny-1, ny
     float* pot;                // [N][L][C] node potentials / beliefs of the blocked sweep
     const uint8_t* skip;       // [E] 1 = edge kept exact (no dual bit) in a learned sweep; null otherwise
+    // deferred ties of the dual step: per warp of k_dual (32 consecutive items),
+    // tie_cap 16-bit records and their count (see k_dual / k_dual_ties)
+    uint16_t* ties;            // [warps][tie_cap]
+    uint8_t* tie_count;        // [warps]
+    int32_t tie_cap;
 };
+
+// Records reserved per warp for deferred dual ties: ~1.5 x the expected
+// 32 M / 256 plus 16, rounded up to 8 (<= 64 for M <= 225).  A warp with more
+// ties decides the excess itself.
+inline int32_t tie_cap_for(int M) { return ((32 * M * 3 / 512 + 1 + 16) + 7) / 8 * 8; }
+
+// k_dual warps (blocks of 256 threads) for E * C items.
+inline int64_t dual_warps(int64_t items) { return (items + 255) / 256 * 8; }
 
 // Learned block proposal (learned.cu).
 constexpr int kLearnBlock = 16;                                   // sites per block (max)

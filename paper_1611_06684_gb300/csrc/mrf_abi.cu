@@ -35,6 +35,8 @@ struct mrf {
     int2* d_inc = nullptr;
     uint8_t* d_x = nullptr;
     uint32_t* d_theta = nullptr;
+    uint16_t* d_ties = nullptr;        // deferred dual ties [dual warps][tie_cap]
+    uint8_t* d_tie_count = nullptr;    // [dual warps]
     uint32_t* d_counts = nullptr;
     float* d_logp = nullptr;
     Ctl* d_ctl = nullptr;
@@ -131,6 +133,14 @@ cudaError_t timed(mrf_t* h, int id, Fn fn) {
     return e;
 }
 
+// Deferred-tie records and counts of the dual step for `slots` edge slots.
+cudaError_t alloc_ties(mrf_t* h, int64_t slots) {
+    const int64_t warps = dual_warps(slots * h->C);
+    cudaError_t e = dalloc(h->d_ties, (size_t)warps * tie_cap_for(h->M));
+    if (e == cudaSuccess) e = dalloc(h->d_tie_count, (size_t)warps);
+    return e;
+}
+
 void drop_graphs(mrf_t* h) {
     for (auto& g : h->graph)
         if (g) { cudaGraphExecDestroy(g); g = nullptr; }
@@ -144,6 +154,7 @@ SweepArgs make_args(const mrf_t* h) {
     a.tpl = h->d_tpl; a.utf = h->d_utf;
     a.inc_ptr = h->d_inc_ptr; a.inc = h->d_inc; a.ut = h->d_ut;
     a.x = h->d_x; a.theta = h->d_theta; a.counts = h->d_counts; a.logp = h->d_logp;
+    a.ties = h->d_ties; a.tie_count = h->d_tie_count; a.tie_cap = tie_cap_for(h->M);
     a.ctl = h->d_ctl; a.key = h->key;
     a.rk = round_keys(h->key);
     a.fdC = FastDiv::make((uint32_t)h->C);
@@ -350,7 +361,7 @@ void mrf_destroy(mrf_t* h) {
     drop_graphs(h);
     dfree(h->d_unary); dfree(h->d_ut); dfree(h->d_utf); dfree(h->d_tpl); dfree(h->d_src); dfree(h->d_dst); dfree(h->d_tau); dfree(h->d_thr);
     dfree(h->d_fold); dfree(h->d_cst); dfree(h->d_resid); dfree(h->d_inc_ptr); dfree(h->d_inc); dfree(h->d_x);
-    dfree(h->d_theta); dfree(h->d_counts); dfree(h->d_logp); dfree(h->d_ctl); dfree(h->d_flag); dfree(h->d_stage); dfree(h->d_pot);
+    dfree(h->d_theta); dfree(h->d_ties); dfree(h->d_tie_count); dfree(h->d_counts); dfree(h->d_logp); dfree(h->d_ctl); dfree(h->d_flag); dfree(h->d_stage); dfree(h->d_pot);
     dfree(h->d_csr_work); dfree(h->d_csr_sums);
     dfree(h->d_ed_pair); dfree(h->d_ed_slots); dfree(h->d_ed_new); dfree(h->d_ed_s); dfree(h->d_ed_t);
     dfree(h->d_members); dfree(h->d_nmem); dfree(h->d_intra_ptr); dfree(h->d_intra); dfree(h->d_cf); dfree(h->d_skip);
@@ -414,6 +425,7 @@ mrf_status mrf_set_factors(mrf_t* h, const float* unary_log, int64_t n_edges, co
     MRF_CUDA(h, dalloc(h->d_fold, E * 2 * L)); MRF_CUDA(h, dalloc(h->d_cst, E));
     if (want_resid) MRF_CUDA(h, dalloc(h->d_resid, E * L * L)); else dfree(h->d_resid);
     MRF_CUDA(h, dalloc(h->d_theta, E * h->C * h->W));
+    MRF_CUDA(h, alloc_ties(h, (int64_t)E));
     MRF_CUDA(h, to_device(h->d_src, h->h_src.data(), n_edges, MRF_PTR_HOST, h->stream));
     MRF_CUDA(h, to_device(h->d_dst, h->h_dst.data(), n_edges, MRF_PTR_HOST, h->stream));
     MRF_CUDA(h, build_csr(h));
@@ -512,6 +524,7 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
         MRF_CUDA(h, grow(h->d_tau, pad4(h->M))); MRF_CUDA(h, grow(h->d_thr, h->M)); MRF_CUDA(h, grow(h->d_tpl, h->W * 32));
         MRF_CUDA(h, grow(h->d_fold, 2 * L)); MRF_CUDA(h, grow(h->d_cst, 1));
         MRF_CUDA(h, dalloc(h->d_theta, (size_t)cap * h->C * h->W));
+        MRF_CUDA(h, alloc_ties(h, cap));
         h->E_cap = cap;
     }
     h->h_src.resize(new_slots, -1); h->h_dst.resize(new_slots, -1);

@@ -157,20 +157,23 @@ __device__ __forceinline__ void dual_prefix_bits(uint32_t e, uint32_t c, int xs,
     }
 }
 
-// Decision of a tie at entry k: low 16 bits of the uniform < the part of the
-// case threshold below its 8-bit prefix.
+// Row / column label of entry k.
 template <int L, int LAYOUT>
-__device__ __forceinline__ bool resolve_tie(uint32_t e, uint32_t c, int xs, int xt, int k, uint32_t thr_word,
+__device__ __forceinline__ int entry_row(int k) { return LAYOUT == MRF_LAYOUT_PIVOT ? 1 + k / (L - 1) : k; }
+template <int L, int LAYOUT>
+__device__ __forceinline__ int entry_col(int k) { return LAYOUT == MRF_LAYOUT_PIVOT ? 1 + k % (L - 1) : k; }
+
+// Decision of a tie at entry k in case (y, z) = ([x_s = i_k], [x_t = j_k]):
+// low 16 bits of the uniform < the part of the case threshold below its
+// 8-bit prefix.
+__device__ __forceinline__ bool resolve_tie(uint32_t e, uint32_t c, int y, int z, int k, uint32_t thr_word,
                                             uint32_t sweep, const RoundKeys& key) {
-    const int ik = LAYOUT == MRF_LAYOUT_PIVOT ? 1 + k / (L - 1) : k;
-    const int jk = LAYOUT == MRF_LAYOUT_PIVOT ? 1 + k % (L - 1) : k;
-    const uint32_t t = case_threshold(thr_word, xs == ik, xt == jk);
+    const uint32_t t = case_threshold(thr_word, y, z);
     const uint32_t rem = t - (threshold_prefix(t) << 16);      // in [0, 65536]
     return rem && dual_low16(e, sweep, c, k, key) < rem;
 }
 
-// Dual bits with the ties decided by the thread itself, one after another
-// (for callers whose lanes are not converged).
+// Dual bits with the ties decided by the thread itself, one after another.
 template <int L, int LAYOUT>
 __device__ __forceinline__ void dual_bits(uint32_t e, uint32_t c, int xs, int xt, const uint32_t* __restrict__ tpl_e,
                                           const uint32_t* __restrict__ thr_e, uint32_t sweep, const RoundKeys& key,
@@ -185,77 +188,11 @@ __device__ __forceinline__ void dual_bits(uint32_t e, uint32_t c, int xs, int xt
             const int b = __ffs(tg) - 1;
             tg &= tg - 1u;
             const int k = 32 * g + b;
-            if (resolve_tie<L, LAYOUT>(e, c, xs, xt, k, __ldg(thr_e + k), sweep, key)) bits[g] |= 1u << b;
+            if (resolve_tie(e, c, xs == entry_row<L, LAYOUT>(k), xt == entry_col<L, LAYOUT>(k), k, __ldg(thr_e + k),
+                            sweep, key))
+                bits[g] |= 1u << b;
         }
     }
-}
-
-// Ties of a whole warp decided together: the warp's ties are numbered by an
-// exclusive scan of the per-lane counts and dealt out one per lane, so a warp
-// with up to 32 ties pays for one threshold load and one Philox call per lane
-// instead of its busiest lane's ties in sequence.  The decisions are those of
-// dual_bits (the uniforms are counter-based).  All 32 lanes must call this;
-// lanes without work pass ties = 0.  s_bits: this warp's 32 * W shared words.
-template <int L, int LAYOUT>
-__device__ __forceinline__ void resolve_ties_warp(uint32_t e, uint32_t c, int xs, int xt,
-                                                  const uint32_t* __restrict__ thr, uint32_t sweep,
-                                                  const RoundKeys& key, uint32_t (&bits)[Ent<L, LAYOUT>::W],
-                                                  const uint32_t (&ties)[Ent<L, LAYOUT>::W], uint32_t* s_bits) {
-    using E = Ent<L, LAYOUT>;
-    constexpr uint32_t FULL = 0xFFFFFFFFu;
-    const int lane = threadIdx.x & 31;
-    int n = 0;
-#pragma unroll
-    for (int w = 0; w < E::W; ++w) n += __popc(ties[w]);
-    int incl = n;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int y = __shfl_up_sync(FULL, incl, d);
-        if (lane >= d) incl += y;
-    }
-    const int total = __shfl_sync(FULL, incl, 31);
-    if (total == 0) return;                                   // warp-uniform
-    const int off = incl - n;                                 // exclusive offset, non-decreasing over lanes
-#pragma unroll
-    for (int w = 0; w < E::W; ++w) s_bits[lane * E::W + w] = bits[w];
-    __syncwarp();
-    for (int base = 0; base < total; base += 32) {            // warp-uniform
-        const int j = base + lane;
-        // owner = the last lane whose offset is <= j (it holds at least one tie when j < total)
-        int owner = 0;
-#pragma unroll
-        for (int step = 16; step; step >>= 1) {
-            const int oc = __shfl_sync(FULL, off, owner + step);
-            if (oc <= j) owner += step;
-        }
-        int r = j - __shfl_sync(FULL, off, owner);
-        uint32_t tw[E::W];
-#pragma unroll
-        for (int w = 0; w < E::W; ++w) tw[w] = __shfl_sync(FULL, ties[w], owner);
-        const uint32_t eo = __shfl_sync(FULL, e, owner), co = __shfl_sync(FULL, c, owner);
-        const int xso = __shfl_sync(FULL, xs, owner), xto = __shfl_sync(FULL, xt, owner);
-        if (j < total) {
-            int k = -1;
-#pragma unroll
-            for (int w = 0; w < E::W; ++w) {
-                const int pc = __popc(tw[w]);
-                if (k < 0) {
-                    if (r < pc) {
-                        uint32_t m = tw[w];
-                        for (int i = 0; i < r; ++i) m &= m - 1u;   // drop the r lowest ties of the word
-                        k = 32 * w + __ffs(m) - 1;
-                    } else {
-                        r -= pc;
-                    }
-                }
-            }
-            if (resolve_tie<L, LAYOUT>(eo, co, xso, xto, k, __ldg(thr + (size_t)eo * E::M + k), sweep, key))
-                atomicOr(&s_bits[owner * E::W + (k >> 5)], 1u << (k & 31));
-        }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int w = 0; w < E::W; ++w) bits[w] = s_bits[lane * E::W + w];
 }
 
 // ---------------------------------------------------------------------------- label draw
@@ -301,12 +238,21 @@ __device__ __forceinline__ int draw_label(const float (&F)[L], uint32_t v, uint3
 
 // ---------------------------------------------------------------------------- kernels
 
+// Dual step.  Ties are not decided here: a tie needs a threshold word (a
+// scattered load) and one more Philox call, and only ~M/256 of a thread's
+// entries tie, so deciding them in place keeps whole warps waiting on a few
+// lanes.  Each warp instead writes its ties as 16-bit records
+//   lane | [x_s = i_k] << 5 | [x_t = j_k] << 6 | k << 8
+// to its own tie_cap slots (numbered by a warp scan of the per-lane counts)
+// and its count; k_dual_ties then decides all of them with every lane busy.
+// Ties beyond tie_cap are decided in place.
 template <int L, int LAYOUT>
 __global__ void __launch_bounds__(256, 4) k_dual(SweepArgs a) {
     using E = Ent<L, LAYOUT>;
-    __shared__ uint32_t s_bits[256 * E::W];
+    constexpr uint32_t FULL = 0xFFFFFFFFu;
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;     // E * C < 2^32 (checked by the host)
-    const bool in_range = g < (uint64_t)a.E * a.C;                // every lane stays for the warp's tie pass
+    const int lane = threadIdx.x & 31;
+    const bool in_range = g < (uint64_t)a.E * a.C;                // every lane stays for the warp scan
     const uint32_t e = in_range ? a.fdC.div(g) : 0u;
     const uint32_t c = in_range ? g - e * (uint32_t)a.C : 0u;
     const uint32_t sweep = (uint32_t)a.ctl->sweep;
@@ -323,7 +269,37 @@ __global__ void __launch_bounds__(256, 4) k_dual(SweepArgs a) {
 #pragma unroll
         for (int w = 0; w < E::W; ++w) { bits[w] = 0; ties[w] = 0; }
     }
-    resolve_ties_warp<L, LAYOUT>(e, c, xs, xt, a.thr, sweep, a.rk, bits, ties, s_bits + (threadIdx.x & ~31u) * E::W);
+    int n = 0;
+#pragma unroll
+    for (int w = 0; w < E::W; ++w) n += __popc(ties[w]);
+    int incl = n;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += y;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (lane == 0) a.tie_count[gw] = (uint8_t)min(total, a.tie_cap);
+    if (n) {
+        uint16_t* rec = a.ties + gw * a.tie_cap;
+        int i = incl - n;
+#pragma unroll 1
+        for (int w = 0; w < E::W; ++w) {
+            uint32_t tw = ties[w];
+            while (tw) {
+                const int b = __ffs(tw) - 1;
+                tw &= tw - 1u;
+                const int k = 32 * w + b;
+                const int y = xs == entry_row<L, LAYOUT>(k), z = xt == entry_col<L, LAYOUT>(k);
+                if (i < a.tie_cap)
+                    rec[i] = (uint16_t)(lane | (y << 5) | (z << 6) | (k << 8));
+                else if (resolve_tie(e, c, y, z, k, __ldg(a.thr + (int64_t)e * E::M + k), sweep, a.rk))
+                    bits[w] |= 1u << b;
+                ++i;
+            }
+        }
+    }
     if (!in_range) return;
     uint32_t* out = a.theta + (int64_t)g * E::W;
     if (E::W % 2 == 0) {
@@ -332,6 +308,29 @@ __global__ void __launch_bounds__(256, 4) k_dual(SweepArgs a) {
     } else {
 #pragma unroll
         for (int w = 0; w < E::W; ++w) out[w] = bits[w];
+    }
+}
+
+// Deferred ties of the dual step: thread q handles the records of k_dual warp
+// q (items 32 q .. 32 q + 31), setting the won bits in theta with atomicOr.
+template <int L, int LAYOUT>
+__global__ void __launch_bounds__(256) k_dual_ties(SweepArgs a, int64_t n_warps) {
+    using E = Ent<L, LAYOUT>;
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n_warps) return;
+    const int cnt = a.tie_count[q];
+    if (!cnt) return;
+    const uint32_t sweep = (uint32_t)a.ctl->sweep;
+    const uint16_t* rec = a.ties + q * a.tie_cap;
+#pragma unroll 1
+    for (int i = 0; i < cnt; ++i) {
+        const uint32_t r = rec[i];
+        const uint32_t g = (uint32_t)(q * 32) + (r & 31u);
+        const int k = (int)(r >> 8);
+        const uint32_t e = a.fdC.div(g);
+        const uint32_t c = g - e * (uint32_t)a.C;
+        if (resolve_tie(e, c, (r >> 5) & 1, (r >> 6) & 1, k, __ldg(a.thr + (int64_t)e * E::M + k), sweep, a.rk))
+            atomicOr(a.theta + (int64_t)g * E::W + (k >> 5), 1u << (k & 31));
     }
 }
 
@@ -538,7 +537,10 @@ cudaError_t run_primal_cta(const SweepArgs& a, cudaStream_t s) {
 template <int L, int LAYOUT>
 cudaError_t run_dual(const SweepArgs& a, cudaStream_t s) {
     const int64_t n = a.E * a.C;
-    if (n > 0) k_dual<L, LAYOUT><<<blocks_for(n, 256), 256, 0, s>>>(a);
+    if (n <= 0) return cudaSuccess;
+    k_dual<L, LAYOUT><<<blocks_for(n, 256), 256, 0, s>>>(a);
+    const int64_t warps = dual_warps(n);
+    k_dual_ties<L, LAYOUT><<<blocks_for(warps, 256), 256, 0, s>>>(a, warps);
     return cudaGetLastError();
 }
 
