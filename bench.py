@@ -241,6 +241,11 @@ def run_ours(args, ws, rank, local):
             kt = h.kernel_times()
             variants[name] = {"ms_per_step": msv, "value": C * model.n_vars / (msv / 1e3), "unit": METRIC,
                               "kernels": {k: v[0] / v[1] for k, v in kt.items()}}
+        if args.ess_sweeps > 0:
+            ms_of = {"plain": ms_step if args.mode == "plain" else None}
+            ms_of.update({k: v["ms_per_step"] for k, v in variants.items()})
+            variants["ess"] = ess_comparison(h, model, C, stream, args.ess_sweeps, ms_of,
+                                             [("plain", M.MODE_PLAIN)] + ([("splash", M.MODE_SPLASH)] if model.grid else []))
 
     # end to end through the C ABI with pinned host buffers: labels in, sweep, labels out
     e2e = None
@@ -275,7 +280,7 @@ def run_ours(args, ws, rank, local):
         out = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 (f64 unary/field accumulation, u32 integer draws)",
+            "vs_baseline": None, "dtype": "u32+f32 (dual step: u32 Philox and threshold compare; primal step: f32 with two-sum accumulation)",
             "data": "synthetic (seeded generators)",
             "config": {"workload": args.workload, "description": desc, "n_vars": model.n_vars,
                        "n_edges": model.n_edges, "n_labels": model.n_labels, "chains": C, "mode": args.mode,
@@ -472,6 +477,57 @@ def ess_sum_over_chains(trace):
         tau = -1.0 + 2.0 * np.minimum.accumulate(pairs[:k]).sum() / g[0]
         total += T / max(tau, 1e-12)
     return float(total)
+
+
+def ess_comparison(h, model, C, stream, T, ms_of, forms, n_sites=4096, n_edges=50000):
+    """ESS/s of sweep forms on one handle from a common start: per chain, the
+    fraction of label 0 over n_sites fixed sites, their unary energy, and the
+    pairwise energy of n_edges fixed edges, traced every sweep on the device
+    (labels copied device to device, statistics reduced by torch).  ESS/s =
+    min over statistics of the ESS summed over chains / (T x ms per sweep)."""
+    import torch
+    from paper_1611_06684_gb300 import mrf as M
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rng = np.random.default_rng(12345)
+    sites = torch.as_tensor(np.sort(rng.choice(model.n_vars, size=min(n_sites, model.n_vars), replace=False)),
+                            device=dev)
+    esel = np.sort(rng.choice(model.n_edges, size=min(n_edges, model.n_edges), replace=False))
+    es = torch.as_tensor(model.src[esel].astype(np.int64), device=dev)
+    et = torch.as_tensor(model.dst[esel].astype(np.int64), device=dev)
+    w = torch.as_tensor(model.pair[esel], device=dev)
+    u = torch.as_tensor(model.unary, device=dev)
+    ar = torch.arange(len(esel), device=dev)
+    x = torch.empty((C, model.n_vars), dtype=torch.uint8, device=dev)
+    h.get_labels_into(x)
+    torch.cuda.synchronize()
+    x_start = x.clone()
+    t_start = h.info().sweep_index
+    out = {}
+    for name, md in forms:
+        if ms_of.get(name) is None:
+            continue
+        h.set_labels(x_start)
+        h.set_sweep_index(t_start + 7919)
+        stats = torch.empty((3, T, C), dtype=torch.float64, device=dev)
+        for t in range(T):
+            h.sweep(1, md)
+            with torch.cuda.stream(stream):
+                h.get_labels_into(x)
+                xl = x.long()
+                xs = xl[:, sites]
+                stats[0, t] = (xs == 0).double().mean(dim=1)
+                stats[1, t] = u[sites[None, :], xs].double().sum(dim=1)
+                stats[2, t] = w[ar[None, :], xl[:, es], xl[:, et]].double().sum(dim=1)
+        torch.cuda.synchronize()
+        tr = stats.cpu().numpy()
+        ess = {k: ess_sum_over_chains(tr[i]) for i, k in enumerate(("label0_fraction", "unary_energy", "pair_energy"))}
+        ms = ms_of[name]
+        out[name] = {"ess": ess, "ess_min": min(ess.values()), "ms_per_sweep": ms,
+                     "ess_per_s": min(ess.values()) / (T * ms / 1e3)}
+    out["sweeps"] = T
+    out["statistics"] = (f"per chain: label-0 fraction and unary energy of {len(sites)} fixed sites, pairwise "
+                         f"energy of {len(esel)} fixed edges; ESS summed over chains, min over statistics")
+    return out
 
 
 def tv_mean(p, q):

@@ -336,7 +336,8 @@ __global__ void __launch_bounds__(256) k_dual_ties(SweepArgs a, int64_t n_warps)
 
 // Accumulate the beta terms of edge e's set dual bits for one endpoint side
 // (tau row loaded as 16-byte vectors; beta1 = tau_signed, beta2 = |tau_signed|).
-template <int L, int LAYOUT>
+// GLOBAL: the row is in global memory (read-only path); else in shared memory.
+template <int L, int LAYOUT, bool GLOBAL = true>
 __device__ __forceinline__ void add_side(const uint32_t (&bits)[Ent<L, LAYOUT>::W], const float* __restrict__ tau_e,
                                          int side, float (&acc)[L]) {
     using E = Ent<L, LAYOUT>;
@@ -344,7 +345,7 @@ __device__ __forceinline__ void add_side(const uint32_t (&bits)[Ent<L, LAYOUT>::
     if (side == 0) {
 #pragma unroll
         for (int k4 = 0; k4 < E::MP / 4; ++k4) {
-            const float4 q = __ldg(t4 + k4);
+            const float4 q = GLOBAL ? __ldg(t4 + k4) : t4[k4];
             const float tv[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -355,7 +356,7 @@ __device__ __forceinline__ void add_side(const uint32_t (&bits)[Ent<L, LAYOUT>::
     } else {
 #pragma unroll
         for (int k4 = 0; k4 < E::MP / 4; ++k4) {
-            const float4 q = __ldg(t4 + k4);
+            const float4 q = GLOBAL ? __ldg(t4 + k4) : t4[k4];
             const float tv[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -441,6 +442,104 @@ __global__ void __launch_bounds__(256, FUSED ? 2 : 4) k_primal(SweepArgs a) {
                 flushed = true;
             }
         }
+    }
+    float F[L];
+    const float* uf = a.utf + (int64_t)v * L;
+    if (flushed) {
+#pragma unroll
+        for (int x = 0; x < L; ++x) { two_sum_add(hi[x], lo[x], acc[x]); F[x] = __ldg(uf + x) + (hi[x] + lo[x]); }
+    } else {
+#pragma unroll
+        for (int x = 0; x < L; ++x) F[x] = __ldg(uf + x) + acc[x];
+    }
+    if (POT) {
+        float* pv = a.pot + (int64_t)v * L * a.C + c;
+#pragma unroll
+        for (int x = 0; x < L; ++x) pv[(int64_t)x * a.C] = F[x];
+        return;
+    }
+    float* lp = a.logp ? a.logp + ((int64_t)c * a.N + v) * L : nullptr;
+    xout[g] = (uint8_t)draw_label<L>(F, v, c, sweep, a.rk, PH_PRIMAL, lp, a.ctl);
+}
+
+// Warp-per-site form of the plain primal step (chains a multiple of 32, so a
+// warp is one site and 32 of its chains).  Incidences go in chunks of K: the
+// lanes load the chunk's incidence records in parallel, then the chunk's tau
+// rows into shared memory (one row per incidence, shared by the 32 chains)
+// while every lane loads its own theta words, so a chunk costs two dependent
+// memory latencies instead of one per incidence.  Same additions in the same
+// order as k_primal.
+template <int L, int LAYOUT>
+struct PrimalWarp {
+    static constexpr int MP = Ent<L, LAYOUT>::MP;
+    static constexpr int K = 2;                          // incidences per chunk (larger K spills at 64 registers)
+    static constexpr int WARPS = 8;                      // 256 threads
+};
+
+template <int L, int LAYOUT, bool POT = false>
+__global__ void __launch_bounds__(256, 4) k_primal_warp(SweepArgs a) {
+    using E = Ent<L, LAYOUT>;
+    using PW = PrimalWarp<L, LAYOUT>;
+    constexpr int K = PW::K, MP = PW::MP, Q = MP / 4;    // float4 per tau row
+    constexpr uint32_t FULL = 0xFFFFFFFFu;
+    __shared__ __align__(16) float4 s_tau[PW::WARPS][K][Q];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;     // N * C < 2^32, C % 32 == 0 (host)
+    if (g >= (uint64_t)a.N * a.C) return;                         // whole warps only
+    const uint32_t v = a.fdC.div(g), c = g - v * (uint32_t)a.C;
+    const uint32_t sweep = (uint32_t)a.ctl->sweep;
+    uint8_t* xout = a.x + (size_t)((sweep + 1) & 1) * a.N * a.C;
+    float acc[L], hi[L], lo[L];
+#pragma unroll
+    for (int x = 0; x < L; ++x) { acc[x] = 0.0f; hi[x] = 0.0f; lo[x] = 0.0f; }
+    const int64_t p0 = a.inc_ptr[v], p1 = a.inc_ptr[v + 1];
+    const float4* tau4 = reinterpret_cast<const float4*>(a.tau);
+    int chunk = 0;
+    bool flushed = false;
+    for (int64_t base = p0; base < p1; base += K) {              // warp-uniform
+        const int cnt = p1 - base < K ? (int)(p1 - base) : K;
+        const int code_l = lane < cnt ? __ldg(&a.inc[base + lane]).x : 0;
+        // tau rows of the chunk -> shared memory (uniform trip count; lanes split the float4s)
+#pragma unroll
+        for (int i0 = 0; i0 < K * Q; i0 += 32) {
+            const int i = i0 + lane;
+            const int u = i / Q;
+            const int cu = __shfl_sync(FULL, code_l, u < K ? u : 0);
+            if (i < K * Q && u < cnt) s_tau[warp][u][i - u * Q] = __ldg(tau4 + (int64_t)(cu >> 1) * Q + (i - u * Q));
+        }
+        uint32_t bits[K][E::W];
+        int code[K];
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            code[u] = __shfl_sync(FULL, code_l, u);
+            if (u < cnt) {
+                const uint32_t* th = a.theta + ((int64_t)(code[u] >> 1) * a.C + c) * E::W;
+                if (E::W % 2 == 0) {
+#pragma unroll
+                    for (int w = 0; w < E::W; w += 2) {
+                        const uint2 q = __ldcs(reinterpret_cast<const uint2*>(th + w));
+                        bits[u][w] = q.x;
+                        bits[u][w + 1 < E::W ? w + 1 : w] = q.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int w = 0; w < E::W; ++w) bits[u][w] = __ldcs(th + w);
+                }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            if (u >= cnt) break;
+            add_side<L, LAYOUT, false>(bits[u], reinterpret_cast<const float*>(&s_tau[warp][u][0]), code[u] & 1, acc);
+            if (++chunk == 32) {
+#pragma unroll
+                for (int x = 0; x < L; ++x) { two_sum_add(hi[x], lo[x], acc[x]); acc[x] = 0.0f; }
+                chunk = 0;
+                flushed = true;
+            }
+        }
+        __syncwarp();                                              // rows consumed before the next chunk
     }
     float F[L];
     const float* uf = a.utf + (int64_t)v * L;
@@ -547,14 +646,22 @@ cudaError_t run_dual(const SweepArgs& a, cudaStream_t s) {
 template <int L, int LAYOUT, bool FUSED>
 cudaError_t run_primal(const SweepArgs& a, cudaStream_t s) {
     const int64_t n = (int64_t)a.N * a.C;
-    if (n > 0) k_primal<L, LAYOUT, FUSED><<<blocks_for(n, 256), 256, 0, s>>>(a);
+    if (n <= 0) return cudaSuccess;
+    if (!FUSED && a.C % 32 == 0)
+        k_primal_warp<L, LAYOUT><<<blocks_for(n, 256), 256, 0, s>>>(a);
+    else
+        k_primal<L, LAYOUT, FUSED><<<blocks_for(n, 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int L, int LAYOUT>
 cudaError_t run_potential(const SweepArgs& a, cudaStream_t s) {
     const int64_t n = (int64_t)a.N * a.C;
-    if (n > 0) k_primal<L, LAYOUT, false, true><<<blocks_for(n, 256), 256, 0, s>>>(a);
+    if (n <= 0) return cudaSuccess;
+    if (a.C % 32 == 0)
+        k_primal_warp<L, LAYOUT, true><<<blocks_for(n, 256), 256, 0, s>>>(a);
+    else
+        k_primal<L, LAYOUT, false, true><<<blocks_for(n, 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

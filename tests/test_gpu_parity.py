@@ -37,6 +37,9 @@ CASES = {
     "pottsdiag_L4": (lambda: wl.tiny_potts(300, 4, 1500, seed=3), 32),
     "random_L16": (lambda: wl.random_graph(200, k=2, L=16, seed=4, w_std=0.3), 3),
     "random_L3_dup": (lambda: wl.tiny_random(40, 3, 120, seed=5, allow_duplicates=True), 5),
+    # chains a multiple of 32 (warp-per-site primal): degree > 32 (two-sum flush), and L = 16
+    "dense_L4_C32": (lambda: wl.dense_potts(120, L=4, seed=8), 32),
+    "random_L16_C32": (lambda: wl.random_graph(60, k=2, L=16, seed=9, w_std=0.3), 32),
 }
 
 
