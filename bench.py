@@ -101,11 +101,19 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+# Issue cost of one Philox4x32-10 call on GB300, from the ncu counters of the
+# Philox-only kernel (mrf_philox_rate: 79.7 M calls, 146.3 us at 2068 MHz):
+# 15.1 warp instructions per warp-wide call run on the fmaheavy pipe (integer
+# multiplies), which is busy 83.2 % of the cycles, i.e. 61.5 pipe cycles per
+# warp-wide call on each SM sub-partition; its 19.3 alu-pipe instructions
+# (2 cycles each) and 38.6 issue slots per call fit inside that.
+PHILOX_FMAHEAVY_CYCLES_PER_WARP_CALL = 61.5
+
+
 def alu_peak_philox_calls(sm_mhz):
-    """Philox4x32-10 calls/s bound of the integer-multiply pipe: 152 SMs x 64
-    32-bit multiply results per SM per clock; one call needs 10 rounds x 2
-    products x 2 halves = 40 multiply results."""
-    return 152 * 64 / 40.0 * sm_mhz * 1e6
+    """Philox4x32-10 calls/s roof of the fmaheavy pipe: 152 SMs x 4
+    sub-partitions x 32 lanes x clock / 61.5 pipe cycles per warp-wide call."""
+    return 152 * 4 * 32 / PHILOX_FMAHEAVY_CYCLES_PER_WARP_CALL * sm_mhz * 1e6
 
 
 def kernel_work(name, model_info, C):
@@ -216,7 +224,7 @@ def run_ours(args, ws, rank, local):
         alu_peak = alu_peak_philox_calls(peaks.get("sm_max_mhz", 2070.0))
         roof = {"bound": "alu", "achieved": calls / (dom_ms / 1e3) / 1e9, "peak": alu_peak / 1e9,
                 "unit": "G Philox4x32-10 calls/s", "frac": calls / (dom_ms / 1e3) / alu_peak, "traffic": None,
-                "kernel": dom, "peak_source": "derived: 152 SMs x 64 int32 multiplies/clk x 2070 MHz / 40 per call",
+                "kernel": dom, "peak_source": "derived: 152 SMs x 4 SMSPs x 32 lanes x 2070 MHz / 61.5 fmaheavy-pipe cycles per warp-wide call (ncu counters of the Philox-only kernel)",
                 "hbm_view": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac")},
                 "philox_only_kernel": {"calls_per_s": philox_measured,
                                        "frac": (calls / (dom_ms / 1e3) / philox_measured) if philox_measured else None}}

@@ -4,6 +4,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <iterator>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -461,14 +462,12 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
     MRF_CUDA(h, to_host(rem, edge_ids, n_remove, ptr_kind, h->stream));
     MRF_CUDA(h, to_host(as, src, n_add, ptr_kind, h->stream));
     MRF_CUDA(h, to_host(at, dst, n_add, ptr_kind, h->stream));
-    {
-        std::vector<int64_t> sorted = rem;
-        std::sort(sorted.begin(), sorted.end());
-        for (size_t i = 0; i < sorted.size(); ++i) {
-            const int64_t e = sorted[i];
-            if (e < 0 || e >= h->E_slots || h->h_src[e] < 0 || (i && sorted[i - 1] == e))
-                return fail(h, MRF_ERANGE, "edit: slot " + std::to_string(e) + " is not a live edge");
-        }
+    std::vector<int64_t> rem_sorted = rem;
+    std::sort(rem_sorted.begin(), rem_sorted.end());
+    for (size_t i = 0; i < rem_sorted.size(); ++i) {
+        const int64_t e = rem_sorted[i];
+        if (e < 0 || e >= h->E_slots || h->h_src[e] < 0 || (i && rem_sorted[i - 1] == e))
+            return fail(h, MRF_ERANGE, "edit: slot " + std::to_string(e) + " is not a live edge");
     }
     for (int64_t i = 0; i < n_add; ++i) {
         if (as[i] < 0 || as[i] >= N || at[i] < 0 || at[i] >= N) return fail(h, MRF_ERANGE, "edit: vertex id out of range");
@@ -494,9 +493,8 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
     drop_graphs(h);
     // free removed slots
     for (int64_t e : rem) { h->h_src[e] = -1; h->h_dst[e] = -1; }
-    std::vector<int64_t> pool = h->free_slots;
-    pool.insert(pool.end(), rem.begin(), rem.end());
-    std::sort(pool.begin(), pool.end());
+    std::vector<int64_t> pool(h->free_slots.size() + rem_sorted.size());      // both sorted: merge
+    std::merge(h->free_slots.begin(), h->free_slots.end(), rem_sorted.begin(), rem_sorted.end(), pool.begin());
     // new edges: freed slots in increasing order, then fresh slots
     std::vector<int64_t> slots((size_t)n_add);
     size_t used = 0;
@@ -531,10 +529,10 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
     for (int64_t i = 0; i < n_add; ++i) { h->h_src[slots[i]] = as[i]; h->h_dst[slots[i]] = at[i]; }
     // device: every touched slot gets its final endpoints from the host mirror
     // (a removed slot is usually reused by an added edge of the same edit)
-    std::vector<int64_t> upd_slot(rem.begin(), rem.end());
-    upd_slot.insert(upd_slot.end(), slots.begin(), slots.end());
-    std::sort(upd_slot.begin(), upd_slot.end());
-    upd_slot.erase(std::unique(upd_slot.begin(), upd_slot.end()), upd_slot.end());
+    // (removed slots and new slots are both ascending: their union by a merge)
+    std::vector<int64_t> upd_slot;
+    upd_slot.reserve(rem_sorted.size() + slots.size());
+    std::set_union(rem_sorted.begin(), rem_sorted.end(), slots.begin(), slots.end(), std::back_inserter(upd_slot));
     std::vector<int32_t> upd_s(upd_slot.size()), upd_t(upd_slot.size());
     for (size_t i = 0; i < upd_slot.size(); ++i) { upd_s[i] = h->h_src[upd_slot[i]]; upd_t[i] = h->h_dst[upd_slot[i]]; }
     const int64_t n_upd = (int64_t)upd_slot.size();
@@ -854,6 +852,10 @@ struct mrf_batch {
     std::vector<mrf_t*> h;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     std::string err;
+    // per-class edit staging, kept across edits (capacity reused)
+    std::vector<std::vector<int64_t>> ed_rm, ed_idx, ed_ids;
+    std::vector<std::vector<int32_t>> ed_s, ed_t;
+    std::vector<std::vector<float>> ed_p;
 };
 
 namespace {
@@ -988,35 +990,53 @@ mrf_status mrf_batch_edit_factors(mrf_batch_t* b, int64_t n_remove, const int32_
         return bfail(b, MRF_EINVAL, "null edit arrays");
     drop_batch_graphs(b);
     const int K = (int)b->h.size();
-    std::vector<std::vector<int64_t>> rm(K);
+    b->ed_rm.resize(K); b->ed_idx.resize(K); b->ed_ids.resize(K);
+    b->ed_s.resize(K); b->ed_t.resize(K); b->ed_p.resize(K);
+    std::vector<int64_t> n_rm(K, 0), n_ad(K, 0), n_fl(K, 0);
     for (int64_t i = 0; i < n_remove; ++i) {
         const int g = remove_graph[i];
         if (g < 0 || g >= b->G) return bfail(b, MRF_ERANGE, "edit: graph id out of range");
-        rm[b->cls[g]].push_back(remove_slot[i]);
+        n_rm[b->cls[g]]++;
     }
-    std::vector<std::vector<int64_t>> idx(K);
-    std::vector<std::vector<int32_t>> s(K), t(K);
-    std::vector<std::vector<float>> p(K);
-    int64_t poff = 0;
     for (int64_t i = 0; i < n_add; ++i) {
         const int g = add_graph[i];
         if (g < 0 || g >= b->G) return bfail(b, MRF_ERANGE, "edit: graph id out of range");
-        const int k = b->cls[g], L = b->n_labels[g];
         if (src[i] < 0 || src[i] >= b->n_vars[g] || dst[i] < 0 || dst[i] >= b->n_vars[g])
             return bfail(b, MRF_ERANGE, "edit: vertex id out of range");
-        idx[k].push_back(i);
-        s[k].push_back(src[i] + b->site_off[g]);
-        t[k].push_back(dst[i] + b->site_off[g]);
-        p[k].insert(p[k].end(), pair_log + poff, pair_log + poff + (int64_t)L * L);
-        poff += (int64_t)L * L;
+        const int k = b->cls[g];
+        n_ad[k]++;
+        n_fl[k] += (int64_t)b->n_labels[g] * b->n_labels[g];
     }
     for (int k = 0; k < K; ++k) {
-        if (rm[k].empty() && idx[k].empty()) continue;
-        std::vector<int64_t> ids(idx[k].size());
-        mrf_status st = mrf_edit_factors(b->h[k], (int64_t)rm[k].size(), rm[k].data(), (int64_t)idx[k].size(),
-                                         s[k].data(), t[k].data(), p[k].data(), ids.data(), MRF_PTR_HOST);
+        b->ed_rm[k].clear(); b->ed_rm[k].reserve(n_rm[k]);
+        b->ed_idx[k].clear(); b->ed_idx[k].reserve(n_ad[k]);
+        b->ed_s[k].clear(); b->ed_s[k].reserve(n_ad[k]);
+        b->ed_t[k].clear(); b->ed_t[k].reserve(n_ad[k]);
+        b->ed_p[k].resize(n_fl[k]);
+        b->ed_ids[k].resize(n_ad[k]);
+    }
+    for (int64_t i = 0; i < n_remove; ++i) b->ed_rm[b->cls[remove_graph[i]]].push_back(remove_slot[i]);
+    std::vector<int64_t> pos(K, 0);
+    int64_t poff = 0;
+    for (int64_t i = 0; i < n_add; ++i) {
+        const int g = add_graph[i];
+        const int k = b->cls[g];
+        const int64_t LL = (int64_t)b->n_labels[g] * b->n_labels[g];
+        b->ed_idx[k].push_back(i);
+        b->ed_s[k].push_back(src[i] + b->site_off[g]);
+        b->ed_t[k].push_back(dst[i] + b->site_off[g]);
+        std::memcpy(b->ed_p[k].data() + pos[k], pair_log + poff, (size_t)LL * sizeof(float));
+        pos[k] += LL;
+        poff += LL;
+    }
+    for (int k = 0; k < K; ++k) {
+        if (b->ed_rm[k].empty() && b->ed_idx[k].empty()) continue;
+        std::vector<int64_t>& ids = b->ed_ids[k];
+        mrf_status st = mrf_edit_factors(b->h[k], (int64_t)b->ed_rm[k].size(), b->ed_rm[k].data(),
+                                         (int64_t)b->ed_idx[k].size(), b->ed_s[k].data(), b->ed_t[k].data(),
+                                         b->ed_p[k].data(), ids.data(), MRF_PTR_HOST);
         if (st != MRF_OK) return class_status(b, k, st);
-        for (size_t j = 0; j < ids.size(); ++j) out_slots[idx[k][j]] = ids[j];
+        for (size_t j = 0; j < ids.size(); ++j) out_slots[b->ed_idx[k][j]] = ids[j];
     }
     return MRF_OK;
 }
