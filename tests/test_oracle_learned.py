@@ -54,8 +54,9 @@ def test_bf16_rounding():
     assert abs(r[3] + 3.140625) < 1e-12
 
 
-def _learned_kernel(model, dec, block_of_site, params):
-    """Exact K(x, x') of one learned sweep over all labelings."""
+def _learned_kernel(model, dec, block_of_site, params, drop_q_ratio=False):
+    """Exact K(x, x') of one learned sweep over all labelings.  drop_q_ratio:
+    plant the mistake of accepting with pi(x') / pi(x) alone."""
     L, N = model.n_labels, model.n_vars
     X_all = brute.all_labelings(N, L)
     members = ln.block_members(block_of_site)
@@ -95,7 +96,8 @@ def _learned_kernel(model, dec, block_of_site, params):
                         xp = xx.copy(); xp[m] = lab
                         lq_new = lq[np.arange(len(m)), lab].sum()
                         lp_new = ln.block_log_target(phi, w, members, lists, xp[None], b)[0]
-                        a = min(1.0, np.exp(lp_new - lp_cur + lq_cur - lq_new))
+                        q_term = 0.0 if drop_q_ratio else lq_cur - lq_new
+                        a = min(1.0, np.exp(lp_new - lp_cur + q_term))
                         pm = np.exp(lq_new) * a
                         stay -= pm
                         new.append((xp, pr * pm))
@@ -135,3 +137,14 @@ def test_learned_sweep_draws_follow_definition():
             if not out["accepted"][b, c]:
                 assert np.array_equal(out["x"][c, m], x[c, m])
     assert not out["theta"][:, ln.intra_mask(dec.src, dec.dst, bos), :].any()
+
+
+def test_planted_acceptance_without_proposal_ratio_breaks_stationarity():
+    model = wl.tiny_potts(4, 3, 3, seed=2, beta_max=1.2)
+    block_of_site = np.array([0, 0, 1, 1])
+    dec = dc.decompose(model)
+    params = _rand_params(model.n_labels, 5, seed=9)
+    _, K = _learned_kernel(model, dec, block_of_site, params, drop_q_ratio=True)
+    _, p, _ = brute.exact_distribution(model)
+    np.testing.assert_allclose(K.sum(axis=1), 1.0, atol=1e-12)
+    assert np.abs(p @ K - p).max() > 1e-4
