@@ -132,6 +132,12 @@ def kernel_work(name, model_info, C):
     return 0, 0
 
 
+# DRAM bytes of the dual step (k_dual + k_dual_ties) per (edge, chain) item,
+# from the ncu capture of the 64^3 L = 8, 64-chain case (1,146.5 MB per launch
+# pair for 774,144 x 64 items); traffic grows with the items, so it is scaled
+# to the bench's launch.  Valid for m = 49 entries and 64 chains only.
+DUAL_DRAM_BYTES_PER_ITEM = {(49, 64): 1146.5e6 / (774144 * 64)}
+
 # kernels behind one kernel-timing record of the library
 KERNELS_PER_RECORD = {"k_dual": 2}
 
@@ -222,8 +228,12 @@ def run_ours(args, ws, rank, local):
         philox_measured = None
     if calls and dom in ("k_dual", "k_primal<fused>"):
         alu_peak = alu_peak_philox_calls(peaks.get("sm_max_mhz", 2070.0))
+        per_item = DUAL_DRAM_BYTES_PER_ITEM.get((minfo["m"], C)) if dom == "k_dual" else None
         roof = {"bound": "alu", "achieved": calls / (dom_ms / 1e3) / 1e9, "peak": alu_peak / 1e9,
-                "unit": "G Philox4x32-10 calls/s", "frac": calls / (dom_ms / 1e3) / alu_peak, "traffic": None,
+                "unit": "G Philox4x32-10 calls/s", "frac": calls / (dom_ms / 1e3) / alu_peak,
+                "traffic": per_item * minfo["E"] * C if per_item else None,
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_dual + k_dual_ties at "
+                                   "64^3, scaled by edge x chain items") if per_item else None,
                 "kernel": dom, "peak_source": "derived: 152 SMs x 4 SMSPs x 32 lanes x 2070 MHz / 61.5 fmaheavy-pipe cycles per warp-wide call (ncu counters of the Philox-only kernel)",
                 "hbm_view": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac")},
                 "philox_only_kernel": {"calls_per_s": philox_measured,
