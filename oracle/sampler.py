@@ -93,23 +93,27 @@ def inverse_cdf(logp, u):
     return np.where(hit.any(axis=-1), first, last_pos), cdf
 
 
-def site_uniforms(n_vars: int, n_chains: int, sweep: int, seed: int, phase=ph.PH_PRIMAL):
-    return ph.site_uniform(np.arange(n_vars)[None, :], np.arange(n_chains)[:, None], sweep, seed, phase)
+def site_uniforms(n_vars: int, n_chains: int, sweep: int, seed: int, phase=ph.PH_PRIMAL, site_ids=None):
+    v = np.arange(n_vars) if site_ids is None else np.asarray(site_ids, np.int64)
+    return ph.site_uniform(v[None, :], np.arange(n_chains)[:, None], sweep, seed, phase)
 
 
-def primal_step(dec: Decomposition, theta, sweep: int, seed: int):
-    """x ~ p(x | theta): returns labels [C][N], log p [C][N][L], uniforms, cdf."""
+def primal_step(dec: Decomposition, theta, sweep: int, seed: int, site_ids=None):
+    """x ~ p(x | theta): returns labels [C][N], log p [C][N][L], uniforms, cdf.
+    site_ids are the RNG indices of the sites (default 0..N-1)."""
     F = primal_field(dec, theta)
     logp = log_softmax(F)
-    u = site_uniforms(F.shape[1], F.shape[0], sweep, seed)
+    u = site_uniforms(F.shape[1], F.shape[0], sweep, seed, site_ids=site_ids)
     x, cdf = inverse_cdf(logp, u)
     return x, logp, u, cdf
 
 
-def sweep(dec: Decomposition, x, sweep_index: int, seed: int, edge_ids=None):
-    """One sweep from labels x: theta | x, then x | theta.  Returns a dict."""
+def sweep(dec: Decomposition, x, sweep_index: int, seed: int, edge_ids=None, site_ids=None):
+    """One sweep from labels x: theta | x, then x | theta.  Returns a dict.
+    edge_ids / site_ids: RNG indices of the edges / sites (a sub-model of a
+    larger one draws what the larger model draws for the same edges / sites)."""
     theta, p_dual, u_dual = dual_step(dec, x, sweep_index, seed, edge_ids)
-    x_new, logp, u_site, cdf = primal_step(dec, theta, sweep_index, seed)
+    x_new, logp, u_site, cdf = primal_step(dec, theta, sweep_index, seed, site_ids)
     return dict(x=x_new, theta=theta, p_dual=p_dual, u_dual=u_dual, logp=logp, u_site=u_site, cdf=cdf)
 
 

@@ -30,6 +30,31 @@ def _gpu():
     torch.cuda.set_device(0)
 
 
+def _no_edges():
+    rng = np.random.default_rng(21)
+    return wl.Model(n_vars=37, n_labels=3, unary=rng.normal(size=(37, 3)).astype(np.float32),
+                    src=np.zeros(0, np.int32), dst=np.zeros(0, np.int32), pair=np.zeros((0, 3, 3), np.float32),
+                    name="no_edges")
+
+
+def _constant_tables():
+    m = wl.random_graph(60, k=2, L=3, seed=22)
+    m.pair[:] = 0.0                      # every entry l = 0: no dual variable at all
+    return m
+
+
+def _isolated_sites():
+    return wl.tiny_random(80, 4, 30, seed=23)          # most sites have no edge
+
+
+def _star(n_leaves=700, L=3, seed=24):
+    rng = np.random.default_rng(seed)
+    src = np.zeros(n_leaves, np.int32)
+    dst = np.arange(1, n_leaves + 1, dtype=np.int32)
+    return wl.Model(n_vars=n_leaves + 1, n_labels=L, unary=rng.normal(size=(n_leaves + 1, L)).astype(np.float32),
+                    src=src, dst=dst, pair=rng.normal(0, 0.3, size=(n_leaves, L, L)).astype(np.float32), name="star")
+
+
 CASES = {
     "ising32": (lambda: wl.ising_grid(32, 32, seed=0), 1),
     "potts3d_L8": (lambda: wl.potts_grid3d(13, 11, 9, L=8, seed=1), 64),
@@ -40,7 +65,40 @@ CASES = {
     # chains a multiple of 32 (warp-per-site primal): degree > 32 (two-sum flush), and L = 16
     "dense_L4_C32": (lambda: wl.dense_potts(120, L=4, seed=8), 32),
     "random_L16_C32": (lambda: wl.random_graph(60, k=2, L=16, seed=9, w_std=0.3), 32),
+    # degenerate models
+    "no_edges": (_no_edges, 4),
+    "constant_tables": (_constant_tables, 32),
+    "isolated_sites": (_isolated_sites, 7),
+    "potts_L16_diag": (lambda: wl.tiny_potts(40, 16, 90, seed=25), 32),
+    "star_degree700": (_star, 32),
 }
+
+
+@pytest.mark.parametrize("name", ["star_degree700", "dense_L4_C32", "random_L3_dup"])
+def test_cta_schedule_matches_oracle(name):
+    model, C = CASES[name][0](), CASES[name][1]
+    seed, t = 77, 5
+    dec = dc.decompose(model)
+    x0 = np.random.default_rng(12).integers(0, model.n_labels, size=(C, model.n_vars))
+    h = make_handle(model, C, seed, record_logp=True, schedule=2)
+    h.set_labels(x0.astype(np.uint8))
+    h.set_sweep_index(t)
+    h.sweep(1, M.MODE_PLAIN)
+    assert h.info().schedule == 2
+    lp, _ = h.debug_logp()
+    ref = sampler.sweep(dec, x0, t, seed)
+    compare_sweep(dec, ref, h.get_labels(), lp, M.unpack_theta(h.debug_theta(), dec.n_entries))
+    h.close()
+
+
+def test_edges_times_chains_limit():
+    # E x C must stay below 2^32 (item indices are 32-bit): 4096 edges x 2^20 chains is refused
+    model = wl.tiny_random(10, 2, 4096, seed=26, allow_duplicates=True)
+    h = M.MRF(10, 2, 1 << 20, seed=0)
+    with pytest.raises(M.MrfError) as e:
+        h.set_factors(model.unary, model.src, model.dst, model.pair)
+    assert e.value.status == M.MRF_ERANGE
+    h.close()
 
 
 @pytest.mark.parametrize("name", list(CASES))

@@ -112,3 +112,25 @@ def test_inverse_cdf_rule():
     # rounding leaves none: pick the largest label with p > 0
     x, _ = sampler.inverse_cdf(np.log(np.array([[0.5, 0.5 - 1e-9, 0.0]])), np.array([0.9999999999]))
     assert x[0] == 1
+
+
+def test_sub_model_sweep_equals_full_sweep_at_sampled_sites():
+    """A sweep of the sampled sites' incident edges (with the full model's edge
+    slots and site ids as RNG indices) draws exactly the full sweep's labels at
+    those sites: a site's conditional involves only its incident edges."""
+    model = wl.potts_grid3d(7, 6, 5, L=4, seed=3)
+    dec = dc.decompose(model)
+    C, seed, t = 3, 11, 4
+    x0 = np.random.default_rng(2).integers(0, 4, size=(C, model.n_vars))
+    full = sampler.sweep(dec, x0, t, seed)
+    sites = np.sort(np.random.default_rng(4).choice(model.n_vars, size=25, replace=False))
+    eids = np.nonzero(np.isin(model.src, sites) | np.isin(model.dst, sites))[0]
+    local = np.unique(np.concatenate([sites, model.src[eids], model.dst[eids]]))
+    sub = wl.Model(n_vars=len(local), n_labels=4, unary=model.unary[local],
+                   src=np.searchsorted(local, model.src[eids]).astype(np.int32),
+                   dst=np.searchsorted(local, model.dst[eids]).astype(np.int32), pair=model.pair[eids])
+    ref = sampler.sweep(dc.decompose(sub), x0[:, local], t, seed, edge_ids=eids, site_ids=local)
+    pos = np.searchsorted(local, sites)
+    assert np.array_equal(ref["x"][:, pos], full["x"][:, sites])
+    np.testing.assert_allclose(ref["logp"][:, pos], full["logp"][:, sites], rtol=0, atol=1e-12)
+    assert np.array_equal(ref["theta"], full["theta"][:, eids])
