@@ -24,19 +24,31 @@ __global__ void k_splash_offset(SweepArgs a) {
 // out[b] = log sum_a exp(bel[a] + psi[b][a]) - max_b(...)  (message to the
 // parent with label b).  Subtracting the maximum over b keeps beliefs of the
 // size of one node's potentials however large the subtree; a constant shift
-// of a message changes no conditional.
+// of a message changes no conditional.  psi rows are read as 16-byte vectors
+// when L is a multiple of 4.
 template <int L>
 __device__ __forceinline__ void tree_message(const float (&bel)[L], const float* __restrict__ psi, float (&out)[L]) {
     float top = -INFINITY;
 #pragma unroll
     for (int b = 0; b < L; ++b) {
         float t[L];
+        if (L % 4 == 0) {
+            const float4* r4 = reinterpret_cast<const float4*>(psi + b * L);
+#pragma unroll
+            for (int q = 0; q < L / 4; ++q) {
+                const float4 v = __ldg(r4 + q);
+                t[4 * q + 0] = bel[4 * q + 0] + v.x;
+                t[4 * q + 1] = bel[4 * q + 1] + v.y;
+                t[4 * q + 2] = bel[4 * q + 2] + v.z;
+                t[4 * q + 3] = bel[4 * q + 3] + v.w;
+            }
+        } else {
+#pragma unroll
+            for (int x = 0; x < L; ++x) t[x] = bel[x] + __ldg(psi + b * L + x);
+        }
         float mx = -INFINITY;
 #pragma unroll
-        for (int x = 0; x < L; ++x) {
-            t[x] = bel[x] + __ldg(psi + b * L + x);
-            mx = fmaxf(mx, t[x]);
-        }
+        for (int x = 0; x < L; ++x) mx = fmaxf(mx, t[x]);
         float s = 0.0f;
 #pragma unroll
         for (int x = 0; x < L; ++x) s += expf(t[x] - mx);
@@ -107,29 +119,49 @@ __global__ void __launch_bounds__(128) k_ffbs(SweepArgs a) {
     auto yedge = [&](int x, int y, int z) -> int64_t { return a.nxe + ((int64_t)z * (ny - 1) + y) * nx + x; };
     auto zedge = [&](int x, int y, int z) -> int64_t { return a.nxe + a.nye + ((int64_t)z * ny + y) * nx + x; };
 
-    // upward pass: beliefs bel_v = phi_v + messages of the children, stored in place
+    // upward pass: beliefs bel_v = phi_v + messages of the children, stored in
+    // place.  Nodes in reverse order i = n-1 .. 0 (i = lx + sx (ly + sy lz));
+    // the next node's potentials are loaded before the current node's message
+    // is computed, so their latency overlaps it.
     float xm[L], ym[L], zm[L];
 #pragma unroll
     for (int x = 0; x < L; ++x) { xm[x] = 0.0f; ym[x] = 0.0f; zm[x] = 0.0f; }
-    for (int lz = sz - 1; lz >= 0; --lz)
-        for (int ly = sy - 1; ly >= 0; --ly)
-            for (int lx = sx - 1; lx >= 0; --lx) {
-                const int X = x0 + lx, Y = y0 + ly, Z = z0 + lz;
-                float* pv = a.pot + site(X, Y, Z) * L * C + c;
-                float bel[L];
+    const int n_nodes = sx * sy * sz;
+    float nxt[L];
+    {
+        const float* pv = a.pot + site(x1 - 1, y1 - 1, z1 - 1) * L * C + c;
 #pragma unroll
-                for (int x = 0; x < L; ++x) {
-                    float f = pv[x * C];
-                    if (lx + 1 < sx) f += xm[x];
-                    if (lx == 0 && ly + 1 < sy) f += ym[x];
-                    if (lx == 0 && ly == 0 && lz + 1 < sz) f += zm[x];
-                    bel[x] = f;
-                    pv[x * C] = f;
-                }
-                if (lx > 0) tree_message<L>(bel, a.resid + xedge(X - 1, Y, Z) * L * L, xm);
-                else if (ly > 0) tree_message<L>(bel, a.resid + yedge(X, Y - 1, Z) * L * L, ym);
-                else if (lz > 0) tree_message<L>(bel, a.resid + zedge(X, Y, Z - 1) * L * L, zm);
-            }
+        for (int x = 0; x < L; ++x) nxt[x] = pv[x * C];
+    }
+    int lx = sx - 1, ly = sy - 1, lz = sz - 1;
+    for (int i = n_nodes - 1; i >= 0; --i) {
+        float bel[L];
+#pragma unroll
+        for (int x = 0; x < L; ++x) bel[x] = nxt[x];
+        const int X = x0 + lx, Y = y0 + ly, Z = z0 + lz;
+        // coordinates of node i - 1
+        int px = lx - 1, py = ly, pz = lz;
+        if (px < 0) { px = sx - 1; if (--py < 0) { py = sy - 1; --pz; } }
+        if (i > 0) {
+            const float* pn = a.pot + site(x0 + px, y0 + py, z0 + pz) * L * C + c;
+#pragma unroll
+            for (int x = 0; x < L; ++x) nxt[x] = pn[x * C];
+        }
+        float* pv = a.pot + site(X, Y, Z) * L * C + c;
+#pragma unroll
+        for (int x = 0; x < L; ++x) {
+            float f = bel[x];
+            if (lx + 1 < sx) f += xm[x];
+            if (lx == 0 && ly + 1 < sy) f += ym[x];
+            if (lx == 0 && ly == 0 && lz + 1 < sz) f += zm[x];
+            bel[x] = f;
+            pv[x * C] = f;
+        }
+        if (lx > 0) tree_message<L>(bel, a.resid + xedge(X - 1, Y, Z) * L * L, xm);
+        else if (ly > 0) tree_message<L>(bel, a.resid + yedge(X, Y - 1, Z) * L * L, ym);
+        else if (lz > 0) tree_message<L>(bel, a.resid + zedge(X, Y, Z - 1) * L * L, zm);
+        lx = px; ly = py; lz = pz;
+    }
     // downward pass: root, then every child given its parent's label
     int xl = 0, yl = 0, zl = 0;
     for (int lz = 0; lz < sz; ++lz)
