@@ -595,8 +595,10 @@ def run_learned_workload(args):
     kt_plain = {k: v[0] / v[1] for k, v in h.kernel_times().items()}
     h.set_kernel_timing(False)
     R = nb * C
-    mlp_flop = 2.0 * R * (256 * 192 + 256 * 256 + 256 * 64)
-    ms_mlp = kt_learned.get("k_gemm_nt (mlp)", float("nan"))
+    Kx = (16 * 4 + 31) // 32 * 32                                 # per-chain first-layer width (couplings folded)
+    mlp_flop = 2.0 * R * (256 * Kx + 256 * 256 + 64 * 256)
+    ms_mlp = next((v for k, v in kt_learned.items() if k.startswith("k_gemm_nt") or "mlp" in k), float("nan"))
+    peaks, peak_src = load_peaks()
     p0, a0 = h.learned_stats()
     h.sweep(4, M.MODE_LEARNED)
     p1, a1 = h.learned_stats()
@@ -639,6 +641,12 @@ def run_learned_workload(args):
                         "loss_first": float(trace[:20].mean()), "loss_last": float(trace[-20:].mean())},
             "kernels_learned_ms": kt_learned, "kernels_plain_ms": kt_plain,
             "mlp_tflops": mlp_flop / (ms_mlp / 1e3) / 1e12 if ms_mlp == ms_mlp else None, "mlp_rows": R,
+            "mlp_path": "fused tcgen05 (tensor memory accumulators, bulk-copied swizzled weights)",
+            "mlp_roofline": {"bound": "tensor", "achieved": mlp_flop / (ms_mlp / 1e3) / 1e12,
+                             "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                             "frac": mlp_flop / (ms_mlp / 1e3) / 1e12 / peaks["bf16_tflops"],
+                             "flop_per_launch": mlp_flop,
+                             "peak_source": f"MEASURED_PEAKS.json bf16_tflops ({peak_src})"} if ms_mlp == ms_mlp else None,
             "reference_sweeps": args.ref_sweeps,
             "statistics": "per chain: fraction of label 0 over 4096 fixed sites; pairwise energy of 50,000 fixed edges",
             "comparison": out}

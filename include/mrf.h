@@ -81,7 +81,11 @@ typedef struct {
                                           events (graphs off); see mrf_kernel_times */
     int32_t exact_edges;               /* 1: keep every edge's exact folded table
                                           (needed by mrf_learned_setup)          */
-    int32_t reserved[6];
+    int32_t mlp_path;                  /* learned proposal MLP: 0 = fused tensor-core
+                                          (tcgen05) kernel when its shapes allow
+                                          (hidden % 64 == 0, <= 256), else 1;
+                                          1 = three mma.sync GEMMs             */
+    int32_t reserved[5];
 } mrf_options;
 
 typedef struct {

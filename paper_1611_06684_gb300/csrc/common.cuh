@@ -144,6 +144,8 @@ struct LearnedArgs {
     float* t_h1; float* t_h2; float* t_z; float* t_dz; float* t_d2; float* t_d1;   // training scratch
     __nv_bfloat16* ds_X; uint8_t* ds_y; uint8_t* ds_n;                               // dataset
     unsigned long long* n_accepted;
+    uint8_t* wimg;                      // swizzled bf16 images of W1x, W2, W3 for the tensor-core MLP
+    unsigned* tc_err;                   // set by the tensor-core MLP when a wait timed out
 };
 
 // Kernel launchers (sweep.cu, splash.cu, decompose.cu).  All return cudaGetLastError().
@@ -153,6 +155,11 @@ cudaError_t launch_primal(const SweepArgs& a, int layout, int schedule, cudaStre
 cudaError_t launch_fused(const SweepArgs& a, int layout, int schedule, cudaStream_t s);
 cudaError_t launch_accumulate(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_philox_rate(uint64_t threads, int calls, uint32_t* sink, cudaStream_t s);
+// Tensor-core MLP (mlp_tc.cu)
+bool mlp_tc_supported(const LearnedArgs& a);
+int64_t mlp_tc_image_bytes(int H, int O, int Kx);
+cudaError_t launch_mlp_images(const LearnedArgs& a, cudaStream_t s);
+cudaError_t launch_learned_mlp_tc(const LearnedArgs& a, cudaStream_t s);
 cudaError_t launch_advance(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_splash(const SweepArgs& a, int layout, cudaStream_t s);
 cudaError_t launch_splash_offset(const SweepArgs& a, cudaStream_t s);

@@ -547,6 +547,11 @@ cudaError_t learned_sync_bf16(const LearnedArgs& a, cudaStream_t s) {
     if (a.W1xb) {
         const int64_t nx = (int64_t)a.H * a.Kx;
         k_copy_cols_bf16<<<(unsigned)((nx + 255) / 256), 256, 0, s>>>(a.W1b, a.Dp, kLearnBlock * a.L, a.W1xb, a.Kx, a.H);
+        if (a.wimg) {
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            return launch_mlp_images(a, s);
+        }
     }
     return cudaGetLastError();
 }

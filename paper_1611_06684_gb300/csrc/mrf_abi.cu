@@ -74,6 +74,7 @@ struct mrf {
     int64_t ds_cap = 0, ds_rows = 0;
     double* d_loss = nullptr; int64_t loss_cap = 0;
     __nv_bfloat16* d_W1x = nullptr; __nv_bfloat16* d_cfb = nullptr; float* d_rowbias = nullptr;
+    uint8_t* d_wimg = nullptr; unsigned* d_tc_err = nullptr;    // tensor-core MLP weight images, error flag
     bool rowbias_dirty = true;
     unsigned long long* d_acc = nullptr;
     uint64_t proposed = 0;
@@ -369,7 +370,7 @@ void mrf_destroy(mrf_t* h) {
     dfree(h->d_X); dfree(h->d_H1); dfree(h->d_H2); dfree(h->d_Z); dfree(h->d_w32); dfree(h->d_Wb); dfree(h->d_grad);
     dfree(h->d_m); dfree(h->d_v); dfree(h->d_train); dfree(h->d_bidx); dfree(h->d_bX); dfree(h->d_by); dfree(h->d_bn);
     dfree(h->d_dsX); dfree(h->d_dsy); dfree(h->d_dsn); dfree(h->d_loss); dfree(h->d_acc);
-    dfree(h->d_W1x); dfree(h->d_cfb); dfree(h->d_rowbias);
+    dfree(h->d_W1x); dfree(h->d_cfb); dfree(h->d_rowbias); dfree(h->d_wimg); dfree(h->d_tc_err);
     for (auto& r : h->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : h->pool) cudaEventDestroy(e);
     delete h;
@@ -621,6 +622,8 @@ static mrf_status tune_schedule(mrf_t* h) {
     return MRF_OK;
 }
 
+static bool use_mlp_tc(const mrf_t* h) { return h->opt.mlp_path == 0 && mlp_tc_supported(h->la); }
+
 static mrf_status enqueue_sweep(mrf_t* h, int mode) {
     SweepArgs a = make_args(h);
     cudaStream_t s = h->stream;
@@ -635,7 +638,10 @@ static mrf_status enqueue_sweep(mrf_t* h, int mode) {
         e = timed(h, MRF_K_DUAL, [&] { return launch_dual(a, h->layout, s); });
         if (e == cudaSuccess) e = timed(h, MRF_K_POTENTIAL, [&] { return launch_potential(a, h->layout, s); });
         if (e == cudaSuccess) e = timed(h, MRF_K_FEATURES, [&] { return launch_learned_features(h->la, a, s); });
-        if (e == cudaSuccess) e = timed(h, MRF_K_MLP, [&] { return launch_learned_mlp_blocks(h->la, s); });
+        if (e == cudaSuccess)
+            e = timed(h, MRF_K_MLP, [&] {
+                return use_mlp_tc(h) ? launch_learned_mlp_tc(h->la, s) : launch_learned_mlp_blocks(h->la, s);
+            });
         if (e == cudaSuccess) e = timed(h, MRF_K_MH, [&] { return launch_learned_mh(h->la, a, s); });
     } else {
         a.splash = 1;
@@ -689,7 +695,15 @@ mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode) {
         }
     }
     h->sweep_host += n_sweeps;
-    if (mode == MRF_MODE_LEARNED) h->proposed += (uint64_t)n_sweeps * h->la.nb * h->C;
+    if (mode == MRF_MODE_LEARNED) {
+        h->proposed += (uint64_t)n_sweeps * h->la.nb * h->C;
+        if (use_mlp_tc(h) && n_sweeps > 0) {                 // a bounded wait of the tensor-core MLP gave up
+            unsigned err = 0;
+            MRF_CUDA(h, cudaMemcpyAsync(&err, h->d_tc_err, sizeof(err), cudaMemcpyDeviceToHost, h->stream));
+            MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+            if (err) return fail(h, MRF_ETIMEOUT, "tensor-core MLP: a wait timed out");
+        }
+    }
     return MRF_OK;
 }
 
@@ -1221,6 +1235,9 @@ mrf_status mrf_learned_setup(mrf_t* h, const int32_t* block_of_site, int32_t hid
     MRF_CUDA(h, dalloc(h->d_m, (size_t)h->n_params)); MRF_CUDA(h, dalloc(h->d_v, (size_t)h->n_params));
     MRF_CUDA(h, dalloc(h->d_Wb, (size_t)(H * Dp + H * H + O * H)));
     MRF_CUDA(h, dalloc(h->d_acc, 1));
+    MRF_CUDA(h, dalloc(h->d_wimg, (size_t)mlp_tc_image_bytes(H, O, a.Kx)));
+    MRF_CUDA(h, dalloc(h->d_tc_err, 1));
+    MRF_CUDA(h, cudaMemsetAsync(h->d_tc_err, 0, sizeof(unsigned), h->stream));
     if (!h->d_pot) MRF_CUDA(h, dalloc(h->d_pot, (size_t)N * L * C));
     MRF_CUDA(h, to_device(h->d_members, members.data(), (int64_t)members.size(), MRF_PTR_HOST, h->stream));
     MRF_CUDA(h, to_device(h->d_nmem, nmem.data(), nb, MRF_PTR_HOST, h->stream));
@@ -1250,6 +1267,7 @@ mrf_status mrf_learned_setup(mrf_t* h, const int32_t* block_of_site, int32_t hid
     a.grad = h->d_grad; a.adam_m = h->d_m; a.adam_v = h->d_v; a.n_accepted = h->d_acc;
     a.ds_X = h->d_dsX; a.ds_y = h->d_dsy; a.ds_n = h->d_dsn;
     a.W1xb = h->d_W1x; a.cfb = h->d_cfb; a.rowbias = h->d_rowbias;
+    a.wimg = h->d_wimg; a.tc_err = h->d_tc_err;
     MRF_CUDA(h, learned_sync_bf16(a, h->stream));
     MRF_CUDA(h, launch_learned_couplings(a, h->d_resid, h->d_cf, h->stream));
     h->rowbias_dirty = true;

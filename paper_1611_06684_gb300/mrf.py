@@ -24,13 +24,14 @@ MODE_PLAIN, MODE_FUSED, MODE_SPLASH, MODE_LEARNED = 0, 1, 2, 3
 LAYOUT_PIVOT, LAYOUT_DIAG = 0, 1
 K_DUAL, K_PRIMAL, K_FUSED, K_POTENTIAL, K_FFBS, K_ACCUMULATE, K_FEATURES, K_MLP, K_MH, K_COUNT = range(10)
 KERNEL_NAMES = ["k_dual", "k_primal", "k_primal<fused>", "k_potential", "k_ffbs", "k_accumulate",
-                "k_learned_features", "k_gemm_nt (mlp)", "k_learned_mh"]
+                "k_learned_features", "k_mlp", "k_learned_mh"]
 
 
 class mrf_options(ct.Structure):
     _fields_ = [("grid_nx", ct.c_int32), ("grid_ny", ct.c_int32), ("grid_nz", ct.c_int32),
                 ("record_logp", ct.c_int32), ("use_graphs", ct.c_int32), ("schedule", ct.c_int32),
-                ("kernel_timing", ct.c_int32), ("exact_edges", ct.c_int32), ("reserved", ct.c_int32 * 6)]
+                ("kernel_timing", ct.c_int32), ("exact_edges", ct.c_int32), ("mlp_path", ct.c_int32),
+                ("reserved", ct.c_int32 * 5)]
 
 
 class mrf_info(ct.Structure):
@@ -147,7 +148,7 @@ class MRF:
 
     def __init__(self, n_vars: int, n_labels: int, n_chains: int, seed: int = 0, grid=None,
                  record_logp: bool = False, use_graphs: bool = True, schedule: int = 0, stream=None,
-                 kernel_timing: bool = False, exact_edges: bool = False):
+                 kernel_timing: bool = False, exact_edges: bool = False, mlp_path: int = 0):
         lib = load()
         opt = mrf_options()
         lib.mrf_default_options(ct.byref(opt))
@@ -158,6 +159,7 @@ class MRF:
         opt.schedule = int(schedule)
         opt.kernel_timing = int(kernel_timing)
         opt.exact_edges = int(exact_edges)
+        opt.mlp_path = int(mlp_path)
         self.stream = _current_stream() if stream is None else int(stream)
         h = _P()
         st = lib.mrf_create(ct.byref(h), n_vars, n_labels, n_chains, ct.c_uint64(seed & (2**64 - 1)), ct.byref(opt),

@@ -35,8 +35,9 @@ def _params(L, hidden, seed, bias_scale=0.1):
     return p
 
 
-def _setup(model, C, seed, hidden, bos, wseed=5):
-    h = M.MRF(model.n_vars, model.n_labels, C, seed=seed, exact_edges=True, use_graphs=False, record_logp=False)
+def _setup(model, C, seed, hidden, bos, wseed=5, mlp_path=0):
+    h = M.MRF(model.n_vars, model.n_labels, C, seed=seed, exact_edges=True, use_graphs=False, record_logp=False,
+              mlp_path=mlp_path)
     h.set_factors(model.unary, model.src, model.dst, model.pair)
     h.learned_setup(bos, hidden=hidden, seed=1)
     params = _params(model.n_labels, hidden, wseed)
@@ -78,6 +79,32 @@ def test_training_gradients_match_oracle():
         gg = g[off:off + n].reshape(gr.shape)
         off += n
         assert np.abs(gg - gr).max() <= 1e-2 * max(np.abs(gr).max(), 1e-6)
+
+
+@pytest.mark.parametrize("L,hidden", [(4, 256), (3, 64), (2, 128)])
+def test_tensor_core_mlp_matches_gemm_path(L, hidden):
+    """The fused tcgen05 MLP and the three mma.sync GEMMs give the same logits
+    from the same features (several 128-row tiles, a partial last tile)."""
+    model = wl.ba_potts(1500, m=5, L=L, seed=11)
+    bos = wl.bfs_blocks(model, 16, seed=3)
+    C, seed, t = 24, 4, 9
+    x0 = np.random.default_rng(8).integers(0, L, size=(C, model.n_vars)).astype(np.uint8)
+    out = []
+    for path in (0, 1):
+        h, _ = _setup(model, C, seed, hidden, bos, mlp_path=path)
+        h.set_labels(x0)
+        h.set_sweep_index(t)
+        h.sweep(1, M.MODE_LEARNED)
+        nb = int(bos.max()) + 1
+        d, dp = ln.feature_width(L)
+        out.append(h.learned_debug(nb * C, dp, 16 * L))
+        h.close()
+    (X0, z0), (X1, z1) = out
+    assert np.array_equal(X0, X1)
+    assert nb * C > 256
+    err = np.abs(z0 - z1) / np.maximum(1.0, np.abs(z1))
+    assert err.max() < 2e-2, err.max()
+    assert np.median(err) < 1e-5, np.median(err)
 
 
 def test_learned_sweep_matches_oracle():
