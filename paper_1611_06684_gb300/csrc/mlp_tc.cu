@@ -380,12 +380,41 @@ __device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, ui
         : "memory");
 }
 
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};"
+        ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+          "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
+// 16-byte asynchronous global -> shared copy; src_bytes = 0 fills zeros.
+__device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
 namespace tcr {
-constexpr int THREADS = 256;
+constexpr int THREADS = 512;               // four warps per 32-lane quarter of tensor memory
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACOL = 256;            // first column of the A operand
-constexpr int MAX_W_BYTES = 200 * 1024;
+constexpr int MAX_SMEM = 220 * 1024;      // weights + X staging
 }  // namespace tcr
+
+// Stage the X rows of tile t (row-major, Kxp bf16 per row, zero padded) with
+// cp.async; every thread issues its share of the 16-byte pieces.
+__device__ __forceinline__ void stage_x(const MlpTc& p, int64_t t, uint8_t* stage) {
+    const int pieces_per_row = p.Kxp / 8;
+    const int pieces = 128 * pieces_per_row;
+    for (int i = threadIdx.x; i < pieces; i += blockDim.x) {
+        const int rr = i / pieces_per_row, c8 = i - rr * pieces_per_row;
+        const int64_t r = t * 128 + rr;
+        const bool in = r < p.R && c8 * 8 < p.Kx;
+        const bf16* src = p.X + (in ? r * (int64_t)p.Kx + c8 * 8 : 0);
+        cp_async16_zfill(smem_u32(stage + (size_t)i * 16), src, in ? 16u : 0u);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
 
 __global__ void __launch_bounds__(tcr::THREADS, 1) k_mlp_tc_resident(const MlpTc p) {
     extern __shared__ uint8_t smem_raw[];
@@ -394,7 +423,8 @@ __global__ void __launch_bounds__(tcr::THREADS, 1) k_mlp_tc_resident(const MlpTc
     uint8_t* w1s = base;
     uint8_t* w2s = w1s + w1b;
     uint8_t* w3s = w2s + w2b;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(w3s + ((w3b + 15) & ~(int64_t)15));    // [0]: weights, [1]: done, [2]: drain
+    uint8_t* stage = w3s + ((w3b + 15) & ~(int64_t)15);             // X rows of the next tile
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stage + 128 * (int64_t)p.Kxp * 2);    // [0]: weights, [1]: done, [2]: drain
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3);
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t wbar = smem_u32(bars), done = smem_u32(bars + 1), drain = smem_u32(bars + 2);
@@ -421,30 +451,31 @@ __global__ void __launch_bounds__(tcr::THREADS, 1) k_mlp_tc_resident(const MlpTc
             for (int64_t o = 0; o < len[k]; o += 32768)
                 bulk_g2s(smem_u32(dst[k] + o), src[k] + o, (uint32_t)std::min<int64_t>(32768, len[k] - o), wbar);
     }
+    const int64_t n_tiles = (p.R + 127) / 128;
+    if (blockIdx.x < n_tiles) stage_x(p, blockIdx.x, stage);
     bool ok = !__syncthreads_or(!mbar_wait(wbar, 0));              // the same verdict in every thread
-    const int row = tid & 127, half = tid >> 7;
+    const int row = tid & 127, quarter = tid >> 7;
     const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;
     const uint32_t acc_addr = tmem + lane, a_addr = tmem + lane + tcr::ACOL;
-    const int64_t n_tiles = (p.R + 127) / 128;
     uint32_t done_phase = 0;
     for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         const int64_t r = t * 128 + row;
-        // X row -> A operand (Kxp / 2 columns; this thread's half of them)
-        {
-            const uint4* xr = reinterpret_cast<const uint4*>(p.X + (r < p.R ? r : 0) * (int64_t)p.Kx);
-            for (int c0 = 32 * half; c0 < p.Kxp / 2; c0 += 64) {          // 32 columns = 64 bf16
-                uint32_t w[32];
+        // staged X rows -> A operand: 16 packed columns (32 bf16) per step, quarters alternate
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        for (int c0 = 16 * quarter; c0 < p.Kxp / 2; c0 += 64) {
+            const uint4* src = reinterpret_cast<const uint4*>(stage + (size_t)row * p.Kxp * 2 + (size_t)c0 * 4);
+            uint32_t w[16];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int e = 2 * c0 + 8 * q;                         // first bf16 element of this 16-byte piece
-                    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                    if (r < p.R && e < p.Kx) v = __ldg(xr + e / 8);
-                    w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
-                }
-                tmem_st32(a_addr + (uint32_t)c0, w);
+            for (int q = 0; q < 4; ++q) {
+                const uint4 v = src[q];
+                w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
             }
-            tmem_st_wait();
+            tmem_st16(a_addr + (uint32_t)c0, w);
         }
+        tmem_st_wait();
+        __syncthreads();                                           // staging read by all before it is refilled
+        if (t + gridDim.x < n_tiles) stage_x(p, t + gridDim.x, stage);
         for (int g = 0; g < 3 && ok; ++g) {
             tc_fence_before();
             __syncthreads();
@@ -466,26 +497,25 @@ __global__ void __launch_bounds__(tcr::THREADS, 1) k_mlp_tc_resident(const MlpTc
             const int N = g < 2 ? p.H : p.O;
             const float* bias = g == 1 ? p.b2 : p.b3;
             if (g == 0) bias = p.rowbias + (int64_t)p.fdC.div((uint32_t)(r < p.R ? r : p.R - 1)) * p.H;
-            // 64 accumulator columns (32 packed A columns) per step, halves of the CTA alternate
-            for (int c0 = 64 * half; c0 < N; c0 += 128) {
-                float v[64];
-                tmem_ld32(acc_addr + (uint32_t)c0, *reinterpret_cast<float(*)[32]>(v));
-                if (c0 + 32 < N) tmem_ld32(acc_addr + (uint32_t)c0 + 32u, *reinterpret_cast<float(*)[32]>(v + 32));
+            // 32 accumulator columns (16 packed A columns) per step, quarters alternate
+            for (int c0 = 32 * quarter; c0 < N; c0 += 128) {
+                float v[32];
+                tmem_ld32(acc_addr + (uint32_t)c0, v);
                 const float4* b4 = reinterpret_cast<const float4*>(bias + c0);
                 if (g < 2) {
-                    uint32_t packed[32];
+                    uint32_t packed[16];
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
+                    for (int q = 0; q < 8; ++q) {
                         const float4 bq = __ldg(b4 + q);
                         __nv_bfloat162 lo = __floats2bfloat162_rn(fmaxf(v[4 * q] + bq.x, 0.0f), fmaxf(v[4 * q + 1] + bq.y, 0.0f));
                         __nv_bfloat162 hi = __floats2bfloat162_rn(fmaxf(v[4 * q + 2] + bq.z, 0.0f), fmaxf(v[4 * q + 3] + bq.w, 0.0f));
                         packed[2 * q] = *reinterpret_cast<uint32_t*>(&lo);
                         packed[2 * q + 1] = *reinterpret_cast<uint32_t*>(&hi);
                     }
-                    tmem_st32(a_addr + (uint32_t)(c0 / 2), packed);
+                    tmem_st16(a_addr + (uint32_t)(c0 / 2), packed);
                 } else if (r < p.R) {
                     float4* zr = reinterpret_cast<float4*>(p.Z + r * (int64_t)p.O + c0);
-                    const int nv = min(64, N - c0) / 4;
+                    const int nv = min(32, N - c0) / 4;
                     for (int q = 0; q < nv; ++q) {
                         const float4 bq = __ldg(b4 + q);
                         zr[q] = make_float4(v[4 * q] + bq.x, v[4 * q + 1] + bq.y, v[4 * q + 2] + bq.z, v[4 * q + 3] + bq.w);
@@ -495,6 +525,7 @@ __global__ void __launch_bounds__(tcr::THREADS, 1) k_mlp_tc_resident(const MlpTc
             if (g < 2) tmem_st_wait();
         }
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     if (__syncthreads_or(!ok)) {
         if (tid == 0) {
             atomicOr(p.err, 1u);
@@ -561,9 +592,10 @@ cudaError_t launch_learned_mlp_tc(const LearnedArgs& a, cudaStream_t s) {
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const int64_t n_tiles = (p.R + tc::TILE_M - 1) / tc::TILE_M;
     const int64_t wbytes = 2 * ((int64_t)p.H * p.Kxp + (int64_t)p.H * p.H + (int64_t)p.O * p.H);
-    if (wbytes <= tcr::MAX_W_BYTES && p.Kxp <= 256 && p.H <= 256) {
+    const int64_t resident_bytes = 1024 + wbytes + 16 + 128 * (int64_t)p.Kxp * 2 + 64;
+    if (resident_bytes <= tcr::MAX_SMEM && p.Kxp <= 256 && p.H <= 256) {
         // at least 120 KB: one CTA (512 TMEM columns) per SM
-        const size_t smem = std::max<size_t>(120 * 1024, 1024 + (size_t)wbytes + 16 + 64);
+        const size_t smem = std::max<size_t>(120 * 1024, (size_t)resident_bytes);
         static int attr_r = 0;
         if ((int)smem > attr_r) {
             e = cudaFuncSetAttribute(k_mlp_tc_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
