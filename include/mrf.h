@@ -277,6 +277,13 @@ mrf_status mrf_learned_stats(mrf_t* h, uint64_t* proposed, uint64_t* accepted);
 /* Features [n_blocks * C][Dp] and logits [n_blocks * C][16 L] of the last learned
  * sweep (host float32; rows b * C + c). */
 mrf_status mrf_learned_debug(mrf_t* h, float* X, float* z);
+/* Test hook for the bounded waits of the tensor-core MLP: with on = 1 the
+ * next learned sweep's MLP kernel does not signal the completion of its first
+ * layer, so its waits run out (after roughly a second); the kernel then
+ * records the timeout, lets its own copies and MMAs finish, frees its tensor
+ * memory and returns, and mrf_sweep returns MRF_ETIMEOUT.  The handle stays
+ * usable.  The hook disarms itself after that sweep. */
+mrf_status mrf_debug_mlp_timeout(mrf_t* h, int32_t on);
 
 /* Capacity, in 32-bit words, of the fixed device array that holds the dual
  * bits of mrf_sweep_noalloc (16 MiB). */

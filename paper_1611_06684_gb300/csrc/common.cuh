@@ -146,6 +146,7 @@ struct LearnedArgs {
     unsigned long long* n_accepted;
     uint8_t* wimg;                      // swizzled bf16 images of W1x, W2, W3 for the tensor-core MLP
     unsigned* tc_err;                   // set by the tensor-core MLP when a wait timed out
+    int32_t tc_inject_timeout;          // test hook: the next tensor-core MLP launch waits on a completion never signalled
 };
 
 // Kernel launchers (sweep.cu, splash.cu, decompose.cu).  All return cudaGetLastError().

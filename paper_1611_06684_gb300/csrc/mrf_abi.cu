@@ -701,7 +701,11 @@ mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode) {
             unsigned err = 0;
             MRF_CUDA(h, cudaMemcpyAsync(&err, h->d_tc_err, sizeof(err), cudaMemcpyDeviceToHost, h->stream));
             MRF_CUDA(h, cudaStreamSynchronize(h->stream));
-            if (err) return fail(h, MRF_ETIMEOUT, "tensor-core MLP: a wait timed out");
+            if (h->la.tc_inject_timeout) { h->la.tc_inject_timeout = 0; drop_graphs(h); }
+            if (err) {
+                MRF_CUDA(h, cudaMemsetAsync(h->d_tc_err, 0, sizeof(unsigned), h->stream));
+                return fail(h, MRF_ETIMEOUT, "tensor-core MLP: a wait timed out");
+            }
         }
     }
     return MRF_OK;
@@ -1406,6 +1410,15 @@ mrf_status mrf_learned_stats(mrf_t* h, uint64_t* proposed, uint64_t* accepted) {
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));
     if (proposed) *proposed = h->proposed;
     if (accepted) *accepted = acc;
+    return MRF_OK;
+}
+
+mrf_status mrf_debug_mlp_timeout(mrf_t* h, int32_t on) {
+    if (!h) return MRF_EINVAL;
+    if (!h->learned) return fail(h, MRF_ESTATE, "mrf_learned_setup first");
+    if (!use_mlp_tc(h)) return fail(h, MRF_ESTATE, "the tensor-core MLP is not in use on this handle");
+    h->la.tc_inject_timeout = on ? 1 : 0;
+    drop_graphs(h);                                         // captured launches carry the hook's old value
     return MRF_OK;
 }
 

@@ -74,6 +74,7 @@ _SIGS = {
     "mrf_learned_forward": (ct.c_int, [_P, _P, ct.c_int32, _P]),
     "mrf_learned_stats": (ct.c_int, [_P, ct.POINTER(ct.c_uint64), ct.POINTER(ct.c_uint64)]),
     "mrf_learned_debug": (ct.c_int, [_P, _P, _P]),
+    "mrf_debug_mlp_timeout": (ct.c_int, [_P, ct.c_int32]),
     "mrf_batch_create": (ct.c_int, [ct.POINTER(_P), ct.c_int32, _P, _P, ct.c_int32, ct.c_uint64,
                                     ct.POINTER(mrf_options), _P]),
     "mrf_batch_set_factors": (ct.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -319,6 +320,10 @@ class MRF:
         X = np.zeros((rows, width), np.float32); z = np.zeros((rows, n_out), np.float32)
         self._check(self.lib.mrf_learned_debug(self.h, X.ctypes.data, z.ctypes.data))
         return X, z
+
+    def debug_mlp_timeout(self, on: bool = True):
+        """Arm the tensor-core MLP's timeout test hook for the next learned sweep."""
+        self._check(self.lib.mrf_debug_mlp_timeout(self.h, int(bool(on))))
 
     def set_kernel_timing(self, on: bool):
         self._check(self.lib.mrf_set_kernel_timing(self.h, int(bool(on))))

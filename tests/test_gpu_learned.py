@@ -187,3 +187,28 @@ def test_training_reduces_loss_and_raises_acceptance():
     after = acceptance(4)
     print("acceptance before", before, "after", after, "loss", trace[:5], trace[-5:])
     assert after > before + 0.05
+
+
+def test_tensor_core_mlp_wait_timeout_is_reported_and_recoverable():
+    """A completion that is never signalled (test hook) makes the MLP kernel's
+    bounded waits run out: the sweep reports MRF_ETIMEOUT, and the handle and
+    the CUDA context keep working (the next sweep matches a fresh handle's)."""
+    model = wl.ba_potts(600, m=5, L=4, seed=13)
+    bos = wl.bfs_blocks(model, 16, seed=2)
+    C, seed = 8, 3
+    h, params = _setup(model, C, seed, 128, bos)
+    ref, _ = _setup(model, C, seed, 128, bos)
+    x0 = np.random.default_rng(1).integers(0, 4, size=(C, model.n_vars)).astype(np.uint8)
+    for hh in (h, ref):
+        hh.set_labels(x0)
+        hh.set_sweep_index(40)
+    h.debug_mlp_timeout(True)
+    with pytest.raises(M.MrfError) as e:
+        h.sweep(1, M.MODE_LEARNED)
+    assert e.value.status == M.MRF_ETIMEOUT
+    h.set_labels(x0)
+    h.set_sweep_index(40)
+    h.sweep(1, M.MODE_LEARNED)
+    ref.sweep(1, M.MODE_LEARNED)
+    assert np.array_equal(h.get_labels(), ref.get_labels())
+    h.close(); ref.close()
