@@ -178,6 +178,18 @@ mrf_status mrf_kernel_times(mrf_t* h, double* ms, int64_t* launches);
  * integer-ALU roof of the dual step. */
 mrf_status mrf_philox_rate(uint64_t threads, int32_t calls, void* cuda_stream, double* calls_per_s);
 
+/* Estimator of the log-partition function (Section 5.2).  Runs n_sweeps plain
+ * sweeps from the current state and, after each, writes for every chain c
+ *   log_v[i * C + c] = log p~(x) - sum_v log p(x_v | theta)
+ * = log V(x, theta) of the sweep's duals theta and new labels x, with p~ the
+ * model's unnormalised density exp(sum u + sum w).  At stationarity
+ * E[V] = Z and E[log V] <= log Z (the gap is the mutual information of x and
+ * theta): the mean of log_v is a lower bound on log Z and log(mean(exp(log_v)))
+ * an unbiased-in-Z estimate.  log_v: host float64 [n_sweeps][C].  Needs the
+ * exact edge tables (options.grid or options.exact_edges), else MRF_ESTATE.
+ * The sweeps advance the chains and the marginal counts like mrf_sweep. */
+mrf_status mrf_estimate_log_partition(mrf_t* h, int32_t n_sweeps, double* log_v);
+
 /* Switch options.kernel_timing on (1) or off (0) for later sweeps. */
 mrf_status mrf_set_kernel_timing(mrf_t* h, int32_t on);
 

@@ -91,6 +91,7 @@ struct SweepArgs {
     uint32_t* theta;           // [E][C][W]
     uint32_t* counts;          // [N][L]
     float* logp;               // [C][N][L] or null
+    float* lpv;                // [N][C] log p of each drawn label (log-partition estimator) or null
     Ctl* ctl;
     uint2 key;
     RoundKeys rk;              // Philox round keys of `key`
@@ -156,6 +157,7 @@ cudaError_t launch_primal(const SweepArgs& a, int layout, int schedule, cudaStre
 cudaError_t launch_fused(const SweepArgs& a, int layout, int schedule, cudaStream_t s);
 cudaError_t launch_accumulate(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_philox_rate(uint64_t threads, int calls, uint32_t* sink, cudaStream_t s);
+cudaError_t launch_log_v(const SweepArgs& a, const double* ut, double* out, cudaStream_t s);
 // Tensor-core MLP (mlp_tc.cu)
 bool mlp_tc_supported(const LearnedArgs& a);
 int64_t mlp_tc_image_bytes(int H, int O, int Kx);

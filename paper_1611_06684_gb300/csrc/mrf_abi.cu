@@ -36,6 +36,10 @@ struct mrf {
     int2* d_inc = nullptr;
     uint8_t* d_x = nullptr;
     uint32_t* d_theta = nullptr;
+    float* d_lpv = nullptr;            // [N][C] log p of the drawn labels (log-partition estimator)
+    double* d_logv = nullptr;          // [sweeps][C] log V of the estimator
+    int64_t logv_cap = 0;
+    bool lpv_on = false;
     uint16_t* d_ties = nullptr;        // deferred dual ties [dual warps][tie_cap]
     uint8_t* d_tie_count = nullptr;    // [dual warps]
     uint32_t* d_counts = nullptr;
@@ -157,6 +161,7 @@ SweepArgs make_args(const mrf_t* h) {
     a.inc_ptr = h->d_inc_ptr; a.inc = h->d_inc; a.ut = h->d_ut;
     a.x = h->d_x; a.theta = h->d_theta; a.counts = h->d_counts; a.logp = h->d_logp;
     a.ties = h->d_ties; a.tie_count = h->d_tie_count; a.tie_cap = tie_cap_for(h->M);
+    a.lpv = h->lpv_on ? h->d_lpv : nullptr;
     a.ctl = h->d_ctl; a.key = h->key;
     a.rk = round_keys(h->key);
     a.fdC = FastDiv::make((uint32_t)h->C);
@@ -363,7 +368,7 @@ void mrf_destroy(mrf_t* h) {
     drop_graphs(h);
     dfree(h->d_unary); dfree(h->d_ut); dfree(h->d_utf); dfree(h->d_tpl); dfree(h->d_src); dfree(h->d_dst); dfree(h->d_tau); dfree(h->d_thr);
     dfree(h->d_fold); dfree(h->d_cst); dfree(h->d_resid); dfree(h->d_inc_ptr); dfree(h->d_inc); dfree(h->d_x);
-    dfree(h->d_theta); dfree(h->d_ties); dfree(h->d_tie_count); dfree(h->d_counts); dfree(h->d_logp); dfree(h->d_ctl); dfree(h->d_flag); dfree(h->d_stage); dfree(h->d_pot);
+    dfree(h->d_theta); dfree(h->d_ties); dfree(h->d_tie_count); dfree(h->d_counts); dfree(h->d_lpv); dfree(h->d_logv); dfree(h->d_logp); dfree(h->d_ctl); dfree(h->d_flag); dfree(h->d_stage); dfree(h->d_pot);
     dfree(h->d_csr_work); dfree(h->d_csr_sums);
     dfree(h->d_ed_pair); dfree(h->d_ed_slots); dfree(h->d_ed_new); dfree(h->d_ed_s); dfree(h->d_ed_t);
     dfree(h->d_members); dfree(h->d_nmem); dfree(h->d_intra_ptr); dfree(h->d_intra); dfree(h->d_cf); dfree(h->d_skip);
@@ -708,6 +713,39 @@ mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode) {
             }
         }
     }
+    return MRF_OK;
+}
+
+mrf_status mrf_estimate_log_partition(mrf_t* h, int32_t n_sweeps, double* log_v) {
+    if (!h || n_sweeps < 0 || (n_sweeps > 0 && !log_v)) return MRF_EINVAL;
+    if (!h->has_factors) return fail(h, MRF_ESTATE, "mrf_set_factors first");
+    if (!h->d_resid) return fail(h, MRF_ESTATE, "the estimator needs exact edge tables (options.grid or options.exact_edges)");
+    if (n_sweeps == 0) return MRF_OK;
+    if (h->schedule == 0) {
+        mrf_status st = tune_schedule(h);
+        if (st != MRF_OK) return st;
+    }
+    if (!h->d_lpv) MRF_CUDA(h, dalloc(h->d_lpv, (size_t)h->N * h->C));
+    if ((int64_t)n_sweeps * h->C > h->logv_cap) {
+        MRF_CUDA(h, dalloc(h->d_logv, (size_t)n_sweeps * h->C));
+        h->logv_cap = (int64_t)n_sweeps * h->C;
+    }
+    MRF_CUDA(h, cudaMemsetAsync(h->d_logv, 0, sizeof(double) * (size_t)n_sweeps * h->C, h->stream));
+    h->lpv_on = true;
+    mrf_status st = MRF_OK;
+    for (int i = 0; i < n_sweeps && st == MRF_OK; ++i) {
+        st = enqueue_sweep(h, MRF_MODE_PLAIN);                  // not from a graph: the launches carry lpv
+        if (st == MRF_OK) {
+            cudaError_t e = launch_log_v(make_args(h), h->d_ut, h->d_logv + (int64_t)i * h->C, h->stream);
+            if (e != cudaSuccess) { cudaGetLastError(); st = fail(h, MRF_ECUDA, std::string("log V: ") + cudaGetErrorString(e)); }
+        }
+        if (st == MRF_OK) h->sweep_host++;
+    }
+    h->lpv_on = false;
+    if (st != MRF_OK) return st;
+    MRF_CUDA(h, cudaMemcpyAsync(log_v, h->d_logv, sizeof(double) * (size_t)n_sweeps * h->C, cudaMemcpyDeviceToHost,
+                                h->stream));
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
     return MRF_OK;
 }
 

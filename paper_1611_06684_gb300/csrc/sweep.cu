@@ -137,6 +137,60 @@ cudaError_t launch_philox_rate(uint64_t threads, int calls, uint32_t* sink, cuda
     return cudaGetLastError();
 }
 
+// log V of Section 5.2 for every chain after a plain sweep (a.lpv recorded by
+// the primal step): out[c] += sum_v (u~_v(x_v) - log p(x_v | theta))
+//                            + sum_e psi_e(x_s, x_t),
+// psi = w - fold_s - fold_t the exact edge tables (so that sum_v u~ + sum_e psi
+// = sum_v u + sum_e w = log p~(x)).  The item stride is a multiple of C, so a
+// thread always sums one chain; per-chain partials meet in shared memory
+// (float64) and then in out[c].
+__global__ void k_log_v(SweepArgs a, const double* __restrict__ ut, double* __restrict__ out, int64_t stride) {
+    extern __shared__ double s_acc[];
+    const bool use_smem = a.C <= 4096;
+    if (use_smem) {
+        for (int i = threadIdx.x; i < a.C; i += blockDim.x) s_acc[i] = 0.0;
+        __syncthreads();
+    }
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int c = (int)(g % a.C);
+    const uint8_t* x = a.x + (size_t)((uint32_t)a.ctl->sweep & 1u) * a.N * a.C;
+    double acc = 0.0;
+    const int64_t nsite = (int64_t)a.N * a.C, nedge = a.E * a.C;
+    for (int64_t i = g; i < nsite; i += stride) {
+        const int64_t v = i / a.C;
+        acc += ut[v * a.L + x[i]] - (double)a.lpv[i];
+    }
+    for (int64_t i = g; i < nedge; i += stride) {
+        const int64_t e = i / a.C;
+        const int s = a.src[e];
+        if (s < 0) continue;
+        const int t = a.dst[e];
+        acc += (double)a.resid[(e * a.L + x[(int64_t)s * a.C + c]) * a.L + x[(int64_t)t * a.C + c]];
+    }
+    if (use_smem) {
+        atomicAdd(&s_acc[c], acc);
+        __syncthreads();
+        for (int i = threadIdx.x; i < a.C; i += blockDim.x) atomicAdd(&out[i], s_acc[i]);
+    } else {
+        atomicAdd(&out[c], acc);
+    }
+}
+
+static int64_t gcd64(int64_t p, int64_t q) {
+    while (q) { const int64_t r = p % q; p = q; q = r; }
+    return p;
+}
+
+cudaError_t launch_log_v(const SweepArgs& a, const double* ut, double* out, cudaStream_t s) {
+    // blocks * 256 must be a multiple of C; about four blocks per SM
+    const int64_t unit = a.C / gcd64(256, a.C);                   // blocks per stride unit
+    int64_t blocks = unit * std::max<int64_t>(1, (152 * 4 + unit - 1) / unit);
+    blocks = std::min<int64_t>(blocks, std::max<int64_t>(unit, unit * ((((int64_t)a.N + a.E) * a.C / 256 + unit) / unit)));
+    const size_t smem = a.C <= 4096 ? (size_t)a.C * sizeof(double) : 0;
+    k_log_v<<<(unsigned)blocks, 256, smem, s>>>(a, ut, out, blocks * 256);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------- dispatch
 
 #define MRF_DISPATCH_L(L_, ...)                                                   \

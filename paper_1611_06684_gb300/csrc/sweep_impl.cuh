@@ -200,9 +200,11 @@ __device__ __forceinline__ void dual_bits(uint32_t e, uint32_t c, int xs, int xt
 // Draw x_v from exp(F)/Z by the inverse CDF with the 23-bit uniform u of
 // Philox phase `phase` (u is exact in float32); optionally record log p.
 // Counts draws within 1e-6 of a CDF boundary.
+// lp_drawn (optional) receives log p of the drawn label.
 template <int L>
 __device__ __forceinline__ int draw_label(const float (&F)[L], uint32_t v, uint32_t c, uint32_t sweep,
-                                          const RoundKeys& key, uint32_t phase, float* __restrict__ logp_out, Ctl* ctl) {
+                                          const RoundKeys& key, uint32_t phase, float* __restrict__ logp_out, Ctl* ctl,
+                                          float* __restrict__ lp_drawn = nullptr) {
     float mx = F[0];
 #pragma unroll
     for (int a = 1; a < L; ++a) mx = fmaxf(mx, F[a]);
@@ -233,7 +235,14 @@ __device__ __forceinline__ int draw_label(const float (&F)[L], uint32_t v, uint3
         near |= fabsf(u - cdf) < 1e-6f;
     }
     if (near) atomicAdd(&ctl->boundary, 1ull);
-    return lab < 0 ? last_pos : lab;
+    const int pick = lab < 0 ? last_pos : lab;
+    if (lp_drawn) {
+        float fp = F[0];
+#pragma unroll
+        for (int a = 1; a < L; ++a) fp = a == pick ? F[a] : fp;
+        *lp_drawn = (fp - mx) - logf(s);
+    }
+    return pick;
 }
 
 // ---------------------------------------------------------------------------- kernels
@@ -459,7 +468,7 @@ __global__ void __launch_bounds__(256, FUSED ? 2 : 4) k_primal(SweepArgs a) {
         return;
     }
     float* lp = a.logp ? a.logp + ((int64_t)c * a.N + v) * L : nullptr;
-    xout[g] = (uint8_t)draw_label<L>(F, v, c, sweep, a.rk, PH_PRIMAL, lp, a.ctl);
+    xout[g] = (uint8_t)draw_label<L>(F, v, c, sweep, a.rk, PH_PRIMAL, lp, a.ctl, a.lpv ? a.lpv + g : nullptr);
 }
 
 // Warp-per-site form of the plain primal step (chains a multiple of 32, so a
@@ -557,7 +566,7 @@ __global__ void __launch_bounds__(256, 4) k_primal_warp(SweepArgs a) {
         return;
     }
     float* lp = a.logp ? a.logp + ((int64_t)c * a.N + v) * L : nullptr;
-    xout[g] = (uint8_t)draw_label<L>(F, v, c, sweep, a.rk, PH_PRIMAL, lp, a.ctl);
+    xout[g] = (uint8_t)draw_label<L>(F, v, c, sweep, a.rk, PH_PRIMAL, lp, a.ctl, a.lpv ? a.lpv + g : nullptr);
 }
 
 // CTA-per-site schedule of the plain primal step for high-degree sites: a CTA
@@ -619,7 +628,8 @@ __global__ void __launch_bounds__(256) k_primal_cta(SweepArgs a, int CG) {
         for (int x = 0; x < L; ++x) F[x] = __ldg(uf + x) + (hi[x] + lo[x]);
         uint8_t* xout = a.x + (size_t)((sweep + 1) & 1) * a.N * a.C;
         float* lp = a.logp ? a.logp + ((int64_t)c * a.N + v) * L : nullptr;
-        xout[(int64_t)v * a.C + c] = (uint8_t)draw_label<L>(F, v, (uint32_t)c, sweep, a.rk, PH_PRIMAL, lp, a.ctl);
+        xout[(int64_t)v * a.C + c] = (uint8_t)draw_label<L>(F, v, (uint32_t)c, sweep, a.rk, PH_PRIMAL, lp, a.ctl,
+                                                            a.lpv ? a.lpv + (int64_t)v * a.C + c : nullptr);
     }
 }
 

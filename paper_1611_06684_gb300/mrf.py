@@ -62,6 +62,7 @@ _SIGS = {
     "mrf_debug_theta": (ct.c_int, [_P, _P]),
     "mrf_kernel_times": (ct.c_int, [_P, _P, _P]),
     "mrf_set_kernel_timing": (ct.c_int, [_P, ct.c_int32]),
+    "mrf_estimate_log_partition": (ct.c_int, [_P, ct.c_int32, _P]),
     "mrf_philox_rate": (ct.c_int, [ct.c_uint64, ct.c_int32, _P, ct.POINTER(ct.c_double)]),
     "mrf_sweep_noalloc": (ct.c_int, [_P, _P, _P, ct.c_int64]),
     "mrf_learned_setup": (ct.c_int, [_P, _P, ct.c_int32, ct.c_uint64]),
@@ -320,6 +321,12 @@ class MRF:
         X = np.zeros((rows, width), np.float32); z = np.zeros((rows, n_out), np.float32)
         self._check(self.lib.mrf_learned_debug(self.h, X.ctypes.data, z.ctypes.data))
         return X, z
+
+    def estimate_log_partition(self, n_sweeps: int):
+        """log V [n_sweeps][C] of Section 5.2's estimator over n plain sweeps."""
+        out = np.zeros((int(n_sweeps), self.C), np.float64)
+        self._check(self.lib.mrf_estimate_log_partition(self.h, int(n_sweeps), out.ctypes.data))
+        return out
 
     def debug_mlp_timeout(self, on: bool = True):
         """Arm the tensor-core MLP's timeout test hook for the next learned sweep."""
