@@ -259,6 +259,18 @@ def run_ours(args, ws, rank, local):
             kt = h.kernel_times()
             variants[name] = {"ms_per_step": msv, "value": C * model.n_vars / (msv / 1e3), "unit": METRIC,
                               "kernels": {k: v[0] / v[1] for k, v in kt.items()}}
+        if model.grid:
+            # log-partition estimator of Section 5.2 (plain sweeps recording log p of the drawn labels)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lv = h.estimate_log_partition(5)
+            dt = (time.perf_counter() - t0) / 5
+            w = np.exp(lv - lv.max())
+            variants["log_partition"] = {
+                "sweeps": 5, "chains": C, "ms_per_sweep_wall": dt * 1e3,
+                "mean_log_v": float(lv.mean()), "log_mean_exp_v": float(lv.max() + np.log(w.mean())),
+                "lower_bound_per_site": float(lv.mean() / model.n_vars),
+                "note": "mean of log V is a lower bound on log Z (Section 5.2); chains after the timed sweeps"}
         if args.ess_sweeps > 0:
             ms_of = {"plain": ms_step if args.mode == "plain" else None}
             ms_of.update({k: v["ms_per_step"] for k, v in variants.items()})
