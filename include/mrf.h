@@ -190,6 +190,20 @@ mrf_status mrf_philox_rate(uint64_t threads, int32_t calls, void* cuda_stream, d
  * The sweeps advance the chains and the marginal counts like mrf_sweep. */
 mrf_status mrf_estimate_log_partition(mrf_t* h, int32_t n_sweeps, double* log_v);
 
+/* Primal-dual EM (local MAP, Section 5.3): n_iters iterations of
+ *   xi = E[r(theta) | x]  (pi_k = sigmoid(q_k + beta1_k [x_s = i_k] + beta2_k [x_t = j_k]))
+ *   x  = argmax_x h(x) exp(<s(x), xi>)  (per site: the first label of largest field)
+ * from labels[C][N] (in/out, uint8, host or device per ptr_kind).  Every
+ * iteration does not decrease log p~(x).  The sampler's state is untouched. */
+mrf_status mrf_map_em(mrf_t* h, int32_t n_iters, uint8_t* labels, int32_t ptr_kind);
+
+/* Primal-dual mean field (Section 5.3): n_iters iterations of
+ *   xi = E[r(theta) | eta],  eta = E[s(x)] from the site marginals q
+ *   q_v = softmax of the field of xi
+ * from marginals[C][N][L] (in/out, float32, host or device per ptr_kind; each
+ * row a distribution over labels).  The sampler's state is untouched. */
+mrf_status mrf_mean_field(mrf_t* h, int32_t n_iters, float* marginals, int32_t ptr_kind);
+
 /* Switch options.kernel_timing on (1) or off (0) for later sweeps. */
 mrf_status mrf_set_kernel_timing(mrf_t* h, int32_t on);
 

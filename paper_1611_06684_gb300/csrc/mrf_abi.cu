@@ -36,6 +36,9 @@ struct mrf {
     int2* d_inc = nullptr;
     uint8_t* d_x = nullptr;
     uint32_t* d_theta = nullptr;
+    uint8_t* d_em = nullptr;           // [2][N][C] labels of the EM iterations
+    float* d_mfq = nullptr;            // [2][N][L][C] marginals of the mean-field iterations
+    float* d_mfs = nullptr;            // [C][N][L] staging of the mean-field interface
     float* d_lpv = nullptr;            // [N][C] log p of the drawn labels (log-partition estimator)
     double* d_logv = nullptr;          // [sweeps][C] log V of the estimator
     int64_t logv_cap = 0;
@@ -368,7 +371,7 @@ void mrf_destroy(mrf_t* h) {
     drop_graphs(h);
     dfree(h->d_unary); dfree(h->d_ut); dfree(h->d_utf); dfree(h->d_tpl); dfree(h->d_src); dfree(h->d_dst); dfree(h->d_tau); dfree(h->d_thr);
     dfree(h->d_fold); dfree(h->d_cst); dfree(h->d_resid); dfree(h->d_inc_ptr); dfree(h->d_inc); dfree(h->d_x);
-    dfree(h->d_theta); dfree(h->d_ties); dfree(h->d_tie_count); dfree(h->d_counts); dfree(h->d_lpv); dfree(h->d_logv); dfree(h->d_logp); dfree(h->d_ctl); dfree(h->d_flag); dfree(h->d_stage); dfree(h->d_pot);
+    dfree(h->d_theta); dfree(h->d_ties); dfree(h->d_tie_count); dfree(h->d_counts); dfree(h->d_lpv); dfree(h->d_logv); dfree(h->d_em); dfree(h->d_mfq); dfree(h->d_mfs); dfree(h->d_logp); dfree(h->d_ctl); dfree(h->d_flag); dfree(h->d_stage); dfree(h->d_pot);
     dfree(h->d_csr_work); dfree(h->d_csr_sums);
     dfree(h->d_ed_pair); dfree(h->d_ed_slots); dfree(h->d_ed_new); dfree(h->d_ed_s); dfree(h->d_ed_t);
     dfree(h->d_members); dfree(h->d_nmem); dfree(h->d_intra_ptr); dfree(h->d_intra); dfree(h->d_cf); dfree(h->d_skip);
@@ -745,6 +748,50 @@ mrf_status mrf_estimate_log_partition(mrf_t* h, int32_t n_sweeps, double* log_v)
     if (st != MRF_OK) return st;
     MRF_CUDA(h, cudaMemcpyAsync(log_v, h->d_logv, sizeof(double) * (size_t)n_sweeps * h->C, cudaMemcpyDeviceToHost,
                                 h->stream));
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    return MRF_OK;
+}
+
+mrf_status mrf_map_em(mrf_t* h, int32_t n_iters, uint8_t* labels, int32_t ptr_kind) {
+    if (!h || !labels || n_iters < 0) return MRF_EINVAL;
+    if (!h->has_factors) return fail(h, MRF_ESTATE, "mrf_set_factors first");
+    const size_t NC = (size_t)h->N * h->C;
+    if (!h->d_stage) MRF_CUDA(h, dalloc(h->d_stage, NC));
+    if (!h->d_em) MRF_CUDA(h, dalloc(h->d_em, 2 * NC));
+    MRF_CUDA(h, to_device(h->d_stage, labels, (int64_t)NC, ptr_kind, h->stream));
+    MRF_CUDA(h, cudaMemsetAsync(h->d_flag, 0, sizeof(unsigned long long), h->stream));
+    MRF_CUDA(h, launch_count_ge(h->d_stage, (int64_t)NC, h->L, h->d_flag, h->stream));
+    unsigned long long bad = 0;
+    MRF_CUDA(h, cudaMemcpyAsync(&bad, h->d_flag, sizeof(bad), cudaMemcpyDeviceToHost, h->stream));
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (bad) return fail(h, MRF_ERANGE, "label out of range");
+    MRF_CUDA(h, launch_labels_from_abi(h->d_stage, h->d_em, h->N, h->C, h->stream));
+    const SweepArgs a = make_args(h);
+    for (int i = 0; i < n_iters; ++i)
+        MRF_CUDA(h, launch_em(a, h->layout, h->d_em + (i & 1) * NC, h->d_em + ((i + 1) & 1) * NC, h->stream));
+    MRF_CUDA(h, launch_labels_to_abi(h->d_em + (n_iters & 1) * NC, h->d_stage, h->N, h->C, h->stream));
+    MRF_CUDA(h, cudaMemcpyAsync(labels, h->d_stage, NC,
+                                ptr_kind == MRF_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream));
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    return MRF_OK;
+}
+
+mrf_status mrf_mean_field(mrf_t* h, int32_t n_iters, float* marginals, int32_t ptr_kind) {
+    if (!h || !marginals || n_iters < 0) return MRF_EINVAL;
+    if (!h->has_factors) return fail(h, MRF_ESTATE, "mrf_set_factors first");
+    const size_t n = (size_t)h->N * h->L * h->C;
+    if (!h->d_mfq) MRF_CUDA(h, dalloc(h->d_mfq, 2 * n));
+    if (!h->d_mfs) MRF_CUDA(h, dalloc(h->d_mfs, n));
+    MRF_CUDA(h, to_device(h->d_mfs, marginals, (int64_t)n, ptr_kind, h->stream));
+    mrf_status st = check_finite_device(h, h->d_mfs, (int64_t)n, "marginals");
+    if (st != MRF_OK) return st;
+    MRF_CUDA(h, launch_marg_layout(h->d_mfs, h->d_mfq, h->N, h->L, h->C, false, h->stream));
+    const SweepArgs a = make_args(h);
+    for (int i = 0; i < n_iters; ++i)
+        MRF_CUDA(h, launch_mf(a, h->layout, h->d_mfq + (i & 1) * n, h->d_mfq + ((i + 1) & 1) * n, h->stream));
+    MRF_CUDA(h, launch_marg_layout(h->d_mfq + (n_iters & 1) * n, h->d_mfs, h->N, h->L, h->C, true, h->stream));
+    MRF_CUDA(h, cudaMemcpyAsync(marginals, h->d_mfs, n * sizeof(float),
+                                ptr_kind == MRF_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream));
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));
     return MRF_OK;
 }

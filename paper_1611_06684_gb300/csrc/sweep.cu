@@ -219,6 +219,43 @@ cudaError_t launch_init_labels(const SweepArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int L, int LAYOUT> cudaError_t run_em(const SweepArgs&, const uint8_t*, uint8_t*, cudaStream_t);
+template <int L, int LAYOUT> cudaError_t run_mf(const SweepArgs&, const float*, float*, cudaStream_t);
+
+cudaError_t launch_em(const SweepArgs& a, int layout, const uint8_t* xin, uint8_t* xout, cudaStream_t s) {
+    if (layout == MRF_LAYOUT_PIVOT) {
+        MRF_DISPATCH_L(a.L, return (run_em<LL, MRF_LAYOUT_PIVOT>(a, xin, xout, s)));
+    } else {
+        MRF_DISPATCH_L(a.L, return (run_em<LL, MRF_LAYOUT_DIAG>(a, xin, xout, s)));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mf(const SweepArgs& a, int layout, const float* qin, float* qout, cudaStream_t s) {
+    if (layout == MRF_LAYOUT_PIVOT) {
+        MRF_DISPATCH_L(a.L, return (run_mf<LL, MRF_LAYOUT_PIVOT>(a, qin, qout, s)));
+    } else {
+        MRF_DISPATCH_L(a.L, return (run_mf<LL, MRF_LAYOUT_DIAG>(a, qin, qout, s)));
+    }
+    return cudaGetLastError();
+}
+
+// marginals [C][N][L] (interface) <-> [N][L][C] (kernels)
+__global__ void k_marg_layout(const float* __restrict__ in, float* __restrict__ out, int N, int L, int C, int to_abi) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)N * L * C) return;
+    const int c = (int)(i % C);
+    const int64_t vl = i / C;                          // v * L + a
+    const int64_t j = (int64_t)c * N * L + vl;         // [c][v][a]
+    if (to_abi) out[j] = in[i]; else out[i] = in[j];
+}
+
+cudaError_t launch_marg_layout(const float* in, float* out, int N, int L, int C, bool to_abi, cudaStream_t s) {
+    const int64_t n = (int64_t)N * L * C;
+    if (n > 0) k_marg_layout<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, N, L, C, to_abi ? 1 : 0);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dual(const SweepArgs& a, int layout, cudaStream_t s) {
     const int64_t n = a.E * a.C;
     if (n == 0) return cudaSuccess;

@@ -633,6 +633,101 @@ __global__ void __launch_bounds__(256) k_primal_cta(SweepArgs a, int CG) {
     }
 }
 
+// ---------------------------------------------------------------------------- EM and mean field
+
+// Theta-update of Section 5.3's primal-dual EM / mean field for one incident
+// edge: with eta_y,k and eta_z,k the (expected) indicators of the entry's row
+// and column labels, pi_k = sigmoid(q_k + beta1 eta_y + beta2 eta_z),
+// q = -max(tau, 0), beta1 = tau, beta2 = |tau| (tau signed), and its beta pi
+// is added to the field of this endpoint (row i_k on the source side, column
+// j_k on the destination side).  ey / ez give eta for label a of the source /
+// destination endpoint.
+template <int L, int LAYOUT, typename EtaS, typename EtaT>
+__device__ __forceinline__ void add_side_mean(const float* __restrict__ tau_e, int side, EtaS ey, EtaT ez,
+                                              float (&acc)[L]) {
+    using E = Ent<L, LAYOUT>;
+    const float4* t4 = reinterpret_cast<const float4*>(tau_e);
+#pragma unroll
+    for (int k4 = 0; k4 < E::MP / 4; ++k4) {
+        const float4 qv = __ldg(t4 + k4);
+        const float tv[4] = {qv.x, qv.y, qv.z, qv.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = 4 * k4 + u;
+            if (k >= E::M) continue;
+            const float ts = tv[u], b2 = fabsf(ts);
+            const float logit = -fmaxf(ts, 0.0f) + ts * ey(E::i(k)) + b2 * ez(E::j(k));
+            const float pi = 1.0f / (1.0f + expf(-logit));
+            if (side == 0) acc[E::i(k)] += ts * pi;
+            else acc[E::j(k)] += b2 * pi;
+        }
+    }
+}
+
+// EM (local MAP): x' = argmax of the field of the expected duals given x.
+template <int L, int LAYOUT>
+__global__ void __launch_bounds__(256) k_em(SweepArgs a, const uint8_t* __restrict__ xin, uint8_t* __restrict__ xout) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (uint64_t)a.N * a.C) return;
+    const uint32_t v = a.fdC.div(g), c = g - v * (uint32_t)a.C;
+    const int xv = xin[g];
+    float acc[L];
+#pragma unroll
+    for (int x = 0; x < L; ++x) acc[x] = 0.0f;
+    for (int64_t p = a.inc_ptr[v]; p < a.inc_ptr[v + 1]; ++p) {
+        const int2 ic = __ldg(&a.inc[p]);
+        const int side = ic.x & 1;
+        const int xu = xin[(int64_t)ic.y * a.C + c];
+        const int xs = side == 0 ? xv : xu, xt = side == 0 ? xu : xv;
+        add_side_mean<L, LAYOUT>(a.tau + (int64_t)(ic.x >> 1) * Ent<L, LAYOUT>::MP, side,
+                                 [&](int i) { return xs == i ? 1.0f : 0.0f; }, [&](int j) { return xt == j ? 1.0f : 0.0f; }, acc);
+    }
+    const float* uf = a.utf + (int64_t)v * L;
+    int best = 0;
+    float fb = __ldg(uf) + acc[0];
+#pragma unroll
+    for (int x = 1; x < L; ++x) {
+        const float f = __ldg(uf + x) + acc[x];
+        if (f > fb) { fb = f; best = x; }
+    }
+    xout[g] = (uint8_t)best;
+}
+
+// Mean field: q' = softmax of the field of the expected duals given the site
+// marginals q ([N][L][C], chain innermost).
+template <int L, int LAYOUT>
+__global__ void __launch_bounds__(256) k_mf(SweepArgs a, const float* __restrict__ qin, float* __restrict__ qout) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (uint64_t)a.N * a.C) return;
+    const uint32_t v = a.fdC.div(g), c = g - v * (uint32_t)a.C;
+    const int64_t C = a.C;
+    float qv[L], acc[L];
+#pragma unroll
+    for (int x = 0; x < L; ++x) { qv[x] = qin[((int64_t)v * L + x) * C + c]; acc[x] = 0.0f; }
+    for (int64_t p = a.inc_ptr[v]; p < a.inc_ptr[v + 1]; ++p) {
+        const int2 ic = __ldg(&a.inc[p]);
+        const int side = ic.x & 1;
+        float qu[L];
+#pragma unroll
+        for (int x = 0; x < L; ++x) qu[x] = qin[((int64_t)ic.y * L + x) * C + c];
+        const float* tau_e = a.tau + (int64_t)(ic.x >> 1) * Ent<L, LAYOUT>::MP;
+        if (side == 0)
+            add_side_mean<L, LAYOUT>(tau_e, 0, [&](int i) { return qv[i]; }, [&](int j) { return qu[j]; }, acc);
+        else
+            add_side_mean<L, LAYOUT>(tau_e, 1, [&](int i) { return qu[i]; }, [&](int j) { return qv[j]; }, acc);
+    }
+    const float* uf = a.utf + (int64_t)v * L;
+    float F[L], mx = -INFINITY;
+#pragma unroll
+    for (int x = 0; x < L; ++x) { F[x] = __ldg(uf + x) + acc[x]; mx = fmaxf(mx, F[x]); }
+    float s = 0.0f;
+#pragma unroll
+    for (int x = 0; x < L; ++x) { F[x] = expf(F[x] - mx); s += F[x]; }
+    const float inv = 1.0f / s;
+#pragma unroll
+    for (int x = 0; x < L; ++x) qout[((int64_t)v * L + x) * C + c] = F[x] * inv;
+}
+
 static inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 template <int L, int LAYOUT>
@@ -675,7 +770,25 @@ cudaError_t run_potential(const SweepArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int L, int LAYOUT>
+cudaError_t run_em(const SweepArgs& a, const uint8_t* xin, uint8_t* xout, cudaStream_t s) {
+    const int64_t n = (int64_t)a.N * a.C;
+    if (n > 0) k_em<L, LAYOUT><<<blocks_for(n, 256), 256, 0, s>>>(a, xin, xout);
+    return cudaGetLastError();
+}
+
+template <int L, int LAYOUT>
+cudaError_t run_mf(const SweepArgs& a, const float* qin, float* qout, cudaStream_t s) {
+    const int64_t n = (int64_t)a.N * a.C;
+    if (n > 0) k_mf<L, LAYOUT><<<blocks_for(n, 256), 256, 0, s>>>(a, qin, qout);
+    return cudaGetLastError();
+}
+
 #define MRF_INSTANTIATE_SWEEP(L)                                                                 \
+    template cudaError_t run_em<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, const uint8_t*, uint8_t*, cudaStream_t); \
+    template cudaError_t run_em<L, MRF_LAYOUT_DIAG>(const SweepArgs&, const uint8_t*, uint8_t*, cudaStream_t);  \
+    template cudaError_t run_mf<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, const float*, float*, cudaStream_t);     \
+    template cudaError_t run_mf<L, MRF_LAYOUT_DIAG>(const SweepArgs&, const float*, float*, cudaStream_t);      \
     template cudaError_t run_primal_cta<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, cudaStream_t);     \
     template cudaError_t run_primal_cta<L, MRF_LAYOUT_DIAG>(const SweepArgs&, cudaStream_t);      \
     template cudaError_t run_potential<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, cudaStream_t);      \

@@ -63,6 +63,8 @@ _SIGS = {
     "mrf_kernel_times": (ct.c_int, [_P, _P, _P]),
     "mrf_set_kernel_timing": (ct.c_int, [_P, ct.c_int32]),
     "mrf_estimate_log_partition": (ct.c_int, [_P, ct.c_int32, _P]),
+    "mrf_map_em": (ct.c_int, [_P, ct.c_int32, _P, ct.c_int32]),
+    "mrf_mean_field": (ct.c_int, [_P, ct.c_int32, _P, ct.c_int32]),
     "mrf_philox_rate": (ct.c_int, [ct.c_uint64, ct.c_int32, _P, ct.POINTER(ct.c_double)]),
     "mrf_sweep_noalloc": (ct.c_int, [_P, _P, _P, ct.c_int64]),
     "mrf_learned_setup": (ct.c_int, [_P, _P, ct.c_int32, ct.c_uint64]),
@@ -327,6 +329,18 @@ class MRF:
         out = np.zeros((int(n_sweeps), self.C), np.float64)
         self._check(self.lib.mrf_estimate_log_partition(self.h, int(n_sweeps), out.ctypes.data))
         return out
+
+    def map_em(self, labels, n_iters: int):
+        """Primal-dual EM from labels [C][N]; returns the labels after n_iters iterations."""
+        x = np.ascontiguousarray(labels, np.uint8).copy()
+        self._check(self.lib.mrf_map_em(self.h, int(n_iters), x.ctypes.data, MRF_PTR_HOST))
+        return x
+
+    def mean_field(self, marginals, n_iters: int):
+        """Primal-dual mean field from marginals [C][N][L]; returns them after n_iters iterations."""
+        q = np.ascontiguousarray(marginals, np.float32).copy()
+        self._check(self.lib.mrf_mean_field(self.h, int(n_iters), q.ctypes.data, MRF_PTR_HOST))
+        return q
 
     def debug_mlp_timeout(self, on: bool = True):
         """Arm the tensor-core MLP's timeout test hook for the next learned sweep."""
