@@ -273,7 +273,7 @@ def run_ours(args, ws, rank, local):
                 "note": "mean of log V is a lower bound on log Z (Section 5.2); chains after the timed sweeps"}
         if args.ess_sweeps > 0:
             ms_of = {"plain": ms_step if args.mode == "plain" else None}
-            ms_of.update({k: v["ms_per_step"] for k, v in variants.items()})
+            ms_of.update({k: v["ms_per_step"] for k, v in variants.items() if "ms_per_step" in v})
             variants["ess"] = ess_comparison(h, model, C, stream, args.ess_sweeps, ms_of,
                                              [("plain", M.MODE_PLAIN)] + ([("splash", M.MODE_SPLASH)] if model.grid else []))
 
