@@ -132,7 +132,10 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
                             const float* pair_log, int64_t* out_new_ids, int32_t ptr_kind);
 
 /* Run n_sweeps sweeps (Section 5.1 or 5.4) and accumulate label counts for
- * sweeps with index >= burn-in.  Asynchronous on the handle's stream. */
+ * sweeps with index >= burn-in.  Asynchronous on the handle's stream.  Plain
+ * sweeps of a small model (at most 2^16 site x chain and edge x chain items)
+ * with n_sweeps >= 2 run in one single-CTA launch (the same chain, bit for
+ * bit, as one sweep at a time). */
 mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode);
 
 /* Estimated marginals out[n_vars][L] = counts / n_samples (float32) and the
@@ -167,7 +170,9 @@ mrf_status mrf_debug_theta(mrf_t* h, uint32_t* out);
 
 /* Kernel ids of mrf_kernel_times. */
 enum { MRF_K_DUAL = 0, MRF_K_PRIMAL = 1, MRF_K_FUSED = 2, MRF_K_POTENTIAL = 3, MRF_K_FFBS = 4,
-       MRF_K_ACCUMULATE = 5, MRF_K_FEATURES = 6, MRF_K_MLP = 7, MRF_K_MH = 8, MRF_K_COUNT = 9 };
+       MRF_K_ACCUMULATE = 5, MRF_K_FEATURES = 6, MRF_K_MLP = 7, MRF_K_MH = 8,
+       MRF_K_SMALL = 9,    /* whole plain sweeps of a small model in one launch (see mrf_sweep) */
+       MRF_K_COUNT = 10 };
 /* With options.kernel_timing: total device milliseconds ms[MRF_K_COUNT] and
  * launch counts launches[MRF_K_COUNT] of every sweep kernel since the last
  * call (CUDA events on the handle's stream); resets the totals.  Synchronises. */

@@ -159,6 +159,8 @@ cudaError_t launch_accumulate(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_philox_rate(uint64_t threads, int calls, uint32_t* sink, cudaStream_t s);
 cudaError_t launch_log_v(const SweepArgs& a, const double* ut, double* out, cudaStream_t s);
 cudaError_t launch_em(const SweepArgs& a, int layout, const uint8_t* xin, uint8_t* xout, cudaStream_t s);
+int64_t sweep_small_smem(const SweepArgs& a);
+cudaError_t launch_sweep_small(const SweepArgs& a, int layout, int n_sweeps, cudaStream_t s);
 cudaError_t launch_mf(const SweepArgs& a, int layout, const float* qin, float* qout, cudaStream_t s);
 cudaError_t launch_marg_layout(const float* in, float* out, int N, int L, int C, bool to_abi, cudaStream_t s);
 // Tensor-core MLP (mlp_tc.cu)

@@ -632,6 +632,13 @@ static mrf_status tune_schedule(mrf_t* h) {
 
 static bool use_mlp_tc(const mrf_t* h) { return h->opt.mlp_path == 0 && mlp_tc_supported(h->la); }
 
+// Models small enough for k_sweep_small: at most 2^16 (site, chain) and
+// (edge, chain) items, theta of all items within 200 KB of shared memory.
+static bool small_model(const mrf_t* h) {
+    const int64_t nv = (int64_t)h->N * h->C, ne = h->E_slots * h->C;
+    return nv <= 65536 && ne <= 65536 && ne * h->W * 4 <= 200 * 1024;
+}
+
 static mrf_status enqueue_sweep(mrf_t* h, int mode) {
     SweepArgs a = make_args(h);
     cudaStream_t s = h->stream;
@@ -681,6 +688,13 @@ mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode) {
     if (mode == MRF_MODE_PLAIN && h->schedule == 0 && n_sweeps > 0) {
         mrf_status st = tune_schedule(h);
         if (st != MRF_OK) return st;
+    }
+    // small models: all the sweeps in one single-CTA launch (launch latency dominates there)
+    if (mode == MRF_MODE_PLAIN && n_sweeps >= 2 && small_model(h)) {
+        const SweepArgs a = make_args(h);
+        MRF_CUDA(h, timed(h, MRF_K_SMALL, [&] { return launch_sweep_small(a, h->layout, n_sweeps, h->stream); }));
+        h->sweep_host += n_sweeps;
+        return MRF_OK;
     }
     const bool graphs = h->opt.use_graphs && h->stream != nullptr && !h->opt.kernel_timing;
     if (graphs && !h->graph[mode] && n_sweeps > 0) {

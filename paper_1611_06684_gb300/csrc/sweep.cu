@@ -219,6 +219,20 @@ cudaError_t launch_init_labels(const SweepArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int L, int LAYOUT> cudaError_t run_sweep_small(const SweepArgs&, int, cudaStream_t);
+
+// Small models: the smem need of k_sweep_small (theta of all items) in bytes.
+int64_t sweep_small_smem(const SweepArgs& a) { return a.E * a.C * (int64_t)a.W * 4; }
+
+cudaError_t launch_sweep_small(const SweepArgs& a, int layout, int n_sweeps, cudaStream_t s) {
+    if (layout == MRF_LAYOUT_PIVOT) {
+        MRF_DISPATCH_L(a.L, return (run_sweep_small<LL, MRF_LAYOUT_PIVOT>(a, n_sweeps, s)));
+    } else {
+        MRF_DISPATCH_L(a.L, return (run_sweep_small<LL, MRF_LAYOUT_DIAG>(a, n_sweeps, s)));
+    }
+    return cudaGetLastError();
+}
+
 template <int L, int LAYOUT> cudaError_t run_em(const SweepArgs&, const uint8_t*, uint8_t*, cudaStream_t);
 template <int L, int LAYOUT> cudaError_t run_mf(const SweepArgs&, const float*, float*, cudaStream_t);
 

@@ -633,6 +633,92 @@ __global__ void __launch_bounds__(256) k_primal_cta(SweepArgs a, int CG) {
     }
 }
 
+// ---------------------------------------------------------------------------- small models
+
+// n_sweeps whole plain sweeps of a small model in one CTA (sizes where launch
+// latency, not work, sets the time): dual half-step into shared memory,
+// primal half-step, marginal counts and the sweep advance, separated by CTA
+// barriers only.  The draws and the order of every addition are those of
+// k_dual / k_primal, so the chain is the same bit for bit.
+template <int L, int LAYOUT>
+__global__ void __launch_bounds__(1024) k_sweep_small(SweepArgs a, int n_sweeps) {
+    using E = Ent<L, LAYOUT>;
+    extern __shared__ uint32_t s_theta[];                          // [E][C][W]
+    const int64_t ne = a.E * a.C, nv = (int64_t)a.N * a.C;
+    uint32_t sweep = (uint32_t)a.ctl->sweep;
+    const unsigned long long count_from = a.ctl->count_from;
+    for (int it = 0; it < n_sweeps; ++it, ++sweep) {
+        const uint8_t* xin = a.x + (size_t)(sweep & 1) * a.N * a.C;
+        uint8_t* xout = a.x + (size_t)((sweep + 1) & 1) * a.N * a.C;
+        for (int64_t g = threadIdx.x; g < ne; g += blockDim.x) {
+            const uint32_t e = a.fdC.div((uint32_t)g), c = (uint32_t)g - e * (uint32_t)a.C;
+            uint32_t bits[E::W];
+            const int s = a.src[e];
+            if (s >= 0) {
+                const int t = a.dst[e];
+                dual_bits<L, LAYOUT>(e, c, xin[(int64_t)s * a.C + c], xin[(int64_t)t * a.C + c],
+                                     a.tpl + (int64_t)e * E::W * 32, a.thr + (int64_t)e * E::M, sweep, a.rk, bits);
+            } else {
+#pragma unroll
+                for (int w = 0; w < E::W; ++w) bits[w] = 0;
+            }
+#pragma unroll
+            for (int w = 0; w < E::W; ++w) s_theta[g * E::W + w] = bits[w];
+        }
+        __syncthreads();
+        for (int64_t g = threadIdx.x; g < nv; g += blockDim.x) {
+            const uint32_t v = a.fdC.div((uint32_t)g), c = (uint32_t)g - v * (uint32_t)a.C;
+            float acc[L], hi[L], lo[L];
+#pragma unroll
+            for (int x = 0; x < L; ++x) { acc[x] = 0.0f; hi[x] = 0.0f; lo[x] = 0.0f; }
+            int chunk = 0;
+            bool flushed = false;
+            for (int64_t p = a.inc_ptr[v]; p < a.inc_ptr[v + 1]; ++p) {
+                const int2 ic = __ldg(&a.inc[p]);
+                const int64_t e = ic.x >> 1;
+                uint32_t bits[E::W];
+#pragma unroll
+                for (int w = 0; w < E::W; ++w) bits[w] = s_theta[(e * a.C + c) * E::W + w];
+                add_side<L, LAYOUT>(bits, a.tau + e * E::MP, ic.x & 1, acc);
+                if (++chunk == 32) {
+#pragma unroll
+                    for (int x = 0; x < L; ++x) { two_sum_add(hi[x], lo[x], acc[x]); acc[x] = 0.0f; }
+                    chunk = 0;
+                    flushed = true;
+                }
+            }
+            float F[L];
+            const float* uf = a.utf + (int64_t)v * L;
+            if (flushed) {
+#pragma unroll
+                for (int x = 0; x < L; ++x) { two_sum_add(hi[x], lo[x], acc[x]); F[x] = __ldg(uf + x) + (hi[x] + lo[x]); }
+            } else {
+#pragma unroll
+                for (int x = 0; x < L; ++x) F[x] = __ldg(uf + x) + acc[x];
+            }
+            float* lp = a.logp ? a.logp + ((int64_t)c * a.N + v) * L : nullptr;
+            xout[g] = (uint8_t)draw_label<L>(F, v, c, sweep, a.rk, PH_PRIMAL, lp, a.ctl);
+        }
+        __syncthreads();
+        if (sweep >= count_from) {
+            for (int64_t v = threadIdx.x; v < a.N; v += blockDim.x) {
+                uint32_t tot[L];
+#pragma unroll
+                for (int x = 0; x < L; ++x) tot[x] = 0;
+                for (int c = 0; c < a.C; ++c) {
+                    const int x = xout[v * a.C + c];
+#pragma unroll
+                    for (int y = 0; y < L; ++y) tot[y] += x == y ? 1u : 0u;
+                }
+#pragma unroll
+                for (int x = 0; x < L; ++x) a.counts[v * L + x] += tot[x];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a.ctl->sweep = sweep;
+}
+
 // ---------------------------------------------------------------------------- EM and mean field
 
 // Theta-update of Section 5.3's primal-dual EM / mean field for one incident
@@ -784,7 +870,20 @@ cudaError_t run_mf(const SweepArgs& a, const float* qin, float* qout, cudaStream
     return cudaGetLastError();
 }
 
+template <int L, int LAYOUT>
+cudaError_t run_sweep_small(const SweepArgs& a, int n_sweeps, cudaStream_t s) {
+    const size_t smem = (size_t)a.E * a.C * Ent<L, LAYOUT>::W * sizeof(uint32_t);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_sweep_small<L, LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_sweep_small<L, LAYOUT><<<1, 1024, smem, s>>>(a, n_sweeps);
+    return cudaGetLastError();
+}
+
 #define MRF_INSTANTIATE_SWEEP(L)                                                                 \
+    template cudaError_t run_sweep_small<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, int, cudaStream_t); \
+    template cudaError_t run_sweep_small<L, MRF_LAYOUT_DIAG>(const SweepArgs&, int, cudaStream_t);  \
     template cudaError_t run_em<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, const uint8_t*, uint8_t*, cudaStream_t); \
     template cudaError_t run_em<L, MRF_LAYOUT_DIAG>(const SweepArgs&, const uint8_t*, uint8_t*, cudaStream_t);  \
     template cudaError_t run_mf<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, const float*, float*, cudaStream_t);     \

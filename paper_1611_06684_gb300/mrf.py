@@ -22,9 +22,9 @@ MRF_OK, MRF_EINVAL, MRF_ENONFINITE, MRF_ENOMEM, MRF_ECUDA, MRF_ERANGE, MRF_ETIME
 MRF_PTR_HOST, MRF_PTR_DEVICE = 0, 1
 MODE_PLAIN, MODE_FUSED, MODE_SPLASH, MODE_LEARNED = 0, 1, 2, 3
 LAYOUT_PIVOT, LAYOUT_DIAG = 0, 1
-K_DUAL, K_PRIMAL, K_FUSED, K_POTENTIAL, K_FFBS, K_ACCUMULATE, K_FEATURES, K_MLP, K_MH, K_COUNT = range(10)
+K_DUAL, K_PRIMAL, K_FUSED, K_POTENTIAL, K_FFBS, K_ACCUMULATE, K_FEATURES, K_MLP, K_MH, K_SMALL, K_COUNT = range(11)
 KERNEL_NAMES = ["k_dual", "k_primal", "k_primal<fused>", "k_potential", "k_ffbs", "k_accumulate",
-                "k_learned_features", "k_mlp", "k_learned_mh"]
+                "k_learned_features", "k_mlp", "k_learned_mh", "k_sweep_small"]
 
 
 class mrf_options(ct.Structure):

@@ -298,3 +298,26 @@ def test_philox_matches_curand_and_oracle():
             assert np.array_equal(mine, ref)
             orc = np.stack(ph.philox4x32_10(ctr[:, 0], ctr[:, 1], ctr[:, 2], ctr[:, 3], k0, k1), -1)
             assert np.array_equal(orc, ref)
+
+
+@pytest.mark.parametrize("name", ["ising32", "random_L3_dup", "potts_L16_diag", "star_degree700", "random_L16_C32"])
+def test_small_model_single_launch_equals_sweep_by_sweep(name):
+    """Several sweeps of a small model run in one single-CTA launch; the chain
+    (labels, counts, boundary count) is the same as one sweep at a time."""
+    model, C = CASES[name][0](), CASES[name][1]
+    out = []
+    for one_at_a_time in (False, True):
+        h = make_handle(model, C, seed=31, kernel_timing=True)
+        h.reset_marginals(2)
+        if one_at_a_time:
+            for _ in range(9):
+                h.sweep(1, M.MODE_PLAIN)
+        else:
+            h.sweep(9, M.MODE_PLAIN)
+        kt = h.kernel_times()
+        assert ("k_sweep_small" in kt) == (not one_at_a_time)
+        out.append((h.get_labels(), h.counts(), h.info().sweep_index))
+        h.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2] == 9
