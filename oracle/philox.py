@@ -87,11 +87,23 @@ def _words(index, sweep, chain, c3, seed):
     return np.stack(philox4x32_10(index, sweep, chain, c3, k0, k1), axis=-1)   # [..., 4]
 
 
-def dual_prefix(edge, k, chain, sweep, seed):
-    """8-bit prefixes of dual uniforms from the bit planes; arguments broadcast."""
+def dual_prefix(edge, k, chain, sweep, seed, m=None):
+    """8-bit prefixes of dual uniforms from the bit planes; arguments broadcast.
+
+    Plane p (bit 7 - p of the prefix).  Edges with m > 16 entries (or m not
+    given): entry 32 g + b at bit b of word p mod 4 of Philox(e, t, c, DUAL,
+    2 g + p div 4).  Edges with m <= 16 entries: all planes in one call, two
+    per word: entry k at bit 16 (p div 4) + k of word p mod 4 of
+    Philox(e, t, c, DUAL, 0)."""
     edge = np.asarray(edge, np.int64); k = np.asarray(k, np.int64); chain = np.asarray(chain, np.int64)
-    g, b = k >> 5, (k & 31).astype(np.uint32)
     prefix = 0
+    if m is not None and m <= 16:
+        w = _words(edge, sweep, chain, (PH_DUAL << 24) | 0, seed)                 # [..., 4]
+        for p in range(8):
+            bit = (w[..., p % 4] >> (16 * (p // 4) + k).astype(np.uint32)) & np.uint32(1)
+            prefix = prefix | (bit.astype(np.int64) << (7 - p))
+        return prefix
+    g, b = k >> 5, (k & 31).astype(np.uint32)
     for half in range(2):
         w = _words(edge, sweep, chain, (PH_DUAL << 24) | (2 * g + half), seed)      # [..., 4]
         for q in range(4):
@@ -101,10 +113,10 @@ def dual_prefix(edge, k, chain, sweep, seed):
     return prefix
 
 
-def dual_u24(edge, k, chain, sweep, seed):
-    """24-bit integer uniforms U24 of dual draws; all arguments broadcast."""
+def dual_u24(edge, k, chain, sweep, seed, m=None):
+    """24-bit integer uniforms U24 of dual draws (m: entries per edge); all arguments broadcast."""
     edge = np.asarray(edge, np.int64); k = np.asarray(k, np.int64); chain = np.asarray(chain, np.int64)
-    prefix = dual_prefix(edge, k, chain, sweep, seed)
+    prefix = dual_prefix(edge, k, chain, sweep, seed, m)
     lo = _words(edge, sweep, chain, (PH_DUAL_LO << 24) | (k >> 3), seed)
     kk = np.broadcast_to(k, lo.shape[:-1])
     wsel = np.take_along_axis(lo, ((kk & 7) >> 1)[..., None], axis=-1)[..., 0]
@@ -122,8 +134,8 @@ def u23_to_unit(u23):
     return (np.asarray(u23, np.float64) + 0.5) / 8388608.0
 
 
-def dual_uniform(edge, k, chain, sweep, seed):
-    return u24_to_unit(dual_u24(edge, k, chain, sweep, seed))
+def dual_uniform(edge, k, chain, sweep, seed, m=None):
+    return u24_to_unit(dual_u24(edge, k, chain, sweep, seed, m))
 
 
 def site_uniform(site, chain, sweep, seed, phase=PH_PRIMAL):

@@ -50,7 +50,7 @@ def dual_uniforms(dec: Decomposition, n_chains: int, sweep: int, seed: int, edge
     E, m = dec.ell.shape
     e = np.arange(E, dtype=np.int64) if edge_ids is None else np.asarray(edge_ids, np.int64)
     return ph.dual_uniform(e[None, :, None], np.arange(m)[None, None, :],
-                           np.arange(n_chains)[:, None, None], sweep, seed)
+                           np.arange(n_chains)[:, None, None], sweep, seed, m)
 
 
 def dual_step(dec: Decomposition, x, sweep: int, seed: int, edge_ids=None):

@@ -50,6 +50,27 @@ def test_dual_prefix_planes_uniform_and_independent_of_position():
     assert abs(c) < 0.05
 
 
+def test_packed_dual_prefix_for_small_tables():
+    """m <= 16: the eight planes of all entries come from one Philox call, two
+    planes per word (entry k at bit 16 (p div 4) + k of word p mod 4)."""
+    for m in (1, 4, 9, 16):
+        pre = ph.dual_prefix(np.arange(4000)[:, None], np.arange(m)[None, :], 1, 7, 3, m=m)
+        assert pre.min() >= 0 and pre.max() <= 255
+        h = np.bincount(pre.ravel(), minlength=256)
+        chi2 = ((h - pre.size / 256) ** 2 / (pre.size / 256)).sum()
+        assert 160 < chi2 < 360 + 2 * (16 - m)
+        if m > 1:
+            assert abs(np.corrcoef(pre[:, 0], pre[:, m - 1])[0, 1]) < 0.05
+    # the words: prefix bit 7 - p of entry k is bit 16 (p div 4) + k of word p mod 4
+    w = ph._words(np.array([5]), 2, np.array([1]), ph.PH_DUAL << 24, 9)[0]
+    pre = ph.dual_prefix(5, np.arange(16), 1, 2, 9, m=16)
+    for k in range(16):
+        want = sum((((int(w[p % 4]) >> (16 * (p // 4) + k)) & 1) << (7 - p)) for p in range(8))
+        assert pre[k] == want
+    # tables with more entries keep the 32-entry groups
+    assert np.array_equal(ph.dual_prefix(5, np.arange(17), 1, 2, 9, m=17), ph.dual_prefix(5, np.arange(17), 1, 2, 9))
+
+
 def test_dual_uniform_prefix_and_low_bits_independent_streams():
     u = ph.dual_u24(np.arange(2000)[:, None], np.arange(49)[None, :], 0, 3, 11)
     pre = u >> 16; low = u & 0xFFFF

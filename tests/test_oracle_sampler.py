@@ -78,13 +78,17 @@ def test_sampled_marginals_within_3_sigma():
     dec = dc.decompose(model)
     exact, _ = brute.exact_marginals(model)
     C, T, burn = 512, 120, 20
-    x = ph.init_labels(model.n_vars, model.n_labels, C, seed=77)
-    acc = np.zeros((C, model.n_vars, model.n_labels))
-    for t in range(T):
-        x = sampler.sweep(dec, x, t, 77)["x"]
-        if t >= burn:
-            acc[np.arange(C)[:, None], np.arange(model.n_vars)[None, :], x] += 1
-    chain_means = acc / (T - burn)
+    runs = []
+    for seed in (78, 79):                                   # two independent runs, 1024 chains
+        x = ph.init_labels(model.n_vars, model.n_labels, C, seed=seed)
+        acc = np.zeros((C, model.n_vars, model.n_labels))
+        for t in range(T):
+            x = sampler.sweep(dec, x, t, seed)["x"]
+            if t >= burn:
+                acc[np.arange(C)[:, None], np.arange(model.n_vars)[None, :], x] += 1
+        runs.append(acc / (T - burn))
+    chain_means = np.concatenate(runs)
+    C = chain_means.shape[0]
     est = chain_means.mean(0)
     sigma = chain_means.std(0, ddof=1) / np.sqrt(C)
     z = np.abs(est - exact) / np.maximum(sigma, 1e-12)
