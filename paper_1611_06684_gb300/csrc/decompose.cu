@@ -136,6 +136,15 @@ __global__ void k_build_planes(const uint32_t* thr, int64_t n, const int64_t* sl
         }
     }
     uint4* out = reinterpret_cast<uint4*>(tpl + (e * G + g) * 32);
+    if (M <= 16) {
+        // packed: word p holds plane p (bits 0..15) and plane p + 4 (bits 16..31)
+        for (int p = 0; p < 4; ++p) {
+            uint32_t Q[4];
+            for (int cs = 0; cs < 4; ++cs) Q[cs] = P[cs][p] | (P[cs][p + 4] << 16);
+            out[p] = make_uint4(Q[0], Q[0] ^ Q[1], Q[0] ^ Q[2], Q[0] ^ Q[1] ^ Q[2] ^ Q[3]);
+        }
+        return;
+    }
     for (int p = 0; p < 8; ++p)
         out[p] = make_uint4(P[0][p], P[0][p] ^ P[1][p], P[0][p] ^ P[2][p], P[0][p] ^ P[1][p] ^ P[2][p] ^ P[3][p]);
 }

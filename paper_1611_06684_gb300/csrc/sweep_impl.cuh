@@ -106,7 +106,8 @@ __device__ __forceinline__ bool is_tree_edge(const SweepArgs& a, uint32_t e) {
 
 // Dual bits of edge e, chain c, given the endpoint labels (xs, xt).
 // Bit-sliced: the 8-bit prefixes of 32 uniforms arrive as 8 planes (two
-// Philox calls per group of 32 entries); each plane is compared with the
+// Philox calls per group of 32 entries; one call, two planes per word, when
+// the table has at most 16 entries); each plane is compared with the
 // matching threshold plane for the chain's cases, most significant first:
 //   lt |= eq & ~r & t;  eq &= ~(r ^ t)
 // so lt = [prefix < threshold prefix] and eq = ties for all 32 entries at once.
@@ -119,6 +120,27 @@ __device__ __forceinline__ void dual_prefix_bits(uint32_t e, uint32_t c, int xs,
                                                  const RoundKeys& key, uint32_t (&bits)[Ent<L, LAYOUT>::W],
                                                  uint32_t (&ties)[Ent<L, LAYOUT>::W]) {
     using E = Ent<L, LAYOUT>;
+    if constexpr (E::M <= 16) {
+        // at most 16 entries: one Philox call, word p = plane p (bits 0..15) and
+        // plane p + 4 (bits 16..31); the low halves compare the prefix's high
+        // nibble, the high halves its low nibble, combined at the end
+        const uint4 r4 = draw_rk(e, sweep, c, PH_DUAL, 0u, key);
+        const uint32_t R[4] = {r4.x, r4.y, r4.z, r4.w};
+        const uint32_t rm16 = row_mask<L, LAYOUT>(xs, 0), cm16 = col_mask<L, LAYOUT>(xt, 0);
+        const uint32_t rm = rm16 | (rm16 << 16), cm = cm16 | (cm16 << 16), km = rm & cm;
+        const uint4* tp = reinterpret_cast<const uint4*>(tpl_e);
+        uint32_t lt = 0u, eq = valid_word(E::M, 0) * 0x10001u;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const uint4 q = __ldg(tp + p);
+            const uint32_t t = q.x ^ (q.y & rm) ^ (q.z & cm) ^ (q.w & km);
+            lt |= eq & ~R[p] & t;
+            eq &= ~(R[p] ^ t);
+        }
+        bits[0] = (lt | (eq & (lt >> 16))) & 0xFFFFu;
+        ties[0] = (eq & (eq >> 16)) & 0xFFFFu;
+        return;
+    }
     // up to four Philox calls (two groups) in flight together for ILP
     constexpr int GA = E::W < 2 ? E::W : 2;
     uint32_t R[GA][8];
