@@ -18,8 +18,17 @@ parallel over entries and over sites:
                  mean field: q_v = softmax(F_v).
 One iteration is a theta-update followed by an x-update.
 
-Pins (tests/test_oracle_meanfield.py): EM never decreases log p~(x) (EM on
-the latent theta); the mean-field objective KL(q_x q_theta || p(x, theta)),
+Blocked EM (Sections 5.3 and 5.4): the duals of a spanning forest T are not
+introduced (their factors stay exact); the theta-update runs on the other
+edges and the x-update is the exact MAP of the tree MRF with node potentials
+phi (oracle.blocked.node_potentials of pi) and the exact edge factors on T,
+by max-product from the leaves and argmax from the roots.  On lattices the
+forest is the comb forest of the blocked sweep, its block-grid offset drawn
+from the SPLASH phase with index = iteration number.
+
+Pins (tests/test_oracle_meanfield.py): EM and blocked EM never decrease
+log p~(x) (EM on the latent theta); the tree MAP equals the enumerated argmax
+of the tree MRF; the mean-field objective KL(q_x q_theta || p(x, theta)),
 computed by enumeration, never increases; Lemma 6's inequality
 KL(q_x q_theta* || p(x, theta)) >= KL(q_x || p(x)) at every iterate.
 """
@@ -27,9 +36,9 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import brute
+from . import blocked, brute, philox as ph
 from .decompose import Decomposition
-from .sampler import primal_field, log_softmax, sigmoid
+from .sampler import dual_probs, primal_field, log_softmax, sigmoid
 
 
 def dual_mean(dec: Decomposition, eta_y, eta_z):
@@ -76,3 +85,40 @@ def mf_objective(model, dec: Decomposition, q, pi):
     wx = np.exp(lqx)
     kl_x = float((wx * (lqx - lpx)).sum())
     return kl_joint, kl_x
+
+
+def tree_map(model, phi, parent, tree, order):
+    """MAP labels [C][N] of the tree MRF (node potentials phi [C][N][L], exact
+    edge factors on the forest), by max-product messages and argmax (first
+    maximum) from the roots down."""
+    C, N, L = phi.shape
+    pe, child_is_src = blocked._edge_to_parent(model.src, model.dst, parent, tree)
+    w = np.asarray(model.pair, np.float64)
+    inbox = np.zeros((C, N, L))
+    psi = np.zeros((N, L, L))
+    for v in order[::-1]:
+        p = parent[v]
+        if p < 0:
+            continue
+        psi[v] = w[pe[v]].T if child_is_src[v] else w[pe[v]]      # [parent label][child label]
+        lv = phi[:, v, :] + inbox[:, v, :]
+        inbox[:, p, :] += np.max(lv[:, None, :] + psi[v][None], axis=-1)
+    x = np.zeros((C, N), np.int64)
+    for v in order:
+        lv = phi[:, v, :] + inbox[:, v, :]
+        p = parent[v]
+        if p >= 0:
+            lv = lv + psi[v][x[:, p]]
+        x[:, v] = np.argmax(lv, axis=1)
+    return x
+
+
+def blocked_em_step(model, dec: Decomposition, x, iteration: int, seed: int, parent=None):
+    """One blocked EM iteration from labels x [C][N]; returns the new labels."""
+    if parent is None:
+        parent = blocked.comb_forest(model.grid, ph.splash_offset(iteration, seed))
+    tree = blocked.tree_edge_mask(dec.src, dec.dst, parent)
+    pi = np.where(dec.active[None] & ~tree[None, :, None], dual_probs(dec, x), 0.0)
+    phi = blocked.node_potentials(model, dec, tree, pi)
+    order, _ = blocked.bfs_order(parent)
+    return tree_map(model, phi, parent, tree, order)

@@ -49,3 +49,36 @@ def test_mf_step_uses_expected_indicators():
     _, pi_e, F_e = mf.em_step(dec, x)
     np.testing.assert_allclose(pi_m, pi_e, rtol=0, atol=1e-15)
     np.testing.assert_allclose(F_m, F_e, rtol=0, atol=1e-12)
+
+
+def test_tree_map_is_the_enumerated_argmax():
+    """One 4x4x4-block lattice small enough to enumerate: the tree MAP equals
+    the argmax of phi + exact tree factors over all labelings."""
+    model = wl.potts_grid3d(3, 2, 2, L=3, seed=6)
+    dec = dc.decompose(model)
+    from oracle import blocked
+    parent = blocked.comb_forest(model.grid, (0, 0, 0))
+    tree = blocked.tree_edge_mask(dec.src, dec.dst, parent)
+    rng = np.random.default_rng(3)
+    phi = rng.normal(0, 1, size=(4, model.n_vars, 3))
+    order, _ = blocked.bfs_order(parent)
+    x = mf.tree_map(model, phi, parent, tree, order)
+    X = brute.all_labelings(model.n_vars, 3)
+    w = np.asarray(model.pair, np.float64)
+    te = np.nonzero(tree)[0]
+    for c in range(4):
+        score = phi[c][np.arange(model.n_vars)[None, :], X].sum(axis=1)
+        score += w[te[None, :], X[:, model.src[te]], X[:, model.dst[te]]].sum(axis=1)
+        assert np.array_equal(x[c], X[np.argmax(score)])
+
+
+def test_blocked_em_never_decreases_log_ptilde():
+    model = wl.potts_grid3d(9, 7, 6, L=4, seed=7)
+    dec = dc.decompose(model)
+    x = np.random.default_rng(4).integers(0, 4, size=(3, model.n_vars))
+    prev = brute.log_ptilde(model, x)
+    for it in range(8):
+        x = mf.blocked_em_step(model, dec, x, it, 11)
+        cur = brute.log_ptilde(model, x)
+        assert (cur >= prev - 1e-9).all()
+        prev = cur
