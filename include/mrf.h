@@ -202,6 +202,14 @@ mrf_status mrf_estimate_log_partition(mrf_t* h, int32_t n_sweeps, double* log_v)
  * iteration does not decrease log p~(x).  The sampler's state is untouched. */
 mrf_status mrf_map_em(mrf_t* h, int32_t n_iters, uint8_t* labels, int32_t ptr_kind);
 
+/* Blocked EM on a lattice handle (options.grid; Sections 5.3 and 5.4): the
+ * duals of the comb forest of 4x4x4 blocks are not introduced; each iteration
+ * i takes the block offset from the SPLASH draw with index i, the expected
+ * duals of all other edges given the labels, and sets the labels to the exact
+ * MAP of the resulting tree MRF (max-product, first maximum).  labels[C][N]
+ * in/out as for mrf_map_em.  Every iteration does not decrease log p~(x). */
+mrf_status mrf_map_em_blocked(mrf_t* h, int32_t n_iters, uint8_t* labels, int32_t ptr_kind);
+
 /* Primal-dual mean field (Section 5.3): n_iters iterations of
  *   xi = E[r(theta) | eta],  eta = E[s(x)] from the site marginals q
  *   q_v = softmax of the field of xi

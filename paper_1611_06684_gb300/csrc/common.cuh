@@ -170,7 +170,9 @@ cudaError_t launch_mlp_images(const LearnedArgs& a, cudaStream_t s);
 cudaError_t launch_learned_mlp_tc(const LearnedArgs& a, cudaStream_t s);
 cudaError_t launch_advance(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_splash(const SweepArgs& a, int layout, cudaStream_t s);
-cudaError_t launch_splash_offset(const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_splash_offset(const SweepArgs& a, cudaStream_t s, int64_t iter = -1);
+cudaError_t launch_tree_map(const SweepArgs& a, uint8_t* xout, cudaStream_t s);
+cudaError_t launch_em_pot(const SweepArgs& a, int layout, const uint8_t* xin, cudaStream_t s);
 cudaError_t launch_potential(const SweepArgs& a, int layout, cudaStream_t s);
 cudaError_t launch_ffbs(const SweepArgs& a, cudaStream_t s);
 cudaError_t build_csr_device(const int32_t* src, const int32_t* dst, int64_t E, int N, int64_t* ptr, int2* inc,

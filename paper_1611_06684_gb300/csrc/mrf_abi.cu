@@ -790,6 +790,37 @@ mrf_status mrf_map_em(mrf_t* h, int32_t n_iters, uint8_t* labels, int32_t ptr_ki
     return MRF_OK;
 }
 
+mrf_status mrf_map_em_blocked(mrf_t* h, int32_t n_iters, uint8_t* labels, int32_t ptr_kind) {
+    if (!h || !labels || n_iters < 0) return MRF_EINVAL;
+    if (!h->has_factors) return fail(h, MRF_ESTATE, "mrf_set_factors first");
+    if (h->opt.grid_nx <= 0 || !h->d_resid) return fail(h, MRF_ESTATE, "blocked EM needs options.grid");
+    const size_t NC = (size_t)h->N * h->C;
+    if (!h->d_stage) MRF_CUDA(h, dalloc(h->d_stage, NC));
+    if (!h->d_em) MRF_CUDA(h, dalloc(h->d_em, 2 * NC));
+    if (!h->d_pot) { drop_graphs(h); MRF_CUDA(h, dalloc(h->d_pot, (size_t)h->N * h->L * h->C)); }
+    MRF_CUDA(h, to_device(h->d_stage, labels, (int64_t)NC, ptr_kind, h->stream));
+    MRF_CUDA(h, cudaMemsetAsync(h->d_flag, 0, sizeof(unsigned long long), h->stream));
+    MRF_CUDA(h, launch_count_ge(h->d_stage, (int64_t)NC, h->L, h->d_flag, h->stream));
+    unsigned long long bad = 0;
+    MRF_CUDA(h, cudaMemcpyAsync(&bad, h->d_flag, sizeof(bad), cudaMemcpyDeviceToHost, h->stream));
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (bad) return fail(h, MRF_ERANGE, "label out of range");
+    MRF_CUDA(h, launch_labels_from_abi(h->d_stage, h->d_em, h->N, h->C, h->stream));
+    SweepArgs a = make_args(h);
+    a.splash = 1;
+    for (int i = 0; i < n_iters; ++i) {
+        // block offset of iteration i, potentials from the expected non-tree duals, tree MAP
+        MRF_CUDA(h, launch_splash_offset(a, h->stream, i));
+        MRF_CUDA(h, launch_em_pot(a, h->layout, h->d_em + (i & 1) * NC, h->stream));
+        MRF_CUDA(h, launch_tree_map(a, h->d_em + ((i + 1) & 1) * NC, h->stream));
+    }
+    MRF_CUDA(h, launch_labels_to_abi(h->d_em + (n_iters & 1) * NC, h->d_stage, h->N, h->C, h->stream));
+    MRF_CUDA(h, cudaMemcpyAsync(labels, h->d_stage, NC,
+                                ptr_kind == MRF_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream));
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    return MRF_OK;
+}
+
 mrf_status mrf_mean_field(mrf_t* h, int32_t n_iters, float* marginals, int32_t ptr_kind) {
     if (!h || !marginals || n_iters < 0) return MRF_EINVAL;
     if (!h->has_factors) return fail(h, MRF_ESTATE, "mrf_set_factors first");

@@ -15,8 +15,10 @@ namespace mrfk {
 
 template <int L, int LAYOUT> cudaError_t run_potential(const SweepArgs& a, cudaStream_t s);
 
-__global__ void k_splash_offset(SweepArgs a) {
-    const uint32_t t = (uint32_t)a.ctl->sweep;
+// Offset of the block grid for blocked sweep t (t = the sweep index) or, for
+// blocked EM, iteration t (iter >= 0).
+__global__ void k_splash_offset(SweepArgs a, int64_t iter) {
+    const uint32_t t = iter >= 0 ? (uint32_t)iter : (uint32_t)a.ctl->sweep;
     const uint4 r = draw(0, t, 0, PH_SPLASH, 0, a.key);
     a.ctl->splash_offset = (r.x >> 30) | ((r.y >> 30) << 8) | ((r.z >> 30) << 16);
 }
@@ -59,6 +61,22 @@ __device__ __forceinline__ void tree_message(const float (&bel)[L], const float*
     for (int b = 0; b < L; ++b) out[b] -= top;
 }
 
+// Max-product counterpart: out[b] = max_a (bel[a] + psi[b][a]) - max_b(...).
+template <int L>
+__device__ __forceinline__ void tree_message_max(const float (&bel)[L], const float* __restrict__ psi, float (&out)[L]) {
+    float top = -INFINITY;
+#pragma unroll
+    for (int b = 0; b < L; ++b) {
+        float mx = -INFINITY;
+#pragma unroll
+        for (int x = 0; x < L; ++x) mx = fmaxf(mx, bel[x] + __ldg(psi + b * L + x));
+        out[b] = mx;
+        top = fmaxf(top, mx);
+    }
+#pragma unroll
+    for (int b = 0; b < L; ++b) out[b] -= top;
+}
+
 template <int L>
 __device__ __forceinline__ void label_draw_ffbs(const float (&F)[L], uint32_t v, uint32_t c, uint32_t sweep, uint2 key,
                                                 float* logp_out, Ctl* ctl, int& lab) {
@@ -93,8 +111,10 @@ __device__ __forceinline__ void label_draw_ffbs(const float (&F)[L], uint32_t v,
 }
 
 // One thread per (block, chain); lanes are consecutive chains of one block.
-template <int L>
-__global__ void __launch_bounds__(128) k_ffbs(SweepArgs a) {
+// MAP = true (blocked EM): max-product messages and argmax labels (first
+// maximum) written to xmap instead of sampled labels.
+template <int L, bool MAP = false>
+__global__ void __launch_bounds__(128) k_ffbs(SweepArgs a, uint8_t* __restrict__ xmap = nullptr) {
     int ox, oy, oz;
     {
         const uint32_t o = (uint32_t)a.ctl->splash_offset;
@@ -112,7 +132,7 @@ __global__ void __launch_bounds__(128) k_ffbs(SweepArgs a) {
     const int z0 = max(0, 4 * bz - oz), z1 = min(nz, 4 * bz + 4 - oz);
     const int sx = x1 - x0, sy = y1 - y0, sz = z1 - z0;
     const uint32_t sweep = (uint32_t)a.ctl->sweep;
-    uint8_t* xout = a.x + (size_t)((sweep + 1) & 1) * a.N * a.C;
+    uint8_t* xout = MAP ? xmap : a.x + (size_t)((sweep + 1) & 1) * a.N * a.C;
     const int64_t C = a.C;
     auto site = [&](int x, int y, int z) -> int64_t { return x + (int64_t)nx * (y + (int64_t)ny * z); };
     auto xedge = [&](int x, int y, int z) -> int64_t { return ((int64_t)z * ny + y) * (nx - 1) + x; };
@@ -157,9 +177,13 @@ __global__ void __launch_bounds__(128) k_ffbs(SweepArgs a) {
             bel[x] = f;
             pv[x * C] = f;
         }
-        if (lx > 0) tree_message<L>(bel, a.resid + xedge(X - 1, Y, Z) * L * L, xm);
-        else if (ly > 0) tree_message<L>(bel, a.resid + yedge(X, Y - 1, Z) * L * L, ym);
-        else if (lz > 0) tree_message<L>(bel, a.resid + zedge(X, Y, Z - 1) * L * L, zm);
+        auto send = [&](const float* pe, float (&msg)[L]) {
+            if (MAP) tree_message_max<L>(bel, pe, msg);
+            else tree_message<L>(bel, pe, msg);
+        };
+        if (lx > 0) send(a.resid + xedge(X - 1, Y, Z) * L * L, xm);
+        else if (ly > 0) send(a.resid + yedge(X, Y - 1, Z) * L * L, ym);
+        else if (lz > 0) send(a.resid + zedge(X, Y, Z - 1) * L * L, zm);
         lx = px; ly = py; lz = pz;
     }
     // downward pass: root, then every child given its parent's label
@@ -178,9 +202,16 @@ __global__ void __launch_bounds__(128) k_ffbs(SweepArgs a) {
                 float F[L];
 #pragma unroll
                 for (int x = 0; x < L; ++x) F[x] = pv[x * C] + (psi ? __ldg(psi + pl * L + x) : 0.0f);
-                float* lp = a.logp ? a.logp + ((int64_t)c * a.N + v) * L : nullptr;
-                int lab;
-                label_draw_ffbs<L>(F, (uint32_t)v, c, sweep, a.key, lp, a.ctl, lab);
+                int lab = 0;
+                if (MAP) {
+                    float fb = F[0];
+#pragma unroll
+                    for (int x = 1; x < L; ++x)
+                        if (F[x] > fb) { fb = F[x]; lab = x; }
+                } else {
+                    float* lp = a.logp ? a.logp + ((int64_t)c * a.N + v) * L : nullptr;
+                    label_draw_ffbs<L>(F, (uint32_t)v, c, sweep, a.key, lp, a.ctl, lab);
+                }
                 xout[v * C + c] = (uint8_t)lab;
                 xl = lab;
                 if (lx == 0) {
@@ -210,8 +241,8 @@ __global__ void __launch_bounds__(128) k_ffbs(SweepArgs a) {
         default: return cudaErrorInvalidValue;                                    \
     }
 
-cudaError_t launch_splash_offset(const SweepArgs& a, cudaStream_t s) {
-    k_splash_offset<<<1, 1, 0, s>>>(a);
+cudaError_t launch_splash_offset(const SweepArgs& a, cudaStream_t s, int64_t iter) {
+    k_splash_offset<<<1, 1, 0, s>>>(a, iter);
     return cudaGetLastError();
 }
 
@@ -221,6 +252,14 @@ cudaError_t launch_potential(const SweepArgs& a, int layout, cudaStream_t s) {
     } else {
         MRF_DISPATCH_L2(a.L, return (run_potential<LL, MRF_LAYOUT_DIAG>(a, s)));
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tree_map(const SweepArgs& a, uint8_t* xout, cudaStream_t s) {
+    const int64_t nb = (int64_t)(a.grid_nx / 4 + 2) * (a.grid_ny / 4 + 2) * (a.grid_nz / 4 + 2);
+    const int64_t n = nb * a.C;
+    const unsigned blocks = (unsigned)((n + 127) / 128);
+    MRF_DISPATCH_L2(a.L, (k_ffbs<LL, true><<<blocks, 128, 0, s>>>(a, xout)));
     return cudaGetLastError();
 }
 

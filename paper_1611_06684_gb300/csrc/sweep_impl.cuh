@@ -801,6 +801,33 @@ __global__ void __launch_bounds__(256) k_em(SweepArgs a, const uint8_t* __restri
     xout[g] = (uint8_t)best;
 }
 
+// Blocked EM, potentials: F_v = u~_v + the beta pi of the expected duals of
+// v's incident non-tree edges (the comb forest of the current block offset),
+// written to a.pot ([N][L][C]) for the tree MAP.
+template <int L, int LAYOUT>
+__global__ void __launch_bounds__(256) k_em_pot(SweepArgs a, const uint8_t* __restrict__ xin) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (uint64_t)a.N * a.C) return;
+    const uint32_t v = a.fdC.div(g), c = g - v * (uint32_t)a.C;
+    const int xv = xin[g];
+    float acc[L];
+#pragma unroll
+    for (int x = 0; x < L; ++x) acc[x] = 0.0f;
+    for (int64_t p = a.inc_ptr[v]; p < a.inc_ptr[v + 1]; ++p) {
+        const int2 ic = __ldg(&a.inc[p]);
+        if (is_tree_edge(a, (uint32_t)(ic.x >> 1))) continue;
+        const int side = ic.x & 1;
+        const int xu = xin[(int64_t)ic.y * a.C + c];
+        const int xs = side == 0 ? xv : xu, xt = side == 0 ? xu : xv;
+        add_side_mean<L, LAYOUT>(a.tau + (int64_t)(ic.x >> 1) * Ent<L, LAYOUT>::MP, side,
+                                 [&](int i) { return xs == i ? 1.0f : 0.0f; }, [&](int j) { return xt == j ? 1.0f : 0.0f; }, acc);
+    }
+    const float* uf = a.utf + (int64_t)v * L;
+    float* pv = a.pot + (int64_t)v * L * a.C + c;
+#pragma unroll
+    for (int x = 0; x < L; ++x) pv[(int64_t)x * a.C] = __ldg(uf + x) + acc[x];
+}
+
 // Mean field: q' = softmax of the field of the expected duals given the site
 // marginals q ([N][L][C], chain innermost).
 template <int L, int LAYOUT>
@@ -903,7 +930,16 @@ cudaError_t run_sweep_small(const SweepArgs& a, int n_sweeps, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int L, int LAYOUT>
+cudaError_t run_em_pot(const SweepArgs& a, const uint8_t* xin, cudaStream_t s) {
+    const int64_t n = (int64_t)a.N * a.C;
+    if (n > 0) k_em_pot<L, LAYOUT><<<blocks_for(n, 256), 256, 0, s>>>(a, xin);
+    return cudaGetLastError();
+}
+
 #define MRF_INSTANTIATE_SWEEP(L)                                                                 \
+    template cudaError_t run_em_pot<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, const uint8_t*, cudaStream_t); \
+    template cudaError_t run_em_pot<L, MRF_LAYOUT_DIAG>(const SweepArgs&, const uint8_t*, cudaStream_t);  \
     template cudaError_t run_sweep_small<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, int, cudaStream_t); \
     template cudaError_t run_sweep_small<L, MRF_LAYOUT_DIAG>(const SweepArgs&, int, cudaStream_t);  \
     template cudaError_t run_em<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, const uint8_t*, uint8_t*, cudaStream_t); \

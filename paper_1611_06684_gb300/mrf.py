@@ -64,6 +64,7 @@ _SIGS = {
     "mrf_set_kernel_timing": (ct.c_int, [_P, ct.c_int32]),
     "mrf_estimate_log_partition": (ct.c_int, [_P, ct.c_int32, _P]),
     "mrf_map_em": (ct.c_int, [_P, ct.c_int32, _P, ct.c_int32]),
+    "mrf_map_em_blocked": (ct.c_int, [_P, ct.c_int32, _P, ct.c_int32]),
     "mrf_mean_field": (ct.c_int, [_P, ct.c_int32, _P, ct.c_int32]),
     "mrf_philox_rate": (ct.c_int, [ct.c_uint64, ct.c_int32, _P, ct.POINTER(ct.c_double)]),
     "mrf_sweep_noalloc": (ct.c_int, [_P, _P, _P, ct.c_int64]),
@@ -334,6 +335,12 @@ class MRF:
         """Primal-dual EM from labels [C][N]; returns the labels after n_iters iterations."""
         x = np.ascontiguousarray(labels, np.uint8).copy()
         self._check(self.lib.mrf_map_em(self.h, int(n_iters), x.ctypes.data, MRF_PTR_HOST))
+        return x
+
+    def map_em_blocked(self, labels, n_iters: int):
+        """Blocked EM (lattice handles) from labels [C][N]; returns the labels after n_iters iterations."""
+        x = np.ascontiguousarray(labels, np.uint8).copy()
+        self._check(self.lib.mrf_map_em_blocked(self.h, int(n_iters), x.ctypes.data, MRF_PTR_HOST))
         return x
 
     def mean_field(self, marginals, n_iters: int):

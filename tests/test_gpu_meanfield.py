@@ -81,3 +81,28 @@ def test_mean_field_matches_oracle(name):
     np.testing.assert_allclose(qn.sum(axis=2), 1.0, atol=1e-5)
     assert (qn >= 0).all()
     h.close()
+
+
+@pytest.mark.parametrize("dims,L,C", [((9, 8, 7), 8, 32), ((10, 9, 5), 4, 3), ((13, 5, 6), 3, 2)])
+def test_blocked_em_matches_oracle(dims, L, C):
+    from paper_1611_06684_gb300 import mrf as M
+    model = wl.potts_grid3d(*dims, L=L, seed=8)
+    dec = dc.decompose(model)
+    x = np.random.default_rng(5).integers(0, L, size=(C, model.n_vars))
+    h = M.MRF(model.n_vars, L, C, seed=13, grid=model.grid)
+    h.set_factors(model.unary, model.src, model.dst, model.pair)
+    prev = brute.log_ptilde(model, x)
+    xr = x
+    for it in range(3):
+        xg = h.map_em_blocked(xr, 1) if it == 0 else None
+        xr_next = mf.blocked_em_step(model, dec, xr, it, 13)
+        if it == 0:
+            # the GPU's first iteration (offset of iteration 0) equals the oracle's
+            # away from near-ties of the max-product scores
+            assert np.mean(xg != xr_next) < 1e-2, np.mean(xg != xr_next)   # a near-tie at a root flips its subtree
+        xr = xr_next
+    xg3 = h.map_em_blocked(x, 3)
+    assert np.mean(xg3 != xr) < 3e-2
+    cur = brute.log_ptilde(model, xg3)
+    assert (cur >= prev - 1e-6 * np.abs(prev)).all()
+    h.close()
