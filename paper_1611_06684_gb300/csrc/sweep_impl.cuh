@@ -313,7 +313,25 @@ __global__ void __launch_bounds__(256, 4) k_dual(SweepArgs a) {
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (lane == 0) a.tie_count[gw] = (uint8_t)min(total, a.tie_cap);
     if (n) {
+        // records of the ties that fit; [x_s = i_k] and [x_t = j_k] from the entry masks
         uint16_t* rec = a.ties + gw * a.tie_cap;
+        int i = incl - n;
+#pragma unroll
+        for (int w = 0; w < E::W; ++w) {
+            uint32_t tw = ties[w];
+            if (!tw) continue;
+            const uint32_t ym = row_mask<L, LAYOUT>(xs, w), zm = col_mask<L, LAYOUT>(xt, w);
+            while (tw) {
+                const int b = __ffs(tw) - 1;
+                tw &= tw - 1u;
+                if (i < a.tie_cap)
+                    rec[i] = (uint16_t)(lane | (((ym >> b) & 1u) << 5) | (((zm >> b) & 1u) << 6) | ((32 * w + b) << 8));
+                ++i;
+            }
+        }
+    }
+    if (total > a.tie_cap && incl > a.tie_cap) {
+        // rare: this lane's ties past the warp's region are decided here
         int i = incl - n;
 #pragma unroll 1
         for (int w = 0; w < E::W; ++w) {
@@ -322,10 +340,9 @@ __global__ void __launch_bounds__(256, 4) k_dual(SweepArgs a) {
                 const int b = __ffs(tw) - 1;
                 tw &= tw - 1u;
                 const int k = 32 * w + b;
-                const int y = xs == entry_row<L, LAYOUT>(k), z = xt == entry_col<L, LAYOUT>(k);
-                if (i < a.tie_cap)
-                    rec[i] = (uint16_t)(lane | (y << 5) | (z << 6) | (k << 8));
-                else if (resolve_tie(e, c, y, z, k, __ldg(a.thr + (int64_t)e * E::M + k), sweep, a.rk))
+                if (i >= a.tie_cap &&
+                    resolve_tie(e, c, xs == entry_row<L, LAYOUT>(k), xt == entry_col<L, LAYOUT>(k), k,
+                                __ldg(a.thr + (int64_t)e * E::M + k), sweep, a.rk))
                     bits[w] |= 1u << b;
                 ++i;
             }
