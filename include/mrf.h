@@ -217,6 +217,17 @@ mrf_status mrf_map_em_blocked(mrf_t* h, int32_t n_iters, uint8_t* labels, int32_
  * row a distribution over labels).  The sampler's state is untouched. */
 mrf_status mrf_mean_field(mrf_t* h, int32_t n_iters, float* marginals, int32_t ptr_kind);
 
+/* Checkpoint of a handle to a file: the model's device tables (unaries,
+ * edge slots, decomposition tables), the labels of every chain, the marginal
+ * counts and the sweep index, so that mrf_load resumes the same chains: the
+ * sweeps after a load are the ones the saved handle would have run, bit for
+ * bit.  The learned proposal is not saved (set it up again after a load).
+ * Errors: MRF_ESTATE before mrf_set_factors, MRF_EINVAL if the file cannot be
+ * written / read or is not a checkpoint. */
+mrf_status mrf_save(mrf_t* h, const char* path);
+/* A new handle from a checkpoint, on `cuda_stream`; *out = NULL on error. */
+mrf_status mrf_load(mrf_t** out, const char* path, void* cuda_stream);
+
 /* Switch options.kernel_timing on (1) or off (0) for later sweeps. */
 mrf_status mrf_set_kernel_timing(mrf_t* h, int32_t on);
 

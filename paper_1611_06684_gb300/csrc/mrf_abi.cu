@@ -841,6 +841,137 @@ mrf_status mrf_mean_field(mrf_t* h, int32_t n_iters, float* marginals, int32_t p
     return MRF_OK;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------- checkpoints
+
+namespace {
+
+constexpr char kCkptMagic[8] = {'M', 'R', 'F', 'C', 'K', 'P', 'T', '1'};
+
+struct CkptHeader {
+    int32_t N, L, C, layout, M, W;
+    int64_t E_live, E_slots, n_free, sweep_host, count_from_host;
+    uint64_t seed;
+    double log_const;
+    int32_t has_resid, reserved;
+    mrf_options opt;
+    Ctl ctl;
+};
+
+template <typename T>
+bool write_dev(FILE* f, const T* d, size_t n, std::vector<uint8_t>& buf, cudaStream_t s) {
+    if (n == 0) return true;
+    buf.resize(n * sizeof(T));
+    if (cudaMemcpyAsync(buf.data(), d, n * sizeof(T), cudaMemcpyDeviceToHost, s) != cudaSuccess) return false;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return false;
+    return fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+}
+
+template <typename T>
+bool read_dev(FILE* f, T* d, size_t n, std::vector<uint8_t>& buf, cudaStream_t s) {
+    if (n == 0) return true;
+    buf.resize(n * sizeof(T));
+    if (fread(buf.data(), 1, buf.size(), f) != buf.size()) return false;
+    if (cudaMemcpyAsync(d, buf.data(), buf.size(), cudaMemcpyHostToDevice, s) != cudaSuccess) return false;
+    return cudaStreamSynchronize(s) == cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+mrf_status mrf_save(mrf_t* h, const char* path) {
+    if (!h || !path) return MRF_EINVAL;
+    if (!h->has_factors) return fail(h, MRF_ESTATE, "mrf_set_factors first");
+    CkptHeader hd{};
+    hd.N = h->N; hd.L = h->L; hd.C = h->C; hd.layout = h->layout; hd.M = h->M; hd.W = h->W;
+    hd.E_live = h->E_live; hd.E_slots = h->E_slots; hd.n_free = (int64_t)h->free_slots.size();
+    hd.sweep_host = h->sweep_host; hd.count_from_host = h->count_from_host; hd.seed = h->seed; hd.log_const = h->log_const;
+    hd.has_resid = h->d_resid ? 1 : 0;
+    hd.opt = h->opt;
+    MRF_CUDA(h, cudaMemcpyAsync(&hd.ctl, h->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(h, MRF_EINVAL, std::string("cannot open ") + path + " for writing");
+    const size_t NL = (size_t)h->N * h->L, E = (size_t)h->E_slots, L = (size_t)h->L;
+    std::vector<uint8_t> buf;
+    bool ok = fwrite(kCkptMagic, 1, 8, f) == 8 && fwrite(&hd, sizeof(hd), 1, f) == 1;
+    ok = ok && write_dev(f, h->d_unary, NL, buf, h->stream) && write_dev(f, h->d_ut, NL, buf, h->stream) &&
+         write_dev(f, h->d_utf, NL, buf, h->stream);
+    ok = ok && (E == 0 || (fwrite(h->h_src.data(), sizeof(int32_t), E, f) == E && fwrite(h->h_dst.data(), sizeof(int32_t), E, f) == E));
+    ok = ok && write_dev(f, h->d_tau, E * pad4(h->M), buf, h->stream) && write_dev(f, h->d_thr, E * h->M, buf, h->stream) &&
+         write_dev(f, h->d_tpl, E * h->W * 32, buf, h->stream) && write_dev(f, h->d_fold, E * 2 * L, buf, h->stream) &&
+         write_dev(f, h->d_cst, E, buf, h->stream);
+    if (hd.has_resid) ok = ok && write_dev(f, h->d_resid, E * L * L, buf, h->stream);
+    ok = ok && write_dev(f, h->d_x, 2 * (size_t)h->N * h->C, buf, h->stream) && write_dev(f, h->d_counts, NL, buf, h->stream);
+    ok = ok && (hd.n_free == 0 || fwrite(h->free_slots.data(), sizeof(int64_t), (size_t)hd.n_free, f) == (size_t)hd.n_free);
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) return fail(h, MRF_ECUDA, std::string("writing ") + path + " failed");
+    return MRF_OK;
+}
+
+mrf_status mrf_load(mrf_t** out, const char* path, void* cuda_stream) {
+    if (!out || !path) return MRF_EINVAL;
+    *out = nullptr;
+    FILE* f = fopen(path, "rb");
+    if (!f) return MRF_EINVAL;
+    char magic[8];
+    CkptHeader hd{};
+    if (fread(magic, 1, 8, f) != 8 || std::memcmp(magic, kCkptMagic, 8) != 0 || fread(&hd, sizeof(hd), 1, f) != 1 ||
+        hd.E_slots < 0 || hd.E_live < 0 || hd.E_live > hd.E_slots || hd.n_free < 0 || hd.M != n_entries(hd.L, hd.layout)) {
+        fclose(f);
+        return MRF_EINVAL;
+    }
+    mrf_t* h = nullptr;
+    mrf_status st = mrf_create(&h, hd.N, hd.L, hd.C, hd.seed, &hd.opt, cuda_stream);
+    if (st != MRF_OK) { fclose(f); return st; }
+    auto bail = [&](mrf_status code) { fclose(f); mrf_destroy(h); return code; };
+    h->layout = hd.layout; h->M = hd.M; h->W = hd.W;
+    h->E_live = hd.E_live; h->E_slots = h->E_cap = hd.E_slots;
+    const size_t NL = (size_t)h->N * h->L, E = (size_t)hd.E_slots, L = (size_t)h->L;
+    if ((uint64_t)E * h->C >= (1ull << 32)) return bail(MRF_ERANGE);
+    std::vector<uint8_t> buf;
+    bool ok = read_dev(f, h->d_unary, NL, buf, h->stream) && read_dev(f, h->d_ut, NL, buf, h->stream) &&
+              read_dev(f, h->d_utf, NL, buf, h->stream);
+    h->h_src.resize(E); h->h_dst.resize(E);
+    ok = ok && (E == 0 || (fread(h->h_src.data(), sizeof(int32_t), E, f) == E && fread(h->h_dst.data(), sizeof(int32_t), E, f) == E));
+    for (size_t e = 0; ok && e < E; ++e)
+        if (h->h_src[e] >= h->N || h->h_dst[e] >= h->N || (h->h_src[e] < 0) != (h->h_dst[e] < 0)) ok = false;
+    if (!ok) return bail(MRF_EINVAL);
+    if (dalloc(h->d_src, E) || dalloc(h->d_dst, E) || dalloc(h->d_tau, E * pad4(h->M)) || dalloc(h->d_thr, E * h->M) ||
+        dalloc(h->d_tpl, E * h->W * 32) || dalloc(h->d_fold, E * 2 * L) || dalloc(h->d_cst, E) ||
+        (hd.has_resid && dalloc(h->d_resid, E * L * L)) || dalloc(h->d_theta, E * h->C * h->W) || alloc_ties(h, (int64_t)E)) {
+        cudaGetLastError();
+        return bail(MRF_ENOMEM);
+    }
+    ok = to_device(h->d_src, h->h_src.data(), (int64_t)E, MRF_PTR_HOST, h->stream) == cudaSuccess &&
+         to_device(h->d_dst, h->h_dst.data(), (int64_t)E, MRF_PTR_HOST, h->stream) == cudaSuccess;
+    ok = ok && read_dev(f, h->d_tau, E * pad4(h->M), buf, h->stream) && read_dev(f, h->d_thr, E * h->M, buf, h->stream) &&
+         read_dev(f, h->d_tpl, E * h->W * 32, buf, h->stream) && read_dev(f, h->d_fold, E * 2 * L, buf, h->stream) &&
+         read_dev(f, h->d_cst, E, buf, h->stream);
+    if (hd.has_resid) ok = ok && read_dev(f, h->d_resid, E * L * L, buf, h->stream);
+    ok = ok && read_dev(f, h->d_x, 2 * (size_t)h->N * h->C, buf, h->stream) && read_dev(f, h->d_counts, NL, buf, h->stream);
+    h->free_slots.resize((size_t)hd.n_free);
+    ok = ok && (hd.n_free == 0 || fread(h->free_slots.data(), sizeof(int64_t), (size_t)hd.n_free, f) == (size_t)hd.n_free);
+    if (!ok) return bail(MRF_EINVAL);
+    fclose(f);
+    if (build_csr(h) != cudaSuccess) { cudaGetLastError(); mrf_destroy(h); return MRF_ECUDA; }
+    if (cudaMemcpyAsync(h->d_ctl, &hd.ctl, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        mrf_destroy(h);
+        return MRF_ECUDA;
+    }
+    h->sweep_host = hd.sweep_host;
+    h->count_from_host = hd.count_from_host;
+    h->log_const = hd.log_const;
+    h->has_factors = true;
+    h->schedule = 0;
+    *out = h;
+    return MRF_OK;
+}
+
 mrf_status mrf_get_counts(mrf_t* h, uint32_t* out, int32_t ptr_kind) {
     if (!h || !out) return MRF_EINVAL;
     const size_t n = (size_t)h->N * h->L;

@@ -64,6 +64,8 @@ _SIGS = {
     "mrf_set_kernel_timing": (ct.c_int, [_P, ct.c_int32]),
     "mrf_estimate_log_partition": (ct.c_int, [_P, ct.c_int32, _P]),
     "mrf_map_em": (ct.c_int, [_P, ct.c_int32, _P, ct.c_int32]),
+    "mrf_save": (ct.c_int, [_P, ct.c_char_p]),
+    "mrf_load": (ct.c_int, [ct.POINTER(_P), ct.c_char_p, _P]),
     "mrf_map_em_blocked": (ct.c_int, [_P, ct.c_int32, _P, ct.c_int32]),
     "mrf_mean_field": (ct.c_int, [_P, ct.c_int32, _P, ct.c_int32]),
     "mrf_philox_rate": (ct.c_int, [ct.c_uint64, ct.c_int32, _P, ct.POINTER(ct.c_double)]),
@@ -330,6 +332,26 @@ class MRF:
         out = np.zeros((int(n_sweeps), self.C), np.float64)
         self._check(self.lib.mrf_estimate_log_partition(self.h, int(n_sweeps), out.ctypes.data))
         return out
+
+    def save(self, path: str):
+        """Checkpoint of the model and the chains (mrf_save)."""
+        self._check(self.lib.mrf_save(self.h, str(path).encode()))
+
+    @classmethod
+    def load(cls, path: str, stream=None):
+        """A handle resumed from a checkpoint (mrf_load)."""
+        lib = load()
+        st_ptr = _current_stream() if stream is None else int(stream)
+        h = _P()
+        st = lib.mrf_load(ct.byref(h), str(path).encode(), _P(st_ptr))
+        if st != MRF_OK:
+            raise MrfError(st, lib.mrf_status_string(st).decode())
+        obj = cls.__new__(cls)
+        inf = mrf_info()
+        lib.mrf_get_info(h, ct.byref(inf))
+        obj.h, obj.lib, obj.stream = h, lib, st_ptr
+        obj.N, obj.L, obj.C = inf.n_vars, inf.n_labels, inf.n_chains
+        return obj
 
     def map_em(self, labels, n_iters: int):
         """Primal-dual EM from labels [C][N]; returns the labels after n_iters iterations."""
