@@ -65,3 +65,22 @@ def test_chain_estimates_bracket_log_z():
     se = w.std() / w.mean() / np.sqrt(len(w) / 10)                    # blocks of correlated sweeps
     assert abs(est - logZ) < 4 * se + 1e-3
     assert lv.mean() < logZ + 4 * lv.std() / np.sqrt(len(lv) / 10)
+
+
+@pytest.mark.parametrize("name", list(MODELS))
+def test_mutual_information_is_expected_kl(name):
+    """Lemma 5: I(x; theta) = E_theta KL(p(x | theta), p(x)) >= min over theta of
+    the same KL (by enumeration; p(x | theta) is of the form p(x | xi))."""
+    model = MODELS[name]()
+    dec = dc.decompose(model)
+    _, _, mi = logz.exact_moments(model, dec)
+    X = brute.all_labelings(model.n_vars, model.n_labels)
+    Th = brute.all_dual_configs(brute.active_entries(dec).shape[0])
+    J = brute.joint_log(dec, X, Th)
+    lpj = J - np.logaddexp.reduce(J, axis=None)
+    lpt = np.logaddexp.reduce(lpj, axis=0)                          # log p(theta)
+    lpx = np.logaddexp.reduce(lpj, axis=1)                          # log p(x)
+    lp_x_t = lpj - lpt[None, :]                                     # log p(x | theta)
+    kl = (np.exp(lp_x_t) * (lp_x_t - lpx[:, None])).sum(axis=0)     # KL(p(x|theta), p(x)) per theta
+    assert abs((np.exp(lpt) * kl).sum() - mi) < 1e-10
+    assert mi >= kl.min() - 1e-12
