@@ -52,6 +52,8 @@ PH_FFBS = 5
 PH_SPLASH = 6
 PH_PROPOSAL = 7
 PH_ACCEPT = 8
+PH_BOND = 9       # Swendsen-Wang bond of (edge, chain) (word 0, 23-bit uniform)
+PH_CLUSTER = 10   # Swendsen-Wang cluster label, index = the cluster's smallest site (word 0)
 
 _MASK32 = np.uint64(0xFFFFFFFF)
 

@@ -1,0 +1,102 @@
+"""Pins of the Swendsen-Wang duality (Section 4.3) by enumeration."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import brute, decompose as dc, philox as ph, swendsen_wang as sw
+from oracle.sampler import log_softmax
+from paper_1611_06684_gb300 import workloads as wl
+
+
+def _model(seed, N=5, L=3, E=6):
+    """Generalised ferromagnetic Potts tables w_e(a, b) = beta_{e,a} [a = b] with a
+    different beta per label, so that a label-independent slip in the bond weight
+    log(e^l - 1) would not cancel out of the cluster label distribution."""
+    m = wl.tiny_potts(N, L, E, seed=seed, beta_max=1.0)
+    rng = np.random.default_rng(100 + seed)
+    beta = rng.uniform(0.05, 1.5, (m.src.size, L)).astype(np.float32)
+    pair = np.zeros((m.src.size, L, L), np.float32)
+    pair[:, np.arange(L), np.arange(L)] = beta
+    m = wl.Model(m.n_vars, L, m.unary, m.src, m.dst, pair, name="tinypotts_gen")
+    return m, dc.decompose(m)
+
+
+def _joint_log(model, dec, X, B):
+    """log p~(x, theta) [S_x][S_theta] = sum u + sum over bonded edges of log(e^{l} - 1) (or -inf)."""
+    u = np.asarray(model.unary, np.float64)
+    lu = u[np.arange(model.n_vars)[None, :], X].sum(axis=1)
+    xs, xt = X[:, dec.src], X[:, dec.dst]
+    ell = np.where(dec.active, dec.ell, 0.0)
+    l_at = ell[np.arange(dec.src.size)[None, :], xs]
+    with np.errstate(divide="ignore"):
+        lb = np.where(xs == xt, np.log(np.expm1(l_at)), -np.inf)          # [S_x][E]
+    out = lu[:, None] + (B[None, :, :] * np.where(np.isfinite(lb), lb, -1e300)[:, None, :]).sum(axis=2)
+    ok = ~((B[None, :, :] == 1) & ~np.isfinite(lb)[:, None, :]).any(axis=2)
+    return np.where(ok, out, -np.inf)
+
+
+def test_decomposition_reproduces_the_factor():
+    """sum_theta g(theta) exp(-theta I(a = b)) = exp(w(a, b)) with g(0) = 1,
+    g(1) = e^l - 1 (the paper's g(0) = e^{-w}, g(1) = 1 - e^{-w} after scaling by e^{-l})."""
+    for l in (0.1, 0.7, 2.5):
+        for a, b in itertools.product(range(3), repeat=2):
+            I0 = 0.0 if a == b else np.inf
+            val = 1.0 + (np.expm1(l) * np.exp(-I0))
+            assert abs(val - np.exp(l * (a == b))) < 1e-12
+            # paper's normalisation
+            assert abs(np.exp(-l) + (1 - np.exp(-l)) * np.exp(-I0) - np.exp(l * (a == b) - l)) < 1e-12
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_joint_marginalises_and_cluster_rule_is_the_conditional(seed):
+    model, dec = _model(seed)
+    X = brute.all_labelings(model.n_vars, model.n_labels)
+    B = brute.all_dual_configs(dec.src.size)
+    J = _joint_log(model, dec, X, B)
+    np.testing.assert_allclose(np.logaddexp.reduce(J, axis=1), brute.log_ptilde(model, X), atol=1e-10)
+    rng = np.random.default_rng(seed)
+    for bi in rng.choice(B.shape[0], size=6, replace=False):
+        col = J[:, bi]
+        if not np.isfinite(col).any():
+            continue
+        p_exact = np.exp(col - np.logaddexp.reduce(col))
+        root = sw.clusters(model.n_vars, dec.src, dec.dst, B[bi].astype(bool))
+        lw = sw.cluster_log_weights(model, dec, root, B[bi].astype(bool))
+        rs = np.unique(root)
+        lp = log_softmax(lw[rs])
+        pos = {r: i for i, r in enumerate(rs)}
+        p_rule = np.zeros(X.shape[0])
+        for xi, x in enumerate(X):
+            if all(x[v] == x[root[v]] for v in range(model.n_vars)):
+                p_rule[xi] = np.exp(sum(lp[pos[r], x[r]] for r in rs))
+        np.testing.assert_allclose(p_rule, p_exact, atol=1e-12)
+
+
+def test_sw_kernel_is_stationary():
+    model, dec = _model(3, N=4, L=3, E=5)
+    X = brute.all_labelings(model.n_vars, model.n_labels)
+    B = brute.all_dual_configs(dec.src.size)
+    J = _joint_log(model, dec, X, B)
+    lp_b_x = J - np.logaddexp.reduce(J, axis=1)[:, None]                # p(theta | x)
+    lp_x_b = J - np.logaddexp.reduce(J, axis=0)[None, :]                # p(x | theta)
+    with np.errstate(invalid="ignore"):
+        K = np.nan_to_num(np.exp(lp_b_x)) @ np.nan_to_num(np.exp(lp_x_b)).T
+    _, p, _ = brute.exact_distribution(model)
+    np.testing.assert_allclose(K.sum(axis=1), 1.0, atol=1e-12)
+    np.testing.assert_allclose(p @ K, p, atol=1e-12)
+
+
+def test_sw_chain_marginals_within_3_sigma():
+    model, dec = _model(4, N=6, L=3, E=8)
+    exact, _ = brute.exact_marginals(model)
+    C, T, burn, seed = 512, 60, 10, 5
+    x = ph.init_labels(model.n_vars, 3, C, seed)
+    acc = np.zeros((C, model.n_vars, 3))
+    for t in range(T):
+        x = sw.sw_sweep(model, dec, x, t, seed)["x"]
+        if t >= burn:
+            acc[np.arange(C)[:, None], np.arange(model.n_vars)[None, :], x] += 1
+    cm = acc / (T - burn)
+    z = np.abs(cm.mean(0) - exact) / np.maximum(cm.std(0, ddof=1) / np.sqrt(C), 1e-12)
+    assert z.max() < 4.5 and np.mean(z < 3.0) > 0.9, z
