@@ -33,6 +33,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "site-updates/s"
+FERRO_BETA = (0.0, 1.0)
+FERRO_U_STD = 0.5
 
 WORKLOADS = {
     # name: (generator, chains, description)
@@ -42,6 +44,11 @@ WORKLOADS = {
                 1, "2-D Ising grid 32x32, L=2, h~N(0,0.5^2), J~U[0,0.3], 1 chain"),
     "dense4096": (lambda: __import__("paper_1611_06684_gb300.workloads", fromlist=["x"]).dense_potts(4096, L=4, seed=0),
                   16, "fully connected N=4096 (8,386,560 edges), L=4, w~N(0,(0.2/64)^2), unaries N(0,1), 16 chains"),
+    # ferromagnetic Potts lattice: the Swendsen-Wang sweep (Section 4.3) applies
+    "ferro3d": (lambda: __import__("paper_1611_06684_gb300.workloads", fromlist=["x"]).ferro_potts_grid3d(
+                    128, L=8, beta_lo=FERRO_BETA[0], beta_hi=FERRO_BETA[1], u_std=FERRO_U_STD, seed=0),
+                64, "3-D 6-neighbour ferromagnetic Potts grid 128^3, L=8, w_e(a,b) = beta_e [a=b], "
+                    "beta_e~U[%g,%g], unaries N(0,%g^2), 64 chains"),
 }
 
 
@@ -110,6 +117,11 @@ def load_peaks():
 PHILOX_FMAHEAVY_CYCLES_PER_WARP_CALL = 61.5
 
 
+def _describe(workload):
+    desc = WORKLOADS[workload][2]
+    return desc % (FERRO_BETA[0], FERRO_BETA[1], FERRO_U_STD) if "%g" in desc else desc
+
+
 def alu_peak_philox_calls(sm_mhz):
     """Philox4x32-10 calls/s roof of the fmaheavy pipe: 152 SMs x 4
     sub-partitions x 32 lanes x clock / 61.5 pipe cycles per warp-wide call."""
@@ -129,6 +141,18 @@ def kernel_work(name, model_info, C):
         return 2 * calls_dual + N * C, 2 * E * m * 4 + N * L * 8 + 2 * E * 8 + 2 * N * C
     if name == "k_accumulate":
         return 0, N * C + 2 * N * L * 4
+    # Swendsen-Wang: one pass over each per-(site, chain) array the kernel
+    # touches (parent 4 B, banned labels 4 B, fixed-point weight row 8 L B,
+    # labels 1 B) and the per-edge tables; union-find walks and atomics to
+    # other rows depend on the clusters and are not counted
+    if name == "k_sw_init":
+        return 0, N * C * (8 + 8 * L) + N * L * 4
+    if name == "k_sw_bond":
+        return 0, E * 8 + E * L * 12 + 2 * E * C
+    if name == "k_sw_flatten":
+        return 0, N * C * (8 + 8 * L)
+    if name == "k_sw_draw":
+        return 0, N * C * (4 + 8 * L + 1) + N * C * (4 + 1)
     return 0, 0
 
 
@@ -139,7 +163,7 @@ def kernel_work(name, model_info, C):
 DUAL_DRAM_BYTES_PER_ITEM = {(49, 64): 1146.5e6 / (774144 * 64)}
 
 # kernels behind one kernel-timing record of the library
-KERNELS_PER_RECORD = {"k_dual": 2}
+KERNELS_PER_RECORD = {"k_dual": 2, "k_sw_draw": 2}
 
 
 def rank_seed(seed: int, rank: int) -> int:
@@ -181,7 +205,9 @@ def run_ours(args, ws, rank, local):
         desc = desc.replace("128^3", f"{args.scale}^3")
     else:
         model = gen()
-    mode = {"plain": M.MODE_PLAIN, "fused": M.MODE_FUSED}[args.mode]
+    if "%g" in desc:
+        desc = _describe(args.workload)
+    mode = {"plain": M.MODE_PLAIN, "fused": M.MODE_FUSED, "sw": M.MODE_SW}[args.mode]
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         h = M.MRF(model.n_vars, model.n_labels, C, seed=rank_seed(args.seed, rank), stream=stream.cuda_stream,
@@ -252,7 +278,10 @@ def run_ours(args, ws, rank, local):
     # other sweep forms on the same handle, timed separately (not part of the headline)
     variants = {}
     if not args.no_variants:
-        forms = [("fused", M.MODE_FUSED)] + ([("splash", M.MODE_SPLASH)] if model.grid else [])
+        potts = inf.layout == M.LAYOUT_DIAG and bool((model.pair >= 0).all())
+        forms = [(n, md) for n, md in (("plain", M.MODE_PLAIN), ("fused", M.MODE_FUSED)) if n != args.mode] + \
+            ([("splash", M.MODE_SPLASH)] if model.grid else []) + \
+            ([("sw", M.MODE_SW)] if potts and args.mode != "sw" else [])
         for name, md in forms:
             h.sweep(1, md)
             h.kernel_times()
@@ -280,10 +309,11 @@ def run_ours(args, ws, rank, local):
                 "lower_bound_per_site": float(lv.mean() / model.n_vars),
                 "note": "mean of log V is a lower bound on log Z (Section 5.2); chains after the timed sweeps"}
         if args.ess_sweeps > 0:
-            ms_of = {"plain": ms_step if args.mode == "plain" else None}
+            ms_of = {args.mode: ms_step}
             ms_of.update({k: v["ms_per_step"] for k, v in variants.items() if "ms_per_step" in v})
             variants["ess"] = ess_comparison(h, model, C, stream, args.ess_sweeps, ms_of,
-                                             [("plain", M.MODE_PLAIN)] + ([("splash", M.MODE_SPLASH)] if model.grid else []))
+                                             [("plain", M.MODE_PLAIN)] + ([("splash", M.MODE_SPLASH)] if model.grid else [])
+                                             + ([("sw", M.MODE_SW)] if potts else []))
 
     # end to end through the C ABI with pinned host buffers: labels in, sweep, labels out
     e2e = None
@@ -349,6 +379,11 @@ class OracleSample:
             self.C = 2
             model = wl.potts_grid3d(24, L=8, seed=0)
             self.sample = "{C} chains x {S} sweeps of a 24^3 sub-lattice with the same L=8 table and unary distributions"
+        elif args.workload == "ferro3d":
+            self.C = 2
+            model = wl.ferro_potts_grid3d(24, L=8, beta_lo=FERRO_BETA[0], beta_hi=FERRO_BETA[1], u_std=FERRO_U_STD,
+                                          seed=0)
+            self.sample = "{C} chains x {S} sweeps of a 24^3 sub-lattice with the same L=8 coupling and unary distributions"
         elif args.workload == "dense4096":
             self.C = 1
             model = wl.dense_potts(256, L=4, w_std=0.2 / 64, seed=0)
@@ -359,15 +394,22 @@ class OracleSample:
             self.sample = "{C} chain x {S} sweeps of the full workload"
         self.model = model
         self.dec = dc.decompose(model)
+        self.mode = args.mode
+        self.sw_tables = None
         self.seed = args.seed
         self.x = ph.init_labels(model.n_vars, model.n_labels, self.C, args.seed)
         self.t = 0
 
     def sweep(self):
         """One oracle sweep; returns its wall time in seconds."""
-        from oracle import sampler
+        from oracle import sampler, swendsen_wang
         t0 = time.perf_counter()
-        self.x = sampler.sweep(self.dec, self.x, self.t, self.seed)["x"]
+        if self.mode == "sw":
+            if self.sw_tables is None:
+                self.sw_tables = swendsen_wang.sw_tables(self.model)
+            self.x = swendsen_wang.sw_sweep(self.model, self.x, self.t, self.seed, tables=self.sw_tables)["x"]
+        else:
+            self.x = sampler.sweep(self.dec, self.x, self.t, self.seed)["x"]
         self.t += 1
         return time.perf_counter() - t0
 
@@ -400,7 +442,7 @@ def run_reference(args, ws, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_s * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded generators)",
-            "config": {"workload": args.workload, "description": WORKLOADS[args.workload][2],
+            "config": {"workload": args.workload, "description": _describe(args.workload), "mode": args.mode,
                        "reference": "CPU float64 oracle (oracle/), one bounded-sample sweep per step"},
             "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value, "unit": METRIC},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -681,7 +723,7 @@ def main():
     ap.add_argument("--workload", default="potts3d", choices=list(WORKLOADS) + ["er_batch", "ba_learned"])
     ap.add_argument("--ref-sweeps", type=int, default=2000)
     ap.add_argument("--ess-sweeps", type=int, default=200)
-    ap.add_argument("--mode", default="plain", choices=["plain", "fused"])
+    ap.add_argument("--mode", default="plain", choices=["plain", "fused", "sw"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--scale", type=int, default=0, help="lattice edge for potts3d (default 128)")
     ap.add_argument("--no-e2e", action="store_true")

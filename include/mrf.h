@@ -61,9 +61,11 @@ enum {
                             from the counter-based RNG (never stored)        */
     MRF_MODE_SPLASH = 2, /* Section 5.4 blocked sweep on a lattice (needs
                             mrf_options.grid); 4x4x4 blocks, comb trees      */
-    MRF_MODE_LEARNED = 3 /* cut-edge duals, then one Metropolis-Hastings step
+    MRF_MODE_LEARNED = 3,/* cut-edge duals, then one Metropolis-Hastings step
                             per block with the learned proposal (needs
                             mrf_learned_setup)                               */
+    MRF_MODE_SW = 4      /* Section 4.3: Swendsen-Wang as a degenerate
+                            duality (two labels or Potts-type tables, l >= 0)  */
 };
 
 /* Dualised table layout chosen by mrf_set_factors (mrf_info.layout). */
@@ -135,7 +137,29 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
  * sweeps with index >= burn-in.  Asynchronous on the handle's stream.  Plain
  * sweeps of a small model (at most 2^16 site x chain and edge x chain items)
  * with n_sweeps >= 2 run in one single-CTA launch (the same chain, bit for
- * bit, as one sweep at a time). */
+ * bit, as one sweep at a time).
+ *
+ * MRF_MODE_SW (Section 4.3): every table is read as c + f(x_s) + g(x_t) +
+ * l_{x_s} [x_s = x_t] with f, g folded into the unaries -- Potts-type tables
+ * (diagonal layout): l_x = w(x,x), f = g = 0; two labels, any table:
+ * l = (w00 + w11 - w01 - w10) / 2, f(1) = w10 - w00 + l, g(1) = w01 - w00 + l --
+ * and needs every l >= 0.  Every edge whose endpoints agree on label x is
+ * bonded with probability
+ * 1 - e^{-l_x} (draw: 23-bit uniform of Philox(edge slot, t, chain, BOND)
+ * compared with the exact threshold); every connected component of the
+ * bonds (cluster) takes one label, label x with weight
+ * exp(sum_{v in cluster} u_v(x) + sum_{bonds in cluster} log(e^{l_x} - 1))
+ * (u with the offsets folded in)
+ * (a bond with l_x = 0 excludes x), drawn by the inverse CDF with the 23-bit
+ * uniform of Philox(smallest site of the cluster, t, chain, CLUSTER).
+ * A model without live edges is accepted with any layout.  Cluster weights
+ * are summed exactly in 64-bit fixed point (2^-32), so runs
+ * are reproducible.  Errors: MRF_EINVAL when L >= 3 and the tables are not
+ * diagonal, or some l < 0; MRF_ERANGE when sum_v max_x |u_v(x)| + sum_e max_x
+ * |log(e^{l_x} - 1)| reaches 2^30; MRF_ETIMEOUT if a union-find walk
+ * exceeded its bound of n_vars steps (cannot happen for a consistent forest).
+ * The call synchronises the stream at its end to read that flag.
+ * mrf_debug_logp and the log-partition estimator do not cover this mode. */
 mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode);
 
 /* Estimated marginals out[n_vars][L] = counts / n_samples (float32) and the
@@ -172,7 +196,9 @@ mrf_status mrf_debug_theta(mrf_t* h, uint32_t* out);
 enum { MRF_K_DUAL = 0, MRF_K_PRIMAL = 1, MRF_K_FUSED = 2, MRF_K_POTENTIAL = 3, MRF_K_FFBS = 4,
        MRF_K_ACCUMULATE = 5, MRF_K_FEATURES = 6, MRF_K_MLP = 7, MRF_K_MH = 8,
        MRF_K_SMALL = 9,    /* whole plain sweeps of a small model in one launch (see mrf_sweep) */
-       MRF_K_COUNT = 10 };
+       MRF_K_SW_INIT = 10, MRF_K_SW_BOND = 11, MRF_K_SW_FLATTEN = 12,
+       MRF_K_SW_DRAW = 13, /* Swendsen-Wang: label draw of every cluster and the copy to its sites */
+       MRF_K_COUNT = 14 };
 /* With options.kernel_timing: total device milliseconds ms[MRF_K_COUNT] and
  * launch counts launches[MRF_K_COUNT] of every sweep kernel since the last
  * call (CUDA events on the handle's stream); resets the totals.  Synchronises. */

@@ -3,26 +3,33 @@
 Test infrastructure: only the tests, the smoke check and the benchmark's CPU
 legs use this package.
 
-For a ferromagnetic Potts factor P(a, b) = exp(l_a [a = b]) with l_a >= 0
-(the diagonal layout of oracle.decompose, every active entry positive),
-    P(a, b) = sum_{theta in {0,1}} g(theta) exp(-theta I(a = b)),
+Every table is first written as w_e(a, b) = c_e + f_e(a) + g_e(b) + l_{e,a} [a = b]
+(sw_tables), with f and g folded into the unaries and c_e dropped:
+  * L >= 3, diagonal tables (w(a, b) = 0 for a != b): l_{e,a} = w(a, a), f = g = 0;
+  * L = 2, any table: one coupling l = (w00 + w11 - w01 - w10) / 2 for both
+    labels, f(1) = w10 - w00 + l, g(1) = w01 - w00 + l, f(0) = g(0) = 0
+    (the paper's Ising factor [[1, e^{-w}], [e^{-w}, 1]] is the case f = g = 0).
+For a ferromagnetic factor (every l >= 0) the remaining table exp(l_a [a = b]) is
+    sum_{theta in {0,1}} g(theta) exp(-theta I(a = b)),
     g(0) = 1, g(1) = e^{l_a} - 1 on the diagonal (the paper's form up to the
     factor e^{l}: g(0) = e^{-l}, g(1) = 1 - e^{-l}),
 with I(a = b) = 0 if a = b and infinity otherwise.  Hence
     p(theta_e = 1 | x) = 1 - e^{-l_{x_s}} if x_s = x_t, else 0     (a bond),
     p(x | theta): the bonds' connected components ("clusters") take one
     label each, cluster K with probability proportional to
-    exp(sum_{v in K} u_v(a) + sum_{bonded e in K} log(e^{l_{e,a}} - 1)).
-One sweep draws the bonds given x, then the cluster labels.
+    exp(sum_{v in K} u_v(a) + sum_{bonded e in K} log(e^{l_{e,a}} - 1))
+(u the unaries with the offsets folded in; a bonded edge with l_{e,a} = 0
+excludes a).  One sweep draws the bonds given x, then the cluster labels.
 
 Draws: bond of edge e, chain c, sweep t: u from word 0 of Philox(e, t, c,
 BOND) (23-bit form), bond = [u < p]; label of cluster K: inverse CDF with u
 from word 0 of Philox(r, t, c, CLUSTER), r = the smallest site of K.
 
 Pins (tests/test_oracle_sw.py): the decomposition reproduces every factor;
-p~(x, theta) marginalises to p~(x); the cluster label distribution equals
-p(x | theta) by enumeration; the SW kernel leaves p invariant (enumeration);
-chain marginals within 3 sigma of exact.
+p~(x, theta) marginalises to p~(x) (enumeration, diagonal Potts and two-label
+tables); the cluster label distribution equals p(x | theta) by enumeration;
+the SW kernel leaves p invariant (enumeration); chain marginals within 3 sigma
+of exact.
 """
 from __future__ import annotations
 
@@ -31,31 +38,38 @@ from scipy.sparse import coo_matrix
 from scipy.sparse.csgraph import connected_components
 
 from . import philox as ph
-from .decompose import Decomposition, LAYOUT_DIAG
 from .sampler import log_softmax, inverse_cdf
 
 
-def check_model(dec: Decomposition):
-    """SW needs the diagonal layout with every active entry l > 0."""
-    if dec.layout != LAYOUT_DIAG:
-        raise ValueError("Swendsen-Wang needs Potts tables (diagonal layout)")
-    if np.any(dec.ell[dec.active] <= 0):
+def sw_tables(model):
+    """(l [E][L], u [N][L]) of the Swendsen-Wang form of the model (float64).
+    Raises ValueError for tables outside the form or with some l < 0."""
+    L, N = model.n_labels, model.n_vars
+    w = np.asarray(model.pair, np.float64)
+    u = np.asarray(model.unary, np.float64).copy()
+    E = w.shape[0]
+    if E == 0:
+        return np.zeros((0, L)), u
+    if L == 2:
+        kappa = 0.5 * (w[:, 0, 0] + w[:, 1, 1] - w[:, 0, 1] - w[:, 1, 0])
+        ell = np.repeat(kappa[:, None], 2, axis=1)
+        np.add.at(u[:, 1], np.asarray(model.src, np.int64), w[:, 1, 0] - w[:, 0, 0] + kappa)
+        np.add.at(u[:, 1], np.asarray(model.dst, np.int64), w[:, 0, 1] - w[:, 0, 0] + kappa)
+    else:
+        if np.any(w[:, ~np.eye(L, dtype=bool)] != 0):
+            raise ValueError("Swendsen-Wang needs diagonal (Potts-type) tables when L >= 3")
+        ell = np.diagonal(w, axis1=1, axis2=2).copy()
+    if np.any(ell < 0):
         raise ValueError("Swendsen-Wang needs ferromagnetic tables (l >= 0)")
+    return ell, u
 
 
-def bond_probs(dec: Decomposition, x):
+def bond_probs(ell, src, dst, x):
     """p(theta_e = 1 | x) [C][E]."""
     x = np.asarray(x, np.int64)
-    xs, xt = x[:, dec.src], x[:, dec.dst]
-    ell = np.where(dec.active, dec.ell, 0.0)                              # [E][L]
+    xs, xt = x[:, src], x[:, dst]
     l_at = np.take_along_axis(np.broadcast_to(ell, (x.shape[0],) + ell.shape), xs[:, :, None], axis=2)[:, :, 0]
     return np.where(xs == xt, -np.expm1(-l_at), 0.0)
-
-
-def bond_uniforms(dec: Decomposition, n_chains, sweep, seed, edge_ids=None):
-    E = dec.src.shape[0]
-    e = np.arange(E, dtype=np.int64) if edge_ids is None else np.asarray(edge_ids, np.int64)
-    return ph.site_uniform(e[None, :], np.arange(n_chains)[:, None], sweep, seed, ph.PH_BOND)
 
 
 def clusters(n_vars, src, dst, bonds_c):
@@ -68,38 +82,42 @@ def clusters(n_vars, src, dst, bonds_c):
     return smallest[comp]
 
 
-def cluster_log_weights(model, dec: Decomposition, root, bonds_c):
+def cluster_log_weights(u, ell, src, root, bonds_c):
     """log weight [N][L] of each cluster's label, indexed by its root (other rows 0)."""
-    N, L = model.n_vars, model.n_labels
-    lw = np.zeros((N, L))
-    np.add.at(lw, root, np.asarray(model.unary, np.float64))
-    ell = np.where(dec.active, dec.ell, 0.0)
+    lw = np.zeros(u.shape)
+    np.add.at(lw, root, u)
     with np.errstate(divide="ignore"):
         lb = np.log(np.expm1(ell))                                         # log(e^l - 1); -inf where l = 0
     sel = np.nonzero(bonds_c)[0]
-    np.add.at(lw, root[dec.src[sel]], lb[sel])
+    if sel.size:
+        np.add.at(lw, root[src[sel]], lb[sel])
     return lw
 
 
-def sw_sweep(model, dec: Decomposition, x, sweep_index: int, seed: int):
-    """One Swendsen-Wang sweep from labels x [C][N]."""
-    check_model(dec)
+def sw_sweep(model, x, sweep_index: int, seed: int, edge_ids=None, chain_ids=None, tables=None):
+    """One Swendsen-Wang sweep from labels x [C][N].  edge_ids are the RNG
+    indices of the edges (default 0..E-1), chain_ids those of the rows of x
+    (default 0..C-1); tables = sw_tables(model) if already computed."""
+    ell, u = sw_tables(model) if tables is None else tables
+    src, dst = np.asarray(model.src, np.int64), np.asarray(model.dst, np.int64)
     x = np.asarray(x, np.int64)
     C, N = x.shape
-    p = bond_probs(dec, x)
-    u = bond_uniforms(dec, C, sweep_index, seed)
-    bonds = u < p
+    ch = np.arange(C, dtype=np.int64) if chain_ids is None else np.asarray(chain_ids, np.int64)
+    p = bond_probs(ell, src, dst, x)
+    e = np.arange(src.shape[0], dtype=np.int64) if edge_ids is None else np.asarray(edge_ids, np.int64)
+    ub = ph.site_uniform(e[None, :], ch[:, None], sweep_index, seed, ph.PH_BOND)
+    bonds = ub < p
     x_new = np.zeros_like(x)
     roots = np.zeros_like(x)
     u_cl = np.zeros((C, N)); cdf_cl = np.zeros((C, N, model.n_labels))
     for c in range(C):
-        root = clusters(N, dec.src, dec.dst, bonds[c])
-        lw = cluster_log_weights(model, dec, root, bonds[c])
+        root = clusters(N, src, dst, bonds[c])
+        lw = cluster_log_weights(u, ell, src, root, bonds[c])
         rs = np.unique(root)
-        uc = ph.site_uniform(rs, c, sweep_index, seed, ph.PH_CLUSTER)
+        uc = ph.site_uniform(rs, ch[c], sweep_index, seed, ph.PH_CLUSTER)
         lab, cdf = inverse_cdf(log_softmax(lw[rs]), uc)
         lab_of = np.zeros(N, np.int64); lab_of[rs] = lab
         x_new[c] = lab_of[root]
         roots[c] = root
         u_cl[c, rs] = uc; cdf_cl[c, rs] = cdf
-    return dict(x=x_new, bonds=bonds, p_bond=p, u_bond=u, roots=roots, u_cluster=u_cl, cdf_cluster=cdf_cl)
+    return dict(x=x_new, bonds=bonds, p_bond=p, u_bond=ub, roots=roots, u_cluster=u_cl, cdf_cluster=cdf_cl)

@@ -14,6 +14,19 @@ namespace mrfk {
 
 constexpr int kMaxLabels = 16;
 
+// Swendsen-Wang cluster log weights are summed in 64-bit fixed point with 32
+// fraction bits, so that the sum is exact and independent of the order of the
+// atomic adds (every run draws the same clusters' labels).  Terms are clamped
+// to +-kSwFixMax; the sweep refuses a model whose summed term magnitudes could
+// reach it, which keeps every partial sum far inside the int64 range.
+constexpr double kSwFixScale = 4294967296.0;               // 2^32
+constexpr double kSwFixMax = 1073741824.0;                 // 2^30
+constexpr int64_t kSwNoLabel = (int64_t)(-0x7fffffffffffffffLL - 1);   // bonded: label excluded
+__host__ __device__ inline int64_t sw_fix(double x) {
+    x = x > kSwFixMax ? kSwFixMax : (x < -kSwFixMax ? -kSwFixMax : x);
+    return (int64_t)llrint(x * kSwFixScale);
+}
+
 // Control block in device memory, read by every sweep kernel so that a
 // captured CUDA graph of one sweep can be replayed: the sweep index decides
 // the RNG counter and which half of the label double buffer is current.
@@ -118,6 +131,26 @@ inline int32_t tie_cap_for(int M) { return ((32 * M * 3 / 512 + 1 + 16) + 7) / 8
 // k_dual warps (blocks of 256 threads) for E * C items.
 inline int64_t dual_warps(int64_t items) { return (items + 255) / 256 * 8; }
 
+// Swendsen-Wang sweep (sw.cu): bonds, union-find and cluster labels.
+struct SwArgs {
+    int32_t N, C, L;
+    int64_t E;                 // edge slots
+    const int32_t* src;        // [E] (-1 = free slot)
+    const int32_t* dst;        // [E]
+    const uint32_t* thr;       // [E][L] 23-bit bond thresholds
+    const int64_t* lwe;        // [E][L] fixed-point bond log weights (kSwNoLabel: label excluded)
+    const float* unary;        // [N][L] raw unaries (diagonal tables)
+    const double* unary_d;     // [N][L] unaries with the two-label offsets folded in, or null
+    uint8_t* x;                // [2][N][C] label double buffer
+    int32_t* parent;           // [N][C] union-find forest, links to smaller sites only
+    uint32_t* ban;             // [N][C] labels a cluster may not take (bit per label)
+    int64_t* lw;               // [N][L][C] fixed-point cluster label log weights (valid at roots)
+    unsigned* err;             // set when a union-find walk exceeded its step bound
+    Ctl* ctl;
+    RoundKeys rk;
+    FastDiv fdC;
+};
+
 // Learned block proposal (learned.cu).
 constexpr int kLearnBlock = 16;                                   // sites per block (max)
 constexpr int kLearnPairs = kLearnBlock * (kLearnBlock - 1) / 2;  // pair-coupling features
@@ -197,6 +230,13 @@ cudaError_t launch_to_bf16(const float* src, __nv_bfloat16* dst, int64_t n, cuda
 cudaError_t noalloc_scratch(uint32_t** out);
 cudaError_t launch_sweep_noalloc(const SweepArgs& a, int layout, const uint8_t* xin, uint8_t* xout, uint32_t sweep,
                                  cudaStream_t s);
+// Swendsen-Wang (sw.cu)
+cudaError_t launch_sw_check(const int32_t* src, const float* tau, int64_t E, int M, const int64_t* lwe, int L,
+                            const float* unary, const double* unary_d, int N, double* out, cudaStream_t s);
+cudaError_t launch_sw_init(const SwArgs& a, cudaStream_t s);
+cudaError_t launch_sw_bond(const SwArgs& a, cudaStream_t s);
+cudaError_t launch_sw_flatten(const SwArgs& a, cudaStream_t s);
+cudaError_t launch_sw_draw(const SwArgs& a, cudaStream_t s);
 cudaError_t launch_labels_to_abi(const uint8_t* x, uint8_t* y, int N, int C, cudaStream_t s);
 cudaError_t launch_labels_from_abi(const uint8_t* y, uint8_t* x, int N, int C, cudaStream_t s);
 cudaError_t launch_count_ge(const uint8_t* y, int64_t n, int L, unsigned long long* bad, cudaStream_t s);
@@ -212,6 +252,9 @@ struct DecompArgs {
     double* fold;              // [E][2][L]
     double* cst;               // [E] per-edge log constant
     float* resid;              // [E][L][L] or null
+    uint32_t* sw_thr;          // [E][L] Swendsen-Wang bond thresholds (diagonal layout) or null
+    int64_t* sw_lw;            // [E][L] Swendsen-Wang bond log weights, fixed point, or null
+    double* sw_fold;           // [E][2][L] Swendsen-Wang unary offsets (two labels) or null
 };
 cudaError_t launch_check_finite(const float* p, int64_t n, unsigned long long* bad, cudaStream_t s);
 cudaError_t launch_count_offdiag(const float* pair, int64_t n_edges, int L, unsigned long long* nz, cudaStream_t s);

@@ -99,6 +99,40 @@ __global__ void k_decompose(DecompArgs a) {
         a.fold[(e * 2 + 1) * L + x] = ft[x];
     }
     a.cst[e] = cst;
+    if (a.sw_thr && (a.layout == MRF_LAYOUT_DIAG || L == 2)) {
+        // Swendsen-Wang tables (Section 4.3): the table as
+        // c + f(a) + g(b) + l_a [a = b] -- diagonal tables: l_x = w(x,x), f = g = 0;
+        // two labels: l = (w00 + w11 - w01 - w10) / 2 for both labels,
+        // f(1) = w10 - w00 + l, g(1) = w01 - w00 + l (folded into the SW unaries).
+        // Per label x: bond probability 1 - e^{-l_x} as the exact 23-bit threshold
+        // T = ceil(p 2^23 - 1/2) (a draw U bonds iff U < T, i.e. (U + 1/2) / 2^23 < p),
+        // and the bond's label weight log(e^{l_x} - 1) in fixed point (sw_fix);
+        // l <= 0: no bond (T = 0) and the label is excluded when bonded (kSwNoLabel).
+        double lx[kMaxLabels];
+        if (L == 2) {
+            const double k2 = 0.5 * ((double)w[0] + (double)w[3] - (double)w[1] - (double)w[2]);
+            lx[0] = lx[1] = k2;
+            if (a.sw_fold) {
+                a.sw_fold[(e * 2 + 0) * 2 + 0] = 0.0;
+                a.sw_fold[(e * 2 + 0) * 2 + 1] = (double)w[2] - (double)w[0] + k2;
+                a.sw_fold[(e * 2 + 1) * 2 + 0] = 0.0;
+                a.sw_fold[(e * 2 + 1) * 2 + 1] = (double)w[1] - (double)w[0] + k2;
+            }
+        } else {
+            for (int x = 0; x < L; ++x) lx[x] = (double)w[x * L + x];
+        }
+        for (int x = 0; x < L; ++x) {
+            const double l = lx[x];
+            uint32_t T = 0;
+            int64_t lw = kSwNoLabel;
+            if (l > 0.0) {
+                T = (uint32_t)ceil(-expm1(-l) * 8388608.0 - 0.5);
+                lw = sw_fix(log(expm1(l)));
+            }
+            a.sw_thr[e * L + x] = T;
+            a.sw_lw[e * L + x] = lw;
+        }
+    }
     if (a.resid) {
         // exact pairwise potential in the folded representation (tree edges of
         // the blocked sweep): w(a,b) - fold_s(a) - fold_t(b)
@@ -163,7 +197,7 @@ __global__ void k_fold_unary(const float* unary, const double* fold, const int64
     }
     for (int x = 0; x < L; ++x) {
         ut[(int64_t)v * L + x] = acc[x];
-        utf[(int64_t)v * L + x] = (float)acc[x];
+        if (utf) utf[(int64_t)v * L + x] = (float)acc[x];
     }
 }
 

@@ -55,8 +55,19 @@ struct mrf {
     int64_t sweep_host = 0, count_from_host = 0;
     double log_const = NAN;
     std::string err;
-    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaGraphExec_t graph[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     uint8_t* d_stage = nullptr;        // [C][N] staging for the ABI label view
+    // Swendsen-Wang (diagonal layout): per-edge tables and per-sweep union-find state
+    uint32_t* d_swt = nullptr;         // [E][L] 23-bit bond thresholds
+    int64_t* d_swl = nullptr;          // [E][L] fixed-point bond log weights
+    double* d_swfold = nullptr;        // [E][2][L] two-label unary offsets
+    double* d_swut = nullptr;          // [N][L] two-label unaries with the offsets folded in
+    int32_t* d_swpar = nullptr;        // [N][C] union-find parents
+    uint32_t* d_swban = nullptr;       // [N][C] excluded labels of a cluster
+    int64_t* d_swlw = nullptr;         // [N][L][C] fixed-point cluster log weights
+    unsigned* d_swerr = nullptr;       // union-find step bound exceeded
+    double* d_swchk = nullptr;         // [3] model check sums (k_sw_check)
+    bool sw_checked = false;           // the model passed the check since the factors last changed
     float* d_pot = nullptr;            // [N][L][C] node potentials of the blocked sweep
     int schedule = 0;                  // primal schedule in use (1 thread, 2 CTA); 0 = not tuned yet
     int32_t* d_csr_work = nullptr;     // [2N] degrees and cursors of the device CSR build
@@ -372,6 +383,7 @@ void mrf_destroy(mrf_t* h) {
     dfree(h->d_unary); dfree(h->d_ut); dfree(h->d_utf); dfree(h->d_tpl); dfree(h->d_src); dfree(h->d_dst); dfree(h->d_tau); dfree(h->d_thr);
     dfree(h->d_fold); dfree(h->d_cst); dfree(h->d_resid); dfree(h->d_inc_ptr); dfree(h->d_inc); dfree(h->d_x);
     dfree(h->d_theta); dfree(h->d_ties); dfree(h->d_tie_count); dfree(h->d_counts); dfree(h->d_lpv); dfree(h->d_logv); dfree(h->d_em); dfree(h->d_mfq); dfree(h->d_mfs); dfree(h->d_logp); dfree(h->d_ctl); dfree(h->d_flag); dfree(h->d_stage); dfree(h->d_pot);
+    dfree(h->d_swt); dfree(h->d_swl); dfree(h->d_swfold); dfree(h->d_swut); dfree(h->d_swpar); dfree(h->d_swban); dfree(h->d_swlw); dfree(h->d_swerr); dfree(h->d_swchk);
     dfree(h->d_csr_work); dfree(h->d_csr_sums);
     dfree(h->d_ed_pair); dfree(h->d_ed_slots); dfree(h->d_ed_new); dfree(h->d_ed_s); dfree(h->d_ed_t);
     dfree(h->d_members); dfree(h->d_nmem); dfree(h->d_intra_ptr); dfree(h->d_intra); dfree(h->d_cf); dfree(h->d_skip);
@@ -434,6 +446,17 @@ mrf_status mrf_set_factors(mrf_t* h, const float* unary_log, int64_t n_edges, co
     MRF_CUDA(h, dalloc(h->d_tpl, E * h->W * 32));
     MRF_CUDA(h, dalloc(h->d_fold, E * 2 * L)); MRF_CUDA(h, dalloc(h->d_cst, E));
     if (want_resid) MRF_CUDA(h, dalloc(h->d_resid, E * L * L)); else dfree(h->d_resid);
+    if (h->layout == MRF_LAYOUT_DIAG || L == 2) {
+        MRF_CUDA(h, dalloc(h->d_swt, E * L)); MRF_CUDA(h, dalloc(h->d_swl, E * L));
+    } else {
+        dfree(h->d_swt); dfree(h->d_swl);
+    }
+    if (L == 2) {
+        MRF_CUDA(h, dalloc(h->d_swfold, E * 2 * L)); MRF_CUDA(h, dalloc(h->d_swut, (size_t)N * L));
+    } else {
+        dfree(h->d_swfold); dfree(h->d_swut);
+    }
+    h->sw_checked = false;
     MRF_CUDA(h, dalloc(h->d_theta, E * h->C * h->W));
     MRF_CUDA(h, alloc_ties(h, (int64_t)E));
     MRF_CUDA(h, to_device(h->d_src, h->h_src.data(), n_edges, MRF_PTR_HOST, h->stream));
@@ -442,9 +465,12 @@ mrf_status mrf_set_factors(mrf_t* h, const float* unary_log, int64_t n_edges, co
     DecompArgs d{};
     d.L = L; d.M = h->M; d.layout = h->layout; d.n = n_edges; d.slots = nullptr; d.first_slot = 0;
     d.pair = d_pair; d.tau = h->d_tau; d.thr = h->d_thr; d.fold = h->d_fold; d.cst = h->d_cst; d.resid = h->d_resid;
+    d.sw_thr = h->d_swt; d.sw_lw = h->d_swl; d.sw_fold = h->d_swfold;
     MRF_CUDA(h, launch_decompose(d, h->stream));
     MRF_CUDA(h, launch_build_planes(h->d_thr, n_edges, nullptr, 0, h->M, h->d_tpl, h->stream));
     MRF_CUDA(h, launch_fold_unary(h->d_unary, h->d_fold, h->d_inc_ptr, h->d_inc, N, L, h->d_ut, h->d_utf, h->stream));
+    if (h->d_swut)
+        MRF_CUDA(h, launch_fold_unary(h->d_unary, h->d_swfold, h->d_inc_ptr, h->d_inc, N, L, h->d_swut, nullptr, h->stream));
     // log constant (for log-partition estimates): sum of per-edge constants
     std::vector<double> cst((size_t)n_edges);
     if (n_edges) MRF_CUDA(h, cudaMemcpyAsync(cst.data(), h->d_cst, E * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -530,6 +556,8 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
         if ((uint64_t)cap * h->C >= (1ull << 32)) return fail(h, MRF_ERANGE, "edges x chains must be below 2^32");
         MRF_CUDA(h, grow(h->d_tau, pad4(h->M))); MRF_CUDA(h, grow(h->d_thr, h->M)); MRF_CUDA(h, grow(h->d_tpl, h->W * 32));
         MRF_CUDA(h, grow(h->d_fold, 2 * L)); MRF_CUDA(h, grow(h->d_cst, 1));
+        if (h->d_swt) { MRF_CUDA(h, grow(h->d_swt, L)); MRF_CUDA(h, grow(h->d_swl, L)); }
+        if (h->d_swfold) MRF_CUDA(h, grow(h->d_swfold, 2 * L));
         MRF_CUDA(h, dalloc(h->d_theta, (size_t)cap * h->C * h->W));
         MRF_CUDA(h, alloc_ties(h, cap));
         h->E_cap = cap;
@@ -570,6 +598,8 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
     DecompArgs d{};
     d.L = L; d.M = h->M; d.layout = h->layout; d.n = n_add; d.slots = d_new;
     d.pair = d_pair; d.tau = h->d_tau; d.thr = h->d_thr; d.fold = h->d_fold; d.cst = h->d_cst; d.resid = nullptr;
+    d.sw_thr = h->d_swt; d.sw_lw = h->d_swl; d.sw_fold = h->d_swfold;
+    h->sw_checked = false;
     MRF_CUDA(h, launch_decompose(d, h->stream));
     MRF_CUDA(h, launch_build_planes(h->d_thr, n_add, d_new, 0, h->M, h->d_tpl, h->stream));
     // incidence lists rebuilt on the device (host build if a site is very long)
@@ -589,6 +619,8 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));
     if (too_long) { MRF_CUDA(h, build_csr(h)); h->n_host_csr++; } else h->n_device_csr++;
     MRF_CUDA(h, launch_fold_unary(h->d_unary, h->d_fold, h->d_inc_ptr, h->d_inc, N, L, h->d_ut, h->d_utf, h->stream));
+    if (h->d_swut)
+        MRF_CUDA(h, launch_fold_unary(h->d_unary, h->d_swfold, h->d_inc_ptr, h->d_inc, N, L, h->d_swut, nullptr, h->stream));
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));
     std::copy(slots.begin(), slots.end(), out_new_ids);
     return MRF_OK;
@@ -639,6 +671,46 @@ static bool small_model(const mrf_t* h) {
     return nv <= 65536 && ne <= 65536 && ne * h->W * 4 <= 200 * 1024;
 }
 
+static SwArgs make_sw_args(const mrf_t* h) {
+    SwArgs w{};
+    w.N = h->N; w.C = h->C; w.L = h->L; w.E = h->E_slots;
+    w.src = h->d_src; w.dst = h->d_dst; w.thr = h->d_swt; w.lwe = h->d_swl; w.unary = h->d_unary; w.unary_d = h->d_swut;
+    w.x = h->d_x; w.parent = h->d_swpar; w.ban = h->d_swban; w.lw = h->d_swlw; w.err = h->d_swerr;
+    w.ctl = h->d_ctl; w.rk = round_keys(h->key); w.fdC = FastDiv::make((uint32_t)h->C);
+    return w;
+}
+
+// Before Swendsen-Wang sweeps: the model must have Potts-type (diagonal)
+// tables with every l >= 0, and cluster weights must fit the fixed-point sum
+// (checked once per factor change); the union-find buffers are allocated on
+// first use.
+static mrf_status sw_prepare(mrf_t* h) {
+    // (a model without live edges has no tables to check: every cluster is one site)
+    if (!h->d_swt && h->E_live > 0)
+        return fail(h, MRF_EINVAL, "Swendsen-Wang sweeps need two labels or Potts-type tables (diagonal layout)");
+    if (!h->sw_checked) {
+        if (!h->d_swchk) MRF_CUDA(h, dalloc(h->d_swchk, 3));
+        MRF_CUDA(h, cudaMemsetAsync(h->d_swchk, 0, 3 * sizeof(double), h->stream));
+        MRF_CUDA(h, launch_sw_check(h->d_src, h->d_tau, h->E_slots, h->M, h->d_swl, h->L, h->d_unary, h->d_swut, h->N,
+                                    h->d_swchk, h->stream));
+        double chk[3] = {0.0, 0.0, 0.0};
+        MRF_CUDA(h, cudaMemcpyAsync(chk, h->d_swchk, sizeof(chk), cudaMemcpyDeviceToHost, h->stream));
+        MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+        if (chk[0] > 0.0) return fail(h, MRF_EINVAL, "Swendsen-Wang sweeps need ferromagnetic tables (w(x,x) >= 0)");
+        if (chk[1] + chk[2] >= kSwFixMax)
+            return fail(h, MRF_ERANGE, "Swendsen-Wang: summed |log weights| exceed the fixed-point range (2^30)");
+        h->sw_checked = true;
+    }
+    if (!h->d_swpar) {
+        drop_graphs(h);
+        const size_t NC = (size_t)h->N * h->C;
+        MRF_CUDA(h, dalloc(h->d_swpar, NC)); MRF_CUDA(h, dalloc(h->d_swban, NC));
+        MRF_CUDA(h, dalloc(h->d_swlw, NC * h->L)); MRF_CUDA(h, dalloc(h->d_swerr, 1));
+        MRF_CUDA(h, cudaMemsetAsync(h->d_swerr, 0, sizeof(unsigned), h->stream));
+    }
+    return MRF_OK;
+}
+
 static mrf_status enqueue_sweep(mrf_t* h, int mode) {
     SweepArgs a = make_args(h);
     cudaStream_t s = h->stream;
@@ -648,6 +720,12 @@ static mrf_status enqueue_sweep(mrf_t* h, int mode) {
         if (e == cudaSuccess) e = timed(h, MRF_K_PRIMAL, [&] { return launch_primal(a, h->layout, h->schedule, s); });
     } else if (mode == MRF_MODE_FUSED) {
         e = timed(h, MRF_K_FUSED, [&] { return launch_fused(a, h->layout, h->opt.schedule, s); });
+    } else if (mode == MRF_MODE_SW) {
+        const SwArgs w = make_sw_args(h);
+        e = timed(h, MRF_K_SW_INIT, [&] { return launch_sw_init(w, s); });
+        if (e == cudaSuccess) e = timed(h, MRF_K_SW_BOND, [&] { return launch_sw_bond(w, s); });
+        if (e == cudaSuccess) e = timed(h, MRF_K_SW_FLATTEN, [&] { return launch_sw_flatten(w, s); });
+        if (e == cudaSuccess) e = timed(h, MRF_K_SW_DRAW, [&] { return launch_sw_draw(w, s); });
     } else if (mode == MRF_MODE_LEARNED) {
         a.skip = h->d_skip;
         e = timed(h, MRF_K_DUAL, [&] { return launch_dual(a, h->layout, s); });
@@ -674,7 +752,11 @@ static mrf_status enqueue_sweep(mrf_t* h, int mode) {
 mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode) {
     if (!h) return MRF_EINVAL;
     if (!h->has_factors) return fail(h, MRF_ESTATE, "mrf_set_factors first");
-    if (n_sweeps < 0 || mode < MRF_MODE_PLAIN || mode > MRF_MODE_LEARNED) return fail(h, MRF_EINVAL, "bad sweep count or mode");
+    if (n_sweeps < 0 || mode < MRF_MODE_PLAIN || mode > MRF_MODE_SW) return fail(h, MRF_EINVAL, "bad sweep count or mode");
+    if (mode == MRF_MODE_SW) {
+        mrf_status st = sw_prepare(h);
+        if (st != MRF_OK) return st;
+    }
     if (mode == MRF_MODE_LEARNED && !h->learned) return fail(h, MRF_ESTATE, "learned mode needs mrf_learned_setup");
     if (mode == MRF_MODE_LEARNED && h->rowbias_dirty) {      // per-block first-layer bias of the current weights
         MRF_CUDA(h, learned_rowbias(h->la, h->stream));
@@ -717,6 +799,15 @@ mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode) {
         }
     }
     h->sweep_host += n_sweeps;
+    if (mode == MRF_MODE_SW && n_sweeps > 0) {             // a union-find walk exceeded its step bound
+        unsigned err = 0;
+        MRF_CUDA(h, cudaMemcpyAsync(&err, h->d_swerr, sizeof(err), cudaMemcpyDeviceToHost, h->stream));
+        MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+        if (err) {
+            MRF_CUDA(h, cudaMemsetAsync(h->d_swerr, 0, sizeof(unsigned), h->stream));
+            return fail(h, MRF_ETIMEOUT, "Swendsen-Wang: a union-find walk exceeded its step bound");
+        }
+    }
     if (mode == MRF_MODE_LEARNED) {
         h->proposed += (uint64_t)n_sweeps * h->la.nb * h->C;
         if (use_mlp_tc(h) && n_sweeps > 0) {                 // a bounded wait of the tensor-core MLP gave up
@@ -854,7 +945,7 @@ struct CkptHeader {
     int64_t E_live, E_slots, n_free, sweep_host, count_from_host;
     uint64_t seed;
     double log_const;
-    int32_t has_resid, reserved;
+    int32_t has_resid, has_sw;
     mrf_options opt;
     Ctl ctl;
 };
@@ -889,6 +980,7 @@ mrf_status mrf_save(mrf_t* h, const char* path) {
     hd.E_live = h->E_live; hd.E_slots = h->E_slots; hd.n_free = (int64_t)h->free_slots.size();
     hd.sweep_host = h->sweep_host; hd.count_from_host = h->count_from_host; hd.seed = h->seed; hd.log_const = h->log_const;
     hd.has_resid = h->d_resid ? 1 : 0;
+    hd.has_sw = (h->d_swt ? 1 : 0) | (h->d_swfold ? 2 : 0);
     hd.opt = h->opt;
     MRF_CUDA(h, cudaMemcpyAsync(&hd.ctl, h->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -904,6 +996,8 @@ mrf_status mrf_save(mrf_t* h, const char* path) {
          write_dev(f, h->d_tpl, E * h->W * 32, buf, h->stream) && write_dev(f, h->d_fold, E * 2 * L, buf, h->stream) &&
          write_dev(f, h->d_cst, E, buf, h->stream);
     if (hd.has_resid) ok = ok && write_dev(f, h->d_resid, E * L * L, buf, h->stream);
+    if (hd.has_sw & 1) ok = ok && write_dev(f, h->d_swt, E * L, buf, h->stream) && write_dev(f, h->d_swl, E * L, buf, h->stream);
+    if (hd.has_sw & 2) ok = ok && write_dev(f, h->d_swfold, E * 2 * L, buf, h->stream);
     ok = ok && write_dev(f, h->d_x, 2 * (size_t)h->N * h->C, buf, h->stream) && write_dev(f, h->d_counts, NL, buf, h->stream);
     ok = ok && (hd.n_free == 0 || fwrite(h->free_slots.data(), sizeof(int64_t), (size_t)hd.n_free, f) == (size_t)hd.n_free);
     ok = (fclose(f) == 0) && ok;
@@ -941,7 +1035,9 @@ mrf_status mrf_load(mrf_t** out, const char* path, void* cuda_stream) {
     if (!ok) return bail(MRF_EINVAL);
     if (dalloc(h->d_src, E) || dalloc(h->d_dst, E) || dalloc(h->d_tau, E * pad4(h->M)) || dalloc(h->d_thr, E * h->M) ||
         dalloc(h->d_tpl, E * h->W * 32) || dalloc(h->d_fold, E * 2 * L) || dalloc(h->d_cst, E) ||
-        (hd.has_resid && dalloc(h->d_resid, E * L * L)) || dalloc(h->d_theta, E * h->C * h->W) || alloc_ties(h, (int64_t)E)) {
+        (hd.has_resid && dalloc(h->d_resid, E * L * L)) || ((hd.has_sw & 1) && (dalloc(h->d_swt, E * L) || dalloc(h->d_swl, E * L))) ||
+        ((hd.has_sw & 2) && (dalloc(h->d_swfold, E * 2 * L) || dalloc(h->d_swut, NL))) ||
+        dalloc(h->d_theta, E * h->C * h->W) || alloc_ties(h, (int64_t)E)) {
         cudaGetLastError();
         return bail(MRF_ENOMEM);
     }
@@ -951,12 +1047,31 @@ mrf_status mrf_load(mrf_t** out, const char* path, void* cuda_stream) {
          read_dev(f, h->d_tpl, E * h->W * 32, buf, h->stream) && read_dev(f, h->d_fold, E * 2 * L, buf, h->stream) &&
          read_dev(f, h->d_cst, E, buf, h->stream);
     if (hd.has_resid) ok = ok && read_dev(f, h->d_resid, E * L * L, buf, h->stream);
+    if (hd.has_sw & 1) ok = ok && read_dev(f, h->d_swt, E * L, buf, h->stream) && read_dev(f, h->d_swl, E * L, buf, h->stream);
+    if (hd.has_sw & 2) ok = ok && read_dev(f, h->d_swfold, E * 2 * L, buf, h->stream);
     ok = ok && read_dev(f, h->d_x, 2 * (size_t)h->N * h->C, buf, h->stream) && read_dev(f, h->d_counts, NL, buf, h->stream);
     h->free_slots.resize((size_t)hd.n_free);
     ok = ok && (hd.n_free == 0 || fread(h->free_slots.data(), sizeof(int64_t), (size_t)hd.n_free, f) == (size_t)hd.n_free);
     if (!ok) return bail(MRF_EINVAL);
     fclose(f);
-    if (build_csr(h) != cudaSuccess) { cudaGetLastError(); mrf_destroy(h); return MRF_ECUDA; }
+    if (build_csr(h) != cudaSuccess ||
+        (h->d_swut && launch_fold_unary(h->d_unary, h->d_swfold, h->d_inc_ptr, h->d_inc, h->N, h->L, h->d_swut,
+                                        nullptr, h->stream) != cudaSuccess)) {
+        cudaGetLastError();
+        mrf_destroy(h);
+        return MRF_ECUDA;
+    }
+    // labels index per-label tables in every kernel: a file with a label >= L is rejected
+    unsigned long long bad_labels = 1;
+    if (cudaMemsetAsync(h->d_flag, 0, sizeof(unsigned long long), h->stream) != cudaSuccess ||
+        launch_count_ge(h->d_x, 2 * (int64_t)h->N * h->C, h->L, h->d_flag, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&bad_labels, h->d_flag, sizeof(bad_labels), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        mrf_destroy(h);
+        return MRF_ECUDA;
+    }
+    if (bad_labels) { mrf_destroy(h); return MRF_EINVAL; }
     if (cudaMemcpyAsync(h->d_ctl, &hd.ctl, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess) {
         cudaGetLastError();

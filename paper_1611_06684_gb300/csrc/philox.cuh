@@ -20,6 +20,8 @@ enum Phase : uint32_t {
     PH_SPLASH = 6,    // block-grid offset of a blocked sweep (words 0..2)
     PH_PROPOSAL = 7,
     PH_ACCEPT = 8,
+    PH_BOND = 9,      // Swendsen-Wang bond of (edge, chain) (word 0, 23-bit uniform)
+    PH_CLUSTER = 10,  // Swendsen-Wang cluster label, index = the cluster's smallest site (word 0)
 };
 
 __host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {

@@ -1,0 +1,260 @@
+// Swendsen-Wang sweep as a degenerate duality (Section 4.3).
+//
+// For a ferromagnetic Potts-type table exp(l_x [x_s = x_t]) with l_x >= 0 the
+// dual variable of an edge is one bond bit: given x it is 1 with probability
+// 1 - e^{-l_{x_s}} when x_s = x_t (never otherwise); given the bonds, the
+// bonds' connected components (clusters) take one label each, cluster K
+// label x with weight exp(sum_{v in K} u_v(x) + sum_{bonds in K} log(e^{l_x} - 1)).
+//
+// One sweep on the device, items (site or edge, chain) with the chain
+// innermost so that a warp works on one site or edge for 32 chains:
+//   k_sw_init     parent[v][c] = v, cluster weights of singletons (the unaries)
+//   k_sw_bond     bond draws; each bond unions its endpoints' trees and adds
+//                 its label weights to its source site's row
+//   k_sw_flatten  every site finds its root (the smallest site of its cluster)
+//                 and adds its row into the root's row
+//   k_sw_draw     roots draw their cluster's label; then k_sw_assign copies it
+//                 to the other sites.
+// The union-find is lock-free: a link always points from a root to a smaller
+// site (atomicCAS on the root's entry), so every walk visits strictly
+// decreasing sites and ends within N steps; a walk that exceeds that bound
+// sets the error flag instead of looping.  The forest of a chain is its own
+// column of parent[][], so chains never contend.
+#include "sweep_impl.cuh"   // draw_label
+
+namespace mrfk {
+
+namespace {
+
+__device__ __forceinline__ int64_t pidx(int32_t v, int32_t c, int32_t C) { return (int64_t)v * C + c; }
+
+// Root of v.  While k_sw_bond links roots, loads bypass L1 and the walk
+// halves the path: a halving store only ever replaces a non-root's parent by
+// one of its ancestors, so it never conflicts with a link.  k_sw_flatten walks
+// without stores: there every site's owner thread writes the root into its
+// own entry, and a halving store from another walk landing after it would
+// leave a non-root ancestor there.  Returns -1 when the step bound is exceeded.
+template <bool LINKING>
+__device__ __forceinline__ int32_t sw_find(int32_t* __restrict__ par, int32_t v, int32_t c, int32_t C, int32_t N) {
+    for (int32_t step = 0; step <= N; ++step) {
+        const int32_t p = LINKING ? __ldcg(par + pidx(v, c, C)) : par[pidx(v, c, C)];
+        if (p == v) return v;
+        if (LINKING) {
+            const int32_t gp = __ldcg(par + pidx(p, c, C));
+            if (gp != p) par[pidx(v, c, C)] = gp;
+            v = gp;
+        } else {
+            v = p;
+        }
+    }
+    return -1;
+}
+
+// Union of the trees of a and b: the larger root is linked to the smaller one.
+// A failed link means that root was linked meanwhile; the retry starts from
+// roots strictly smaller than before, so at most N retries happen.
+__device__ __forceinline__ bool sw_union(int32_t* __restrict__ par, int32_t a, int32_t b, int32_t c, int32_t C,
+                                         int32_t N) {
+    for (int32_t step = 0; step <= N; ++step) {
+        a = sw_find<true>(par, a, c, C, N);
+        b = sw_find<true>(par, b, c, C, N);
+        if (a < 0 || b < 0) return false;
+        if (a == b) return true;
+        if (a < b) { const int32_t t = a; a = b; b = t; }
+        if (atomicCAS(par + pidx(a, c, C), a, b) == a) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void red_add_s64(int64_t* p, int64_t v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_sw_init(SwArgs a) {
+    const int64_t n = (int64_t)a.N * a.C;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = (int32_t)a.fdC.div((uint32_t)g), c = (int32_t)(g - (int64_t)v * a.C);
+        a.parent[g] = v;
+        a.ban[g] = 0u;
+        for (int x = 0; x < a.L; ++x) {
+            const int64_t i = (int64_t)v * a.L + x;
+            a.lw[i * a.C + c] = sw_fix(a.unary_d ? a.unary_d[i] : (double)a.unary[i]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_sw_bond(SwArgs a) {
+    const int64_t n = a.E * a.C;
+    const unsigned long long t = a.ctl->sweep;
+    const uint8_t* __restrict__ xin = a.x + (size_t)(t & 1) * a.N * a.C;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = a.fdC.div((uint32_t)g);
+        const int32_t c = (int32_t)(g - e * a.C);
+        const int32_t s = a.src[e];
+        if (s < 0) continue;
+        const int32_t d = a.dst[e];
+        const int xs = xin[pidx(s, c, a.C)];
+        if (xs != xin[pidx(d, c, a.C)]) continue;
+        const uint32_t T = a.thr[e * a.L + xs];
+        if (T == 0u) continue;
+        const uint32_t U = draw_rk((uint32_t)e, (uint32_t)t, (uint32_t)c, PH_BOND, 0, a.rk).x >> 9;
+        if (U >= T) continue;
+        if (!sw_union(a.parent, s, d, c, a.C, a.N)) { atomicOr(a.err, 1u); continue; }
+        uint32_t ban = 0u;
+        for (int x = 0; x < a.L; ++x) {
+            const int64_t w = a.lwe[e * a.L + x];
+            if (w == kSwNoLabel) ban |= 1u << x;
+            else red_add_s64(a.lw + ((int64_t)s * a.L + x) * a.C + c, w);
+        }
+        if (ban) atomicOr(a.ban + pidx(s, c, a.C), ban);
+    }
+}
+
+// Roots are final once k_sw_bond has finished: a site's row (its unaries and
+// the weights of bonds it is the source of) moves into its root's row.  Only
+// roots' rows are written here and only non-roots' rows are read.
+__global__ void __launch_bounds__(256) k_sw_flatten(SwArgs a) {
+    const int64_t n = (int64_t)a.N * a.C;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = (int32_t)a.fdC.div((uint32_t)g), c = (int32_t)(g - (int64_t)v * a.C);
+        const int32_t r = sw_find<false>(a.parent, v, c, a.C, a.N);
+        if (r < 0) { atomicOr(a.err, 1u); continue; }
+        if (r == v) continue;
+        a.parent[g] = r;
+        for (int x = 0; x < a.L; ++x)
+            red_add_s64(a.lw + ((int64_t)r * a.L + x) * a.C + c, a.lw[((int64_t)v * a.L + x) * a.C + c]);
+        const uint32_t ban = a.ban[g];
+        if (ban) atomicOr(a.ban + pidx(r, c, a.C), ban);
+    }
+}
+
+// Label of every cluster, drawn at its root r by the inverse CDF with the
+// uniform of Philox(r, t, c, CLUSTER).  Differences to the largest weight are
+// exact in fixed point and then rounded to float for the softmax.
+template <int L>
+__global__ void __launch_bounds__(256) k_sw_draw(SwArgs a) {
+    const int64_t n = (int64_t)a.N * a.C;
+    const unsigned long long t = a.ctl->sweep;
+    uint8_t* __restrict__ xout = a.x + (size_t)((t + 1) & 1) * a.N * a.C;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = (int32_t)a.fdC.div((uint32_t)g), c = (int32_t)(g - (int64_t)v * a.C);
+        if (a.parent[g] != v) continue;
+        const uint32_t ban = a.ban[g];
+        int64_t w[L];
+        int64_t mx = 0;
+        bool any = false;
+#pragma unroll
+        for (int x = 0; x < L; ++x) {
+            w[x] = a.lw[((int64_t)v * L + x) * a.C + c];
+            if (!((ban >> x) & 1u) && (!any || w[x] > mx)) { mx = w[x]; any = true; }
+        }
+        float F[L];
+#pragma unroll
+        for (int x = 0; x < L; ++x)
+            F[x] = ((ban >> x) & 1u) ? -INFINITY : (float)(w[x] - mx) * (float)(1.0 / kSwFixScale);
+        xout[g] = (uint8_t)draw_label<L>(F, (uint32_t)v, (uint32_t)c, (uint32_t)t, a.rk, PH_CLUSTER, nullptr, a.ctl);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_sw_assign(SwArgs a) {
+    const int64_t n = (int64_t)a.N * a.C;
+    const unsigned long long t = a.ctl->sweep;
+    uint8_t* __restrict__ xout = a.x + (size_t)((t + 1) & 1) * a.N * a.C;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = (int32_t)a.fdC.div((uint32_t)g), c = (int32_t)(g - (int64_t)v * a.C);
+        const int32_t r = a.parent[g];
+        if (r != v) xout[g] = xout[pidx(r, c, a.C)];
+    }
+}
+
+// Model check before the first Swendsen-Wang sweep after the factors change:
+// out[0] = dual weights tau < 0 on live edges (antiferromagnetic entries; with
+// two labels the one pivot entry's tau has the sign of l),
+// out[1] = sum over live edges of max_x |log(e^{l_x} - 1)| over bondable labels,
+// out[2] = sum over sites of max_x |u_v(x)| (the unaries the sweep uses).
+// out[1] + out[2] bounds the magnitude of every partial sum of a cluster weight.
+__global__ void k_sw_check(const int32_t* src, const float* tau, int64_t E, int M, const int64_t* lwe, int L,
+                           const float* unary, const double* unary_d, int N, double* out) {
+    double neg = 0.0, se = 0.0, su = 0.0;
+    const int MP = pad4(M);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        if (src[e] < 0) continue;
+        double m = 0.0;
+        for (int k = 0; k < M; ++k) neg += tau[e * MP + k] < 0.0f;
+        for (int x = 0; x < L; ++x) {
+            const int64_t w = lwe[e * L + x];
+            if (w != kSwNoLabel) m = fmax(m, fabs((double)w / kSwFixScale));
+        }
+        se += m;
+    }
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
+        double m = 0.0;
+        for (int x = 0; x < L; ++x) m = fmax(m, fabs(unary_d ? unary_d[v * L + x] : (double)unary[v * L + x]));
+        su += m;
+    }
+    if (neg != 0.0) atomicAdd(out + 0, neg);
+    if (se != 0.0) atomicAdd(out + 1, se);
+    if (su != 0.0) atomicAdd(out + 2, su);
+}
+
+#define MRF_DISPATCH_LSW(L_, ...)                                                 \
+    switch (L_) {                                                                 \
+        case 2: { constexpr int LL = 2; __VA_ARGS__; } break;                     \
+        case 3: { constexpr int LL = 3; __VA_ARGS__; } break;                     \
+        case 4: { constexpr int LL = 4; __VA_ARGS__; } break;                     \
+        case 5: { constexpr int LL = 5; __VA_ARGS__; } break;                     \
+        case 6: { constexpr int LL = 6; __VA_ARGS__; } break;                     \
+        case 7: { constexpr int LL = 7; __VA_ARGS__; } break;                     \
+        case 8: { constexpr int LL = 8; __VA_ARGS__; } break;                     \
+        case 9: { constexpr int LL = 9; __VA_ARGS__; } break;                     \
+        case 10: { constexpr int LL = 10; __VA_ARGS__; } break;                   \
+        case 11: { constexpr int LL = 11; __VA_ARGS__; } break;                   \
+        case 12: { constexpr int LL = 12; __VA_ARGS__; } break;                   \
+        case 13: { constexpr int LL = 13; __VA_ARGS__; } break;                   \
+        case 14: { constexpr int LL = 14; __VA_ARGS__; } break;                   \
+        case 15: { constexpr int LL = 15; __VA_ARGS__; } break;                   \
+        case 16: { constexpr int LL = 16; __VA_ARGS__; } break;                   \
+        default: return cudaErrorInvalidValue;                                    \
+    }
+
+static inline unsigned sw_blocks(int64_t n) {
+    // grid-stride loops over at most 8 resident blocks of 256 threads per SM
+    const int64_t b = (n + 255) / 256;
+    return (unsigned)(b < 152 * 8 ? (b > 0 ? b : 1) : 152 * 8);
+}
+
+cudaError_t launch_sw_check(const int32_t* src, const float* tau, int64_t E, int M, const int64_t* lwe, int L,
+                            const float* unary, const double* unary_d, int N, double* out, cudaStream_t s) {
+    k_sw_check<<<sw_blocks(E > N ? E : N), 256, 0, s>>>(src, tau, E, M, lwe, L, unary, unary_d, N, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sw_init(const SwArgs& a, cudaStream_t s) {
+    const int64_t n = (int64_t)a.N * a.C;
+    if (n > 0) k_sw_init<<<sw_blocks(n), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sw_bond(const SwArgs& a, cudaStream_t s) {
+    const int64_t n = a.E * a.C;
+    if (n > 0) k_sw_bond<<<sw_blocks(n), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sw_flatten(const SwArgs& a, cudaStream_t s) {
+    const int64_t n = (int64_t)a.N * a.C;
+    if (n > 0) k_sw_flatten<<<sw_blocks(n), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sw_draw(const SwArgs& a, cudaStream_t s) {
+    const int64_t n = (int64_t)a.N * a.C;
+    if (n <= 0) return cudaSuccess;
+    MRF_DISPATCH_LSW(a.L, (k_sw_draw<LL><<<sw_blocks(n), 256, 0, s>>>(a)));
+    k_sw_assign<<<sw_blocks(n), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace mrfk

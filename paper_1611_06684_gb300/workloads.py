@@ -202,6 +202,37 @@ def tiny_potts(N: int, L: int, E: int, beta_max: float = 0.8, u_std: float = 1.0
     return Model(N, L, unary, src, dst, pair, name=f"tinypotts_N{N}_L{L}")
 
 
+def ferro_potts_grid3d(nx: int = 128, ny: Optional[int] = None, nz: Optional[int] = None, L: int = 8,
+                       beta_lo: float = 0.0, beta_hi: float = 1.0, u_std: float = 0.5, seed: int = 0) -> Model:
+    """3-D 6-neighbour grid with ferromagnetic Potts tables w_e(a,b) = beta_e [a=b],
+    beta_e ~ U[beta_lo, beta_hi], and unaries ~ N(0, u_std^2) (Swendsen-Wang workloads)."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    rng = np.random.default_rng(seed)
+    N = nx * ny * nz
+    src, dst = grid3d_edges(nx, ny, nz)
+    unary = _f32_normal(rng, u_std, (N, L))
+    beta = _f32_uniform(rng, beta_lo, beta_hi, src.shape[0])
+    pair = np.zeros((src.shape[0], L, L), np.float32)
+    pair[:, np.arange(L), np.arange(L)] = beta[:, None]
+    return Model(N, L, unary, src, dst, pair, grid=(nx, ny, nz), name=f"ferro3d_{nx}x{ny}x{nz}_L{L}")
+
+
+def ferro_potts_graph(N: int, L: int, E: int, beta_lo: float = 0.05, beta_hi: float = 1.5, u_std: float = 1.0,
+                      p_zero: float = 0.0, seed: int = 0) -> Model:
+    """Random graph with generalised ferromagnetic Potts tables w_e(a,b) = beta_{e,a} [a=b]
+    (a coupling per label, ~ U[beta_lo, beta_hi]; each set to 0 with probability p_zero)."""
+    rng = np.random.default_rng(seed)
+    src, dst = _distinct_pairs(rng, N, E)
+    unary = _f32_normal(rng, u_std, (N, L))
+    beta = _f32_uniform(rng, beta_lo, beta_hi, (src.shape[0], L))
+    if p_zero > 0:
+        beta[rng.random(beta.shape) < p_zero] = 0.0
+    pair = np.zeros((src.shape[0], L, L), np.float32)
+    pair[:, np.arange(L), np.arange(L)] = beta
+    return Model(N, L, unary, src, dst, pair, name=f"ferro_graph_N{N}_L{L}")
+
+
 def ba_potts(N: int = 1_000_000, m: int = 5, L: int = 4, beta_max: float = 0.8, u_std: float = 1.0,
              seed: int = 0) -> Model:
     """Barabasi-Albert preferential-attachment graph (m edges per new node,

@@ -4,7 +4,7 @@ import itertools
 import numpy as np
 import pytest
 
-from oracle import brute, decompose as dc, philox as ph, swendsen_wang as sw
+from oracle import brute, philox as ph, swendsen_wang as sw
 from oracle.sampler import log_softmax
 from paper_1611_06684_gb300 import workloads as wl
 
@@ -18,22 +18,39 @@ def _model(seed, N=5, L=3, E=6):
     beta = rng.uniform(0.05, 1.5, (m.src.size, L)).astype(np.float32)
     pair = np.zeros((m.src.size, L, L), np.float32)
     pair[:, np.arange(L), np.arange(L)] = beta
-    m = wl.Model(m.n_vars, L, m.unary, m.src, m.dst, pair, name="tinypotts_gen")
-    return m, dc.decompose(m)
+    return wl.Model(m.n_vars, L, m.unary, m.src, m.dst, pair, name="tinypotts_gen")
 
 
-def _joint_log(model, dec, X, B):
-    """log p~(x, theta) [S_x][S_theta] = sum u + sum over bonded edges of log(e^{l} - 1) (or -inf)."""
-    u = np.asarray(model.unary, np.float64)
+def _model_two_labels(seed, N=5, E=7):
+    """Two labels, arbitrary ferromagnetic tables (w00 + w11 >= w01 + w10) with
+    nonzero off-diagonal entries, so that the folded offsets matter."""
+    m = wl.tiny_random(N, 2, E, seed=seed)
+    w = m.pair.astype(np.float64)
+    k = 0.5 * (w[:, 0, 0] + w[:, 1, 1] - w[:, 0, 1] - w[:, 1, 0])
+    w[:, 0, 0] += np.where(k < 0, -2 * k + 0.1, 0.0)                # make every coupling positive
+    return wl.Model(m.n_vars, 2, m.unary, m.src, m.dst, w.astype(np.float32), name="tiny_two_labels")
+
+
+MODELS = {"potts_L3_s1": lambda: _model(1), "potts_L3_s2": lambda: _model(2),
+          "two_labels_s3": lambda: _model_two_labels(3), "two_labels_s4": lambda: _model_two_labels(4)}
+
+
+def _joint_log(model, X, B):
+    """log p~(x, theta) [S_x][S_theta] = sum u + sum over bonded edges of log(e^{l} - 1)
+    (-inf where a bond joins unequal labels or has l = 0), from the SW tables."""
+    ell, u = sw.sw_tables(model)
     lu = u[np.arange(model.n_vars)[None, :], X].sum(axis=1)
-    xs, xt = X[:, dec.src], X[:, dec.dst]
-    ell = np.where(dec.active, dec.ell, 0.0)
-    l_at = ell[np.arange(dec.src.size)[None, :], xs]
+    xs, xt = X[:, model.src], X[:, model.dst]
+    l_at = ell[np.arange(model.src.size)[None, :], xs]
     with np.errstate(divide="ignore"):
         lb = np.where(xs == xt, np.log(np.expm1(l_at)), -np.inf)          # [S_x][E]
     out = lu[:, None] + (B[None, :, :] * np.where(np.isfinite(lb), lb, -1e300)[:, None, :]).sum(axis=2)
     ok = ~((B[None, :, :] == 1) & ~np.isfinite(lb)[:, None, :]).any(axis=2)
     return np.where(ok, out, -np.inf)
+
+
+def _normalised(lp):
+    return lp - np.logaddexp.reduce(lp)
 
 
 def test_decomposition_reproduces_the_factor():
@@ -48,21 +65,24 @@ def test_decomposition_reproduces_the_factor():
             assert abs(np.exp(-l) + (1 - np.exp(-l)) * np.exp(-I0) - np.exp(l * (a == b) - l)) < 1e-12
 
 
-@pytest.mark.parametrize("seed", [1, 2])
-def test_joint_marginalises_and_cluster_rule_is_the_conditional(seed):
-    model, dec = _model(seed)
+@pytest.mark.parametrize("name", list(MODELS))
+def test_joint_marginalises_and_cluster_rule_is_the_conditional(name):
+    model = MODELS[name]()
     X = brute.all_labelings(model.n_vars, model.n_labels)
-    B = brute.all_dual_configs(dec.src.size)
-    J = _joint_log(model, dec, X, B)
-    np.testing.assert_allclose(np.logaddexp.reduce(J, axis=1), brute.log_ptilde(model, X), atol=1e-10)
-    rng = np.random.default_rng(seed)
+    B = brute.all_dual_configs(model.src.size)
+    J = _joint_log(model, X, B)
+    # p~(x) up to the dropped constants c_e
+    np.testing.assert_allclose(_normalised(np.logaddexp.reduce(J, axis=1)), _normalised(brute.log_ptilde(model, X)),
+                               atol=1e-10)
+    ell, u = sw.sw_tables(model)
+    rng = np.random.default_rng(len(name))
     for bi in rng.choice(B.shape[0], size=6, replace=False):
         col = J[:, bi]
         if not np.isfinite(col).any():
             continue
         p_exact = np.exp(col - np.logaddexp.reduce(col))
-        root = sw.clusters(model.n_vars, dec.src, dec.dst, B[bi].astype(bool))
-        lw = sw.cluster_log_weights(model, dec, root, B[bi].astype(bool))
+        root = sw.clusters(model.n_vars, model.src, model.dst, B[bi].astype(bool))
+        lw = sw.cluster_log_weights(u, ell, model.src, root, B[bi].astype(bool))
         rs = np.unique(root)
         lp = log_softmax(lw[rs])
         pos = {r: i for i, r in enumerate(rs)}
@@ -73,11 +93,12 @@ def test_joint_marginalises_and_cluster_rule_is_the_conditional(seed):
         np.testing.assert_allclose(p_rule, p_exact, atol=1e-12)
 
 
-def test_sw_kernel_is_stationary():
-    model, dec = _model(3, N=4, L=3, E=5)
+@pytest.mark.parametrize("name", ["potts_L3_s1", "two_labels_s3"])
+def test_sw_kernel_is_stationary(name):
+    model = MODELS[name]()
     X = brute.all_labelings(model.n_vars, model.n_labels)
-    B = brute.all_dual_configs(dec.src.size)
-    J = _joint_log(model, dec, X, B)
+    B = brute.all_dual_configs(model.src.size)
+    J = _joint_log(model, X, B)
     lp_b_x = J - np.logaddexp.reduce(J, axis=1)[:, None]                # p(theta | x)
     lp_x_b = J - np.logaddexp.reduce(J, axis=0)[None, :]                # p(x | theta)
     with np.errstate(invalid="ignore"):
@@ -87,16 +108,32 @@ def test_sw_kernel_is_stationary():
     np.testing.assert_allclose(p @ K, p, atol=1e-12)
 
 
-def test_sw_chain_marginals_within_3_sigma():
-    model, dec = _model(4, N=6, L=3, E=8)
+@pytest.mark.parametrize("name", ["potts_L3", "two_labels"])
+def test_sw_chain_marginals_within_3_sigma(name):
+    model = _model(4, N=6, L=3, E=8) if name == "potts_L3" else _model_two_labels(5, N=7, E=10)
+    L = model.n_labels
     exact, _ = brute.exact_marginals(model)
     C, T, burn, seed = 512, 60, 10, 5
-    x = ph.init_labels(model.n_vars, 3, C, seed)
-    acc = np.zeros((C, model.n_vars, 3))
+    x = ph.init_labels(model.n_vars, L, C, seed)
+    tables = sw.sw_tables(model)
+    acc = np.zeros((C, model.n_vars, L))
     for t in range(T):
-        x = sw.sw_sweep(model, dec, x, t, seed)["x"]
+        x = sw.sw_sweep(model, x, t, seed, tables=tables)["x"]
         if t >= burn:
             acc[np.arange(C)[:, None], np.arange(model.n_vars)[None, :], x] += 1
     cm = acc / (T - burn)
     z = np.abs(cm.mean(0) - exact) / np.maximum(cm.std(0, ddof=1) / np.sqrt(C), 1e-12)
     assert z.max() < 4.5 and np.mean(z < 3.0) > 0.9, z
+
+
+def test_sw_tables_reject_other_models():
+    with pytest.raises(ValueError):
+        sw.sw_tables(wl.tiny_random(5, 3, 6, seed=1))                      # full L = 3 tables
+    m = _model(1)
+    m.pair[2, 1, 1] = -0.3
+    with pytest.raises(ValueError):
+        sw.sw_tables(m)                                                  # antiferromagnetic entry
+    m = _model_two_labels(3)
+    m.pair[0, 0, 1] += 10.0
+    with pytest.raises(ValueError):
+        sw.sw_tables(m)                                                  # w00 + w11 < w01 + w10
