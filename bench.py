@@ -141,18 +141,14 @@ def kernel_work(name, model_info, C):
         return 2 * calls_dual + N * C, 2 * E * m * 4 + N * L * 8 + 2 * E * 8 + 2 * N * C
     if name == "k_accumulate":
         return 0, N * C + 2 * N * L * 4
-    # Swendsen-Wang: one pass over each per-(site, chain) array the kernel
-    # touches (parent 4 B, banned labels 4 B, fixed-point weight row 8 L B,
-    # labels 1 B) and the per-edge tables; union-find walks and atomics to
-    # other rows depend on the clusters and are not counted
-    if name == "k_sw_init":
-        return 0, N * C * (8 + 8 * L) + N * L * 4
+    # Swendsen-Wang: one pass over the arrays every item touches (labels of
+    # both endpoints per (edge, chain), the per-edge tables; ban word, label
+    # and the unaries per (site, chain)); union-find walks, bonded sites' rows
+    # and list traffic depend on the clusters and are not counted
     if name == "k_sw_bond":
         return 0, E * 8 + E * L * 12 + 2 * E * C
-    if name == "k_sw_flatten":
-        return 0, N * C * (8 + 8 * L)
     if name == "k_sw_draw":
-        return 0, N * C * (4 + 8 * L + 1) + N * C * (4 + 1)
+        return 0, N * C * (4 + 1) + N * L * 4
     return 0, 0
 
 
@@ -715,6 +711,7 @@ def run_learned_workload(args):
 
 
 def main():
+    global FERRO_BETA, FERRO_U_STD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
@@ -726,11 +723,17 @@ def main():
     ap.add_argument("--mode", default="plain", choices=["plain", "fused", "sw"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--scale", type=int, default=0, help="lattice edge for potts3d (default 128)")
+    ap.add_argument("--ferro-beta", default=None, help="lo,hi of the ferro3d couplings (default %g,%g)" % FERRO_BETA)
+    ap.add_argument("--ferro-u-std", type=float, default=None, help="unary std of ferro3d (default %g)" % FERRO_U_STD)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.ferro_beta:
+        FERRO_BETA = tuple(float(v) for v in args.ferro_beta.split(","))
+    if args.ferro_u_std is not None:
+        FERRO_U_STD = args.ferro_u_std
     ws, rank, local = dist_env()
     if args.workload in ("er_batch", "ba_learned") and args.impl == "ours":
         out = run_batch_workload(args) if args.workload == "er_batch" else run_learned_workload(args)

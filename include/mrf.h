@@ -196,9 +196,9 @@ mrf_status mrf_debug_theta(mrf_t* h, uint32_t* out);
 enum { MRF_K_DUAL = 0, MRF_K_PRIMAL = 1, MRF_K_FUSED = 2, MRF_K_POTENTIAL = 3, MRF_K_FFBS = 4,
        MRF_K_ACCUMULATE = 5, MRF_K_FEATURES = 6, MRF_K_MLP = 7, MRF_K_MH = 8,
        MRF_K_SMALL = 9,    /* whole plain sweeps of a small model in one launch (see mrf_sweep) */
-       MRF_K_SW_INIT = 10, MRF_K_SW_BOND = 11, MRF_K_SW_FLATTEN = 12,
-       MRF_K_SW_DRAW = 13, /* Swendsen-Wang: label draw of every cluster and the copy to its sites */
-       MRF_K_COUNT = 14 };
+       MRF_K_SW_BOND = 10, MRF_K_SW_FLATTEN = 11,
+       MRF_K_SW_DRAW = 12, /* Swendsen-Wang: label draw of every cluster and the copy to its sites */
+       MRF_K_COUNT = 13 };
 /* With options.kernel_timing: total device milliseconds ms[MRF_K_COUNT] and
  * launch counts launches[MRF_K_COUNT] of every sweep kernel since the last
  * call (CUDA events on the handle's stream); resets the totals.  Synchronises. */

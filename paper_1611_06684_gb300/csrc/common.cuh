@@ -22,6 +22,12 @@ constexpr int kMaxLabels = 16;
 constexpr double kSwFixScale = 4294967296.0;               // 2^32
 constexpr double kSwFixMax = 1073741824.0;                 // 2^30
 constexpr int64_t kSwNoLabel = (int64_t)(-0x7fffffffffffffffLL - 1);   // bonded: label excluded
+// Swendsen-Wang ban word of a (site, chain): bits 0..15 labels the cluster
+// may not take, kSwBonded = the site has a bond in this sweep, kSwRow = its
+// weight row holds bond weights (it is the source of a bond).
+constexpr uint32_t kSwLabelMask = 0xFFFFu;
+constexpr uint32_t kSwRow = 1u << 30;
+constexpr uint32_t kSwBonded = 1u << 31;
 __host__ __device__ inline int64_t sw_fix(double x) {
     x = x > kSwFixMax ? kSwFixMax : (x < -kSwFixMax ? -kSwFixMax : x);
     return (int64_t)llrint(x * kSwFixScale);
@@ -139,12 +145,12 @@ struct SwArgs {
     const int32_t* dst;        // [E]
     const uint32_t* thr;       // [E][L] 23-bit bond thresholds
     const int64_t* lwe;        // [E][L] fixed-point bond log weights (kSwNoLabel: label excluded)
-    const float* unary;        // [N][L] raw unaries (diagonal tables)
-    const double* unary_d;     // [N][L] unaries with the two-label offsets folded in, or null
+    const int64_t* ufix;       // [N][L] fixed-point unaries (two labels: offsets folded in)
     uint8_t* x;                // [2][N][C] label double buffer
     int32_t* parent;           // [N][C] union-find forest, links to smaller sites only
+    int32_t* root;             // [N][C] root of a bonded site (written by k_sw_flatten)
     uint32_t* ban;             // [N][C] labels a cluster may not take (bit per label)
-    int64_t* lw;               // [N][L][C] fixed-point cluster label log weights (valid at roots)
+    int64_t* lw;               // [N][L][C] fixed-point bond weights, then cluster weights at roots
     unsigned* err;             // set when a union-find walk exceeded its step bound
     Ctl* ctl;
     RoundKeys rk;
@@ -233,7 +239,8 @@ cudaError_t launch_sweep_noalloc(const SweepArgs& a, int layout, const uint8_t* 
 // Swendsen-Wang (sw.cu)
 cudaError_t launch_sw_check(const int32_t* src, const float* tau, int64_t E, int M, const int64_t* lwe, int L,
                             const float* unary, const double* unary_d, int N, double* out, cudaStream_t s);
-cudaError_t launch_sw_init(const SwArgs& a, cudaStream_t s);
+cudaError_t launch_sw_fix_unary(const float* unary, const double* unary_d, int64_t n, int64_t* ufix, cudaStream_t s);
+cudaError_t launch_sw_reset(const SwArgs& a, cudaStream_t s);
 cudaError_t launch_sw_bond(const SwArgs& a, cudaStream_t s);
 cudaError_t launch_sw_flatten(const SwArgs& a, cudaStream_t s);
 cudaError_t launch_sw_draw(const SwArgs& a, cudaStream_t s);

@@ -63,9 +63,11 @@ struct mrf {
     double* d_swfold = nullptr;        // [E][2][L] two-label unary offsets
     double* d_swut = nullptr;          // [N][L] two-label unaries with the offsets folded in
     int32_t* d_swpar = nullptr;        // [N][C] union-find parents
+    int32_t* d_swroot = nullptr;       // [N][C] roots of bonded sites
     uint32_t* d_swban = nullptr;       // [N][C] excluded labels of a cluster
     int64_t* d_swlw = nullptr;         // [N][L][C] fixed-point cluster log weights
     unsigned* d_swerr = nullptr;       // union-find step bound exceeded
+    int64_t* d_swufix = nullptr;       // [N][L] fixed-point unaries of the Swendsen-Wang sweep
     double* d_swchk = nullptr;         // [3] model check sums (k_sw_check)
     bool sw_checked = false;           // the model passed the check since the factors last changed
     float* d_pot = nullptr;            // [N][L][C] node potentials of the blocked sweep
@@ -383,7 +385,8 @@ void mrf_destroy(mrf_t* h) {
     dfree(h->d_unary); dfree(h->d_ut); dfree(h->d_utf); dfree(h->d_tpl); dfree(h->d_src); dfree(h->d_dst); dfree(h->d_tau); dfree(h->d_thr);
     dfree(h->d_fold); dfree(h->d_cst); dfree(h->d_resid); dfree(h->d_inc_ptr); dfree(h->d_inc); dfree(h->d_x);
     dfree(h->d_theta); dfree(h->d_ties); dfree(h->d_tie_count); dfree(h->d_counts); dfree(h->d_lpv); dfree(h->d_logv); dfree(h->d_em); dfree(h->d_mfq); dfree(h->d_mfs); dfree(h->d_logp); dfree(h->d_ctl); dfree(h->d_flag); dfree(h->d_stage); dfree(h->d_pot);
-    dfree(h->d_swt); dfree(h->d_swl); dfree(h->d_swfold); dfree(h->d_swut); dfree(h->d_swpar); dfree(h->d_swban); dfree(h->d_swlw); dfree(h->d_swerr); dfree(h->d_swchk);
+    dfree(h->d_swt); dfree(h->d_swl); dfree(h->d_swfold); dfree(h->d_swut); dfree(h->d_swpar); dfree(h->d_swroot); dfree(h->d_swban); dfree(h->d_swlw); dfree(h->d_swerr); dfree(h->d_swchk);
+    dfree(h->d_swufix);
     dfree(h->d_csr_work); dfree(h->d_csr_sums);
     dfree(h->d_ed_pair); dfree(h->d_ed_slots); dfree(h->d_ed_new); dfree(h->d_ed_s); dfree(h->d_ed_t);
     dfree(h->d_members); dfree(h->d_nmem); dfree(h->d_intra_ptr); dfree(h->d_intra); dfree(h->d_cf); dfree(h->d_skip);
@@ -674,8 +677,8 @@ static bool small_model(const mrf_t* h) {
 static SwArgs make_sw_args(const mrf_t* h) {
     SwArgs w{};
     w.N = h->N; w.C = h->C; w.L = h->L; w.E = h->E_slots;
-    w.src = h->d_src; w.dst = h->d_dst; w.thr = h->d_swt; w.lwe = h->d_swl; w.unary = h->d_unary; w.unary_d = h->d_swut;
-    w.x = h->d_x; w.parent = h->d_swpar; w.ban = h->d_swban; w.lw = h->d_swlw; w.err = h->d_swerr;
+    w.src = h->d_src; w.dst = h->d_dst; w.thr = h->d_swt; w.lwe = h->d_swl; w.ufix = h->d_swufix;
+    w.x = h->d_x; w.parent = h->d_swpar; w.root = h->d_swroot; w.ban = h->d_swban; w.lw = h->d_swlw; w.err = h->d_swerr;
     w.ctl = h->d_ctl; w.rk = round_keys(h->key); w.fdC = FastDiv::make((uint32_t)h->C);
     return w;
 }
@@ -699,14 +702,17 @@ static mrf_status sw_prepare(mrf_t* h) {
         if (chk[0] > 0.0) return fail(h, MRF_EINVAL, "Swendsen-Wang sweeps need ferromagnetic tables (w(x,x) >= 0)");
         if (chk[1] + chk[2] >= kSwFixMax)
             return fail(h, MRF_ERANGE, "Swendsen-Wang: summed |log weights| exceed the fixed-point range (2^30)");
+        if (!h->d_swufix) { drop_graphs(h); MRF_CUDA(h, dalloc(h->d_swufix, (size_t)h->N * h->L)); }
+        MRF_CUDA(h, launch_sw_fix_unary(h->d_unary, h->d_swut, (int64_t)h->N * h->L, h->d_swufix, h->stream));
         h->sw_checked = true;
     }
     if (!h->d_swpar) {
         drop_graphs(h);
         const size_t NC = (size_t)h->N * h->C;
-        MRF_CUDA(h, dalloc(h->d_swpar, NC)); MRF_CUDA(h, dalloc(h->d_swban, NC));
+        MRF_CUDA(h, dalloc(h->d_swpar, NC)); MRF_CUDA(h, dalloc(h->d_swroot, NC)); MRF_CUDA(h, dalloc(h->d_swban, NC));
         MRF_CUDA(h, dalloc(h->d_swlw, NC * h->L)); MRF_CUDA(h, dalloc(h->d_swerr, 1));
         MRF_CUDA(h, cudaMemsetAsync(h->d_swerr, 0, sizeof(unsigned), h->stream));
+        MRF_CUDA(h, launch_sw_reset(make_sw_args(h), h->stream));
     }
     return MRF_OK;
 }
@@ -722,8 +728,7 @@ static mrf_status enqueue_sweep(mrf_t* h, int mode) {
         e = timed(h, MRF_K_FUSED, [&] { return launch_fused(a, h->layout, h->opt.schedule, s); });
     } else if (mode == MRF_MODE_SW) {
         const SwArgs w = make_sw_args(h);
-        e = timed(h, MRF_K_SW_INIT, [&] { return launch_sw_init(w, s); });
-        if (e == cudaSuccess) e = timed(h, MRF_K_SW_BOND, [&] { return launch_sw_bond(w, s); });
+        e = timed(h, MRF_K_SW_BOND, [&] { return launch_sw_bond(w, s); });
         if (e == cudaSuccess) e = timed(h, MRF_K_SW_FLATTEN, [&] { return launch_sw_flatten(w, s); });
         if (e == cudaSuccess) e = timed(h, MRF_K_SW_DRAW, [&] { return launch_sw_draw(w, s); });
     } else if (mode == MRF_MODE_LEARNED) {
@@ -803,8 +808,9 @@ mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode) {
         unsigned err = 0;
         MRF_CUDA(h, cudaMemcpyAsync(&err, h->d_swerr, sizeof(err), cudaMemcpyDeviceToHost, h->stream));
         MRF_CUDA(h, cudaStreamSynchronize(h->stream));
-        if (err) {
+        if (err) {                                          // the between-sweeps state is not restored
             MRF_CUDA(h, cudaMemsetAsync(h->d_swerr, 0, sizeof(unsigned), h->stream));
+            MRF_CUDA(h, launch_sw_reset(make_sw_args(h), h->stream));
             return fail(h, MRF_ETIMEOUT, "Swendsen-Wang: a union-find walk exceeded its step bound");
         }
     }

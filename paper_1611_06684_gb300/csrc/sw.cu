@@ -7,19 +7,28 @@
 // label x with weight exp(sum_{v in K} u_v(x) + sum_{bonds in K} log(e^{l_x} - 1)).
 //
 // One sweep on the device, items (site or edge, chain) with the chain
-// innermost so that a warp works on one site or edge for 32 chains:
-//   k_sw_init     parent[v][c] = v, cluster weights of singletons (the unaries)
-//   k_sw_bond     bond draws; each bond unions its endpoints' trees and adds
-//                 its label weights to its source site's row
-//   k_sw_flatten  every site finds its root (the smallest site of its cluster)
-//                 and adds its row into the root's row
-//   k_sw_draw     roots draw their cluster's label; then k_sw_assign copies it
-//                 to the other sites.
+// innermost so that a warp works on one site or edge for 32 chains.  Between
+// sweeps every site is its own tree (parent[v][c] = v), its ban word is 0 and
+// its weight row lw[v][.][c] is 0; a sweep touches only what its bonds reach
+// and restores that state:
+//   k_sw_bond     bond draws; a bond unions its endpoints' trees, adds its
+//                 label weights to its source site's row and marks both
+//                 endpoints bonded
+//   k_sw_flatten  every bonded site records its root (the smallest site of its
+//                 cluster) and adds its unaries and row into the root's row
+//   k_sw_draw     every root (bonded or not) draws its cluster's label from
+//                 its unaries plus its row
+//   k_sw_assign   bonded non-roots copy the root's label; rows, parents and
+//                 ban words of bonded sites are reset.
+// Unaries enter as fixed-point values precomputed once per factor change.
 // The union-find is lock-free: a link always points from a root to a smaller
 // site (atomicCAS on the root's entry), so every walk visits strictly
 // decreasing sites and ends within N steps; a walk that exceeds that bound
-// sets the error flag instead of looping.  The forest of a chain is its own
-// column of parent[][], so chains never contend.
+// sets the error flag instead of looping (the host then resets the state).
+// The forest of a chain is its own column of parent[][], so chains never
+// contend.
+#include <cooperative_groups.h>
+
 #include "sweep_impl.cuh"   // draw_label
 
 namespace mrfk {
@@ -28,24 +37,20 @@ namespace {
 
 __device__ __forceinline__ int64_t pidx(int32_t v, int32_t c, int32_t C) { return (int64_t)v * C + c; }
 
-// Root of v.  While k_sw_bond links roots, loads bypass L1 and the walk
-// halves the path: a halving store only ever replaces a non-root's parent by
-// one of its ancestors, so it never conflicts with a link.  k_sw_flatten walks
-// without stores: there every site's owner thread writes the root into its
-// own entry, and a halving store from another walk landing after it would
-// leave a non-root ancestor there.  Returns -1 when the step bound is exceeded.
-template <bool LINKING>
+// Root of v, halving the path on the way (loads bypass L1: other threads
+// rewrite entries meanwhile).  A halving store replaces a non-root's parent by
+// one of its ancestors, so it never meets a link (links only rewrite roots)
+// and any interleaving of halving stores leaves a forest with the same roots.
+// Roots found by k_sw_flatten go to a separate array, not into parent[][]: a
+// halving store landing after such a write would leave a non-root there.
+// Returns -1 when the step bound is exceeded.
 __device__ __forceinline__ int32_t sw_find(int32_t* __restrict__ par, int32_t v, int32_t c, int32_t C, int32_t N) {
     for (int32_t step = 0; step <= N; ++step) {
-        const int32_t p = LINKING ? __ldcg(par + pidx(v, c, C)) : par[pidx(v, c, C)];
+        const int32_t p = __ldcg(par + pidx(v, c, C));
         if (p == v) return v;
-        if (LINKING) {
-            const int32_t gp = __ldcg(par + pidx(p, c, C));
-            if (gp != p) par[pidx(v, c, C)] = gp;
-            v = gp;
-        } else {
-            v = p;
-        }
+        const int32_t gp = __ldcg(par + pidx(p, c, C));
+        if (gp != p) par[pidx(v, c, C)] = gp;
+        v = gp;
     }
     return -1;
 }
@@ -56,8 +61,8 @@ __device__ __forceinline__ int32_t sw_find(int32_t* __restrict__ par, int32_t v,
 __device__ __forceinline__ bool sw_union(int32_t* __restrict__ par, int32_t a, int32_t b, int32_t c, int32_t C,
                                          int32_t N) {
     for (int32_t step = 0; step <= N; ++step) {
-        a = sw_find<true>(par, a, c, C, N);
-        b = sw_find<true>(par, b, c, C, N);
+        a = sw_find(par, a, c, C, N);
+        b = sw_find(par, b, c, C, N);
         if (a < 0 || b < 0) return false;
         if (a == b) return true;
         if (a < b) { const int32_t t = a; a = b; b = t; }
@@ -72,19 +77,23 @@ __device__ __forceinline__ void red_add_s64(int64_t* p, int64_t v) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_sw_init(SwArgs a) {
+// float of a fixed-point weight difference d <= 0 (two 32-bit conversions:
+// GB300's 64-bit conversions run on its slow FP64 path).
+__device__ __forceinline__ float sw_float(int64_t d) {
+    return (float)(int32_t)(d >> 32) + (float)(uint32_t)d * (1.0f / 4294967296.0f);
+}
+
+// State between sweeps: parent[v][c] = v, ban[v][c] = 0, lw = 0 (the kernels
+// below restore it); this kernel sets parent and ban, the host zeroes lw.
+__global__ void __launch_bounds__(256) k_sw_reset(SwArgs a) {
     const int64_t n = (int64_t)a.N * a.C;
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t v = (int32_t)a.fdC.div((uint32_t)g), c = (int32_t)(g - (int64_t)v * a.C);
-        a.parent[g] = v;
+        a.parent[g] = (int32_t)a.fdC.div((uint32_t)g);
         a.ban[g] = 0u;
-        for (int x = 0; x < a.L; ++x) {
-            const int64_t i = (int64_t)v * a.L + x;
-            a.lw[i * a.C + c] = sw_fix(a.unary_d ? a.unary_d[i] : (double)a.unary[i]);
-        }
     }
 }
 
+template <int L>
 __global__ void __launch_bounds__(256) k_sw_bond(SwArgs a) {
     const int64_t n = a.E * a.C;
     const unsigned long long t = a.ctl->sweep;
@@ -97,42 +106,72 @@ __global__ void __launch_bounds__(256) k_sw_bond(SwArgs a) {
         const int32_t d = a.dst[e];
         const int xs = xin[pidx(s, c, a.C)];
         if (xs != xin[pidx(d, c, a.C)]) continue;
-        const uint32_t T = a.thr[e * a.L + xs];
+        const uint32_t T = a.thr[e * L + xs];
         if (T == 0u) continue;
         const uint32_t U = draw_rk((uint32_t)e, (uint32_t)t, (uint32_t)c, PH_BOND, 0, a.rk).x >> 9;
         if (U >= T) continue;
         if (!sw_union(a.parent, s, d, c, a.C, a.N)) { atomicOr(a.err, 1u); continue; }
-        uint32_t ban = 0u;
-        for (int x = 0; x < a.L; ++x) {
-            const int64_t w = a.lwe[e * a.L + x];
-            if (w == kSwNoLabel) ban |= 1u << x;
-            else red_add_s64(a.lw + ((int64_t)s * a.L + x) * a.C + c, w);
+        // every load before the first atomic (the compiler cannot move a load
+        // above an atomic to a possibly aliasing address)
+        int64_t wv[L];
+#pragma unroll
+        for (int x = 0; x < L; ++x) wv[x] = __ldg(a.lwe + e * L + x);
+        // a weight equal for every label shifts all of a cluster's exact sums
+        // alike and leaves its draw unchanged: such a bond adds nothing
+        // (Potts tables with one coupling per edge, every two-label table)
+        bool uniform = wv[0] != kSwNoLabel;
+#pragma unroll
+        for (int x = 1; x < L; ++x) uniform &= wv[x] == wv[0];
+        uint32_t flags = kSwBonded;
+        if (!uniform) {
+            flags |= kSwRow;
+#pragma unroll
+            for (int x = 0; x < L; ++x) {
+                if (wv[x] == kSwNoLabel) flags |= 1u << x;
+                else red_add_s64(a.lw + ((int64_t)s * L + x) * a.C + c, wv[x]);
+            }
         }
-        if (ban) atomicOr(a.ban + pidx(s, c, a.C), ban);
+        atomicOr(a.ban + pidx(s, c, a.C), flags);
+        atomicOr(a.ban + pidx(d, c, a.C), kSwBonded);
     }
 }
 
-// Roots are final once k_sw_bond has finished: a site's row (its unaries and
-// the weights of bonds it is the source of) moves into its root's row.  Only
-// roots' rows are written here and only non-roots' rows are read.
+// Bonded sites only (a site without a bond is its own cluster).  The forest
+// is final once k_sw_bond has finished: every bonded site records its root
+// (the smallest site of its cluster), and a non-root adds its unaries and the
+// weights of the bonds it is the source of into its root's row.  Only roots'
+// rows and ban words are written here, and only non-roots' are read.
+template <int L>
 __global__ void __launch_bounds__(256) k_sw_flatten(SwArgs a) {
     const int64_t n = (int64_t)a.N * a.C;
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t b = a.ban[g];
+        if (!(b & kSwBonded)) continue;
         const int32_t v = (int32_t)a.fdC.div((uint32_t)g), c = (int32_t)(g - (int64_t)v * a.C);
-        const int32_t r = sw_find<false>(a.parent, v, c, a.C, a.N);
+        const int32_t r = sw_find(a.parent, v, c, a.C, a.N);
         if (r < 0) { atomicOr(a.err, 1u); continue; }
+        a.root[g] = r;
         if (r == v) continue;
-        a.parent[g] = r;
-        for (int x = 0; x < a.L; ++x)
-            red_add_s64(a.lw + ((int64_t)r * a.L + x) * a.C + c, a.lw[((int64_t)v * a.L + x) * a.C + c]);
-        const uint32_t ban = a.ban[g];
-        if (ban) atomicOr(a.ban + pidx(r, c, a.C), ban);
+        int64_t w[L];
+#pragma unroll
+        for (int x = 0; x < L; ++x) w[x] = __ldg(a.ufix + (int64_t)v * L + x);
+        if (b & kSwRow) {
+            const int64_t* row = a.lw + (int64_t)v * L * a.C + c;
+#pragma unroll
+            for (int x = 0; x < L; ++x) w[x] += row[(int64_t)x * a.C];
+        }
+#pragma unroll
+        for (int x = 0; x < L; ++x) red_add_s64(a.lw + ((int64_t)r * L + x) * a.C + c, w[x]);
+        if (b & kSwLabelMask) atomicOr(a.ban + pidx(r, c, a.C), b & kSwLabelMask);
     }
 }
 
 // Label of every cluster, drawn at its root r by the inverse CDF with the
-// uniform of Philox(r, t, c, CLUSTER).  Differences to the largest weight are
-// exact in fixed point and then rounded to float for the softmax.
+// uniform of Philox(r, t, c, CLUSTER): weights are the root's unaries plus its
+// row (bonded sites), the differences to the largest are exact in fixed point
+// and then rounded to float for the softmax.  Nothing but the label is written
+// here: a store right behind the loads of the same row stalled the kernel
+// several-fold, so k_sw_assign clears rows and ban words.
 template <int L>
 __global__ void __launch_bounds__(256) k_sw_draw(SwArgs a) {
     const int64_t n = (int64_t)a.N * a.C;
@@ -140,32 +179,51 @@ __global__ void __launch_bounds__(256) k_sw_draw(SwArgs a) {
     uint8_t* __restrict__ xout = a.x + (size_t)((t + 1) & 1) * a.N * a.C;
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = (int32_t)a.fdC.div((uint32_t)g), c = (int32_t)(g - (int64_t)v * a.C);
-        if (a.parent[g] != v) continue;
-        const uint32_t ban = a.ban[g];
+        const uint32_t b = a.ban[g];
+        const bool bonded = (b & kSwBonded) != 0u;
+        if (bonded && a.root[g] != v) continue;            // labelled by k_sw_assign
         int64_t w[L];
+#pragma unroll
+        for (int x = 0; x < L; ++x) w[x] = __ldg(a.ufix + (int64_t)v * L + x);
+        if (bonded) {
+            const int64_t* row = a.lw + (int64_t)v * L * a.C + c;
+#pragma unroll
+            for (int x = 0; x < L; ++x) w[x] += row[(int64_t)x * a.C];
+        }
         int64_t mx = 0;
         bool any = false;
 #pragma unroll
-        for (int x = 0; x < L; ++x) {
-            w[x] = a.lw[((int64_t)v * L + x) * a.C + c];
-            if (!((ban >> x) & 1u) && (!any || w[x] > mx)) { mx = w[x]; any = true; }
-        }
+        for (int x = 0; x < L; ++x)
+            if (!((b >> x) & 1u) && (!any || w[x] > mx)) { mx = w[x]; any = true; }
         float F[L];
 #pragma unroll
         for (int x = 0; x < L; ++x)
-            F[x] = ((ban >> x) & 1u) ? -INFINITY : (float)(w[x] - mx) * (float)(1.0 / kSwFixScale);
+            F[x] = ((b >> x) & 1u) ? -INFINITY : sw_float(w[x] - mx);
         xout[g] = (uint8_t)draw_label<L>(F, (uint32_t)v, (uint32_t)c, (uint32_t)t, a.rk, PH_CLUSTER, nullptr, a.ctl);
     }
 }
 
+// Bonded sites return to the between-sweeps state: non-roots copy their
+// root's label; a root's row (its cluster's sums) and a bond source's row are
+// cleared; parent and ban words are reset.
+template <int L>
 __global__ void __launch_bounds__(256) k_sw_assign(SwArgs a) {
     const int64_t n = (int64_t)a.N * a.C;
     const unsigned long long t = a.ctl->sweep;
     uint8_t* __restrict__ xout = a.x + (size_t)((t + 1) & 1) * a.N * a.C;
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t b = a.ban[g];
+        if (!(b & kSwBonded)) continue;
         const int32_t v = (int32_t)a.fdC.div((uint32_t)g), c = (int32_t)(g - (int64_t)v * a.C);
-        const int32_t r = a.parent[g];
+        const int32_t r = a.root[g];
         if (r != v) xout[g] = xout[pidx(r, c, a.C)];
+        if (r == v || (b & kSwRow)) {
+            int64_t* row = a.lw + (int64_t)v * L * a.C + c;
+#pragma unroll
+            for (int x = 0; x < L; ++x) row[(int64_t)x * a.C] = 0;
+        }
+        a.parent[g] = v;
+        a.ban[g] = 0u;
     }
 }
 
@@ -231,21 +289,38 @@ cudaError_t launch_sw_check(const int32_t* src, const float* tau, int64_t E, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_sw_init(const SwArgs& a, cudaStream_t s) {
+// Fixed-point unaries ufix[v][x] = sw_fix(u_v(x)) (once per factor change).
+__global__ void k_sw_fix_unary(const float* unary, const double* unary_d, int64_t n, int64_t* ufix) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        ufix[i] = sw_fix(unary_d ? unary_d[i] : (double)unary[i]);
+}
+
+cudaError_t launch_sw_fix_unary(const float* unary, const double* unary_d, int64_t n, int64_t* ufix, cudaStream_t s) {
+    if (n > 0) k_sw_fix_unary<<<sw_blocks(n), 256, 0, s>>>(unary, unary_d, n, ufix);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sw_reset(const SwArgs& a, cudaStream_t s) {
     const int64_t n = (int64_t)a.N * a.C;
-    if (n > 0) k_sw_init<<<sw_blocks(n), 256, 0, s>>>(a);
+    if (n > 0) {
+        k_sw_reset<<<sw_blocks(n), 256, 0, s>>>(a);
+        const cudaError_t e = cudaMemsetAsync(a.lw, 0, (size_t)n * a.L * sizeof(int64_t), s);
+        if (e != cudaSuccess) return e;
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_sw_bond(const SwArgs& a, cudaStream_t s) {
     const int64_t n = a.E * a.C;
-    if (n > 0) k_sw_bond<<<sw_blocks(n), 256, 0, s>>>(a);
+    if (n <= 0) return cudaSuccess;
+    MRF_DISPATCH_LSW(a.L, (k_sw_bond<LL><<<sw_blocks(n), 256, 0, s>>>(a)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_sw_flatten(const SwArgs& a, cudaStream_t s) {
     const int64_t n = (int64_t)a.N * a.C;
-    if (n > 0) k_sw_flatten<<<sw_blocks(n), 256, 0, s>>>(a);
+    if (n <= 0) return cudaSuccess;
+    MRF_DISPATCH_LSW(a.L, (k_sw_flatten<LL><<<sw_blocks(n), 256, 0, s>>>(a)));
     return cudaGetLastError();
 }
 
@@ -253,7 +328,7 @@ cudaError_t launch_sw_draw(const SwArgs& a, cudaStream_t s) {
     const int64_t n = (int64_t)a.N * a.C;
     if (n <= 0) return cudaSuccess;
     MRF_DISPATCH_LSW(a.L, (k_sw_draw<LL><<<sw_blocks(n), 256, 0, s>>>(a)));
-    k_sw_assign<<<sw_blocks(n), 256, 0, s>>>(a);
+    MRF_DISPATCH_LSW(a.L, (k_sw_assign<LL><<<sw_blocks(n), 256, 0, s>>>(a)));
     return cudaGetLastError();
 }
 

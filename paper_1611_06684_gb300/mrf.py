@@ -23,10 +23,10 @@ MRF_PTR_HOST, MRF_PTR_DEVICE = 0, 1
 MODE_PLAIN, MODE_FUSED, MODE_SPLASH, MODE_LEARNED, MODE_SW = 0, 1, 2, 3, 4
 LAYOUT_PIVOT, LAYOUT_DIAG = 0, 1
 (K_DUAL, K_PRIMAL, K_FUSED, K_POTENTIAL, K_FFBS, K_ACCUMULATE, K_FEATURES, K_MLP, K_MH, K_SMALL,
- K_SW_INIT, K_SW_BOND, K_SW_FLATTEN, K_SW_DRAW, K_COUNT) = range(15)
+ K_SW_BOND, K_SW_FLATTEN, K_SW_DRAW, K_COUNT) = range(14)
 KERNEL_NAMES = ["k_dual", "k_primal", "k_primal<fused>", "k_potential", "k_ffbs", "k_accumulate",
                 "k_learned_features", "k_mlp", "k_learned_mh", "k_sweep_small",
-                "k_sw_init", "k_sw_bond", "k_sw_flatten", "k_sw_draw"]
+                "k_sw_bond", "k_sw_flatten", "k_sw_draw"]
 
 
 class mrf_options(ct.Structure):
