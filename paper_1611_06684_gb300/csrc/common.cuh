@@ -149,6 +149,7 @@ struct SwArgs {
     uint8_t* x;                // [2][N][C] label double buffer
     int32_t* parent;           // [N][C] union-find forest, links to smaller sites only
     int32_t* root;             // [N][C] root of a bonded site (written by k_sw_flatten)
+    uint32_t* bits;            // [ceil(E C / 32)] bond bitmap of the sweep, bit g of item g = e C + c
     uint32_t* ban;             // [N][C] labels a cluster may not take (bit per label)
     int64_t* lw;               // [N][L][C] fixed-point bond weights, then cluster weights at roots
     unsigned* err;             // set when a union-find walk exceeded its step bound

@@ -64,6 +64,8 @@ struct mrf {
     double* d_swut = nullptr;          // [N][L] two-label unaries with the offsets folded in
     int32_t* d_swpar = nullptr;        // [N][C] union-find parents
     int32_t* d_swroot = nullptr;       // [N][C] roots of bonded sites
+    uint32_t* d_swbits = nullptr;      // bond bitmap, one bit per (edge slot, chain)
+    int64_t swbits_cap = 0;            // words of d_swbits
     uint32_t* d_swban = nullptr;       // [N][C] excluded labels of a cluster
     int64_t* d_swlw = nullptr;         // [N][L][C] fixed-point cluster log weights
     unsigned* d_swerr = nullptr;       // union-find step bound exceeded
@@ -385,7 +387,7 @@ void mrf_destroy(mrf_t* h) {
     dfree(h->d_unary); dfree(h->d_ut); dfree(h->d_utf); dfree(h->d_tpl); dfree(h->d_src); dfree(h->d_dst); dfree(h->d_tau); dfree(h->d_thr);
     dfree(h->d_fold); dfree(h->d_cst); dfree(h->d_resid); dfree(h->d_inc_ptr); dfree(h->d_inc); dfree(h->d_x);
     dfree(h->d_theta); dfree(h->d_ties); dfree(h->d_tie_count); dfree(h->d_counts); dfree(h->d_lpv); dfree(h->d_logv); dfree(h->d_em); dfree(h->d_mfq); dfree(h->d_mfs); dfree(h->d_logp); dfree(h->d_ctl); dfree(h->d_flag); dfree(h->d_stage); dfree(h->d_pot);
-    dfree(h->d_swt); dfree(h->d_swl); dfree(h->d_swfold); dfree(h->d_swut); dfree(h->d_swpar); dfree(h->d_swroot); dfree(h->d_swban); dfree(h->d_swlw); dfree(h->d_swerr); dfree(h->d_swchk);
+    dfree(h->d_swt); dfree(h->d_swl); dfree(h->d_swfold); dfree(h->d_swut); dfree(h->d_swpar); dfree(h->d_swroot); dfree(h->d_swbits); dfree(h->d_swban); dfree(h->d_swlw); dfree(h->d_swerr); dfree(h->d_swchk);
     dfree(h->d_swufix);
     dfree(h->d_csr_work); dfree(h->d_csr_sums);
     dfree(h->d_ed_pair); dfree(h->d_ed_slots); dfree(h->d_ed_new); dfree(h->d_ed_s); dfree(h->d_ed_t);
@@ -678,7 +680,7 @@ static SwArgs make_sw_args(const mrf_t* h) {
     SwArgs w{};
     w.N = h->N; w.C = h->C; w.L = h->L; w.E = h->E_slots;
     w.src = h->d_src; w.dst = h->d_dst; w.thr = h->d_swt; w.lwe = h->d_swl; w.ufix = h->d_swufix;
-    w.x = h->d_x; w.parent = h->d_swpar; w.root = h->d_swroot; w.ban = h->d_swban; w.lw = h->d_swlw; w.err = h->d_swerr;
+    w.x = h->d_x; w.parent = h->d_swpar; w.root = h->d_swroot; w.bits = h->d_swbits; w.ban = h->d_swban; w.lw = h->d_swlw; w.err = h->d_swerr;
     w.ctl = h->d_ctl; w.rk = round_keys(h->key); w.fdC = FastDiv::make((uint32_t)h->C);
     return w;
 }
@@ -705,6 +707,12 @@ static mrf_status sw_prepare(mrf_t* h) {
         if (!h->d_swufix) { drop_graphs(h); MRF_CUDA(h, dalloc(h->d_swufix, (size_t)h->N * h->L)); }
         MRF_CUDA(h, launch_sw_fix_unary(h->d_unary, h->d_swut, (int64_t)h->N * h->L, h->d_swufix, h->stream));
         h->sw_checked = true;
+    }
+    const int64_t words = (h->E_slots * h->C + 31) / 32;       // edge slots grow with edits
+    if (words > h->swbits_cap) {
+        drop_graphs(h);
+        MRF_CUDA(h, dalloc(h->d_swbits, (size_t)std::max<int64_t>(words, 1)));
+        h->swbits_cap = words;
     }
     if (!h->d_swpar) {
         drop_graphs(h);

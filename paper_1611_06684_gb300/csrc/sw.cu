@@ -11,9 +11,11 @@
 // sweeps every site is its own tree (parent[v][c] = v), its ban word is 0 and
 // its weight row lw[v][.][c] is 0; a sweep touches only what its bonds reach
 // and restores that state:
-//   k_sw_bond     bond draws; a bond unions its endpoints' trees, adds its
-//                 label weights to its source site's row and marks both
-//                 endpoints bonded
+//   k_sw_bond     bond draws into a bitmap (one ballot word per warp)
+//   k_sw_union    a thread per bitmap word: each bond unions its endpoints'
+//                 trees, adds its label weights to its source site's row and
+//                 marks both endpoints bonded (dense work: the sparse bonds no
+//                 longer hold whole warps of non-bonded lanes)
 //   k_sw_flatten  every bonded site records its root (the smallest site of its
 //                 cluster) and adds its unaries and row into the root's row
 //   k_sw_draw     every root (bonded or not) draws its cluster's label from
@@ -93,46 +95,75 @@ __global__ void __launch_bounds__(256) k_sw_reset(SwArgs a) {
     }
 }
 
-template <int L>
+// Bond draws, one item per (edge, chain), items g = e C + c.  A warp's 32
+// lanes hold 32 consecutive items (the grid stride is a multiple of 32), so
+// its bonds form one 32-bit word of the bond bitmap, bits[g / 32], written by
+// one lane; every word is written every sweep.
 __global__ void __launch_bounds__(256) k_sw_bond(SwArgs a) {
     const int64_t n = a.E * a.C;
     const unsigned long long t = a.ctl->sweep;
     const uint8_t* __restrict__ xin = a.x + (size_t)(t & 1) * a.N * a.C;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = a.fdC.div((uint32_t)g);
-        const int32_t c = (int32_t)(g - e * a.C);
-        const int32_t s = a.src[e];
-        if (s < 0) continue;
-        const int32_t d = a.dst[e];
-        const int xs = xin[pidx(s, c, a.C)];
-        if (xs != xin[pidx(d, c, a.C)]) continue;
-        const uint32_t T = a.thr[e * L + xs];
-        if (T == 0u) continue;
-        const uint32_t U = draw_rk((uint32_t)e, (uint32_t)t, (uint32_t)c, PH_BOND, 0, a.rk).x >> 9;
-        if (U >= T) continue;
-        if (!sw_union(a.parent, s, d, c, a.C, a.N)) { atomicOr(a.err, 1u); continue; }
-        // every load before the first atomic (the compiler cannot move a load
-        // above an atomic to a possibly aliasing address)
-        int64_t wv[L];
-#pragma unroll
-        for (int x = 0; x < L; ++x) wv[x] = __ldg(a.lwe + e * L + x);
-        // a weight equal for every label shifts all of a cluster's exact sums
-        // alike and leaves its draw unchanged: such a bond adds nothing
-        // (Potts tables with one coupling per edge, every two-label table)
-        bool uniform = wv[0] != kSwNoLabel;
-#pragma unroll
-        for (int x = 1; x < L; ++x) uniform &= wv[x] == wv[0];
-        uint32_t flags = kSwBonded;
-        if (!uniform) {
-            flags |= kSwRow;
-#pragma unroll
-            for (int x = 0; x < L; ++x) {
-                if (wv[x] == kSwNoLabel) flags |= 1u << x;
-                else red_add_s64(a.lw + ((int64_t)s * L + x) * a.C + c, wv[x]);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g - lane < n; g += stride) {
+        bool bond = false;
+        if (g < n) {
+            const int64_t e = a.fdC.div((uint32_t)g);
+            const int32_t c = (int32_t)(g - e * a.C);
+            const int32_t s = a.src[e];
+            if (s >= 0) {
+                const int xs = xin[pidx(s, c, a.C)];
+                if (xs == xin[pidx(a.dst[e], c, a.C)]) {
+                    const uint32_t T = a.thr[e * a.L + xs];
+                    bond = T != 0u && (draw_rk((uint32_t)e, (uint32_t)t, (uint32_t)c, PH_BOND, 0, a.rk).x >> 9) < T;
+                }
             }
         }
-        atomicOr(a.ban + pidx(s, c, a.C), flags);
-        atomicOr(a.ban + pidx(d, c, a.C), kSwBonded);
+        const uint32_t word = __ballot_sync(0xffffffffu, bond);
+        if (lane == 0) a.bits[(g - lane) >> 5] = word;
+    }
+}
+
+// Unions of the bonds: one bitmap word per thread, its set bits in order.
+// Each bond links its endpoints' trees, adds its label weights to its source
+// site's row unless they are equal for every label (then they would shift all
+// of a cluster's exact sums alike and leave its draw unchanged: Potts tables
+// with one coupling per edge, every two-label table), and marks both
+// endpoints bonded.
+template <int L>
+__global__ void __launch_bounds__(256) k_sw_union(SwArgs a) {
+    const int64_t n = a.E * a.C;
+    const int64_t words = (n + 31) >> 5;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t word = a.bits[i];
+        while (word) {
+            const int bit = __ffs(word) - 1;
+            word &= word - 1u;
+            const int64_t g = i * 32 + bit;
+            const int64_t e = a.fdC.div((uint32_t)g);
+            const int32_t c = (int32_t)(g - e * a.C);
+            const int32_t s = a.src[e], d = a.dst[e];
+            if (!sw_union(a.parent, s, d, c, a.C, a.N)) { atomicOr(a.err, 1u); continue; }
+            // every load before the first atomic (the compiler cannot move a
+            // load above an atomic to a possibly aliasing address)
+            int64_t wv[L];
+#pragma unroll
+            for (int x = 0; x < L; ++x) wv[x] = __ldg(a.lwe + e * L + x);
+            bool uniform = wv[0] != kSwNoLabel;
+#pragma unroll
+            for (int x = 1; x < L; ++x) uniform &= wv[x] == wv[0];
+            uint32_t flags = kSwBonded;
+            if (!uniform) {
+                flags |= kSwRow;
+#pragma unroll
+                for (int x = 0; x < L; ++x) {
+                    if (wv[x] == kSwNoLabel) flags |= 1u << x;
+                    else red_add_s64(a.lw + ((int64_t)s * L + x) * a.C + c, wv[x]);
+                }
+            }
+            atomicOr(a.ban + pidx(s, c, a.C), flags);
+            atomicOr(a.ban + pidx(d, c, a.C), kSwBonded);
+        }
     }
 }
 
@@ -313,7 +344,8 @@ cudaError_t launch_sw_reset(const SwArgs& a, cudaStream_t s) {
 cudaError_t launch_sw_bond(const SwArgs& a, cudaStream_t s) {
     const int64_t n = a.E * a.C;
     if (n <= 0) return cudaSuccess;
-    MRF_DISPATCH_LSW(a.L, (k_sw_bond<LL><<<sw_blocks(n), 256, 0, s>>>(a)));
+    k_sw_bond<<<sw_blocks(n), 256, 0, s>>>(a);
+    MRF_DISPATCH_LSW(a.L, (k_sw_union<LL><<<sw_blocks((n + 31) / 32), 256, 0, s>>>(a)));
     return cudaGetLastError();
 }
 
