@@ -25,11 +25,17 @@ Draws: bond of edge e, chain c, sweep t: u from word 0 of Philox(e, t, c,
 BOND) (23-bit form), bond = [u < p]; label of cluster K: inverse CDF with u
 from word 0 of Philox(r, t, c, CLUSTER), r = the smallest site of K.
 
+log_v: Section 5.2's estimator log V = log p~(x) - log p(x | theta) on this
+duality, for the labels a sweep draws given its bonds.
+
 Pins (tests/test_oracle_sw.py): the decomposition reproduces every factor;
 p~(x, theta) marginalises to p~(x) (enumeration, diagonal Potts and two-label
 tables); the cluster label distribution equals p(x | theta) by enumeration;
 the SW kernel leaves p invariant (enumeration); chain marginals within 3 sigma
-of exact.
+of exact; log V: E[log V] = log Z - I(x; theta) under the joint and
+E[V] = Z (p(x) x p(theta))(support) (enumeration; the joint is not strictly
+positive here, so V is not unbiased, but E[log V] stays a lower bound on
+log Z), and C(theta) log 2 + log p~(x) for the Ising model without fields.
 """
 from __future__ import annotations
 
@@ -92,6 +98,39 @@ def cluster_log_weights(u, ell, src, root, bonds_c):
     if sel.size:
         np.add.at(lw, root[src[sel]], lb[sel])
     return lw
+
+
+def log_ptilde(model, x):
+    """log p~(x) [C] of the model itself: sum u_v(x_v) + sum w_e(x_s, x_t) (Section 4)."""
+    x = np.asarray(x, np.int64)
+    u = np.asarray(model.unary, np.float64)
+    w = np.asarray(model.pair, np.float64)
+    lp = u[np.arange(model.n_vars)[None, :], x].sum(axis=1)
+    if w.shape[0]:
+        lp += w[np.arange(w.shape[0])[None, :], x[:, model.src], x[:, model.dst]].sum(axis=1)
+    return lp
+
+
+def log_v(model, x, bonds, tables=None):
+    """Section 5.2's estimator on the Swendsen-Wang duality, per chain:
+    log V = log p~(x) + log p~(theta) - log p~(x, theta) = log p~(x) - log p(x | theta),
+    p(x | theta) the product over clusters of the probability of the cluster's
+    label (zero where x is not constant on a cluster: log V = +inf).  For the
+    Ising model without fields every cluster label has probability 1/2, so
+    log V = C(theta) log 2 + log p~(x) (the example of Section 5.2)."""
+    ell, u = sw_tables(model) if tables is None else tables
+    src, dst = np.asarray(model.src, np.int64), np.asarray(model.dst, np.int64)
+    x = np.asarray(x, np.int64)
+    out = log_ptilde(model, x)
+    for c in range(x.shape[0]):
+        root = clusters(model.n_vars, src, dst, bonds[c])
+        rs = np.unique(root)
+        if np.any(x[c] != x[c][root]):
+            out[c] = np.inf
+            continue
+        lw = cluster_log_weights(u, ell, src, root, bonds[c])
+        out[c] -= log_softmax(lw[rs])[np.arange(rs.size), x[c][rs]].sum()
+    return out
 
 
 def sw_sweep(model, x, sweep_index: int, seed: int, edge_ids=None, chain_ids=None, tables=None):

@@ -137,3 +137,48 @@ def test_sw_tables_reject_other_models():
     m.pair[0, 0, 1] += 10.0
     with pytest.raises(ValueError):
         sw.sw_tables(m)                                                  # w00 + w11 < w01 + w10
+
+
+@pytest.mark.parametrize("name", ["potts_L3_s1", "two_labels_s3"])
+def test_log_v_mean_is_log_z_minus_mutual_information(name):
+    """Section 5.2 on the SW duality, by enumeration of (x, theta) under the joint.
+    log V = log Z + log p(x) p(theta) / p(x, theta), so E[log V] = log Z - I(x; theta)
+    exactly.  The joint is zero wherever a bond joins unequal labels, so
+    E[V] = Z (p(x) x p(theta))(support) < Z: V is not unbiased on this
+    degenerate duality, but E[log V] <= log E[V] < log Z keeps the lower bound."""
+    model = MODELS[name]()
+    X = brute.all_labelings(model.n_vars, model.n_labels)
+    B = brute.all_dual_configs(model.src.size).astype(bool)
+    J = _joint_log(model, X, B)                                         # up to the dropped constants
+    logZ = np.logaddexp.reduce(brute.log_ptilde(model, X))
+    P = np.exp(J - np.logaddexp.reduce(J.ravel()))
+    tables = sw.sw_tables(model)
+    lv = np.full(J.shape, np.nan)
+    for bi in range(B.shape[0]):
+        ok = np.isfinite(J[:, bi])
+        if ok.any():
+            lv[ok, bi] = sw.log_v(model, X[ok], np.repeat(B[bi][None], ok.sum(), 0), tables)
+    m = P > 0
+    assert np.all(np.isfinite(lv[m]))
+    px, pt = P.sum(axis=1), P.sum(axis=0)
+    # E[V] = Z times the product measure of the support
+    mass = np.outer(px, pt)[m].sum()
+    np.testing.assert_allclose(np.logaddexp.reduce(np.log(P[m]) + lv[m]), logZ + np.log(mass), atol=1e-10)
+    assert mass < 1.0
+    # log Z - E[log V] = I(x; theta) = sum p log p(x,theta) / (p(x) p(theta))
+    mi = (P[m] * (np.log(P[m]) - np.log(np.outer(px, pt)[m]))).sum()
+    np.testing.assert_allclose(logZ - (P[m] * lv[m]).sum(), mi, atol=1e-10)
+    assert mi > 0
+
+
+def test_log_v_of_the_ising_model_without_fields_counts_clusters():
+    """Example of Section 5.2: log V = C(theta) log 2 + log p~(x)."""
+    m = wl.ising_grid(4, 5, h_std=0.0, j_lo=0.2, j_hi=0.9, seed=7)
+    C, seed = 64, 3
+    x = ph.init_labels(m.n_vars, 2, C, seed)
+    for t in range(4):
+        res = sw.sw_sweep(m, x, t, seed)
+        x = res["x"]
+        n_clusters = np.array([np.unique(r).size for r in res["roots"]])
+        np.testing.assert_allclose(sw.log_v(m, x, res["bonds"]), n_clusters * np.log(2.0) + sw.log_ptilde(m, x),
+                                   rtol=0, atol=1e-10)
