@@ -199,10 +199,15 @@ def run_ours(args, ws, rank, local):
         from paper_1611_06684_gb300 import workloads as wl
         model = wl.potts_grid3d(args.scale, L=8, seed=0)
         desc = desc.replace("128^3", f"{args.scale}^3")
+    elif args.scale and args.workload == "ferro3d":
+        from paper_1611_06684_gb300 import workloads as wl
+        model = wl.ferro_potts_grid3d(args.scale, L=8, beta_lo=FERRO_BETA[0], beta_hi=FERRO_BETA[1],
+                                      u_std=FERRO_U_STD, seed=0)
+        desc = desc.replace("128^3", f"{args.scale}^3")
     else:
         model = gen()
     if "%g" in desc:
-        desc = _describe(args.workload)
+        desc = desc % (FERRO_BETA[0], FERRO_BETA[1], FERRO_U_STD)
     mode = {"plain": M.MODE_PLAIN, "fused": M.MODE_FUSED, "sw": M.MODE_SW}[args.mode]
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
@@ -236,7 +241,7 @@ def run_ours(args, ws, rank, local):
     # a timed dual step is two kernels (k_dual, k_dual_ties); + k_advance per sweep
     # (a small model runs all its sweeps in one k_sweep_small launch, which advances itself)
     launches = sum(n * KERNELS_PER_RECORD.get(k, 1) for k, (_, n) in ktimes.items())
-    if "k_sweep_small" not in ktimes:
+    if "k_sweep_small" not in ktimes and "k_sw_small" not in ktimes:
         launches += args.steps
 
     # roofline of the dominant kernel (device time inside the timed region)
@@ -247,6 +252,9 @@ def run_ours(args, ws, rank, local):
         cd, bd = kernel_work("k_dual", minfo, C)
         cp, bp = kernel_work("k_primal", minfo, C)
         calls, nbytes = (cd + cp) * args.steps, (bd + bp) * args.steps
+    elif dom == "k_sw_small":
+        calls = 0
+        nbytes = (kernel_work("k_sw_bond", minfo, C)[1] + kernel_work("k_sw_draw", minfo, C)[1]) * args.steps
     else:
         calls, nbytes = kernel_work(dom, minfo, C)
     sm_mhz = clocks["sm_mhz"] if clocks else peaks.get("sm_max_mhz", 2070.0)
@@ -274,10 +282,15 @@ def run_ours(args, ws, rank, local):
     # other sweep forms on the same handle, timed separately (not part of the headline)
     variants = {}
     if not args.no_variants:
-        potts = inf.layout == M.LAYOUT_DIAG and bool((model.pair >= 0).all())
+        # the Swendsen-Wang form exists for two labels and Potts-type tables with l >= 0
+        try:
+            h.sweep(1, M.MODE_SW)
+            sw_ok = True
+        except M.MrfError:
+            sw_ok = False
         forms = [(n, md) for n, md in (("plain", M.MODE_PLAIN), ("fused", M.MODE_FUSED)) if n != args.mode] + \
             ([("splash", M.MODE_SPLASH)] if model.grid else []) + \
-            ([("sw", M.MODE_SW)] if potts and args.mode != "sw" else [])
+            ([("sw", M.MODE_SW)] if sw_ok and args.mode != "sw" else [])
         for name, md in forms:
             h.sweep(1, md)
             h.kernel_times()
@@ -309,7 +322,7 @@ def run_ours(args, ws, rank, local):
             ms_of.update({k: v["ms_per_step"] for k, v in variants.items() if "ms_per_step" in v})
             variants["ess"] = ess_comparison(h, model, C, stream, args.ess_sweeps, ms_of,
                                              [("plain", M.MODE_PLAIN)] + ([("splash", M.MODE_SPLASH)] if model.grid else [])
-                                             + ([("sw", M.MODE_SW)] if potts else []))
+                                             + ([("sw", M.MODE_SW)] if sw_ok else []))
 
     # end to end through the C ABI with pinned host buffers: labels in, sweep, labels out
     e2e = None
@@ -722,7 +735,7 @@ def main():
     ap.add_argument("--ess-sweeps", type=int, default=200)
     ap.add_argument("--mode", default="plain", choices=["plain", "fused", "sw"])
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--scale", type=int, default=0, help="lattice edge for potts3d (default 128)")
+    ap.add_argument("--scale", type=int, default=0, help="lattice edge for potts3d and ferro3d (default 128)")
     ap.add_argument("--ferro-beta", default=None, help="lo,hi of the ferro3d couplings (default %g,%g)" % FERRO_BETA)
     ap.add_argument("--ferro-u-std", type=float, default=None, help="unary std of ferro3d (default %g)" % FERRO_U_STD)
     ap.add_argument("--no-e2e", action="store_true")

@@ -158,7 +158,11 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
  * diagonal, or some l < 0; MRF_ERANGE when sum_v max_x |u_v(x)| + sum_e max_x
  * |log(e^{l_x} - 1)| reaches 2^30; MRF_ETIMEOUT if a union-find walk
  * exceeded its bound of n_vars steps (cannot happen for a consistent forest).
- * The call synchronises the stream at its end to read that flag.
+ * The call synchronises the stream at its end to read that flag.  As for
+ * plain sweeps, n_sweeps >= 2 sweeps of a small model (at most 2^16 site x
+ * chain and edge x chain items, union-find state within 200 KB) run in one
+ * single-CTA launch with the state in shared memory (the same chain, bit for
+ * bit).
  * mrf_debug_logp and the log-partition estimator do not cover this mode. */
 mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode);
 
@@ -198,7 +202,8 @@ enum { MRF_K_DUAL = 0, MRF_K_PRIMAL = 1, MRF_K_FUSED = 2, MRF_K_POTENTIAL = 3, M
        MRF_K_SMALL = 9,    /* whole plain sweeps of a small model in one launch (see mrf_sweep) */
        MRF_K_SW_BOND = 10, MRF_K_SW_FLATTEN = 11,
        MRF_K_SW_DRAW = 12, /* Swendsen-Wang: label draw of every cluster and the copy to its sites */
-       MRF_K_COUNT = 13 };
+       MRF_K_SW_SMALL = 13,/* whole Swendsen-Wang sweeps of a small model in one launch */
+       MRF_K_COUNT = 14 };
 /* With options.kernel_timing: total device milliseconds ms[MRF_K_COUNT] and
  * launch counts launches[MRF_K_COUNT] of every sweep kernel since the last
  * call (CUDA events on the handle's stream); resets the totals.  Synchronises. */
@@ -220,6 +225,17 @@ mrf_status mrf_philox_rate(uint64_t threads, int32_t calls, void* cuda_stream, d
  * exact edge tables (options.grid or options.exact_edges), else MRF_ESTATE.
  * The sweeps advance the chains and the marginal counts like mrf_sweep. */
 mrf_status mrf_estimate_log_partition(mrf_t* h, int32_t n_sweeps, double* log_v);
+
+/* The same estimator on the Swendsen-Wang duality (Sections 4.3 and 5.2):
+ * n_sweeps MRF_MODE_SW sweeps, after each
+ *   log_v[i * C + c] = log p~(x) - sum_clusters log p(x_cluster | theta),
+ * which for the Ising model without fields is C(theta) log 2 + log p~(x)
+ * (C = number of clusters).  The joint of x and the bonds is zero wherever a
+ * bond joins unequal labels, so here E[V] = Z (p(x) p(theta))(support) < Z:
+ * exp(log_v) is biased low, while E[log V] = log Z - I(x; theta) remains a
+ * lower bound on log Z.  Same requirements as MRF_MODE_SW and
+ * mrf_estimate_log_partition. */
+mrf_status mrf_estimate_log_partition_sw(mrf_t* h, int32_t n_sweeps, double* log_v);
 
 /* Primal-dual EM (local MAP, Section 5.3): n_iters iterations of
  *   xi = E[r(theta) | x]  (pi_k = sigmoid(q_k + beta1_k [x_s = i_k] + beta2_k [x_t = j_k]))

@@ -133,6 +133,38 @@ def log_v(model, x, bonds, tables=None):
     return out
 
 
+def exact_moments(model):
+    """(E[log V], log Z, I(x; theta)) under the joint of the labels and the bonds,
+    by enumerating every (x, theta) (tiny models): the joint is
+    p~(x, theta) = exp(sum u_v(x_v) + sum over bonds log(e^{l_{x_s}} - 1)) where
+    every bond joins equal labels, else 0 (the tables' split constants dropped)."""
+    from .brute import all_labelings, all_dual_configs
+    ell, u = sw_tables(model)
+    src, dst = np.asarray(model.src, np.int64), np.asarray(model.dst, np.int64)
+    X = all_labelings(model.n_vars, model.n_labels)
+    B = all_dual_configs(src.size).astype(bool)
+    lu = u[np.arange(model.n_vars)[None, :], X].sum(axis=1)
+    xs, xt = X[:, src], X[:, dst]
+    with np.errstate(divide="ignore"):
+        lb = np.where(xs == xt, np.log(np.expm1(ell[np.arange(src.size)[None, :], xs])), -np.inf)   # [S_x][E]
+    J = np.full((X.shape[0], B.shape[0]), -np.inf)
+    for bi in range(B.shape[0]):
+        sel = B[bi]
+        J[:, bi] = lu + (lb[:, sel].sum(axis=1) if sel.any() else 0.0)
+    logZ = np.logaddexp.reduce(log_ptilde(model, X))
+    P = np.exp(J - np.logaddexp.reduce(J.ravel()))
+    m = P > 0
+    lv = np.zeros(J.shape)
+    for bi in range(B.shape[0]):
+        ok = m[:, bi]
+        if ok.any():
+            lv[ok, bi] = log_v(model, X[ok], np.repeat(B[bi][None], ok.sum(), 0), (ell, u))
+    e_logv = float((P[m] * lv[m]).sum())
+    px, pt = P.sum(axis=1), P.sum(axis=0)
+    mi = float((P[m] * (np.log(P[m]) - np.log(np.outer(px, pt)[m]))).sum())
+    return e_logv, float(logZ), mi
+
+
 def sw_sweep(model, x, sweep_index: int, seed: int, edge_ids=None, chain_ids=None, tables=None):
     """One Swendsen-Wang sweep from labels x [C][N].  edge_ids are the RNG
     indices of the edges (default 0..E-1), chain_ids those of the rows of x

@@ -153,6 +153,8 @@ struct SwArgs {
     uint32_t* ban;             // [N][C] labels a cluster may not take (bit per label)
     int64_t* lw;               // [N][L][C] fixed-point bond weights, then cluster weights at roots
     unsigned* err;             // set when a union-find walk exceeded its step bound
+    float* lpv;                // [N][C] log p of each root's drawn label, 0 at other sites (estimator) or null
+    uint32_t* counts;          // [N][L] marginal counts (k_sw_small accumulates them itself)
     Ctl* ctl;
     RoundKeys rk;
     FastDiv fdC;
@@ -245,6 +247,8 @@ cudaError_t launch_sw_reset(const SwArgs& a, cudaStream_t s);
 cudaError_t launch_sw_bond(const SwArgs& a, cudaStream_t s);
 cudaError_t launch_sw_flatten(const SwArgs& a, cudaStream_t s);
 cudaError_t launch_sw_draw(const SwArgs& a, cudaStream_t s);
+int64_t sw_small_smem(const SwArgs& a);
+cudaError_t launch_sw_small(const SwArgs& a, int n_sweeps, cudaStream_t s);
 cudaError_t launch_labels_to_abi(const uint8_t* x, uint8_t* y, int N, int C, cudaStream_t s);
 cudaError_t launch_labels_from_abi(const uint8_t* y, uint8_t* x, int N, int C, cudaStream_t s);
 cudaError_t launch_count_ge(const uint8_t* y, int64_t n, int L, unsigned long long* bad, cudaStream_t s);

@@ -682,6 +682,8 @@ static SwArgs make_sw_args(const mrf_t* h) {
     w.src = h->d_src; w.dst = h->d_dst; w.thr = h->d_swt; w.lwe = h->d_swl; w.ufix = h->d_swufix;
     w.x = h->d_x; w.parent = h->d_swpar; w.root = h->d_swroot; w.bits = h->d_swbits; w.ban = h->d_swban; w.lw = h->d_swlw; w.err = h->d_swerr;
     w.ctl = h->d_ctl; w.rk = round_keys(h->key); w.fdC = FastDiv::make((uint32_t)h->C);
+    w.lpv = h->lpv_on ? h->d_lpv : nullptr;
+    w.counts = h->d_counts;
     return w;
 }
 
@@ -721,6 +723,20 @@ static mrf_status sw_prepare(mrf_t* h) {
         MRF_CUDA(h, dalloc(h->d_swlw, NC * h->L)); MRF_CUDA(h, dalloc(h->d_swerr, 1));
         MRF_CUDA(h, cudaMemsetAsync(h->d_swerr, 0, sizeof(unsigned), h->stream));
         MRF_CUDA(h, launch_sw_reset(make_sw_args(h), h->stream));
+    }
+    return MRF_OK;
+}
+
+// After Swendsen-Wang sweeps: a union-find walk that exceeded its step bound
+// left the between-sweeps state unrestored; it is reset and reported.
+static mrf_status sw_check_error(mrf_t* h) {
+    unsigned err = 0;
+    MRF_CUDA(h, cudaMemcpyAsync(&err, h->d_swerr, sizeof(err), cudaMemcpyDeviceToHost, h->stream));
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (err) {
+        MRF_CUDA(h, cudaMemsetAsync(h->d_swerr, 0, sizeof(unsigned), h->stream));
+        MRF_CUDA(h, launch_sw_reset(make_sw_args(h), h->stream));
+        return fail(h, MRF_ETIMEOUT, "Swendsen-Wang: a union-find walk exceeded its step bound");
     }
     return MRF_OK;
 }
@@ -769,6 +785,14 @@ mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode) {
     if (mode == MRF_MODE_SW) {
         mrf_status st = sw_prepare(h);
         if (st != MRF_OK) return st;
+        // small models: all the sweeps in one single-CTA launch, state in shared memory
+        const SwArgs w = make_sw_args(h);
+        if (n_sweeps >= 2 && (int64_t)h->N * h->C <= 65536 && h->E_slots * h->C <= 65536 &&
+            sw_small_smem(w) <= 200 * 1024) {
+            MRF_CUDA(h, timed(h, MRF_K_SW_SMALL, [&] { return launch_sw_small(w, n_sweeps, h->stream); }));
+            h->sweep_host += n_sweeps;
+            return sw_check_error(h);
+        }
     }
     if (mode == MRF_MODE_LEARNED && !h->learned) return fail(h, MRF_ESTATE, "learned mode needs mrf_learned_setup");
     if (mode == MRF_MODE_LEARNED && h->rowbias_dirty) {      // per-block first-layer bias of the current weights
@@ -812,15 +836,9 @@ mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode) {
         }
     }
     h->sweep_host += n_sweeps;
-    if (mode == MRF_MODE_SW && n_sweeps > 0) {             // a union-find walk exceeded its step bound
-        unsigned err = 0;
-        MRF_CUDA(h, cudaMemcpyAsync(&err, h->d_swerr, sizeof(err), cudaMemcpyDeviceToHost, h->stream));
-        MRF_CUDA(h, cudaStreamSynchronize(h->stream));
-        if (err) {                                          // the between-sweeps state is not restored
-            MRF_CUDA(h, cudaMemsetAsync(h->d_swerr, 0, sizeof(unsigned), h->stream));
-            MRF_CUDA(h, launch_sw_reset(make_sw_args(h), h->stream));
-            return fail(h, MRF_ETIMEOUT, "Swendsen-Wang: a union-find walk exceeded its step bound");
-        }
+    if (mode == MRF_MODE_SW && n_sweeps > 0) {
+        mrf_status st = sw_check_error(h);
+        if (st != MRF_OK) return st;
     }
     if (mode == MRF_MODE_LEARNED) {
         h->proposed += (uint64_t)n_sweeps * h->la.nb * h->C;
@@ -838,12 +856,15 @@ mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode) {
     return MRF_OK;
 }
 
-mrf_status mrf_estimate_log_partition(mrf_t* h, int32_t n_sweeps, double* log_v) {
+static mrf_status estimate_log_partition(mrf_t* h, int32_t n_sweeps, int mode, double* log_v) {
     if (!h || n_sweeps < 0 || (n_sweeps > 0 && !log_v)) return MRF_EINVAL;
     if (!h->has_factors) return fail(h, MRF_ESTATE, "mrf_set_factors first");
     if (!h->d_resid) return fail(h, MRF_ESTATE, "the estimator needs exact edge tables (options.grid or options.exact_edges)");
     if (n_sweeps == 0) return MRF_OK;
-    if (h->schedule == 0) {
+    if (mode == MRF_MODE_SW) {
+        mrf_status st = sw_prepare(h);
+        if (st != MRF_OK) return st;
+    } else if (h->schedule == 0) {
         mrf_status st = tune_schedule(h);
         if (st != MRF_OK) return st;
     }
@@ -856,7 +877,7 @@ mrf_status mrf_estimate_log_partition(mrf_t* h, int32_t n_sweeps, double* log_v)
     h->lpv_on = true;
     mrf_status st = MRF_OK;
     for (int i = 0; i < n_sweeps && st == MRF_OK; ++i) {
-        st = enqueue_sweep(h, MRF_MODE_PLAIN);                  // not from a graph: the launches carry lpv
+        st = enqueue_sweep(h, mode);                            // not from a graph: the launches carry lpv
         if (st == MRF_OK) {
             cudaError_t e = launch_log_v(make_args(h), h->d_ut, h->d_logv + (int64_t)i * h->C, h->stream);
             if (e != cudaSuccess) { cudaGetLastError(); st = fail(h, MRF_ECUDA, std::string("log V: ") + cudaGetErrorString(e)); }
@@ -868,7 +889,16 @@ mrf_status mrf_estimate_log_partition(mrf_t* h, int32_t n_sweeps, double* log_v)
     MRF_CUDA(h, cudaMemcpyAsync(log_v, h->d_logv, sizeof(double) * (size_t)n_sweeps * h->C, cudaMemcpyDeviceToHost,
                                 h->stream));
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (mode == MRF_MODE_SW) return sw_check_error(h);
     return MRF_OK;
+}
+
+mrf_status mrf_estimate_log_partition(mrf_t* h, int32_t n_sweeps, double* log_v) {
+    return estimate_log_partition(h, n_sweeps, MRF_MODE_PLAIN, log_v);
+}
+
+mrf_status mrf_estimate_log_partition_sw(mrf_t* h, int32_t n_sweeps, double* log_v) {
+    return estimate_log_partition(h, n_sweeps, MRF_MODE_SW, log_v);
 }
 
 mrf_status mrf_map_em(mrf_t* h, int32_t n_iters, uint8_t* labels, int32_t ptr_kind) {

@@ -212,7 +212,10 @@ __global__ void __launch_bounds__(256) k_sw_draw(SwArgs a) {
         const int32_t v = (int32_t)a.fdC.div((uint32_t)g), c = (int32_t)(g - (int64_t)v * a.C);
         const uint32_t b = a.ban[g];
         const bool bonded = (b & kSwBonded) != 0u;
-        if (bonded && a.root[g] != v) continue;            // labelled by k_sw_assign
+        if (bonded && a.root[g] != v) {                     // labelled by k_sw_assign
+            if (a.lpv) a.lpv[g] = 0.0f;
+            continue;
+        }
         int64_t w[L];
 #pragma unroll
         for (int x = 0; x < L; ++x) w[x] = __ldg(a.ufix + (int64_t)v * L + x);
@@ -230,13 +233,16 @@ __global__ void __launch_bounds__(256) k_sw_draw(SwArgs a) {
 #pragma unroll
         for (int x = 0; x < L; ++x)
             F[x] = ((b >> x) & 1u) ? -INFINITY : sw_float(w[x] - mx);
-        xout[g] = (uint8_t)draw_label<L>(F, (uint32_t)v, (uint32_t)c, (uint32_t)t, a.rk, PH_CLUSTER, nullptr, a.ctl);
+        xout[g] = (uint8_t)draw_label<L>(F, (uint32_t)v, (uint32_t)c, (uint32_t)t, a.rk, PH_CLUSTER, nullptr, a.ctl,
+                                         a.lpv ? a.lpv + g : nullptr);
     }
 }
 
 // Bonded sites return to the between-sweeps state: non-roots copy their
 // root's label; a root's row (its cluster's sums) and a bond source's row are
-// cleared; parent and ban words are reset.
+// cleared; parent and ban words are reset.  (Clearing whole 32-byte sectors
+// whenever any lane of a warp clears its entries wrote more than the merged
+// 8-byte writes cost: measured slower.)
 template <int L>
 __global__ void __launch_bounds__(256) k_sw_assign(SwArgs a) {
     const int64_t n = (int64_t)a.N * a.C;
@@ -256,6 +262,160 @@ __global__ void __launch_bounds__(256) k_sw_assign(SwArgs a) {
         a.parent[g] = v;
         a.ban[g] = 0u;
     }
+}
+
+// Small models: n_sweeps whole Swendsen-Wang sweeps in one launch of a single
+// 1024-thread CTA (launch latency dominates there), the union-find state in
+// shared memory: parent, root and ban words [N][C], weight rows [N][L][C].
+// The same draws, exact sums and rules as the kernels above, phases separated
+// by CTA barriers, hence the same chain bit for bit; marginal counts and the
+// sweep counter are advanced here too.
+__device__ __forceinline__ int32_t sws_find(volatile int32_t* par, int32_t v, int32_t c, int32_t C, int32_t N) {
+    for (int32_t step = 0; step <= N; ++step) {
+        const int32_t p = par[pidx(v, c, C)];
+        if (p == v) return v;
+        const int32_t gp = par[pidx(p, c, C)];
+        if (gp != p) par[pidx(v, c, C)] = gp;
+        v = gp;
+    }
+    return -1;
+}
+
+template <int L>
+__global__ void __launch_bounds__(1024) k_sw_small(SwArgs a, int n_sweeps) {
+    extern __shared__ int64_t s_lw[];                                  // [N][L][C]
+    const int64_t nv = (int64_t)a.N * a.C, ne = a.E * a.C;
+    int32_t* s_par = reinterpret_cast<int32_t*>(s_lw + nv * L);       // [N][C]
+    int32_t* s_root = s_par + nv;                                     // [N][C]
+    uint32_t* s_ban = reinterpret_cast<uint32_t*>(s_root + nv);       // [N][C]
+    volatile int32_t* vpar = s_par;
+    for (int64_t g = threadIdx.x; g < nv; g += blockDim.x) {
+        s_par[g] = (int32_t)a.fdC.div((uint32_t)g);
+        s_ban[g] = 0u;
+    }
+    for (int64_t i = threadIdx.x; i < nv * L; i += blockDim.x) s_lw[i] = 0;
+    __syncthreads();
+    uint32_t sweep = (uint32_t)a.ctl->sweep;
+    const unsigned long long count_from = a.ctl->count_from;
+    for (int it = 0; it < n_sweeps; ++it, ++sweep) {
+        const uint8_t* xin = a.x + (size_t)(sweep & 1) * a.N * a.C;
+        uint8_t* xout = a.x + (size_t)((sweep + 1) & 1) * a.N * a.C;
+        // bonds and unions
+        for (int64_t g = threadIdx.x; g < ne; g += blockDim.x) {
+            const int64_t e = a.fdC.div((uint32_t)g);
+            const int32_t c = (int32_t)(g - e * a.C);
+            const int32_t s = a.src[e];
+            if (s < 0) continue;
+            const int32_t d = a.dst[e];
+            const int xs = xin[pidx(s, c, a.C)];
+            if (xs != xin[pidx(d, c, a.C)]) continue;
+            const uint32_t T = a.thr[e * L + xs];
+            if (T == 0u || (draw_rk((uint32_t)e, sweep, (uint32_t)c, PH_BOND, 0, a.rk).x >> 9) >= T) continue;
+            int32_t ra = s, rb = d;
+            bool linked = false;
+            for (int32_t step = 0; step <= a.N && !linked; ++step) {
+                ra = sws_find(vpar, ra, c, a.C, a.N);
+                rb = sws_find(vpar, rb, c, a.C, a.N);
+                if (ra < 0 || rb < 0) break;
+                if (ra == rb) { linked = true; break; }
+                if (ra < rb) { const int32_t t2 = ra; ra = rb; rb = t2; }
+                linked = atomicCAS(s_par + pidx(ra, c, a.C), ra, rb) == ra;
+            }
+            if (!linked) { atomicOr(a.err, 1u); continue; }
+            int64_t wv[L];
+#pragma unroll
+            for (int x = 0; x < L; ++x) wv[x] = __ldg(a.lwe + e * L + x);
+            bool uniform = wv[0] != kSwNoLabel;
+#pragma unroll
+            for (int x = 1; x < L; ++x) uniform &= wv[x] == wv[0];
+            uint32_t flags = kSwBonded;
+            if (!uniform) {
+                flags |= kSwRow;
+#pragma unroll
+                for (int x = 0; x < L; ++x) {
+                    if (wv[x] == kSwNoLabel) flags |= 1u << x;
+                    else atomicAdd(reinterpret_cast<unsigned long long*>(s_lw + ((int64_t)s * L + x) * a.C + c),
+                                   (unsigned long long)wv[x]);
+                }
+            }
+            atomicOr(s_ban + pidx(s, c, a.C), flags);
+            atomicOr(s_ban + pidx(d, c, a.C), kSwBonded);
+        }
+        __syncthreads();
+        // roots and cluster sums
+        for (int64_t g = threadIdx.x; g < nv; g += blockDim.x) {
+            const uint32_t b = s_ban[g];
+            if (!(b & kSwBonded)) continue;
+            const int32_t v = (int32_t)a.fdC.div((uint32_t)g), c = (int32_t)(g - (int64_t)v * a.C);
+            const int32_t r = sws_find(vpar, v, c, a.C, a.N);
+            if (r < 0) { atomicOr(a.err, 1u); s_root[g] = v; continue; }
+            s_root[g] = r;
+            if (r == v) continue;
+#pragma unroll
+            for (int x = 0; x < L; ++x) {
+                int64_t w = __ldg(a.ufix + (int64_t)v * L + x);
+                if (b & kSwRow) w += s_lw[((int64_t)v * L + x) * a.C + c];
+                atomicAdd(reinterpret_cast<unsigned long long*>(s_lw + ((int64_t)r * L + x) * a.C + c),
+                          (unsigned long long)w);
+            }
+            if (b & kSwLabelMask) atomicOr(s_ban + pidx(r, c, a.C), b & kSwLabelMask);
+        }
+        __syncthreads();
+        // labels of the roots
+        for (int64_t g = threadIdx.x; g < nv; g += blockDim.x) {
+            const int32_t v = (int32_t)a.fdC.div((uint32_t)g), c = (int32_t)(g - (int64_t)v * a.C);
+            const uint32_t b = s_ban[g];
+            const bool bonded = (b & kSwBonded) != 0u;
+            if (bonded && s_root[g] != v) continue;
+            int64_t w[L];
+#pragma unroll
+            for (int x = 0; x < L; ++x) {
+                w[x] = __ldg(a.ufix + (int64_t)v * L + x);
+                if (bonded) w[x] += s_lw[((int64_t)v * L + x) * a.C + c];
+            }
+            int64_t mx = 0;
+            bool any = false;
+#pragma unroll
+            for (int x = 0; x < L; ++x)
+                if (!((b >> x) & 1u) && (!any || w[x] > mx)) { mx = w[x]; any = true; }
+            float F[L];
+#pragma unroll
+            for (int x = 0; x < L; ++x) F[x] = ((b >> x) & 1u) ? -INFINITY : sw_float(w[x] - mx);
+            xout[g] = (uint8_t)draw_label<L>(F, (uint32_t)v, (uint32_t)c, sweep, a.rk, PH_CLUSTER, nullptr, a.ctl);
+        }
+        __syncthreads();
+        // labels of the other sites, state reset
+        for (int64_t g = threadIdx.x; g < nv; g += blockDim.x) {
+            const uint32_t b = s_ban[g];
+            if (!(b & kSwBonded)) continue;
+            const int32_t v = (int32_t)a.fdC.div((uint32_t)g), c = (int32_t)(g - (int64_t)v * a.C);
+            const int32_t r = s_root[g];
+            if (r != v) xout[g] = xout[pidx(r, c, a.C)];
+            if (r == v || (b & kSwRow)) {
+#pragma unroll
+                for (int x = 0; x < L; ++x) s_lw[((int64_t)v * L + x) * a.C + c] = 0;
+            }
+            s_par[g] = v;
+            s_ban[g] = 0u;
+        }
+        __syncthreads();
+        if (sweep >= count_from) {
+            for (int64_t v = threadIdx.x; v < a.N; v += blockDim.x) {
+                uint32_t tot[L];
+#pragma unroll
+                for (int x = 0; x < L; ++x) tot[x] = 0;
+                for (int c = 0; c < a.C; ++c) {
+                    const int x = xout[v * a.C + c];
+#pragma unroll
+                    for (int y = 0; y < L; ++y) tot[y] += x == y ? 1u : 0u;
+                }
+#pragma unroll
+                for (int x = 0; x < L; ++x) a.counts[v * L + x] += tot[x];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a.ctl->sweep = sweep;
 }
 
 // Model check before the first Swendsen-Wang sweep after the factors change:
@@ -353,6 +513,22 @@ cudaError_t launch_sw_flatten(const SwArgs& a, cudaStream_t s) {
     const int64_t n = (int64_t)a.N * a.C;
     if (n <= 0) return cudaSuccess;
     MRF_DISPATCH_LSW(a.L, (k_sw_flatten<LL><<<sw_blocks(n), 256, 0, s>>>(a)));
+    return cudaGetLastError();
+}
+
+int64_t sw_small_smem(const SwArgs& a) { return (int64_t)a.N * a.C * (12 + 8 * a.L); }
+
+cudaError_t launch_sw_small(const SwArgs& a, int n_sweeps, cudaStream_t s) {
+    if (!a.counts || !a.ufix || !a.err || !a.ctl || !a.x || (a.E > 0 && (!a.src || !a.dst || !a.thr || !a.lwe)))
+        return cudaErrorInvalidValue;
+    const size_t smem = (size_t)sw_small_smem(a);
+    MRF_DISPATCH_LSW(a.L, ({
+        if (smem > 48 * 1024) {
+            const cudaError_t e = cudaFuncSetAttribute(k_sw_small<LL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k_sw_small<LL><<<1, 1024, smem, s>>>(a, n_sweeps);
+    }));
     return cudaGetLastError();
 }
 

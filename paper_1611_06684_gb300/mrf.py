@@ -23,10 +23,10 @@ MRF_PTR_HOST, MRF_PTR_DEVICE = 0, 1
 MODE_PLAIN, MODE_FUSED, MODE_SPLASH, MODE_LEARNED, MODE_SW = 0, 1, 2, 3, 4
 LAYOUT_PIVOT, LAYOUT_DIAG = 0, 1
 (K_DUAL, K_PRIMAL, K_FUSED, K_POTENTIAL, K_FFBS, K_ACCUMULATE, K_FEATURES, K_MLP, K_MH, K_SMALL,
- K_SW_BOND, K_SW_FLATTEN, K_SW_DRAW, K_COUNT) = range(14)
+ K_SW_BOND, K_SW_FLATTEN, K_SW_DRAW, K_SW_SMALL, K_COUNT) = range(15)
 KERNEL_NAMES = ["k_dual", "k_primal", "k_primal<fused>", "k_potential", "k_ffbs", "k_accumulate",
                 "k_learned_features", "k_mlp", "k_learned_mh", "k_sweep_small",
-                "k_sw_bond", "k_sw_flatten", "k_sw_draw"]
+                "k_sw_bond", "k_sw_flatten", "k_sw_draw", "k_sw_small"]
 
 
 class mrf_options(ct.Structure):
@@ -65,6 +65,7 @@ _SIGS = {
     "mrf_kernel_times": (ct.c_int, [_P, _P, _P]),
     "mrf_set_kernel_timing": (ct.c_int, [_P, ct.c_int32]),
     "mrf_estimate_log_partition": (ct.c_int, [_P, ct.c_int32, _P]),
+    "mrf_estimate_log_partition_sw": (ct.c_int, [_P, ct.c_int32, _P]),
     "mrf_map_em": (ct.c_int, [_P, ct.c_int32, _P, ct.c_int32]),
     "mrf_save": (ct.c_int, [_P, ct.c_char_p]),
     "mrf_load": (ct.c_int, [ct.POINTER(_P), ct.c_char_p, _P]),
@@ -329,10 +330,14 @@ class MRF:
         self._check(self.lib.mrf_learned_debug(self.h, X.ctypes.data, z.ctypes.data))
         return X, z
 
-    def estimate_log_partition(self, n_sweeps: int):
-        """log V [n_sweeps][C] of Section 5.2's estimator over n plain sweeps."""
+    def estimate_log_partition(self, n_sweeps: int, mode: int = MODE_PLAIN):
+        """log V [n_sweeps][C] of Section 5.2's estimator over n plain (or, with
+        mode=MODE_SW, Swendsen-Wang) sweeps."""
         out = np.zeros((int(n_sweeps), self.C), np.float64)
-        self._check(self.lib.mrf_estimate_log_partition(self.h, int(n_sweeps), out.ctypes.data))
+        fn = self.lib.mrf_estimate_log_partition_sw if mode == MODE_SW else self.lib.mrf_estimate_log_partition
+        if mode not in (MODE_PLAIN, MODE_SW):
+            raise ValueError("the estimator runs plain or Swendsen-Wang sweeps")
+        self._check(fn(self.h, int(n_sweeps), out.ctypes.data))
         return out
 
     def save(self, path: str):

@@ -255,3 +255,77 @@ def test_sw_resumes_from_checkpoint(tmp_path):
     g.sweep(4, M.MODE_SW)
     assert np.array_equal(g.get_labels(), want)
     g.close()
+
+
+@pytest.mark.parametrize("which", ["ferro3d_L4", "ising_L2"])
+def test_sw_log_v_of_one_sweep_matches_oracle(which):
+    """Section 5.2's estimator on the Swendsen-Wang duality: log V per chain of
+    one sweep from a common state, within the summed per-cluster float32
+    tolerance of the drawn labels' log-probabilities."""
+    from oracle.sampler import log_softmax
+    if which == "ferro3d_L4":
+        model = wl.ferro_potts_grid3d(7, 6, 5, L=4, seed=23)
+    else:
+        model = wl.ising_grid(12, 10, j_lo=0.2, j_hi=0.8, seed=24)
+    C, seed, t = 32, 48, 13
+    x0 = np.random.default_rng(5).integers(0, model.n_labels, size=(C, model.n_vars))
+    h = M.MRF(model.n_vars, model.n_labels, C, seed=seed, grid=model.grid)
+    h.set_factors(model.unary, model.src, model.dst, model.pair)
+    h.set_labels(x0.astype(np.uint8))
+    h.set_sweep_index(t)
+    lv = h.estimate_log_partition(1, M.MODE_SW)[0]
+    x1 = h.get_labels()
+    h.close()
+    tables = sw.sw_tables(model)
+    res = sw.sw_sweep(model, x0, t, seed, tables=tables)
+    ref = sw.log_v(model, res["x"], res["bonds"], tables)
+    near = np.any(np.abs(res["u_cluster"][..., None] - res["cdf_cluster"]) < BOUNDARY_EPS, axis=-1)
+    clean = (x1 == res["x"]).all(axis=1) & ~(near & (res["roots"] == np.arange(model.n_vars)[None, :])).any(axis=1)
+    assert clean.sum() >= C // 2
+    tol = np.zeros(C)
+    for c in range(C):
+        root = res["roots"][c]
+        rs = np.unique(root)
+        lw = sw.cluster_log_weights(tables[1], tables[0], model.src, root, res["bonds"][c])
+        lp = log_softmax(lw[rs])[np.arange(rs.size), res["x"][c][rs]]
+        tol[c] = 1e-5 * np.maximum(1.0, np.abs(lp)).sum() + 1e-6 * (model.n_vars + model.n_edges)
+    err = np.abs(lv - ref)
+    assert (err[clean] <= tol[clean]).all(), (err[clean].max(), tol[clean].min())
+
+
+def test_sw_estimator_moments_match_enumeration():
+    """Many chains of a tiny model at stationarity: the mean of log V over
+    Swendsen-Wang sweeps matches the exact E[log V] = log Z - I(x; theta)."""
+    model = wl.ferro_potts_graph(5, 3, 6, beta_lo=0.2, beta_hi=1.2, seed=25)
+    e_logv, logZ, mi = sw.exact_moments(model)
+    C = 8192
+    h = M.MRF(model.n_vars, 3, C, seed=26, exact_edges=True)
+    h.set_factors(model.unary, model.src, model.dst, model.pair)
+    h.sweep(20, M.MODE_SW)
+    lv = h.estimate_log_partition(16, M.MODE_SW).ravel()
+    h.close()
+    n_eff = lv.size / 4                                               # consecutive sweeps are correlated
+    se_mean = lv.std() / np.sqrt(n_eff)
+    assert abs(lv.mean() - e_logv) < 4 * se_mean + 1e-6, (lv.mean(), e_logv, se_mean)
+    assert e_logv < logZ and mi > 0
+
+
+@pytest.mark.parametrize("name", ["ising32_C1", "graph_L4_C37", "zero_entries_L5_C33"])
+def test_sw_small_model_kernel_is_the_same_chain(name):
+    """n >= 2 sweeps of a small model run in one single-CTA launch; the chain,
+    counts and sweep index equal those of one sweep per call."""
+    model, C = CASES[name][0](), CASES[name][1]
+    assert model.n_vars * C <= 65536 and model.n_edges * C <= 65536
+    seed = 49
+    one = make_handle(model, C, seed)
+    many = make_handle(model, C, seed)
+    for h in (one, many):
+        h.reset_marginals(2)
+    for _ in range(7):
+        one.sweep(1, M.MODE_SW)
+    many.sweep(7, M.MODE_SW)
+    assert np.array_equal(one.get_labels(), many.get_labels())
+    assert np.array_equal(one.counts(), many.counts())
+    assert one.info().sweep_index == many.info().sweep_index == 7
+    assert many.boundary_draws() == one.boundary_draws()
+    one.close(); many.close()

@@ -182,3 +182,12 @@ def test_log_v_of_the_ising_model_without_fields_counts_clusters():
         n_clusters = np.array([np.unique(r).size for r in res["roots"]])
         np.testing.assert_allclose(sw.log_v(m, x, res["bonds"]), n_clusters * np.log(2.0) + sw.log_ptilde(m, x),
                                    rtol=0, atol=1e-10)
+
+
+def test_exact_moments_match_the_enumerated_joint():
+    model = MODELS["potts_L3_s2"]()
+    e_logv, logZ, mi = sw.exact_moments(model)
+    X = brute.all_labelings(model.n_vars, model.n_labels)
+    np.testing.assert_allclose(logZ, np.logaddexp.reduce(brute.log_ptilde(model, X)), atol=1e-10)
+    assert mi > 0
+    np.testing.assert_allclose(e_logv, logZ - mi, atol=1e-10)
