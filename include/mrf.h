@@ -64,8 +64,10 @@ enum {
     MRF_MODE_LEARNED = 3,/* cut-edge duals, then one Metropolis-Hastings step
                             per block with the learned proposal (needs
                             mrf_learned_setup)                               */
-    MRF_MODE_SW = 4      /* Section 4.3: Swendsen-Wang as a degenerate
+    MRF_MODE_SW = 4,     /* Section 4.3: Swendsen-Wang as a degenerate
                             duality (two labels or Potts-type tables, l >= 0)  */
+    MRF_MODE_HIGDON = 5  /* Section 4.3: Higdon's partial Swendsen-Wang with
+                            three-state duals (mrf_set_higdon)               */
 };
 
 /* Dualised table layout chosen by mrf_set_factors (mrf_info.layout). */
@@ -165,6 +167,25 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
  * bit).
  * mrf_debug_logp and the log-partition estimator do not cover this mode. */
 mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode);
+
+/* Fraction rho in [0, 1] of MRF_MODE_HIGDON (default 0.5).  Section 4.3:
+ * with the Swendsen-Wang form 1 + (e^{l_a} - 1)[a = b] of every table, the
+ * factor splits into a bond part alpha_a [a = b], alpha_a = rho (e^{l_a} - 1),
+ * and a remainder A = exp(l'_a [a = b]), l'_a = log(1 + (1 - rho)(e^{l_a} - 1)),
+ * that is dualised as in Sections 4.1-4.2 (one bit per label with l' != 0).
+ * A sweep draws, given x, each edge's bond (probability rho (1 - e^{-l_a})
+ * when both ends have label a; 23-bit uniform of Philox(edge slot, t, chain,
+ * BOND)) and, for every edge that is not a bond, A's bits (the plain sweep's
+ * dual-bit contract); then every cluster of the bonds takes one label with
+ * weight exp(sum_{v in cluster} F_v(a) + sum_{bonds} (log alpha_a - alpha1_a -
+ * alpha2_a)), F the primal field of A's bits with A's folded unaries and
+ * alpha1, alpha2 the Theorem-2 terms of A's entry a, drawn as in
+ * MRF_MODE_SW.  rho = 1 is Swendsen-Wang, rho = 0 a plain dual sweep of the
+ * Potts form.  The fields enter the exact fixed-point cluster sums from
+ * float32 (per-site rounding 2^-24 relative).  Errors as for MRF_MODE_SW;
+ * MRF_ERANGE also when the fields' bound reaches 2^30; MRF_EINVAL for rho
+ * outside [0, 1]. */
+mrf_status mrf_set_higdon(mrf_t* h, double rho);
 
 /* Estimated marginals out[n_vars][L] = counts / n_samples (float32) and the
  * number of samples per site.  Synchronises. */

@@ -137,6 +137,34 @@ inline int32_t tie_cap_for(int M) { return ((32 * M * 3 / 512 + 1 + 16) + 7) / 8
 // k_dual warps (blocks of 256 threads) for E * C items.
 inline int64_t dual_warps(int64_t items) { return (items + 255) / 256 * 8; }
 
+// One dualised entry of log-value l != 0 (Lemma 2-4 and Theorem 2 in closed
+// form, float64): tau = 2 arccosh(e^{|l|/2}) = |l| + 2 log1p(sqrt(-expm1(-|l|))),
+// the packed threshold word of its dual draw (T+ = ceil(sigmoid(tau) 2^24 - 1/2)
+// in bits 0..24, d = T+ + T- - (2^24 - 1) in bits 25..26, the sign of l in bit
+// 31), the signed tau, the Theorem-2 terms alpha1, alpha2 folded into the
+// source and destination unaries, and -log(1 + e^q) for the log constant.
+struct EntryDual {
+    float tau_s;
+    uint32_t word;
+    double alpha1, alpha2, log_norm;
+};
+__host__ __device__ inline EntryDual entry_dual(double l) {
+    const double al = fabs(l);
+    const double tau = al + 2.0 * log1p(sqrt(-expm1(-al)));
+    const double pp = 1.0 / (1.0 + exp(-tau));   // sigmoid(+tau)
+    const double pm = 1.0 / (1.0 + exp(tau));    // sigmoid(-tau)
+    const uint32_t tp = (uint32_t)ceil(pp * 16777216.0 - 0.5), tm = (uint32_t)ceil(pm * 16777216.0 - 0.5);
+    const uint32_t d = tp + tm - ((1u << 24) - 1u);   // in {0,1,2}
+    EntryDual r;
+    r.word = tp | (d << 25) | (l < 0 ? 0x80000000u : 0u);
+    r.tau_s = (float)(l > 0 ? tau : -tau);
+    const double q = l > 0 ? -tau : 0.0;
+    r.alpha1 = l > 0 ? 0.5 * (l - tau) : 0.5 * (l + tau);
+    r.alpha2 = 0.5 * (l - tau);
+    r.log_norm = -(q > 0 ? q + log1p(exp(-q)) : log1p(exp(q)));
+    return r;
+}
+
 // Swendsen-Wang sweep (sw.cu): bonds, union-find and cluster labels.
 struct SwArgs {
     int32_t N, C, L;
@@ -146,6 +174,7 @@ struct SwArgs {
     const uint32_t* thr;       // [E][L] 23-bit bond thresholds
     const int64_t* lwe;        // [E][L] fixed-point bond log weights (kSwNoLabel: label excluded)
     const int64_t* ufix;       // [N][L] fixed-point unaries (two labels: offsets folded in)
+    const float* pot;          // [N][L][C] per-chain unaries instead of ufix (Higdon's sweep), or null
     uint8_t* x;                // [2][N][C] label double buffer
     int32_t* parent;           // [N][C] union-find forest, links to smaller sites only
     int32_t* root;             // [N][C] root of a bonded site (written by k_sw_flatten)
@@ -242,6 +271,20 @@ cudaError_t launch_sweep_noalloc(const SweepArgs& a, int layout, const uint8_t* 
 // Swendsen-Wang (sw.cu)
 cudaError_t launch_sw_check(const int32_t* src, const float* tau, int64_t E, int M, const int64_t* lwe, int L,
                             const float* unary, const double* unary_d, int N, double* out, cudaStream_t s);
+// Higdon's partial Swendsen-Wang (sw.cu)
+struct HigdonTables {
+    uint32_t* bond_thr;        // [E][L] 23-bit thresholds of rho (1 - e^{-l})
+    int64_t* bond_lw;          // [E][L] fixed-point log alpha - alpha1 - alpha2 (kSwNoLabel where alpha = 0)
+    float* tau;                // [E][pad4(L)] signed dual weights of the remainder A
+    uint32_t* thr;             // [E][L] packed thresholds of A's bits
+    double* fold;              // [E][2][L] A's Theorem-2 terms for the unaries
+    double* bound;             // [E] max |bond weight| + 2 max tau of the edge (range check)
+};
+cudaError_t launch_hg_tables(const int32_t* src, const double* ell, int64_t E, int L, double rho, HigdonTables t,
+                             cudaStream_t s);
+cudaError_t launch_hg_check(const double* ut, int N, int L, const int32_t* src, const double* bound, int64_t E,
+                            double* out, cudaStream_t s);
+cudaError_t launch_hg_clear(const uint32_t* bits, uint32_t* theta, int64_t items, cudaStream_t s);
 cudaError_t launch_sw_fix_unary(const float* unary, const double* unary_d, int64_t n, int64_t* ufix, cudaStream_t s);
 cudaError_t launch_sw_reset(const SwArgs& a, cudaStream_t s);
 cudaError_t launch_sw_bond(const SwArgs& a, cudaStream_t s);
@@ -267,6 +310,7 @@ struct DecompArgs {
     uint32_t* sw_thr;          // [E][L] Swendsen-Wang bond thresholds (diagonal layout) or null
     int64_t* sw_lw;            // [E][L] Swendsen-Wang bond log weights, fixed point, or null
     double* sw_fold;           // [E][2][L] Swendsen-Wang unary offsets (two labels) or null
+    double* sw_ell;            // [E][L] Swendsen-Wang couplings l_x (float64) or null
 };
 cudaError_t launch_check_finite(const float* p, int64_t n, unsigned long long* bad, cudaStream_t s);
 cudaError_t launch_count_offdiag(const float* pair, int64_t n_edges, int L, unsigned long long* nz, cudaStream_t s);
@@ -274,6 +318,7 @@ cudaError_t launch_decompose(const DecompArgs& a, cudaStream_t s);
 cudaError_t launch_build_planes(const uint32_t* thr, int64_t n, const int64_t* slots, int64_t first_slot, int M,
                                 uint32_t* tpl, cudaStream_t s);
 cudaError_t launch_fold_unary(const float* unary, const double* fold, const int64_t* inc_ptr, const int2* inc,
-                              int N, int L, double* ut, float* utf, cudaStream_t s);
+                              int N, int L, double* ut, float* utf, cudaStream_t s,
+                              const double* unary_d = nullptr);
 
 }  // namespace mrfk

@@ -42,10 +42,6 @@ __global__ void k_count_offdiag(const float* pair, int64_t n_edges, int L, unsig
     if (cnt) atomicAdd(nz, cnt);
 }
 
-__device__ inline uint32_t threshold24(double p) {
-    return (uint32_t)ceil(p * 16777216.0 - 0.5);
-}
-
 __global__ void k_decompose(DecompArgs a) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.n) return;
@@ -77,18 +73,12 @@ __global__ void k_decompose(DecompArgs a) {
         float tau_s = 0.0f;
         uint32_t word = 0;
         if (l != 0.0) {
-            const double al = fabs(l);
-            const double tau = al + 2.0 * log1p(sqrt(-expm1(-al)));
-            const double pp = 1.0 / (1.0 + exp(-tau));   // sigmoid(+tau)
-            const double pm = 1.0 / (1.0 + exp(tau));    // sigmoid(-tau)
-            const uint32_t tp = threshold24(pp), tm = threshold24(pm);
-            const uint32_t d = tp + tm - ((1u << 24) - 1u);   // in {0,1,2}
-            word = tp | (d << 25) | (l < 0 ? 0x80000000u : 0u);
-            tau_s = (float)(l > 0 ? tau : -tau);
-            const double q = l > 0 ? -tau : 0.0;
-            fs[ii] += l > 0 ? 0.5 * (l - tau) : 0.5 * (l + tau);
-            ft[jj] += 0.5 * (l - tau);
-            cst -= (q > 0 ? q + log1p(exp(-q)) : log1p(exp(q)));   // -log(1 + e^q)
+            const EntryDual d = entry_dual(l);
+            word = d.word;
+            tau_s = d.tau_s;
+            fs[ii] += d.alpha1;
+            ft[jj] += d.alpha2;
+            cst += d.log_norm;   // -log(1 + e^q)
         }
         a.tau[e * pad4(M) + k] = tau_s;
         a.thr[e * M + k] = word;
@@ -131,6 +121,7 @@ __global__ void k_decompose(DecompArgs a) {
             }
             a.sw_thr[e * L + x] = T;
             a.sw_lw[e * L + x] = lw;
+            if (a.sw_ell) a.sw_ell[e * L + x] = l;
         }
     }
     if (a.resid) {
@@ -183,12 +174,12 @@ __global__ void k_build_planes(const uint32_t* thr, int64_t n, const int64_t* sl
         out[p] = make_uint4(P[0][p], P[0][p] ^ P[1][p], P[0][p] ^ P[2][p], P[0][p] ^ P[1][p] ^ P[2][p] ^ P[3][p]);
 }
 
-__global__ void k_fold_unary(const float* unary, const double* fold, const int64_t* inc_ptr, const int2* inc,
-                             int N, int L, double* ut, float* utf) {
+__global__ void k_fold_unary(const float* unary, const double* unary_d, const double* fold, const int64_t* inc_ptr,
+                             const int2* inc, int N, int L, double* ut, float* utf) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= N) return;
     double acc[kMaxLabels];
-    for (int x = 0; x < L; ++x) acc[x] = unary[(int64_t)v * L + x];
+    for (int x = 0; x < L; ++x) acc[x] = unary_d ? unary_d[(int64_t)v * L + x] : (double)unary[(int64_t)v * L + x];
     for (int64_t p = inc_ptr[v]; p < inc_ptr[v + 1]; ++p) {
         const int code = inc[p].x;
         const int64_t e = code >> 1;
@@ -217,8 +208,8 @@ cudaError_t launch_decompose(const DecompArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_fold_unary(const float* unary, const double* fold, const int64_t* inc_ptr, const int2* inc,
-                              int N, int L, double* ut, float* utf, cudaStream_t s) {
-    if (N > 0) k_fold_unary<<<(N + 127) / 128, 128, 0, s>>>(unary, fold, inc_ptr, inc, N, L, ut, utf);
+                              int N, int L, double* ut, float* utf, cudaStream_t s, const double* unary_d) {
+    if (N > 0) k_fold_unary<<<(N + 127) / 128, 128, 0, s>>>(unary, unary_d, fold, inc_ptr, inc, N, L, ut, utf);
     return cudaGetLastError();
 }
 

@@ -55,7 +55,7 @@ struct mrf {
     int64_t sweep_host = 0, count_from_host = 0;
     double log_const = NAN;
     std::string err;
-    cudaGraphExec_t graph[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaGraphExec_t graph[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     uint8_t* d_stage = nullptr;        // [C][N] staging for the ABI label view
     // Swendsen-Wang (diagonal layout): per-edge tables and per-sweep union-find state
     uint32_t* d_swt = nullptr;         // [E][L] 23-bit bond thresholds
@@ -71,6 +71,14 @@ struct mrf {
     unsigned* d_swerr = nullptr;       // union-find step bound exceeded
     int64_t* d_swufix = nullptr;       // [N][L] fixed-point unaries of the Swendsen-Wang sweep
     double* d_swchk = nullptr;         // [3] model check sums (k_sw_check)
+    double* d_swell = nullptr;         // [E][L] couplings l_x of the Swendsen-Wang form (float64)
+    // Higdon's partial Swendsen-Wang: tables of the split at hg_rho (rebuilt after factor changes)
+    double hg_rho = 0.5;
+    bool hg_ready = false;
+    int64_t hg_cap = 0;                // edge slots the tables below hold
+    uint32_t* d_hgT = nullptr; int64_t* d_hglb = nullptr; float* d_hgtau = nullptr; uint32_t* d_hgthr = nullptr;
+    uint32_t* d_hgtpl = nullptr; double* d_hgfold = nullptr; double* d_hgbound = nullptr;
+    double* d_hgut = nullptr; float* d_hgutf = nullptr;
     bool sw_checked = false;           // the model passed the check since the factors last changed
     float* d_pot = nullptr;            // [N][L][C] node potentials of the blocked sweep
     int schedule = 0;                  // primal schedule in use (1 thread, 2 CTA); 0 = not tuned yet
@@ -388,7 +396,9 @@ void mrf_destroy(mrf_t* h) {
     dfree(h->d_fold); dfree(h->d_cst); dfree(h->d_resid); dfree(h->d_inc_ptr); dfree(h->d_inc); dfree(h->d_x);
     dfree(h->d_theta); dfree(h->d_ties); dfree(h->d_tie_count); dfree(h->d_counts); dfree(h->d_lpv); dfree(h->d_logv); dfree(h->d_em); dfree(h->d_mfq); dfree(h->d_mfs); dfree(h->d_logp); dfree(h->d_ctl); dfree(h->d_flag); dfree(h->d_stage); dfree(h->d_pot);
     dfree(h->d_swt); dfree(h->d_swl); dfree(h->d_swfold); dfree(h->d_swut); dfree(h->d_swpar); dfree(h->d_swroot); dfree(h->d_swbits); dfree(h->d_swban); dfree(h->d_swlw); dfree(h->d_swerr); dfree(h->d_swchk);
-    dfree(h->d_swufix);
+    dfree(h->d_swufix); dfree(h->d_swell);
+    dfree(h->d_hgT); dfree(h->d_hglb); dfree(h->d_hgtau); dfree(h->d_hgthr); dfree(h->d_hgtpl); dfree(h->d_hgfold);
+    dfree(h->d_hgbound); dfree(h->d_hgut); dfree(h->d_hgutf);
     dfree(h->d_csr_work); dfree(h->d_csr_sums);
     dfree(h->d_ed_pair); dfree(h->d_ed_slots); dfree(h->d_ed_new); dfree(h->d_ed_s); dfree(h->d_ed_t);
     dfree(h->d_members); dfree(h->d_nmem); dfree(h->d_intra_ptr); dfree(h->d_intra); dfree(h->d_cf); dfree(h->d_skip);
@@ -452,10 +462,11 @@ mrf_status mrf_set_factors(mrf_t* h, const float* unary_log, int64_t n_edges, co
     MRF_CUDA(h, dalloc(h->d_fold, E * 2 * L)); MRF_CUDA(h, dalloc(h->d_cst, E));
     if (want_resid) MRF_CUDA(h, dalloc(h->d_resid, E * L * L)); else dfree(h->d_resid);
     if (h->layout == MRF_LAYOUT_DIAG || L == 2) {
-        MRF_CUDA(h, dalloc(h->d_swt, E * L)); MRF_CUDA(h, dalloc(h->d_swl, E * L));
+        MRF_CUDA(h, dalloc(h->d_swt, E * L)); MRF_CUDA(h, dalloc(h->d_swl, E * L)); MRF_CUDA(h, dalloc(h->d_swell, E * L));
     } else {
-        dfree(h->d_swt); dfree(h->d_swl);
+        dfree(h->d_swt); dfree(h->d_swl); dfree(h->d_swell);
     }
+    h->hg_ready = false;
     if (L == 2) {
         MRF_CUDA(h, dalloc(h->d_swfold, E * 2 * L)); MRF_CUDA(h, dalloc(h->d_swut, (size_t)N * L));
     } else {
@@ -470,7 +481,7 @@ mrf_status mrf_set_factors(mrf_t* h, const float* unary_log, int64_t n_edges, co
     DecompArgs d{};
     d.L = L; d.M = h->M; d.layout = h->layout; d.n = n_edges; d.slots = nullptr; d.first_slot = 0;
     d.pair = d_pair; d.tau = h->d_tau; d.thr = h->d_thr; d.fold = h->d_fold; d.cst = h->d_cst; d.resid = h->d_resid;
-    d.sw_thr = h->d_swt; d.sw_lw = h->d_swl; d.sw_fold = h->d_swfold;
+    d.sw_thr = h->d_swt; d.sw_lw = h->d_swl; d.sw_fold = h->d_swfold; d.sw_ell = h->d_swell;
     MRF_CUDA(h, launch_decompose(d, h->stream));
     MRF_CUDA(h, launch_build_planes(h->d_thr, n_edges, nullptr, 0, h->M, h->d_tpl, h->stream));
     MRF_CUDA(h, launch_fold_unary(h->d_unary, h->d_fold, h->d_inc_ptr, h->d_inc, N, L, h->d_ut, h->d_utf, h->stream));
@@ -561,7 +572,7 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
         if ((uint64_t)cap * h->C >= (1ull << 32)) return fail(h, MRF_ERANGE, "edges x chains must be below 2^32");
         MRF_CUDA(h, grow(h->d_tau, pad4(h->M))); MRF_CUDA(h, grow(h->d_thr, h->M)); MRF_CUDA(h, grow(h->d_tpl, h->W * 32));
         MRF_CUDA(h, grow(h->d_fold, 2 * L)); MRF_CUDA(h, grow(h->d_cst, 1));
-        if (h->d_swt) { MRF_CUDA(h, grow(h->d_swt, L)); MRF_CUDA(h, grow(h->d_swl, L)); }
+        if (h->d_swt) { MRF_CUDA(h, grow(h->d_swt, L)); MRF_CUDA(h, grow(h->d_swl, L)); MRF_CUDA(h, grow(h->d_swell, L)); }
         if (h->d_swfold) MRF_CUDA(h, grow(h->d_swfold, 2 * L));
         MRF_CUDA(h, dalloc(h->d_theta, (size_t)cap * h->C * h->W));
         MRF_CUDA(h, alloc_ties(h, cap));
@@ -603,8 +614,9 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
     DecompArgs d{};
     d.L = L; d.M = h->M; d.layout = h->layout; d.n = n_add; d.slots = d_new;
     d.pair = d_pair; d.tau = h->d_tau; d.thr = h->d_thr; d.fold = h->d_fold; d.cst = h->d_cst; d.resid = nullptr;
-    d.sw_thr = h->d_swt; d.sw_lw = h->d_swl; d.sw_fold = h->d_swfold;
+    d.sw_thr = h->d_swt; d.sw_lw = h->d_swl; d.sw_fold = h->d_swfold; d.sw_ell = h->d_swell;
     h->sw_checked = false;
+    h->hg_ready = false;
     MRF_CUDA(h, launch_decompose(d, h->stream));
     MRF_CUDA(h, launch_build_planes(h->d_thr, n_add, d_new, 0, h->M, h->d_tpl, h->stream));
     // incidence lists rebuilt on the device (host build if a site is very long)
@@ -741,6 +753,44 @@ static mrf_status sw_check_error(mrf_t* h) {
     return MRF_OK;
 }
 
+// Before Higdon sweeps: the Swendsen-Wang prerequisites, then the tables of
+// the split at hg_rho (once per factor or rho change), the remainder's folded
+// unaries and the range check that now includes the bits' fields.
+static mrf_status hg_prepare(mrf_t* h) {
+    mrf_status st = sw_prepare(h);
+    if (st != MRF_OK) return st;
+    if (!h->d_pot) { drop_graphs(h); MRF_CUDA(h, dalloc(h->d_pot, (size_t)h->N * h->L * h->C)); }
+    if (h->hg_ready) return MRF_OK;
+    if (h->E_live > 0 && !h->d_swell) return fail(h, MRF_EINVAL, "Higdon sweeps need two labels or Potts-type tables");
+    const int L = h->L;
+    const int64_t E = h->E_slots;
+    if (h->hg_cap < E || !h->d_hgut) {
+        drop_graphs(h);
+        const size_t cap = (size_t)std::max<int64_t>(E, 1);
+        MRF_CUDA(h, dalloc(h->d_hgT, cap * L)); MRF_CUDA(h, dalloc(h->d_hglb, cap * L));
+        MRF_CUDA(h, dalloc(h->d_hgtau, cap * pad4(L))); MRF_CUDA(h, dalloc(h->d_hgthr, cap * L));
+        MRF_CUDA(h, dalloc(h->d_hgtpl, cap * 32)); MRF_CUDA(h, dalloc(h->d_hgfold, cap * 2 * L));
+        MRF_CUDA(h, dalloc(h->d_hgbound, cap));
+        MRF_CUDA(h, dalloc(h->d_hgut, (size_t)h->N * L)); MRF_CUDA(h, dalloc(h->d_hgutf, (size_t)h->N * L));
+        h->hg_cap = (int64_t)cap;
+    }
+    HigdonTables t{h->d_hgT, h->d_hglb, h->d_hgtau, h->d_hgthr, h->d_hgfold, h->d_hgbound};
+    MRF_CUDA(h, launch_hg_tables(h->d_src, h->d_swell, E, L, h->hg_rho, t, h->stream));
+    MRF_CUDA(h, launch_build_planes(h->d_hgthr, E, nullptr, 0, L, h->d_hgtpl, h->stream));
+    // the remainder's unaries: the Swendsen-Wang unaries plus A's Theorem-2 terms of every edge
+    MRF_CUDA(h, launch_fold_unary(h->d_unary, h->d_hgfold, h->d_inc_ptr, h->d_inc, h->N, L, h->d_hgut, h->d_hgutf,
+                                  h->stream, h->d_swut));
+    MRF_CUDA(h, cudaMemsetAsync(h->d_swchk, 0, sizeof(double), h->stream));
+    MRF_CUDA(h, launch_hg_check(h->d_hgut, h->N, L, h->d_src, h->d_hgbound, E, h->d_swchk, h->stream));
+    double bound = 0.0;
+    MRF_CUDA(h, cudaMemcpyAsync(&bound, h->d_swchk, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (bound >= kSwFixMax)
+        return fail(h, MRF_ERANGE, "Higdon: summed |log weights| exceed the fixed-point range (2^30)");
+    h->hg_ready = true;
+    return MRF_OK;
+}
+
 static mrf_status enqueue_sweep(mrf_t* h, int mode) {
     SweepArgs a = make_args(h);
     cudaStream_t s = h->stream;
@@ -753,6 +803,23 @@ static mrf_status enqueue_sweep(mrf_t* h, int mode) {
     } else if (mode == MRF_MODE_SW) {
         const SwArgs w = make_sw_args(h);
         e = timed(h, MRF_K_SW_BOND, [&] { return launch_sw_bond(w, s); });
+        if (e == cudaSuccess) e = timed(h, MRF_K_SW_FLATTEN, [&] { return launch_sw_flatten(w, s); });
+        if (e == cudaSuccess) e = timed(h, MRF_K_SW_DRAW, [&] { return launch_sw_draw(w, s); });
+    } else if (mode == MRF_MODE_HIGDON) {
+        // bonds (and their unions), A's bits of the other edges, the bits'
+        // potentials, then the clusters as in the Swendsen-Wang sweep
+        SwArgs w = make_sw_args(h);
+        w.thr = h->d_hgT; w.lwe = h->d_hglb; w.pot = h->d_pot;
+        SweepArgs d = a;
+        d.M = h->L; d.W = 1; d.tau = h->d_hgtau; d.thr = h->d_hgthr; d.tpl = h->d_hgtpl;
+        d.utf = h->d_hgutf; d.ut = h->d_hgut; d.tie_cap = tie_cap_for(h->L); d.logp = nullptr; d.lpv = nullptr;
+        d.pot = h->d_pot;
+        e = timed(h, MRF_K_SW_BOND, [&] { return launch_sw_bond(w, s); });
+        if (e == cudaSuccess) e = timed(h, MRF_K_DUAL, [&] {
+            const cudaError_t e2 = launch_dual(d, MRF_LAYOUT_DIAG, s);
+            return e2 != cudaSuccess ? e2 : launch_hg_clear(w.bits, d.theta, h->E_slots * h->C, s);
+        });
+        if (e == cudaSuccess) e = timed(h, MRF_K_POTENTIAL, [&] { return launch_potential(d, MRF_LAYOUT_DIAG, s); });
         if (e == cudaSuccess) e = timed(h, MRF_K_SW_FLATTEN, [&] { return launch_sw_flatten(w, s); });
         if (e == cudaSuccess) e = timed(h, MRF_K_SW_DRAW, [&] { return launch_sw_draw(w, s); });
     } else if (mode == MRF_MODE_LEARNED) {
@@ -781,7 +848,11 @@ static mrf_status enqueue_sweep(mrf_t* h, int mode) {
 mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode) {
     if (!h) return MRF_EINVAL;
     if (!h->has_factors) return fail(h, MRF_ESTATE, "mrf_set_factors first");
-    if (n_sweeps < 0 || mode < MRF_MODE_PLAIN || mode > MRF_MODE_SW) return fail(h, MRF_EINVAL, "bad sweep count or mode");
+    if (n_sweeps < 0 || mode < MRF_MODE_PLAIN || mode > MRF_MODE_HIGDON) return fail(h, MRF_EINVAL, "bad sweep count or mode");
+    if (mode == MRF_MODE_HIGDON) {
+        mrf_status st = hg_prepare(h);
+        if (st != MRF_OK) return st;
+    }
     if (mode == MRF_MODE_SW) {
         mrf_status st = sw_prepare(h);
         if (st != MRF_OK) return st;
@@ -836,7 +907,7 @@ mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode) {
         }
     }
     h->sweep_host += n_sweeps;
-    if (mode == MRF_MODE_SW && n_sweeps > 0) {
+    if ((mode == MRF_MODE_SW || mode == MRF_MODE_HIGDON) && n_sweeps > 0) {
         mrf_status st = sw_check_error(h);
         if (st != MRF_OK) return st;
     }
@@ -890,6 +961,13 @@ static mrf_status estimate_log_partition(mrf_t* h, int32_t n_sweeps, int mode, d
                                 h->stream));
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));
     if (mode == MRF_MODE_SW) return sw_check_error(h);
+    return MRF_OK;
+}
+
+mrf_status mrf_set_higdon(mrf_t* h, double rho) {
+    if (!h) return MRF_EINVAL;
+    if (!(rho >= 0.0 && rho <= 1.0)) return fail(h, MRF_EINVAL, "Higdon's fraction rho must lie in [0, 1]");
+    if (rho != h->hg_rho) { h->hg_rho = rho; h->hg_ready = false; drop_graphs(h); }
     return MRF_OK;
 }
 
@@ -982,7 +1060,7 @@ mrf_status mrf_mean_field(mrf_t* h, int32_t n_iters, float* marginals, int32_t p
 
 namespace {
 
-constexpr char kCkptMagic[8] = {'M', 'R', 'F', 'C', 'K', 'P', 'T', '1'};
+constexpr char kCkptMagic[8] = {'M', 'R', 'F', 'C', 'K', 'P', 'T', '2'};   // 2: Swendsen-Wang tables
 
 struct CkptHeader {
     int32_t N, L, C, layout, M, W;
@@ -1040,7 +1118,8 @@ mrf_status mrf_save(mrf_t* h, const char* path) {
          write_dev(f, h->d_tpl, E * h->W * 32, buf, h->stream) && write_dev(f, h->d_fold, E * 2 * L, buf, h->stream) &&
          write_dev(f, h->d_cst, E, buf, h->stream);
     if (hd.has_resid) ok = ok && write_dev(f, h->d_resid, E * L * L, buf, h->stream);
-    if (hd.has_sw & 1) ok = ok && write_dev(f, h->d_swt, E * L, buf, h->stream) && write_dev(f, h->d_swl, E * L, buf, h->stream);
+    if (hd.has_sw & 1) ok = ok && write_dev(f, h->d_swt, E * L, buf, h->stream) && write_dev(f, h->d_swl, E * L, buf, h->stream) &&
+                          write_dev(f, h->d_swell, E * L, buf, h->stream);
     if (hd.has_sw & 2) ok = ok && write_dev(f, h->d_swfold, E * 2 * L, buf, h->stream);
     ok = ok && write_dev(f, h->d_x, 2 * (size_t)h->N * h->C, buf, h->stream) && write_dev(f, h->d_counts, NL, buf, h->stream);
     ok = ok && (hd.n_free == 0 || fwrite(h->free_slots.data(), sizeof(int64_t), (size_t)hd.n_free, f) == (size_t)hd.n_free);
@@ -1079,7 +1158,7 @@ mrf_status mrf_load(mrf_t** out, const char* path, void* cuda_stream) {
     if (!ok) return bail(MRF_EINVAL);
     if (dalloc(h->d_src, E) || dalloc(h->d_dst, E) || dalloc(h->d_tau, E * pad4(h->M)) || dalloc(h->d_thr, E * h->M) ||
         dalloc(h->d_tpl, E * h->W * 32) || dalloc(h->d_fold, E * 2 * L) || dalloc(h->d_cst, E) ||
-        (hd.has_resid && dalloc(h->d_resid, E * L * L)) || ((hd.has_sw & 1) && (dalloc(h->d_swt, E * L) || dalloc(h->d_swl, E * L))) ||
+        (hd.has_resid && dalloc(h->d_resid, E * L * L)) || ((hd.has_sw & 1) && (dalloc(h->d_swt, E * L) || dalloc(h->d_swl, E * L) || dalloc(h->d_swell, E * L))) ||
         ((hd.has_sw & 2) && (dalloc(h->d_swfold, E * 2 * L) || dalloc(h->d_swut, NL))) ||
         dalloc(h->d_theta, E * h->C * h->W) || alloc_ties(h, (int64_t)E)) {
         cudaGetLastError();
@@ -1091,7 +1170,8 @@ mrf_status mrf_load(mrf_t** out, const char* path, void* cuda_stream) {
          read_dev(f, h->d_tpl, E * h->W * 32, buf, h->stream) && read_dev(f, h->d_fold, E * 2 * L, buf, h->stream) &&
          read_dev(f, h->d_cst, E, buf, h->stream);
     if (hd.has_resid) ok = ok && read_dev(f, h->d_resid, E * L * L, buf, h->stream);
-    if (hd.has_sw & 1) ok = ok && read_dev(f, h->d_swt, E * L, buf, h->stream) && read_dev(f, h->d_swl, E * L, buf, h->stream);
+    if (hd.has_sw & 1) ok = ok && read_dev(f, h->d_swt, E * L, buf, h->stream) && read_dev(f, h->d_swl, E * L, buf, h->stream) &&
+                          read_dev(f, h->d_swell, E * L, buf, h->stream);
     if (hd.has_sw & 2) ok = ok && read_dev(f, h->d_swfold, E * 2 * L, buf, h->stream);
     ok = ok && read_dev(f, h->d_x, 2 * (size_t)h->N * h->C, buf, h->stream) && read_dev(f, h->d_counts, NL, buf, h->stream);
     h->free_slots.resize((size_t)hd.n_free);

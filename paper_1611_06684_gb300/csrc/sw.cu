@@ -79,6 +79,30 @@ __device__ __forceinline__ void red_add_s64(int64_t* p, int64_t v) {
 
 }  // namespace
 
+// sw_fix of a float32 value without float64 arithmetic: the value is
+// m 2^(e - 150) with a 24-bit mantissa m, so its fixed-point form m 2^(e - 118)
+// is a shift of m (rounded half away from zero when it drops bits; |f| < 2^30
+// is guaranteed by the model check).
+__device__ __forceinline__ int64_t fix_from_float(float f) {
+    const uint32_t bits = __float_as_uint(f);
+    const int e = (int)((bits >> 23) & 0xFFu);
+    if (e == 0) return 0;                                          // zero and subnormals (|f| < 2^-126)
+    const int64_t m = (int64_t)((bits & 0x7FFFFFu) | 0x800000u);
+    const int sh = e - 118;
+    int64_t v;
+    if (sh >= 0) v = m << (sh < 38 ? sh : 38);
+    else if (sh > -25) v = (m + ((int64_t)1 << (-sh - 1))) >> (-sh);
+    else v = 0;
+    return (bits >> 31) ? -v : v;
+}
+
+// Unary term of label x of item (v, c): the fixed-point unary, or the
+// per-chain potential of Higdon's sweep.
+template <int L>
+__device__ __forceinline__ int64_t sw_unary(const SwArgs& a, int32_t v, int32_t c, int x) {
+    return a.pot ? fix_from_float(a.pot[((int64_t)v * L + x) * a.C + c]) : __ldg(a.ufix + (int64_t)v * L + x);
+}
+
 // float of a fixed-point weight difference d <= 0 (two 32-bit conversions:
 // GB300's 64-bit conversions run on its slow FP64 path).
 __device__ __forceinline__ float sw_float(int64_t d) {
@@ -185,7 +209,7 @@ __global__ void __launch_bounds__(256) k_sw_flatten(SwArgs a) {
         if (r == v) continue;
         int64_t w[L];
 #pragma unroll
-        for (int x = 0; x < L; ++x) w[x] = __ldg(a.ufix + (int64_t)v * L + x);
+        for (int x = 0; x < L; ++x) w[x] = sw_unary<L>(a, v, c, x);
         if (b & kSwRow) {
             const int64_t* row = a.lw + (int64_t)v * L * a.C + c;
 #pragma unroll
@@ -218,7 +242,7 @@ __global__ void __launch_bounds__(256) k_sw_draw(SwArgs a) {
         }
         int64_t w[L];
 #pragma unroll
-        for (int x = 0; x < L; ++x) w[x] = __ldg(a.ufix + (int64_t)v * L + x);
+        for (int x = 0; x < L; ++x) w[x] = sw_unary<L>(a, v, c, x);
         if (bonded) {
             const int64_t* row = a.lw + (int64_t)v * L * a.C + c;
 #pragma unroll
@@ -418,6 +442,81 @@ __global__ void __launch_bounds__(1024) k_sw_small(SwArgs a, int n_sweeps) {
     if (threadIdx.x == 0) a.ctl->sweep = sweep;
 }
 
+// Higdon's partial Swendsen-Wang (Section 4.3): per edge and label a with
+// coupling l (float64), alpha = rho (e^l - 1) and the remainder
+// A = exp(l' [a = b]), l' = log(1 + (1 - rho)(e^l - 1)), dualised by
+// entry_dual (diagonal layout, entry k = label k).  Written per edge: the bond
+// threshold of rho (1 - e^{-l}), the bond weight log alpha - alpha1 - alpha2
+// in fixed point, A's dual weights, thresholds and unary terms, and the
+// edge's bound for the range check.
+__global__ void k_hg_tables(const int32_t* __restrict__ src, const double* __restrict__ ell, int64_t E, int L,
+                            double rho, HigdonTables t) {
+    const int MP = pad4(L);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        double bound_w = 0.0, bound_tau = 0.0;
+        for (int x = 0; x < L; ++x) {
+            const double l = src[e] >= 0 ? ell[e * L + x] : 0.0;
+            const double alpha = rho * expm1(l);
+            const double lp = log1p((1.0 - rho) * expm1(l));
+            uint32_t T = 0;
+            if (l > 0.0 && rho > 0.0) T = (uint32_t)ceil(rho * -expm1(-l) * 8388608.0 - 0.5);
+            float tau_s = 0.0f;
+            uint32_t word = 0;
+            double a12 = 0.0;
+            if (lp != 0.0) {
+                const EntryDual d = entry_dual(lp);
+                tau_s = d.tau_s; word = d.word; a12 = d.alpha1 + d.alpha2;
+                t.fold[(e * 2 + 0) * L + x] = d.alpha1;
+                t.fold[(e * 2 + 1) * L + x] = d.alpha2;
+            } else {
+                t.fold[(e * 2 + 0) * L + x] = 0.0;
+                t.fold[(e * 2 + 1) * L + x] = 0.0;
+            }
+            int64_t lw = kSwNoLabel;
+            if (alpha > 0.0) {
+                const double w = log(alpha) - a12;
+                lw = sw_fix(w);
+                bound_w = fmax(bound_w, fabs(w));
+            }
+            bound_tau = fmax(bound_tau, fabs((double)tau_s));
+            t.bond_thr[e * L + x] = T;
+            t.bond_lw[e * L + x] = lw;
+            t.tau[e * MP + x] = tau_s;
+            t.thr[e * L + x] = word;
+        }
+        for (int x = L; x < MP; ++x) t.tau[e * MP + x] = 0.0f;
+        t.bound[e] = src[e] >= 0 ? bound_w + 2.0 * bound_tau : 0.0;
+    }
+}
+
+// out[0] += sum over sites of max_x |ut_v(x)| + sum over live edges of their bound.
+__global__ void k_hg_check(const double* __restrict__ ut, int N, int L, const int32_t* __restrict__ src,
+                           const double* __restrict__ bound, int64_t E, double* out) {
+    double acc = 0.0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
+        double m = 0.0;
+        for (int x = 0; x < L; ++x) m = fmax(m, fabs(ut[v * L + x]));
+        acc += m;
+    }
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x)
+        if (src[e] >= 0) acc += bound[e];
+    if (acc != 0.0) atomicAdd(out, acc);
+}
+
+// A bond carries no bits of A: clear the dual bits of every bonded (edge,
+// chain) item (one dual word per item: the diagonal layout with L <= 16).
+__global__ void k_hg_clear(const uint32_t* __restrict__ bits, uint32_t* __restrict__ theta, int64_t items) {
+    const int64_t words = (items + 31) >> 5;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t word = bits[i];
+        while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1u;
+            theta[i * 32 + b] = 0u;
+        }
+    }
+}
+
 // Model check before the first Swendsen-Wang sweep after the factors change:
 // out[0] = dual weights tau < 0 on live edges (antiferromagnetic entries; with
 // two labels the one pivot entry's tau has the sign of l),
@@ -484,6 +583,23 @@ cudaError_t launch_sw_check(const int32_t* src, const float* tau, int64_t E, int
 __global__ void k_sw_fix_unary(const float* unary, const double* unary_d, int64_t n, int64_t* ufix) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         ufix[i] = sw_fix(unary_d ? unary_d[i] : (double)unary[i]);
+}
+
+cudaError_t launch_hg_tables(const int32_t* src, const double* ell, int64_t E, int L, double rho, HigdonTables t,
+                             cudaStream_t s) {
+    if (E > 0) k_hg_tables<<<sw_blocks(E), 256, 0, s>>>(src, ell, E, L, rho, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hg_check(const double* ut, int N, int L, const int32_t* src, const double* bound, int64_t E,
+                            double* out, cudaStream_t s) {
+    k_hg_check<<<sw_blocks(E > N ? E : N), 256, 0, s>>>(ut, N, L, src, bound, E, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hg_clear(const uint32_t* bits, uint32_t* theta, int64_t items, cudaStream_t s) {
+    if (items > 0) k_hg_clear<<<sw_blocks((items + 31) / 32), 256, 0, s>>>(bits, theta, items);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sw_fix_unary(const float* unary, const double* unary_d, int64_t n, int64_t* ufix, cudaStream_t s) {

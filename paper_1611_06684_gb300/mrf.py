@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libmrf.so")
 
 MRF_OK, MRF_EINVAL, MRF_ENONFINITE, MRF_ENOMEM, MRF_ECUDA, MRF_ERANGE, MRF_ETIMEOUT, MRF_ESTATE = range(8)
 MRF_PTR_HOST, MRF_PTR_DEVICE = 0, 1
-MODE_PLAIN, MODE_FUSED, MODE_SPLASH, MODE_LEARNED, MODE_SW = 0, 1, 2, 3, 4
+MODE_PLAIN, MODE_FUSED, MODE_SPLASH, MODE_LEARNED, MODE_SW, MODE_HIGDON = 0, 1, 2, 3, 4, 5
 LAYOUT_PIVOT, LAYOUT_DIAG = 0, 1
 (K_DUAL, K_PRIMAL, K_FUSED, K_POTENTIAL, K_FFBS, K_ACCUMULATE, K_FEATURES, K_MLP, K_MH, K_SMALL,
  K_SW_BOND, K_SW_FLATTEN, K_SW_DRAW, K_SW_SMALL, K_COUNT) = range(15)
@@ -66,6 +66,7 @@ _SIGS = {
     "mrf_set_kernel_timing": (ct.c_int, [_P, ct.c_int32]),
     "mrf_estimate_log_partition": (ct.c_int, [_P, ct.c_int32, _P]),
     "mrf_estimate_log_partition_sw": (ct.c_int, [_P, ct.c_int32, _P]),
+    "mrf_set_higdon": (ct.c_int, [_P, ct.c_double]),
     "mrf_map_em": (ct.c_int, [_P, ct.c_int32, _P, ct.c_int32]),
     "mrf_save": (ct.c_int, [_P, ct.c_char_p]),
     "mrf_load": (ct.c_int, [ct.POINTER(_P), ct.c_char_p, _P]),
@@ -216,6 +217,10 @@ class MRF:
     # -- sampling
     def sweep(self, n: int = 1, mode: int = MODE_PLAIN):
         self._check(self.lib.mrf_sweep(self.h, int(n), int(mode)))
+
+    def set_higdon(self, rho: float):
+        """Fraction rho of Higdon's partial Swendsen-Wang sweep (MODE_HIGDON)."""
+        self._check(self.lib.mrf_set_higdon(self.h, float(rho)))
 
     def reset_marginals(self, burn_in: int = 0):
         self._check(self.lib.mrf_reset_marginals(self.h, int(burn_in)))
