@@ -208,12 +208,13 @@ def run_ours(args, ws, rank, local):
         model = gen()
     if "%g" in desc:
         desc = desc % (FERRO_BETA[0], FERRO_BETA[1], FERRO_U_STD)
-    mode = {"plain": M.MODE_PLAIN, "fused": M.MODE_FUSED, "sw": M.MODE_SW}[args.mode]
+    mode = {"plain": M.MODE_PLAIN, "fused": M.MODE_FUSED, "sw": M.MODE_SW, "higdon": M.MODE_HIGDON}[args.mode]
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         h = M.MRF(model.n_vars, model.n_labels, C, seed=rank_seed(args.seed, rank), stream=stream.cuda_stream,
                   kernel_timing=True, grid=model.grid if model.grid else None)
         h.set_factors(model.unary, model.src, model.dst, model.pair)
+    h.set_higdon(args.higdon_rho)
     inf = h.info()
     minfo = dict(E=inf.n_edge_slots, N=inf.n_vars, L=inf.n_labels, m=inf.n_entries)
     # warm-up
@@ -290,7 +291,8 @@ def run_ours(args, ws, rank, local):
             sw_ok = False
         forms = [(n, md) for n, md in (("plain", M.MODE_PLAIN), ("fused", M.MODE_FUSED)) if n != args.mode] + \
             ([("splash", M.MODE_SPLASH)] if model.grid else []) + \
-            ([("sw", M.MODE_SW)] if sw_ok and args.mode != "sw" else [])
+            ([("sw", M.MODE_SW)] if sw_ok and args.mode != "sw" else []) + \
+            ([("higdon", M.MODE_HIGDON)] if sw_ok and args.mode != "higdon" else [])
         for name, md in forms:
             h.sweep(1, md)
             h.kernel_times()
@@ -322,7 +324,7 @@ def run_ours(args, ws, rank, local):
             ms_of.update({k: v["ms_per_step"] for k, v in variants.items() if "ms_per_step" in v})
             variants["ess"] = ess_comparison(h, model, C, stream, args.ess_sweeps, ms_of,
                                              [("plain", M.MODE_PLAIN)] + ([("splash", M.MODE_SPLASH)] if model.grid else [])
-                                             + ([("sw", M.MODE_SW)] if sw_ok else []))
+                                             + ([("sw", M.MODE_SW), ("higdon", M.MODE_HIGDON)] if sw_ok else []))
 
     # end to end through the C ABI with pinned host buffers: labels in, sweep, labels out
     e2e = None
@@ -404,6 +406,7 @@ class OracleSample:
         self.model = model
         self.dec = dc.decompose(model)
         self.mode = args.mode
+        self.higdon_rho = args.higdon_rho
         self.sw_tables = None
         self.seed = args.seed
         self.x = ph.init_labels(model.n_vars, model.n_labels, self.C, args.seed)
@@ -417,6 +420,12 @@ class OracleSample:
             if self.sw_tables is None:
                 self.sw_tables = swendsen_wang.sw_tables(self.model)
             self.x = swendsen_wang.sw_sweep(self.model, self.x, self.t, self.seed, tables=self.sw_tables)["x"]
+        elif self.mode == "higdon":
+            from oracle import higdon
+            if self.sw_tables is None:
+                self.sw_tables = higdon.higdon_split(self.model, self.higdon_rho)
+            self.x = higdon.higdon_sweep(self.model, self.x, self.higdon_rho, self.t, self.seed,
+                                         split=self.sw_tables)["x"]
         else:
             self.x = sampler.sweep(self.dec, self.x, self.t, self.seed)["x"]
         self.t += 1
@@ -733,7 +742,8 @@ def main():
     ap.add_argument("--workload", default="potts3d", choices=list(WORKLOADS) + ["er_batch", "ba_learned"])
     ap.add_argument("--ref-sweeps", type=int, default=2000)
     ap.add_argument("--ess-sweeps", type=int, default=200)
-    ap.add_argument("--mode", default="plain", choices=["plain", "fused", "sw"])
+    ap.add_argument("--mode", default="plain", choices=["plain", "fused", "sw", "higdon"])
+    ap.add_argument("--higdon-rho", type=float, default=0.5, help="bond fraction of the Higdon sweep")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--scale", type=int, default=0, help="lattice edge for potts3d and ferro3d (default 128)")
     ap.add_argument("--ferro-beta", default=None, help="lo,hi of the ferro3d couplings (default %g,%g)" % FERRO_BETA)
