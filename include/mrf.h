@@ -281,8 +281,9 @@ mrf_status mrf_map_em_blocked(mrf_t* h, int32_t n_iters, uint8_t* labels, int32_
 mrf_status mrf_mean_field(mrf_t* h, int32_t n_iters, float* marginals, int32_t ptr_kind);
 
 /* Checkpoint of a handle to a file: the model's device tables (unaries,
- * edge slots, decomposition tables), the labels of every chain, the marginal
- * counts and the sweep index, so that mrf_load resumes the same chains: the
+ * edge slots, decomposition and Swendsen-Wang tables), Higdon's fraction,
+ * the labels of every chain, the marginal counts and the sweep index, so
+ * that mrf_load resumes the same chains: the
  * sweeps after a load are the ones the saved handle would have run, bit for
  * bit.  The learned proposal is not saved (set it up again after a load).
  * Errors: MRF_ESTATE before mrf_set_factors, MRF_EINVAL if the file cannot be

@@ -1068,6 +1068,7 @@ struct CkptHeader {
     uint64_t seed;
     double log_const;
     int32_t has_resid, has_sw;
+    double hg_rho;                     // fraction of Higdon's sweep
     mrf_options opt;
     Ctl ctl;
 };
@@ -1103,6 +1104,7 @@ mrf_status mrf_save(mrf_t* h, const char* path) {
     hd.sweep_host = h->sweep_host; hd.count_from_host = h->count_from_host; hd.seed = h->seed; hd.log_const = h->log_const;
     hd.has_resid = h->d_resid ? 1 : 0;
     hd.has_sw = (h->d_swt ? 1 : 0) | (h->d_swfold ? 2 : 0);
+    hd.hg_rho = h->hg_rho;
     hd.opt = h->opt;
     MRF_CUDA(h, cudaMemcpyAsync(&hd.ctl, h->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -1204,6 +1206,7 @@ mrf_status mrf_load(mrf_t** out, const char* path, void* cuda_stream) {
     }
     h->sweep_host = hd.sweep_host;
     h->count_from_host = hd.count_from_host;
+    h->hg_rho = (hd.hg_rho >= 0.0 && hd.hg_rho <= 1.0) ? hd.hg_rho : 0.5;
     h->log_const = hd.log_const;
     h->has_factors = true;
     h->schedule = 0;

@@ -141,3 +141,20 @@ def test_higdon_errors():
         h.sweep(1, M.MODE_HIGDON)
     assert e.value.status == M.MRF_EINVAL
     h.close()
+
+
+def test_higdon_resumes_from_checkpoint(tmp_path):
+    model = wl.ferro_potts_graph(300, 5, 900, seed=56)
+    C, seed = 32, 57
+    h = make_handle(model, C, seed)
+    h.set_higdon(0.35)
+    h.sweep(2, M.MODE_HIGDON)
+    path = str(tmp_path / "hg.ckpt")
+    h.save(path)
+    h.sweep(3, M.MODE_HIGDON)
+    want = h.get_labels()
+    h.close()
+    g = M.MRF.load(path)                                            # the fraction travels with the checkpoint
+    g.sweep(3, M.MODE_HIGDON)
+    assert np.array_equal(g.get_labels(), want)
+    g.close()
