@@ -23,14 +23,15 @@
 //   k_sw_assign   bonded non-roots copy the root's label; rows, parents and
 //                 ban words of bonded sites are reset.
 // Unaries enter as fixed-point values precomputed once per factor change.
+// Higdon's partial Swendsen-Wang (k_hg_*) runs the same kernels with its own
+// bond tables and per-chain potentials in place of the unaries; small models
+// run whole Swendsen-Wang sweeps in one single-CTA launch (k_sw_small).
 // The union-find is lock-free: a link always points from a root to a smaller
 // site (atomicCAS on the root's entry), so every walk visits strictly
 // decreasing sites and ends within N steps; a walk that exceeds that bound
 // sets the error flag instead of looping (the host then resets the state).
 // The forest of a chain is its own column of parent[][], so chains never
 // contend.
-#include <cooperative_groups.h>
-
 #include "sweep_impl.cuh"   // draw_label
 
 namespace mrfk {
