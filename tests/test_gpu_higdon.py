@@ -158,3 +158,31 @@ def test_higdon_resumes_from_checkpoint(tmp_path):
     g.sweep(3, M.MODE_HIGDON)
     assert np.array_equal(g.get_labels(), want)
     g.close()
+
+
+@pytest.mark.parametrize("L", [4, 2])
+def test_higdon_after_edits_uses_slot_ids(L):
+    """Edits grow the edge slots past the tables' capacity and leave free slots;
+    the split is rebuilt and the RNG index of an edge is its slot."""
+    model = wl.ferro_potts_graph(300, 4, 1000, seed=58) if L == 4 else _two_labels(300, 1000, 59)
+    C, seed, rho = 16, 60, 0.6
+    h = make_handle(model, C, seed)
+    h.set_higdon(rho)
+    h.sweep(1, M.MODE_HIGDON)
+    rng = np.random.default_rng(4)
+    rem = np.sort(rng.choice(model.n_edges, size=100, replace=False))
+    add = wl.ferro_potts_graph(300, 4, 400, seed=61) if L == 4 else _two_labels(300, 400, 62)
+    ids = h.edit_factors(rem, add.src, add.dst, add.pair)           # 300 fresh slots beyond the first 1000
+    src = np.concatenate([model.src, np.zeros(300, model.src.dtype)])
+    dst = np.concatenate([model.dst, np.zeros(300, model.dst.dtype)])
+    pair = np.concatenate([model.pair, np.zeros((300,) + model.pair.shape[1:], model.pair.dtype)])
+    src[ids] = add.src; dst[ids] = add.dst; pair[ids] = add.pair
+    live = np.ones(src.size, bool); live[rem] = False; live[ids] = True
+    slots = np.nonzero(live)[0]
+    edited = wl.Model(model.n_vars, L, model.unary, src[slots], dst[slots], pair[slots])
+    for _ in range(2):
+        t = h.info().sweep_index
+        x0 = h.get_labels().astype(np.int64)
+        h.sweep(1, M.MODE_HIGDON)
+        compare_higdon(edited, hg.higdon_sweep(edited, x0, rho, t, seed, edge_ids=slots), h.get_labels())
+    h.close()
