@@ -292,6 +292,8 @@ cudaError_t launch_sw_flatten(const SwArgs& a, cudaStream_t s);
 cudaError_t launch_sw_draw(const SwArgs& a, cudaStream_t s);
 int64_t sw_small_smem(const SwArgs& a);
 cudaError_t launch_sw_small(const SwArgs& a, int n_sweeps, cudaStream_t s);
+int64_t hg_small_smem(const SwArgs& a);
+cudaError_t launch_hg_small(const SweepArgs& d, const SwArgs& a, int n_sweeps, cudaStream_t s);
 cudaError_t launch_labels_to_abi(const uint8_t* x, uint8_t* y, int N, int C, cudaStream_t s);
 cudaError_t launch_labels_from_abi(const uint8_t* y, uint8_t* x, int N, int C, cudaStream_t s);
 cudaError_t launch_count_ge(const uint8_t* y, int64_t n, int L, unsigned long long* bad, cudaStream_t s);

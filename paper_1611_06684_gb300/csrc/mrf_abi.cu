@@ -791,6 +791,18 @@ static mrf_status hg_prepare(mrf_t* h) {
     return MRF_OK;
 }
 
+// Arguments of Higdon's sweep: the remainder's tables in the dual and
+// potential kernels, the bond tables and per-chain potentials in the cluster
+// kernels.
+static void make_hg_args(const mrf_t* h, SweepArgs& d, SwArgs& w) {
+    w = make_sw_args(h);
+    w.thr = h->d_hgT; w.lwe = h->d_hglb; w.pot = h->d_pot;
+    d = make_args(h);
+    d.M = h->L; d.W = 1; d.tau = h->d_hgtau; d.thr = h->d_hgthr; d.tpl = h->d_hgtpl;
+    d.utf = h->d_hgutf; d.ut = h->d_hgut; d.tie_cap = tie_cap_for(h->L); d.logp = nullptr; d.lpv = nullptr;
+    d.pot = h->d_pot;
+}
+
 static mrf_status enqueue_sweep(mrf_t* h, int mode) {
     SweepArgs a = make_args(h);
     cudaStream_t s = h->stream;
@@ -808,12 +820,9 @@ static mrf_status enqueue_sweep(mrf_t* h, int mode) {
     } else if (mode == MRF_MODE_HIGDON) {
         // bonds (and their unions), A's bits of the other edges, the bits'
         // potentials, then the clusters as in the Swendsen-Wang sweep
-        SwArgs w = make_sw_args(h);
-        w.thr = h->d_hgT; w.lwe = h->d_hglb; w.pot = h->d_pot;
-        SweepArgs d = a;
-        d.M = h->L; d.W = 1; d.tau = h->d_hgtau; d.thr = h->d_hgthr; d.tpl = h->d_hgtpl;
-        d.utf = h->d_hgutf; d.ut = h->d_hgut; d.tie_cap = tie_cap_for(h->L); d.logp = nullptr; d.lpv = nullptr;
-        d.pot = h->d_pot;
+        SweepArgs d;
+        SwArgs w;
+        make_hg_args(h, d, w);
         e = timed(h, MRF_K_SW_BOND, [&] { return launch_sw_bond(w, s); });
         if (e == cudaSuccess) e = timed(h, MRF_K_DUAL, [&] {
             const cudaError_t e2 = launch_dual(d, MRF_LAYOUT_DIAG, s);
@@ -852,6 +861,16 @@ mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode) {
     if (mode == MRF_MODE_HIGDON) {
         mrf_status st = hg_prepare(h);
         if (st != MRF_OK) return st;
+        // small models: all the sweeps in one single-CTA launch, state and bits in shared memory
+        SweepArgs d;
+        SwArgs w;
+        make_hg_args(h, d, w);
+        if (n_sweeps >= 2 && (int64_t)h->N * h->C <= 65536 && h->E_slots * h->C <= 65536 &&
+            hg_small_smem(w) <= 200 * 1024) {
+            MRF_CUDA(h, timed(h, MRF_K_SW_SMALL, [&] { return launch_hg_small(d, w, n_sweeps, h->stream); }));
+            h->sweep_host += n_sweeps;
+            return sw_check_error(h);
+        }
     }
     if (mode == MRF_MODE_SW) {
         mrf_status st = sw_prepare(h);

@@ -518,6 +518,184 @@ __global__ void k_hg_clear(const uint32_t* __restrict__ bits, uint32_t* __restri
     }
 }
 
+// Small models, Higdon's sweep: n_sweeps whole sweeps in one single-CTA
+// launch, the remainder's dual bits, the union-find state and the cluster
+// rows in shared memory.  The bonds, bits (the dual contract of k_dual,
+// decided by dual_bits), potentials (summed in the incidence order of the
+// primal kernels, flushed every 32 incidences) and exact cluster sums are
+// those of the launch-per-step path, hence the same chain bit for bit.
+template <int L>
+__global__ void __launch_bounds__(1024) k_hg_small(SweepArgs d, SwArgs a, int n_sweeps) {
+    using En = Ent<L, MRF_LAYOUT_DIAG>;
+    extern __shared__ int64_t s_lw[];                                  // [N][L][C]
+    const int64_t nv = (int64_t)a.N * a.C, ne = a.E * a.C;
+    int32_t* s_par = reinterpret_cast<int32_t*>(s_lw + nv * L);       // [N][C]
+    int32_t* s_root = s_par + nv;                                     // [N][C]
+    uint32_t* s_ban = reinterpret_cast<uint32_t*>(s_root + nv);       // [N][C]
+    uint32_t* s_theta = s_ban + nv;                                   // [E][C] remainder's bits
+    volatile int32_t* vpar = s_par;
+    for (int64_t g = threadIdx.x; g < nv; g += blockDim.x) {
+        s_par[g] = (int32_t)a.fdC.div((uint32_t)g);
+        s_ban[g] = 0u;
+    }
+    for (int64_t i = threadIdx.x; i < nv * L; i += blockDim.x) s_lw[i] = 0;
+    __syncthreads();
+    uint32_t sweep = (uint32_t)a.ctl->sweep;
+    const unsigned long long count_from = a.ctl->count_from;
+    for (int it = 0; it < n_sweeps; ++it, ++sweep) {
+        const uint8_t* xin = a.x + (size_t)(sweep & 1) * a.N * a.C;
+        uint8_t* xout = a.x + (size_t)((sweep + 1) & 1) * a.N * a.C;
+        // bonds (with their unions) or the remainder's bits, per (edge, chain)
+        for (int64_t g = threadIdx.x; g < ne; g += blockDim.x) {
+            const int64_t e = a.fdC.div((uint32_t)g);
+            const int32_t c = (int32_t)(g - e * a.C);
+            const int32_t s = a.src[e];
+            s_theta[g] = 0u;
+            if (s < 0) continue;
+            const int32_t t = a.dst[e];
+            const int xs = xin[pidx(s, c, a.C)], xt = xin[pidx(t, c, a.C)];
+            bool bond = false;
+            if (xs == xt) {
+                const uint32_t T = a.thr[e * L + xs];
+                bond = T != 0u && (draw_rk((uint32_t)e, sweep, (uint32_t)c, PH_BOND, 0, a.rk).x >> 9) < T;
+            }
+            if (!bond) {
+                uint32_t bits[En::W];
+                dual_bits<L, MRF_LAYOUT_DIAG>((uint32_t)e, (uint32_t)c, xs, xt, d.tpl + e * En::W * 32, d.thr + e * En::M,
+                                              sweep, d.rk, bits);
+                s_theta[g] = bits[0];
+                continue;
+            }
+            int32_t ra = s, rb = t;
+            bool linked = false;
+            for (int32_t step = 0; step <= a.N && !linked; ++step) {
+                ra = sws_find(vpar, ra, c, a.C, a.N);
+                rb = sws_find(vpar, rb, c, a.C, a.N);
+                if (ra < 0 || rb < 0) break;
+                if (ra == rb) { linked = true; break; }
+                if (ra < rb) { const int32_t t2 = ra; ra = rb; rb = t2; }
+                linked = atomicCAS(s_par + pidx(ra, c, a.C), ra, rb) == ra;
+            }
+            if (!linked) { atomicOr(a.err, 1u); continue; }
+            int64_t wv[L];
+#pragma unroll
+            for (int x = 0; x < L; ++x) wv[x] = __ldg(a.lwe + e * L + x);
+            bool uniform = wv[0] != kSwNoLabel;
+#pragma unroll
+            for (int x = 1; x < L; ++x) uniform &= wv[x] == wv[0];
+            uint32_t flags = kSwBonded;
+            if (!uniform) {
+                flags |= kSwRow;
+#pragma unroll
+                for (int x = 0; x < L; ++x) {
+                    if (wv[x] == kSwNoLabel) flags |= 1u << x;
+                    else atomicAdd(reinterpret_cast<unsigned long long*>(s_lw + ((int64_t)s * L + x) * a.C + c),
+                                   (unsigned long long)wv[x]);
+                }
+            }
+            atomicOr(s_ban + pidx(s, c, a.C), flags);
+            atomicOr(s_ban + pidx(t, c, a.C), kSwBonded);
+        }
+        __syncthreads();
+        // potentials of every site, moved into the rows of the cluster roots
+        for (int64_t g = threadIdx.x; g < nv; g += blockDim.x) {
+            const int32_t v = (int32_t)a.fdC.div((uint32_t)g), c = (int32_t)(g - (int64_t)v * a.C);
+            float acc[L], hi[L], lo[L];
+#pragma unroll
+            for (int x = 0; x < L; ++x) { acc[x] = 0.0f; hi[x] = 0.0f; lo[x] = 0.0f; }
+            int chunk = 0;
+            bool flushed = false;
+            for (int64_t p = d.inc_ptr[v]; p < d.inc_ptr[v + 1]; ++p) {
+                const int2 ic = __ldg(&d.inc[p]);
+                const int64_t e = ic.x >> 1;
+                const uint32_t bits[En::W] = {s_theta[e * a.C + c]};
+                add_side<L, MRF_LAYOUT_DIAG>(bits, d.tau + e * En::MP, ic.x & 1, acc);
+                if (++chunk == 32) {
+#pragma unroll
+                    for (int x = 0; x < L; ++x) { two_sum_add(hi[x], lo[x], acc[x]); acc[x] = 0.0f; }
+                    chunk = 0;
+                    flushed = true;
+                }
+            }
+            int64_t w[L];
+            const float* uf = d.utf + (int64_t)v * L;
+#pragma unroll
+            for (int x = 0; x < L; ++x) {
+                float F;
+                if (flushed) { two_sum_add(hi[x], lo[x], acc[x]); F = __ldg(uf + x) + (hi[x] + lo[x]); }
+                else F = __ldg(uf + x) + acc[x];
+                w[x] = fix_from_float(F);
+            }
+            const uint32_t b = s_ban[g];
+            int32_t r = v;
+            if (b & kSwBonded) {
+                r = sws_find(vpar, v, c, a.C, a.N);
+                if (r < 0) { atomicOr(a.err, 1u); r = v; }
+                s_root[g] = r;
+                if (r != v && (b & kSwRow)) {
+#pragma unroll
+                    for (int x = 0; x < L; ++x) w[x] += s_lw[((int64_t)v * L + x) * a.C + c];
+                }
+                if (r != v && (b & kSwLabelMask)) atomicOr(s_ban + pidx(r, c, a.C), b & kSwLabelMask);
+            }
+#pragma unroll
+            for (int x = 0; x < L; ++x)
+                atomicAdd(reinterpret_cast<unsigned long long*>(s_lw + ((int64_t)r * L + x) * a.C + c),
+                          (unsigned long long)w[x]);
+        }
+        __syncthreads();
+        // labels of the roots
+        for (int64_t g = threadIdx.x; g < nv; g += blockDim.x) {
+            const int32_t v = (int32_t)a.fdC.div((uint32_t)g), c = (int32_t)(g - (int64_t)v * a.C);
+            const uint32_t b = s_ban[g];
+            if ((b & kSwBonded) && s_root[g] != v) continue;
+            int64_t w[L];
+#pragma unroll
+            for (int x = 0; x < L; ++x) w[x] = s_lw[((int64_t)v * L + x) * a.C + c];
+            int64_t mx = 0;
+            bool any = false;
+#pragma unroll
+            for (int x = 0; x < L; ++x)
+                if (!((b >> x) & 1u) && (!any || w[x] > mx)) { mx = w[x]; any = true; }
+            float F[L];
+#pragma unroll
+            for (int x = 0; x < L; ++x) F[x] = ((b >> x) & 1u) ? -INFINITY : sw_float(w[x] - mx);
+            xout[g] = (uint8_t)draw_label<L>(F, (uint32_t)v, (uint32_t)c, sweep, a.rk, PH_CLUSTER, nullptr, a.ctl);
+        }
+        __syncthreads();
+        // labels of the other sites, state reset (every root's row holds sums now)
+        for (int64_t g = threadIdx.x; g < nv; g += blockDim.x) {
+            const int32_t v = (int32_t)a.fdC.div((uint32_t)g), c = (int32_t)(g - (int64_t)v * a.C);
+            const uint32_t b = s_ban[g];
+            const int32_t r = (b & kSwBonded) ? s_root[g] : v;
+            if (r != v) xout[g] = xout[pidx(r, c, a.C)];
+            if (r == v || (b & kSwRow)) {
+#pragma unroll
+                for (int x = 0; x < L; ++x) s_lw[((int64_t)v * L + x) * a.C + c] = 0;
+            }
+            s_par[g] = v;
+            s_ban[g] = 0u;
+        }
+        __syncthreads();
+        if (sweep >= count_from) {
+            for (int64_t v = threadIdx.x; v < a.N; v += blockDim.x) {
+                uint32_t tot[L];
+#pragma unroll
+                for (int x = 0; x < L; ++x) tot[x] = 0;
+                for (int c = 0; c < a.C; ++c) {
+                    const int x = xout[v * a.C + c];
+#pragma unroll
+                    for (int y = 0; y < L; ++y) tot[y] += x == y ? 1u : 0u;
+                }
+#pragma unroll
+                for (int x = 0; x < L; ++x) a.counts[v * L + x] += tot[x];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a.ctl->sweep = sweep;
+}
+
 // Model check before the first Swendsen-Wang sweep after the factors change:
 // out[0] = dual weights tau < 0 on live edges (antiferromagnetic entries; with
 // two labels the one pivot entry's tau has the sign of l),
@@ -645,6 +823,23 @@ cudaError_t launch_sw_small(const SwArgs& a, int n_sweeps, cudaStream_t s) {
             if (e != cudaSuccess) return e;
         }
         k_sw_small<LL><<<1, 1024, smem, s>>>(a, n_sweeps);
+    }));
+    return cudaGetLastError();
+}
+
+int64_t hg_small_smem(const SwArgs& a) { return (int64_t)a.N * a.C * (12 + 8 * a.L) + a.E * a.C * 4; }
+
+cudaError_t launch_hg_small(const SweepArgs& d, const SwArgs& a, int n_sweeps, cudaStream_t s) {
+    if (!a.counts || !a.ufix || !a.err || !a.ctl || !a.x || !d.utf || !d.inc_ptr ||
+        (a.E > 0 && (!a.src || !a.dst || !a.thr || !a.lwe || !d.tau || !d.thr || !d.tpl || !d.inc)))
+        return cudaErrorInvalidValue;
+    const size_t smem = (size_t)hg_small_smem(a);
+    MRF_DISPATCH_LSW(a.L, ({
+        if (smem > 48 * 1024) {
+            const cudaError_t e = cudaFuncSetAttribute(k_hg_small<LL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k_hg_small<LL><<<1, 1024, smem, s>>>(d, a, n_sweeps);
     }));
     return cudaGetLastError();
 }

@@ -186,3 +186,32 @@ def test_higdon_after_edits_uses_slot_ids(L):
         h.sweep(1, M.MODE_HIGDON)
         compare_higdon(edited, hg.higdon_sweep(edited, x0, rho, t, seed, edge_ids=slots), h.get_labels())
     h.close()
+
+
+SMALL = {
+    "ising_C4": (lambda: wl.ising_grid(24, 20, j_lo=0.2, j_hi=0.9, seed=32), 4, 0.9),
+    "graph_L4_C37": (lambda: wl.ferro_potts_graph(80, 4, 200, seed=1), 37, 0.3),
+    "zero_entries_L5_C33": (lambda: wl.ferro_potts_graph(60, 5, 150, p_zero=0.3, seed=4), 33, 0.6),
+}
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_higdon_small_model_kernel_is_the_same_chain(name):
+    """n >= 2 Higdon sweeps of a small model run in one single-CTA launch; the
+    chain, counts and sweep index equal those of one sweep per call."""
+    make, C, rho = SMALL[name]
+    model = make()
+    seed = 63
+    one = make_handle(model, C, seed)
+    many = make_handle(model, C, seed, kernel_timing=True)
+    for h in (one, many):
+        h.set_higdon(rho)
+        h.reset_marginals(2)
+    for _ in range(7):
+        one.sweep(1, M.MODE_HIGDON)
+    many.sweep(7, M.MODE_HIGDON)
+    assert "k_sw_small" in many.kernel_times()                     # the single-CTA kernel ran
+    assert np.array_equal(one.get_labels(), many.get_labels())
+    assert np.array_equal(one.counts(), many.counts())
+    assert one.info().sweep_index == many.info().sweep_index == 7
+    one.close(); many.close()

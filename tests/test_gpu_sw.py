@@ -310,20 +310,27 @@ def test_sw_estimator_moments_match_enumeration():
     assert e_logv < logZ and mi > 0
 
 
-@pytest.mark.parametrize("name", ["ising32_C1", "graph_L4_C37", "zero_entries_L5_C33"])
+SMALL = {
+    "ising32_C1": (lambda: wl.ising_grid(32, 32, seed=0), 1),
+    "graph_L4_C37": (lambda: wl.ferro_potts_graph(80, 4, 200, seed=1), 37),
+    "zero_entries_L5_C33": (lambda: wl.ferro_potts_graph(60, 5, 150, p_zero=0.3, seed=4), 33),
+}
+
+
+@pytest.mark.parametrize("name", list(SMALL))
 def test_sw_small_model_kernel_is_the_same_chain(name):
     """n >= 2 sweeps of a small model run in one single-CTA launch; the chain,
     counts and sweep index equal those of one sweep per call."""
-    model, C = CASES[name][0](), CASES[name][1]
-    assert model.n_vars * C <= 65536 and model.n_edges * C <= 65536
+    model, C = SMALL[name][0](), SMALL[name][1]
     seed = 49
     one = make_handle(model, C, seed)
-    many = make_handle(model, C, seed)
+    many = make_handle(model, C, seed, kernel_timing=True)
     for h in (one, many):
         h.reset_marginals(2)
     for _ in range(7):
         one.sweep(1, M.MODE_SW)
     many.sweep(7, M.MODE_SW)
+    assert "k_sw_small" in many.kernel_times()                     # the single-CTA kernel ran
     assert np.array_equal(one.get_labels(), many.get_labels())
     assert np.array_equal(one.counts(), many.counts())
     assert one.info().sweep_index == many.info().sweep_index == 7
