@@ -61,6 +61,8 @@ CASES = {
     "L16_C32": (lambda: wl.ferro_potts_graph(60, 16, 150, seed=5), 32),
     "isolated_sites_L4_C7": (lambda: wl.ferro_potts_graph(80, 4, 30, seed=6), 7),
     "no_edges_C4": (_no_edges, 4),
+    # every coupling zero: no bond can form, each site is its own cluster
+    "zero_couplings_L3_C32": (lambda: wl.ferro_potts_graph(150, 3, 400, beta_lo=0.0, beta_hi=0.0, seed=8), 32),
 }
 
 
