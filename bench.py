@@ -153,10 +153,11 @@ def kernel_work(name, model_info, C):
 
 
 # DRAM bytes of the dual step (k_dual + k_dual_ties) per (edge, chain) item,
-# from the ncu capture of the 64^3 L = 8, 64-chain case (1,146.5 MB per launch
-# pair for 774,144 x 64 items); traffic grows with the items, so it is scaled
-# to the bench's launch.  Valid for m = 49 entries and 64 chains only.
-DUAL_DRAM_BYTES_PER_ITEM = {(49, 64): 1146.5e6 / (774144 * 64)}
+# from the ncu counters of the 64^3 L = 8, 64-chain case with the current
+# kernels (1,142.0 MB per launch pair for 774,144 x 64 items); traffic grows
+# with the items, so it is scaled to the bench's launch.  Valid for m = 49
+# entries and 64 chains only.
+DUAL_DRAM_BYTES_PER_ITEM = {(49, 64): 1142.0e6 / (774144 * 64)}
 
 # kernels behind one kernel-timing record of the library
 KERNELS_PER_RECORD = {"k_dual": 2, "k_sw_draw": 2}
