@@ -258,6 +258,13 @@ mrf_status mrf_estimate_log_partition(mrf_t* h, int32_t n_sweeps, double* log_v)
  * mrf_estimate_log_partition. */
 mrf_status mrf_estimate_log_partition_sw(mrf_t* h, int32_t n_sweeps, double* log_v);
 
+/* The same estimator on Higdon's duality (MRF_MODE_HIGDON sweeps at the
+ * fraction of mrf_set_higdon): log V = log p~(x) - sum_clusters
+ * log p(x_cluster | bonds, remainder's bits).  The joint is again zero where
+ * a bond joins unequal labels (for rho > 0), so E[log V] = log Z - I(x; theta)
+ * is the lower bound to use.  Requirements as for mrf_estimate_log_partition_sw. */
+mrf_status mrf_estimate_log_partition_higdon(mrf_t* h, int32_t n_sweeps, double* log_v);
+
 /* Primal-dual EM (local MAP, Section 5.3): n_iters iterations of
  *   xi = E[r(theta) | x]  (pi_k = sigmoid(q_k + beta1_k [x_s = i_k] + beta2_k [x_t = j_k]))
  *   x  = argmax_x h(x) exp(<s(x), xi>)  (per site: the first label of largest field)

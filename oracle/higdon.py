@@ -30,11 +30,15 @@ BOND) against rho (1 - e^{-l}); A's bits by the dual-bit contract of the
 plain sweep (phase DUAL); cluster labels by the inverse CDF with the 23-bit
 uniform of Philox(smallest site of the cluster, t, c, CLUSTER).
 
+log_v: Section 5.2's estimator log V = log p~(x) - log p(x | theta) on this
+duality, for the labels a sweep draws given its duals.
+
 Pins (tests/test_oracle_higdon.py): the split reproduces every factor; by
 enumeration of the three-state duals, the joint marginalises to p~(x), the
 bond and bit probabilities given x and the cluster rule given the duals are
 the joint's conditionals, and the kernel leaves p invariant; rho = 1 gives
-the Swendsen-Wang weights; chain marginals within 3 sigma of exact.
+the Swendsen-Wang weights; chain marginals within 3 sigma of exact; log V:
+E[log V] = log Z - I(x; theta) under the joint (enumeration).
 """
 from __future__ import annotations
 
@@ -86,6 +90,26 @@ def cluster_log_weights(model, split, bonds_c, field_c):
     if sel.size:
         np.add.at(lw, root[src[sel]], bond_log_weights(alpha, dec)[sel])
     return root, lw
+
+
+def log_v(model, x, bonds, theta, split):
+    """Section 5.2's estimator on this duality, per chain:
+    log V = log p~(x) - log p(x | bonds, bits), p(x | .) the product over the
+    clusters of the probability of the cluster's label (+inf where x is not
+    constant on a cluster).  x [C][N], bonds [C][E], theta [C][E][L] (A's bits)."""
+    from .swendsen_wang import log_ptilde
+    alpha, dec = split
+    x = np.asarray(x, np.int64)
+    F = primal_field(dec, np.asarray(theta) & ~np.asarray(bonds)[:, :, None])
+    out = log_ptilde(model, x)
+    for c in range(x.shape[0]):
+        root, lw = cluster_log_weights(model, split, bonds[c], F[c])
+        if np.any(x[c] != x[c][root]):
+            out[c] = np.inf
+            continue
+        rs = np.unique(root)
+        out[c] -= log_softmax(lw[rs])[np.arange(rs.size), x[c][rs]].sum()
+    return out
 
 
 def higdon_sweep(model, x, rho: float, sweep_index: int, seed: int, edge_ids=None, chain_ids=None, split=None):

@@ -951,8 +951,8 @@ static mrf_status estimate_log_partition(mrf_t* h, int32_t n_sweeps, int mode, d
     if (!h->has_factors) return fail(h, MRF_ESTATE, "mrf_set_factors first");
     if (!h->d_resid) return fail(h, MRF_ESTATE, "the estimator needs exact edge tables (options.grid or options.exact_edges)");
     if (n_sweeps == 0) return MRF_OK;
-    if (mode == MRF_MODE_SW) {
-        mrf_status st = sw_prepare(h);
+    if (mode == MRF_MODE_SW || mode == MRF_MODE_HIGDON) {
+        mrf_status st = mode == MRF_MODE_SW ? sw_prepare(h) : hg_prepare(h);
         if (st != MRF_OK) return st;
     } else if (h->schedule == 0) {
         mrf_status st = tune_schedule(h);
@@ -979,7 +979,7 @@ static mrf_status estimate_log_partition(mrf_t* h, int32_t n_sweeps, int mode, d
     MRF_CUDA(h, cudaMemcpyAsync(log_v, h->d_logv, sizeof(double) * (size_t)n_sweeps * h->C, cudaMemcpyDeviceToHost,
                                 h->stream));
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));
-    if (mode == MRF_MODE_SW) return sw_check_error(h);
+    if (mode == MRF_MODE_SW || mode == MRF_MODE_HIGDON) return sw_check_error(h);
     return MRF_OK;
 }
 
@@ -996,6 +996,10 @@ mrf_status mrf_estimate_log_partition(mrf_t* h, int32_t n_sweeps, double* log_v)
 
 mrf_status mrf_estimate_log_partition_sw(mrf_t* h, int32_t n_sweeps, double* log_v) {
     return estimate_log_partition(h, n_sweeps, MRF_MODE_SW, log_v);
+}
+
+mrf_status mrf_estimate_log_partition_higdon(mrf_t* h, int32_t n_sweeps, double* log_v) {
+    return estimate_log_partition(h, n_sweeps, MRF_MODE_HIGDON, log_v);
 }
 
 mrf_status mrf_map_em(mrf_t* h, int32_t n_iters, uint8_t* labels, int32_t ptr_kind) {

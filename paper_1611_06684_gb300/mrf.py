@@ -67,6 +67,7 @@ _SIGS = {
     "mrf_estimate_log_partition": (ct.c_int, [_P, ct.c_int32, _P]),
     "mrf_estimate_log_partition_sw": (ct.c_int, [_P, ct.c_int32, _P]),
     "mrf_set_higdon": (ct.c_int, [_P, ct.c_double]),
+    "mrf_estimate_log_partition_higdon": (ct.c_int, [_P, ct.c_int32, _P]),
     "mrf_map_em": (ct.c_int, [_P, ct.c_int32, _P, ct.c_int32]),
     "mrf_save": (ct.c_int, [_P, ct.c_char_p]),
     "mrf_load": (ct.c_int, [ct.POINTER(_P), ct.c_char_p, _P]),
@@ -337,11 +338,13 @@ class MRF:
 
     def estimate_log_partition(self, n_sweeps: int, mode: int = MODE_PLAIN):
         """log V [n_sweeps][C] of Section 5.2's estimator over n plain (or, with
-        mode=MODE_SW, Swendsen-Wang) sweeps."""
+        mode=MODE_SW / MODE_HIGDON, Swendsen-Wang / Higdon) sweeps."""
         out = np.zeros((int(n_sweeps), self.C), np.float64)
-        fn = self.lib.mrf_estimate_log_partition_sw if mode == MODE_SW else self.lib.mrf_estimate_log_partition
-        if mode not in (MODE_PLAIN, MODE_SW):
-            raise ValueError("the estimator runs plain or Swendsen-Wang sweeps")
+        fns = {MODE_PLAIN: self.lib.mrf_estimate_log_partition, MODE_SW: self.lib.mrf_estimate_log_partition_sw,
+               MODE_HIGDON: self.lib.mrf_estimate_log_partition_higdon}
+        if mode not in fns:
+            raise ValueError("the estimator runs plain, Swendsen-Wang or Higdon sweeps")
+        fn = fns[mode]
         self._check(fn(self.h, int(n_sweeps), out.ctypes.data))
         return out
 

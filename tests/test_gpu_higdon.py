@@ -215,3 +215,38 @@ def test_higdon_small_model_kernel_is_the_same_chain(name):
     assert np.array_equal(one.counts(), many.counts())
     assert one.info().sweep_index == many.info().sweep_index == 7
     one.close(); many.close()
+
+
+def test_higdon_log_v_of_one_sweep_matches_oracle():
+    """Section 5.2's estimator on Higdon's duality: log V per chain of one sweep
+    from a common state, within the float32 tolerance of the fields and of the
+    drawn clusters' log-probabilities."""
+    from oracle.sampler import log_softmax
+    model = wl.ferro_potts_grid3d(7, 6, 5, L=4, seed=23)
+    C, seed, t, rho = 32, 64, 13, 0.5
+    x0 = np.random.default_rng(6).integers(0, model.n_labels, size=(C, model.n_vars))
+    h = M.MRF(model.n_vars, model.n_labels, C, seed=seed, grid=model.grid)
+    h.set_factors(model.unary, model.src, model.dst, model.pair)
+    h.set_higdon(rho)
+    h.set_labels(x0.astype(np.uint8))
+    h.set_sweep_index(t)
+    lv = h.estimate_log_partition(1, M.MODE_HIGDON)[0]
+    x1 = h.get_labels()
+    h.close()
+    split = hg.higdon_split(model, rho)
+    res = hg.higdon_sweep(model, x0, rho, t, seed, split=split)
+    ref = hg.log_v(model, res["x"], res["bonds"], res["theta"], split)
+    # chains whose labels agree and whose remainder's bits were all decided away
+    # from their boundaries (a flipped bit changes the fields, hence log V)
+    near_bit = ((np.abs(res["u_dual"] - res["p_dual"]) < 1e-6) & ~res["bonds"][:, :, None]).any(axis=(1, 2))
+    clean = (x1 == res["x"]).all(axis=1) & ~near_bit
+    assert clean.sum() >= C // 2
+    tol = np.zeros(C)
+    for c in range(C):
+        root, lw = hg.cluster_log_weights(model, split, res["bonds"][c], res["field"][c])
+        rs = np.unique(root)
+        lp = log_softmax(lw[rs])[np.arange(rs.size), res["x"][c][rs]]
+        tol[c] = 1e-5 * np.maximum(1.0, np.abs(lp)).sum() + 5e-7 * np.abs(res["field"][c]).max(axis=1).sum() \
+            + 1e-6 * (model.n_vars + model.n_edges)
+    err = np.abs(lv - ref)
+    assert (err[clean] <= tol[clean]).all(), (err[clean].max(), tol[clean].min())

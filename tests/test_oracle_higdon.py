@@ -152,3 +152,30 @@ def test_chain_marginals_within_3_sigma(kind, rho):
     cm = acc / (T - burn)
     z = np.abs(cm.mean(0) - exact) / np.maximum(cm.std(0, ddof=1) / np.sqrt(C), 1e-12)
     assert z.max() < 4.5 and np.mean(z < 3.0) > 0.9, z
+
+
+def test_log_v_mean_is_log_z_minus_mutual_information():
+    """Section 5.2 on the three-state duality, by enumerating (x, theta)."""
+    model, rho = _tiny("two"), 0.6
+    L, E = model.n_labels, model.src.size
+    X = brute.all_labelings(model.n_vars, L)
+    states = _states(E, L)
+    J = _joint_log(model, rho, X, states)
+    P = np.exp(J - np.logaddexp.reduce(J.ravel()))
+    logZ = np.logaddexp.reduce(brute.log_ptilde(model, X))
+    split = hg.higdon_split(model, rho)
+    lv = np.zeros(J.shape)
+    for si, st in enumerate(states):
+        ok = P[:, si] > 0
+        if not ok.any():
+            continue
+        bonds = np.array([b for b, _ in st], bool)
+        theta = np.array([bits for _, bits in st], bool)
+        n = int(ok.sum())
+        lv[ok, si] = hg.log_v(model, X[ok], np.repeat(bonds[None], n, 0), np.repeat(theta[None], n, 0), split)
+    m = P > 0
+    assert np.all(np.isfinite(lv[m]))
+    px, pt = P.sum(axis=1), P.sum(axis=0)
+    mi = (P[m] * (np.log(P[m]) - np.log(np.outer(px, pt)[m]))).sum()
+    np.testing.assert_allclose(logZ - (P[m] * lv[m]).sum(), mi, atol=1e-10)
+    assert mi > 0
