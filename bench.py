@@ -152,15 +152,15 @@ def kernel_work(name, model_info, C):
     return 0, 0
 
 
-# DRAM bytes of the dual step (k_dual + k_dual_ties) per (edge, chain) item,
-# from the ncu counters of the 64^3 L = 8, 64-chain case with the current
-# kernels (1,142.0 MB per launch pair for 774,144 x 64 items); traffic grows
-# with the items, so it is scaled to the bench's launch.  Valid for m = 49
-# entries and 64 chains only.
-DUAL_DRAM_BYTES_PER_ITEM = {(49, 64): 1142.0e6 / (774144 * 64)}
+# DRAM bytes of the dual step per (edge, chain) item, from ncu counters of a
+# smaller case of the same workload; traffic grows with the items, so it is
+# scaled to the bench's launch.  Keyed by (entries per edge, chains).
+# (49, 64): k_dual at 64^3, L = 8, 64 chains: 327.7 MB read + 349.7 MB written
+# for 774,144 x 64 items.
+DUAL_DRAM_BYTES_PER_ITEM = {(49, 64): (327740928 + 349712896) / (774144 * 64)}
 
 # kernels behind one kernel-timing record of the library
-KERNELS_PER_RECORD = {"k_dual": 2, "k_sw_draw": 2}
+KERNELS_PER_RECORD = {"k_sw_draw": 2}
 
 
 def rank_seed(seed: int, rank: int) -> int:
@@ -240,7 +240,7 @@ def run_ours(args, ws, rank, local):
     ktimes = h.kernel_times()
     ms_total, value = aggregate(ms_total, C * model.n_vars * args.steps, ws, dev)
     ms_step = ms_total / args.steps
-    # a timed dual step is two kernels (k_dual, k_dual_ties); + k_advance per sweep
+    # one launch per kernel-timing record (two for the Swendsen-Wang draw); + k_advance per sweep
     # (a small model runs all its sweeps in one k_sweep_small launch, which advances itself)
     launches = sum(n * KERNELS_PER_RECORD.get(k, 1) for k, (_, n) in ktimes.items())
     if "k_sweep_small" not in ktimes and "k_sw_small" not in ktimes:
@@ -272,7 +272,7 @@ def run_ours(args, ws, rank, local):
         roof = {"bound": "alu", "achieved": calls / (dom_ms / 1e3) / 1e9, "peak": alu_peak / 1e9,
                 "unit": "G Philox4x32-10 calls/s", "frac": calls / (dom_ms / 1e3) / alu_peak,
                 "traffic": per_item * minfo["E"] * C if per_item else None,
-                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_dual + k_dual_ties at "
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_dual at "
                                    "64^3, scaled by edge x chain items") if per_item else None,
                 "kernel": dom, "peak_source": "derived: 152 SMs x 4 SMSPs x 32 lanes x 2070 MHz / 61.5 fmaheavy-pipe cycles per warp-wide call (ncu counters of the Philox-only kernel)",
                 "hbm_view": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac")},

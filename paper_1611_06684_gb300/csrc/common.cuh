@@ -64,11 +64,16 @@ struct FastDiv {
 // tau table are padded to MP = M rounded up to 4 floats (16-byte loads).
 __host__ __device__ constexpr int pad4(int m) { return (m + 3) & ~3; }
 
+// 32-bit words of threshold planes per edge (see k_build_planes): 20 per
+// group of 32 entries, 12 for tables with at most 16 entries (two planes per word).
+__host__ __device__ constexpr int plane_words(int m) { return m <= 16 ? 12 : 20 * ((m + 31) / 32); }
+
 template <int L, int LAYOUT>
 struct Ent {
     static constexpr int M = (LAYOUT == MRF_LAYOUT_PIVOT) ? (L - 1) * (L - 1) : L;
     static constexpr int MP = pad4(M);
     static constexpr int W = (M + 31) / 32;
+    static constexpr int PW = plane_words(M);
     __host__ __device__ static constexpr int i(int k) { return LAYOUT == MRF_LAYOUT_PIVOT ? 1 + k / (L - 1) : k; }
     __host__ __device__ static constexpr int j(int k) { return LAYOUT == MRF_LAYOUT_PIVOT ? 1 + k % (L - 1) : k; }
 };
@@ -77,16 +82,13 @@ __host__ __device__ inline int n_entries(int L, int layout) {
     return layout == MRF_LAYOUT_PIVOT ? (L - 1) * (L - 1) : L;
 }
 
-// Exact 24-bit threshold of a dual draw from the packed entry word `w`
-// (T+ in bits 0..24, d = T+ + T- - (2^24 - 1) in bits 25..26, sign of l in
-// bit 31, 0 = no dual bit) for the case y = [x_s = i_k], z = [x_t = j_k]:
-// the dual logit q + beta1 y + beta2 z is -tau, 0 or +tau.
-__host__ __device__ __forceinline__ uint32_t case_threshold(uint32_t w, int y, int z) {
+// Exact 24-bit threshold of a dual draw at logit level 0 (-tau, lev2 = 0) or
+// level 2 (+tau, lev2 = 1) from the packed entry word; 0 for an entry without
+// a dual bit.  (Level 1, logit 0, is T = 2^23 and never needs the low bits.)
+__host__ __device__ __forceinline__ uint32_t level_threshold(uint32_t w, bool lev2) {
     const uint32_t tp = w & 0x1FFFFFFu;
     const uint32_t tm = (1u << 24) - tp + ((w >> 25) & 3u) - 1u;
-    const int lvl = (w >> 31) ? (z - y + 1) : (y + z);      // 0: -tau, 1: 0, 2: +tau
-    const uint32_t t = lvl == 0 ? tm : (lvl == 1 ? (1u << 23) : tp);
-    return w ? t : 0u;
+    return w ? (lev2 ? tp : tm) : 0u;
 }
 
 // 8-bit prefix of a threshold (255 stands for T = 2^24, decided by the low bits).
@@ -100,7 +102,7 @@ struct SweepArgs {
     const int32_t* dst;        // [E]
     const float* tau;          // [E][MP] signed dual weight (rows padded to 4)
     const uint32_t* thr;       // [E][M] packed thresholds
-    const uint32_t* tpl;       // [E][G][8][4] threshold prefix planes {P00, D10, D01, D11} per plane
+    const uint32_t* tpl;       // [E][plane_words(M)] threshold prefix planes (k_build_planes)
     const float* utf;          // [N][L] folded unaries, float32
     const float* resid;        // [E][L][L] exact tree-edge potentials (blocked sweep)
     const int64_t* inc_ptr;    // [N+1]
@@ -122,20 +124,7 @@ struct SweepArgs {
     FastDiv fdX1, fdX, fdY1, fdY;   // division by nx-1, nx, ny-1, ny
     float* pot;                // [N][L][C] node potentials / beliefs of the blocked sweep
     const uint8_t* skip;       // [E] 1 = edge kept exact (no dual bit) in a learned sweep; null otherwise
-    // deferred ties of the dual step: per warp of k_dual (32 consecutive items),
-    // tie_cap 16-bit records and their count (see k_dual / k_dual_ties)
-    uint16_t* ties;            // [warps][tie_cap]
-    uint8_t* tie_count;        // [warps]
-    int32_t tie_cap;
 };
-
-// Records reserved per warp for deferred dual ties: ~1.5 x the expected
-// 32 M / 256 plus 16, rounded up to 8 (<= 64 for M <= 225).  A warp with more
-// ties decides the excess itself.
-inline int32_t tie_cap_for(int M) { return ((32 * M * 3 / 512 + 1 + 16) + 7) / 8 * 8; }
-
-// k_dual warps (blocks of 256 threads) for E * C items.
-inline int64_t dual_warps(int64_t items) { return (items + 255) / 256 * 8; }
 
 // One dualised entry of log-value l != 0 (Lemma 2-4 and Theorem 2 in closed
 // form, float64): tau = 2 arccosh(e^{|l|/2}) = |l| + 2 log1p(sqrt(-expm1(-|l|))),

@@ -134,12 +134,19 @@ __global__ void k_decompose(DecompArgs a) {
 }
 
 // Threshold prefix planes of the bit-sliced dual draw, per edge and group of
-// 32 entries: for each case (y, z) of an entry the 8-bit prefix of its
-// threshold, stored as 8 bit planes (plane p holds bit 7-p of the prefix of
-// entry 32g + b at bit b).  Kept in difference form so that a chain with
-// row mask R (entries with y = 1) and column mask C (z = 1) gets its planes as
-//   P00 ^ (D10 & R) ^ (D01 & C) ^ (D11 & R & C),
-// with D10 = P00^P10, D01 = P00^P01, D11 = P00^P10^P01^P11.
+// 32 entries (entry 32g + b at bit b).  An entry's dual logit is at one of
+// three levels: 0 (-tau, threshold T-), 1 (logit 0, T = 2^23) or 2 (+tau, T+);
+// which one depends on its sign and its case (see dual_prefix_bits).  Stored:
+// the 8 bit planes of the 8-bit prefix of T+ (B_p: bit 7 - p of the prefix),
+// the planes of the difference between the prefixes of T- and T+
+// (AB_p = A_p ^ B_p, A_p the planes of T-'s prefix), the sign mask and the mask
+// of entries with a dual bit:
+//   uint4 {AB_p, B_p, AB_p+1, B_p+1} for p = 0, 2, 4, 6,   uint4 {S, Act, 0, 0}
+// 20 words per group.  A chain whose level-0 entries are L0 reads its
+// threshold plane as B_p ^ (AB_p & L0).  Tables with at most 16 entries pack
+// two planes per word (plane p in bits 0..15, plane p + 4 in bits 16..31), 12
+// words per edge:
+//   uint4 {AB_0|AB_4<<16, .., AB_3|AB_7<<16}, uint4 {B likewise}, uint4 {S | Act << 16, 0, 0, 0}.
 __global__ void k_build_planes(const uint32_t* thr, int64_t n, const int64_t* slots, int64_t first_slot, int M,
                                uint32_t* tpl) {
     const int G = (M + 31) / 32;
@@ -148,30 +155,30 @@ __global__ void k_build_planes(const uint32_t* thr, int64_t n, const int64_t* sl
     const int64_t i = gid / G;
     const int g = (int)(gid % G);
     const int64_t e = slots ? slots[i] : first_slot + i;
-    uint32_t P[4][8];
-    for (int cs = 0; cs < 4; ++cs)
-        for (int p = 0; p < 8; ++p) P[cs][p] = 0;
+    uint32_t A[8] = {0, 0, 0, 0, 0, 0, 0, 0}, B[8] = {0, 0, 0, 0, 0, 0, 0, 0}, S = 0, Act = 0;
     for (int b = 0; b < 32; ++b) {
         const int k = 32 * g + b;
         if (k >= M) break;
         const uint32_t w = thr[e * M + k];
-        for (int cs = 0; cs < 4; ++cs) {
-            const uint32_t pre = threshold_prefix(case_threshold(w, cs & 1, cs >> 1));
-            for (int p = 0; p < 8; ++p) P[cs][p] |= ((pre >> (7 - p)) & 1u) << b;
+        const uint32_t pa = threshold_prefix(level_threshold(w, false));
+        const uint32_t pb = threshold_prefix(level_threshold(w, true));
+        for (int p = 0; p < 8; ++p) {
+            A[p] |= ((pa >> (7 - p)) & 1u) << b;
+            B[p] |= ((pb >> (7 - p)) & 1u) << b;
         }
+        S |= (w >> 31) << b;
+        Act |= (w != 0u ? 1u : 0u) << b;
     }
-    uint4* out = reinterpret_cast<uint4*>(tpl + (e * G + g) * 32);
+    uint4* out = reinterpret_cast<uint4*>(tpl + e * (int64_t)plane_words(M) + 20 * g);
+    for (int p = 0; p < 8; ++p) A[p] ^= B[p];
     if (M <= 16) {
-        // packed: word p holds plane p (bits 0..15) and plane p + 4 (bits 16..31)
-        for (int p = 0; p < 4; ++p) {
-            uint32_t Q[4];
-            for (int cs = 0; cs < 4; ++cs) Q[cs] = P[cs][p] | (P[cs][p + 4] << 16);
-            out[p] = make_uint4(Q[0], Q[0] ^ Q[1], Q[0] ^ Q[2], Q[0] ^ Q[1] ^ Q[2] ^ Q[3]);
-        }
+        out[0] = make_uint4(A[0] | A[4] << 16, A[1] | A[5] << 16, A[2] | A[6] << 16, A[3] | A[7] << 16);
+        out[1] = make_uint4(B[0] | B[4] << 16, B[1] | B[5] << 16, B[2] | B[6] << 16, B[3] | B[7] << 16);
+        out[2] = make_uint4(S | Act << 16, 0u, 0u, 0u);
         return;
     }
-    for (int p = 0; p < 8; ++p)
-        out[p] = make_uint4(P[0][p], P[0][p] ^ P[1][p], P[0][p] ^ P[2][p], P[0][p] ^ P[1][p] ^ P[2][p] ^ P[3][p]);
+    for (int p = 0; p < 8; p += 2) out[p / 2] = make_uint4(A[p], B[p], A[p + 1], B[p + 1]);
+    out[4] = make_uint4(S, Act, 0u, 0u);
 }
 
 __global__ void k_fold_unary(const float* unary, const double* unary_d, const double* fold, const int64_t* inc_ptr,

@@ -43,8 +43,6 @@ struct mrf {
     double* d_logv = nullptr;          // [sweeps][C] log V of the estimator
     int64_t logv_cap = 0;
     bool lpv_on = false;
-    uint16_t* d_ties = nullptr;        // deferred dual ties [dual warps][tie_cap]
-    uint8_t* d_tie_count = nullptr;    // [dual warps]
     uint32_t* d_counts = nullptr;
     float* d_logp = nullptr;
     Ctl* d_ctl = nullptr;
@@ -165,14 +163,6 @@ cudaError_t timed(mrf_t* h, int id, Fn fn) {
     return e;
 }
 
-// Deferred-tie records and counts of the dual step for `slots` edge slots.
-cudaError_t alloc_ties(mrf_t* h, int64_t slots) {
-    const int64_t warps = dual_warps(slots * h->C);
-    cudaError_t e = dalloc(h->d_ties, (size_t)warps * tie_cap_for(h->M));
-    if (e == cudaSuccess) e = dalloc(h->d_tie_count, (size_t)warps);
-    return e;
-}
-
 void drop_graphs(mrf_t* h) {
     for (auto& g : h->graph)
         if (g) { cudaGraphExecDestroy(g); g = nullptr; }
@@ -186,7 +176,6 @@ SweepArgs make_args(const mrf_t* h) {
     a.tpl = h->d_tpl; a.utf = h->d_utf;
     a.inc_ptr = h->d_inc_ptr; a.inc = h->d_inc; a.ut = h->d_ut;
     a.x = h->d_x; a.theta = h->d_theta; a.counts = h->d_counts; a.logp = h->d_logp;
-    a.ties = h->d_ties; a.tie_count = h->d_tie_count; a.tie_cap = tie_cap_for(h->M);
     a.lpv = h->lpv_on ? h->d_lpv : nullptr;
     a.ctl = h->d_ctl; a.key = h->key;
     a.rk = round_keys(h->key);
@@ -394,7 +383,7 @@ void mrf_destroy(mrf_t* h) {
     drop_graphs(h);
     dfree(h->d_unary); dfree(h->d_ut); dfree(h->d_utf); dfree(h->d_tpl); dfree(h->d_src); dfree(h->d_dst); dfree(h->d_tau); dfree(h->d_thr);
     dfree(h->d_fold); dfree(h->d_cst); dfree(h->d_resid); dfree(h->d_inc_ptr); dfree(h->d_inc); dfree(h->d_x);
-    dfree(h->d_theta); dfree(h->d_ties); dfree(h->d_tie_count); dfree(h->d_counts); dfree(h->d_lpv); dfree(h->d_logv); dfree(h->d_em); dfree(h->d_mfq); dfree(h->d_mfs); dfree(h->d_logp); dfree(h->d_ctl); dfree(h->d_flag); dfree(h->d_stage); dfree(h->d_pot);
+    dfree(h->d_theta); dfree(h->d_counts); dfree(h->d_lpv); dfree(h->d_logv); dfree(h->d_em); dfree(h->d_mfq); dfree(h->d_mfs); dfree(h->d_logp); dfree(h->d_ctl); dfree(h->d_flag); dfree(h->d_stage); dfree(h->d_pot);
     dfree(h->d_swt); dfree(h->d_swl); dfree(h->d_swfold); dfree(h->d_swut); dfree(h->d_swpar); dfree(h->d_swroot); dfree(h->d_swbits); dfree(h->d_swban); dfree(h->d_swlw); dfree(h->d_swerr); dfree(h->d_swchk);
     dfree(h->d_swufix); dfree(h->d_swell);
     dfree(h->d_hgT); dfree(h->d_hglb); dfree(h->d_hgtau); dfree(h->d_hgthr); dfree(h->d_hgtpl); dfree(h->d_hgfold);
@@ -458,7 +447,7 @@ mrf_status mrf_set_factors(mrf_t* h, const float* unary_log, int64_t n_edges, co
     MRF_CUDA(h, dalloc(h->d_src, E)); MRF_CUDA(h, dalloc(h->d_dst, E));
     if ((uint64_t)E * h->C >= (1ull << 32)) return fail(h, MRF_ERANGE, "edges x chains must be below 2^32");
     MRF_CUDA(h, dalloc(h->d_tau, E * pad4(h->M))); MRF_CUDA(h, dalloc(h->d_thr, E * h->M));
-    MRF_CUDA(h, dalloc(h->d_tpl, E * h->W * 32));
+    MRF_CUDA(h, dalloc(h->d_tpl, E * plane_words(h->M)));
     MRF_CUDA(h, dalloc(h->d_fold, E * 2 * L)); MRF_CUDA(h, dalloc(h->d_cst, E));
     if (want_resid) MRF_CUDA(h, dalloc(h->d_resid, E * L * L)); else dfree(h->d_resid);
     if (h->layout == MRF_LAYOUT_DIAG || L == 2) {
@@ -474,7 +463,6 @@ mrf_status mrf_set_factors(mrf_t* h, const float* unary_log, int64_t n_edges, co
     }
     h->sw_checked = false;
     MRF_CUDA(h, dalloc(h->d_theta, E * h->C * h->W));
-    MRF_CUDA(h, alloc_ties(h, (int64_t)E));
     MRF_CUDA(h, to_device(h->d_src, h->h_src.data(), n_edges, MRF_PTR_HOST, h->stream));
     MRF_CUDA(h, to_device(h->d_dst, h->h_dst.data(), n_edges, MRF_PTR_HOST, h->stream));
     MRF_CUDA(h, build_csr(h));
@@ -570,12 +558,11 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
         };
         MRF_CUDA(h, grow(h->d_src, 1)); MRF_CUDA(h, grow(h->d_dst, 1));
         if ((uint64_t)cap * h->C >= (1ull << 32)) return fail(h, MRF_ERANGE, "edges x chains must be below 2^32");
-        MRF_CUDA(h, grow(h->d_tau, pad4(h->M))); MRF_CUDA(h, grow(h->d_thr, h->M)); MRF_CUDA(h, grow(h->d_tpl, h->W * 32));
+        MRF_CUDA(h, grow(h->d_tau, pad4(h->M))); MRF_CUDA(h, grow(h->d_thr, h->M)); MRF_CUDA(h, grow(h->d_tpl, plane_words(h->M)));
         MRF_CUDA(h, grow(h->d_fold, 2 * L)); MRF_CUDA(h, grow(h->d_cst, 1));
         if (h->d_swt) { MRF_CUDA(h, grow(h->d_swt, L)); MRF_CUDA(h, grow(h->d_swl, L)); MRF_CUDA(h, grow(h->d_swell, L)); }
         if (h->d_swfold) MRF_CUDA(h, grow(h->d_swfold, 2 * L));
         MRF_CUDA(h, dalloc(h->d_theta, (size_t)cap * h->C * h->W));
-        MRF_CUDA(h, alloc_ties(h, cap));
         h->E_cap = cap;
     }
     h->h_src.resize(new_slots, -1); h->h_dst.resize(new_slots, -1);
@@ -769,7 +756,7 @@ static mrf_status hg_prepare(mrf_t* h) {
         const size_t cap = (size_t)std::max<int64_t>(E, 1);
         MRF_CUDA(h, dalloc(h->d_hgT, cap * L)); MRF_CUDA(h, dalloc(h->d_hglb, cap * L));
         MRF_CUDA(h, dalloc(h->d_hgtau, cap * pad4(L))); MRF_CUDA(h, dalloc(h->d_hgthr, cap * L));
-        MRF_CUDA(h, dalloc(h->d_hgtpl, cap * 32)); MRF_CUDA(h, dalloc(h->d_hgfold, cap * 2 * L));
+        MRF_CUDA(h, dalloc(h->d_hgtpl, cap * plane_words(L))); MRF_CUDA(h, dalloc(h->d_hgfold, cap * 2 * L));
         MRF_CUDA(h, dalloc(h->d_hgbound, cap));
         MRF_CUDA(h, dalloc(h->d_hgut, (size_t)h->N * L)); MRF_CUDA(h, dalloc(h->d_hgutf, (size_t)h->N * L));
         h->hg_cap = (int64_t)cap;
@@ -799,7 +786,7 @@ static void make_hg_args(const mrf_t* h, SweepArgs& d, SwArgs& w) {
     w.thr = h->d_hgT; w.lwe = h->d_hglb; w.pot = h->d_pot;
     d = make_args(h);
     d.M = h->L; d.W = 1; d.tau = h->d_hgtau; d.thr = h->d_hgthr; d.tpl = h->d_hgtpl;
-    d.utf = h->d_hgutf; d.ut = h->d_hgut; d.tie_cap = tie_cap_for(h->L); d.logp = nullptr; d.lpv = nullptr;
+    d.utf = h->d_hgutf; d.ut = h->d_hgut; d.logp = nullptr; d.lpv = nullptr;
     d.pot = h->d_pot;
 }
 
@@ -1140,7 +1127,7 @@ mrf_status mrf_save(mrf_t* h, const char* path) {
          write_dev(f, h->d_utf, NL, buf, h->stream);
     ok = ok && (E == 0 || (fwrite(h->h_src.data(), sizeof(int32_t), E, f) == E && fwrite(h->h_dst.data(), sizeof(int32_t), E, f) == E));
     ok = ok && write_dev(f, h->d_tau, E * pad4(h->M), buf, h->stream) && write_dev(f, h->d_thr, E * h->M, buf, h->stream) &&
-         write_dev(f, h->d_tpl, E * h->W * 32, buf, h->stream) && write_dev(f, h->d_fold, E * 2 * L, buf, h->stream) &&
+         write_dev(f, h->d_tpl, E * plane_words(h->M), buf, h->stream) && write_dev(f, h->d_fold, E * 2 * L, buf, h->stream) &&
          write_dev(f, h->d_cst, E, buf, h->stream);
     if (hd.has_resid) ok = ok && write_dev(f, h->d_resid, E * L * L, buf, h->stream);
     if (hd.has_sw & 1) ok = ok && write_dev(f, h->d_swt, E * L, buf, h->stream) && write_dev(f, h->d_swl, E * L, buf, h->stream) &&
@@ -1182,17 +1169,17 @@ mrf_status mrf_load(mrf_t** out, const char* path, void* cuda_stream) {
         if (h->h_src[e] >= h->N || h->h_dst[e] >= h->N || (h->h_src[e] < 0) != (h->h_dst[e] < 0)) ok = false;
     if (!ok) return bail(MRF_EINVAL);
     if (dalloc(h->d_src, E) || dalloc(h->d_dst, E) || dalloc(h->d_tau, E * pad4(h->M)) || dalloc(h->d_thr, E * h->M) ||
-        dalloc(h->d_tpl, E * h->W * 32) || dalloc(h->d_fold, E * 2 * L) || dalloc(h->d_cst, E) ||
+        dalloc(h->d_tpl, E * plane_words(h->M)) || dalloc(h->d_fold, E * 2 * L) || dalloc(h->d_cst, E) ||
         (hd.has_resid && dalloc(h->d_resid, E * L * L)) || ((hd.has_sw & 1) && (dalloc(h->d_swt, E * L) || dalloc(h->d_swl, E * L) || dalloc(h->d_swell, E * L))) ||
         ((hd.has_sw & 2) && (dalloc(h->d_swfold, E * 2 * L) || dalloc(h->d_swut, NL))) ||
-        dalloc(h->d_theta, E * h->C * h->W) || alloc_ties(h, (int64_t)E)) {
+        dalloc(h->d_theta, E * h->C * h->W)) {
         cudaGetLastError();
         return bail(MRF_ENOMEM);
     }
     ok = to_device(h->d_src, h->h_src.data(), (int64_t)E, MRF_PTR_HOST, h->stream) == cudaSuccess &&
          to_device(h->d_dst, h->h_dst.data(), (int64_t)E, MRF_PTR_HOST, h->stream) == cudaSuccess;
     ok = ok && read_dev(f, h->d_tau, E * pad4(h->M), buf, h->stream) && read_dev(f, h->d_thr, E * h->M, buf, h->stream) &&
-         read_dev(f, h->d_tpl, E * h->W * 32, buf, h->stream) && read_dev(f, h->d_fold, E * 2 * L, buf, h->stream) &&
+         read_dev(f, h->d_tpl, E * plane_words(h->M), buf, h->stream) && read_dev(f, h->d_fold, E * 2 * L, buf, h->stream) &&
          read_dev(f, h->d_cst, E, buf, h->stream);
     if (hd.has_resid) ok = ok && read_dev(f, h->d_resid, E * L * L, buf, h->stream);
     if (hd.has_sw & 1) ok = ok && read_dev(f, h->d_swt, E * L, buf, h->stream) && read_dev(f, h->d_swl, E * L, buf, h->stream) &&

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256, 4) k_dual_noalloc(SweepArgs a, const uint
     if (s >= 0) {
         const int t = a.dst[e];
         dual_bits<L, LAYOUT>(e, c, xin[(int64_t)s * a.C + c], xin[(int64_t)t * a.C + c],
-                             a.tpl + (int64_t)e * E::W * 32, a.thr + (int64_t)e * E::M, sweep, a.rk, bits);
+                             a.tpl + (int64_t)e * E::PW, a.thr + (int64_t)e * E::M, sweep, a.rk, bits);
     } else {
 #pragma unroll
         for (int w = 0; w < E::W; ++w) bits[w] = 0;

@@ -12,7 +12,7 @@
 namespace mrfk {
 
 enum Phase : uint32_t {
-    PH_DUAL = 1,      // prefix bytes of dual-bit uniforms (16 per call)
+    PH_DUAL = 1,      // bit planes of the 8-bit prefixes of dual-bit uniforms
     PH_DUAL_LO = 2,   // low 16 bits of dual-bit uniforms (8 per call)
     PH_PRIMAL = 3,    // label draw of the plain sweep (word 0)
     PH_INIT = 4,      // initial labels (word 0)
@@ -76,6 +76,38 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const RoundKeys& rk) 
 __device__ __forceinline__ uint4 draw_rk(uint32_t index, uint32_t sweep, uint32_t chain, uint32_t phase, uint32_t sub,
                                          const RoundKeys& rk) {
     return philox4x32_10_rk(make_uint4(index, sweep, chain, (phase << 24) | sub), rk);
+}
+
+// NC calls draw_rk(index, sweep, chain, phase, s, rk) for s = 0 .. NC-1 (NC <= 256).
+// The counters differ only in the low bits of word 3, which enters round 1
+// only through the new word 2; so the round-1 products, the round-2 product
+// of word 0 and the round-3 product of word 2 are the same for every call and
+// are computed once.
+template <int NC>
+__device__ __forceinline__ void draw_rk_subs(uint32_t index, uint32_t sweep, uint32_t chain, uint32_t phase,
+                                             const RoundKeys& rk, uint4 (&out)[NC]) {
+    constexpr uint32_t kMul0 = 0xD2511F53u, kMul1 = 0xCD9E8D57u;
+    const uint64_t pa = (uint64_t)kMul0 * index, pb = (uint64_t)kMul1 * chain;
+    const uint32_t x1 = (uint32_t)(pb >> 32) ^ sweep ^ rk.k0[0], y1 = (uint32_t)pb;
+    const uint32_t z1b = (uint32_t)(pa >> 32) ^ (phase << 24) ^ rk.k1[0], w1 = (uint32_t)pa;
+    const uint64_t pc = (uint64_t)kMul0 * x1;
+    const uint32_t z2 = (uint32_t)(pc >> 32) ^ w1 ^ rk.k1[1], w2 = (uint32_t)pc;
+    const uint64_t pd = (uint64_t)kMul1 * z2;
+    const uint32_t y3 = (uint32_t)pd, h3 = (uint32_t)(pd >> 32);
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+        const uint64_t p1 = (uint64_t)kMul1 * (z1b ^ (uint32_t)s);
+        const uint32_t x2 = (uint32_t)(p1 >> 32) ^ y1 ^ rk.k0[1], y2 = (uint32_t)p1;
+        const uint64_t p0 = (uint64_t)kMul0 * x2;
+        uint4 c = make_uint4(h3 ^ y2 ^ rk.k0[2], y3, (uint32_t)(p0 >> 32) ^ w2 ^ rk.k1[2], (uint32_t)p0);
+#pragma unroll
+        for (int r = 3; r < 10; ++r) {
+            const uint64_t q0 = (uint64_t)kMul0 * c.x, q1 = (uint64_t)kMul1 * c.z;
+            c = make_uint4((uint32_t)(q1 >> 32) ^ c.y ^ rk.k0[r], (uint32_t)q1, (uint32_t)(q0 >> 32) ^ c.w ^ rk.k1[r],
+                           (uint32_t)q0);
+        }
+        out[s] = c;
+    }
 }
 
 __host__ __device__ __forceinline__ uint2 seed_key(uint64_t seed) {

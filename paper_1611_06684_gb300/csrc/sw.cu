@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(1024) k_hg_small(SweepArgs d, SwArgs a, int n_
             }
             if (!bond) {
                 uint32_t bits[En::W];
-                dual_bits<L, MRF_LAYOUT_DIAG>((uint32_t)e, (uint32_t)c, xs, xt, d.tpl + e * En::W * 32, d.thr + e * En::M,
+                dual_bits<L, MRF_LAYOUT_DIAG>((uint32_t)e, (uint32_t)c, xs, xt, d.tpl + e * En::PW, d.thr + e * En::M,
                                               sweep, d.rk, bits);
                 s_theta[g] = bits[0];
                 continue;

@@ -104,93 +104,123 @@ __device__ __forceinline__ bool is_tree_edge(const SweepArgs& a, uint32_t e) {
 
 // ---------------------------------------------------------------------------- dual bits
 
+// Row and column masks of the entries of a PIVOT table with at most 64
+// entries as 64-bit words: entries (xs, j) and (i, xt).
+template <int L>
+__device__ __forceinline__ void pivot_masks64(int xs, int xt, uint64_t& Y, uint64_t& Z) {
+    constexpr int R = L - 1;
+    constexpr uint64_t row = (1ull << R) - 1ull;
+    uint64_t col = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) col |= 1ull << (R * r);
+    Y = xs ? row << (R * (xs - 1)) : 0ull;
+    Z = xt ? col << (xt - 1) : 0ull;
+}
+
 // Dual bits of edge e, chain c, given the endpoint labels (xs, xt).
-// Bit-sliced: the 8-bit prefixes of 32 uniforms arrive as 8 planes (two
+// Bit-sliced: the 8-bit prefixes of 32 uniforms arrive as 8 bit planes (two
 // Philox calls per group of 32 entries; one call, two planes per word, when
-// the table has at most 16 entries); each plane is compared with the
-// matching threshold plane for the chain's cases, most significant first:
-//   lt |= eq & ~r & t;  eq &= ~(r ^ t)
-// so lt = [prefix < threshold prefix] and eq = ties for all 32 entries at once.
-// Returns lt in bits and the ties in ties; a tie (probability 1/256 per entry)
-// is decided by the low 16 bits of its uniform against the exact 24-bit
-// threshold (resolve_tie).
+// the table has at most 16 entries).  An entry's dual logit q + beta1 y +
+// beta2 z sits at one of three levels, fixed by its sign s = [l < 0] and its
+// case y = [x_s = i_k], z = [x_t = j_k]:
+//   s = 0: level y + z,   s = 1: level z - y + 1   (0: -tau, 1: 0, 2: +tau)
+// so with X = S ^ Y over a group's masks:
+//   L0 = Act & ~Z & ~X,   L2 = Act & Z & X,   L1 = Act & ~(L0 | L2).
+// Level 1 is p = 1/2 exactly (T = 2^23): its bit is the complement of the
+// prefix's top bit.  For levels 0 and 2 the planes of the matching threshold
+// prefix, t = B ^ (AB & L0) (k_build_planes), are compared with the random
+// planes least significant first:
+//   lt = (~r & t) | (~(r ^ t) & lt)        prefix <  threshold prefix
+//   le = (~r & t) | (~(r ^ t) & le)        prefix <= threshold prefix
+// Returns lt in bits, the ties le & ~lt (probability 1/256 per entry) in ties
+// and the level-2 mask in lev2; a tie is decided by the low 16 bits of its
+// uniform against the exact threshold of its level (resolve_tie).
 template <int L, int LAYOUT>
 __device__ __forceinline__ void dual_prefix_bits(uint32_t e, uint32_t c, int xs, int xt,
                                                  const uint32_t* __restrict__ tpl_e, uint32_t sweep,
                                                  const RoundKeys& key, uint32_t (&bits)[Ent<L, LAYOUT>::W],
-                                                 uint32_t (&ties)[Ent<L, LAYOUT>::W]) {
+                                                 uint32_t (&ties)[Ent<L, LAYOUT>::W],
+                                                 uint32_t (&lev2)[Ent<L, LAYOUT>::W]) {
     using E = Ent<L, LAYOUT>;
+    const uint4* tp = reinterpret_cast<const uint4*>(tpl_e);
     if constexpr (E::M <= 16) {
-        // at most 16 entries: one Philox call, word p = plane p (bits 0..15) and
-        // plane p + 4 (bits 16..31); the low halves compare the prefix's high
-        // nibble, the high halves its low nibble, combined at the end
+        // one Philox call: word p = plane p (bits 0..15) and plane p + 4 (bits
+        // 16..31); the low halves compare the prefix's high nibble, the high
+        // halves its low nibble, combined at the end
         const uint4 r4 = draw_rk(e, sweep, c, PH_DUAL, 0u, key);
         const uint32_t R[4] = {r4.x, r4.y, r4.z, r4.w};
-        const uint32_t rm16 = row_mask<L, LAYOUT>(xs, 0), cm16 = col_mask<L, LAYOUT>(xt, 0);
-        const uint32_t rm = rm16 | (rm16 << 16), cm = cm16 | (cm16 << 16), km = rm & cm;
-        const uint4* tp = reinterpret_cast<const uint4*>(tpl_e);
-        uint32_t lt = 0u, eq = valid_word(E::M, 0) * 0x10001u;
+        const uint4 qa = __ldg(tp), qb = __ldg(tp + 1);
+        const uint32_t sa = __ldg(tpl_e + 8);
+        const uint32_t AB[4] = {qa.x, qa.y, qa.z, qa.w}, B[4] = {qb.x, qb.y, qb.z, qb.w};
+        const uint32_t Y = row_mask<L, LAYOUT>(xs, 0), Z = col_mask<L, LAYOUT>(xt, 0);
+        const uint32_t X = (sa & 0xFFFFu) ^ Y, act = sa >> 16;
+        const uint32_t l0 = act & ~Z & ~X, l2 = act & Z & X, l02 = l0 | l2;
+        const uint32_t L0 = l0 | (l0 << 16);
+        uint32_t lt = 0u, le = 0xFFFFFFFFu;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const uint4 q = __ldg(tp + p);
-            const uint32_t t = q.x ^ (q.y & rm) ^ (q.z & cm) ^ (q.w & km);
-            lt |= eq & ~R[p] & t;
-            eq &= ~(R[p] ^ t);
+        for (int p = 3; p >= 0; --p) {
+            const uint32_t t = B[p] ^ (AB[p] & L0), r = R[p];
+            lt = (~r & t) | (~(r ^ t) & lt);
+            le = (~r & t) | (~(r ^ t) & le);
         }
-        bits[0] = (lt | (eq & (lt >> 16))) & 0xFFFFu;
-        ties[0] = (eq & (eq >> 16)) & 0xFFFFu;
+        const uint32_t eq = le & ~lt;
+        bits[0] = ((lt | (eq & (lt >> 16))) & l02) | (~R[0] & act & ~l02);
+        ties[0] = eq & (eq >> 16) & l02;
+        lev2[0] = l2;
         return;
     }
-    // up to four Philox calls (two groups) in flight together for ILP
+    constexpr bool M64 = LAYOUT == MRF_LAYOUT_PIVOT && E::M <= 64;
+    uint64_t Y64 = 0, Z64 = 0;
+    if constexpr (M64) pivot_masks64<L>(xs, xt, Y64, Z64);
+    // the first two groups' four Philox calls share their first rounds and are in flight together
     constexpr int GA = E::W < 2 ? E::W : 2;
-    uint32_t R[GA][8];
-#pragma unroll
-    for (int g = 0; g < GA; ++g) {
-        const uint4 r0 = draw_rk(e, sweep, c, PH_DUAL, 2u * g, key);
-        const uint4 r1 = draw_rk(e, sweep, c, PH_DUAL, 2u * g + 1u, key);
-        R[g][0] = r0.x; R[g][1] = r0.y; R[g][2] = r0.z; R[g][3] = r0.w;
-        R[g][4] = r1.x; R[g][5] = r1.y; R[g][6] = r1.z; R[g][7] = r1.w;
-    }
+    uint4 RA[2 * GA];
+    draw_rk_subs<2 * GA>(e, sweep, c, PH_DUAL, key, RA);
 #pragma unroll
     for (int g = 0; g < E::W; ++g) {
-        uint32_t Rg[8];
+        uint4 r0, r1;
         if (g < GA) {
-#pragma unroll
-            for (int p = 0; p < 8; ++p) Rg[p] = R[g < GA ? g : 0][p];
+            r0 = RA[2 * (g < GA ? g : 0)];
+            r1 = RA[2 * (g < GA ? g : 0) + 1];
         } else {
-            const uint4 r0 = draw_rk(e, sweep, c, PH_DUAL, 2u * g, key);
-            const uint4 r1 = draw_rk(e, sweep, c, PH_DUAL, 2u * g + 1u, key);
-            Rg[0] = r0.x; Rg[1] = r0.y; Rg[2] = r0.z; Rg[3] = r0.w;
-            Rg[4] = r1.x; Rg[5] = r1.y; Rg[6] = r1.z; Rg[7] = r1.w;
+            r0 = draw_rk(e, sweep, c, PH_DUAL, 2u * g, key);
+            r1 = draw_rk(e, sweep, c, PH_DUAL, 2u * g + 1u, key);
         }
-        const uint32_t rm = row_mask<L, LAYOUT>(xs, g), cm = col_mask<L, LAYOUT>(xt, g), km = rm & cm;
-        const uint4* tp = reinterpret_cast<const uint4*>(tpl_e + g * 32);
-        uint32_t lt = 0u, eq = valid_word(E::M, g);
+        const uint32_t Rg[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+        const uint4* tg = tp + 5 * g;
+        const uint4 sq = __ldg(tg + 4);                    // {S, Act}
+        uint32_t Y, Z;
+        if constexpr (M64) {
+            Y = (uint32_t)(Y64 >> (32 * g));
+            Z = (uint32_t)(Z64 >> (32 * g));
+        } else {
+            Y = row_mask<L, LAYOUT>(xs, g);
+            Z = col_mask<L, LAYOUT>(xt, g);
+        }
+        const uint32_t X = sq.x ^ Y;
+        const uint32_t L0 = sq.y & ~Z & ~X, L2 = sq.y & Z & X, L02 = L0 | L2;
+        uint32_t lt = 0u, le = 0xFFFFFFFFu;
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
-            const uint4 q = __ldg(tp + p);                 // {P00, D10, D01, D11} of plane p
-            const uint32_t t = q.x ^ (q.y & rm) ^ (q.z & cm) ^ (q.w & km);
-            const uint32_t r = Rg[p];
-            lt |= eq & ~r & t;
-            eq &= ~(r ^ t);
+        for (int h = 3; h >= 0; --h) {
+            const uint4 q = __ldg(tg + h);                 // {AB_2h, B_2h, AB_2h+1, B_2h+1}
+            uint32_t t = q.w ^ (q.z & L0), r = Rg[2 * h + 1];
+            lt = (~r & t) | (~(r ^ t) & lt);
+            le = (~r & t) | (~(r ^ t) & le);
+            t = q.y ^ (q.x & L0); r = Rg[2 * h];
+            lt = (~r & t) | (~(r ^ t) & lt);
+            le = (~r & t) | (~(r ^ t) & le);
         }
-        bits[g] = lt;
-        ties[g] = eq;
+        bits[g] = (lt & L02) | (~Rg[0] & sq.y & ~L02);
+        ties[g] = le & ~lt & L02;
+        lev2[g] = L2;
     }
 }
 
-// Row / column label of entry k.
-template <int L, int LAYOUT>
-__device__ __forceinline__ int entry_row(int k) { return LAYOUT == MRF_LAYOUT_PIVOT ? 1 + k / (L - 1) : k; }
-template <int L, int LAYOUT>
-__device__ __forceinline__ int entry_col(int k) { return LAYOUT == MRF_LAYOUT_PIVOT ? 1 + k % (L - 1) : k; }
-
-// Decision of a tie at entry k in case (y, z) = ([x_s = i_k], [x_t = j_k]):
-// low 16 bits of the uniform < the part of the case threshold below its
-// 8-bit prefix.
-__device__ __forceinline__ bool resolve_tie(uint32_t e, uint32_t c, int y, int z, int k, uint32_t thr_word,
+// Decision of a tie at entry k (its 8-bit prefix equals the prefix of the
+// threshold T of its level): low 16 bits of the uniform < T - (prefix << 16).
+__device__ __forceinline__ bool resolve_tie(uint32_t e, uint32_t c, bool lev2, int k, uint32_t thr_word,
                                             uint32_t sweep, const RoundKeys& key) {
-    const uint32_t t = case_threshold(thr_word, y, z);
+    const uint32_t t = level_threshold(thr_word, lev2);
     const uint32_t rem = t - (threshold_prefix(t) << 16);      // in [0, 65536]
     return rem && dual_low16(e, sweep, c, k, key) < rem;
 }
@@ -201,8 +231,8 @@ __device__ __forceinline__ void dual_bits(uint32_t e, uint32_t c, int xs, int xt
                                           const uint32_t* __restrict__ thr_e, uint32_t sweep, const RoundKeys& key,
                                           uint32_t (&bits)[Ent<L, LAYOUT>::W]) {
     using E = Ent<L, LAYOUT>;
-    uint32_t ties[E::W];
-    dual_prefix_bits<L, LAYOUT>(e, c, xs, xt, tpl_e, sweep, key, bits, ties);
+    uint32_t ties[E::W], lev2[E::W];
+    dual_prefix_bits<L, LAYOUT>(e, c, xs, xt, tpl_e, sweep, key, bits, ties, lev2);
 #pragma unroll 1
     for (int g = 0; g < E::W; ++g) {
         uint32_t tg = ties[g];
@@ -210,9 +240,7 @@ __device__ __forceinline__ void dual_bits(uint32_t e, uint32_t c, int xs, int xt
             const int b = __ffs(tg) - 1;
             tg &= tg - 1u;
             const int k = 32 * g + b;
-            if (resolve_tie(e, c, xs == entry_row<L, LAYOUT>(k), xt == entry_col<L, LAYOUT>(k), k, __ldg(thr_e + k),
-                            sweep, key))
-                bits[g] |= 1u << b;
+            if (resolve_tie(e, c, (lev2[g] >> b) & 1u, k, __ldg(thr_e + k), sweep, key)) bits[g] |= 1u << b;
         }
     }
 }
@@ -269,116 +297,110 @@ __device__ __forceinline__ int draw_label(const float (&F)[L], uint32_t v, uint3
 
 // ---------------------------------------------------------------------------- kernels
 
-// Dual step.  Ties are not decided here: a tie needs a threshold word (a
-// scattered load) and one more Philox call, and only ~M/256 of a thread's
-// entries tie, so deciding them in place keeps whole warps waiting on a few
-// lanes.  Each warp instead writes its ties as 16-bit records
-//   lane | [x_s = i_k] << 5 | [x_t = j_k] << 6 | k << 8
-// to its own tie_cap slots (numbered by a warp scan of the per-lane counts)
-// and its count; k_dual_ties then decides all of them with every lane busy.
-// Ties beyond tie_cap are decided in place.
+// Dual step.  A warp takes NG consecutive groups of 32 (edge, chain) items
+// (item g = e C + c, one item per lane).  A tie needs one more Philox call and
+// a scattered threshold word; deciding it in the owning lane would hold the
+// whole warp for a few lanes.  Instead the warp stages its dual words in
+// shared memory and queues every nonzero tie word of a lane as one entry
+// {group, lane, word | tie mask | level-2 mask}; after its NG groups the warp
+// decides the queued entries with one entry per lane per round and ORs the
+// won bits into the staged words, which are then stored.  Ties of a lane
+// whose entry does not fit the queue are decided by the lane itself.
+template <int M, int W>
+struct DualTile {
+    static constexpr int WARPS = 8;                                         // 256 threads
+    static constexpr int NG = W >= 4 ? 2 : (M >= 32 ? 4 : (M >= 8 ? 8 : 16));
+    // nonzero tie words expected per warp: NG 32 W (1 - (1 - 1/256)^32) <= NG 32 M / 256;
+    // capacity twice that plus 32, in whole rounds of 32
+    static constexpr int Q = ((NG * 32 * M * 2 / 256 + 32) + 31) / 32 * 32;
+};
+
 template <int L, int LAYOUT>
 __global__ void __launch_bounds__(256, 4) k_dual(SweepArgs a) {
     using E = Ent<L, LAYOUT>;
+    using T = DualTile<E::M, E::W>;
+    constexpr int W = E::W, NG = T::NG, Q = T::Q;
     constexpr uint32_t FULL = 0xFFFFFFFFu;
-    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;     // E * C < 2^32 (checked by the host)
-    const int lane = threadIdx.x & 31;
-    const bool in_range = g < (uint64_t)a.E * a.C;                // every lane stays for the warp scan
-    const uint32_t e = in_range ? a.fdC.div(g) : 0u;
-    const uint32_t c = in_range ? g - e * (uint32_t)a.C : 0u;
+    __shared__ uint32_t s_th[T::WARPS][NG * W][32];        // staged dual words, [group, word][lane]
+    __shared__ uint4 s_q[T::WARPS][Q];                     // queued tie words
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t below = (1u << lane) - 1u;
+    const uint64_t n_items = (uint64_t)a.E * a.C;          // < 2^32 (checked by the host)
+    const uint64_t base = ((uint64_t)blockIdx.x * T::WARPS + warp) * (NG * 32);
     const uint32_t sweep = (uint32_t)a.ctl->sweep;
     const uint8_t* xin = a.x + (size_t)(sweep & 1) * a.N * a.C;
-    uint32_t bits[E::W], ties[E::W];
-    int xs = 0, xt = 0;
-    const int s = in_range ? a.src[e] : -1;
-    if (s >= 0 && !(a.splash && is_tree_edge(a, e)) && !(a.skip && a.skip[e])) {
-        const int t = a.dst[e];
-        xs = xin[(int64_t)s * a.C + c];
-        xt = xin[(int64_t)t * a.C + c];
-        dual_prefix_bits<L, LAYOUT>(e, c, xs, xt, a.tpl + (int64_t)e * E::W * 32, sweep, a.rk, bits, ties);
-    } else {
-#pragma unroll
-        for (int w = 0; w < E::W; ++w) { bits[w] = 0; ties[w] = 0; }
-    }
-    int n = 0;
-#pragma unroll
-    for (int w = 0; w < E::W; ++w) n += __popc(ties[w]);
-    int incl = n;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int y = __shfl_up_sync(FULL, incl, d);
-        if (lane >= d) incl += y;
-    }
-    const int total = __shfl_sync(FULL, incl, 31);
-    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (lane == 0) a.tie_count[gw] = (uint8_t)min(total, a.tie_cap);
-    if (n) {
-        // records of the ties that fit; [x_s = i_k] and [x_t = j_k] from the entry masks
-        uint16_t* rec = a.ties + gw * a.tie_cap;
-        int i = incl - n;
-#pragma unroll
-        for (int w = 0; w < E::W; ++w) {
-            uint32_t tw = ties[w];
-            if (!tw) continue;
-            const uint32_t ym = row_mask<L, LAYOUT>(xs, w), zm = col_mask<L, LAYOUT>(xt, w);
-            while (tw) {
-                const int b = __ffs(tw) - 1;
-                tw &= tw - 1u;
-                if (i < a.tie_cap)
-                    rec[i] = (uint16_t)(lane | (((ym >> b) & 1u) << 5) | (((zm >> b) & 1u) << 6) | ((32 * w + b) << 8));
-                ++i;
-            }
-        }
-    }
-    if (total > a.tie_cap && incl > a.tie_cap) {
-        // rare: this lane's ties past the warp's region are decided here
-        int i = incl - n;
+    int nq = 0;                                            // entries queued (warp-uniform)
 #pragma unroll 1
-        for (int w = 0; w < E::W; ++w) {
-            uint32_t tw = ties[w];
-            while (tw) {
-                const int b = __ffs(tw) - 1;
-                tw &= tw - 1u;
-                const int k = 32 * w + b;
-                if (i >= a.tie_cap &&
-                    resolve_tie(e, c, xs == entry_row<L, LAYOUT>(k), xt == entry_col<L, LAYOUT>(k), k,
-                                __ldg(a.thr + (int64_t)e * E::M + k), sweep, a.rk))
-                    bits[w] |= 1u << b;
-                ++i;
-            }
-        }
-    }
-    if (!in_range) return;
-    uint32_t* out = a.theta + (int64_t)g * E::W;
-    if (E::W % 2 == 0) {
-#pragma unroll
-        for (int w = 0; w < E::W; w += 2) *reinterpret_cast<uint2*>(out + w) = make_uint2(bits[w], bits[w + 1 < E::W ? w + 1 : w]);
-    } else {
-#pragma unroll
-        for (int w = 0; w < E::W; ++w) out[w] = bits[w];
-    }
-}
-
-// Deferred ties of the dual step: thread q handles the records of k_dual warp
-// q (items 32 q .. 32 q + 31), setting the won bits in theta with atomicOr.
-template <int L, int LAYOUT>
-__global__ void __launch_bounds__(256) k_dual_ties(SweepArgs a, int64_t n_warps) {
-    using E = Ent<L, LAYOUT>;
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= n_warps) return;
-    const int cnt = a.tie_count[q];
-    if (!cnt) return;
-    const uint32_t sweep = (uint32_t)a.ctl->sweep;
-    const uint16_t* rec = a.ties + q * a.tie_cap;
-#pragma unroll 1
-    for (int i = 0; i < cnt; ++i) {
-        const uint32_t r = rec[i];
-        const uint32_t g = (uint32_t)(q * 32) + (r & 31u);
-        const int k = (int)(r >> 8);
-        const uint32_t e = a.fdC.div(g);
+    for (int j = 0; j < NG; ++j) {
+        const uint64_t g64 = base + 32 * j + lane;
+        const uint32_t g = (uint32_t)g64;
+        const bool in_range = g64 < n_items;
+        const uint32_t e = in_range ? a.fdC.div(g) : 0u;
         const uint32_t c = g - e * (uint32_t)a.C;
-        if (resolve_tie(e, c, (r >> 5) & 1, (r >> 6) & 1, k, __ldg(a.thr + (int64_t)e * E::M + k), sweep, a.rk))
-            atomicOr(a.theta + (int64_t)g * E::W + (k >> 5), 1u << (k & 31));
+        uint32_t bits[W], ties[W], lev2[W];
+        const int s = in_range ? a.src[e] : -1;
+        if (s >= 0 && !(a.splash && is_tree_edge(a, e)) && !(a.skip && a.skip[e])) {
+            const int t = a.dst[e];
+            const int xs = xin[(int64_t)s * a.C + c], xt = xin[(int64_t)t * a.C + c];
+            dual_prefix_bits<L, LAYOUT>(e, c, xs, xt, a.tpl + (int64_t)e * E::PW, sweep, a.rk, bits, ties, lev2);
+        } else {
+#pragma unroll
+            for (int w = 0; w < W; ++w) { bits[w] = 0u; ties[w] = 0u; lev2[w] = 0u; }
+        }
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const bool has = ties[w] != 0u;
+            const uint32_t bal = __ballot_sync(FULL, has);
+            const int pos = nq + __popc(bal & below);
+            nq += __popc(bal);
+            if (has) {
+                if (pos < Q) {
+                    s_q[warp][pos] = make_uint4((uint32_t)(j * W + w) | ((uint32_t)lane << 8), ties[w], lev2[w] & ties[w], 0u);
+                } else {
+                    uint32_t tw = ties[w];                 // queue full: decide here
+                    while (tw) {
+                        const int b = __ffs(tw) - 1;
+                        tw &= tw - 1u;
+                        const int k = 32 * w + b;
+                        if (resolve_tie(e, c, (lev2[w] >> b) & 1u, k, __ldg(a.thr + (int64_t)e * E::M + k), sweep, a.rk))
+                            bits[w] |= 1u << b;
+                    }
+                }
+            }
+            s_th[warp][j * W + w][lane] = bits[w];
+        }
+    }
+    __syncwarp();
+    const int nres = nq < Q ? nq : Q;
+#pragma unroll 1
+    for (int r = lane; r < nres; r += 32) {
+        const uint4 q = s_q[warp][r];
+        const int jw = (int)(q.x & 0xFFu), l = (int)(q.x >> 8), j = jw / W, w = jw - j * W;
+        const uint32_t g = (uint32_t)(base + 32 * j + l);
+        const uint32_t e = a.fdC.div(g), c = g - e * (uint32_t)a.C;
+        uint32_t tw = q.y, won = 0u;
+        while (tw) {
+            const int b = __ffs(tw) - 1;
+            tw &= tw - 1u;
+            const int k = 32 * w + b;
+            if (resolve_tie(e, c, (q.z >> b) & 1u, k, __ldg(a.thr + (int64_t)e * E::M + k), sweep, a.rk)) won |= 1u << b;
+        }
+        if (won) atomicOr(&s_th[warp][jw][l], won);
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int j = 0; j < NG; ++j) {
+        const uint64_t g64 = base + 32 * j + lane;
+        if (g64 >= n_items) break;
+        uint32_t* out = a.theta + g64 * W;
+        if (W % 2 == 0) {
+#pragma unroll
+            for (int w = 0; w < W; w += 2)
+                *reinterpret_cast<uint2*>(out + w) = make_uint2(s_th[warp][j * W + w][lane], s_th[warp][j * W + (w + 1 < W ? w + 1 : w)][lane]);
+        } else {
+#pragma unroll
+            for (int w = 0; w < W; ++w) out[w] = s_th[warp][j * W + w][lane];
+        }
     }
 }
 
@@ -462,7 +484,7 @@ __global__ void __launch_bounds__(256, FUSED ? 2 : 4) k_primal(SweepArgs a) {
             } else if (FUSED) {
                 const int side = ic[u].x & 1;
                 const int xn = xin[(int64_t)ic[u].y * a.C + c];
-                dual_bits<L, LAYOUT>((uint32_t)e, c, side == 0 ? xv : xn, side == 0 ? xn : xv, a.tpl + e * E::W * 32,
+                dual_bits<L, LAYOUT>((uint32_t)e, c, side == 0 ? xv : xn, side == 0 ? xn : xv, a.tpl + e * E::PW,
                                      a.thr + e * E::M, sweep, a.rk, bits[u]);
             } else {
                 const uint32_t* th = a.theta + (e * a.C + c) * E::W;
@@ -696,7 +718,7 @@ __global__ void __launch_bounds__(1024) k_sweep_small(SweepArgs a, int n_sweeps)
             if (s >= 0) {
                 const int t = a.dst[e];
                 dual_bits<L, LAYOUT>(e, c, xin[(int64_t)s * a.C + c], xin[(int64_t)t * a.C + c],
-                                     a.tpl + (int64_t)e * E::W * 32, a.thr + (int64_t)e * E::M, sweep, a.rk, bits);
+                                     a.tpl + (int64_t)e * E::PW, a.thr + (int64_t)e * E::M, sweep, a.rk, bits);
             } else {
 #pragma unroll
                 for (int w = 0; w < E::W; ++w) bits[w] = 0;
@@ -892,11 +914,10 @@ cudaError_t run_primal_cta(const SweepArgs& a, cudaStream_t s) {
 
 template <int L, int LAYOUT>
 cudaError_t run_dual(const SweepArgs& a, cudaStream_t s) {
+    using T = DualTile<Ent<L, LAYOUT>::M, Ent<L, LAYOUT>::W>;
     const int64_t n = a.E * a.C;
     if (n <= 0) return cudaSuccess;
-    k_dual<L, LAYOUT><<<blocks_for(n, 256), 256, 0, s>>>(a);
-    const int64_t warps = dual_warps(n);
-    k_dual_ties<L, LAYOUT><<<blocks_for(warps, 256), 256, 0, s>>>(a, warps);
+    k_dual<L, LAYOUT><<<blocks_for(n, 32 * T::NG * T::WARPS), 32 * T::WARPS, 0, s>>>(a);
     return cudaGetLastError();
 }
 
