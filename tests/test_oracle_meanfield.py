@@ -82,3 +82,102 @@ def test_blocked_em_never_decreases_log_ptilde():
         cur = brute.log_ptilde(model, x)
         assert (cur >= prev - 1e-9).all()
         prev = cur
+
+
+def _tree_setup(model, offset=(0, 0, 0)):
+    from oracle import blocked
+    dec = dc.decompose(model)
+    parent = blocked.comb_forest(model.grid, offset)
+    tree = blocked.tree_edge_mask(dec.src, dec.dst, parent)
+    order, _ = blocked.bfs_order(parent)
+    return dec, parent, tree, order
+
+
+def _enumerated_tree_marginals(model, tree, phi_c):
+    X = brute.all_labelings(model.n_vars, model.n_labels)
+    w = np.asarray(model.pair, np.float64)
+    te = np.nonzero(tree)[0]
+    score = phi_c[np.arange(model.n_vars)[None, :], X].sum(axis=1)
+    score += w[te[None, :], X[:, model.src[te]], X[:, model.dst[te]]].sum(axis=1)
+    p = np.exp(score - np.logaddexp.reduce(score))
+    marg = np.zeros((model.n_vars, model.n_labels))
+    for v in range(model.n_vars):
+        np.add.at(marg[v], X[:, v], p)
+    return marg
+
+
+@pytest.mark.parametrize("offset", [(0, 0, 0), (1, 2, 3)])
+def test_tree_marginals_are_the_enumerated_tree_marginals(offset):
+    """Sum-product marginals of the tree MRF (node potentials phi, exact
+    forest factors) equal the marginals of the enumerated distribution; with
+    offset (1, 2, 3) the clipped blocks give a forest of several trees."""
+    model = wl.potts_grid3d(3, 2, 2, L=3, seed=6, w_half=1.0)
+    dec, parent, tree, order = _tree_setup(model, offset)
+    rng = np.random.default_rng(3)
+    phi = rng.normal(0, 1, size=(2, model.n_vars, 3))
+    q = mf.tree_marginals(model, phi, parent, tree, order)
+    for c in range(2):
+        np.testing.assert_allclose(q[c], _enumerated_tree_marginals(model, tree, phi[c]), rtol=0, atol=1e-12)
+
+
+def test_tree_marginals_planted_mistake_fails():
+    """A downward pass that does not remove the child's own upward message
+    from its parent's belief (a plausible slip) misses the enumeration."""
+    from oracle import blocked
+    model = wl.potts_grid3d(3, 2, 2, L=3, seed=6, w_half=1.0)
+    dec, parent, tree, order = _tree_setup(model)
+    phi = np.random.default_rng(3).normal(0, 1, size=(1, model.n_vars, 3))
+    inbox, psi = blocked.tree_messages(model, phi, parent, tree, order)
+    down = np.zeros_like(phi)
+    for v in order:
+        p = parent[v]
+        if p < 0:
+            continue
+        bp = phi[:, p, :] + inbox[:, p, :] + down[:, p, :]              # the child's message not removed
+        down[:, v, :] = np.logaddexp.reduce(bp[:, :, None] + psi[v][None], axis=1)
+    wrong = np.exp(phi + inbox + down - np.logaddexp.reduce(phi + inbox + down, axis=2)[..., None])
+    assert np.abs(wrong[0] - _enumerated_tree_marginals(model, tree, phi[0])).max() > 1e-3
+
+
+@pytest.mark.parametrize("model", [wl.potts_grid3d(2, 2, 2, L=2, seed=8, w_half=1.5),
+                                   wl.potts_grid3d(3, 2, 1, L=3, seed=9, w_half=1.2)])
+def test_blocked_mean_field_objective_decreases_and_bounds_primal_kl(model):
+    """Tree mean field with a fixed forest: the theta-update (expected
+    non-forest duals from the tree marginals) and the x-update (the tree MRF of
+    their potentials) each never increase KL(q_x q_theta1 || p(x, theta_1)),
+    which stays above KL(q_x || p(x)) (Lemma 6 with the forest's duals summed out)."""
+    from oracle import blocked
+    dec, parent, tree, order = _tree_setup(model)
+    assert tree.any() and (~tree).any()
+    rng = np.random.default_rng(4)
+    phi = rng.normal(0, 1, size=(1, model.n_vars, model.n_labels))
+    prev = None
+    for _ in range(8):
+        q = mf.tree_marginals(model, phi, parent, tree, order)
+        eta_y = q[:, dec.src][:, :, dec.i_pos]; eta_z = q[:, dec.dst][:, :, dec.j_pos]
+        pi = np.where(~tree[None, :, None], mf.dual_mean(dec, eta_y, eta_z), 0.0)
+        kl_joint, kl_x = mf.blocked_mf_objective(model, dec, tree, phi[0], pi[0])
+        assert kl_joint >= kl_x - 1e-10
+        if prev is not None:
+            assert kl_joint <= prev + 1e-10
+        phi = blocked.node_potentials(model, dec, tree, pi)
+        kl_after, _ = mf.blocked_mf_objective(model, dec, tree, phi[0], pi[0])
+        assert kl_after <= kl_joint + 1e-10
+        prev = kl_after
+
+
+def test_blocked_mf_step_composes_the_two_updates():
+    """blocked_mf_step from marginals q equals the tree marginals of the node
+    potentials of the expected non-forest duals of q, with the forest of the
+    iteration's block offset."""
+    from oracle import blocked, philox as ph
+    model = wl.potts_grid3d(7, 6, 5, L=4, seed=10)
+    dec = dc.decompose(model)
+    q = np.random.default_rng(5).dirichlet(np.ones(4), size=(2, model.n_vars))
+    q1, pi, phi = mf.blocked_mf_step(model, dec, q, 3, 17)
+    parent = blocked.comb_forest(model.grid, ph.splash_offset(3, 17))
+    tree = blocked.tree_edge_mask(dec.src, dec.dst, parent)
+    assert (pi[:, tree] == 0).all()
+    np.testing.assert_allclose(q1.sum(axis=2), 1.0, atol=1e-12)
+    order, _ = blocked.bfs_order(parent)
+    np.testing.assert_allclose(q1, mf.tree_marginals(model, phi, parent, tree, order), rtol=0, atol=0)
