@@ -287,6 +287,18 @@ mrf_status mrf_map_em_blocked(mrf_t* h, int32_t n_iters, uint8_t* labels, int32_
  * row a distribution over labels).  The sampler's state is untouched. */
 mrf_status mrf_mean_field(mrf_t* h, int32_t n_iters, float* marginals, int32_t ptr_kind);
 
+/* Tree (blocked) mean field on a lattice handle (options.grid; Sections 5.3
+ * and 5.4, Figure 1 caption: the blocked EM with sum-product in place of
+ * max-product).  Each iteration i takes the comb forest of the block offset
+ * of the SPLASH draw with index i, the expected duals of all other edges
+ * given the site marginals (theta-update), and replaces the marginals by the
+ * exact site marginals of the resulting tree MRF (sum-product up and down
+ * the forest; x-update).  marginals[C][N][L] in/out as for mrf_mean_field.
+ * With a fixed forest neither half-step increases KL(q_x q_theta || p(x,
+ * theta)) (the forest's duals summed out).  MRF_ESTATE without options.grid;
+ * MRF_ENONFINITE for non-finite marginals.  The sampler's state is untouched. */
+mrf_status mrf_mean_field_blocked(mrf_t* h, int32_t n_iters, float* marginals, int32_t ptr_kind);
+
 /* Checkpoint of a handle to a file: the model's device tables (unaries,
  * edge slots, decomposition and Swendsen-Wang tables), Higdon's fraction,
  * the labels of every chain, the marginal counts and the sweep index, so

@@ -232,6 +232,8 @@ cudaError_t launch_advance(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_splash(const SweepArgs& a, int layout, cudaStream_t s);
 cudaError_t launch_splash_offset(const SweepArgs& a, cudaStream_t s, int64_t iter = -1);
 cudaError_t launch_tree_map(const SweepArgs& a, uint8_t* xout, cudaStream_t s);
+cudaError_t launch_tree_marginals(const SweepArgs& a, float* qout, cudaStream_t s);
+cudaError_t launch_mf_pot(const SweepArgs& a, int layout, const float* qin, cudaStream_t s);
 cudaError_t launch_em_pot(const SweepArgs& a, int layout, const uint8_t* xin, cudaStream_t s);
 cudaError_t launch_potential(const SweepArgs& a, int layout, cudaStream_t s);
 cudaError_t launch_ffbs(const SweepArgs& a, cudaStream_t s);

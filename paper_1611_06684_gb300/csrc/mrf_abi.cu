@@ -1064,6 +1064,33 @@ mrf_status mrf_mean_field(mrf_t* h, int32_t n_iters, float* marginals, int32_t p
     return MRF_OK;
 }
 
+mrf_status mrf_mean_field_blocked(mrf_t* h, int32_t n_iters, float* marginals, int32_t ptr_kind) {
+    if (!h || !marginals || n_iters < 0) return MRF_EINVAL;
+    if (!h->has_factors) return fail(h, MRF_ESTATE, "mrf_set_factors first");
+    if (h->opt.grid_nx <= 0 || !h->d_resid) return fail(h, MRF_ESTATE, "blocked mean field needs options.grid");
+    const size_t n = (size_t)h->N * h->L * h->C;
+    if (!h->d_mfq) MRF_CUDA(h, dalloc(h->d_mfq, 2 * n));
+    if (!h->d_mfs) MRF_CUDA(h, dalloc(h->d_mfs, n));
+    if (!h->d_pot) { drop_graphs(h); MRF_CUDA(h, dalloc(h->d_pot, (size_t)h->N * h->L * h->C)); }
+    MRF_CUDA(h, to_device(h->d_mfs, marginals, (int64_t)n, ptr_kind, h->stream));
+    mrf_status st = check_finite_device(h, h->d_mfs, (int64_t)n, "marginals");
+    if (st != MRF_OK) return st;
+    MRF_CUDA(h, launch_marg_layout(h->d_mfs, h->d_mfq, h->N, h->L, h->C, false, h->stream));
+    SweepArgs a = make_args(h);
+    a.splash = 1;
+    for (int i = 0; i < n_iters; ++i) {
+        // block offset of iteration i, potentials of the expected non-forest duals, forest marginals
+        MRF_CUDA(h, launch_splash_offset(a, h->stream, i));
+        MRF_CUDA(h, launch_mf_pot(a, h->layout, h->d_mfq + (i & 1) * n, h->stream));
+        MRF_CUDA(h, launch_tree_marginals(a, h->d_mfq + ((i + 1) & 1) * n, h->stream));
+    }
+    MRF_CUDA(h, launch_marg_layout(h->d_mfq + (n_iters & 1) * n, h->d_mfs, h->N, h->L, h->C, true, h->stream));
+    MRF_CUDA(h, cudaMemcpyAsync(marginals, h->d_mfs, n * sizeof(float),
+                                ptr_kind == MRF_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream));
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    return MRF_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------- checkpoints

@@ -110,11 +110,35 @@ __device__ __forceinline__ void label_draw_ffbs(const float (&F)[L], uint32_t v,
     lab = pick < 0 ? last_pos : pick;
 }
 
+// Downward sum-product message to a child: out[a] = log sum_b exp(B[b] +
+// psi[b][a]), B the parent's belief without the child's own message.
+template <int L>
+__device__ __forceinline__ void tree_message_down(const float (&B)[L], const float* __restrict__ psi, float (&out)[L]) {
+#pragma unroll
+    for (int x = 0; x < L; ++x) {
+        float t[L], mx = -INFINITY;
+#pragma unroll
+        for (int b = 0; b < L; ++b) { t[b] = B[b] + __ldg(psi + b * L + x); mx = fmaxf(mx, t[b]); }
+        float s = 0.0f;
+#pragma unroll
+        for (int b = 0; b < L; ++b) s += expf(t[b] - mx);
+        out[x] = mx + logf(s);
+    }
+}
+
+enum FfbsMode { FFBS_SAMPLE = 0, FFBS_MAP = 1, FFBS_MARGINALS = 2 };
+
 // One thread per (block, chain); lanes are consecutive chains of one block.
-// MAP = true (blocked EM): max-product messages and argmax labels (first
-// maximum) written to xmap instead of sampled labels.
-template <int L, bool MAP = false>
-__global__ void __launch_bounds__(128) k_ffbs(SweepArgs a, uint8_t* __restrict__ xmap = nullptr) {
+// MODE = FFBS_SAMPLE: forward filtering / backward sampling (blocked sweep).
+// MODE = FFBS_MAP (blocked EM): max-product messages and argmax labels (first
+// maximum) written to xmap.  MODE = FFBS_MARGINALS (tree mean field):
+// sum-product messages up, then down (each child's message from its parent's
+// full belief minus the child's own upward message), site marginals written
+// to qmarg ([N][L][C]).
+template <int L, int MODE = FFBS_SAMPLE>
+__global__ void __launch_bounds__(128) k_ffbs(SweepArgs a, uint8_t* __restrict__ xmap = nullptr,
+                                              float* __restrict__ qmarg = nullptr) {
+    constexpr bool MAP = MODE == FFBS_MAP;
     int ox, oy, oz;
     {
         const uint32_t o = (uint32_t)a.ctl->splash_offset;
@@ -185,6 +209,60 @@ __global__ void __launch_bounds__(128) k_ffbs(SweepArgs a, uint8_t* __restrict__
         else if (ly > 0) send(a.resid + yedge(X, Y - 1, Z) * L * L, ym);
         else if (lz > 0) send(a.resid + zedge(X, Y, Z - 1) * L * L, zm);
         lx = px; ly = py; lz = pz;
+    }
+    if constexpr (MODE == FFBS_MARGINALS) {
+        // downward pass: total belief (upward belief + message from the parent)
+        // of the last node of the x-chain, of the first node of the row and of
+        // the first node of the plane, each shifted to maximum 0
+        float xT[L], yT[L], zT[L];
+#pragma unroll
+        for (int x = 0; x < L; ++x) { xT[x] = 0.0f; yT[x] = 0.0f; zT[x] = 0.0f; }
+        for (int lz = 0; lz < sz; ++lz)
+            for (int ly = 0; ly < sy; ++ly)
+                for (int lx = 0; lx < sx; ++lx) {
+                    const int X = x0 + lx, Y = y0 + ly, Z = z0 + lz;
+                    const int64_t v = site(X, Y, Z);
+                    const float* pv = a.pot + v * L * C + c;
+                    float bel[L], tot[L];
+#pragma unroll
+                    for (int x = 0; x < L; ++x) bel[x] = pv[x * C];
+                    const float* psi = nullptr;
+                    const float* PT = nullptr;
+                    if (lx > 0) { psi = a.resid + xedge(X - 1, Y, Z) * L * L; PT = xT; }
+                    else if (ly > 0) { psi = a.resid + yedge(X, Y - 1, Z) * L * L; PT = yT; }
+                    else if (lz > 0) { psi = a.resid + zedge(X, Y, Z - 1) * L * L; PT = zT; }
+                    if (psi) {
+                        float up[L], B[L], dn[L];
+                        tree_message<L>(bel, psi, up);          // the message this node sent up
+#pragma unroll
+                        for (int x = 0; x < L; ++x) B[x] = PT[x] - up[x];
+                        tree_message_down<L>(B, psi, dn);
+#pragma unroll
+                        for (int x = 0; x < L; ++x) tot[x] = bel[x] + dn[x];
+                    } else {
+#pragma unroll
+                        for (int x = 0; x < L; ++x) tot[x] = bel[x];
+                    }
+                    float mx = -INFINITY;
+#pragma unroll
+                    for (int x = 0; x < L; ++x) mx = fmaxf(mx, tot[x]);
+                    float ex[L], sum = 0.0f;
+#pragma unroll
+                    for (int x = 0; x < L; ++x) { tot[x] -= mx; ex[x] = expf(tot[x]); sum += ex[x]; }
+                    const float inv = 1.0f / sum;
+                    float* qv = qmarg + v * L * C + c;
+#pragma unroll
+                    for (int x = 0; x < L; ++x) qv[x * C] = ex[x] * inv;
+#pragma unroll
+                    for (int x = 0; x < L; ++x) {
+                        xT[x] = tot[x];
+                        if (lx == 0) {
+                            yT[x] = tot[x];
+                            if (ly == 0) zT[x] = tot[x];
+                        }
+                    }
+                }
+        return;
     }
     // downward pass: root, then every child given its parent's label
     int xl = 0, yl = 0, zl = 0;
@@ -259,7 +337,15 @@ cudaError_t launch_tree_map(const SweepArgs& a, uint8_t* xout, cudaStream_t s) {
     const int64_t nb = (int64_t)(a.grid_nx / 4 + 2) * (a.grid_ny / 4 + 2) * (a.grid_nz / 4 + 2);
     const int64_t n = nb * a.C;
     const unsigned blocks = (unsigned)((n + 127) / 128);
-    MRF_DISPATCH_L2(a.L, (k_ffbs<LL, true><<<blocks, 128, 0, s>>>(a, xout)));
+    MRF_DISPATCH_L2(a.L, (k_ffbs<LL, FFBS_MAP><<<blocks, 128, 0, s>>>(a, xout)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tree_marginals(const SweepArgs& a, float* qout, cudaStream_t s) {
+    const int64_t nb = (int64_t)(a.grid_nx / 4 + 2) * (a.grid_ny / 4 + 2) * (a.grid_nz / 4 + 2);
+    const int64_t n = nb * a.C;
+    const unsigned blocks = (unsigned)((n + 127) / 128);
+    MRF_DISPATCH_L2(a.L, (k_ffbs<LL, FFBS_MARGINALS><<<blocks, 128, 0, s>>>(a, nullptr, qout)));
     return cudaGetLastError();
 }
 

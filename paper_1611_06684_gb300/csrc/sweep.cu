@@ -236,6 +236,16 @@ cudaError_t launch_sweep_small(const SweepArgs& a, int layout, int n_sweeps, cud
 template <int L, int LAYOUT> cudaError_t run_em(const SweepArgs&, const uint8_t*, uint8_t*, cudaStream_t);
 template <int L, int LAYOUT> cudaError_t run_mf(const SweepArgs&, const float*, float*, cudaStream_t);
 template <int L, int LAYOUT> cudaError_t run_em_pot(const SweepArgs&, const uint8_t*, cudaStream_t);
+template <int L, int LAYOUT> cudaError_t run_mf_pot(const SweepArgs&, const float*, cudaStream_t);
+
+cudaError_t launch_mf_pot(const SweepArgs& a, int layout, const float* qin, cudaStream_t s) {
+    if (layout == MRF_LAYOUT_PIVOT) {
+        MRF_DISPATCH_L(a.L, return (run_mf_pot<LL, MRF_LAYOUT_PIVOT>(a, qin, s)));
+    } else {
+        MRF_DISPATCH_L(a.L, return (run_mf_pot<LL, MRF_LAYOUT_DIAG>(a, qin, s)));
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_em_pot(const SweepArgs& a, int layout, const uint8_t* xin, cudaStream_t s) {
     if (layout == MRF_LAYOUT_PIVOT) {

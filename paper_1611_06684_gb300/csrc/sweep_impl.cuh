@@ -902,6 +902,37 @@ __global__ void __launch_bounds__(256) k_mf(SweepArgs a, const float* __restrict
     for (int x = 0; x < L; ++x) qout[((int64_t)v * L + x) * C + c] = F[x] * inv;
 }
 
+// Blocked (tree) mean field, potentials: F_v = u~_v + the beta pi of the
+// expected duals of v's incident non-forest edges given the site marginals q
+// ([N][L][C]), written to a.pot for the forest's sum-product pass.
+template <int L, int LAYOUT>
+__global__ void __launch_bounds__(256) k_mf_pot(SweepArgs a, const float* __restrict__ qin) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (uint64_t)a.N * a.C) return;
+    const uint32_t v = a.fdC.div(g), c = g - v * (uint32_t)a.C;
+    const int64_t C = a.C;
+    float qv[L], acc[L];
+#pragma unroll
+    for (int x = 0; x < L; ++x) { qv[x] = qin[((int64_t)v * L + x) * C + c]; acc[x] = 0.0f; }
+    for (int64_t p = a.inc_ptr[v]; p < a.inc_ptr[v + 1]; ++p) {
+        const int2 ic = __ldg(&a.inc[p]);
+        if (is_tree_edge(a, (uint32_t)(ic.x >> 1))) continue;
+        const int side = ic.x & 1;
+        float qu[L];
+#pragma unroll
+        for (int x = 0; x < L; ++x) qu[x] = qin[((int64_t)ic.y * L + x) * C + c];
+        const float* tau_e = a.tau + (int64_t)(ic.x >> 1) * Ent<L, LAYOUT>::MP;
+        if (side == 0)
+            add_side_mean<L, LAYOUT>(tau_e, 0, [&](int i) { return qv[i]; }, [&](int j) { return qu[j]; }, acc);
+        else
+            add_side_mean<L, LAYOUT>(tau_e, 1, [&](int i) { return qu[i]; }, [&](int j) { return qv[j]; }, acc);
+    }
+    const float* uf = a.utf + (int64_t)v * L;
+    float* pv = a.pot + (int64_t)v * L * C + c;
+#pragma unroll
+    for (int x = 0; x < L; ++x) pv[(int64_t)x * C] = __ldg(uf + x) + acc[x];
+}
+
 static inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 template <int L, int LAYOUT>
@@ -969,6 +1000,13 @@ cudaError_t run_sweep_small(const SweepArgs& a, int n_sweeps, cudaStream_t s) {
 }
 
 template <int L, int LAYOUT>
+cudaError_t run_mf_pot(const SweepArgs& a, const float* qin, cudaStream_t s) {
+    const int64_t n = (int64_t)a.N * a.C;
+    if (n > 0) k_mf_pot<L, LAYOUT><<<blocks_for(n, 256), 256, 0, s>>>(a, qin);
+    return cudaGetLastError();
+}
+
+template <int L, int LAYOUT>
 cudaError_t run_em_pot(const SweepArgs& a, const uint8_t* xin, cudaStream_t s) {
     const int64_t n = (int64_t)a.N * a.C;
     if (n > 0) k_em_pot<L, LAYOUT><<<blocks_for(n, 256), 256, 0, s>>>(a, xin);
@@ -976,6 +1014,8 @@ cudaError_t run_em_pot(const SweepArgs& a, const uint8_t* xin, cudaStream_t s) {
 }
 
 #define MRF_INSTANTIATE_SWEEP(L)                                                                 \
+    template cudaError_t run_mf_pot<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, const float*, cudaStream_t); \
+    template cudaError_t run_mf_pot<L, MRF_LAYOUT_DIAG>(const SweepArgs&, const float*, cudaStream_t);  \
     template cudaError_t run_em_pot<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, const uint8_t*, cudaStream_t); \
     template cudaError_t run_em_pot<L, MRF_LAYOUT_DIAG>(const SweepArgs&, const uint8_t*, cudaStream_t);  \
     template cudaError_t run_sweep_small<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, int, cudaStream_t); \

@@ -73,6 +73,7 @@ _SIGS = {
     "mrf_load": (ct.c_int, [ct.POINTER(_P), ct.c_char_p, _P]),
     "mrf_map_em_blocked": (ct.c_int, [_P, ct.c_int32, _P, ct.c_int32]),
     "mrf_mean_field": (ct.c_int, [_P, ct.c_int32, _P, ct.c_int32]),
+    "mrf_mean_field_blocked": (ct.c_int, [_P, ct.c_int32, _P, ct.c_int32]),
     "mrf_philox_rate": (ct.c_int, [ct.c_uint64, ct.c_int32, _P, ct.POINTER(ct.c_double)]),
     "mrf_sweep_noalloc": (ct.c_int, [_P, _P, _P, ct.c_int64]),
     "mrf_learned_setup": (ct.c_int, [_P, _P, ct.c_int32, ct.c_uint64]),
@@ -384,6 +385,12 @@ class MRF:
         """Primal-dual mean field from marginals [C][N][L]; returns them after n_iters iterations."""
         q = np.ascontiguousarray(marginals, np.float32).copy()
         self._check(self.lib.mrf_mean_field(self.h, int(n_iters), q.ctypes.data, MRF_PTR_HOST))
+        return q
+
+    def mean_field_blocked(self, marginals, n_iters: int):
+        """Tree (blocked) mean field from marginals [C][N][L] on a lattice handle."""
+        q = np.ascontiguousarray(marginals, np.float32).copy()
+        self._check(self.lib.mrf_mean_field_blocked(self.h, int(n_iters), q.ctypes.data, MRF_PTR_HOST))
         return q
 
     def debug_mlp_timeout(self, on: bool = True):

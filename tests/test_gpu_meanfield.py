@@ -106,3 +106,50 @@ def test_blocked_em_matches_oracle(dims, L, C):
     cur = brute.log_ptilde(model, xg3)
     assert (cur >= prev - 1e-6 * np.abs(prev)).all()
     h.close()
+
+
+# Tree mean-field marginals: float32 messages along a forest path of at most
+# 9 edges (comb tree of a 4x4x4 block), each log-sum-exp off by a few units in
+# the last place of log-beliefs of magnitude <= ~20, give log-marginal errors
+# of order 9 x 4 x 2^-24 x 20 ~ 4e-5; the bound below leaves a factor 2.5.
+MARGINAL_TOL = 1e-4
+
+
+@pytest.mark.parametrize("dims,L,C", [((9, 8, 7), 8, 32), ((10, 9, 5), 4, 3), ((13, 5, 6), 3, 2), ((5, 4, 3), 16, 4)])
+def test_blocked_mean_field_matches_oracle(dims, L, C):
+    """Tree mean field (Sections 5.3-5.4): each GPU iteration from the
+    oracle's state (float32-rounded) against the oracle's float64 iteration,
+    with the forest of the iteration's block offset."""
+    from paper_1611_06684_gb300 import mrf as M
+    model = wl.potts_grid3d(*dims, L=L, seed=9)
+    dec = dc.decompose(model)
+    q0 = np.random.default_rng(6).dirichlet(np.ones(L), size=(C, model.n_vars))
+    h = M.MRF(model.n_vars, L, C, seed=21, grid=model.grid)
+    h.set_factors(model.unary, model.src, model.dst, model.pair)
+    q1 = h.mean_field_blocked(q0.astype(np.float32), 1)
+    r1, _, _ = mf.blocked_mf_step(model, dec, q0.astype(np.float32).astype(np.float64), 0, 21)
+    err = np.abs(q1 - r1).max()
+    print("iteration 0 max abs error", err)
+    assert err < MARGINAL_TOL, err
+    # three iterations (offsets of iterations 0, 1, 2) against the oracle's three
+    r = q0.astype(np.float32).astype(np.float64)
+    for it in range(3):
+        r, _, _ = mf.blocked_mf_step(model, dec, r, it, 21)
+    q3 = h.mean_field_blocked(q0.astype(np.float32), 3)
+    err3 = np.abs(q3 - r).max()
+    print("three iterations max abs error", err3)
+    assert err3 < 3 * MARGINAL_TOL, err3
+    qn = h.mean_field_blocked(q0.astype(np.float32), 6)
+    np.testing.assert_allclose(qn.sum(axis=2), 1.0, atol=1e-5)
+    assert (qn >= 0).all()
+    h.close()
+
+
+def test_blocked_mean_field_needs_a_lattice_handle():
+    from paper_1611_06684_gb300 import mrf as M
+    model = wl.random_graph(50, k=2, L=3, seed=3)
+    h = M.MRF(model.n_vars, 3, 2, seed=0)
+    h.set_factors(model.unary, model.src, model.dst, model.pair)
+    with pytest.raises(M.MrfError):
+        h.mean_field_blocked(np.full((2, 50, 3), 1 / 3, np.float32), 1)
+    h.close()
