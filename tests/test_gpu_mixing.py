@@ -1,0 +1,157 @@
+"""The paper's mixing experiments (Section 6), reproduced: mixing times of the
+primal-dual sampler (this library, on the GPU) and of the sequential Gibbs
+sampler (oracle.gibbs, on the CPU) from the potential scale reduction factor
+over 10 chains.
+
+Protocol (the paper gives its outline only; the readings are stated here):
+  * statistics per chain and sweep: the energy log p~(x) and the absolute
+    magnetisation |2 mean(x) - 1| (both invariant under swapping the two
+    labels, so chains in the two symmetric phases agree);
+  * PSRF(t) of each statistic over the samples of sweeps t/2 .. t (the first
+    half discarded), at every 10th sweep; the mixing time is the first such
+    t after which the larger of the two PSRFs stays below 1.01;
+  * initial labels uniform (the library's INIT draw; a numpy Generator for
+    the sequential sampler).
+Models:
+  * the 50 x 50 Ising grid with couplings w_e(a, b) = beta [a = b] for beta in
+    {0.1, 0.3, 0.5} and no field (the spin form beta s_s s_t would put
+    beta >= 0.44 at or beyond the critical coupling, where neither sampler's
+    PSRF settles within thousands of sweeps, while the paper reports finite
+    times up to beta = 0.5); the sequential sampler visits all even sites,
+    then all odd sites (a systematic scan);
+  * random graphs N = 1000, F = k N factors, unary and pairwise log-potentials
+    N(0, 1), k = 2 (with k = 8 the primal-dual sampler's PSRF does not settle
+    within 20,000 sweeps while the sequential one settles after about 1,300:
+    the paper advises against the method for many strong factors per site);
+    sequential sweeps visit sites 0 .. N-1;
+  * the fully connected Ising model N = 100 (spin form, beta = 0.015; at
+    beta = 0.01 = 1/N, the critical coupling of this model, the sequential
+    sampler needs about 50,000 updates, beyond this test's budget): primal-dual sweeps
+    against single-site updates of the sequential sampler (its statistics
+    recorded after every update), as the paper does.
+The paper reports ratios of 2 to 7 on the grid and improved mixing (in sweeps
+against single-site updates) on the fully connected model.  Checked here: the
+mixing times are finite, the primal-dual sampler needs at least as many
+sweeps as the sequential one on the grid and the random graphs (the blocking
+argument at the end of Section 5.4), and it needs fewer sweeps than the
+sequential sampler needs single-site updates on the fully connected model.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import brute, diagnostics as dg, gibbs
+from paper_1611_06684_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+C = 10
+THRESHOLD = 1.01
+EVERY = 10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1611_06684_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _grid(n, beta):
+    src, dst = wl.grid3d_edges(n, n, 1)
+    pair = np.broadcast_to(np.float32(beta) * np.eye(2, dtype=np.float32), (len(src), 2, 2)).copy()
+    return wl.Model(n * n, 2, np.zeros((n * n, 2), np.float32), src, dst, pair, grid=(n, n, 1), name="ising_potts_form")
+
+
+def _stats(model, x):
+    return np.stack([brute.log_ptilde(model, x), np.abs(2.0 * x.mean(axis=1) - 1.0)], 0)
+
+
+def mixing_time(trace, every=EVERY, threshold=THRESHOLD):
+    """trace [statistic][t][chain]; first checkpoint t after which max PSRF < threshold (None if never)."""
+    T = trace.shape[1]
+    ts = np.arange(every, T + 1, every)
+    ps = np.array([max(dg.psrf(trace[s, t // 2:t, :].T) for s in range(trace.shape[0])) for t in ts])
+    above = np.nonzero(ps >= threshold)[0]
+    if above.size and above[-1] == len(ts) - 1:
+        return None
+    return int(ts[above[-1] + 1]) if above.size else int(ts[0])
+
+
+def _pd_trace(model, T, seed):
+    from paper_1611_06684_gb300 import mrf as M
+    h = M.MRF(model.n_vars, model.n_labels, C, seed=seed, use_graphs=True)
+    h.set_factors(model.unary, model.src, model.dst, model.pair)
+    tr = np.zeros((2, T, C))
+    for t in range(T):
+        h.sweep(1, M.MODE_PLAIN)
+        tr[:, t] = _stats(model, h.get_labels().astype(np.int64))
+    h.close()
+    return tr
+
+
+@pytest.mark.parametrize("beta", [0.1, 0.3, 0.5])
+def test_ising_grid_mixing_ratio(beta):
+    model = _grid(50, beta)
+    t0 = time.time()
+    mt_pd = mixing_time(_pd_trace(model, 2000, seed=int(beta * 1000) + 7))
+    rng = np.random.default_rng(int(beta * 1000) + 11)
+    x = rng.integers(0, 2, size=(C, model.n_vars))
+    classes = gibbs.grid_colour_classes(model.grid)
+    T = 800
+    tr = np.zeros((2, T, C))
+    for t in range(T):
+        gibbs.sweep_classes(model, x, rng, classes)
+        tr[:, t] = _stats(model, x)
+    mt_seq = mixing_time(tr)
+    print(f"grid 50x50 beta={beta}: primal-dual {mt_pd} sweeps, sequential {mt_seq} sweeps, "
+          f"ratio {None if not (mt_pd and mt_seq) else round(mt_pd / mt_seq, 2)} ({time.time() - t0:.1f} s)")
+    assert mt_pd is not None and mt_seq is not None
+    assert mt_pd >= mt_seq
+
+
+@pytest.mark.parametrize("k", [2])
+def test_random_graph_mixing_ratio(k):
+    model = wl.random_graph(1000, k=k, L=2, seed=k)
+    t0 = time.time()
+    mt_pd = mixing_time(_pd_trace(model, 3000, seed=100 + k))
+    rng = np.random.default_rng(200 + k)
+    x = rng.integers(0, 2, size=(C, model.n_vars))
+    inc = gibbs.incidence(model)
+    T = 300
+    tr = np.zeros((2, T, C))
+    for t in range(T):
+        gibbs.sweep(model, x, rng, inc=inc)
+        tr[:, t] = _stats(model, x)
+    mt_seq = mixing_time(tr)
+    print(f"random graph N=1000 k={k}: primal-dual {mt_pd} sweeps, sequential {mt_seq} sweeps, "
+          f"ratio {None if not (mt_pd and mt_seq) else round(mt_pd / mt_seq, 2)} ({time.time() - t0:.1f} s)")
+    assert mt_pd is not None and mt_seq is not None
+    assert mt_pd >= mt_seq
+
+
+@pytest.mark.parametrize("beta", [0.015])
+def test_complete_ising_sweeps_against_single_site_updates(beta):
+    model = wl.complete_ising(100, beta=beta, seed=3)
+    t0 = time.time()
+    mt_pd = mixing_time(_pd_trace(model, 2000, seed=300 + int(beta * 1e4)))
+    rng = np.random.default_rng(400 + int(beta * 1e4))
+    x = rng.integers(0, 2, size=(C, model.n_vars))
+    inc = gibbs.incidence(model)
+    T = 120                                       # sweeps of 100 single-site updates
+    tr = np.zeros((2, T * model.n_vars, C))
+    i = 0
+    for t in range(T):
+        for v in range(model.n_vars):
+            gibbs.sweep(model, x, rng, order=[v], inc=inc)
+            tr[:, i] = _stats(model, x)
+            i += 1
+    mt_ss = mixing_time(tr, every=model.n_vars // 10)
+    print(f"complete Ising N=100 beta={beta}: primal-dual {mt_pd} sweeps, sequential {mt_ss} single-site updates "
+          f"({time.time() - t0:.1f} s)")
+    assert mt_pd is not None and mt_ss is not None
+    assert mt_pd < mt_ss
