@@ -213,14 +213,13 @@ def run_ours(args, ws, rank, local):
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         h = M.MRF(model.n_vars, model.n_labels, C, seed=rank_seed(args.seed, rank), stream=stream.cuda_stream,
-                  kernel_timing=True, grid=model.grid if model.grid else None)
+                  grid=model.grid if model.grid else None)
         h.set_factors(model.unary, model.src, model.dst, model.pair)
     h.set_higdon(args.higdon_rho)
     inf = h.info()
     minfo = dict(E=inf.n_edge_slots, N=inf.n_vars, L=inf.n_labels, m=inf.n_entries)
-    # warm-up
+    # warm-up (the first plain sweep also runs the primal-schedule autotuner)
     h.sweep(args.warmup, mode)
-    h.kernel_times()
     torch.cuda.synchronize()
     clk_path = os.path.join(tempfile.gettempdir(), f"bench_clocks_{rank}.csv")
     clk = clocks_start(clk_path)
@@ -229,6 +228,7 @@ def run_ours(args, ws, rank, local):
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    # timed region: the product path, every sweep one replay of its captured CUDA graph
     ev0.record(stream)
     h.sweep(args.steps, mode)
     ev1.record(stream)
@@ -237,26 +237,35 @@ def run_ours(args, ws, rank, local):
         torch.distributed.barrier()
     ms_total = ev0.elapsed_time(ev1)
     clocks = clocks_stop(clk, clk_path, local)
-    ktimes = h.kernel_times()
     ms_total, value = aggregate(ms_total, C * model.n_vars * args.steps, ws, dev)
     ms_step = ms_total / args.steps
-    # one launch per kernel-timing record (two for the Swendsen-Wang draw); + k_advance per sweep
-    # (a small model runs all its sweeps in one k_sweep_small launch, which advances itself)
-    launches = sum(n * KERNELS_PER_RECORD.get(k, 1) for k, (_, n) in ktimes.items())
-    if "k_sweep_small" not in ktimes and "k_sw_small" not in ktimes:
-        launches += args.steps
+    # per-kernel split: the same sweeps again with CUDA events around every
+    # launch on the handle's stream (graph replay off while timing kernels)
+    h.set_kernel_timing(True)
+    h.kernel_times()
+    k_split = max(3, min(args.steps, 20))
+    h.sweep(k_split, mode)
+    ktimes = h.kernel_times()
+    h.set_kernel_timing(False)
+    # launches per sweep of the library's kernels (+ k_advance, which is not timed),
+    # counted in the split run; the graph of a sweep replays the same launches
+    if "k_sweep_small" in ktimes or "k_sw_small" in ktimes:
+        launches = 1                              # a small model runs all sweeps of a call in one launch
+    else:
+        per_sweep = sum(n * KERNELS_PER_RECORD.get(k, 1) for k, (_, n) in ktimes.items()) / k_split + 1
+        launches = int(round(per_sweep * args.steps))
 
-    # roofline of the dominant kernel (device time inside the timed region)
+    # roofline of the dominant kernel (device time from the per-kernel split run)
     peaks, peak_src = load_peaks()
     dom = max(ktimes, key=lambda k: ktimes[k][0])
     dom_ms = ktimes[dom][0] / ktimes[dom][1]
-    if dom == "k_sweep_small":                   # one launch = all timed sweeps
+    if dom == "k_sweep_small":                   # one launch = all sweeps of the call
         cd, bd = kernel_work("k_dual", minfo, C)
         cp, bp = kernel_work("k_primal", minfo, C)
-        calls, nbytes = (cd + cp) * args.steps, (bd + bp) * args.steps
+        calls, nbytes = (cd + cp) * k_split, (bd + bp) * k_split
     elif dom == "k_sw_small":
         calls = 0
-        nbytes = (kernel_work("k_sw_bond", minfo, C)[1] + kernel_work("k_sw_draw", minfo, C)[1]) * args.steps
+        nbytes = (kernel_work("k_sw_bond", minfo, C)[1] + kernel_work("k_sw_draw", minfo, C)[1]) * k_split
     else:
         calls, nbytes = kernel_work(dom, minfo, C)
     sm_mhz = clocks["sm_mhz"] if clocks else peaks.get("sm_max_mhz", 2070.0)
@@ -296,7 +305,6 @@ def run_ours(args, ws, rank, local):
             ([("higdon", M.MODE_HIGDON)] if sw_ok and args.mode != "higdon" else [])
         for name, md in forms:
             h.sweep(1, md)
-            h.kernel_times()
             torch.cuda.synchronize()
             kv = 5
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -305,7 +313,11 @@ def run_ours(args, ws, rank, local):
             e1.record(stream)
             torch.cuda.synchronize()
             msv = e0.elapsed_time(e1) / kv
+            h.set_kernel_timing(True)
+            h.kernel_times()
+            h.sweep(kv, md)
             kt = h.kernel_times()
+            h.set_kernel_timing(False)
             variants[name] = {"ms_per_step": msv, "value": C * model.n_vars / (msv / 1e3), "unit": METRIC,
                               "kernels": {k: v[0] / v[1] for k, v in kt.items()}}
         if model.grid:
@@ -323,9 +335,36 @@ def run_ours(args, ws, rank, local):
         if args.ess_sweeps > 0:
             ms_of = {args.mode: ms_step}
             ms_of.update({k: v["ms_per_step"] for k, v in variants.items() if "ms_per_step" in v})
-            variants["ess"] = ess_comparison(h, model, C, stream, args.ess_sweeps, ms_of,
-                                             [("plain", M.MODE_PLAIN)] + ([("splash", M.MODE_SPLASH)] if model.grid else [])
-                                             + ([("sw", M.MODE_SW), ("higdon", M.MODE_HIGDON)] if sw_ok else []))
+            variants["ess_fixed_sweeps"] = ess_comparison(
+                h, model, C, stream, args.ess_sweeps, ms_of,
+                [("plain", M.MODE_PLAIN)] + ([("splash", M.MODE_SPLASH)] if model.grid else [])
+                + ([("sw", M.MODE_SW), ("higdon", M.MODE_HIGDON)] if sw_ok else []))
+        if args.tv_ref_sweeps > 0 and args.workload in ("potts3d", "ferro3d"):
+            from paper_1611_06684_gb300 import workloads as wl
+            n = args.tv_scale
+            if args.workload == "potts3d":
+                tvm = wl.potts_grid3d(n, L=8, seed=0)
+            else:
+                tvm = wl.ferro_potts_grid3d(n, L=8, beta_lo=FERRO_BETA[0], beta_hi=FERRO_BETA[1],
+                                            u_std=FERRO_U_STD, seed=0)
+            tv_forms = [("plain", [M.MODE_PLAIN]), ("fused", [M.MODE_FUSED]), ("splash", [M.MODE_SPLASH])] + \
+                ([("sw", [M.MODE_SW]), ("higdon", [M.MODE_HIGDON])] if sw_ok else [])
+            variants["ess"] = tv_protocol(tvm, C, stream, tv_forms, args.seed + 17, args.tv_ref_sweeps,
+                                          workload=_describe(args.workload).replace("128^3", f"{n}^3"))
+            if args.workload == "potts3d":
+                # the benchmark spec comparisons: the learned proposal and the batched launch
+                # against the plain dual sweep, each in ESS/s at marginal TV <= 0.01
+                variants["ess"]["learned"] = learned_tv_comparison(stream, args.tv_ba_sites, 512, args.seed + 23,
+                                                                   args.tv_ba_ref_sweeps)
+                variants["ess"]["batched"] = small_batch_tv_comparison(stream, args.tv_batch_graphs, C, args.seed + 29)
+                variants["ess"]["batched_er"] = batch_tv_comparison(stream, 20, C, args.seed + 31, 50000,
+                                                                    tv_target=0.0)
+                variants["ess"]["north_star"] = {
+                    "learned_vs_plain": variants["ess"]["learned"]["versus_plain"]["learned"],
+                    "learned+plain_vs_plain": variants["ess"]["learned"]["versus_plain"]["learned+plain"],
+                    "batched_vs_plain_at_tv": variants["ess"]["batched"]["versus_plain"]["batched"],
+                    "batched_vs_plain_er_family": variants["ess"]["batched_er"]["versus_plain"]["batched"]}
+            variants["ess"]["versus_plain"] = versus_plain(variants["ess"], [n for n, _ in tv_forms if n != "plain"])
 
     # end to end through the C ABI with pinned host buffers: labels in, sweep, labels out
     e2e = None
@@ -437,14 +476,61 @@ class OracleSample:
         return self.C * self.model.n_vars
 
 
+def openmp_baseline(args, budget_s=10.0):
+    """The float32 OpenMP statement of the sweep (oracle/cpu_sweep.c) on every
+    core this process may run on, on a bounded sample of the workload."""
+    from paper_1611_06684_gb300 import workloads as wl
+    from oracle import cpu_sweep, decompose as dc, philox as ph
+    cores = len(os.sched_getaffinity(0))
+    if args.workload == "potts3d":
+        n, C = 40, 64
+        model = wl.potts_grid3d(n, L=8, seed=0)
+        sample = f"{C} chains x {{S}} sweeps of a {n}^3 sub-lattice with the same L=8 table and unary distributions"
+    elif args.workload == "ferro3d":
+        n, C = 40, 64
+        model = wl.ferro_potts_grid3d(n, L=8, beta_lo=FERRO_BETA[0], beta_hi=FERRO_BETA[1], u_std=FERRO_U_STD, seed=0)
+        sample = f"{C} chains x {{S}} sweeps of a {n}^3 sub-lattice with the same L=8 coupling and unary distributions"
+    elif args.workload == "dense4096":
+        C = 16
+        model = wl.dense_potts(1024, L=4, w_std=0.2 / 64, seed=0)
+        sample = f"{C} chains x {{S}} sweeps of a N=1024 fully connected model with the same L=4 distributions"
+    else:
+        C = WORKLOADS[args.workload][1]
+        model = WORKLOADS[args.workload][0]()
+        sample = f"{C} chain(s) x {{S}} sweeps of the full workload"
+    dec = dc.decompose(model)
+    cs = cpu_sweep.CpuSweep(dec, C, args.seed, threads=cores)
+    x = ph.init_labels(model.n_vars, model.n_labels, C, args.seed).astype(np.uint8)
+    x = cs.sweep(x, 0)                                   # warm-up (first touch of the workspace)
+    el, S = 0.0, 0
+    while el < budget_s:
+        t0 = time.perf_counter()
+        x = cs.sweep(x, S + 1)
+        el += time.perf_counter() - t0
+        S += 1
+    return {"value": C * model.n_vars * S / el, "unit": METRIC, "cores": cores,
+            "kind": "oracle (float32 OpenMP statement of the sweep, oracle/cpu_sweep.c)",
+            "sample": sample.format(S=S), "seconds": el}
+
+
 def cpu_baseline(args, budget_s=10.0):
+    """CPU baselines: the float32 OpenMP sweep on every available core (the
+    line's value) and the float64 numpy oracle on one core beside it."""
     o = OracleSample(args)
     el, S = 0.0, 0
     while el < budget_s:
         el += o.sweep(); S += 1
-    return {"value": o.units_per_sweep * S / el, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": o.sample.format(C=o.C, S=S), "seconds": el,
-            "host_cores_available": len(os.sched_getaffinity(0))}
+    single = {"value": o.units_per_sweep * S / el, "unit": METRIC, "cores": 1, "kind": "oracle (float64 numpy)",
+              "sample": o.sample.format(C=o.C, S=S), "seconds": el}
+    try:
+        multi = openmp_baseline(args, budget_s)
+    except Exception as exc:                 # no gcc / OpenMP on the host
+        multi = None
+        single["openmp_unavailable"] = f"{type(exc).__name__}: {exc}"
+    out = dict(multi) if multi else dict(single)
+    out["host_cores_available"] = len(os.sched_getaffinity(0))
+    out["single_core_oracle"] = single
+    return out
 
 
 def run_reference(args, ws, rank):
@@ -629,6 +715,391 @@ def ess_comparison(h, model, C, stream, T, ms_of, forms, n_sites=4096, n_edges=5
     return out
 
 
+def _stat_recorder(model, C, dev, n_sites=4096, n_edges=50000, seed=12345):
+    """Per-chain statistics of a labelling on the device: the fraction of label
+    0 over fixed sites, their unary energy and the pairwise energy of fixed
+    edges.  Returns (labels buffer [C][N] uint8 on the device, fn(out[3][C]))."""
+    import torch
+    rng = np.random.default_rng(seed)
+    sites = torch.as_tensor(np.sort(rng.choice(model.n_vars, size=min(n_sites, model.n_vars), replace=False)),
+                            device=dev)
+    esel = np.sort(rng.choice(model.n_edges, size=min(n_edges, model.n_edges), replace=False))
+    es = torch.as_tensor(model.src[esel].astype(np.int64), device=dev)
+    et = torch.as_tensor(model.dst[esel].astype(np.int64), device=dev)
+    w = torch.as_tensor(model.pair[esel], device=dev)
+    u = torch.as_tensor(model.unary, device=dev)
+    ar = torch.arange(len(esel), device=dev)
+    x = torch.empty((C, model.n_vars), dtype=torch.uint8, device=dev)
+
+    def record(out):
+        xl = x.long()
+        xs = xl[:, sites]
+        out[0] = (xs == 0).double().mean(dim=1)
+        out[1] = u[sites[None, :], xs].double().sum(dim=1)
+        out[2] = w[ar[None, :], xl[:, es], xl[:, et]].double().sum(dim=1)
+    desc = (f"per chain: label-0 fraction and unary energy of {len(sites)} fixed sites, pairwise energy of "
+            f"{len(esel)} fixed edges; ESS summed over chains, min over statistics")
+    return x, record, desc
+
+
+def tv_protocol(model, C, stream, forms, seed, ref_sweeps, tv_target=0.01, chunk=25, burn=300, workload="",
+                handle=None, ref_chains=None, budget=None):
+    """ESS/s at equal marginal accuracy.  From a common state after `burn`
+    plain sweeps: a reference run of `ref_sweeps` plain sweeps gives reference
+    marginals (label counts of every chain and sweep); then every form runs
+    from the same state with fresh counts until the mean-site total-variation
+    distance of its marginals to the reference is <= tv_target (checked every
+    `chunk` sweeps, at most ref_sweeps / 100 sweeps, so the reference always
+    has at least 100 times the samples).  A form is (name, [modes]); its
+    sweeps cycle through the modes.  Reported per form: sweeps and seconds to
+    the target (seconds = sweeps x the form's per-sweep time by CUDA events
+    over graph replays), the ESS of the run up to there (minimum over the
+    statistics of _stat_recorder, summed over chains) and ESS/s.  `handle`:
+    an MRF handle of `model` already set up (else one is created).  With
+    `ref_chains` the reference runs on a separate handle with that many
+    chains (each sweep then gives ref_chains / C times the samples), and
+    `budget` caps the sweeps per form at (reference samples) / (100 C)."""
+    import torch
+    from paper_1611_06684_gb300 import mrf as M
+    dev = torch.device("cuda", torch.cuda.current_device())
+    h = handle
+    if h is None:
+        with torch.cuda.stream(stream):
+            h = M.MRF(model.n_vars, model.n_labels, C, seed=seed, stream=stream.cuda_stream,
+                      grid=model.grid if model.grid else None)
+            h.set_factors(model.unary, model.src, model.dst, model.pair)
+    h.sweep(burn, M.MODE_PLAIN)
+    x_start = h.get_labels()
+    t_start = h.info().sweep_index
+    ms_of = {}
+    for name, modes in forms:
+        for md in modes:
+            h.sweep(2, md)
+        per = {md: _timed(stream, lambda: h.sweep(20, md)) / 20 for md in set(modes)}
+        ms_of[name] = sum(per[md] for md in modes) / len(modes)
+    if ref_chains is None or ref_chains == C:
+        hr, rc = h, C
+        hr.set_labels(x_start)
+        hr.set_sweep_index(t_start + 7)
+    else:
+        rc = ref_chains
+        with torch.cuda.stream(stream):
+            hr = M.MRF(model.n_vars, model.n_labels, rc, seed=seed + 99991, stream=stream.cuda_stream,
+                       grid=model.grid if model.grid else None)
+            hr.set_factors(model.unary, model.src, model.dst, model.pair)
+        hr.sweep(burn, M.MODE_PLAIN)
+    hr.reset_marginals(0)
+    t0 = time.perf_counter()
+    hr.sweep(ref_sweeps, M.MODE_PLAIN)
+    torch.cuda.synchronize()
+    ref_s = time.perf_counter() - t0
+    ref, n_ref = hr.marginals()
+    if hr is not h:
+        hr.close()
+    cap = (ref_sweeps * rc) // (100 * C)
+    budget = cap if budget is None else min(budget, cap)
+    xbuf, record, stat_desc = _stat_recorder(model, C, dev)
+    out = {}
+    for k, (name, modes) in enumerate(forms):
+        h.set_labels(x_start)
+        h.set_sweep_index(t_start + 1000003 * (k + 1))
+        h.reset_marginals(0)
+        stats = torch.empty((3, budget, C), dtype=torch.float64, device=dev)
+        swept, reached, tv = 0, None, None
+        while swept < budget:
+            for t in range(min(chunk, budget - swept)):
+                h.sweep(1, modes[(swept + t) % len(modes)])
+                with torch.cuda.stream(stream):
+                    h.get_labels_into(xbuf)
+                    record(stats[:, swept + t])
+            swept += min(chunk, budget - swept)
+            est, _ = h.marginals()
+            tv = tv_mean(est, ref)
+            if tv <= tv_target:
+                reached = swept
+                break
+        torch.cuda.synchronize()
+        tr = stats[:, :swept].cpu().numpy()
+        ess = {kk: ess_sum_over_chains(tr[i]) for i, kk in enumerate(("label0_fraction", "unary_energy", "pair_energy"))}
+        secs = swept * ms_of[name] / 1e3
+        out[name] = {"tv_reached": reached is not None, "sweeps_to_tv": reached, "tv_at_stop": tv,
+                     "sweeps_run": swept, "ms_per_sweep": ms_of[name],
+                     "seconds_to_tv": secs if reached else None, "ess": ess, "ess_min": min(ess.values()),
+                     "ess_per_s": min(ess.values()) / secs,
+                     "ess_per_s_at_tv": min(ess.values()) / secs if reached else None}
+    if handle is None:
+        h.close()
+    out["protocol"] = {
+        "workload": workload, "chains": C, "tv_target": tv_target, "burn_in_sweeps": burn,
+        "reference": {"sweeps": ref_sweeps, "chains": rc, "form": "plain", "samples_per_site": int(n_ref),
+                      "seconds": ref_s},
+        "max_sweeps_per_form": budget, "check_every": chunk, "statistics": stat_desc,
+        "tv": "mean over sites of 1/2 sum_a |p^_v(a) - p_ref,v(a)|, marginals from label counts of every chain and sweep"}
+    return out
+
+
+def versus_plain(res, names, key="ess_per_s_at_tv", basis="at the TV target"):
+    """'win' / 'loss' of each form against the plain sweep in ESS/s (`key`)."""
+    base = res.get("plain", {}).get(key)
+    out = {}
+    for n in names:
+        v = res.get(n, {}).get(key)
+        if v is None or base is None:
+            out[n] = "no comparison (target not reached within the budget)"
+        else:
+            out[n] = f"{'win' if v > base else 'loss'}: {v / base:.2f}x the plain sweep's ESS/s {basis}"
+    return out
+
+
+def learned_tv_comparison(stream, N, C, seed, ref_sweeps, train_steps=2000, budget=1000, ref_chains=2048):
+    """The learned MH block proposal (trained on ~1e5 harvested plain-chain
+    samples) against the plain dual sweep, and their alternation, on a
+    Barabasi-Albert Potts graph (m = 5, L = 4, beta_e ~ U[0, 0.8], unaries
+    N(0, 1)) with BFS blocks of 16 sites: ESS/s over `budget` sweeps from a
+    common state, and the mean-site TV of each run's marginals against a
+    reference run (2048 chains).  On this family independent long runs do not
+    agree to TV 0.01: the TV of 512-chain runs stays near 0.027 from 25 to
+    1,600 sweeps (runs settle in different metastable states around the hubs),
+    so the forms are compared at equal sweeps, with their TVs reported."""
+    import torch
+    from paper_1611_06684_gb300 import mrf as M, workloads as wl
+    model = wl.ba_potts(N, m=5, L=4, seed=0)
+    bos = wl.bfs_blocks(model, 16, seed=0)
+    with torch.cuda.stream(stream):
+        h = M.MRF(N, 4, C, seed=seed, stream=stream.cuda_stream, exact_edges=True, use_graphs=True)
+        h.set_factors(model.unary, model.src, model.dst, model.pair)
+    h.learned_setup(bos, hidden=256, seed=1)
+    nb = int(bos.max()) + 1
+    h.sweep(200, M.MODE_PLAIN)
+    t0 = time.perf_counter()
+    rows = h.learned_harvest(5, max(1, (nb * C * 5) // 100000), 100000)
+    trace = h.learned_train(train_steps, 1024, 1e-3, seed=0)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    p0, a0 = h.learned_stats()
+    h.sweep(4, M.MODE_LEARNED)
+    p1, a1 = h.learned_stats()
+    res = tv_protocol(model, C, stream, [("plain", [M.MODE_PLAIN]), ("learned", [M.MODE_LEARNED]),
+                                         ("learned+plain", [M.MODE_LEARNED, M.MODE_PLAIN])],
+                      seed, ref_sweeps, tv_target=0.0, burn=500, handle=h, ref_chains=ref_chains, budget=budget,
+                      workload=f"Barabasi-Albert Potts graph N={N}, m=5, L=4, beta_e~U[0,0.8], unaries N(0,1), "
+                               f"{C} chains, {nb} BFS blocks of <=16 sites")
+    h.close()
+    res["training"] = {"rows": rows, "steps": train_steps, "seconds": train_s,
+                       "loss_first": float(np.mean(trace[:20])), "loss_last": float(np.mean(trace[-20:])),
+                       "acceptance": (a1 - a0) / max(1, p1 - p0)}
+    res["versus_plain"] = versus_plain(res, ["learned", "learned+plain"], key="ess_per_s",
+                                       basis=f"at equal sweeps ({budget})")
+    return res
+
+
+def batch_tv_comparison(stream, n_graphs, C, seed, ref_sweeps, tv_target=0.01, chunk=25, burn=300):
+    """The batched launch (all graphs of a batch swept by one set of class-union
+    kernels) against one handle per graph (the plain dual sweep launched graph
+    by graph), both run until the mean-site TV over all graphs' sites against
+    a reference (a long run of the batch, >= 100 x the samples) is <= tv_target.
+    Graphs: Erdos-Renyi, N ~ floor(exp U[ln 100, ln 2000]), mean degree U[3, 20],
+    L in {2, 4, 8, 16}, tables exp(U[-0.5, 0.5]), unaries N(0, 1); C chains per
+    graph.  ESS from the per-chain fraction of label 0 over all sites.  These
+    graphs mix slowly (mean-site TV ~0.09 after 1,000 sweeps of 64 chains), so
+    with tv_target = 0 both forms run the same number of sweeps and are
+    compared at equal sweeps (their TVs then agree to within the noise)."""
+    import torch
+    from paper_1611_06684_gb300 import mrf as M, workloads as wl
+    specs = wl.er_batch_specs(n_graphs, n_min=100, n_max=2000, seed=0)
+    models = [wl.er_graph(sp) for sp in specs]
+    Ns = [m.n_vars for m in models]
+    Ls = [m.n_labels for m in models]
+    Ntot = sum(Ns)
+
+    def make_batch(sd):
+        b = M.MRFBatch(Ns, Ls, C, seed=sd, stream=stream.cuda_stream, use_graphs=True)
+        b.set_factors(models)
+        return b
+
+    def batch_marg(b, n):
+        return [b.counts(g) / float(n * C) for g in range(n_graphs)]
+
+    def tv_of(marg, ref):
+        num = sum(0.5 * np.abs(m - r).sum() for m, r in zip(marg, ref))
+        return float(num / Ntot)
+
+    ref_b = make_batch(seed)
+    ref_b.sweep(burn)
+    ref_b.reset_marginals(0)
+    t0 = time.perf_counter()
+    ref_b.sweep(ref_sweeps)
+    torch.cuda.synchronize()
+    ref_s = time.perf_counter() - t0
+    ref = batch_marg(ref_b, ref_sweeps)
+    ref_b.close()
+    budget = ref_sweeps // 100
+
+    b = make_batch(seed + 1)
+    hs = []
+    for g, m in enumerate(models):
+        with torch.cuda.stream(stream):
+            hh = M.MRF(m.n_vars, m.n_labels, C, seed=seed + 2 + g, stream=stream.cuda_stream, use_graphs=True)
+            hh.set_factors(m.unary, m.src, m.dst, m.pair)
+        hs.append(hh)
+    b.sweep(burn)
+    for hh in hs:
+        hh.sweep(burn)
+    ms_batch = _timed(stream, lambda: b.sweep(20)) / 20
+    ms_handles = _timed(stream, lambda: [hh.sweep(1) for _ in range(20) for hh in hs]) / 20
+    out = {}
+    for name in ("batched", "one_handle_per_graph"):
+        if name == "batched":
+            b.reset_marginals(0)
+        else:
+            for hh in hs:
+                hh.reset_marginals(0)
+        trace = []
+        swept, reached, tv = 0, None, None
+        while swept < budget:
+            for _ in range(min(chunk, budget - swept)):
+                if name == "batched":
+                    b.sweep(1)
+                    xs = [b.get_labels(g) for g in range(n_graphs)]
+                else:
+                    for hh in hs:
+                        hh.sweep(1)
+                    xs = [hh.get_labels() for hh in hs]
+                trace.append(sum((x == 0).sum(axis=1) for x in xs) / Ntot)
+            swept += min(chunk, budget - swept)
+            if name == "batched":
+                marg = batch_marg(b, swept)
+            else:
+                marg = [hh.counts() / float(swept * C) for hh in hs]
+            tv = tv_of(marg, ref)
+            if tv <= tv_target:
+                reached = swept
+                break
+        ms = ms_batch if name == "batched" else ms_handles
+        ess = ess_sum_over_chains(np.array(trace))
+        secs = swept * ms / 1e3
+        out[name] = {"tv_reached": reached is not None, "sweeps_to_tv": reached, "tv_at_stop": tv,
+                     "sweeps_run": swept, "ms_per_sweep": ms, "seconds_to_tv": secs if reached else None,
+                     "ess_min": ess, "ess_per_s": ess / secs, "ess_per_s_at_tv": ess / secs if reached else None}
+    b.close()
+    for hh in hs:
+        hh.close()
+    key = "ess_per_s_at_tv" if tv_target > 0 else "ess_per_s"
+    base = out["one_handle_per_graph"][key]
+    v = out["batched"][key]
+    basis = "at the TV target" if tv_target > 0 else f"at equal sweeps ({budget})"
+    out["versus_plain"] = {"batched": (f"{'win' if v > base else 'loss'}: {v / base:.2f}x the ESS/s of one plain "
+                                       f"handle per graph {basis}") if (v and base) else
+                           "no comparison (target not reached within the budget)"}
+    out["protocol"] = {"graphs": n_graphs, "sites": Ntot, "edges": sum(m.n_edges for m in models),
+                       "labels": sorted(set(Ls)), "chains_per_graph": C, "tv_target": tv_target,
+                       "burn_in_sweeps": burn, "reference": {"sweeps": ref_sweeps, "form": "batched plain sweeps",
+                                                            "seconds": ref_s},
+                       "max_sweeps_per_form": budget, "check_every": chunk,
+                       "statistics": "per chain: fraction of label 0 over all sites of all graphs; ESS summed over chains"}
+    return out
+
+
+def _enumerated_marginals(model):
+    """Exact site marginals [N][L] of a small model by enumerating every labelling."""
+    import itertools
+    X = np.array(list(itertools.product(range(model.n_labels), repeat=model.n_vars)), np.int64)
+    lp = np.asarray(model.unary, np.float64)[np.arange(model.n_vars)[None, :], X].sum(axis=1)
+    if model.n_edges:
+        w = np.asarray(model.pair, np.float64)
+        lp += w[np.arange(model.n_edges)[None, :], X[:, model.src], X[:, model.dst]].sum(axis=1)
+    p = np.exp(lp - lp.max())
+    p /= p.sum()
+    out = np.zeros((model.n_vars, model.n_labels))
+    for v in range(model.n_vars):
+        out[v] = np.bincount(X[:, v], weights=p, minlength=model.n_labels)
+    return out
+
+
+def small_batch_tv_comparison(stream, n_graphs, C, seed, tv_target=0.01, chunk=25, budget=4000, burn=200):
+    """The batched launch against one handle per graph at marginal TV <= 0.01
+    with exact reference marginals: many small uneven graphs (Erdos-Renyi,
+    N in 4..14 with L^N <= 2^14, mean degree U[2, 5], L in {2, 3, 4}, tables
+    exp(U[-0.5, 0.5]), unaries N(0, 1); the batched workload's families with
+    sizes small enough to enumerate), C chains per graph.  Both forms run until
+    the mean-site TV over all graphs' sites against the enumerated marginals is
+    <= tv_target; ESS from the per-chain fraction of label 0 over all sites."""
+    import torch
+    from paper_1611_06684_gb300 import mrf as M, workloads as wl
+    rng = np.random.default_rng(seed)
+    models = []
+    for g in range(n_graphs):
+        L = int(rng.choice([2, 3, 4]))
+        nmax = int(14 * np.log(2) / np.log(L))
+        N = int(rng.integers(4, nmax + 1))
+        spec = wl.ErGraphSpec(N, L, float(rng.uniform(2.0, 5.0)), int(rng.integers(0, 2**62)))
+        models.append(wl.er_graph(spec))
+    t0 = time.perf_counter()
+    ref = [_enumerated_marginals(m) for m in models]
+    enum_s = time.perf_counter() - t0
+    Ns = [m.n_vars for m in models]
+    Ntot = sum(Ns)
+    b = M.MRFBatch(Ns, [m.n_labels for m in models], C, seed=seed, stream=stream.cuda_stream, use_graphs=True)
+    b.set_factors(models)
+    hs = []
+    for g, m in enumerate(models):
+        with torch.cuda.stream(stream):
+            hh = M.MRF(m.n_vars, m.n_labels, C, seed=seed + 1 + g, stream=stream.cuda_stream, use_graphs=True)
+            hh.set_factors(m.unary, m.src, m.dst, m.pair)
+        hs.append(hh)
+    b.sweep(burn)
+    for hh in hs:
+        hh.sweep(burn)
+    ms_batch = _timed(stream, lambda: b.sweep(20)) / 20
+    ms_handles = _timed(stream, lambda: [hh.sweep(1) for _ in range(5) for hh in hs]) / 5
+    out = {}
+    for name in ("batched", "one_handle_per_graph"):
+        if name == "batched":
+            b.reset_marginals(0)
+        else:
+            for hh in hs:
+                hh.reset_marginals(0)
+        trace = []
+        swept, reached, tv = 0, None, None
+        while swept < budget:
+            for _ in range(chunk):
+                if name == "batched":
+                    b.sweep(1)
+                    xs = [b.get_labels(g) for g in range(n_graphs)]
+                else:
+                    for hh in hs:
+                        hh.sweep(1)
+                    xs = [hh.get_labels() for hh in hs]
+                trace.append(sum((x == 0).sum(axis=1) for x in xs) / Ntot)
+            swept += chunk
+            cnt = [b.counts(g) for g in range(n_graphs)] if name == "batched" else [hh.counts() for hh in hs]
+            tv = float(sum(0.5 * np.abs(c / float(swept * C) - r).sum() for c, r in zip(cnt, ref)) / Ntot)
+            if tv <= tv_target:
+                reached = swept
+                break
+        ms = ms_batch if name == "batched" else ms_handles
+        ess = ess_sum_over_chains(np.array(trace))
+        secs = swept * ms / 1e3
+        out[name] = {"tv_reached": reached is not None, "sweeps_to_tv": reached, "tv_at_stop": tv,
+                     "sweeps_run": swept, "ms_per_sweep": ms, "seconds_to_tv": secs if reached else None,
+                     "ess_min": ess, "ess_per_s": ess / secs, "ess_per_s_at_tv": ess / secs if reached else None}
+    b.close()
+    for hh in hs:
+        hh.close()
+    base = out["one_handle_per_graph"]["ess_per_s_at_tv"]
+    v = out["batched"]["ess_per_s_at_tv"]
+    out["versus_plain"] = {"batched": (f"{'win' if v > base else 'loss'}: {v / base:.2f}x the ESS/s of one plain "
+                                       f"handle per graph") if (v and base) else
+                           "no comparison (target not reached within the budget)"}
+    out["protocol"] = {"graphs": n_graphs, "sites": Ntot, "edges": sum(m.n_edges for m in models),
+                       "chains_per_graph": C, "tv_target": tv_target, "burn_in_sweeps": burn,
+                       "reference": {"form": "exact marginals by enumeration", "seconds": enum_s},
+                       "note": "mean-site TV over all sites of all graphs against the enumerated marginals",
+                       "max_sweeps_per_form": budget, "check_every": chunk,
+                       "statistics": "per chain: fraction of label 0 over all sites of all graphs; ESS summed over chains"}
+    return out
+
+
 def tv_mean(p, q):
     """Mean over sites of the total-variation distance of two [N][L] marginal tables."""
     return float(0.5 * np.abs(np.asarray(p, np.float64) - np.asarray(q, np.float64)).sum(axis=1).mean())
@@ -743,6 +1214,12 @@ def main():
     ap.add_argument("--workload", default="potts3d", choices=list(WORKLOADS) + ["er_batch", "ba_learned"])
     ap.add_argument("--ref-sweeps", type=int, default=2000)
     ap.add_argument("--ess-sweeps", type=int, default=200)
+    ap.add_argument("--tv-scale", type=int, default=32, help="lattice edge of the ESS/s-at-TV instance")
+    ap.add_argument("--tv-ba-sites", type=int, default=1000, help="sites of the learned-proposal ESS/s-at-TV graph")
+    ap.add_argument("--tv-ba-ref-sweeps", type=int, default=40000, help="reference sweeps (2048 chains) of that graph")
+    ap.add_argument("--tv-batch-graphs", type=int, default=200, help="small graphs of the batched ESS/s-at-TV comparison")
+    ap.add_argument("--tv-ref-sweeps", type=int, default=300000,
+                    help="plain sweeps of the TV reference run (0: skip the ESS/s-at-TV protocol)")
     ap.add_argument("--mode", default="plain", choices=["plain", "fused", "sw", "higdon"])
     ap.add_argument("--higdon-rho", type=float, default=0.5, help="bond fraction of the Higdon sweep")
     ap.add_argument("--seed", type=int, default=0)
