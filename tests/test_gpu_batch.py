@@ -117,3 +117,88 @@ def test_batch_counts_per_graph():
         c = b.counts(g)
         assert c.shape == (m.n_vars, m.n_labels)
         assert np.all(c.sum(1) == 4 * 2)
+
+
+def _host_memory_gb():
+    """Memory this process may use: MemAvailable, capped by a cgroup limit."""
+    avail = None
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                avail = int(line.split()[1]) / 2**20
+    except OSError:
+        pass
+    for path in ("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory/memory.limit_in_bytes"):
+        try:
+            v = open(path).read().strip()
+            if v.isdigit():
+                avail = min(avail or 1e9, int(v) / 2**30)
+        except OSError:
+            pass
+    return avail or 0.0
+
+
+def test_full_batch_2000_graphs_sampled_graphs_match_oracle():
+    """The batched workload at its stated size: 2000 Erdos-Renyi graphs
+    (N ~ floor(exp U[ln 100, ln 50000]), mean degree U[3, 20], L in
+    {2, 4, 8, 16}, tables exp(U[-0.5, 0.5]), one chain each), one sweep, one
+    edit round (1 % of every graph's edges removed, as many added), one more
+    sweep.  Per class of equal L the batch sweeps the disjoint union of its
+    graphs; a graph interacts only with its own edges, so the oracle sweeps
+    sampled graphs alone with their union site ids, edge slots and the class
+    key as RNG indices (the smallest and a random graph of every class)."""
+    torch = pytest.importorskip("torch")
+    if _host_memory_gb() < 160:
+        pytest.skip("the 2000-graph batch needs ~100 GB of host memory for its tables")
+    specs = wl.er_batch_specs(2000, seed=0)
+    models = [wl.er_graph(sp) for sp in specs]
+    C, seed = 1, 5
+    stream = torch.cuda.Stream()
+    b = M.MRFBatch([m.n_vars for m in models], [m.n_labels for m in models], C, seed=seed,
+                   stream=stream.cuda_stream, use_graphs=True)
+    b.set_factors(models)
+    rng = np.random.default_rng(11)
+    sample = []
+    for L in (2, 4, 8, 16):
+        ids = [g for g, m in enumerate(models) if m.n_labels == L]
+        sample += [min(ids, key=lambda g: models[g].n_vars), int(rng.choice(ids))]
+    for g in range(len(models)):
+        models[g].slots = np.arange(models[g].n_edges) + b.graph(g).first_edge_slot
+    checked = 0
+    for rnd in range(2):
+        t = rnd
+        before = {g: b.get_labels(g).astype(np.int64) for g in sample}
+        b.sweep(1, M.MODE_PLAIN)
+        torch.cuda.synchronize()
+        for g in sample:
+            m = models[g]
+            info = b.graph(g)
+            key = (seed + m.n_labels * M.BATCH_KEY_STEP) & (2**64 - 1)
+            order = np.argsort(m.slots)
+            sub = wl.Model(m.n_vars, m.n_labels, m.unary, m.src[order], m.dst[order], m.pair[order])
+            dec = dc.decompose(sub)
+            ref = sampler.sweep(dec, before[g], t, key, edge_ids=m.slots[order],
+                                site_ids=info.site_offset + np.arange(m.n_vars))
+            compare_sweep(dec, ref, b.get_labels(g))
+            checked += 1
+        if rnd == 0:
+            # one edit round on every graph
+            rm_g, rm_s, add_g, add_s, add_t, add_p, pend = [], [], [], [], [], [], []
+            for g, m in enumerate(models):
+                rem, s_new, t_new, p_new = wl.er_edit(m, 0.01, rng)
+                rm_g.append(np.full(len(rem), g)); rm_s.append(m.slots[rem])
+                add_g.append(np.full(len(s_new), g)); add_s.append(s_new); add_t.append(t_new)
+                add_p.append(p_new.ravel()); pend.append((rem, s_new, t_new, p_new))
+            ids = b.edit_factors(np.concatenate(rm_g), np.concatenate(rm_s), np.concatenate(add_g),
+                                 np.concatenate(add_s), np.concatenate(add_t), np.concatenate(add_p))
+            pos = 0
+            for g, m in enumerate(models):
+                rem, s_new, t_new, p_new = pend[g]
+                keep = np.ones(m.n_edges, bool); keep[rem] = False
+                m.src = np.concatenate([m.src[keep], s_new]).astype(np.int32)
+                m.dst = np.concatenate([m.dst[keep], t_new]).astype(np.int32)
+                m.pair = np.concatenate([m.pair[keep], p_new])
+                m.slots = np.concatenate([m.slots[keep], ids[pos:pos + len(s_new)]])
+                pos += len(s_new)
+    assert checked == 2 * len(sample)
+    b.close()

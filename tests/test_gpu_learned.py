@@ -81,10 +81,19 @@ def test_training_gradients_match_oracle():
         assert np.abs(gg - gr).max() <= 1e-2 * max(np.abs(gr).max(), 1e-6)
 
 
-@pytest.mark.parametrize("L,hidden", [(4, 256), (3, 64), (2, 128)])
+def _tc_weight_bytes(L, hidden):
+    """bf16 bytes of the tensor-core MLP's weight images (first layer padded to 64 columns)."""
+    kx = (16 * L + 31) // 32 * 32
+    return 2 * (hidden * ((kx + 63) // 64 * 64) + hidden * hidden + 16 * L * hidden)
+
+
+@pytest.mark.parametrize("L,hidden", [(4, 256), (3, 64), (2, 128), (10, 256), (16, 256)])
 def test_tensor_core_mlp_matches_gemm_path(L, hidden):
     """The fused tcgen05 MLP and the three mma.sync GEMMs give the same logits
-    from the same features (several 128-row tiles, a partial last tile)."""
+    from the same features (several 128-row tiles, a partial last tile).  With
+    L = 10 and 16 at hidden 256 the weights (311 KB, 393 KB) exceed the 200 KB
+    the kernel keeps resident in shared memory, so the streaming tcgen05
+    kernel (weights through a two-slot ring) is the one compared."""
     model = wl.ba_potts(1500, m=5, L=L, seed=11)
     bos = wl.bfs_blocks(model, 16, seed=3)
     C, seed, t = 24, 4, 9
@@ -102,9 +111,35 @@ def test_tensor_core_mlp_matches_gemm_path(L, hidden):
     (X0, z0), (X1, z1) = out
     assert np.array_equal(X0, X1)
     assert nb * C > 256
+    if L >= 10:
+        assert _tc_weight_bytes(L, hidden) > 200 * 1024
     err = np.abs(z0 - z1) / np.maximum(1.0, np.abs(z1))
     assert err.max() < 2e-2, err.max()
     assert np.median(err) < 1e-5, np.median(err)
+
+
+def test_streaming_tensor_core_mlp_matches_oracle():
+    """The streaming tcgen05 MLP (L = 12, hidden 256: 352 KB of weights) against
+    the float64 oracle with bf16 activations, from the GPU's own features."""
+    L, hidden = 12, 256
+    assert _tc_weight_bytes(L, hidden) > 200 * 1024
+    model = wl.ba_potts(1200, m=5, L=L, seed=12)
+    bos = wl.bfs_blocks(model, 16, seed=5)
+    C, seed, t = 16, 7, 3
+    h, params = _setup(model, C, seed, hidden, bos, mlp_path=0)
+    x0 = np.random.default_rng(9).integers(0, L, size=(C, model.n_vars)).astype(np.uint8)
+    h.set_labels(x0)
+    h.set_sweep_index(t)
+    h.sweep(1, M.MODE_LEARNED)
+    nb = int(bos.max()) + 1
+    d, dp = ln.feature_width(L)
+    X, z = h.learned_debug(nb * C, dp, 16 * L)
+    h.close()
+    zr = ln.mlp_forward_bf16(params, X.astype(np.float64))
+    err = np.abs(z - zr) / np.maximum(1.0, np.abs(zr))
+    row_moved = err.max(axis=1) > 1e-4           # a hidden value on a bf16 rounding boundary
+    assert err.max() < 5e-2 and row_moved.mean() < 0.02, (err.max(), row_moved.mean())
+    assert np.median(err) < 1e-4
 
 
 def test_learned_sweep_matches_oracle():

@@ -280,8 +280,11 @@ def test_device_pointer_inputs():
 
 
 def test_philox_matches_curand_and_oracle():
-    """Bit-level pin of both Philox4x32-10 implementations against CUDA's
-    curand_Philox4x32_10 (an independent implementation of the same definition)."""
+    """Bit-level pin of the Philox4x32-10 implementations against CUDA's
+    curand_Philox4x32_10 (an independent implementation of the same
+    definition): the oracle's, the device's with the key schedule, the one with
+    precomputed round keys (the hot path's) and the dual step's four calls
+    sharing their first rounds (draw_rk_subs)."""
     with tempfile.TemporaryDirectory() as d:
         so = os.path.join(d, "philox_check.so")
         subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-shared", "-Xcompiler", "-fPIC",
@@ -298,6 +301,14 @@ def test_philox_matches_curand_and_oracle():
             assert np.array_equal(mine, ref)
             orc = np.stack(ph.philox4x32_10(ctr[:, 0], ctr[:, 1], ctr[:, 2], ctr[:, 3], k0, k1), -1)
             assert np.array_equal(orc, ref)
+            mine = np.zeros((n, 4), np.uint32); ref = np.zeros((n, 4), np.uint32)
+            assert lib.philox_rk_pair(ctr.ctypes.data_as(ct.c_void_p), ct.c_uint32(k0), ct.c_uint32(k1),
+                                      mine.ctypes.data_as(ct.c_void_p), ref.ctypes.data_as(ct.c_void_p), n) == 0
+            assert np.array_equal(mine, ref)
+            mine = np.zeros((n, 4, 4), np.uint32); ref = np.zeros((n, 4, 4), np.uint32)
+            assert lib.philox_subs_pair(ctr.ctypes.data_as(ct.c_void_p), ct.c_uint32(k0), ct.c_uint32(k1),
+                                        mine.ctypes.data_as(ct.c_void_p), ref.ctypes.data_as(ct.c_void_p), n) == 0
+            assert np.array_equal(mine, ref)
 
 
 @pytest.mark.parametrize("name", ["ising32", "random_L3_dup", "potts_L16_diag", "star_degree700", "random_L16_C32"])
