@@ -106,6 +106,7 @@ struct SweepArgs {
     const float* utf;          // [N][L] folded unaries, float32
     const float* resid;        // [E][L][L] exact tree-edge potentials (blocked sweep)
     const int64_t* inc_ptr;    // [N+1]
+    int32_t max_deg;           // largest incidence count of a site (selects the primal kernels' one-batch form)
     const int2* inc;           // [2E] {edge*2 + side, neighbour}
     const double* ut;          // [N][L] folded unaries
     uint8_t* x;                // [2][N][C] label double buffer
@@ -237,6 +238,7 @@ cudaError_t launch_mf_pot(const SweepArgs& a, int layout, const float* qin, cuda
 cudaError_t launch_em_pot(const SweepArgs& a, int layout, const uint8_t* xin, cudaStream_t s);
 cudaError_t launch_potential(const SweepArgs& a, int layout, cudaStream_t s);
 cudaError_t launch_ffbs(const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_max_degree(const int64_t* ptr, int N, unsigned* out, cudaStream_t s);
 cudaError_t build_csr_device(const int32_t* src, const int32_t* dst, int64_t E, int N, int64_t* ptr, int2* inc,
                              int32_t* work, int64_t* sums, unsigned long long* too_long, int max_deg, cudaStream_t s);
 cudaError_t launch_scatter_edges(const int64_t* slots, const int32_t* s, const int32_t* t, int64_t n, int32_t* src,

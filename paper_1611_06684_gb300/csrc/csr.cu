@@ -110,6 +110,26 @@ cudaError_t launch_scatter_edges(const int64_t* slots, const int32_t* s, const i
     return cudaGetLastError();
 }
 
+// Largest incidence count of a site: atomicMax of ptr[v + 1] - ptr[v] into *out (zeroed by the caller).
+__global__ void k_max_degree(const int64_t* __restrict__ ptr, int N, unsigned* out) {
+    unsigned m = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
+        const int64_t d = ptr[v + 1] - ptr[v];
+        const unsigned du = d > 0x7FFFFFFF ? 0x7FFFFFFFu : (unsigned)d;
+        m = du > m ? du : m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned y = __shfl_xor_sync(0xFFFFFFFFu, m, o);
+        m = y > m ? y : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+cudaError_t launch_max_degree(const int64_t* ptr, int N, unsigned* out, cudaStream_t s) {
+    if (N > 0) k_max_degree<<<std::min(1216, (N + 255) / 256), 256, 0, s>>>(ptr, N, out);
+    return cudaGetLastError();
+}
+
 // work: int32 [2N + 2] scratch (degrees, cursors); sums: int64 [ceil((N+1)/1024) + 1].
 cudaError_t build_csr_device(const int32_t* src, const int32_t* dst, int64_t E, int N, int64_t* ptr, int2* inc,
                              int32_t* work, int64_t* sums, unsigned long long* too_long, int max_deg, cudaStream_t s) {

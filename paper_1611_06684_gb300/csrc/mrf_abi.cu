@@ -33,6 +33,7 @@ struct mrf {
     double* d_cst = nullptr;
     float* d_resid = nullptr;
     int64_t* d_inc_ptr = nullptr;
+    int32_t max_deg = 0;               // largest incidence count of a site
     int2* d_inc = nullptr;
     uint8_t* d_x = nullptr;
     uint32_t* d_theta = nullptr;
@@ -174,7 +175,7 @@ SweepArgs make_args(const mrf_t* h) {
     a.E = h->E_slots;
     a.src = h->d_src; a.dst = h->d_dst; a.tau = h->d_tau; a.thr = h->d_thr; a.resid = h->d_resid;
     a.tpl = h->d_tpl; a.utf = h->d_utf;
-    a.inc_ptr = h->d_inc_ptr; a.inc = h->d_inc; a.ut = h->d_ut;
+    a.inc_ptr = h->d_inc_ptr; a.inc = h->d_inc; a.ut = h->d_ut; a.max_deg = h->max_deg;
     a.x = h->d_x; a.theta = h->d_theta; a.counts = h->d_counts; a.logp = h->d_logp;
     a.lpv = h->lpv_on ? h->d_lpv : nullptr;
     a.ctl = h->d_ctl; a.key = h->key;
@@ -222,7 +223,9 @@ cudaError_t build_csr(mrf_t* h) {
         ptr[h->h_src[e] + 1]++;
         ptr[h->h_dst[e] + 1]++;
     }
-    for (int v = 0; v < h->N; ++v) ptr[v + 1] += ptr[v];
+    int64_t md = 0;
+    for (int v = 0; v < h->N; ++v) { md = std::max(md, ptr[v + 1]); ptr[v + 1] += ptr[v]; }
+    h->max_deg = (int32_t)std::min<int64_t>(md, 0x7FFFFFFF);
     std::vector<int2> inc((size_t)ptr[h->N]);
     std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
     for (int64_t e = 0; e < E; ++e) {
@@ -621,7 +624,18 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
     unsigned long long too_long = 0;
     MRF_CUDA(h, cudaMemcpyAsync(&too_long, h->d_flag, sizeof(too_long), cudaMemcpyDeviceToHost, h->stream));
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));
-    if (too_long) { MRF_CUDA(h, build_csr(h)); h->n_host_csr++; } else h->n_device_csr++;
+    if (too_long) {
+        MRF_CUDA(h, build_csr(h));
+        h->n_host_csr++;
+    } else {
+        h->n_device_csr++;
+        unsigned md = 0;
+        MRF_CUDA(h, cudaMemsetAsync(h->d_flag, 0, sizeof(unsigned long long), h->stream));
+        MRF_CUDA(h, launch_max_degree(h->d_inc_ptr, N, reinterpret_cast<unsigned*>(h->d_flag), h->stream));
+        MRF_CUDA(h, cudaMemcpyAsync(&md, h->d_flag, sizeof(md), cudaMemcpyDeviceToHost, h->stream));
+        MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+        h->max_deg = (int32_t)md;
+    }
     MRF_CUDA(h, launch_fold_unary(h->d_unary, h->d_fold, h->d_inc_ptr, h->d_inc, N, L, h->d_ut, h->d_utf, h->stream));
     if (h->d_swut)
         MRF_CUDA(h, launch_fold_unary(h->d_unary, h->d_swfold, h->d_inc_ptr, h->d_inc, N, L, h->d_swut, nullptr, h->stream));

@@ -533,57 +533,52 @@ __global__ void __launch_bounds__(256, FUSED ? 2 : 4) k_primal(SweepArgs a) {
 }
 
 // Warp-per-site form of the plain primal step (chains a multiple of 32, so a
-// warp is one site and 32 of its chains).  Incidences go in chunks of K: the
-// lanes load the chunk's incidence records in parallel, then the chunk's tau
-// rows into shared memory (one row per incidence, shared by the 32 chains)
-// while every lane loads its own theta words, so a chunk costs two dependent
-// memory latencies instead of one per incidence.  Same additions in the same
-// order as k_primal.
+// warp is one site and 32 of its chains).  BATCH (chosen by the host when no
+// site has more than KB incidences, e.g. every lattice): one batch per site --
+// the lanes load the incidence records in parallel, every lane issues the
+// theta loads of all incidences at once, the incidences' tau rows are staged
+// in shared memory (one row per incidence, shared by the 32 chains), then the
+// field is summed.  Otherwise chunks of K incidences (same pattern, a two-sum
+// flush of the partial sums every 32 incidences).  Both keep k_primal's order
+// of additions.
 template <int L, int LAYOUT>
 struct PrimalWarp {
     static constexpr int MP = Ent<L, LAYOUT>::MP;
-    static constexpr int K = 2;                          // incidences per chunk (larger K spills at 64 registers)
+    static constexpr int W = Ent<L, LAYOUT>::W;
+    static constexpr int K = 2;                          // incidences per chunk of the general path
+    static constexpr int KB = W >= 8 ? 2 : (W >= 4 ? 4 : 8);   // one-batch path: degree <= KB
     static constexpr int WARPS = 8;                      // 256 threads
 };
 
-template <int L, int LAYOUT, bool POT = false>
+template <int L, int LAYOUT, bool POT = false, bool BATCH = false>
 __global__ void __launch_bounds__(256, 4) k_primal_warp(SweepArgs a) {
     using E = Ent<L, LAYOUT>;
     using PW = PrimalWarp<L, LAYOUT>;
-    constexpr int K = PW::K, MP = PW::MP, Q = MP / 4;    // float4 per tau row
+    constexpr int K = PW::K, KB = PW::KB, MP = PW::MP, Q = MP / 4;    // float4 per tau row
     constexpr uint32_t FULL = 0xFFFFFFFFu;
-    __shared__ __align__(16) float4 s_tau[PW::WARPS][K][Q];
+    __shared__ __align__(16) float4 s_tau[PW::WARPS][KB > K ? KB : K][Q];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;     // N * C < 2^32, C % 32 == 0 (host)
     if (g >= (uint64_t)a.N * a.C) return;                         // whole warps only
     const uint32_t v = a.fdC.div(g), c = g - v * (uint32_t)a.C;
     const uint32_t sweep = (uint32_t)a.ctl->sweep;
     uint8_t* xout = a.x + (size_t)((sweep + 1) & 1) * a.N * a.C;
-    float acc[L], hi[L], lo[L];
-#pragma unroll
-    for (int x = 0; x < L; ++x) { acc[x] = 0.0f; hi[x] = 0.0f; lo[x] = 0.0f; }
     const int64_t p0 = a.inc_ptr[v], p1 = a.inc_ptr[v + 1];
     const float4* tau4 = reinterpret_cast<const float4*>(a.tau);
-    int chunk = 0;
-    bool flushed = false;
-    for (int64_t base = p0; base < p1; base += K) {              // warp-uniform
-        const int cnt = p1 - base < K ? (int)(p1 - base) : K;
-        const int code_l = lane < cnt ? __ldg(&a.inc[base + lane]).x : 0;
-        // tau rows of the chunk -> shared memory (uniform trip count; lanes split the float4s)
+    float F[L];
+    const float* uf = a.utf + (int64_t)v * L;
+    if constexpr (BATCH) {                                        // every site has at most KB incidences
+        const int deg = (int)(p1 - p0);
+        float acc[L];
 #pragma unroll
-        for (int i0 = 0; i0 < K * Q; i0 += 32) {
-            const int i = i0 + lane;
-            const int u = i / Q;
-            const int cu = __shfl_sync(FULL, code_l, u < K ? u : 0);
-            if (i < K * Q && u < cnt) s_tau[warp][u][i - u * Q] = __ldg(tau4 + (int64_t)(cu >> 1) * Q + (i - u * Q));
-        }
-        uint32_t bits[K][E::W];
-        int code[K];
+        for (int x = 0; x < L; ++x) acc[x] = 0.0f;
+        const int code_l = lane < deg ? __ldg(&a.inc[p0 + lane]).x : 0;
+        uint32_t bits[KB][E::W];
 #pragma unroll
-        for (int u = 0; u < K; ++u) {
-            code[u] = __shfl_sync(FULL, code_l, u);
-            if (u < cnt) {
-                const uint32_t* th = a.theta + ((int64_t)(code[u] >> 1) * a.C + c) * E::W;
+        for (int u = 0; u < KB; ++u) {
+            const int cu = __shfl_sync(FULL, code_l, u);
+            if (u < deg) {
+                const uint32_t* th = a.theta + ((int64_t)(cu >> 1) * a.C + c) * E::W;
                 if (E::W % 2 == 0) {
 #pragma unroll
                     for (int w = 0; w < E::W; w += 2) {
@@ -597,28 +592,80 @@ __global__ void __launch_bounds__(256, 4) k_primal_warp(SweepArgs a) {
                 }
             }
         }
+#pragma unroll
+        for (int i0 = 0; i0 < KB * Q; i0 += 32) {
+            const int i = i0 + lane;
+            const int u = i / Q;
+            const int cu = __shfl_sync(FULL, code_l, u < KB ? u : 0);
+            if (i < KB * Q && u < deg) s_tau[warp][u][i - u * Q] = __ldg(tau4 + (int64_t)(cu >> 1) * Q + (i - u * Q));
+        }
         __syncwarp();
 #pragma unroll
-        for (int u = 0; u < K; ++u) {
-            if (u >= cnt) break;
-            add_side<L, LAYOUT, false>(bits[u], reinterpret_cast<const float*>(&s_tau[warp][u][0]), code[u] & 1, acc);
-            if (++chunk == 32) {
-#pragma unroll
-                for (int x = 0; x < L; ++x) { two_sum_add(hi[x], lo[x], acc[x]); acc[x] = 0.0f; }
-                chunk = 0;
-                flushed = true;
-            }
+        for (int u = 0; u < KB; ++u) {
+            if (u >= deg) break;
+            const int cu = __shfl_sync(FULL, code_l, u);
+            add_side<L, LAYOUT, false>(bits[u], reinterpret_cast<const float*>(&s_tau[warp][u][0]), cu & 1, acc);
         }
-        __syncwarp();                                              // rows consumed before the next chunk
-    }
-    float F[L];
-    const float* uf = a.utf + (int64_t)v * L;
-    if (flushed) {
-#pragma unroll
-        for (int x = 0; x < L; ++x) { two_sum_add(hi[x], lo[x], acc[x]); F[x] = __ldg(uf + x) + (hi[x] + lo[x]); }
-    } else {
 #pragma unroll
         for (int x = 0; x < L; ++x) F[x] = __ldg(uf + x) + acc[x];
+    } else {
+        float acc[L], hi[L], lo[L];
+    #pragma unroll
+        for (int x = 0; x < L; ++x) { acc[x] = 0.0f; hi[x] = 0.0f; lo[x] = 0.0f; }
+        int chunk = 0;
+        bool flushed = false;
+        for (int64_t base = p0; base < p1; base += K) {              // warp-uniform
+            const int cnt = p1 - base < K ? (int)(p1 - base) : K;
+            const int code_l = lane < cnt ? __ldg(&a.inc[base + lane]).x : 0;
+            // tau rows of the chunk -> shared memory (uniform trip count; lanes split the float4s)
+    #pragma unroll
+            for (int i0 = 0; i0 < K * Q; i0 += 32) {
+                const int i = i0 + lane;
+                const int u = i / Q;
+                const int cu = __shfl_sync(FULL, code_l, u < K ? u : 0);
+                if (i < K * Q && u < cnt) s_tau[warp][u][i - u * Q] = __ldg(tau4 + (int64_t)(cu >> 1) * Q + (i - u * Q));
+            }
+            uint32_t bits[K][E::W];
+            int code[K];
+    #pragma unroll
+            for (int u = 0; u < K; ++u) {
+                code[u] = __shfl_sync(FULL, code_l, u);
+                if (u < cnt) {
+                    const uint32_t* th = a.theta + ((int64_t)(code[u] >> 1) * a.C + c) * E::W;
+                    if (E::W % 2 == 0) {
+    #pragma unroll
+                        for (int w = 0; w < E::W; w += 2) {
+                            const uint2 q = __ldcs(reinterpret_cast<const uint2*>(th + w));
+                            bits[u][w] = q.x;
+                            bits[u][w + 1 < E::W ? w + 1 : w] = q.y;
+                        }
+                    } else {
+    #pragma unroll
+                        for (int w = 0; w < E::W; ++w) bits[u][w] = __ldcs(th + w);
+                    }
+                }
+            }
+            __syncwarp();
+    #pragma unroll
+            for (int u = 0; u < K; ++u) {
+                if (u >= cnt) break;
+                add_side<L, LAYOUT, false>(bits[u], reinterpret_cast<const float*>(&s_tau[warp][u][0]), code[u] & 1, acc);
+                if (++chunk == 32) {
+    #pragma unroll
+                    for (int x = 0; x < L; ++x) { two_sum_add(hi[x], lo[x], acc[x]); acc[x] = 0.0f; }
+                    chunk = 0;
+                    flushed = true;
+                }
+            }
+            __syncwarp();                                              // rows consumed before the next chunk
+        }
+        if (flushed) {
+    #pragma unroll
+            for (int x = 0; x < L; ++x) { two_sum_add(hi[x], lo[x], acc[x]); F[x] = __ldg(uf + x) + (hi[x] + lo[x]); }
+        } else {
+    #pragma unroll
+            for (int x = 0; x < L; ++x) F[x] = __ldg(uf + x) + acc[x];
+        }
     }
     if (POT) {
         float* pv = a.pot + (int64_t)v * L * a.C + c;
@@ -956,9 +1003,12 @@ template <int L, int LAYOUT, bool FUSED>
 cudaError_t run_primal(const SweepArgs& a, cudaStream_t s) {
     const int64_t n = (int64_t)a.N * a.C;
     if (n <= 0) return cudaSuccess;
-    if (!FUSED && a.C % 32 == 0)
-        k_primal_warp<L, LAYOUT><<<blocks_for(n, 256), 256, 0, s>>>(a);
-    else
+    if (!FUSED && a.C % 32 == 0) {
+        if (a.max_deg <= PrimalWarp<L, LAYOUT>::KB)
+            k_primal_warp<L, LAYOUT, false, true><<<blocks_for(n, 256), 256, 0, s>>>(a);
+        else
+            k_primal_warp<L, LAYOUT><<<blocks_for(n, 256), 256, 0, s>>>(a);
+    } else
         k_primal<L, LAYOUT, FUSED><<<blocks_for(n, 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -967,9 +1017,12 @@ template <int L, int LAYOUT>
 cudaError_t run_potential(const SweepArgs& a, cudaStream_t s) {
     const int64_t n = (int64_t)a.N * a.C;
     if (n <= 0) return cudaSuccess;
-    if (a.C % 32 == 0)
-        k_primal_warp<L, LAYOUT, true><<<blocks_for(n, 256), 256, 0, s>>>(a);
-    else
+    if (a.C % 32 == 0) {
+        if (a.max_deg <= PrimalWarp<L, LAYOUT>::KB)
+            k_primal_warp<L, LAYOUT, true, true><<<blocks_for(n, 256), 256, 0, s>>>(a);
+        else
+            k_primal_warp<L, LAYOUT, true><<<blocks_for(n, 256), 256, 0, s>>>(a);
+    } else
         k_primal<L, LAYOUT, false, true><<<blocks_for(n, 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
