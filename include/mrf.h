@@ -415,7 +415,10 @@ mrf_status mrf_learned_debug(mrf_t* h, float* X, float* z);
  * layer, so its waits run out (after roughly a second); the kernel then
  * records the timeout, lets its own copies and MMAs finish, frees its tensor
  * memory and returns, and mrf_sweep returns MRF_ETIMEOUT.  The handle stays
- * usable.  The hook disarms itself after that sweep. */
+ * usable.  The hook disarms itself after that sweep.  (Should the kernel's
+ * own copies and MMAs not finish within the bound either, mrf_sweep returns
+ * MRF_ESTATE instead and refuses further learned sweeps on the handle, which
+ * must then be recreated.) */
 mrf_status mrf_debug_mlp_timeout(mrf_t* h, int32_t on);
 
 /* Capacity, in 32-bit words, of the fixed device array that holds the dual
@@ -424,10 +427,10 @@ mrf_status mrf_debug_mlp_timeout(mrf_t* h, int32_t on);
 
 /* One plain sweep that allocates no device memory.  The paper has no
  * counterpart: this is for callers that cannot allocate device memory at the
- * moment they sweep, such as code recording a stream into a CUDA graph under
- * a framework that forbids allocation during capture, or code that keeps all
- * device memory inside its own fixed pool and wants to push several label sets
- * of its own through one loaded model.
+ * moment they sweep, such as code running under a framework that forbids
+ * allocation at that point, or code that keeps all device memory inside its
+ * own fixed pool and wants to push several label sets of its own through one
+ * loaded model.
  *   h           a handle after mrf_set_factors (its tables are the inputs)
  *   labels_in   device pointer, [n_vars][n_chains] uint8 labels (chain
  *               innermost), the state before the sweep; not modified
@@ -443,7 +446,9 @@ mrf_status mrf_debug_mlp_timeout(mrf_t* h, int32_t on);
  * that device current); make that first call before any stream capture.  All
  * calls share the one array and each overwrites it, so calls whose work
  * overlaps on the GPU (other streams, other threads) race.  Work is enqueued
- * on the handle's stream; the call returns without synchronising.
+ * on the handle's stream; the call returns without synchronising.  These
+ * sweeps do not report draws within 1e-6 of a decision boundary (their
+ * counter lives in the shared array and is not read back).
  * Errors: MRF_ERANGE when edge slots x chains x ceil(m/32) exceeds
  * MRF_NOALLOC_THETA_WORDS; MRF_EINVAL for null or overlapping buffers;
  * MRF_ESTATE before mrf_set_factors. */

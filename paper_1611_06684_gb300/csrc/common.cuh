@@ -258,6 +258,10 @@ cudaError_t launch_learned_mlp_blocks(const LearnedArgs& a, cudaStream_t st);
 cudaError_t learned_gather(const LearnedArgs& a, const int32_t* idx, int R, __nv_bfloat16* X, uint8_t* y, uint8_t* nm,
                            cudaStream_t s);
 cudaError_t launch_to_bf16(const float* src, __nv_bfloat16* dst, int64_t n, cudaStream_t s);
+// Layout of the allocation-free sweep's scratch array (noalloc.cu): words
+// [0, kNoallocCtlWords) hold its control block, the dual bits follow.
+constexpr size_t kNoallocCtlWords = 64;
+static_assert(sizeof(Ctl) <= kNoallocCtlWords * sizeof(uint32_t), "control block larger than its reserved words");
 cudaError_t noalloc_scratch(uint32_t** out);
 cudaError_t launch_sweep_noalloc(const SweepArgs& a, int layout, const uint8_t* xin, uint8_t* xout, uint32_t sweep,
                                  cudaStream_t s);

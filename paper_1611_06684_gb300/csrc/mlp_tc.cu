@@ -21,7 +21,9 @@
 // plain byte copy lands them in the layout the tensor core expects; the copy
 // of the next chunk is in flight while the MMAs of the current one run.  Thread 0 issues the
 // copies and the MMAs; every wait is bounded and on a timeout the kernel
-// records an error, drains what it issued and frees its tensor memory.
+// records an error, drains what it issued and frees its tensor memory; if a
+// drain wait also gives up it sets a second error bit (the host then refuses
+// further learned sweeps on the handle, which must be recreated).
 #include "common.cuh"
 
 #include <cuda_bf16.h>
@@ -345,9 +347,10 @@ __global__ void __launch_bounds__(tc::THREADS, 2) k_mlp_tc(const MlpTc p) {
         if (tid == 0) {
             atomicOr(p.err, 1u);
             mma_commit(drain);                                     // completes after all issued MMAs
-            mbar_wait(drain, 0);
+            bool drained = mbar_wait(drain, 0);
             for (int64_t q = q_mma; q < q_load; ++q)                // copies issued but not consumed
-                mbar_wait(full0 + 8 * (int)(q % tc::NSLOT), (uint32_t)((q / tc::NSLOT) & 1));
+                drained &= mbar_wait(full0 + 8 * (int)(q % tc::NSLOT), (uint32_t)((q / tc::NSLOT) & 1));
+            if (!drained) atomicOr(p.err, 2u);                    // work may still be in flight: handle unusable
         }
     }
     tc_fence_before();
@@ -539,8 +542,9 @@ __global__ void __launch_bounds__(tcr::THREADS, 1) k_mlp_tc_resident(const MlpTc
         if (tid == 0) {
             atomicOr(p.err, 1u);
             mma_commit(drain);
-            mbar_wait(drain, 0);
-            mbar_wait(wbar, 0);
+            bool drained = mbar_wait(drain, 0);
+            drained &= mbar_wait(wbar, 0);
+            if (!drained) atomicOr(p.err, 2u);                    // work may still be in flight: handle unusable
         }
     }
     tc_fence_before();

@@ -104,6 +104,7 @@ struct mrf {
     double* d_loss = nullptr; int64_t loss_cap = 0;
     __nv_bfloat16* d_W1x = nullptr; __nv_bfloat16* d_cfb = nullptr; float* d_rowbias = nullptr;
     uint8_t* d_wimg = nullptr; unsigned* d_tc_err = nullptr;    // tensor-core MLP weight images, error flag
+    bool mlp_unusable = false;         // a timed-out tensor-core MLP did not drain: no further learned sweeps
     bool rowbias_dirty = true;
     unsigned long long* d_acc = nullptr;
     uint64_t proposed = 0;
@@ -886,6 +887,8 @@ mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode) {
         }
     }
     if (mode == MRF_MODE_LEARNED && !h->learned) return fail(h, MRF_ESTATE, "learned mode needs mrf_learned_setup");
+    if (mode == MRF_MODE_LEARNED && h->mlp_unusable)
+        return fail(h, MRF_ESTATE, "tensor-core MLP did not drain after a timeout; recreate the handle");
     if (mode == MRF_MODE_LEARNED && h->rowbias_dirty) {      // per-block first-layer bias of the current weights
         MRF_CUDA(h, learned_rowbias(h->la, h->stream));
         h->rowbias_dirty = false;
@@ -938,6 +941,11 @@ mrf_status mrf_sweep(mrf_t* h, int32_t n_sweeps, int32_t mode) {
             MRF_CUDA(h, cudaMemcpyAsync(&err, h->d_tc_err, sizeof(err), cudaMemcpyDeviceToHost, h->stream));
             MRF_CUDA(h, cudaStreamSynchronize(h->stream));
             if (h->la.tc_inject_timeout) { h->la.tc_inject_timeout = 0; drop_graphs(h); }
+            if (err & 2u) {
+                h->mlp_unusable = true;
+                return fail(h, MRF_ESTATE, "tensor-core MLP: a wait timed out and its work did not drain; "
+                                           "recreate the handle");
+            }
             if (err) {
                 MRF_CUDA(h, cudaMemsetAsync(h->d_tc_err, 0, sizeof(unsigned), h->stream));
                 return fail(h, MRF_ETIMEOUT, "tensor-core MLP: a wait timed out");
@@ -1409,7 +1417,7 @@ mrf_status mrf_sweep_noalloc(mrf_t* h, const uint8_t* labels_in, uint8_t* labels
     MRF_CUDA(h, noalloc_scratch(&scratch));
     SweepArgs a = make_args(h);
     a.ctl = reinterpret_cast<Ctl*>(scratch);
-    a.theta = scratch + 64;
+    a.theta = scratch + kNoallocCtlWords;
     a.logp = nullptr;
     MRF_CUDA(h, launch_sweep_noalloc(a, h->layout, labels_in, labels_out, (uint32_t)sweep_index, h->stream));
     return MRF_OK;

@@ -16,7 +16,6 @@
 namespace mrfk {
 
 // words [0, kNoallocCtlWords): control block (boundary counter); then theta.
-constexpr size_t kNoallocCtlWords = 64;
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoallocCtlWords + MRF_NOALLOC_THETA_WORDS];
 
 namespace {

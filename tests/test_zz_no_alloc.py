@@ -1,7 +1,7 @@
 """mrf_sweep_noalloc: the plain sweep for callers that cannot allocate device
-memory when they sweep (for instance while a framework records a stream into
-a CUDA graph and forbids allocation, or when all device memory comes from the
-caller's own fixed pool).  It keeps the dual bits in a fixed device array
+memory when they sweep (for instance under a framework that forbids
+allocation at that point, or when all device memory comes from the caller's
+own fixed pool).  It keeps the dual bits in a fixed device array
 inside the library and uses label buffers the caller owns; its result must
 equal the handle's ordinary plain sweep from the same state.  This file is
 collected last so that a run stopping at the first failure has already run
