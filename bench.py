@@ -118,6 +118,9 @@ PHILOX_FMAHEAVY_CYCLES_PER_WARP_CALL = 61.5
 
 
 def _describe(workload):
+    if workload == "er_batch":
+        return ("2000 Erdos-Renyi graphs, N ~ logU[100, 50000], mean degree U[3, 20], L in {2,4,8,16}, "
+                "tables exp(U[-0.5,0.5]), 1 chain each; 1% edits every 10 sweeps")
     desc = WORKLOADS[workload][2]
     return desc % (FERRO_BETA[0], FERRO_BETA[1], FERRO_U_STD) if "%g" in desc else desc
 
@@ -439,6 +442,14 @@ class OracleSample:
             self.C = 1
             model = wl.dense_potts(256, L=4, w_std=0.2 / 64, seed=0)
             self.sample = "{C} chain x {S} sweeps of a N=256 fully connected model with the same L=4 distributions"
+        elif args.workload == "er_batch":
+            self.C = 1
+            ms = [wl.er_graph(sp) for sp in wl.er_batch_specs(args.scale or 2000, seed=0)[:4]]
+            self.parts = [(dc.decompose(m), ph.init_labels(m.n_vars, m.n_labels, 1, args.seed)) for m in ms]
+            self.n_sites = sum(m.n_vars for m in ms)
+            self.sample = "{C} chain x {S} sweeps of the first 4 of the batch's graphs (%d sites)" % self.n_sites
+            self.mode, self.seed, self.t = "batch", args.seed, 0
+            return
         else:
             self.C = 1
             model = WORKLOADS[args.workload][0]()
@@ -456,7 +467,9 @@ class OracleSample:
         """One oracle sweep; returns its wall time in seconds."""
         from oracle import sampler, swendsen_wang
         t0 = time.perf_counter()
-        if self.mode == "sw":
+        if self.mode == "batch":
+            self.parts = [(d, sampler.sweep(d, x, self.t, self.seed)["x"]) for d, x in self.parts]
+        elif self.mode == "sw":
             if self.sw_tables is None:
                 self.sw_tables = swendsen_wang.sw_tables(self.model)
             self.x = swendsen_wang.sw_sweep(self.model, self.x, self.t, self.seed, tables=self.sw_tables)["x"]
@@ -473,7 +486,7 @@ class OracleSample:
 
     @property
     def units_per_sweep(self):
-        return self.C * self.model.n_vars
+        return self.C * (self.n_sites if self.mode == "batch" else self.model.n_vars)
 
 
 def openmp_baseline(args, budget_s=10.0):
@@ -564,79 +577,195 @@ def _timed(stream, fn):
     return e0.elapsed_time(e1)
 
 
+def batch_cpu_baseline(models, seed, budget_s=10.0):
+    """CPU baselines of the batched workload on a bounded sample: the float32
+    OpenMP sweep (all cores) over the class unions of the sample's graphs, and
+    the float64 numpy oracle (one core) beside it."""
+    from oracle import cpu_sweep, decompose as dc, philox as ph, sampler
+    cores = len(os.sched_getaffinity(0))
+    sample = models[:40]
+    unions = []
+    for L in sorted(set(m.n_labels for m in sample)):
+        ms = [m for m in sample if m.n_labels == L]
+        off = np.cumsum([0] + [m.n_vars for m in ms])[:-1]
+        from paper_1611_06684_gb300 import workloads as wl
+        unions.append(wl.Model(int(sum(m.n_vars for m in ms)), L, np.concatenate([m.unary for m in ms]),
+                               np.concatenate([m.src + o for m, o in zip(ms, off)]).astype(np.int32),
+                               np.concatenate([m.dst + o for m, o in zip(ms, off)]).astype(np.int32),
+                               np.concatenate([m.pair for m in ms])))
+    n_sites = sum(u.n_vars for u in unions)
+    decs = [dc.decompose(u) for u in unions]
+    sweeps = [cpu_sweep.CpuSweep(d, 1, seed, threads=cores) for d in decs]
+    xs = [ph.init_labels(u.n_vars, u.n_labels, 1, seed).astype(np.uint8) for u in unions]
+    xs = [cs.sweep(x, 0) for cs, x in zip(sweeps, xs)]
+    el, S = 0.0, 0
+    while el < budget_s:
+        t0 = time.perf_counter()
+        xs = [cs.sweep(x, S + 1) for cs, x in zip(sweeps, xs)]
+        el += time.perf_counter() - t0
+        S += 1
+    multi = {"value": n_sites * S / el, "unit": METRIC, "cores": cores,
+             "kind": "oracle (float32 OpenMP statement of the sweep, oracle/cpu_sweep.c)",
+             "sample": f"{len(sample)} of the graphs ({n_sites} sites, their class unions), 1 chain x {S} sweeps",
+             "seconds": el}
+    small = models[:4]
+    xo = [ph.init_labels(m.n_vars, m.n_labels, 1, seed) for m in small]
+    do = [dc.decompose(m) for m in small]
+    el1, S1 = 0.0, 0
+    while el1 < budget_s:
+        t0 = time.perf_counter()
+        xo = [sampler.sweep(d, x, S1, seed)["x"] for d, x in zip(do, xo)]
+        el1 += time.perf_counter() - t0
+        S1 += 1
+    multi["single_core_oracle"] = {"value": sum(m.n_vars for m in small) * S1 / el1, "unit": METRIC, "cores": 1,
+                                   "kind": "oracle (float64 numpy)",
+                                   "sample": f"{len(small)} of the graphs, 1 chain x {S1} sweeps", "seconds": el1}
+    multi["host_cores_available"] = cores
+    return multi
+
+
 def run_batch_workload(args):
     """Batched dynamic workload: many Erdos-Renyi graphs (sizes logU[100, 50000],
     mean degree U[3, 20], L in {2,4,8,16}, tables exp(U[-0.5, 0.5])), one chain
-    each; a round = one edit (remove ceil(1%) of every graph's edges, add as many
-    with fresh tables) + 10 sweeps.  Compared with one handle per graph."""
+    each.  A step is one round: an edit (remove ceil(1%) of every graph's edges,
+    add as many with fresh tables) applied by the device edit queue, then 10
+    sweeps, replayed as one CUDA graph.  The edit's inputs are resident in
+    device memory when the timed region starts (the end-to-end figure copies
+    them from pinned host memory and reads the added edges' slots back)."""
     import torch
     from paper_1611_06684_gb300 import build as B, mrf as M, workloads as wl
     B.build()
-    n_graphs = args.scale or 500
+    n_graphs = args.scale or 2000
     specs = wl.er_batch_specs(n_graphs, seed=0)
     t0 = time.time()
     models = [wl.er_graph(sp) for sp in specs]
     gen_s = time.time() - t0
     stream = torch.cuda.Stream()
-    b = M.MRFBatch([m.n_vars for m in models], [m.n_labels for m in models], 1, seed=args.seed,
+    C = 1
+    b = M.MRFBatch([m.n_vars for m in models], [m.n_labels for m in models], C, seed=args.seed,
                    stream=stream.cuda_stream, use_graphs=True)
     b.set_factors(models)
-    for g, m in enumerate(models):
-        m.slots = np.arange(m.n_edges) + b.graph(g).first_edge_slot
-    rng = np.random.default_rng(1)
     N = sum(m.n_vars for m in models)
-    sweeps_per_round = 10
-    times, edit_times = [], []
-    for r in range(args.warmup + args.steps):
-        # the edit's inputs are drawn (untimed), then the library edits and sweeps (timed)
-        rm_g, rm_s, ad_g, ad_s, ad_t, ad_p, pend = [], [], [], [], [], [], []
-        for g, m in enumerate(models):
-            rem, s_, t_, p_ = wl.er_edit(m, 0.01, rng)
-            rm_g.append(np.full(len(rem), g)); rm_s.append(m.slots[rem])
-            ad_g.append(np.full(len(s_), g)); ad_s.append(s_); ad_t.append(t_); ad_p.append(p_.ravel())
-            pend.append((rem, s_, t_, p_))
-        args_e = (np.concatenate(rm_g), np.concatenate(rm_s), np.concatenate(ad_g), np.concatenate(ad_s),
-                  np.concatenate(ad_t), np.concatenate(ad_p))
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        ids = b.edit_factors(*args_e)
-        torch.cuda.synchronize()
-        t_edit = time.perf_counter()
-        b.sweep(sweeps_per_round, M.MODE_PLAIN)
-        torch.cuda.synchronize()
-        times.append(time.perf_counter() - t1)
-        edit_times.append(t_edit - t1)
-        pos = 0
-        for g, m in enumerate(models):
-            rem, s_, t_, p_ = pend[g]
-            keep = np.ones(m.n_edges, bool); keep[rem] = False
-            m.src = np.concatenate([m.src[keep], s_]).astype(np.int32)
-            m.dst = np.concatenate([m.dst[keep], t_]).astype(np.int32)
-            m.pair = np.concatenate([m.pair[keep], p_])
-            m.slots = np.concatenate([m.slots[keep], ids[pos:pos + len(s_)]]); pos += len(s_)
     E = sum(m.n_edges for m in models)
-    dt = sum(times[args.warmup:])
-    value = N * sweeps_per_round * args.steps / dt
-    # sweep-only throughput of the batch (CUDA events)
+    ed = wl.ErBatchEdits(models, [b.graph(g).first_edge_slot for g in range(n_graphs)], seed=1)
+    k = ed.counts(0.01)
+    n_edit = int(k.sum())
+    L_g = np.array([m.n_labels for m in models], np.int64)
+    pair_max = int((k * L_g * L_g).sum())
+    b.queue_create(n_edit, n_edit, pair_max, extra_slots=1024)
+    sweeps_per_round = 10
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def staged(arrays, where):
+        if where == "device":
+            return [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in arrays]
+        return [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in arrays]
+
+    def one_round(where, timed_list, e2e_list=None):
+        arrays = ed.edit(0.01)                                   # untimed: draw the edit on the host
+        st = staged(arrays, where)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0 = time.perf_counter()
+        e0.record(stream)
+        b.queue_load(*st)
+        b.round(sweeps_per_round)
+        e1.record(stream)
+        status, slots = b.queue_result(len(arrays[3]))           # device -> host: status and the new slots
+        w1 = time.perf_counter()
+        if status != 0:
+            raise RuntimeError(f"queue round rejected its edit: status {status}")
+        timed_list.append(e0.elapsed_time(e1))
+        if e2e_list is not None:
+            e2e_list.append((w1 - w0, sum(a.nbytes for a in arrays), 8 * len(slots) + 4))
+        ed.apply(slots)
+
+    warm = []
+    for _ in range(args.warmup):
+        one_round("device", warm)
+    clk_path = os.path.join(tempfile.gettempdir(), "bench_clocks_batch.csv")
+    clk = clocks_start(clk_path)
+    time.sleep(0.3)
+    times = []
+    for _ in range(args.steps):
+        one_round("device", times)
+    clocks = clocks_stop(clk, clk_path, torch.cuda.current_device())
+    ms_round = float(np.mean(times))
+    value = N * C * sweeps_per_round / (ms_round / 1e3)
+    # end to end: the edit's arrays from pinned host memory, the slots read back
+    e2e_rounds, e2e_ms = [], []
+    for _ in range(max(3, min(args.steps, 5))):
+        one_round("host", e2e_ms, e2e_rounds)
+    e2e = {"value": N * C * sweeps_per_round * len(e2e_rounds) / sum(r[0] for r in e2e_rounds), "unit": METRIC,
+           "h2d_bytes_per_step": int(np.mean([r[1] for r in e2e_rounds])),
+           "d2h_bytes_per_step": int(np.mean([r[2] for r in e2e_rounds])), "steps": len(e2e_rounds),
+           "api": "mrf_batch_queue_load(pinned host arrays) + mrf_batch_round(10) + mrf_batch_queue_result"}
+    # sweeps alone, and the per-kernel split of one sweep of every class (CUDA events)
     ms_sweep = _timed(stream, lambda: b.sweep(sweeps_per_round, M.MODE_PLAIN)) / sweeps_per_round
-    # the same graphs with one handle each (a subset, to bound the time)
-    sub = models[: min(len(models), 100)]
-    hs = []
-    for m in sub:
-        h = M.MRF(m.n_vars, m.n_labels, 1, seed=1, stream=stream.cuda_stream, use_graphs=False)
-        h.set_factors(m.unary, m.src, m.dst, m.pair)
-        h.sweep(1, M.MODE_PLAIN)
-        hs.append(h)
-    ms_sep = _timed(stream, lambda: [h.sweep(1, M.MODE_PLAIN) for h in hs])
-    n_sub = sum(m.n_vars for m in sub)
-    return {"metric": METRIC, "workload": f"er_batch_{n_graphs}", "value": value, "unit": METRIC,
-            "n_vars": N, "n_edges": E, "graphs": n_graphs, "rounds": args.steps,
-            "round": "edit(1% remove + 1% add, every graph) + 10 sweeps", "generation_s": gen_s,
-            "edit_s_per_round": float(np.mean(edit_times[args.warmup:])),
-            "edges_edited_per_round": int(sum(math.ceil(0.01 * m.n_edges) for m in models)),
-            "sweep_only": {"ms_per_sweep": ms_sweep, "value": N / (ms_sweep / 1e3)},
-            "one_handle_per_graph": {"graphs": len(sub), "ms_per_sweep": ms_sep, "value": n_sub / (ms_sep / 1e3)},
-            "classes": [b.class_handle(k).info().n_labels for k in range(b.n_classes())]}
+    b.set_kernel_timing(True)
+    for kk in range(b.n_classes()):
+        b.class_handle(kk).kernel_times()
+    b.sweep(3, M.MODE_PLAIN)
+    torch.cuda.synchronize()
+    per_class, dom = [], None
+    for kk in range(b.n_classes()):
+        hk = b.class_handle(kk)
+        inf = hk.info()
+        kt = {n: v[0] / v[1] for n, v in hk.kernel_times().items()}
+        row = {"L": hk.L, "sites": hk.N, "edges": int(inf.n_edges), "edge_slots": int(inf.n_edge_slots),
+               "dual_bits_per_edge": int(inf.n_entries), "kernels_ms": kt}
+        per_class.append(row)
+        for name, ms in kt.items():
+            if dom is None or ms > dom[2]:
+                dom = (row, name, ms)
+    b.set_kernel_timing(False)
+    # the host-side edit of the same size, for comparison (one round)
+    arrays = ed.edit(0.01)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    slots = b.edit_factors(*arrays)
+    torch.cuda.synchronize()
+    host_edit_s = time.perf_counter() - t1
+    ed.apply(slots)
+    peaks, peak_src = load_peaks()
+    row, name, dom_ms = dom
+    minfo = dict(E=row["edges"], N=row["sites"], L=row["L"], m=row["dual_bits_per_edge"])
+    _, nbytes = kernel_work(name, minfo, C)
+    roof = {"bound": "hbm", "achieved": nbytes / (dom_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "traffic": None, "kernel": f"{name} (class L={row['L']})", "bytes_per_launch": nbytes,
+            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    # the whole sweep against the method's own minimum (each class's tables read once, labels, incidence lists)
+    sweep_bytes = sum(r["edges"] * r["dual_bits_per_edge"] * 4 + r["edges"] * 24 + r["sites"] * (r["L"] * 4 + 2 * C)
+                      for r in per_class)
+    roof["sweep_view"] = {"bytes_per_sweep": sweep_bytes, "ms_per_sweep": ms_sweep,
+                          "achieved": sweep_bytes / (ms_sweep / 1e3) / 1e9,
+                          "frac": sweep_bytes / (ms_sweep / 1e3) / 1e9 / peaks["hbm_gbs"],
+                          "counted": "tables once (4 B per dual entry), endpoints (8 B) and two incidence records "
+                                     "(16 B) per edge, unaries (4 B per label) and labels in and out per site"}
+    K = b.n_classes()
+    launches_per_round = 4 + 15 * K + 1 + sweeps_per_round * 4 * K
+    cpu = None if args.no_cpu else batch_cpu_baseline(models, args.seed)
+    return {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_round, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "u32+f32 (dual step: u32 Philox and threshold compare; primal step: f32 with two-sum accumulation)",
+            "data": "synthetic (seeded generators)",
+            "config": {"workload": f"er_batch_{n_graphs}",
+                       "description": f"{n_graphs} Erdos-Renyi graphs, N ~ logU[100, 50000], mean degree U[3, 20], "
+                                      "L in {2,4,8,16}, tables exp(U[-0.5,0.5]), unaries N(0,1), 1 chain each",
+                       "n_vars": N, "n_edges": E, "graphs": n_graphs, "chains": C,
+                       "step": "one round: edit (remove ceil(1%) of every graph's edges, add as many) + 10 sweeps, "
+                               "one CUDA graph replay",
+                       "edges_edited_per_round": n_edit,
+                       "l2": "inputs larger than L2 (tables are tens of GB); no flush needed",
+                       "parallelism": "one GPU"},
+            "roofline": roof, "gpu_launches": launches_per_round * args.steps,
+            "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+            "sweep_only": {"ms_per_sweep": ms_sweep, "value": N * C / (ms_sweep / 1e3)},
+            "edit_in_round_ms": ms_round - sweeps_per_round * ms_sweep,
+            "host_edit_ms": host_edit_s * 1e3,
+            "classes": per_class, "generation_s": gen_s}
 
 
 def ess_sum_over_chains(trace):

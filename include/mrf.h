@@ -354,11 +354,74 @@ mrf_status mrf_batch_edit_factors(mrf_batch_t* b, int64_t n_remove, const int32_
 
 /* n_sweeps sweeps of every graph (MRF_MODE_PLAIN or MRF_MODE_FUSED). */
 mrf_status mrf_batch_sweep(mrf_batch_t* b, int32_t n_sweeps, int32_t mode);
+
+/* ---- Device edit queue of a batch (dynamic networks: abstract, Section 6) ----
+ * The edits of a round are staged in device buffers and applied by kernels
+ * inside the round {edit, n sweeps}, which replays as one CUDA graph: the
+ * route of every removal and addition to its class, the checks, the slot
+ * rule of mrf_batch_edit_factors (freed slots reused in increasing order,
+ * then fresh ones), the decomposition (Sections 4.1-4.2) of the new tables,
+ * the incidence lists and the folded unaries, then the sweeps.  A rejected
+ * edit changes nothing (the sweeps still run); its reasons are status bits: */
+enum {
+    MRF_Q_COUNT = 1,          /* staged counts above the queue's capacities           */
+    MRF_Q_GRAPH = 2,          /* graph id out of range                                */
+    MRF_Q_VERTEX = 4,         /* vertex id out of range                               */
+    MRF_Q_LOOP = 8,           /* self-loop                                            */
+    MRF_Q_SLOT = 16,          /* removed slot is not a live edge of the graph's class */
+    MRF_Q_DUP = 32,           /* slot removed twice                                   */
+    MRF_Q_NONFINITE = 64,     /* non-finite table value                               */
+    MRF_Q_OFFDIAG = 128,      /* off-diagonal value in a diagonal-layout class        */
+    MRF_Q_PAIR = 256,         /* table floats differ from n_pair or exceed capacity   */
+    MRF_Q_SLOTS = 512,        /* a class has too few free slots for its additions     */
+    MRF_Q_UNSORTED = 1024     /* (edit applied) a site with more than 25,600 incidences
+                                 kept an unsorted incidence list: its field sums run
+                                 in another order                                      */
+};
+
+/* Queue of at most max_remove removals, max_add additions and max_pair_floats
+ * table floats per round.  Every class keeps extra_slots free edge slots
+ * beyond its live edges (reserved when a round is first prepared and after
+ * each host-side change); a round whose additions need more free slots in a
+ * class than it has fails with MRF_Q_SLOTS.  Creating a queue again replaces
+ * the previous one.  MRF_EINVAL for negative sizes, MRF_ENOMEM. */
+mrf_status mrf_batch_queue_create(mrf_batch_t* b, int64_t max_remove, int64_t max_add, int64_t max_pair_floats,
+                                  int64_t extra_slots);
+
+/* Stage the next round's edit: the arrays of mrf_batch_edit_factors and
+ * n_pair, the floats of pair_log (the sum over additions of L_g^2), copied on
+ * the batch's stream from host or device memory (ptr_kind).  Pinned host or
+ * device buffers are read when the copy runs: keep them unchanged until the
+ * round has started.  MRF_ERANGE above the capacities, MRF_ESTATE without a
+ * queue. */
+mrf_status mrf_batch_queue_load(mrf_batch_t* b, int64_t n_remove, const int32_t* remove_graph,
+                                const int64_t* remove_slot, int64_t n_add, const int32_t* add_graph,
+                                const int32_t* src, const int32_t* dst, int64_t n_pair, const float* pair_log,
+                                int32_t ptr_kind);
+
+/* One round: the staged edit (none if nothing was staged since the previous
+ * round), then n_sweeps sweeps of every graph (MRF_MODE_PLAIN or
+ * MRF_MODE_FUSED).  With options.use_graphs and a stream it is one CUDA graph
+ * launch (captured on the first round with this n_sweeps and mode); else the
+ * same kernels are launched one by one.  Asynchronous: read the edit's
+ * outcome with mrf_batch_queue_result.  MRF_ESTATE without a queue or
+ * factors. */
+mrf_status mrf_batch_round(mrf_batch_t* b, int32_t n_sweeps, int32_t mode);
+
+/* Waits for the batch's stream; *status = the MRF_Q_* bits of the last round's
+ * edit (0: applied) and out_slots[0..n) = the class slots of its first n
+ * added edges, -1 if the edit was rejected (out_slots may be null when n = 0).
+ * MRF_ERANGE if n exceeds the queue's max_add. */
+mrf_status mrf_batch_queue_result(mrf_batch_t* b, uint32_t* status, int64_t n, int64_t* out_slots);
 mrf_status mrf_batch_reset_marginals(mrf_batch_t* b, int32_t burn_in_sweeps);
 /* Counts [n_vars[g]][L_g] and labels [n_chains][n_vars[g]] of graph g (host). */
 mrf_status mrf_batch_get_counts(mrf_batch_t* b, int32_t graph, uint32_t* out);
 mrf_status mrf_batch_get_labels(mrf_batch_t* b, int32_t graph, uint8_t* out);
 mrf_status mrf_batch_graph(const mrf_batch_t* b, int32_t graph, mrf_batch_graph_info* out);
+/* Kernel timing of every class (as mrf_set_kernel_timing; batch sweeps and
+ * rounds then launch without graphs): read per class with mrf_kernel_times
+ * on mrf_batch_class(b, k). */
+mrf_status mrf_batch_set_kernel_timing(mrf_batch_t* b, int32_t on);
 /* Number of classes and the mrf_t of class k (for info, timing and debug views;
  * owned by the batch). */
 int32_t mrf_batch_n_classes(const mrf_batch_t* b);

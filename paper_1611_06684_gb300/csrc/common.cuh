@@ -310,14 +310,76 @@ struct DecompArgs {
     int64_t* sw_lw;            // [E][L] Swendsen-Wang bond log weights, fixed point, or null
     double* sw_fold;           // [E][2][L] Swendsen-Wang unary offsets (two labels) or null
     double* sw_ell;            // [E][L] Swendsen-Wang couplings l_x (float64) or null
+    // device edit queue (all null elsewhere): the edge count is min(n, *n_dev),
+    // edge i's table starts at pair + pair_off[i], and nothing is written while
+    // *status holds a bit of kQFatal
+    const int64_t* n_dev;
+    const int64_t* pair_off;
+    const uint32_t* status;
 };
 cudaError_t launch_check_finite(const float* p, int64_t n, unsigned long long* bad, cudaStream_t s);
 cudaError_t launch_count_offdiag(const float* pair, int64_t n_edges, int L, unsigned long long* nz, cudaStream_t s);
 cudaError_t launch_decompose(const DecompArgs& a, cudaStream_t s);
 cudaError_t launch_build_planes(const uint32_t* thr, int64_t n, const int64_t* slots, int64_t first_slot, int M,
-                                uint32_t* tpl, cudaStream_t s);
+                                uint32_t* tpl, cudaStream_t s, const int64_t* n_dev = nullptr,
+                                const uint32_t* status = nullptr);
 cudaError_t launch_fold_unary(const float* unary, const double* fold, const int64_t* inc_ptr, const int2* inc,
                               int N, int L, double* ut, float* utf, cudaStream_t s,
                               const double* unary_d = nullptr);
+
+// Device edit queue of a batch (queue.cu).  Status bits of a round: the
+// first ten cancel its edit, kQUnsorted reports a site whose incidence list
+// was too long to sort on the device (its sums then run in another order).
+enum : uint32_t {
+    kQCount = MRF_Q_COUNT, kQGraph = MRF_Q_GRAPH, kQVertex = MRF_Q_VERTEX, kQLoop = MRF_Q_LOOP,
+    kQSlot = MRF_Q_SLOT, kQDup = MRF_Q_DUP, kQFinite = MRF_Q_NONFINITE, kQDiag = MRF_Q_OFFDIAG,
+    kQPair = MRF_Q_PAIR, kQSlots = MRF_Q_SLOTS, kQFatal = 1023u, kQUnsorted = MRF_Q_UNSORTED
+};
+// One label class as the queue kernels see it.
+struct QClass {
+    int32_t* src;              // [E_res] endpoints of the class's slots (-1: free)
+    int32_t* dst;
+    uint32_t* mark;            // [E_res] removal marks, zero between rounds
+    uint8_t* touched;          // [N] sites whose folded unaries are stale
+    int64_t E_res;             // slots the class holds (used, free and reserved)
+    int32_t N, L, layout, pad;
+    int64_t* rm;               // [cap_rm] removed slots of the round
+    int64_t* add_slot;         // [cap_add] slot given to each added edge
+    int64_t* add_idx;          // [cap_add] position of the addition in the queue
+    int64_t* add_poff;         // [cap_add] offset of its table in the queue's table buffer
+    int32_t* add_s;            // [cap_add] endpoints (class site ids)
+    int32_t* add_t;
+    int64_t* cnt;              // [3] removals and additions of the round, live edges
+    int64_t* fsum;             // [ceil(E_res / 1024)] free slots per block of 1024 slots
+};
+struct QArgs {
+    const int32_t* rm_graph;   // [cap_rm]
+    const int64_t* rm_slot;    // [cap_rm] class slots
+    const int32_t* add_graph;  // [cap_add]
+    const int32_t* add_src;    // [cap_add] graph site ids
+    const int32_t* add_dst;
+    const float* pair;         // [cap_pair] the additions' tables, packed in queue order
+    int64_t* counts;           // [3] removals, additions, table floats (zeroed after the edit)
+    int64_t* out_slot;         // [cap_add] class slot of each added edge, -1 if the edit failed
+    uint32_t* status;
+    int64_t cap_rm, cap_add, cap_pair;
+    int32_t G, K;
+    const int32_t* g_cls;      // [G] class of each graph
+    const int32_t* g_off;      // [G] first class site of each graph
+    const int32_t* g_n;        // [G] sites of each graph
+    const int32_t* g_L;        // [G] labels of each graph
+    const QClass* cls;         // [K] in device memory
+    int64_t* blk;              // [nblk][2K + 1] per-block counts of the routing
+    int64_t nblk;              // ceil(max(cap_rm, cap_add) / 1024)
+};
+constexpr int kCsrSortLongSmem = 200 * 1024;
+cudaError_t launch_queue_route(const QArgs& q, cudaStream_t s);
+cudaError_t launch_queue_apply(const QArgs& q, const QClass& c, cudaStream_t s);
+cudaError_t launch_queue_finish(const QArgs& q, cudaStream_t s);
+cudaError_t launch_fold_touched(const float* unary, const double* fold, const int64_t* inc_ptr, const int2* inc,
+                                int N, int L, uint8_t* touched, double* ut, float* utf, cudaStream_t s);
+int csr_sort_long_cap();
+cudaError_t init_csr_sort_long();
+cudaError_t launch_csr_sort_long(const int64_t* ptr, int2* inc, int N, int min_deg, uint32_t* status, cudaStream_t s);
 
 }  // namespace mrfk

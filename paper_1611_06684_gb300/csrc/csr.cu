@@ -3,7 +3,7 @@
 // to the host build: within a site, incidences in increasing edge slot order
 // (a site is never both ends of one edge), code = slot * 2 + side.
 //   1. degree of every site over live edges (atomics)
-//   2. exclusive scan of the degrees into inc_ptr (three-kernel block scan)
+//   2. exclusive scan of the degrees into inc_ptr (block scans, one CTA over the block sums)
 //   3. scatter of every live edge's two incidences (atomic cursors)
 //   4. per-site insertion sort by code (restores the deterministic order)
 #include "common.cuh"
@@ -50,16 +50,41 @@ __global__ void k_scan_blocks(const int32_t* __restrict__ in, int64_t n, int64_t
     if (threadIdx.x == 1023) sums[blockIdx.x] = incl;
 }
 
-// Single-block sequential-chunk exclusive scan of the block totals (in place).
-__global__ void k_scan_sums(int64_t* sums, int64_t nb, int64_t* total) {
-    if (threadIdx.x != 0) return;
-    int64_t run = 0;
-    for (int64_t b = 0; b < nb; ++b) {
+// One CTA of 1024 threads: exclusive scan of the block totals in place, each
+// thread over a contiguous chunk; the grand total to *total.
+__global__ void __launch_bounds__(1024) k_scan_sums(int64_t* sums, int64_t nb, int64_t* total) {
+    __shared__ int64_t warp_tot[32];
+    const int64_t chunk = (nb + 1023) / 1024;
+    const int64_t b0 = threadIdx.x * chunk < nb ? threadIdx.x * chunk : nb;
+    const int64_t b1 = b0 + chunk < nb ? b0 + chunk : nb;
+    int64_t v = 0;
+    for (int64_t b = b0; b < b1; ++b) v += sums[b];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int64_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int64_t t = warp_tot[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t y = __shfl_up_sync(0xFFFFFFFFu, t, d);
+            if (lane >= d) t += y;
+        }
+        warp_tot[lane] = t;
+    }
+    __syncthreads();
+    int64_t run = x - v + (w > 0 ? warp_tot[w - 1] : 0);
+    for (int64_t b = b0; b < b1; ++b) {
         const int64_t t = sums[b];
         sums[b] = run;
         run += t;
     }
-    *total = run;
+    if (threadIdx.x == 1023) *total = warp_tot[31];
 }
 
 __global__ void k_scan_add(int64_t* out, int64_t n, const int64_t* __restrict__ sums, const int64_t* total) {
@@ -80,7 +105,9 @@ __global__ void k_csr_fill(const int32_t* __restrict__ src, const int32_t* __res
 }
 
 // Insertion sort of each site's incidences by code; sites with more than
-// max_deg incidences are left unsorted and counted (the host then rebuilds).
+// max_deg incidences are left unsorted and counted (a host-side edit then
+// rebuilds the lists on the host; a queue round sorts them with one CTA per
+// site, k_csr_sort_long).
 __global__ void k_csr_sort(const int64_t* __restrict__ ptr, int2* __restrict__ inc, int N, int max_deg,
                            unsigned long long* too_long) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -141,7 +168,7 @@ cudaError_t build_csr_device(const int32_t* src, const int32_t* dst, int64_t E, 
     if (E > 0) k_csr_degree<<<eb, 256, 0, s>>>(src, dst, E, deg);
     const int64_t nb = ((int64_t)N + 1 + 1023) / 1024;
     k_scan_blocks<<<(unsigned)nb, 1024, 0, s>>>(deg, N, ptr, sums);
-    k_scan_sums<<<1, 32, 0, s>>>(sums, nb, sums + nb);
+    k_scan_sums<<<1, 1024, 0, s>>>(sums, nb, sums + nb);
     k_scan_add<<<(unsigned)nb, 1024, 0, s>>>(ptr, N, sums, sums + nb);
     if (E > 0) k_csr_fill<<<eb, 256, 0, s>>>(src, dst, E, ptr, cursor, inc);
     k_csr_sort<<<(N + 127) / 128, 128, 0, s>>>(ptr, inc, N, max_deg, too_long);

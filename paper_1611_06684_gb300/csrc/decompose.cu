@@ -44,10 +44,10 @@ __global__ void k_count_offdiag(const float* pair, int64_t n_edges, int L, unsig
 
 __global__ void k_decompose(DecompArgs a) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
+    if (i >= a.n || (a.n_dev && i >= *a.n_dev) || (a.status && (*a.status & kQFatal))) return;
     const int L = a.L, M = a.M;
     const int64_t e = a.slots ? a.slots[i] : a.first_slot + i;
-    const float* w = a.pair + i * L * L;
+    const float* w = a.pair + (a.pair_off ? a.pair_off[i] : i * L * L);
     double fs[kMaxLabels], ft[kMaxLabels];
     double cst = 0.0;
     if (a.layout == MRF_LAYOUT_PIVOT) {
@@ -148,11 +148,12 @@ __global__ void k_decompose(DecompArgs a) {
 // words per edge:
 //   uint4 {AB_0|AB_4<<16, .., AB_3|AB_7<<16}, uint4 {B likewise}, uint4 {S | Act << 16, 0, 0, 0}.
 __global__ void k_build_planes(const uint32_t* thr, int64_t n, const int64_t* slots, int64_t first_slot, int M,
-                               uint32_t* tpl) {
+                               uint32_t* tpl, const int64_t* n_dev, const uint32_t* status) {
     const int G = (M + 31) / 32;
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (gid >= n * G) return;
     const int64_t i = gid / G;
+    if ((n_dev && i >= *n_dev) || (status && (*status & kQFatal))) return;
     const int g = (int)(gid % G);
     const int64_t e = slots ? slots[i] : first_slot + i;
     uint32_t A[8] = {0, 0, 0, 0, 0, 0, 0, 0}, B[8] = {0, 0, 0, 0, 0, 0, 0, 0}, S = 0, Act = 0;
@@ -221,9 +222,10 @@ cudaError_t launch_fold_unary(const float* unary, const double* fold, const int6
 }
 
 cudaError_t launch_build_planes(const uint32_t* thr, int64_t n, const int64_t* slots, int64_t first_slot, int M,
-                                uint32_t* tpl, cudaStream_t s) {
+                                uint32_t* tpl, cudaStream_t s, const int64_t* n_dev, const uint32_t* status) {
     const int64_t work = n * ((M + 31) / 32);
-    if (work > 0) k_build_planes<<<(unsigned)((work + 127) / 128), 128, 0, s>>>(thr, n, slots, first_slot, M, tpl);
+    if (work > 0)
+        k_build_planes<<<(unsigned)((work + 127) / 128), 128, 0, s>>>(thr, n, slots, first_slot, M, tpl, n_dev, status);
     return cudaGetLastError();
 }
 

@@ -51,6 +51,9 @@ struct mrf {
     // host mirrors
     std::vector<int32_t> h_src, h_dst;
     std::vector<int64_t> free_slots;   // sorted ascending
+    bool mirror_stale = false;         // device edits (a batch's edit queue) changed the endpoints since
+    bool dyn_degree = false;           // captured sweeps must not assume the current largest degree
+    const int64_t* d_live_ext = nullptr;   // device count of live edges kept by a batch's edit queue
     int64_t sweep_host = 0, count_from_host = 0;
     double log_const = NAN;
     std::string err;
@@ -176,7 +179,7 @@ SweepArgs make_args(const mrf_t* h) {
     a.E = h->E_slots;
     a.src = h->d_src; a.dst = h->d_dst; a.tau = h->d_tau; a.thr = h->d_thr; a.resid = h->d_resid;
     a.tpl = h->d_tpl; a.utf = h->d_utf;
-    a.inc_ptr = h->d_inc_ptr; a.inc = h->d_inc; a.ut = h->d_ut; a.max_deg = h->max_deg;
+    a.inc_ptr = h->d_inc_ptr; a.inc = h->d_inc; a.ut = h->d_ut; a.max_deg = h->dyn_degree ? 0x7FFFFFFF : h->max_deg;
     a.x = h->d_x; a.theta = h->d_theta; a.counts = h->d_counts; a.logp = h->d_logp;
     a.lpv = h->lpv_on ? h->d_lpv : nullptr;
     a.ctl = h->d_ctl; a.key = h->key;
@@ -276,6 +279,80 @@ mrf_status check_finite_device(mrf_t* h, const float* d, int64_t n, const char* 
     MRF_CUDA(h, cudaMemcpyAsync(&bad, h->d_flag, sizeof(bad), cudaMemcpyDeviceToHost, h->stream));
     MRF_CUDA(h, cudaStreamSynchronize(h->stream));
     if (bad) return fail(h, MRF_ENONFINITE, std::string(what) + ": " + std::to_string(bad) + " non-finite values");
+    return MRF_OK;
+}
+
+// Grow every per-slot buffer to hold new_slots slots (x1.25 slack); the first
+// E_slots slots keep their contents.
+mrf_status grow_slots(mrf_t* h, int64_t new_slots) {
+    if (new_slots <= h->E_cap) return MRF_OK;
+    const int L = h->L;
+    const int64_t cap = std::max<int64_t>(new_slots, h->E_cap + h->E_cap / 4 + 1024);
+    if ((uint64_t)cap * h->C >= (1ull << 32)) return fail(h, MRF_ERANGE, "edges x chains must be below 2^32");
+    auto grow = [&](auto*& p, size_t per) -> cudaError_t {
+        using T = std::remove_reference_t<decltype(*p)>;
+        T* q = nullptr;
+        cudaError_t e = cudaMalloc((void**)&q, (size_t)cap * per * sizeof(T));
+        if (e != cudaSuccess) return e;
+        if (h->E_slots) e = cudaMemcpyAsync(q, p, (size_t)h->E_slots * per * sizeof(T), cudaMemcpyDeviceToDevice, h->stream);
+        if (e != cudaSuccess) { cudaFree(q); return e; }
+        cudaStreamSynchronize(h->stream);
+        dfree(p);
+        p = q;
+        return cudaSuccess;
+    };
+    MRF_CUDA(h, grow(h->d_src, 1)); MRF_CUDA(h, grow(h->d_dst, 1));
+    MRF_CUDA(h, grow(h->d_tau, pad4(h->M))); MRF_CUDA(h, grow(h->d_thr, h->M)); MRF_CUDA(h, grow(h->d_tpl, plane_words(h->M)));
+    MRF_CUDA(h, grow(h->d_fold, 2 * L)); MRF_CUDA(h, grow(h->d_cst, 1));
+    if (h->d_swt) { MRF_CUDA(h, grow(h->d_swt, L)); MRF_CUDA(h, grow(h->d_swl, L)); MRF_CUDA(h, grow(h->d_swell, L)); }
+    if (h->d_swfold) MRF_CUDA(h, grow(h->d_swfold, 2 * L));
+    MRF_CUDA(h, dalloc(h->d_theta, (size_t)cap * h->C * h->W));
+    h->E_cap = cap;
+    return MRF_OK;
+}
+
+// Fresh free slots up to E_new: device endpoints -1, free in the host mirror.
+mrf_status reserve_slots(mrf_t* h, int64_t E_new) {
+    if (E_new <= h->E_slots) return MRF_OK;
+    mrf_status st = grow_slots(h, E_new);
+    if (st != MRF_OK) return st;
+    const size_t n = (size_t)(E_new - h->E_slots);
+    MRF_CUDA(h, cudaMemsetAsync(h->d_src + h->E_slots, 0xFF, n * sizeof(int32_t), h->stream));
+    MRF_CUDA(h, cudaMemsetAsync(h->d_dst + h->E_slots, 0xFF, n * sizeof(int32_t), h->stream));
+    h->h_src.resize((size_t)E_new, -1);
+    h->h_dst.resize((size_t)E_new, -1);
+    for (int64_t e = h->E_slots; e < E_new; ++e) h->free_slots.push_back(e);
+    h->E_slots = E_new;
+    h->sw_checked = false;
+    h->hg_ready = false;
+    drop_graphs(h);
+    return MRF_OK;
+}
+
+// After device edits: endpoints, free slots, live count and largest degree of
+// the host mirror read back from the device.
+mrf_status sync_mirror(mrf_t* h) {
+    if (!h->mirror_stale) return MRF_OK;
+    const size_t E = (size_t)h->E_slots;
+    h->h_src.resize(E);
+    h->h_dst.resize(E);
+    if (E) {
+        MRF_CUDA(h, cudaMemcpyAsync(h->h_src.data(), h->d_src, E * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+        MRF_CUDA(h, cudaMemcpyAsync(h->h_dst.data(), h->d_dst, E * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    }
+    MRF_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->free_slots.clear();
+    std::vector<int32_t> deg((size_t)h->N, 0);
+    int64_t live = 0;
+    for (size_t e = 0; e < E; ++e) {
+        if (h->h_src[e] < 0) { h->free_slots.push_back((int64_t)e); continue; }
+        ++live;
+        ++deg[h->h_src[e]];
+        ++deg[h->h_dst[e]];
+    }
+    h->E_live = live;
+    h->max_deg = deg.empty() ? 0 : *std::max_element(deg.begin(), deg.end());
+    h->mirror_stale = false;
     return MRF_OK;
 }
 
@@ -441,6 +518,7 @@ mrf_status mrf_set_factors(mrf_t* h, const float* unary_log, int64_t n_edges, co
     h->M = n_entries(L, h->layout);
     h->W = (h->M + 31) / 32;
     h->E_live = h->E_slots = h->E_cap = n_edges;
+    h->mirror_stale = false;
     h->free_slots.clear();
     const bool want_resid = h->opt.grid_nx > 0 || h->opt.exact_edges;
     if (h->opt.grid_nx > 0 && !lattice_ok(h)) {
@@ -499,6 +577,8 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
     if (h->opt.grid_nx > 0) return fail(h, MRF_ESTATE, "edits are not available on a lattice handle");
     if (h->learned) return fail(h, MRF_ESTATE, "edits are not available once the learned proposal is set up");
     if (h->d_resid) return fail(h, MRF_ESTATE, "edits are not available with exact edge tables");
+    mrf_status sst = sync_mirror(h);
+    if (sst != MRF_OK) return sst;
     const int L = h->L, N = h->N;
     std::vector<int64_t> rem;
     std::vector<int32_t> as, at;
@@ -546,28 +626,8 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
     h->free_slots.assign(pool.begin() + used, pool.end());
     const int64_t new_slots = next;
     if (new_slots > h->E_cap) {
-        // grow every per-slot buffer (x1.25 slack)
-        const int64_t cap = std::max<int64_t>(new_slots, h->E_cap + h->E_cap / 4 + 1024);
-        auto grow = [&](auto*& p, size_t per) -> cudaError_t {
-            using T = std::remove_reference_t<decltype(*p)>;
-            T* q = nullptr;
-            cudaError_t e = cudaMalloc((void**)&q, (size_t)cap * per * sizeof(T));
-            if (e != cudaSuccess) return e;
-            if (h->E_slots) e = cudaMemcpyAsync(q, p, (size_t)h->E_slots * per * sizeof(T), cudaMemcpyDeviceToDevice, h->stream);
-            if (e != cudaSuccess) { cudaFree(q); return e; }
-            cudaStreamSynchronize(h->stream);
-            dfree(p);
-            p = q;
-            return cudaSuccess;
-        };
-        MRF_CUDA(h, grow(h->d_src, 1)); MRF_CUDA(h, grow(h->d_dst, 1));
-        if ((uint64_t)cap * h->C >= (1ull << 32)) return fail(h, MRF_ERANGE, "edges x chains must be below 2^32");
-        MRF_CUDA(h, grow(h->d_tau, pad4(h->M))); MRF_CUDA(h, grow(h->d_thr, h->M)); MRF_CUDA(h, grow(h->d_tpl, plane_words(h->M)));
-        MRF_CUDA(h, grow(h->d_fold, 2 * L)); MRF_CUDA(h, grow(h->d_cst, 1));
-        if (h->d_swt) { MRF_CUDA(h, grow(h->d_swt, L)); MRF_CUDA(h, grow(h->d_swl, L)); MRF_CUDA(h, grow(h->d_swell, L)); }
-        if (h->d_swfold) MRF_CUDA(h, grow(h->d_swfold, 2 * L));
-        MRF_CUDA(h, dalloc(h->d_theta, (size_t)cap * h->C * h->W));
-        h->E_cap = cap;
+        mrf_status gst = grow_slots(h, new_slots);
+        if (gst != MRF_OK) return gst;
     }
     h->h_src.resize(new_slots, -1); h->h_dst.resize(new_slots, -1);
     for (int64_t i = 0; i < n_add; ++i) { h->h_src[slots[i]] = as[i]; h->h_dst[slots[i]] = at[i]; }
@@ -706,6 +766,10 @@ static SwArgs make_sw_args(const mrf_t* h) {
 // (checked once per factor change); the union-find buffers are allocated on
 // first use.
 static mrf_status sw_prepare(mrf_t* h) {
+    {
+        const mrf_status sst = sync_mirror(h);
+        if (sst != MRF_OK) return sst;
+    }
     // (a model without live edges has no tables to check: every cluster is one site)
     if (!h->d_swt && h->E_live > 0)
         return fail(h, MRF_EINVAL, "Swendsen-Wang sweeps need two labels or Potts-type tables (diagonal layout)");
@@ -759,6 +823,10 @@ static mrf_status sw_check_error(mrf_t* h) {
 // the split at hg_rho (once per factor or rho change), the remainder's folded
 // unaries and the range check that now includes the bits' fields.
 static mrf_status hg_prepare(mrf_t* h) {
+    {
+        const mrf_status sst = sync_mirror(h);
+        if (sst != MRF_OK) return sst;
+    }
     mrf_status st = sw_prepare(h);
     if (st != MRF_OK) return st;
     if (!h->d_pot) { drop_graphs(h); MRF_CUDA(h, dalloc(h->d_pot, (size_t)h->N * h->L * h->C)); }
@@ -1157,6 +1225,8 @@ extern "C" {
 mrf_status mrf_save(mrf_t* h, const char* path) {
     if (!h || !path) return MRF_EINVAL;
     if (!h->has_factors) return fail(h, MRF_ESTATE, "mrf_set_factors first");
+    mrf_status sst = sync_mirror(h);
+    if (sst != MRF_OK) return sst;
     CkptHeader hd{};
     hd.N = h->N; hd.L = h->L; hd.C = h->C; hd.layout = h->layout; hd.M = h->M; hd.W = h->W;
     hd.E_live = h->E_live; hd.E_slots = h->E_slots; hd.n_free = (int64_t)h->free_slots.size();
@@ -1207,6 +1277,7 @@ mrf_status mrf_load(mrf_t** out, const char* path, void* cuda_stream) {
     auto bail = [&](mrf_status code) { fclose(f); mrf_destroy(h); return code; };
     h->layout = hd.layout; h->M = hd.M; h->W = hd.W;
     h->E_live = hd.E_live; h->E_slots = h->E_cap = hd.E_slots;
+    h->mirror_stale = false;
     const size_t NL = (size_t)h->N * h->L, E = (size_t)hd.E_slots, L = (size_t)h->L;
     if ((uint64_t)E * h->C >= (1ull << 32)) return bail(MRF_ERANGE);
     std::vector<uint8_t> buf;
@@ -1359,6 +1430,15 @@ mrf_status mrf_get_info(const mrf_t* h, mrf_info* out) {
     if (!h || !out) return MRF_EINVAL;
     out->n_vars = h->N; out->n_labels = h->L; out->n_chains = h->C; out->layout = h->layout; out->n_entries = h->M;
     out->n_edges = h->E_live; out->n_edge_slots = h->E_slots; out->sweep_index = h->sweep_host;
+    if (h->mirror_stale && h->d_live_ext) {        // live edges after device edits, from the device counter
+        int64_t live = 0;
+        if (cudaMemcpyAsync(&live, h->d_live_ext, sizeof(live), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return MRF_ECUDA;
+        }
+        out->n_edges = live;
+    }
     out->n_samples = std::max<int64_t>(0, h->sweep_host - h->count_from_host) * h->C;
     out->log_const = h->log_const;
     out->schedule = h->schedule;
@@ -1443,6 +1523,23 @@ struct mrf_batch {
     std::vector<std::vector<int64_t>> ed_rm, ed_idx, ed_ids;
     std::vector<std::vector<int32_t>> ed_s, ed_t;
     std::vector<std::vector<float>> ed_p;
+    // device edit queue (mrf_batch_queue_create): buffers, per-class lists and
+    // the round graph {edit, n sweeps}
+    bool q_on = false;
+    int64_t q_cap_rm = 0, q_cap_add = 0, q_cap_pair = 0, q_extra = 0;
+    int32_t* dq_rm_graph = nullptr; int64_t* dq_rm_slot = nullptr;
+    int32_t* dq_add_graph = nullptr; int32_t* dq_add_src = nullptr; int32_t* dq_add_dst = nullptr;
+    float* dq_pair = nullptr;
+    int64_t* dq_counts = nullptr; int64_t* dq_out = nullptr; uint32_t* dq_status = nullptr;
+    int64_t* dq_blk = nullptr; int64_t q_nblk = 0;
+    unsigned long long* dq_toolong = nullptr;
+    int32_t* dq_g = nullptr;               // [4][G]: class, first class site, sites, labels of each graph
+    QClass* dq_cls = nullptr;              // [K]
+    std::vector<QClass> qc;                // host copies
+    std::vector<int64_t> qc_mark_cap, qc_fsum_cap;
+    bool q_ready = false;                  // per-class state matches the class handles
+    cudaGraphExec_t round_graph = nullptr;
+    int32_t round_n = -1, round_mode = -1;
 };
 
 namespace {
@@ -1455,6 +1552,22 @@ mrf_status bfail(mrf_batch_t* b, mrf_status st, const std::string& msg) {
 void drop_batch_graphs(mrf_batch_t* b) {
     for (auto& g : b->graph)
         if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    if (b->round_graph) { cudaGraphExecDestroy(b->round_graph); b->round_graph = nullptr; }
+    b->q_ready = false;
+}
+
+void free_queue(mrf_batch_t* b) {
+    dfree(b->dq_rm_graph); dfree(b->dq_rm_slot); dfree(b->dq_add_graph); dfree(b->dq_add_src); dfree(b->dq_add_dst);
+    dfree(b->dq_pair); dfree(b->dq_counts); dfree(b->dq_out); dfree(b->dq_status); dfree(b->dq_blk);
+    dfree(b->dq_toolong); dfree(b->dq_g); dfree(b->dq_cls);
+    for (QClass& c : b->qc) {
+        dfree(c.mark); dfree(c.touched); dfree(c.rm); dfree(c.add_slot); dfree(c.add_idx); dfree(c.add_poff);
+        dfree(c.add_s); dfree(c.add_t); dfree(c.cnt); dfree(c.fsum);
+    }
+    for (mrf_t* hk : b->h) hk->d_live_ext = nullptr;
+    b->qc.clear(); b->qc_mark_cap.clear(); b->qc_fsum_cap.clear();
+    b->q_on = false;
+    b->q_ready = false;
 }
 
 mrf_status class_status(mrf_batch_t* b, int k, mrf_status st) {
@@ -1513,6 +1626,7 @@ mrf_status mrf_batch_create(mrf_batch_t** out, int32_t n_graphs, const int32_t* 
 void mrf_batch_destroy(mrf_batch_t* b) {
     if (!b) return;
     drop_batch_graphs(b);
+    free_queue(b);
     for (auto* hk : b->h) mrf_destroy(hk);
     delete b;
 }
@@ -1667,6 +1781,277 @@ mrf_status mrf_batch_sweep(mrf_batch_t* b, int32_t n_sweeps, int32_t mode) {
         }
     }
     for (int k = 0; k < K; ++k) b->h[k]->sweep_host += n_sweeps;
+    return MRF_OK;
+}
+
+namespace {
+
+// Per-class queue state matching the class handles: free slots reserved,
+// lists, removal marks, live counts and incidence capacity.  Runs before a
+// round is captured (a new queue, or after set_factors or host edits).
+mrf_status queue_prepare(mrf_batch_t* b) {
+    if (b->q_ready) return MRF_OK;
+    const int K = (int)b->h.size();
+    for (auto& g : b->graph)                     // sweep graphs captured before the reserve
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    if (b->round_graph) { cudaGraphExecDestroy(b->round_graph); b->round_graph = nullptr; }
+    if ((int)b->qc.size() != K) {
+        b->qc.assign(K, QClass{});
+        b->qc_mark_cap.assign(K, 0);
+        b->qc_fsum_cap.assign(K, 0);
+    }
+    for (int k = 0; k < K; ++k) {
+        mrf_t* h = b->h[k];
+        if (!h->has_factors) return bfail(b, MRF_ESTATE, "mrf_batch_set_factors first");
+        mrf_status st = sync_mirror(h);
+        if (st == MRF_OK) st = reserve_slots(h, std::max(h->E_slots, h->E_live + b->q_extra));
+        if (st != MRF_OK) return class_status(b, k, st);
+        h->dyn_degree = true;
+        drop_graphs(h);
+        QClass& c = b->qc[k];
+        auto ok = [&](cudaError_t e) {
+            if (e != cudaSuccess) { cudaGetLastError(); b->err = std::string("queue buffers: ") + cudaGetErrorString(e); }
+            return e == cudaSuccess;
+        };
+        if (!c.cnt) {
+            if (!ok(dalloc(c.rm, (size_t)b->q_cap_rm)) || !ok(dalloc(c.add_slot, (size_t)b->q_cap_add)) ||
+                !ok(dalloc(c.add_idx, (size_t)b->q_cap_add)) || !ok(dalloc(c.add_poff, (size_t)b->q_cap_add)) ||
+                !ok(dalloc(c.add_s, (size_t)b->q_cap_add)) || !ok(dalloc(c.add_t, (size_t)b->q_cap_add)) ||
+                !ok(dalloc(c.touched, (size_t)h->N)) || !ok(dalloc(c.cnt, 3)) ||
+                !ok(cudaMemsetAsync(c.touched, 0, (size_t)h->N, b->stream)) ||
+                !ok(cudaMemsetAsync(c.add_slot, 0xFF, (size_t)std::max<int64_t>(b->q_cap_add, 1) * sizeof(int64_t), b->stream)) ||
+                !ok(cudaMemsetAsync(c.cnt, 0, 3 * sizeof(int64_t), b->stream)))
+                return MRF_ENOMEM;
+        }
+        if (b->qc_mark_cap[k] < h->E_slots) {
+            if (!ok(dalloc(c.mark, (size_t)h->E_slots)) ||
+                !ok(cudaMemsetAsync(c.mark, 0, (size_t)h->E_slots * sizeof(uint32_t), b->stream)))
+                return MRF_ENOMEM;
+            b->qc_mark_cap[k] = h->E_slots;
+        }
+        const int64_t nb = (h->E_slots + 1023) / 1024;
+        if (b->qc_fsum_cap[k] < nb + 1) {
+            if (!ok(dalloc(c.fsum, (size_t)nb + 1))) return MRF_ENOMEM;
+            b->qc_fsum_cap[k] = nb + 1;
+        }
+        if (h->inc_cap < 2 * h->E_slots) {       // every slot may be live; the current lists are kept
+            int2* inc = nullptr;
+            if (!ok(cudaMalloc((void**)&inc, (size_t)(2 * h->E_slots) * sizeof(int2)))) return MRF_ENOMEM;
+            if (!ok(cudaMemcpyAsync(inc, h->d_inc, (size_t)h->inc_cap * sizeof(int2), cudaMemcpyDeviceToDevice, b->stream)) ||
+                !ok(cudaStreamSynchronize(b->stream))) {
+                cudaFree(inc);
+                return MRF_ECUDA;
+            }
+            dfree(h->d_inc);
+            h->d_inc = inc;
+            h->inc_cap = 2 * h->E_slots;
+        }
+        if (!h->d_csr_work) {
+            if (!ok(dalloc(h->d_csr_work, 2 * (size_t)h->N + 2)) ||
+                !ok(dalloc(h->d_csr_sums, (size_t)((h->N + 1 + 1023) / 1024 + 2))))
+                return MRF_ENOMEM;
+        }
+        c.src = h->d_src; c.dst = h->d_dst; c.E_res = h->E_slots;
+        c.N = h->N; c.L = h->L; c.layout = h->layout;
+        const int64_t live = h->E_live;
+        if (!ok(cudaMemcpyAsync(c.cnt + 2, &live, sizeof(live), cudaMemcpyHostToDevice, b->stream)) ||
+            !ok(cudaStreamSynchronize(b->stream)))
+            return MRF_ECUDA;
+        h->d_live_ext = c.cnt + 2;
+    }
+    if (cudaMemcpyAsync(b->dq_cls, b->qc.data(), (size_t)K * sizeof(QClass), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, MRF_ECUDA, "queue class table upload");
+    }
+    b->q_ready = true;
+    return MRF_OK;
+}
+
+QArgs make_qargs(const mrf_batch_t* b) {
+    QArgs q{};
+    q.rm_graph = b->dq_rm_graph; q.rm_slot = b->dq_rm_slot;
+    q.add_graph = b->dq_add_graph; q.add_src = b->dq_add_src; q.add_dst = b->dq_add_dst; q.pair = b->dq_pair;
+    q.counts = b->dq_counts; q.out_slot = b->dq_out; q.status = b->dq_status;
+    q.cap_rm = b->q_cap_rm; q.cap_add = b->q_cap_add; q.cap_pair = b->q_cap_pair;
+    q.G = b->G; q.K = (int32_t)b->h.size();
+    q.g_cls = b->dq_g; q.g_off = b->dq_g + b->G; q.g_n = b->dq_g + 2 * (size_t)b->G; q.g_L = b->dq_g + 3 * (size_t)b->G;
+    q.cls = b->dq_cls; q.blk = b->dq_blk; q.nblk = b->q_nblk;
+    return q;
+}
+
+// The kernels of one round on the batch's stream (captured or launched).
+mrf_status enqueue_round(mrf_batch_t* b, int n_sweeps, int mode) {
+    const QArgs q = make_qargs(b);
+    cudaStream_t s = b->stream;
+    cudaError_t e = cudaMemsetAsync(b->dq_status, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = launch_queue_route(q, s);
+    for (int k = 0; k < (int)b->h.size() && e == cudaSuccess; ++k) {
+        mrf_t* h = b->h[k];
+        const QClass& c = b->qc[k];
+        e = launch_queue_apply(q, c, s);
+        DecompArgs d{};
+        d.L = h->L; d.M = h->M; d.layout = h->layout; d.n = b->q_cap_add; d.slots = c.add_slot;
+        d.pair = b->dq_pair; d.pair_off = c.add_poff; d.n_dev = c.cnt + 1; d.status = b->dq_status;
+        d.tau = h->d_tau; d.thr = h->d_thr; d.fold = h->d_fold; d.cst = h->d_cst; d.resid = nullptr;
+        d.sw_thr = h->d_swt; d.sw_lw = h->d_swl; d.sw_fold = h->d_swfold; d.sw_ell = h->d_swell;
+        if (e == cudaSuccess) e = launch_decompose(d, s);
+        if (e == cudaSuccess)
+            e = launch_build_planes(h->d_thr, b->q_cap_add, c.add_slot, 0, h->M, h->d_tpl, s, c.cnt + 1, b->dq_status);
+        if (e == cudaSuccess)
+            e = build_csr_device(h->d_src, h->d_dst, h->E_slots, h->N, h->d_inc_ptr, h->d_inc, h->d_csr_work,
+                                 h->d_csr_sums, b->dq_toolong, 512, s);
+        if (e == cudaSuccess) e = launch_csr_sort_long(h->d_inc_ptr, h->d_inc, h->N, 512, b->dq_status, s);
+        if (e == cudaSuccess && h->d_swut)
+            e = launch_fold_unary(h->d_unary, h->d_swfold, h->d_inc_ptr, h->d_inc, h->N, h->L, h->d_swut, nullptr, s);
+        if (e == cudaSuccess)
+            e = launch_fold_touched(h->d_unary, h->d_fold, h->d_inc_ptr, h->d_inc, h->N, h->L, c.touched, h->d_ut,
+                                    h->d_utf, s);
+    }
+    if (e == cudaSuccess) e = launch_queue_finish(q, s);
+    if (e != cudaSuccess) { cudaGetLastError(); return bfail(b, MRF_ECUDA, std::string("round launch: ") + cudaGetErrorString(e)); }
+    for (int i = 0; i < n_sweeps; ++i)
+        for (int k = 0; k < (int)b->h.size(); ++k) {
+            mrf_status st = enqueue_sweep(b->h[k], mode);
+            if (st != MRF_OK) return class_status(b, k, st);
+        }
+    return MRF_OK;
+}
+
+}  // namespace
+
+mrf_status mrf_batch_set_kernel_timing(mrf_batch_t* b, int32_t on) {
+    if (!b) return MRF_EINVAL;
+    b->opt.kernel_timing = on ? 1 : 0;
+    for (mrf_t* h : b->h) h->opt.kernel_timing = on ? 1 : 0;
+    return MRF_OK;
+}
+
+mrf_status mrf_batch_queue_create(mrf_batch_t* b, int64_t max_remove, int64_t max_add, int64_t max_pair_floats,
+                                  int64_t extra_slots) {
+    if (!b) return MRF_EINVAL;
+    if (max_remove < 0 || max_add < 0 || max_pair_floats < 0 || extra_slots < 0)
+        return bfail(b, MRF_EINVAL, "negative queue size");
+    drop_batch_graphs(b);
+    free_queue(b);
+    const int G = b->G, K = (int)b->h.size();
+    b->q_cap_rm = max_remove; b->q_cap_add = max_add; b->q_cap_pair = max_pair_floats; b->q_extra = extra_slots;
+    b->q_nblk = (std::max<int64_t>({max_remove, max_add, 1}) + 1023) / 1024;
+    std::vector<int32_t> gt(4 * (size_t)G);
+    for (int g = 0; g < G; ++g) {
+        gt[g] = b->cls[g]; gt[G + g] = b->site_off[g]; gt[2 * G + g] = b->n_vars[g]; gt[3 * G + g] = b->n_labels[g];
+    }
+    auto ok = [&](cudaError_t e) {
+        if (e != cudaSuccess) { cudaGetLastError(); b->err = std::string("queue buffers: ") + cudaGetErrorString(e); }
+        return e == cudaSuccess;
+    };
+    if (!ok(dalloc(b->dq_rm_graph, (size_t)max_remove)) || !ok(dalloc(b->dq_rm_slot, (size_t)max_remove)) ||
+        !ok(dalloc(b->dq_add_graph, (size_t)max_add)) || !ok(dalloc(b->dq_add_src, (size_t)max_add)) ||
+        !ok(dalloc(b->dq_add_dst, (size_t)max_add)) || !ok(dalloc(b->dq_pair, (size_t)max_pair_floats)) ||
+        !ok(dalloc(b->dq_counts, 3)) || !ok(dalloc(b->dq_out, (size_t)max_add)) || !ok(dalloc(b->dq_status, 1)) ||
+        !ok(dalloc(b->dq_blk, (size_t)(b->q_nblk * (2 * K + 1)))) || !ok(dalloc(b->dq_toolong, 1)) ||
+        !ok(dalloc(b->dq_g, gt.size())) || !ok(dalloc(b->dq_cls, (size_t)K)) ||
+        !ok(cudaMemsetAsync(b->dq_counts, 0, 3 * sizeof(int64_t), b->stream)) ||
+        !ok(cudaMemsetAsync(b->dq_status, 0, sizeof(uint32_t), b->stream)) ||
+        !ok(cudaMemcpyAsync(b->dq_g, gt.data(), gt.size() * sizeof(int32_t), cudaMemcpyHostToDevice, b->stream)) ||
+        !ok(cudaStreamSynchronize(b->stream)) || !ok(init_csr_sort_long())) {
+        free_queue(b);
+        return MRF_ENOMEM;
+    }
+    b->q_on = true;
+    return MRF_OK;
+}
+
+mrf_status mrf_batch_queue_load(mrf_batch_t* b, int64_t n_remove, const int32_t* remove_graph,
+                                const int64_t* remove_slot, int64_t n_add, const int32_t* add_graph,
+                                const int32_t* src, const int32_t* dst, int64_t n_pair, const float* pair_log,
+                                int32_t ptr_kind) {
+    if (!b) return MRF_EINVAL;
+    if (!b->q_on) return bfail(b, MRF_ESTATE, "mrf_batch_queue_create first");
+    if (ptr_kind != MRF_PTR_HOST && ptr_kind != MRF_PTR_DEVICE) return bfail(b, MRF_EINVAL, "bad ptr_kind");
+    if (n_remove < 0 || n_add < 0 || n_pair < 0) return bfail(b, MRF_EINVAL, "negative count");
+    if (n_remove > b->q_cap_rm || n_add > b->q_cap_add || n_pair > b->q_cap_pair)
+        return bfail(b, MRF_ERANGE, "edit larger than the queue's capacities");
+    if ((n_remove && (!remove_graph || !remove_slot)) || (n_add && (!add_graph || !src || !dst)) || (n_pair && !pair_log))
+        return bfail(b, MRF_EINVAL, "null edit arrays");
+    const cudaMemcpyKind kind = ptr_kind == MRF_PTR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    cudaStream_t s = b->stream;
+    const int64_t counts[3] = {n_remove, n_add, n_pair};
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void* d, const void* p, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(d, p, bytes, kind, s);
+    };
+    cp(b->dq_rm_graph, remove_graph, (size_t)n_remove * sizeof(int32_t));
+    cp(b->dq_rm_slot, remove_slot, (size_t)n_remove * sizeof(int64_t));
+    cp(b->dq_add_graph, add_graph, (size_t)n_add * sizeof(int32_t));
+    cp(b->dq_add_src, src, (size_t)n_add * sizeof(int32_t));
+    cp(b->dq_add_dst, dst, (size_t)n_add * sizeof(int32_t));
+    cp(b->dq_pair, pair_log, (size_t)n_pair * sizeof(float));
+    // counts[] is pageable: the copy stages it before returning
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->dq_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { cudaGetLastError(); return bfail(b, MRF_ECUDA, std::string("queue load: ") + cudaGetErrorString(e)); }
+    return MRF_OK;
+}
+
+mrf_status mrf_batch_round(mrf_batch_t* b, int32_t n_sweeps, int32_t mode) {
+    if (!b) return MRF_EINVAL;
+    if (!b->q_on) return bfail(b, MRF_ESTATE, "mrf_batch_queue_create first");
+    if (n_sweeps < 0 || (mode != MRF_MODE_PLAIN && mode != MRF_MODE_FUSED)) return bfail(b, MRF_EINVAL, "bad sweep count or mode");
+    mrf_status st = queue_prepare(b);
+    if (st != MRF_OK) return st;
+    const int K = (int)b->h.size();
+    for (int k = 0; k < K; ++k)
+        if (mode == MRF_MODE_PLAIN && b->h[k]->schedule == 0 && n_sweeps > 0) {
+            st = tune_schedule(b->h[k]);
+            if (st != MRF_OK) return class_status(b, k, st);
+        }
+    const bool graphs = b->opt.use_graphs && b->stream != nullptr && !b->opt.kernel_timing;
+    if (graphs && b->round_graph && (b->round_n != n_sweeps || b->round_mode != mode)) {
+        cudaGraphExecDestroy(b->round_graph);
+        b->round_graph = nullptr;
+    }
+    if (graphs && !b->round_graph) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(b, MRF_ECUDA, "stream capture failed");
+        }
+        st = enqueue_round(b, n_sweeps, mode);
+        cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+        if (st != MRF_OK || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return st != MRF_OK ? st : bfail(b, MRF_ECUDA, "round graph capture failed");
+        }
+        ce = cudaGraphInstantiate(&b->round_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) { cudaGetLastError(); b->round_graph = nullptr; return bfail(b, MRF_ECUDA, "round graph instantiate failed"); }
+        b->round_n = n_sweeps;
+        b->round_mode = mode;
+    }
+    if (graphs) {
+        if (cudaGraphLaunch(b->round_graph, b->stream) != cudaSuccess) { cudaGetLastError(); return bfail(b, MRF_ECUDA, "graph launch"); }
+    } else {
+        st = enqueue_round(b, n_sweeps, mode);
+        if (st != MRF_OK) return st;
+    }
+    for (mrf_t* h : b->h) {
+        h->sweep_host += n_sweeps;
+        h->mirror_stale = true;
+        h->sw_checked = false;
+        h->hg_ready = false;
+    }
+    return MRF_OK;
+}
+
+mrf_status mrf_batch_queue_result(mrf_batch_t* b, uint32_t* status, int64_t n, int64_t* out_slots) {
+    if (!b || !status || n < 0 || (n > 0 && !out_slots)) return MRF_EINVAL;
+    if (!b->q_on) return bfail(b, MRF_ESTATE, "mrf_batch_queue_create first");
+    if (n > b->q_cap_add) return bfail(b, MRF_ERANGE, "more slots than the queue's max_add");
+    cudaError_t e = cudaMemcpyAsync(status, b->dq_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess && n) e = cudaMemcpyAsync(out_slots, b->dq_out, (size_t)n * sizeof(int64_t), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) { cudaGetLastError(); return bfail(b, MRF_ECUDA, std::string("queue result: ") + cudaGetErrorString(e)); }
     return MRF_OK;
 }
 

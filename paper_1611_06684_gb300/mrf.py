@@ -21,6 +21,9 @@ LIB_PATH = os.path.join(HERE, "libmrf.so")
 MRF_OK, MRF_EINVAL, MRF_ENONFINITE, MRF_ENOMEM, MRF_ECUDA, MRF_ERANGE, MRF_ETIMEOUT, MRF_ESTATE = range(8)
 MRF_PTR_HOST, MRF_PTR_DEVICE = 0, 1
 MODE_PLAIN, MODE_FUSED, MODE_SPLASH, MODE_LEARNED, MODE_SW, MODE_HIGDON = 0, 1, 2, 3, 4, 5
+# status bits of a queue round's edit (mrf.h MRF_Q_*)
+Q_COUNT, Q_GRAPH, Q_VERTEX, Q_LOOP, Q_SLOT, Q_DUP, Q_NONFINITE, Q_OFFDIAG, Q_PAIR, Q_SLOTS, Q_UNSORTED = \
+    1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024
 LAYOUT_PIVOT, LAYOUT_DIAG = 0, 1
 (K_DUAL, K_PRIMAL, K_FUSED, K_POTENTIAL, K_FFBS, K_ACCUMULATE, K_FEATURES, K_MLP, K_MH, K_SMALL,
  K_SW_BOND, K_SW_FLATTEN, K_SW_DRAW, K_SW_SMALL, K_COUNT) = range(15)
@@ -92,6 +95,11 @@ _SIGS = {
     "mrf_batch_set_factors": (ct.c_int, [_P, _P, _P, _P, _P, _P]),
     "mrf_batch_edit_factors": (ct.c_int, [_P, ct.c_int64, _P, _P, ct.c_int64, _P, _P, _P, _P, _P]),
     "mrf_batch_sweep": (ct.c_int, [_P, ct.c_int32, ct.c_int32]),
+    "mrf_batch_queue_create": (ct.c_int, [_P, ct.c_int64, ct.c_int64, ct.c_int64, ct.c_int64]),
+    "mrf_batch_queue_load": (ct.c_int, [_P, ct.c_int64, _P, _P, ct.c_int64, _P, _P, _P, ct.c_int64, _P, ct.c_int32]),
+    "mrf_batch_round": (ct.c_int, [_P, ct.c_int32, ct.c_int32]),
+    "mrf_batch_set_kernel_timing": (ct.c_int, [_P, ct.c_int32]),
+    "mrf_batch_queue_result": (ct.c_int, [_P, ct.POINTER(ct.c_uint32), ct.c_int64, _P]),
     "mrf_batch_reset_marginals": (ct.c_int, [_P, ct.c_int32]),
     "mrf_batch_get_counts": (ct.c_int, [_P, ct.c_int32, _P]),
     "mrf_batch_get_labels": (ct.c_int, [_P, ct.c_int32, _P]),
@@ -481,6 +489,49 @@ class MRFBatch:
 
     def sweep(self, n: int = 1, mode: int = MODE_PLAIN):
         self._check(self.lib.mrf_batch_sweep(self.b, int(n), int(mode)))
+
+    def set_kernel_timing(self, on: bool):
+        """CUDA events around every class kernel (read with class_handle(k).kernel_times())."""
+        self._check(self.lib.mrf_batch_set_kernel_timing(self.b, int(bool(on))))
+
+    # -- device edit queue
+    def queue_create(self, max_remove: int, max_add: int, max_pair_floats: int, extra_slots: int):
+        self._check(self.lib.mrf_batch_queue_create(self.b, int(max_remove), int(max_add), int(max_pair_floats),
+                                                    int(extra_slots)))
+
+    def queue_load(self, rm_graph, rm_slot, add_graph, src, dst, pair_flat):
+        """Stage the next round's edit: numpy arrays (host) or CUDA tensors
+        (device), all of one kind, with the dtypes of mrf_batch_queue_load."""
+        dts = (np.int32, np.int64, np.int32, np.int32, np.int32, np.float32)
+        arrs = [rm_graph, rm_slot, add_graph, src, dst, pair_flat]
+        kinds, ptrs, keep = set(), [], []
+        for a, dt in zip(arrs, dts):
+            if isinstance(a, np.ndarray) or isinstance(a, (list, tuple)):
+                a = np.ascontiguousarray(a, dt)
+            else:
+                import torch
+                if a.dtype != getattr(torch, np.dtype(dt).name):
+                    raise TypeError(f"queue_load: expected {np.dtype(dt).name}, got {a.dtype}")
+            p, kind, k = _ptr(a)
+            kinds.add(kind); ptrs.append(p); keep.append(k)
+        if len(kinds) != 1:
+            raise TypeError("queue_load: all arrays host or all device")
+        n_rm, n_add, n_pair = int(keep[1].shape[0]), int(keep[2].shape[0]), int(keep[5].shape[0])
+        if int(keep[0].shape[0]) != n_rm or int(keep[3].shape[0]) != n_add or int(keep[4].shape[0]) != n_add:
+            raise ValueError("queue_load: removal or addition arrays of unequal length")
+        self._check(self.lib.mrf_batch_queue_load(self.b, n_rm, ptrs[0], ptrs[1], n_add, ptrs[2], ptrs[3], ptrs[4],
+                                                  n_pair, ptrs[5], kinds.pop()))
+        self._queue_keep = keep                  # host arrays stay alive until the next load
+
+    def round(self, n: int = 10, mode: int = MODE_PLAIN):
+        self._check(self.lib.mrf_batch_round(self.b, int(n), int(mode)))
+
+    def queue_result(self, n_add: int):
+        """(status bits, class slots of the last round's first n_add additions)."""
+        st = ct.c_uint32(0)
+        out = np.zeros(int(n_add), np.int64)
+        self._check(self.lib.mrf_batch_queue_result(self.b, ct.byref(st), int(n_add), out.ctypes.data if n_add else None))
+        return int(st.value), out
 
     def reset_marginals(self, burn_in: int = 0):
         self._check(self.lib.mrf_batch_reset_marginals(self.b, int(burn_in)))

@@ -334,6 +334,106 @@ def er_edit(model: Model, frac: float, rng: np.random.Generator, w_half: float =
     return rem.astype(np.int64), s, t, pair
 
 
+class ErBatchEdits:
+    """Edits of the batched dynamic workload for all graphs at once, with the
+    distributions of er_edit: every round removes ceil(frac E_g) edges of every
+    graph g chosen uniformly, and adds as many new distinct pairs {s, t},
+    s < t, absent from the graph (its edges before the round), with tables
+    exp(U[-w_half, w_half]).  Keeps each graph's edge list (graph-local
+    endpoints and the batch's class slots) and the sorted keys of all edges,
+    key = base_g + s N_g + t, so that a round costs O(edits + sum E_g) numpy
+    work and no table is kept on the host."""
+
+    def __init__(self, models, first_slots, seed: int = 1, w_half: float = 0.5):
+        self.G = len(models)
+        self.n = np.array([m.n_vars for m in models], np.int64)
+        self.L = np.array([m.n_labels for m in models], np.int64)
+        self.base = np.concatenate([[0], np.cumsum(self.n * self.n)[:-1]]).astype(np.int64)
+        self.lo = [np.minimum(m.src, m.dst).astype(np.int32) for m in models]
+        self.hi = [np.maximum(m.src, m.dst).astype(np.int32) for m in models]
+        self.src = [m.src.astype(np.int32) for m in models]
+        self.dst = [m.dst.astype(np.int32) for m in models]
+        self.slot = [np.arange(m.n_edges, dtype=np.int64) + int(first_slots[g]) for g, m in enumerate(models)]
+        self.keys = np.sort(np.concatenate([self.base[g] + self.lo[g].astype(np.int64) * self.n[g] + self.hi[g]
+                                            for g in range(self.G)]))
+        self.rng = np.random.default_rng(seed)
+        self.w_half = w_half
+        self._pending = None
+
+    def n_edges(self):
+        return int(sum(len(s) for s in self.src))
+
+    def counts(self, frac: float):
+        """Removals (= additions) of every graph in one round."""
+        return np.array([int(math.ceil(frac * len(s))) if len(s) else 0 for s in self.src], np.int64)
+
+    def edit(self, frac: float = 0.01):
+        """Arrays of one round for the batch's edit calls: (remove_graph,
+        remove_slot, add_graph, add_src, add_dst, add_tables_flat)."""
+        rng, G = self.rng, self.G
+        k = self.counts(frac)
+        rem = [np.sort(rng.choice(len(self.src[g]), size=int(k[g]), replace=False)) if k[g] else
+               np.zeros(0, np.int64) for g in range(G)]
+        # additions: candidate pairs for the missing count of every graph until all are met
+        acc_keys = np.zeros(0, np.int64)
+        acc_g = np.zeros(0, np.int64)
+        missing = k.copy()
+        while missing.sum() > 0:
+            gid = np.repeat(np.arange(G, dtype=np.int64), missing)
+            a = np.floor(rng.random(gid.shape[0]) * self.n[gid]).astype(np.int64)
+            b = np.floor(rng.random(gid.shape[0]) * self.n[gid]).astype(np.int64)
+            ok = a != b
+            gid, a, b = gid[ok], a[ok], b[ok]
+            key = self.base[gid] + np.minimum(a, b) * self.n[gid] + np.maximum(a, b)
+            pos = np.searchsorted(self.keys, key)
+            fresh = (pos >= self.keys.shape[0]) | (self.keys[np.minimum(pos, self.keys.shape[0] - 1)] != key)
+            acc_keys = np.concatenate([acc_keys, key[fresh]])
+            acc_g = np.concatenate([acc_g, gid[fresh]])
+            _, first = np.unique(acc_keys, return_index=True)
+            first = np.sort(first)
+            acc_keys, acc_g = acc_keys[first], acc_g[first]
+            # keep at most k_g per graph (in draw order)
+            order = np.argsort(acc_g, kind="stable")
+            acc_keys, acc_g = acc_keys[order], acc_g[order]
+            starts = np.searchsorted(acc_g, np.arange(G))
+            rank = np.arange(acc_g.shape[0]) - starts[acc_g]
+            keep = rank < k[acc_g]
+            acc_keys, acc_g = acc_keys[keep], acc_g[keep]
+            missing = k - np.bincount(acc_g, minlength=G)
+        local = acc_keys - self.base[acc_g]
+        s_new = (local // self.n[acc_g]).astype(np.int32)
+        t_new = (local % self.n[acc_g]).astype(np.int32)
+        tables = _f32_uniform(rng, -self.w_half, self.w_half, int((self.L[acc_g] ** 2).sum()))
+        rm_g = np.repeat(np.arange(G, dtype=np.int32), k)
+        rm_slot = np.concatenate([self.slot[g][rem[g]] for g in range(G)]) if G else np.zeros(0, np.int64)
+        self._pending = (k, rem, acc_g, s_new, t_new)
+        return (rm_g, rm_slot.astype(np.int64), acc_g.astype(np.int32), s_new, t_new, tables)
+
+    def apply(self, new_slots):
+        """Record the round once the batch has applied it (new_slots: the
+        class slots of the additions, in the order of edit's arrays)."""
+        k, rem, acc_g, s_new, t_new = self._pending
+        starts = np.concatenate([[0], np.cumsum(k)])
+        rm_keys = []
+        for g in range(self.G):
+            r = rem[g]
+            rm_keys.append(self.base[g] + self.lo[g][r].astype(np.int64) * self.n[g] + self.hi[g][r])
+            keep = np.ones(len(self.src[g]), bool)
+            keep[r] = False
+            a, b = s_new[starts[g]:starts[g + 1]], t_new[starts[g]:starts[g + 1]]
+            self.src[g] = np.concatenate([self.src[g][keep], a])
+            self.dst[g] = np.concatenate([self.dst[g][keep], b])
+            self.lo[g] = np.concatenate([self.lo[g][keep], np.minimum(a, b)])
+            self.hi[g] = np.concatenate([self.hi[g][keep], np.maximum(a, b)])
+            self.slot[g] = np.concatenate([self.slot[g][keep], np.asarray(new_slots[starts[g]:starts[g + 1]], np.int64)])
+        rmk = np.sort(np.concatenate(rm_keys)) if rm_keys else np.zeros(0, np.int64)
+        keys = np.delete(self.keys, np.searchsorted(self.keys, rmk))
+        add = np.sort(self.base[acc_g] + np.minimum(s_new, t_new).astype(np.int64) * self.n[acc_g]
+                      + np.maximum(s_new, t_new))
+        self.keys = np.insert(keys, np.searchsorted(keys, add), add)
+        self._pending = None
+
+
 # ----------------------------------------------------------------------------- blocks
 
 def adjacency(n_vars: int, src: np.ndarray, dst: np.ndarray):
