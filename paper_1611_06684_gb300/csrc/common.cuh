@@ -125,6 +125,7 @@ struct SweepArgs {
     FastDiv fdX1, fdX, fdY1, fdY;   // division by nx-1, nx, ny-1, ny
     float* pot;                // [N][L][C] node potentials / beliefs of the blocked sweep
     const uint8_t* skip;       // [E] 1 = edge kept exact (no dual bit) in a learned sweep; null otherwise
+    float* part;               // [E][C][2][L] partial fields of the edge-partial plain sweep, or null
 };
 
 // One dualised entry of log-value l != 0 (Lemma 2-4 and Theorem 2 in closed
@@ -215,6 +216,10 @@ struct LearnedArgs {
 cudaError_t launch_init_labels(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_dual(const SweepArgs& a, int layout, cudaStream_t s);
 cudaError_t launch_primal(const SweepArgs& a, int layout, int schedule, cudaStream_t s);
+// Plain sweep in the edge-partial form (few chains, more than 16 entries per
+// edge): step 0 the dual bits and per-edge partial fields, step 1 the labels.
+cudaError_t launch_sweep_partial(const SweepArgs& a, int layout, int step, cudaStream_t s);
+constexpr int kPartialMaxChains = 4;
 cudaError_t launch_fused(const SweepArgs& a, int layout, int schedule, cudaStream_t s);
 cudaError_t launch_accumulate(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_philox_rate(uint64_t threads, int calls, uint32_t* sink, cudaStream_t s);

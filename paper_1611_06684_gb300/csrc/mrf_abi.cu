@@ -83,6 +83,8 @@ struct mrf {
     double* d_hgut = nullptr; float* d_hgutf = nullptr;
     bool sw_checked = false;           // the model passed the check since the factors last changed
     float* d_pot = nullptr;            // [N][L][C] node potentials of the blocked sweep
+    float* d_part = nullptr;           // [E_cap][C][2][L] partial fields of the edge-partial plain sweep
+    int64_t part_cap = 0;              // edge slots d_part holds
     int schedule = 0;                  // primal schedule in use (1 thread, 2 CTA); 0 = not tuned yet
     int32_t* d_csr_work = nullptr;     // [2N] degrees and cursors of the device CSR build
     int64_t* d_csr_sums = nullptr;     // block sums of the device scan
@@ -193,9 +195,14 @@ SweepArgs make_args(const mrf_t* h) {
         a.fdY1 = FastDiv::make((uint32_t)(ny - 1)); a.fdY = FastDiv::make((uint32_t)ny);
     }
     a.pot = h->d_pot;
+    a.part = h->d_part;
     a.grid_nx = h->opt.grid_nx; a.grid_ny = h->opt.grid_ny; a.grid_nz = h->opt.grid_nz;
     return a;
 }
+
+// The plain sweep takes the edge-partial form for few chains and tables with
+// more than 16 entries (see k_dual_partial).
+bool use_partial(const mrf_t* h) { return h->C <= kPartialMaxChains && h->M > 16; }
 
 // Copy n elements of T from a host or device pointer to host.
 template <class T>
@@ -307,6 +314,7 @@ mrf_status grow_slots(mrf_t* h, int64_t new_slots) {
     if (h->d_swt) { MRF_CUDA(h, grow(h->d_swt, L)); MRF_CUDA(h, grow(h->d_swl, L)); MRF_CUDA(h, grow(h->d_swell, L)); }
     if (h->d_swfold) MRF_CUDA(h, grow(h->d_swfold, 2 * L));
     MRF_CUDA(h, dalloc(h->d_theta, (size_t)cap * h->C * h->W));
+    if (use_partial(h)) MRF_CUDA(h, dalloc(h->d_part, (size_t)cap * h->C * 2 * L));
     h->E_cap = cap;
     return MRF_OK;
 }
@@ -464,7 +472,7 @@ void mrf_destroy(mrf_t* h) {
     drop_graphs(h);
     dfree(h->d_unary); dfree(h->d_ut); dfree(h->d_utf); dfree(h->d_tpl); dfree(h->d_src); dfree(h->d_dst); dfree(h->d_tau); dfree(h->d_thr);
     dfree(h->d_fold); dfree(h->d_cst); dfree(h->d_resid); dfree(h->d_inc_ptr); dfree(h->d_inc); dfree(h->d_x);
-    dfree(h->d_theta); dfree(h->d_counts); dfree(h->d_lpv); dfree(h->d_logv); dfree(h->d_em); dfree(h->d_mfq); dfree(h->d_mfs); dfree(h->d_logp); dfree(h->d_ctl); dfree(h->d_flag); dfree(h->d_stage); dfree(h->d_pot);
+    dfree(h->d_theta); dfree(h->d_counts); dfree(h->d_lpv); dfree(h->d_logv); dfree(h->d_em); dfree(h->d_mfq); dfree(h->d_mfs); dfree(h->d_logp); dfree(h->d_ctl); dfree(h->d_flag); dfree(h->d_stage); dfree(h->d_pot); dfree(h->d_part);
     dfree(h->d_swt); dfree(h->d_swl); dfree(h->d_swfold); dfree(h->d_swut); dfree(h->d_swpar); dfree(h->d_swroot); dfree(h->d_swbits); dfree(h->d_swban); dfree(h->d_swlw); dfree(h->d_swerr); dfree(h->d_swchk);
     dfree(h->d_swufix); dfree(h->d_swell);
     dfree(h->d_hgT); dfree(h->d_hglb); dfree(h->d_hgtau); dfree(h->d_hgthr); dfree(h->d_hgtpl); dfree(h->d_hgfold);
@@ -545,6 +553,7 @@ mrf_status mrf_set_factors(mrf_t* h, const float* unary_log, int64_t n_edges, co
     }
     h->sw_checked = false;
     MRF_CUDA(h, dalloc(h->d_theta, E * h->C * h->W));
+    if (use_partial(h)) MRF_CUDA(h, dalloc(h->d_part, E * h->C * 2 * h->L));
     MRF_CUDA(h, to_device(h->d_src, h->h_src.data(), n_edges, MRF_PTR_HOST, h->stream));
     MRF_CUDA(h, to_device(h->d_dst, h->h_dst.data(), n_edges, MRF_PTR_HOST, h->stream));
     MRF_CUDA(h, build_csr(h));
@@ -711,6 +720,7 @@ mrf_status mrf_edit_factors(mrf_t* h, int64_t n_remove, const int64_t* edge_ids,
 // unchanged) and keep the faster.  The boundary counter is restored after.
 static mrf_status tune_schedule(mrf_t* h) {
     if (h->opt.schedule == 1 || h->opt.schedule == 2) { h->schedule = h->opt.schedule; return MRF_OK; }
+    if (use_partial(h)) { h->schedule = 1; return MRF_OK; }         // one primal form only
     SweepArgs a = make_args(h);
     a.logp = nullptr;
     unsigned long long bnd = 0;
@@ -745,9 +755,12 @@ static bool use_mlp_tc(const mrf_t* h) { return h->opt.mlp_path == 0 && mlp_tc_s
 
 // Models small enough for k_sweep_small: at most 2^16 (site, chain) and
 // (edge, chain) items, theta of all items within 200 KB of shared memory.
+// Small models run several plain sweeps in one single-CTA launch (k_sweep_small,
+// the additions of k_primal); handles on the edge-partial form keep it for
+// every sweep, so that a chain does not depend on the sweeps per call.
 static bool small_model(const mrf_t* h) {
     const int64_t nv = (int64_t)h->N * h->C, ne = h->E_slots * h->C;
-    return nv <= 65536 && ne <= 65536 && ne * h->W * 4 <= 200 * 1024;
+    return nv <= 65536 && ne <= 65536 && ne * h->W * 4 <= 200 * 1024 && !use_partial(h);
 }
 
 static SwArgs make_sw_args(const mrf_t* h) {
@@ -877,7 +890,10 @@ static mrf_status enqueue_sweep(mrf_t* h, int mode) {
     SweepArgs a = make_args(h);
     cudaStream_t s = h->stream;
     cudaError_t e = cudaSuccess;
-    if (mode == MRF_MODE_PLAIN) {
+    if (mode == MRF_MODE_PLAIN && use_partial(h)) {
+        e = timed(h, MRF_K_DUAL, [&] { return launch_sweep_partial(a, h->layout, 0, s); });
+        if (e == cudaSuccess) e = timed(h, MRF_K_PRIMAL, [&] { return launch_sweep_partial(a, h->layout, 1, s); });
+    } else if (mode == MRF_MODE_PLAIN) {
         e = timed(h, MRF_K_DUAL, [&] { return launch_dual(a, h->layout, s); });
         if (e == cudaSuccess) e = timed(h, MRF_K_PRIMAL, [&] { return launch_primal(a, h->layout, h->schedule, s); });
     } else if (mode == MRF_MODE_FUSED) {
@@ -1292,7 +1308,7 @@ mrf_status mrf_load(mrf_t** out, const char* path, void* cuda_stream) {
         dalloc(h->d_tpl, E * plane_words(h->M)) || dalloc(h->d_fold, E * 2 * L) || dalloc(h->d_cst, E) ||
         (hd.has_resid && dalloc(h->d_resid, E * L * L)) || ((hd.has_sw & 1) && (dalloc(h->d_swt, E * L) || dalloc(h->d_swl, E * L) || dalloc(h->d_swell, E * L))) ||
         ((hd.has_sw & 2) && (dalloc(h->d_swfold, E * 2 * L) || dalloc(h->d_swut, NL))) ||
-        dalloc(h->d_theta, E * h->C * h->W)) {
+        dalloc(h->d_theta, E * h->C * h->W) || (use_partial(h) && dalloc(h->d_part, E * h->C * 2 * L))) {
         cudaGetLastError();
         return bail(MRF_ENOMEM);
     }

@@ -8,6 +8,7 @@ namespace mrfk {
 template <int L, int LAYOUT> cudaError_t run_dual(const SweepArgs& a, cudaStream_t s);
 template <int L, int LAYOUT, bool FUSED> cudaError_t run_primal(const SweepArgs& a, cudaStream_t s);
 template <int L, int LAYOUT> cudaError_t run_primal_cta(const SweepArgs& a, cudaStream_t s);
+template <int L, int LAYOUT> cudaError_t run_sweep_partial(const SweepArgs& a, int step, cudaStream_t s);
 
 __global__ void k_init_labels(SweepArgs a) {
     const int64_t n = (int64_t)a.N * a.C;
@@ -299,6 +300,15 @@ cudaError_t launch_dual(const SweepArgs& a, int layout, cudaStream_t s) {
         MRF_DISPATCH_L(a.L, return (run_dual<LL, MRF_LAYOUT_DIAG>(a, s)));
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_partial(const SweepArgs& a, int layout, int step, cudaStream_t s) {
+    if (layout == MRF_LAYOUT_PIVOT) {
+        MRF_DISPATCH_L(a.L, return (run_sweep_partial<LL, MRF_LAYOUT_PIVOT>(a, step, s)));
+    } else {
+        MRF_DISPATCH_L(a.L, return (run_sweep_partial<LL, MRF_LAYOUT_DIAG>(a, step, s)));
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_primal(const SweepArgs& a, int layout, int schedule, cudaStream_t s) {

@@ -741,6 +741,177 @@ __global__ void __launch_bounds__(256) k_primal_cta(SweepArgs a, int CG) {
     }
 }
 
+// ---------------------------------------------------------------------------- few chains, many entries
+
+// Plain sweep for few chains (C <= 4) and tables with more than 16 entries,
+// where a thread per (edge, chain) or (site, chain) would read every entry's
+// weight row on its own.  The dual step takes one warp per edge; lane b holds
+// the entries k = 32 g + b: their packed threshold words and signed weights
+// are read once per edge (coalesced) and kept for all chains.  Per chain: the
+// prefix draws of the edge's groups (its Philox calls shared out over the
+// lanes, the plane words passed by shuffles), each lane's dual bits (a prefix
+// tie decided by the lane with the low-16-bit draw), the bit words, and the
+// edge's two partial fields -- over the set bits, the row sums of the signed
+// weights (source side, beta1) and the column sums of their magnitudes
+// (destination side, beta2), each in entry order.  The primal step then adds
+// the partial fields of a site's incidences in incidence order (two-sum flush
+// every 32, as k_primal) and draws the label.
+template <int L, int LAYOUT>
+__global__ void __launch_bounds__(256) k_dual_partial(SweepArgs a) {
+    using E = Ent<L, LAYOUT>;
+    constexpr int M = E::M, W = E::W, MP = E::MP;
+    constexpr uint32_t FULL = 0xFFFFFFFFu;
+    static_assert(M > 16 && L <= 16, "edge-partial form: more than 16 entries, at most 16 labels");
+    __shared__ float s_t[8][W * 32];                       // weights of the set bits, per warp
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t e = blockIdx.x * 8ll + warp;
+    if (e >= a.E) return;                                  // whole warps
+    const int C = a.C;
+    const int s = a.src[e];
+    if (s < 0) {                                           // free slot: no bits
+        for (int q = lane; q < C * W; q += 32) a.theta[e * C * W + q] = 0u;
+        return;
+    }
+    const int t = a.dst[e];
+    const uint32_t sweep = (uint32_t)a.ctl->sweep;
+    const uint8_t* xin = a.x + (size_t)(sweep & 1) * a.N * a.C;
+    uint32_t wd[W];
+    float tv[W];
+#pragma unroll
+    for (int g = 0; g < W; ++g) {
+        const int k = 32 * g + lane;
+        wd[g] = k < M ? __ldg(a.thr + e * M + k) : 0u;
+        tv[g] = k < M ? __ldg(a.tau + e * MP + k) : 0.0f;
+    }
+    for (int c = 0; c < C; ++c) {
+        const int xs = xin[(int64_t)s * C + c], xt = xin[(int64_t)t * C + c];
+        // lane q < 2W: call q (group q / 2, half q % 2) of the edge's prefix draws
+        uint4 r = make_uint4(0u, 0u, 0u, 0u);
+        if (lane < 2 * W) r = draw_rk((uint32_t)e, sweep, (uint32_t)c, PH_DUAL, (uint32_t)lane, a.rk);
+        uint32_t bw[W];
+#pragma unroll
+        for (int g = 0; g < W; ++g) {
+            const uint32_t P[8] = {__shfl_sync(FULL, r.x, 2 * g), __shfl_sync(FULL, r.y, 2 * g),
+                                   __shfl_sync(FULL, r.z, 2 * g), __shfl_sync(FULL, r.w, 2 * g),
+                                   __shfl_sync(FULL, r.x, 2 * g + 1), __shfl_sync(FULL, r.y, 2 * g + 1),
+                                   __shfl_sync(FULL, r.z, 2 * g + 1), __shfl_sync(FULL, r.w, 2 * g + 1)};
+            uint32_t u8 = 0;
+#pragma unroll
+            for (int p = 0; p < 8; ++p) u8 |= ((P[p] >> lane) & 1u) << (7 - p);
+            const int k = 32 * g + lane;
+            bool bit = false;
+            if (k < M && wd[g]) {
+                const int y = xs == E::i(k), z = xt == E::j(k);
+                const int level = (wd[g] >> 31) ? 1 + z - y : y + z;
+                const uint32_t T = level == 1 ? (1u << 23) : level_threshold(wd[g], level == 2);
+                const uint32_t T8 = threshold_prefix(T);
+                if (u8 < T8) {
+                    bit = true;
+                } else if (u8 == T8) {
+                    const uint32_t rem = T - (T8 << 16);
+                    bit = rem && dual_low16((uint32_t)e, sweep, (uint32_t)c, k, a.rk) < rem;
+                }
+            }
+            bw[g] = __ballot_sync(FULL, bit);
+            s_t[warp][32 * g + lane] = bit ? tv[g] : 0.0f;
+        }
+        if (lane < W) {
+            uint32_t v = bw[0];
+#pragma unroll
+            for (int g = 1; g < W; ++g) v = lane == g ? bw[g] : v;
+            a.theta[(e * C + c) * W + lane] = v;
+        }
+        __syncwarp();
+        float* pe = a.part + ((e * C + c) * 2) * L;
+        if (lane < L) {                                    // row `lane`: source side
+            float sum = 0.0f;
+            if (LAYOUT == MRF_LAYOUT_PIVOT) {
+                if (lane >= 1)
+                    for (int jj = 1; jj < L; ++jj) sum += s_t[warp][(lane - 1) * (L - 1) + (jj - 1)];
+            } else {
+                sum = s_t[warp][lane];
+            }
+            pe[lane] = sum;
+        } else if (lane >= 16 && lane < 16 + L) {          // column `lane - 16`: destination side
+            const int x = lane - 16;
+            float sum = 0.0f;
+            if (LAYOUT == MRF_LAYOUT_PIVOT) {
+                if (x >= 1)
+                    for (int ii = 1; ii < L; ++ii) sum += fabsf(s_t[warp][(ii - 1) * (L - 1) + (x - 1)]);
+            } else {
+                sum = fabsf(s_t[warp][x]);
+            }
+            pe[L + x] = sum;
+        }
+        __syncwarp();
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(256) k_primal_partial(SweepArgs a) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;     // N * C < 2^32 (checked by the host)
+    if (g >= (uint64_t)a.N * a.C) return;
+    const uint32_t v = a.fdC.div(g), c = g - v * (uint32_t)a.C;
+    const uint32_t sweep = (uint32_t)a.ctl->sweep;
+    uint8_t* xout = a.x + (size_t)((sweep + 1) & 1) * a.N * a.C;
+    float acc[L], hi[L], lo[L];
+#pragma unroll
+    for (int x = 0; x < L; ++x) { acc[x] = 0.0f; hi[x] = 0.0f; lo[x] = 0.0f; }
+    const int64_t p0 = a.inc_ptr[v], p1 = a.inc_ptr[v + 1];
+    int chunk = 0;
+    bool flushed = false;
+    constexpr int B = 4;                                   // incidence records loaded together
+    for (int64_t base = p0; base < p1; base += B) {
+        int code[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) code[u] = base + u < p1 ? __ldg(&a.inc[base + u]).x : -1;
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            if (code[u] < 0) continue;
+            const float* pe = a.part + (((int64_t)(code[u] >> 1) * a.C + c) * 2 + (code[u] & 1)) * L;
+            if constexpr (L % 4 == 0) {
+#pragma unroll
+                for (int x4 = 0; x4 < L / 4; ++x4) {
+                    const float4 q = __ldcs(reinterpret_cast<const float4*>(pe) + x4);
+                    acc[4 * x4] += q.x; acc[4 * x4 + 1] += q.y; acc[4 * x4 + 2] += q.z; acc[4 * x4 + 3] += q.w;
+                }
+            } else {
+#pragma unroll
+                for (int x = 0; x < L; ++x) acc[x] += __ldcs(pe + x);
+            }
+            if (++chunk == 32) {
+#pragma unroll
+                for (int x = 0; x < L; ++x) { two_sum_add(hi[x], lo[x], acc[x]); acc[x] = 0.0f; }
+                chunk = 0;
+                flushed = true;
+            }
+        }
+    }
+    float F[L];
+    const float* uf = a.utf + (int64_t)v * L;
+    if (flushed) {
+#pragma unroll
+        for (int x = 0; x < L; ++x) { two_sum_add(hi[x], lo[x], acc[x]); F[x] = __ldg(uf + x) + (hi[x] + lo[x]); }
+    } else {
+#pragma unroll
+        for (int x = 0; x < L; ++x) F[x] = __ldg(uf + x) + acc[x];
+    }
+    float* lp = a.logp ? a.logp + ((int64_t)c * a.N + v) * L : nullptr;
+    xout[g] = (uint8_t)draw_label<L>(F, v, c, sweep, a.rk, PH_PRIMAL, lp, a.ctl, a.lpv ? a.lpv + g : nullptr);
+}
+
+template <int L, int LAYOUT>
+cudaError_t run_sweep_partial(const SweepArgs& a, int step, cudaStream_t s) {
+    if constexpr (Ent<L, LAYOUT>::M > 16) {
+        const int64_t n = (int64_t)a.N * a.C;
+        if (step == 0 && a.E > 0) k_dual_partial<L, LAYOUT><<<(unsigned)((a.E + 7) / 8), 256, 0, s>>>(a);
+        if (step == 1 && n > 0) k_primal_partial<L><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
 // ---------------------------------------------------------------------------- small models
 
 // n_sweeps whole plain sweeps of a small model in one CTA (sizes where launch
@@ -1081,6 +1252,8 @@ cudaError_t run_em_pot(const SweepArgs& a, const uint8_t* xin, cudaStream_t s) {
     template cudaError_t run_primal_cta<L, MRF_LAYOUT_DIAG>(const SweepArgs&, cudaStream_t);      \
     template cudaError_t run_potential<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, cudaStream_t);      \
     template cudaError_t run_potential<L, MRF_LAYOUT_DIAG>(const SweepArgs&, cudaStream_t);       \
+    template cudaError_t run_sweep_partial<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, int, cudaStream_t); \
+    template cudaError_t run_sweep_partial<L, MRF_LAYOUT_DIAG>(const SweepArgs&, int, cudaStream_t);  \
     template cudaError_t run_dual<L, MRF_LAYOUT_PIVOT>(const SweepArgs&, cudaStream_t);           \
     template cudaError_t run_dual<L, MRF_LAYOUT_DIAG>(const SweepArgs&, cudaStream_t);            \
     template cudaError_t run_primal<L, MRF_LAYOUT_PIVOT, false>(const SweepArgs&, cudaStream_t);  \

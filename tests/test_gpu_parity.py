@@ -70,6 +70,9 @@ CASES = {
     "constant_tables": (_constant_tables, 32),
     "isolated_sites": (_isolated_sites, 7),
     "potts_L16_diag": (lambda: wl.tiny_potts(40, 16, 90, seed=25), 32),
+    # few chains and more than 16 entries per edge (edge-partial plain sweep): degree > 32 too
+    "random_L8_C1": (lambda: wl.random_graph(300, k=3, L=8, seed=31, w_std=0.3), 1),
+    "random_L12_C4": (lambda: wl.random_graph(150, k=4, L=12, seed=32, w_std=0.3), 4),
     "star_degree700": (_star, 32),
 }
 
@@ -141,6 +144,26 @@ def test_one_sweep_matches_oracle(name, mode):
     stats = compare_sweep(dec, ref, h.get_labels(), lp, theta)
     print(name, mode, stats)
     assert h.info().sweep_index == t + 1
+    h.close()
+
+
+def test_edge_partial_form_at_high_degree_matches_oracle():
+    """The edge-partial plain sweep (few chains, > 16 entries per edge) on a
+    fully connected model: 79 incidences per site, so the partial fields go
+    through the two-sum flush; dual bits, log p and labels against the oracle.
+    (The fused form keeps one running sum over ~1,400 weights per site here, so
+    its float32 log p drifts past 1e-5: only the plain form is checked.)"""
+    model, C = wl.dense_potts(80, L=7, seed=33), 2
+    seed, t = 2024, 17
+    dec = dc.decompose(model)
+    x0 = np.random.default_rng(11).integers(0, model.n_labels, size=(C, model.n_vars))
+    h = make_handle(model, C, seed, record_logp=True, kernel_timing=True)
+    h.set_labels(x0.astype(np.uint8))
+    h.set_sweep_index(t)
+    h.sweep(1, M.MODE_PLAIN)
+    lp, _ = h.debug_logp()
+    ref = sampler.sweep(dec, x0, t, seed)
+    print(compare_sweep(dec, ref, h.get_labels(), lp, M.unpack_theta(h.debug_theta(), dec.n_entries)))
     h.close()
 
 
