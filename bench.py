@@ -138,6 +138,11 @@ def kernel_work(name, model_info, C):
     calls_dual = E * C * math.ceil(m / 16)
     if name == "k_dual":
         return calls_dual, E * m * 4 + E * C * W * 4 + N * C
+    if name == "k_primal" and model_info.get("partial"):
+        # edge-partial form: the partial fields of every incidence, incidence records, unaries, labels
+        return N * C, 2 * E * C * L * 4 + 2 * E * 8 + N * L * 4 + 2 * N * C + N * 8
+    if name == "k_edge_partial":
+        return 0, E * m * 4 + E * C * W * 4 + 2 * E * C * L * 4 + E * 4
     if name == "k_primal":
         return N * C, 2 * E * C * W * 4 + 2 * E * m * 4 + N * L * 8 + 2 * E * 8 + 2 * N * C + N * 16
     if name == "k_primal<fused>":
@@ -729,7 +734,8 @@ def run_batch_workload(args):
     ed.apply(slots)
     peaks, peak_src = load_peaks()
     row, name, dom_ms = dom
-    minfo = dict(E=row["edges"], N=row["sites"], L=row["L"], m=row["dual_bits_per_edge"])
+    minfo = dict(E=row["edges"], N=row["sites"], L=row["L"], m=row["dual_bits_per_edge"],
+                 partial=C <= 4 and row["dual_bits_per_edge"] >= 100)
     _, nbytes = kernel_work(name, minfo, C)
     roof = {"bound": "hbm", "achieved": nbytes / (dom_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "traffic": None, "kernel": f"{name} (class L={row['L']})", "bytes_per_launch": nbytes,

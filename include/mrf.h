@@ -224,7 +224,9 @@ enum { MRF_K_DUAL = 0, MRF_K_PRIMAL = 1, MRF_K_FUSED = 2, MRF_K_POTENTIAL = 3, M
        MRF_K_SW_BOND = 10, MRF_K_SW_FLATTEN = 11,
        MRF_K_SW_DRAW = 12, /* Swendsen-Wang: label draw of every cluster and the copy to its sites */
        MRF_K_SW_SMALL = 13,/* whole Swendsen-Wang sweeps of a small model in one launch */
-       MRF_K_COUNT = 14 };
+       MRF_K_PARTIAL = 14, /* per-edge partial fields of the plain sweep for few chains and
+                              tables with more than 16 entries (then MRF_K_PRIMAL adds them) */
+       MRF_K_COUNT = 15 };
 /* With options.kernel_timing: total device milliseconds ms[MRF_K_COUNT] and
  * launch counts launches[MRF_K_COUNT] of every sweep kernel since the last
  * call (CUDA events on the handle's stream); resets the totals.  Synchronises. */

@@ -139,20 +139,27 @@ struct EntryDual {
     uint32_t word;
     double alpha1, alpha2, log_norm;
 };
+//
+// With a = |l|, s = sqrt(1 - e^-a) and b = (1 + s)^2: tau = a + 2 log1p(s) and
+// e^-tau = e^-a / b, so sigmoid(+tau) = b / (b + e^-a), sigmoid(-tau) = e^-a / (b + e^-a)
+// and, for l > 0 (q = -tau), -log(1 + e^q) = -log1p(e^-a / b): four float64
+// transcendentals per entry (expm1, exp, two log1p) and one division.
 __host__ __device__ inline EntryDual entry_dual(double l) {
     const double al = fabs(l);
-    const double tau = al + 2.0 * log1p(sqrt(-expm1(-al)));
-    const double pp = 1.0 / (1.0 + exp(-tau));   // sigmoid(+tau)
-    const double pm = 1.0 / (1.0 + exp(tau));    // sigmoid(-tau)
+    const double s = sqrt(-expm1(-al));
+    const double tau = al + 2.0 * log1p(s);
+    const double ea = exp(-al), b = (1.0 + s) * (1.0 + s);
+    const double inv = 1.0 / (b + ea);
+    const double pp = b * inv;                   // sigmoid(+tau)
+    const double pm = ea * inv;                  // sigmoid(-tau)
     const uint32_t tp = (uint32_t)ceil(pp * 16777216.0 - 0.5), tm = (uint32_t)ceil(pm * 16777216.0 - 0.5);
     const uint32_t d = tp + tm - ((1u << 24) - 1u);   // in {0,1,2}
     EntryDual r;
     r.word = tp | (d << 25) | (l < 0 ? 0x80000000u : 0u);
     r.tau_s = (float)(l > 0 ? tau : -tau);
-    const double q = l > 0 ? -tau : 0.0;
     r.alpha1 = l > 0 ? 0.5 * (l - tau) : 0.5 * (l + tau);
     r.alpha2 = 0.5 * (l - tau);
-    r.log_norm = -(q > 0 ? q + log1p(exp(-q)) : log1p(exp(q)));
+    r.log_norm = l > 0 ? -log1p(ea / b) : -0.69314718055994530942;   // q = -tau, or q = 0: -log 2
     return r;
 }
 
@@ -217,9 +224,10 @@ cudaError_t launch_init_labels(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_dual(const SweepArgs& a, int layout, cudaStream_t s);
 cudaError_t launch_primal(const SweepArgs& a, int layout, int schedule, cudaStream_t s);
 // Plain sweep in the edge-partial form (few chains, more than 16 entries per
-// edge): step 0 the dual bits and per-edge partial fields, step 1 the labels.
+// edge), after the dual step: step 0 the per-edge partial fields, step 1 the labels.
 cudaError_t launch_sweep_partial(const SweepArgs& a, int layout, int step, cudaStream_t s);
 constexpr int kPartialMaxChains = 4;
+constexpr int kPartialMinEntries = 100;
 cudaError_t launch_fused(const SweepArgs& a, int layout, int schedule, cudaStream_t s);
 cudaError_t launch_accumulate(const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_philox_rate(uint64_t threads, int calls, uint32_t* sink, cudaStream_t s);

@@ -42,87 +42,54 @@ __global__ void k_count_offdiag(const float* pair, int64_t n_edges, int L, unsig
     if (cnt) atomicAdd(nz, cnt);
 }
 
-// One warp per edge: the lanes take the entries k = lane, lane + 32, ... (each
-// entry's float64 arithmetic is independent), stage alpha1, alpha2 and the
-// log normaliser in shared memory, then lane x sums row x into the source
-// offsets and column x into the destination offsets, and lane 0 the log
-// constant -- every accumulator in increasing entry order, as a serial loop
-// over the entries would.
-constexpr int kDecompWarps = 4;
-constexpr int kMaxEntries = (kMaxLabels - 1) * (kMaxLabels - 1);
-
-__global__ void __launch_bounds__(32 * kDecompWarps) k_decompose(DecompArgs a) {
-    __shared__ double s_a1[kDecompWarps][kMaxEntries], s_a2[kDecompWarps][kMaxEntries], s_ln[kDecompWarps][kMaxEntries];
-    __shared__ uint32_t s_on[kDecompWarps][(kMaxEntries + 31) / 32];
-    __shared__ double s_f[kDecompWarps][2][kMaxLabels];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = blockIdx.x * (int64_t)kDecompWarps + warp;
-    if (i >= a.n || (a.n_dev && i >= *a.n_dev) || (a.status && (*a.status & kQFatal))) return;   // whole warps
+__global__ void k_decompose(DecompArgs a) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.n || (a.n_dev && i >= *a.n_dev) || (a.status && (*a.status & kQFatal))) return;
     const int L = a.L, M = a.M;
-    const bool pivot = a.layout == MRF_LAYOUT_PIVOT;
     const int64_t e = a.slots ? a.slots[i] : a.first_slot + i;
     const float* w = a.pair + (a.pair_off ? a.pair_off[i] : i * L * L);
-    const double w00 = w[0];
-    for (int k = lane; k < pad4(M); k += 32) {
+    double fs[kMaxLabels], ft[kMaxLabels];
+    double cst = 0.0;
+    if (a.layout == MRF_LAYOUT_PIVOT) {
+        const double w00 = w[0];
+        for (int x = 0; x < L; ++x) {
+            fs[x] = (double)w[x * L] - w00;
+            ft[x] = (double)w[x] - w00;
+        }
+        cst = w00;
+    } else {
+        for (int x = 0; x < L; ++x) fs[x] = ft[x] = 0.0;
+    }
+    for (int k = 0; k < M; ++k) {
+        int ii, jj;
+        double l;
+        if (a.layout == MRF_LAYOUT_PIVOT) {
+            ii = 1 + k / (L - 1); jj = 1 + k % (L - 1);
+            l = (double)w[ii * L + jj] - (double)w[ii * L] - (double)w[jj] + (double)w[0];
+        } else {
+            ii = jj = k;
+            l = (double)w[k * L + k];
+        }
         float tau_s = 0.0f;
         uint32_t word = 0;
-        if (k < M) {
-            int ii, jj;
-            double l;
-            if (pivot) {
-                ii = 1 + k / (L - 1); jj = 1 + k % (L - 1);
-                l = (double)w[ii * L + jj] - (double)w[ii * L] - (double)w[jj] + w00;
-            } else {
-                ii = jj = k;
-                l = (double)w[k * L + k];
-            }
-            if (l != 0.0) {
-                const EntryDual d = entry_dual(l);
-                word = d.word;
-                tau_s = d.tau_s;
-                s_a1[warp][k] = d.alpha1;
-                s_a2[warp][k] = d.alpha2;
-                s_ln[warp][k] = d.log_norm;     // -log(1 + e^q)
-            }
-            a.thr[e * M + k] = word;
+        if (l != 0.0) {
+            const EntryDual d = entry_dual(l);
+            word = d.word;
+            tau_s = d.tau_s;
+            fs[ii] += d.alpha1;
+            ft[jj] += d.alpha2;
+            cst += d.log_norm;   // -log(1 + e^q)
         }
         a.tau[e * pad4(M) + k] = tau_s;
-        const uint32_t on = __ballot_sync(__activemask(), word != 0u);
-        if (lane == 0) s_on[warp][k >> 5] = on;
+        a.thr[e * M + k] = word;
     }
-    __syncwarp();
-    auto active = [&](int k) { return (s_on[warp][k >> 5] >> (k & 31)) & 1u; };
-    if (lane < L) {
-        const int x = lane;
-        double fs = pivot ? (double)w[x * L] - w00 : 0.0, ft = pivot ? (double)w[x] - w00 : 0.0;
-        if (pivot) {
-            if (x >= 1) {
-                for (int jj = 1; jj < L; ++jj) {          // row x: entries (x, jj)
-                    const int k = (x - 1) * (L - 1) + (jj - 1);
-                    if (active(k)) fs += s_a1[warp][k];
-                }
-                for (int ii = 1; ii < L; ++ii) {          // column x: entries (ii, x)
-                    const int k = (ii - 1) * (L - 1) + (x - 1);
-                    if (active(k)) ft += s_a2[warp][k];
-                }
-            }
-        } else if (active(x)) {
-            fs += s_a1[warp][x];
-            ft += s_a2[warp][x];
-        }
-        a.fold[(e * 2 + 0) * L + x] = fs;
-        a.fold[(e * 2 + 1) * L + x] = ft;
-        s_f[warp][0][x] = fs;
-        s_f[warp][1][x] = ft;
+    for (int k = M; k < pad4(M); ++k) a.tau[e * pad4(M) + k] = 0.0f;
+    for (int x = 0; x < L; ++x) {
+        a.fold[(e * 2 + 0) * L + x] = fs[x];
+        a.fold[(e * 2 + 1) * L + x] = ft[x];
     }
-    if (lane == 0) {
-        double cst = pivot ? w00 : 0.0;
-        for (int k = 0; k < M; ++k)
-            if (active(k)) cst += s_ln[warp][k];
-        a.cst[e] = cst;
-    }
-    __syncwarp();
-    if (a.sw_thr && (a.layout == MRF_LAYOUT_DIAG || L == 2) && lane < L) {
+    a.cst[e] = cst;
+    if (a.sw_thr && (a.layout == MRF_LAYOUT_DIAG || L == 2)) {
         // Swendsen-Wang tables (Section 4.3): the table as
         // c + f(a) + g(b) + l_a [a = b] -- diagonal tables: l_x = w(x,x), f = g = 0;
         // two labels: l = (w00 + w11 - w01 - w10) / 2 for both labels,
@@ -131,36 +98,38 @@ __global__ void __launch_bounds__(32 * kDecompWarps) k_decompose(DecompArgs a) {
         // T = ceil(p 2^23 - 1/2) (a draw U bonds iff U < T, i.e. (U + 1/2) / 2^23 < p),
         // and the bond's label weight log(e^{l_x} - 1) in fixed point (sw_fix);
         // l <= 0: no bond (T = 0) and the label is excluded when bonded (kSwNoLabel).
-        const int x = lane;
-        double l;
+        double lx[kMaxLabels];
         if (L == 2) {
-            l = 0.5 * ((double)w[0] + (double)w[3] - (double)w[1] - (double)w[2]);
+            const double k2 = 0.5 * ((double)w[0] + (double)w[3] - (double)w[1] - (double)w[2]);
+            lx[0] = lx[1] = k2;
             if (a.sw_fold) {
-                const double f = x == 0 ? 0.0 : (double)w[2] - (double)w[0] + l;
-                const double g = x == 0 ? 0.0 : (double)w[1] - (double)w[0] + l;
-                a.sw_fold[(e * 2 + 0) * 2 + x] = f;
-                a.sw_fold[(e * 2 + 1) * 2 + x] = g;
+                a.sw_fold[(e * 2 + 0) * 2 + 0] = 0.0;
+                a.sw_fold[(e * 2 + 0) * 2 + 1] = (double)w[2] - (double)w[0] + k2;
+                a.sw_fold[(e * 2 + 1) * 2 + 0] = 0.0;
+                a.sw_fold[(e * 2 + 1) * 2 + 1] = (double)w[1] - (double)w[0] + k2;
             }
         } else {
-            l = (double)w[x * L + x];
+            for (int x = 0; x < L; ++x) lx[x] = (double)w[x * L + x];
         }
-        uint32_t T = 0;
-        int64_t lw = kSwNoLabel;
-        if (l > 0.0) {
-            T = (uint32_t)ceil(-expm1(-l) * 8388608.0 - 0.5);
-            lw = sw_fix(log(expm1(l)));
+        for (int x = 0; x < L; ++x) {
+            const double l = lx[x];
+            uint32_t T = 0;
+            int64_t lw = kSwNoLabel;
+            if (l > 0.0) {
+                T = (uint32_t)ceil(-expm1(-l) * 8388608.0 - 0.5);
+                lw = sw_fix(log(expm1(l)));
+            }
+            a.sw_thr[e * L + x] = T;
+            a.sw_lw[e * L + x] = lw;
+            if (a.sw_ell) a.sw_ell[e * L + x] = l;
         }
-        a.sw_thr[e * L + x] = T;
-        a.sw_lw[e * L + x] = lw;
-        if (a.sw_ell) a.sw_ell[e * L + x] = l;
     }
     if (a.resid) {
         // exact pairwise potential in the folded representation (tree edges of
         // the blocked sweep): w(a,b) - fold_s(a) - fold_t(b)
-        for (int xy = lane; xy < L * L; xy += 32) {
-            const int x = xy / L, y = xy % L;
-            a.resid[(e * L + x) * L + y] = (float)((double)w[x * L + y] - s_f[warp][0][x] - s_f[warp][1][y]);
-        }
+        for (int x = 0; x < L; ++x)
+            for (int y = 0; y < L; ++y)
+                a.resid[(e * L + x) * L + y] = (float)((double)w[x * L + y] - fs[x] - ft[y]);
     }
 }
 
@@ -242,7 +211,7 @@ cudaError_t launch_count_offdiag(const float* pair, int64_t n_edges, int L, unsi
 }
 
 cudaError_t launch_decompose(const DecompArgs& a, cudaStream_t s) {
-    if (a.n > 0) k_decompose<<<(unsigned)((a.n + kDecompWarps - 1) / kDecompWarps), 32 * kDecompWarps, 0, s>>>(a);
+    if (a.n > 0) k_decompose<<<(unsigned)((a.n + 127) / 128), 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -200,9 +200,13 @@ SweepArgs make_args(const mrf_t* h) {
     return a;
 }
 
-// The plain sweep takes the edge-partial form for few chains and tables with
-// more than 16 entries (see k_dual_partial).
-bool use_partial(const mrf_t* h) { return h->C <= kPartialMaxChains && h->M > 16; }
+// The plain sweep takes the edge-partial form (k_edge_partial) for few chains
+// and large tables: there it replaces reading each incident edge's whole
+// weight row per (site, chain).  On 1-chain Erdos-Renyi classes it took the
+// L = 16 class (225 entries) from 18.5 to 12.9 ms per sweep, while L = 8 (49
+// entries, 4 words of weights per lane-pass) went from 2.7 to 4.8 ms: hence
+// at least kPartialMinEntries entries.
+bool use_partial(const mrf_t* h) { return h->C <= kPartialMaxChains && h->M >= kPartialMinEntries; }
 
 // Copy n elements of T from a host or device pointer to host.
 template <class T>
@@ -891,7 +895,8 @@ static mrf_status enqueue_sweep(mrf_t* h, int mode) {
     cudaStream_t s = h->stream;
     cudaError_t e = cudaSuccess;
     if (mode == MRF_MODE_PLAIN && use_partial(h)) {
-        e = timed(h, MRF_K_DUAL, [&] { return launch_sweep_partial(a, h->layout, 0, s); });
+        e = timed(h, MRF_K_DUAL, [&] { return launch_dual(a, h->layout, s); });
+        if (e == cudaSuccess) e = timed(h, MRF_K_PARTIAL, [&] { return launch_sweep_partial(a, h->layout, 0, s); });
         if (e == cudaSuccess) e = timed(h, MRF_K_PRIMAL, [&] { return launch_sweep_partial(a, h->layout, 1, s); });
     } else if (mode == MRF_MODE_PLAIN) {
         e = timed(h, MRF_K_DUAL, [&] { return launch_dual(a, h->layout, s); });

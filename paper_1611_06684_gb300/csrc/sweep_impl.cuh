@@ -744,89 +744,42 @@ __global__ void __launch_bounds__(256) k_primal_cta(SweepArgs a, int CG) {
 // ---------------------------------------------------------------------------- few chains, many entries
 
 // Plain sweep for few chains (C <= 4) and tables with more than 16 entries,
-// where a thread per (edge, chain) or (site, chain) would read every entry's
-// weight row on its own.  The dual step takes one warp per edge; lane b holds
-// the entries k = 32 g + b: their packed threshold words and signed weights
-// are read once per edge (coalesced) and kept for all chains.  Per chain: the
-// prefix draws of the edge's groups (its Philox calls shared out over the
-// lanes, the plane words passed by shuffles), each lane's dual bits (a prefix
-// tie decided by the lane with the low-16-bit draw), the bit words, and the
-// edge's two partial fields -- over the set bits, the row sums of the signed
-// weights (source side, beta1) and the column sums of their magnitudes
-// (destination side, beta2), each in entry order.  The primal step then adds
-// the partial fields of a site's incidences in incidence order (two-sum flush
-// every 32, as k_primal) and draws the label.
+// where a thread per (site, chain) would read every incident entry's weight
+// row on its own.  After the dual step (k_dual), one warp per edge reads the
+// edge's signed weights once (lane b: entries k = 32 g + b, coalesced) and,
+// per chain, its dual bit words, and writes the edge's two partial fields:
+// over the set bits, the row sums of the signed weights (source side, beta1)
+// and the column sums of their magnitudes (destination side, beta2), each in
+// entry order.  The primal step (k_primal_partial) then adds the partial
+// fields of a site's incidences in incidence order (two-sum flush every 32,
+// as k_primal) and draws the label.
 template <int L, int LAYOUT>
-__global__ void __launch_bounds__(256) k_dual_partial(SweepArgs a) {
+__global__ void __launch_bounds__(256) k_edge_partial(SweepArgs a) {
     using E = Ent<L, LAYOUT>;
     constexpr int M = E::M, W = E::W, MP = E::MP;
-    constexpr uint32_t FULL = 0xFFFFFFFFu;
     static_assert(M > 16 && L <= 16, "edge-partial form: more than 16 entries, at most 16 labels");
     __shared__ float s_t[8][W * 32];                       // weights of the set bits, per warp
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t e = blockIdx.x * 8ll + warp;
-    if (e >= a.E) return;                                  // whole warps
+    if (e >= a.E || a.src[e] < 0) return;                  // whole warps; a free slot has no incidences
     const int C = a.C;
-    const int s = a.src[e];
-    if (s < 0) {                                           // free slot: no bits
-        for (int q = lane; q < C * W; q += 32) a.theta[e * C * W + q] = 0u;
-        return;
-    }
-    const int t = a.dst[e];
-    const uint32_t sweep = (uint32_t)a.ctl->sweep;
-    const uint8_t* xin = a.x + (size_t)(sweep & 1) * a.N * a.C;
-    uint32_t wd[W];
     float tv[W];
 #pragma unroll
     for (int g = 0; g < W; ++g) {
         const int k = 32 * g + lane;
-        wd[g] = k < M ? __ldg(a.thr + e * M + k) : 0u;
         tv[g] = k < M ? __ldg(a.tau + e * MP + k) : 0.0f;
     }
     for (int c = 0; c < C; ++c) {
-        const int xs = xin[(int64_t)s * C + c], xt = xin[(int64_t)t * C + c];
-        // lane q < 2W: call q (group q / 2, half q % 2) of the edge's prefix draws
-        uint4 r = make_uint4(0u, 0u, 0u, 0u);
-        if (lane < 2 * W) r = draw_rk((uint32_t)e, sweep, (uint32_t)c, PH_DUAL, (uint32_t)lane, a.rk);
-        uint32_t bw[W];
+        const uint32_t* th = a.theta + (e * C + c) * W;
 #pragma unroll
-        for (int g = 0; g < W; ++g) {
-            const uint32_t P[8] = {__shfl_sync(FULL, r.x, 2 * g), __shfl_sync(FULL, r.y, 2 * g),
-                                   __shfl_sync(FULL, r.z, 2 * g), __shfl_sync(FULL, r.w, 2 * g),
-                                   __shfl_sync(FULL, r.x, 2 * g + 1), __shfl_sync(FULL, r.y, 2 * g + 1),
-                                   __shfl_sync(FULL, r.z, 2 * g + 1), __shfl_sync(FULL, r.w, 2 * g + 1)};
-            uint32_t u8 = 0;
-#pragma unroll
-            for (int p = 0; p < 8; ++p) u8 |= ((P[p] >> lane) & 1u) << (7 - p);
-            const int k = 32 * g + lane;
-            bool bit = false;
-            if (k < M && wd[g]) {
-                const int y = xs == E::i(k), z = xt == E::j(k);
-                const int level = (wd[g] >> 31) ? 1 + z - y : y + z;
-                const uint32_t T = level == 1 ? (1u << 23) : level_threshold(wd[g], level == 2);
-                const uint32_t T8 = threshold_prefix(T);
-                if (u8 < T8) {
-                    bit = true;
-                } else if (u8 == T8) {
-                    const uint32_t rem = T - (T8 << 16);
-                    bit = rem && dual_low16((uint32_t)e, sweep, (uint32_t)c, k, a.rk) < rem;
-                }
-            }
-            bw[g] = __ballot_sync(FULL, bit);
-            s_t[warp][32 * g + lane] = bit ? tv[g] : 0.0f;
-        }
-        if (lane < W) {
-            uint32_t v = bw[0];
-#pragma unroll
-            for (int g = 1; g < W; ++g) v = lane == g ? bw[g] : v;
-            a.theta[(e * C + c) * W + lane] = v;
-        }
+        for (int g = 0; g < W; ++g) s_t[warp][32 * g + lane] = ((__ldcs(th + g) >> lane) & 1u) ? tv[g] : 0.0f;
         __syncwarp();
         float* pe = a.part + ((e * C + c) * 2) * L;
         if (lane < L) {                                    // row `lane`: source side
             float sum = 0.0f;
             if (LAYOUT == MRF_LAYOUT_PIVOT) {
                 if (lane >= 1)
+#pragma unroll
                     for (int jj = 1; jj < L; ++jj) sum += s_t[warp][(lane - 1) * (L - 1) + (jj - 1)];
             } else {
                 sum = s_t[warp][lane];
@@ -837,6 +790,7 @@ __global__ void __launch_bounds__(256) k_dual_partial(SweepArgs a) {
             float sum = 0.0f;
             if (LAYOUT == MRF_LAYOUT_PIVOT) {
                 if (x >= 1)
+#pragma unroll
                     for (int ii = 1; ii < L; ++ii) sum += fabsf(s_t[warp][(ii - 1) * (L - 1) + (x - 1)]);
             } else {
                 sum = fabsf(s_t[warp][x]);
@@ -904,7 +858,7 @@ template <int L, int LAYOUT>
 cudaError_t run_sweep_partial(const SweepArgs& a, int step, cudaStream_t s) {
     if constexpr (Ent<L, LAYOUT>::M > 16) {
         const int64_t n = (int64_t)a.N * a.C;
-        if (step == 0 && a.E > 0) k_dual_partial<L, LAYOUT><<<(unsigned)((a.E + 7) / 8), 256, 0, s>>>(a);
+        if (step == 0 && a.E > 0) k_edge_partial<L, LAYOUT><<<(unsigned)((a.E + 7) / 8), 256, 0, s>>>(a);
         if (step == 1 && n > 0) k_primal_partial<L><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a);
         return cudaGetLastError();
     } else {

@@ -26,10 +26,10 @@ Q_COUNT, Q_GRAPH, Q_VERTEX, Q_LOOP, Q_SLOT, Q_DUP, Q_NONFINITE, Q_OFFDIAG, Q_PAI
     1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024
 LAYOUT_PIVOT, LAYOUT_DIAG = 0, 1
 (K_DUAL, K_PRIMAL, K_FUSED, K_POTENTIAL, K_FFBS, K_ACCUMULATE, K_FEATURES, K_MLP, K_MH, K_SMALL,
- K_SW_BOND, K_SW_FLATTEN, K_SW_DRAW, K_SW_SMALL, K_COUNT) = range(15)
+ K_SW_BOND, K_SW_FLATTEN, K_SW_DRAW, K_SW_SMALL, K_PARTIAL, K_COUNT) = range(16)
 KERNEL_NAMES = ["k_dual", "k_primal", "k_primal<fused>", "k_potential", "k_ffbs", "k_accumulate",
                 "k_learned_features", "k_mlp", "k_learned_mh", "k_sweep_small",
-                "k_sw_bond", "k_sw_flatten", "k_sw_draw", "k_sw_small"]
+                "k_sw_bond", "k_sw_flatten", "k_sw_draw", "k_sw_small", "k_edge_partial"]
 
 
 class mrf_options(ct.Structure):
