@@ -1273,11 +1273,20 @@ def run_learned_workload(args):
     trace = h.learned_train(2000, 1024, 1e-3, seed=0)
     torch.cuda.synchronize()
     train_s = time.time() - t1
-    ms_learned = _timed(stream, lambda: h.sweep(10, M.MODE_LEARNED)) / 10
+    h.sweep(3, M.MODE_LEARNED)                                   # warm-up (graph capture)
+    torch.cuda.synchronize()
+    clk_path = os.path.join(tempfile.gettempdir(), "bench_clocks_learned.csv")
+    clk = clocks_start(clk_path)
+    time.sleep(0.3)
+    n_timed = max(10, args.steps)
+    ms_learned = _timed(stream, lambda: h.sweep(n_timed, M.MODE_LEARNED)) / n_timed
+    clocks = clocks_stop(clk, clk_path, torch.cuda.current_device())
     h.set_kernel_timing(True)
     h.kernel_times()
     h.sweep(5, M.MODE_LEARNED)
-    kt_learned = {k: v[0] / v[1] for k, v in h.kernel_times().items()}
+    kt_raw = h.kernel_times()
+    kt_learned = {k: v[0] / v[1] for k, v in kt_raw.items()}
+    launches_per_sweep = sum(v[1] for v in kt_raw.values()) / 5 + 1          # + k_advance (not timed)
     h.sweep(5, M.MODE_PLAIN)
     kt_plain = {k: v[0] / v[1] for k, v in h.kernel_times().items()}
     h.set_kernel_timing(False)
@@ -1320,7 +1329,66 @@ def run_learned_workload(args):
         out[name] = {"ms_per_sweep": ms, "ess_label0_fraction": ess_a, "ess_pair_energy": ess_b,
                      "ess_per_s_label0": ess_a / (T * ms / 1e3), "ess_per_s_pair_energy": ess_b / (T * ms / 1e3),
                      "tv_vs_reference": tv_mean(est, ref), "sweeps": T}
-    return {"metric": "ESS/s", "workload": f"ba_potts_N{N}_L4_C32_blocks16", "blocks": nb,
+    # end to end through the C ABI: labels from pinned host memory, one learned sweep, labels back
+    x_host = torch.empty((C, N), dtype=torch.uint8).pin_memory()
+    h.get_labels_into(x_host)
+    k_e2e = 10
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        h.set_labels(x_host)
+        h.sweep(1, M.MODE_LEARNED)
+        h.get_labels_into(x_host)
+    torch.cuda.synchronize()
+    e2e = {"value": N * C * k_e2e / (time.perf_counter() - t0), "unit": METRIC, "h2d_bytes_per_step": N * C,
+           "d2h_bytes_per_step": N * C, "steps": k_e2e,
+           "api": "mrf_set_labels(host) + mrf_sweep(1, MRF_MODE_LEARNED) + mrf_get_labels(host), pinned buffers"}
+    dom = max(kt_learned, key=kt_learned.get)
+    roof = None
+    if ms_mlp == ms_mlp:
+        roof = {"bound": "tensor", "achieved": mlp_flop / (ms_mlp / 1e3) / 1e12, "peak": peaks["bf16_tflops"],
+                "unit": "TFLOP/s", "frac": mlp_flop / (ms_mlp / 1e3) / 1e12 / peaks["bf16_tflops"], "traffic": None,
+                "kernel": "k_mlp (fused tcgen05 MLP of the proposal)", "dominant_kernel_of_the_sweep": dom,
+                "flop_per_launch": mlp_flop, "peak_source": f"MEASURED_PEAKS.json bf16_tflops ({peak_src})"}
+    cpu = None
+    if not args.no_cpu:
+        from oracle import cpu_sweep, decompose as dc, philox as ph, sampler
+        cores = len(os.sched_getaffinity(0))
+        sm = wl.ba_potts(50000, m=5, L=4, seed=0)
+        cs = cpu_sweep.CpuSweep(dc.decompose(sm), C, args.seed, threads=cores)
+        xs = cs.sweep(ph.init_labels(sm.n_vars, 4, C, args.seed).astype(np.uint8), 0)
+        el, S = 0.0, 0
+        while el < 10.0:
+            t0 = time.perf_counter(); xs = cs.sweep(xs, S + 1); el += time.perf_counter() - t0; S += 1
+        tiny = wl.ba_potts(2000, m=5, L=4, seed=0)
+        dt_ = dc.decompose(tiny)
+        xo = ph.init_labels(tiny.n_vars, 4, 2, args.seed)
+        el1, S1 = 0.0, 0
+        while el1 < 10.0:
+            t0 = time.perf_counter(); xo = sampler.sweep(dt_, xo, S1, args.seed)["x"]; el1 += time.perf_counter() - t0; S1 += 1
+        cpu = {"value": sm.n_vars * C * S / el, "unit": METRIC, "cores": cores,
+               "kind": "oracle (float32 OpenMP statement of the plain sweep, oracle/cpu_sweep.c)",
+               "sample": f"{C} chains x {S} plain sweeps of a BA graph with N = 50,000 (same m, L and distributions)",
+               "seconds": el, "host_cores_available": cores,
+               "single_core_oracle": {"value": tiny.n_vars * 2 * S1 / el1, "unit": METRIC, "cores": 1,
+                                      "kind": "oracle (float64 numpy)",
+                                      "sample": f"2 chains x {S1} plain sweeps of a BA graph with N = 2,000",
+                                      "seconds": el1},
+               "note": "the learned proposal has no CPU statement; the baseline is the plain sweep"}
+    contract = {"metric": METRIC, "value": N * C / (ms_learned / 1e3), "unit": METRIC, "n_gpus": 1,
+                "steps": n_timed, "warmup": 3, "ms_per_step": ms_learned, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16 MLP (fp32 accumulation) + u32/f32 sweep", "data": "synthetic (seeded generators)",
+                "config": {"workload": f"ba_potts_N{N}_L4_C32_blocks16",
+                           "description": "Barabasi-Albert m=5, L=4, w_e(a,b) = beta_e [a=b], beta_e ~ U[0, 0.8], "
+                                          "unaries N(0,1), 32 chains; learned MH proposal over 16-site BFS blocks "
+                                          "(hidden 256 x 2, bf16 weights, trained on 1e5 harvested samples)",
+                           "step": "one learned sweep (dual bits of the other edges, block potentials, features, "
+                                   "fused MLP, MH accept) replayed as a CUDA graph",
+                           "l2": "inputs larger than L2; no flush needed", "parallelism": "one GPU"},
+                "roofline": roof, "gpu_launches": int(round(launches_per_sweep * n_timed)), "clocks": clocks,
+                "e2e": e2e, "cpu_baseline": cpu}
+    return {**contract, "ess_metric": "ESS/s", "workload": f"ba_potts_N{N}_L4_C32_blocks16", "blocks": nb,
             "generation_s": gen_s, "plain": {"ms_per_sweep": ms_plain, "site_updates_per_s": N * C / (ms_plain / 1e3)},
             "learned": {"ms_per_sweep": ms_learned, "site_updates_per_s": N * C / (ms_learned / 1e3),
                         "acceptance_untrained": acc_untrained, "acceptance_trained": acc_trained,

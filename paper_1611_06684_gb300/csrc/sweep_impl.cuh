@@ -700,18 +700,29 @@ __global__ void __launch_bounds__(256) k_primal_cta(SweepArgs a, int CG) {
     if (active) {
         const int64_t p0 = a.inc_ptr[v], p1 = a.inc_ptr[v + 1];
         int chunk = 0;
-        for (int64_t p = p0 + slice; p < p1; p += S) {
-            const int2 ic = __ldg(&a.inc[p]);
-            const int64_t e = ic.x >> 1;
-            uint32_t bits[E::W];
-            const uint32_t* th = a.theta + (e * a.C + c) * E::W;
+        // B incidences of the slice per iteration, their records and theta words
+        // loaded before any is added (same order of additions)
+        constexpr int B = E::W <= 2 ? 4 : 2;
+        for (int64_t p = p0 + slice; p < p1; p += (int64_t)B * S) {
+            int2 ic[B];
+            uint32_t bits[B][E::W];
 #pragma unroll
-            for (int w = 0; w < E::W; ++w) bits[w] = __ldcs(th + w);
-            add_side<L, LAYOUT>(bits, a.tau + e * E::MP, ic.x & 1, acc);
-            if (++chunk == 32) {
+            for (int u = 0; u < B; ++u) ic[u] = p + (int64_t)u * S < p1 ? __ldg(&a.inc[p + (int64_t)u * S]) : make_int2(-1, 0);
 #pragma unroll
-                for (int x = 0; x < L; ++x) { two_sum_add(hi[x], lo[x], acc[x]); acc[x] = 0.0f; }
-                chunk = 0;
+            for (int u = 0; u < B; ++u) {
+                const uint32_t* th = a.theta + ((int64_t)(ic[u].x >> 1) * a.C + c) * E::W;
+#pragma unroll
+                for (int w = 0; w < E::W; ++w) bits[u][w] = ic[u].x >= 0 ? __ldcs(th + w) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                if (ic[u].x < 0) continue;
+                add_side<L, LAYOUT>(bits[u], a.tau + (int64_t)(ic[u].x >> 1) * E::MP, ic[u].x & 1, acc);
+                if (++chunk == 32) {
+#pragma unroll
+                    for (int x = 0; x < L; ++x) { two_sum_add(hi[x], lo[x], acc[x]); acc[x] = 0.0f; }
+                    chunk = 0;
+                }
             }
         }
 #pragma unroll
@@ -802,7 +813,7 @@ __global__ void __launch_bounds__(256) k_edge_partial(SweepArgs a) {
 }
 
 template <int L>
-__global__ void __launch_bounds__(256) k_primal_partial(SweepArgs a) {
+__global__ void __launch_bounds__(256, 3) k_primal_partial(SweepArgs a) {
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;     // N * C < 2^32 (checked by the host)
     if (g >= (uint64_t)a.N * a.C) return;
     const uint32_t v = a.fdC.div(g), c = g - v * (uint32_t)a.C;
