@@ -641,7 +641,8 @@ def run_batch_workload(args):
     from paper_1611_06684_gb300 import build as B, mrf as M, workloads as wl
     B.build()
     n_graphs = args.scale or 2000
-    specs = wl.er_batch_specs(n_graphs, seed=0)
+    labels = tuple(int(v) for v in args.er_labels.split(","))
+    specs = wl.er_batch_specs(n_graphs, labels=labels, seed=0)
     t0 = time.time()
     models = [wl.er_graph(sp) for sp in specs]
     gen_s = time.time() - t0
@@ -757,9 +758,9 @@ def run_batch_workload(args):
             "vs_baseline": None,
             "dtype": "u32+f32 (dual step: u32 Philox and threshold compare; primal step: f32 with two-sum accumulation)",
             "data": "synthetic (seeded generators)",
-            "config": {"workload": f"er_batch_{n_graphs}",
+            "config": {"workload": f"er_batch_{n_graphs}" + ("" if labels == (2, 4, 8, 16) else f"_L{args.er_labels}"),
                        "description": f"{n_graphs} Erdos-Renyi graphs, N ~ logU[100, 50000], mean degree U[3, 20], "
-                                      "L in {2,4,8,16}, tables exp(U[-0.5,0.5]), unaries N(0,1), 1 chain each",
+                                      f"L in {set(labels)}, tables exp(U[-0.5,0.5]), unaries N(0,1), 1 chain each",
                        "n_vars": N, "n_edges": E, "graphs": n_graphs, "chains": C,
                        "step": "one round: edit (remove ceil(1%) of every graph's edges, add as many) + 10 sweeps, "
                                "one CUDA graph replay",
@@ -1299,20 +1300,22 @@ def run_learned_workload(args):
     h.sweep(4, M.MODE_LEARNED)
     p1, a1 = h.learned_stats()
     acc_trained = (a1 - a0) / max(1, p1 - p0)
+    if args.ess_sweeps <= 0:
+        args.ref_sweeps = 0
     # reference marginals: long plain run
     x_start = h.get_labels()
     t_start = h.info().sweep_index
     h.reset_marginals(0)
     h.sweep(args.ref_sweeps, M.MODE_PLAIN)
-    ref, _ = h.marginals()
+    ref = h.marginals()[0] if args.ref_sweeps > 0 else None
     rng = np.random.default_rng(0)
     subset = np.sort(rng.choice(N, size=4096, replace=False))
     esub = np.sort(rng.choice(model.n_edges, size=50000, replace=False))
     es, et, ew = model.src[esub], model.dst[esub], model.pair[esub].astype(np.float64)
     T = args.ess_sweeps
     out = {}
-    for name, pattern in (("plain", [M.MODE_PLAIN]), ("learned", [M.MODE_LEARNED]),
-                          ("learned+plain", [M.MODE_LEARNED, M.MODE_PLAIN])):
+    for name, pattern in ((("plain", [M.MODE_PLAIN]), ("learned", [M.MODE_LEARNED]),
+                           ("learned+plain", [M.MODE_LEARNED, M.MODE_PLAIN])) if T > 0 else ()):
         h.set_labels(x_start)
         h.set_sweep_index(t_start + 1000003)
         h.reset_marginals(0)
@@ -1432,6 +1435,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--er-labels", default="2,4,8,16", help="label counts of the batched workload's graphs")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads' lines (fully connected, batched, learned) of the default run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.ferro_beta:
@@ -1447,8 +1453,35 @@ def main():
         out = run_reference(args, ws, rank)
     else:
         out = run_ours(args, ws, rank, local)
+    if (args.impl == "ours" and ws == 1 and rank == 0 and out is not None and not args.no_configs
+            and args.workload == "potts3d" and not args.scale):
+        out["other_configs"] = other_configs(args)
     if rank == 0 and out is not None:
         print(json.dumps(out))
+
+
+def other_configs(args):
+    """The other workloads at their stated sizes, each as its own standard line
+    from a child process (its own device memory): fully connected N = 4096,
+    the 2,000-graph batched dynamic workload, the learned proposal on BA 10^6."""
+    import torch
+    torch.cuda.empty_cache()
+    runs = {"dense4096": ["--workload", "dense4096", "--steps", "50", "--warmup", "3", "--no-variants"],
+            "er_batch_2000": ["--workload", "er_batch", "--steps", "3", "--warmup", "3"],
+            "ba_learned_1e6": ["--workload", "ba_learned", "--steps", "20", "--warmup", "3", "--ess-sweeps", "0"]}
+    out = {}
+    for name, extra in runs.items():
+        cmd = [sys.executable, os.path.abspath(__file__)] + extra + ["--no-configs", "--seed", str(args.seed)]
+        if args.no_cpu:
+            cmd.append("--no-cpu")
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=480)
+            lines = [l for l in r.stdout.strip().splitlines() if l.startswith("{")]
+            out[name] = json.loads(lines[-1]) if r.returncode == 0 and lines else \
+                {"unavailable": f"exit {r.returncode}: {r.stderr.strip()[-300:]}"}
+        except subprocess.TimeoutExpired:
+            out[name] = {"unavailable": "timed out after 480 s"}
+    return out
 
 
 if __name__ == "__main__":
