@@ -192,14 +192,22 @@ def intra_edge_lists(model, block_of_site, n_blocks):
 
 
 def learned_sweep(model, dec: Decomposition, x, sweep_index, seed, block_of_site, params, edge_ids=None,
-                  bf16_activations=False):
+                  bf16_activations=False, site_ids=None, block_ids=None, blocks=None):
     """One learned sweep from labels x [C][N]; returns a dict with the new labels.
     bf16_activations: evaluate the proposal with inputs and hidden activations
-    rounded to bfloat16 (the device's storage precision)."""
+    rounded to bfloat16 (the device's storage precision).
+    For a sub-model cut out of a larger one: edge_ids, site_ids and block_ids
+    map its edges, sites and blocks to the larger model's (the indices of the
+    draw contract), and blocks (default all) lists the blocks to update; the
+    MLP then runs on those blocks' rows only (z has nb * C rows, zero
+    elsewhere)."""
     C, N = x.shape
     L = model.n_labels
     members = block_members(block_of_site)
     nb = len(members)
+    sid = np.arange(N) if site_ids is None else np.asarray(site_ids)
+    bid = np.arange(nb) if block_ids is None else np.asarray(block_ids)
+    todo = list(range(nb)) if blocks is None else [int(b) for b in blocks]
     intra = intra_mask(dec.src, dec.dst, block_of_site)
     # cut duals | x
     p = dual_probs(dec, x)
@@ -209,7 +217,10 @@ def learned_sweep(model, dec: Decomposition, x, sweep_index, seed, block_of_site
     phi = node_potentials(model, dec, intra, theta)               # target field
     cf = coupling_features(model, block_of_site, members)
     X = features(phi_f, members, cf, L)
-    z = mlp_forward_bf16(params, X) if bf16_activations else mlp_forward(params, X)[0]
+    rows_todo = (np.asarray(todo, np.int64)[:, None] * C + np.arange(C)[None, :]).ravel()
+    zt = mlp_forward_bf16(params, X[rows_todo]) if bf16_activations else mlp_forward(params, X[rows_todo])[0]
+    z = np.zeros((nb * C, zt.shape[1]))
+    z[rows_todo] = zt
     lz = log_softmax(z.reshape(nb * C, BLOCK, L))                 # rows b*C + c
     w = np.asarray(model.pair, np.float64)
     lists = intra_edge_lists(model, block_of_site, nb)
@@ -218,10 +229,11 @@ def learned_sweep(model, dec: Decomposition, x, sweep_index, seed, block_of_site
     log_alpha = np.zeros((nb, C))
     u_acc_all = np.zeros((nb, C))
     prop_cdf = {}
-    for b, m in enumerate(members):
+    for b in todo:
+        m = members[b]
         rows = b * C + np.arange(C)
         lzb = lz[rows][:, :len(m), :]                             # [C][n_b][L]
-        u_prop = ph.site_uniform(m[None, :], np.arange(C)[:, None], sweep_index, seed, ph.PH_PROPOSAL)
+        u_prop = ph.site_uniform(sid[m][None, :], np.arange(C)[:, None], sweep_index, seed, ph.PH_PROPOSAL)
         xp, cdf = inverse_cdf(lzb, u_prop)                        # [C][n_b]
         prop_cdf[b] = (u_prop, cdf)
         cur = x[:, m]
@@ -231,7 +243,7 @@ def learned_sweep(model, dec: Decomposition, x, sweep_index, seed, block_of_site
         lp_cur = block_log_target(phi, w, members, lists, x, b)
         lp_new = block_log_target(phi, w, members, lists, xprop, b)
         la = (lp_new - lp_cur) + (lq_cur - lq_new)
-        u_acc = ph.site_uniform(np.full((C, 1), b), np.arange(C)[:, None], sweep_index, seed, ph.PH_ACCEPT)[:, 0]
+        u_acc = ph.site_uniform(np.full((C, 1), bid[b]), np.arange(C)[:, None], sweep_index, seed, ph.PH_ACCEPT)[:, 0]
         acc = u_acc < np.exp(np.minimum(0.0, la))
         x_new[np.ix_(np.nonzero(acc)[0], m)] = xp[acc]
         accepted[b] = acc; log_alpha[b] = la; u_acc_all[b] = u_acc

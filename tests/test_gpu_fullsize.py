@@ -175,3 +175,74 @@ def _hub_parity(model, sites, C=32, seed=0):
     bad = (x1[:, sites] != ref["x"][:, pos]) & ~ex
     print("hubs", len(sites), "edges", len(eids), "logp max rel", float(err.max()), "exempt", int(ex.sum()))
     assert not bad.any()
+
+
+def test_ba_million_learned_sweep_sampled_blocks_match_oracle():
+    """The learned sweep at the bench's configuration (BA 10^6, L = 4, 32
+    chains, 16-site BFS blocks, hidden 256 on the tensor cores, graph replay)
+    against the oracle on sampled whole blocks: 150 random blocks and the
+    blocks of the 8 largest hubs, each on the sub-model of its incident edges.
+    Compared: the cut duals of every incident edge (bit for bit away from
+    boundary draws), the logits of every (block, chain) row (bf16 activations:
+    rows where a hidden value sat on a bf16 rounding boundary move by a few
+    1e-2 and are skipped, as in tests/test_gpu_learned.py), and the new labels
+    of the other rows away from CDF and acceptance boundaries."""
+    import ctypes as ct
+    from oracle import learned as ln
+    from paper_1611_06684_gb300 import mrf as M
+    from tests.learned_helpers import learned_sub_model
+    from tests.test_gpu_learned import _flat, _params
+    model = wl.ba_potts(1_000_000, m=5, L=4, seed=0)
+    bos = wl.bfs_blocks(model, 16, seed=0)
+    C, seed, hidden = 32, 3, 256
+    h = M.MRF(model.n_vars, 4, C, seed=seed, exact_edges=True, use_graphs=True)
+    h.set_factors(model.unary, model.src, model.dst, model.pair)
+    h.learned_setup(bos, hidden=hidden, seed=1)
+    params = _params(4, hidden, 5)
+    h.learned_set_params(_flat(params))
+    h.sweep(3, M.MODE_PLAIN)
+    t = h.info().sweep_index
+    x0 = h.get_labels().astype(np.int64)
+    h.sweep(1, M.MODE_LEARNED)
+    x1 = h.get_labels()
+    nb = int(bos.max()) + 1
+    z = np.zeros((nb * C, 16 * 4), np.float32)
+    assert h.lib.mrf_learned_debug(h.h, None, z.ctypes.data) == M.MRF_OK
+    rng = np.random.default_rng(17)
+    deg = np.bincount(np.concatenate([model.src, model.dst]), minlength=model.n_vars)
+    blocks = np.unique(np.concatenate([rng.choice(nb, 150, replace=False), bos[np.argsort(deg)[-8:]]]))
+    sub, local, eids, sbos, bids, k = learned_sub_model(model, bos, blocks)
+    th = M.unpack_theta(h.debug_theta()[eids], h.info().n_entries)
+    h.close()
+    from oracle import decompose as dc
+    dec = dc.decompose(sub)
+    ref = ln.learned_sweep(sub, dec, x0[:, local], t, seed, sbos, params, edge_ids=eids, site_ids=local,
+                           block_ids=bids, blocks=range(k), bf16_activations=True)
+    dual_b = (np.abs(ref["u_dual"] - ref["p_dual"]) < BOUNDARY_EPS) & dec.active[None]
+    assert not ((th != ref["theta"]) & ~dual_b).any()
+    # a boundary dual draw on an incident edge may flip a block's field: that (block, chain) is exempt
+    exempt = np.zeros((k, C), bool)
+    for c_, e_ in zip(*np.nonzero(dual_b.any(axis=2))):
+        for v in (sub.src[e_], sub.dst[e_]):
+            if sbos[v] < k:
+                exempt[sbos[v], c_] = True
+    compared = moved = 0
+    for i, b in enumerate(blocks):
+        m = ref["members"][i]
+        zg, zr = z[b * C:(b + 1) * C], ref["z"][i * C:(i + 1) * C]
+        errz = np.abs(zg - zr) / np.maximum(1.0, np.abs(zr))
+        assert errz[~exempt[i]].max(initial=0.0) < 5e-2, (b, errz.max())
+        u_prop, cdf = ref["prop"][i]
+        for c in range(C):
+            if exempt[i, c]:
+                continue
+            if errz[c].max() > 1e-4:
+                moved += 1
+                continue
+            if np.any(np.abs(u_prop[c][:, None] - cdf[c]) < 1e-3) or \
+                    abs(ref["u_acc"][i, c] - np.exp(min(0.0, ref["log_alpha"][i, c]))) < 1e-3:
+                continue
+            compared += 1
+            assert np.array_equal(x1[c, local[m]], ref["x"][c, m]), (b, c)
+    print("blocks", len(blocks), "rows compared", compared, "moved", moved, "edges", len(eids))
+    assert compared > 0.8 * len(blocks) * C and moved < 0.02 * len(blocks) * C

@@ -148,3 +148,30 @@ def test_planted_acceptance_without_proposal_ratio_breaks_stationarity():
     _, p, _ = brute.exact_distribution(model)
     np.testing.assert_allclose(K.sum(axis=1), 1.0, atol=1e-12)
     assert np.abs(p @ K - p).max() > 1e-4
+
+
+def test_sub_model_of_whole_blocks_reproduces_the_full_sweep():
+    """The learned sweep of a few whole blocks on their sub-model (incident
+    edges and far-end sites, full-model indices for the draws) equals the full
+    model's sweep on those blocks: cut duals, logits and new labels."""
+    from tests.learned_helpers import learned_sub_model
+    model = wl.ba_potts(500, m=4, L=3, seed=9)
+    dec = dc.decompose(model)
+    bos = wl.bfs_blocks(model, 16, seed=2)
+    C, seed, t = 3, 7, 5
+    params = ln.init_params(3, hidden=64, seed=4)
+    x0 = np.random.default_rng(1).integers(0, 3, size=(C, model.n_vars))
+    full = ln.learned_sweep(model, dec, x0, t, seed, bos, params)
+    blocks = np.array([0, 3, int(bos.max()), int(bos[np.argmax(np.bincount(np.concatenate([model.src, model.dst])))])])
+    blocks = np.unique(blocks)
+    sub, local, eids, sbos, bids, k = learned_sub_model(model, bos, blocks)
+    ref = ln.learned_sweep(sub, dc.decompose(sub), x0[:, local], t, seed, sbos, params, edge_ids=eids,
+                           site_ids=local, block_ids=bids, blocks=range(k))
+    assert np.array_equal(ref["theta"], full["theta"][:, eids])
+    for i, b in enumerate(blocks):
+        rows_s, rows_f = i * C + np.arange(C), b * C + np.arange(C)
+        assert np.allclose(ref["z"][rows_s], full["z"][rows_f], rtol=1e-12, atol=1e-12)
+        m_full = full["members"][b]
+        assert np.array_equal(local[ref["members"][i]], m_full)
+        assert np.array_equal(ref["x"][:, ref["members"][i]], full["x"][:, m_full])
+        assert np.array_equal(ref["accepted"][i], full["accepted"][b])
