@@ -403,7 +403,7 @@ def run_ours(args, ws, rank, local):
 
     out = None
     if rank == 0:
-        cpu = None if (ws > 1 or args.no_cpu) else cpu_baseline(args)
+        cpu = None if (ws > 1 or args.no_cpu) else cpu_baseline(args, args.cpu_seconds)
         out = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -752,7 +752,7 @@ def run_batch_workload(args):
                                      "(16 B) per edge, unaries (4 B per label) and labels in and out per site"}
     K = b.n_classes()
     launches_per_round = 4 + 15 * K + 1 + sweeps_per_round * 4 * K
-    cpu = None if args.no_cpu else batch_cpu_baseline(models, args.seed)
+    cpu = None if args.no_cpu else batch_cpu_baseline(models, args.seed, args.cpu_seconds)
     return {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_round, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
@@ -1361,13 +1361,13 @@ def run_learned_workload(args):
         cs = cpu_sweep.CpuSweep(dc.decompose(sm), C, args.seed, threads=cores)
         xs = cs.sweep(ph.init_labels(sm.n_vars, 4, C, args.seed).astype(np.uint8), 0)
         el, S = 0.0, 0
-        while el < 10.0:
+        while el < args.cpu_seconds:
             t0 = time.perf_counter(); xs = cs.sweep(xs, S + 1); el += time.perf_counter() - t0; S += 1
         tiny = wl.ba_potts(2000, m=5, L=4, seed=0)
         dt_ = dc.decompose(tiny)
         xo = ph.init_labels(tiny.n_vars, 4, 2, args.seed)
         el1, S1 = 0.0, 0
-        while el1 < 10.0:
+        while el1 < args.cpu_seconds:
             t0 = time.perf_counter(); xo = sampler.sweep(dt_, xo, S1, args.seed)["x"]; el1 += time.perf_counter() - t0; S1 += 1
         cpu = {"value": sm.n_vars * C * S / el, "unit": METRIC, "cores": cores,
                "kind": "oracle (float32 OpenMP statement of the plain sweep, oracle/cpu_sweep.c)",
@@ -1436,6 +1436,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--er-labels", default="2,4,8,16", help="label counts of the batched workload's graphs")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="time budget of each CPU baseline sample")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workloads' lines (fully connected, batched, learned) of the default run")
     args = ap.parse_args()
@@ -1471,7 +1472,8 @@ def other_configs(args):
             "ba_learned_1e6": ["--workload", "ba_learned", "--steps", "20", "--warmup", "3", "--ess-sweeps", "0"]}
     out = {}
     for name, extra in runs.items():
-        cmd = [sys.executable, os.path.abspath(__file__)] + extra + ["--no-configs", "--seed", str(args.seed)]
+        cmd = [sys.executable, os.path.abspath(__file__)] + extra + ["--no-configs", "--seed", str(args.seed),
+                                                                     "--cpu-seconds", "5"]
         if args.no_cpu:
             cmd.append("--no-cpu")
         try:
