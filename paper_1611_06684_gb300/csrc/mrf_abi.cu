@@ -1577,7 +1577,12 @@ void drop_batch_graphs(mrf_batch_t* b) {
     b->q_ready = false;
 }
 
-void free_queue(mrf_batch_t* b) {
+// Frees the queue; with keep_mirror, the class handles' host mirrors are read
+// back first (the live-edge counter they would report goes away).
+void free_queue(mrf_batch_t* b, bool keep_mirror = true) {
+    if (keep_mirror)
+        for (mrf_t* hk : b->h)
+            if (hk->mirror_stale && sync_mirror(hk) != MRF_OK) hk->err.clear();
     dfree(b->dq_rm_graph); dfree(b->dq_rm_slot); dfree(b->dq_add_graph); dfree(b->dq_add_src); dfree(b->dq_add_dst);
     dfree(b->dq_pair); dfree(b->dq_counts); dfree(b->dq_out); dfree(b->dq_status); dfree(b->dq_blk);
     dfree(b->dq_toolong); dfree(b->dq_g); dfree(b->dq_cls);
@@ -1647,7 +1652,7 @@ mrf_status mrf_batch_create(mrf_batch_t** out, int32_t n_graphs, const int32_t* 
 void mrf_batch_destroy(mrf_batch_t* b) {
     if (!b) return;
     drop_batch_graphs(b);
-    free_queue(b);
+    free_queue(b, false);
     for (auto* hk : b->h) mrf_destroy(hk);
     delete b;
 }

@@ -782,8 +782,19 @@ __global__ void __launch_bounds__(256) k_edge_partial(SweepArgs a) {
     }
     for (int c = 0; c < C; ++c) {
         const uint32_t* th = a.theta + (e * C + c) * W;
+        uint32_t bw[W];
+        if constexpr (W % 4 == 0) {                        // the edge-chain's words in 16-byte loads
 #pragma unroll
-        for (int g = 0; g < W; ++g) s_t[warp][32 * g + lane] = ((__ldcs(th + g) >> lane) & 1u) ? tv[g] : 0.0f;
+            for (int g = 0; g < W; g += 4) {
+                const uint4 q = __ldcs(reinterpret_cast<const uint4*>(th + g));
+                bw[g] = q.x; bw[g + 1] = q.y; bw[g + 2] = q.z; bw[g + 3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int g = 0; g < W; ++g) bw[g] = __ldcs(th + g);
+        }
+#pragma unroll
+        for (int g = 0; g < W; ++g) s_t[warp][32 * g + lane] = ((bw[g] >> lane) & 1u) ? tv[g] : 0.0f;
         __syncwarp();
         float* pe = a.part + ((e * C + c) * 2) * L;
         if (lane < L) {                                    // row `lane`: source side

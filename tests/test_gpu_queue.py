@@ -180,6 +180,10 @@ def test_queue_round_of_many_sweeps_and_host_edit_in_between():
     assert st == 0
     for g in range(len(models)):
         assert np.array_equal(bq.get_labels(g), bh.get_labels(g))
+    # a new queue replaces the old one; the classes' edge counts stay right
+    bq.queue_create(16, 16, 16 * 64, 8)
+    for k in range(bq.n_classes()):
+        assert bq.class_handle(k).info().n_edges == bh.class_handle(k).info().n_edges
     for b in (bq, bn, bh):
         b.close()
 
