@@ -167,6 +167,11 @@ def kernel_work(name, model_info, C):
 # for 774,144 x 64 items.
 DUAL_DRAM_BYTES_PER_ITEM = {(49, 64): (327740928 + 349712896) / (774144 * 64)}
 
+# DRAM bytes of the batched workload's partial-field pass per live edge, from
+# ncu counters of a 30-graph L = 16 batch (1,691,481 edges: 1,604.7 MB read +
+# 208.9 MB written per launch); keyed by (entries per edge, chains).
+EDGE_PARTIAL_DRAM_BYTES_PER_EDGE = {(225, 1): (1604725000 + 208856832) / 1691481}
+
 # kernels behind one kernel-timing record of the library
 KERNELS_PER_RECORD = {"k_sw_draw": 2}
 
@@ -738,8 +743,12 @@ def run_batch_workload(args):
     minfo = dict(E=row["edges"], N=row["sites"], L=row["L"], m=row["dual_bits_per_edge"],
                  partial=C <= 4 and row["dual_bits_per_edge"] >= 100)
     _, nbytes = kernel_work(name, minfo, C)
+    per_edge = EDGE_PARTIAL_DRAM_BYTES_PER_EDGE.get((row["dual_bits_per_edge"], C)) if name == "k_edge_partial" else None
     roof = {"bound": "hbm", "achieved": nbytes / (dom_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "traffic": None, "kernel": f"{name} (class L={row['L']})", "bytes_per_launch": nbytes,
+            "traffic": per_edge * row["edges"] if per_edge else None,
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_edge_partial on a 30-graph "
+                               "L = 16 batch, scaled by live edges") if per_edge else None,
+            "kernel": f"{name} (class L={row['L']})", "bytes_per_launch": nbytes,
             "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     # the whole sweep against the method's own minimum (each class's tables read once, labels, incidence lists)
