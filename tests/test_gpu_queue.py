@@ -288,3 +288,41 @@ def test_queue_sorts_long_incidence_lists_on_device():
         assert np.array_equal(bq.get_labels(0), bh.get_labels(0)), rnd
     assert int((m.src == 0).sum() + (m.dst == 0).sum()) > 512
     bq.close(); bh.close()
+
+
+def test_queue_with_zero_capacity_and_edge_partial_classes():
+    """A queue of capacity zero makes rounds plain sweeps; a batch whose
+    classes take the edge-partial plain sweep (one chain, L = 12 and 16:
+    121 and 225 entries per edge) gives the same chain with queue rounds as
+    with host edits."""
+    torch = pytest.importorskip("torch")
+    stream = torch.cuda.Stream()
+    specs = wl.er_batch_specs(6, n_min=60, n_max=500, labels=(12, 16), seed=21)
+    models = [wl.er_graph(s) for s in specs]
+    bz = _batch(models, 1, 4, stream)
+    bp = _batch(models, 1, 4, stream)
+    bz.queue_create(0, 0, 0, 0)
+    bz.round(3); bp.sweep(3)
+    st, _ = bz.queue_result(0)
+    assert st == 0
+    for g in range(len(models)):
+        assert np.array_equal(bz.get_labels(g), bp.get_labels(g))
+    bz.close(); bp.close()
+    bq = _batch(models, 1, 4, stream)
+    bh = _batch(models, 1, 4, stream)
+    for g, m in enumerate(models):
+        m.slots = np.arange(m.n_edges) + bq.graph(g).first_edge_slot
+    bq.queue_create(1024, 1024, 1024 * 256, 64)
+    rng = np.random.default_rng(8)
+    for rnd in range(3):
+        arrays, pend = _edit(models, 0.04, rng, diag_L=0)
+        bq.queue_load(*arrays)
+        bq.round(4)
+        st, new = bq.queue_result(len(arrays[3]))
+        assert st == 0
+        assert np.array_equal(bh.edit_factors(*arrays), new)
+        bh.sweep(4)
+        _apply(models, pend, new)
+        for g in range(len(models)):
+            assert np.array_equal(bq.get_labels(g), bh.get_labels(g)), (rnd, g)
+    bq.close(); bh.close()
