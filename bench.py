@@ -722,9 +722,12 @@ def run_batch_workload(args):
     for kk in range(b.n_classes()):
         hk = b.class_handle(kk)
         inf = hk.info()
-        kt = {n: v[0] / v[1] for n, v in hk.kernel_times().items()}
+        raw = hk.kernel_times()
+        kt = {n: v[0] / v[1] for n, v in raw.items()}
         row = {"L": hk.L, "sites": hk.N, "edges": int(inf.n_edges), "edge_slots": int(inf.n_edge_slots),
-               "dual_bits_per_edge": int(inf.n_entries), "kernels_ms": kt}
+               "dual_bits_per_edge": int(inf.n_entries), "kernels_ms": kt,
+               "launches_per_sweep": sum(v[1] for v in raw.values()) / 3 + 1,          # + k_advance (not timed)
+               "two_label_unaries": hk.L == 2}
         per_class.append(row)
         for name, ms in kt.items():
             if dom is None or ms > dom[2]:
@@ -760,7 +763,10 @@ def run_batch_workload(args):
                           "counted": "tables once (4 B per dual entry), endpoints (8 B) and two incidence records "
                                      "(16 B) per edge, unaries (4 B per label) and labels in and out per site"}
     K = b.n_classes()
-    launches_per_round = 4 + 15 * K + 1 + sweeps_per_round * 4 * K
+    # the edit: route (4 kernels), per class 15 (remove, slot rule 3, place, decomposition, planes, incidence
+    # lists 6, long lists, refold) and one more where Swendsen-Wang unaries exist, finish (1); then the sweeps
+    launches_per_round = int(round(4 + sum(15 + r["two_label_unaries"] for r in per_class) + 1
+                                   + sweeps_per_round * sum(r["launches_per_sweep"] for r in per_class)))
     cpu = None if args.no_cpu else batch_cpu_baseline(models, args.seed, args.cpu_seconds)
     return {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_round, "higher_is_better": True, "scaling": "weak",
