@@ -706,7 +706,9 @@ __global__ void __launch_bounds__(256) k_primal_cta(SweepArgs a, int CG) {
         int chunk = 0;
         // B incidences of the slice per iteration, their records and theta words
         // loaded before any is added (same order of additions)
-        constexpr int B = E::W <= 2 ? 4 : 2;            // 8 for one word: 62 registers, 1.40 vs 1.12 ms (N = 4096)
+        // (8 for one word: 62 registers, 1.40 vs 1.12 ms at N = 4096; staging a site's records in
+        // shared memory first: 1.14 ms, no gain)
+        constexpr int B = E::W <= 2 ? 4 : 2;
         for (int64_t p = p0 + slice; p < p1; p += (int64_t)B * S) {
             int2 ic[B];
             uint32_t bits[B][E::W];
