@@ -450,11 +450,12 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
 // FUSED = false: read theta written by k_dual.  FUSED = true: regenerate it.
 // POT = true (blocked sweep): write the node potentials F to a.pot instead of
 // drawing labels.
-// Blocks per SM: with 64 registers the field arrays of wide tables spill (L = 9: 354 B, L = 16: 702 B),
-// so L = 9..11 take 3 and L >= 12 two blocks (not timed); L = 8 keeps 4 (28 B spilled), measured faster
-// than 3 (0.386 vs 0.403 ms, one chain, the batched workload's L = 8 class at 300 graphs).
+// Four blocks per SM even where the field arrays of wide tables spill at 64
+// registers (L = 9: 354 B, L = 16: 702 B): fewer blocks measured slower (L = 8,
+// one chain: 0.403 vs 0.386 ms; L = 10, 8 chains: 0.68 vs 0.60 ms; L = 12, 16
+// chains: 0.39 vs 0.26 ms; L = 16, 8 chains: 2.22 vs 1.34 ms).
 template <int L, int LAYOUT, bool FUSED, bool POT = false>
-__global__ void __launch_bounds__(256, FUSED ? 2 : (L >= 12 ? 2 : (L >= 9 ? 3 : 4))) k_primal(SweepArgs a) {
+__global__ void __launch_bounds__(256, FUSED ? 2 : 4) k_primal(SweepArgs a) {
     using E = Ent<L, LAYOUT>;
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;     // N * C < 2^32 (checked by the host)
     if (g >= (uint64_t)a.N * a.C) return;
