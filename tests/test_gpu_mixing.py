@@ -33,9 +33,13 @@ The paper reports ratios of 2 to 7 on the grid and improved mixing (in sweeps
 against single-site updates) on the fully connected model.  Checked here: the
 mixing times are finite, the primal-dual sampler needs at least as many
 sweeps as the sequential one on the grid and the random graphs (the blocking
-argument at the end of Section 5.4), and it needs fewer sweeps than the
-sequential sampler needs single-site updates on the fully connected model.
+argument at the end of Section 5.4), on the grid by a ratio inside the
+paper's band of 2 to 7 (tests/golden/section6_mixing.json), and it needs
+fewer sweeps than the sequential sampler needs single-site updates on the
+fully connected model.
 """
+import json
+import os
 import time
 
 import numpy as np
@@ -49,6 +53,8 @@ pytestmark = pytest.mark.gpu
 C = 10
 THRESHOLD = 1.01
 EVERY = 10
+# the paper's Section 6 numbers (tests/golden/section6_mixing.json, with its citation)
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "section6_mixing.json")))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -112,6 +118,8 @@ def test_ising_grid_mixing_ratio(beta):
           f"ratio {None if not (mt_pd and mt_seq) else round(mt_pd / mt_seq, 2)} ({time.time() - t0:.1f} s)")
     assert mt_pd is not None and mt_seq is not None
     assert mt_pd >= mt_seq
+    lo, hi = GOLDEN["ising_grid"]["mixing_time_ratio_primal_dual_over_sequential"]
+    assert lo <= mt_pd / mt_seq <= hi, (mt_pd, mt_seq)
 
 
 @pytest.mark.parametrize("k", [2])
