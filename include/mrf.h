@@ -354,7 +354,11 @@ mrf_status mrf_batch_edit_factors(mrf_batch_t* b, int64_t n_remove, const int32_
                                   const int64_t* remove_slot, int64_t n_add, const int32_t* add_graph,
                                   const int32_t* src, const int32_t* dst, const float* pair_log, int64_t* out_slots);
 
-/* n_sweeps sweeps of every graph (MRF_MODE_PLAIN or MRF_MODE_FUSED). */
+/* n_sweeps sweeps of every graph: MRF_MODE_PLAIN or MRF_MODE_FUSED (one CUDA
+ * graph per sweep with options.use_graphs and a stream), or the cluster sweeps
+ * MRF_MODE_SW / MRF_MODE_HIGDON, run class by class as mrf_sweep runs them on
+ * one handle (same requirements: two labels or Potts-type tables; the failing
+ * class is named in mrf_batch_last_error). */
 mrf_status mrf_batch_sweep(mrf_batch_t* b, int32_t n_sweeps, int32_t mode);
 
 /* ---- Device edit queue of a batch (dynamic networks: abstract, Section 6) ----

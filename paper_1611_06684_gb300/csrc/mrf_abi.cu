@@ -1770,8 +1770,17 @@ mrf_status mrf_batch_edit_factors(mrf_batch_t* b, int64_t n_remove, const int32_
 
 mrf_status mrf_batch_sweep(mrf_batch_t* b, int32_t n_sweeps, int32_t mode) {
     if (!b) return MRF_EINVAL;
-    if (n_sweeps < 0 || (mode != MRF_MODE_PLAIN && mode != MRF_MODE_FUSED)) return bfail(b, MRF_EINVAL, "bad sweep count or mode");
     const int K = (int)b->h.size();
+    if (n_sweeps >= 0 && (mode == MRF_MODE_SW || mode == MRF_MODE_HIGDON)) {
+        // cluster sweeps (Section 4.3): each class as its own handle would run them
+        for (int k = 0; k < K; ++k) {
+            if (!b->h[k]->has_factors) return bfail(b, MRF_ESTATE, "mrf_batch_set_factors first");
+            mrf_status st = mrf_sweep(b->h[k], n_sweeps, mode);
+            if (st != MRF_OK) return class_status(b, k, st);
+        }
+        return MRF_OK;
+    }
+    if (n_sweeps < 0 || (mode != MRF_MODE_PLAIN && mode != MRF_MODE_FUSED)) return bfail(b, MRF_EINVAL, "bad sweep count or mode");
     for (int k = 0; k < K; ++k) {
         if (!b->h[k]->has_factors) return bfail(b, MRF_ESTATE, "mrf_batch_set_factors first");
         if (mode == MRF_MODE_PLAIN && b->h[k]->schedule == 0 && n_sweeps > 0) {

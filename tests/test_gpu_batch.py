@@ -202,3 +202,33 @@ def test_full_batch_2000_graphs_sampled_graphs_match_oracle():
                 pos += len(s_new)
     assert checked == 2 * len(sample)
     b.close()
+
+
+@pytest.mark.parametrize("mode", [M.MODE_SW, M.MODE_HIGDON])
+def test_batch_cluster_sweeps_equal_one_handle_per_class(mode):
+    """Swendsen-Wang and Higdon sweeps of a batch (ferromagnetic graphs, two
+    label classes) equal the same sweeps of one handle on each class union
+    with the class's key, bit for bit (the union handle is checked against
+    the oracle in tests/test_gpu_sw.py and tests/test_gpu_higdon.py)."""
+    torch = pytest.importorskip("torch")
+    models = [wl.ferro_potts_graph(n, L, e, seed=s) for n, L, e, s in
+              ((60, 2, 150, 1), (90, 3, 200, 2), (40, 2, 90, 3), (70, 3, 160, 4))]
+    C, seed = 4, 19
+    stream = torch.cuda.Stream()
+    b = M.MRFBatch([m.n_vars for m in models], [m.n_labels for m in models], C, seed=seed,
+                   stream=stream.cuda_stream)
+    b.set_factors(models)
+    b.sweep(2, M.MODE_PLAIN)
+    b.sweep(3, mode)
+    for L in (2, 3):
+        ids = [g for g, m in enumerate(models) if m.n_labels == L]
+        un = _union(models, ids)
+        h = M.MRF(un.n_vars, L, C, seed=(seed + L * M.BATCH_KEY_STEP) & (2**64 - 1), use_graphs=False)
+        h.set_factors(un.unary, un.src, un.dst, un.pair)
+        h.sweep(2, M.MODE_PLAIN)
+        h.sweep(3, mode)
+        x = h.get_labels()
+        h.close()
+        xb = np.concatenate([b.get_labels(g) for g in ids], axis=1)
+        assert np.array_equal(xb, x), (L, mode)
+    b.close()
