@@ -365,14 +365,14 @@ def run_ours(args, ws, rank, local):
             variants["ess"] = tv_protocol(tvm, C, stream, tv_forms, args.seed + 17, args.tv_ref_sweeps,
                                           workload=_describe(args.workload).replace("128^3", f"{n}^3"))
             if args.workload == "potts3d":
-                # the benchmark spec comparisons: the learned proposal and the batched launch
+                # the target comparisons: the learned proposal and the batched launch
                 # against the plain dual sweep, each in ESS/s at marginal TV <= 0.01
                 variants["ess"]["learned"] = learned_tv_comparison(stream, args.tv_ba_sites, 512, args.seed + 23,
                                                                    args.tv_ba_ref_sweeps)
                 variants["ess"]["batched"] = small_batch_tv_comparison(stream, args.tv_batch_graphs, C, args.seed + 29)
                 variants["ess"]["batched_er"] = batch_tv_comparison(stream, 20, C, args.seed + 31, 50000,
                                                                     tv_target=0.0)
-                variants["ess"]["north_star"] = {
+                variants["ess"]["targets"] = {
                     "learned_vs_plain": variants["ess"]["learned"]["versus_plain"]["learned"],
                     "learned+plain_vs_plain": variants["ess"]["learned"]["versus_plain"]["learned+plain"],
                     "batched_vs_plain_at_tv": variants["ess"]["batched"]["versus_plain"]["batched"],
