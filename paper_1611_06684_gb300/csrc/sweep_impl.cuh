@@ -1150,8 +1150,8 @@ cudaError_t run_dual(const SweepArgs& a, cudaStream_t s) {
     const int64_t n = a.E * a.C;
     if (n <= 0) return cudaSuccess;
     // few chains and wide tables (two groups per warp): 128 registers and two blocks per SM; at 64
-    // registers the 8-word form spills (224 B), and with one chain (1.69 M edges, L = 16) it
-    // measured 5.14 vs 4.12 ms per sweep at the 2,000-graph batch
+    // registers the 8-word form spills (224 B); with one chain on 25.2 M edges of L = 16 (the
+    // 2,000-graph batch's largest class) it measured 5.14 vs 4.12 ms per sweep
     if (a.C < 32 && T::NG <= 2)
         k_dual<L, LAYOUT, true><<<blocks_for(n, 32 * T::NG * T::WARPS), 32 * T::WARPS, 0, s>>>(a);
     else
